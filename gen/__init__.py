@@ -1,0 +1,454 @@
+"""Seeded synthetic inputs for the multifrontal Cholesky path.
+
+This module is shared by the oracle tests, the GPU tests and the benchmark.
+It builds matrices, orderings and right-hand sides only; it contains no part
+of the factorization or solve arithmetic.
+
+Matrices are returned as full symmetric CSR triples ``(rowptr int64, colind
+int32, values float64)`` with sorted column indices.  Orderings are returned as
+``perm`` with ``perm[new] = old`` (so ``C = A[perm][:, perm]``).
+
+The workloads stand in for the paper's Albany land-ice meshes and the Xyce
+matrices, which are not available (paper Sec. 5, experiment setup):
+
+* ``laplacian_2d``      -- 5-point Dirichlet Laplacian (diag 4, off -1).
+* ``laplacian_3d``      -- 7-point Dirichlet Laplacian, optional coefficient
+                           jumps per 8^3 block with harmonic-mean edge weights.
+* ``q1_extruded``       -- extruded Q1 hexahedral mesh carrying the symmetric
+                           first-order-Stokes (Blatter-Pattyn) velocity form with
+                           two horizontal components per node plus a basal
+                           friction term, the ice-sheet-like stand-in.
+* ``nd_perm``           -- geometric nested dissection on a node grid.
+* ``box_batch``         -- many independent 3D Laplacian boxes (a batch of
+                           subdomains), as a block-diagonal matrix.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "laplacian_1d", "laplacian_2d", "laplacian_3d", "q1_extruded", "nd_perm",
+    "random_spd", "rhs", "box_batch", "block_diag_csr", "csr_matvec",
+    "config1", "config2", "config3", "config5",
+]
+
+
+# --------------------------------------------------------------------------
+# CSR helpers (no factorization arithmetic)
+# --------------------------------------------------------------------------
+def _coo_to_csr(n, rows, cols, vals):
+    """Sum duplicates and return sorted full CSR."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    key = rows * n + cols
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    vals = vals[order]
+    uniq, start = np.unique(key, return_index=True)
+    summed = np.add.reduceat(vals, start) if len(vals) else vals
+    r = uniq // n
+    c = (uniq % n).astype(np.int32)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, c, summed.astype(np.float64)
+
+
+def csr_matvec(rowptr, colind, values, x):
+    """y = A x for CSR A (x may be 1D or 2D column-major-ish (n, nrhs))."""
+    n = len(rowptr) - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    x = np.asarray(x)
+    if x.ndim == 1:
+        return np.bincount(rows, weights=values * x[colind], minlength=n)
+    out = np.zeros((n, x.shape[1]))
+    for r in range(x.shape[1]):
+        out[:, r] = np.bincount(rows, weights=values * x[colind, r], minlength=n)
+    return out
+
+
+def block_diag_csr(mats):
+    """Block-diagonal union of CSR matrices (batch of independent subdomains)."""
+    rowptrs, cols, vals = [], [], []
+    off_n = 0
+    off_nnz = 0
+    for (rp, ci, v) in mats:
+        n = len(rp) - 1
+        rowptrs.append(rp[:-1] + off_nnz)
+        cols.append(ci.astype(np.int64) + off_n)
+        vals.append(v)
+        off_n += n
+        off_nnz += rp[-1]
+    rowptr = np.concatenate(rowptrs + [np.array([off_nnz], dtype=np.int64)])
+    return rowptr.astype(np.int64), np.concatenate(cols).astype(np.int32), np.concatenate(vals)
+
+
+# --------------------------------------------------------------------------
+# Structured stencil matrices
+# --------------------------------------------------------------------------
+def laplacian_1d(n):
+    """Tridiagonal [-1, 2, -1] (Dirichlet), natural order."""
+    i = np.arange(n)
+    rows = np.concatenate([i, i[1:], i[:-1]])
+    cols = np.concatenate([i, i[:-1], i[1:]])
+    vals = np.concatenate([np.full(n, 2.0), np.full(n - 1, -1.0), np.full(n - 1, -1.0)])
+    return _coo_to_csr(n, rows, cols, vals)
+
+
+def _grid_laplacian(shape, kappa=None):
+    """Nodal-coefficient Dirichlet Laplacian on a grid (x fastest).
+
+    Edge weight between neighbours i, j is the harmonic mean
+    2 k_i k_j / (k_i + k_j); each missing (boundary) neighbour adds k_i to the
+    diagonal.  With k == 1 this is the standard 2d+1 point Laplacian with
+    diagonal 2d and off-diagonal -1.
+    """
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    n = int(np.prod(shape))
+    if kappa is None:
+        kappa = np.ones(n)
+    kappa = np.asarray(kappa, dtype=np.float64).reshape(-1)
+    # node index = x + Nx*(y + Ny*z)  (x fastest); numpy arrays indexed [z, y, x]
+    grid = np.arange(n).reshape(shape[::-1])
+    kg = kappa.reshape(shape[::-1])
+    diag = np.zeros(shape[::-1])
+    rows, cols, vals = [], [], []
+    for ax in range(nd):
+        npax = nd - 1 - ax  # numpy axis of grid axis `ax`
+        sl_a = [slice(None)] * nd
+        sl_b = [slice(None)] * nd
+        sl_a[npax] = slice(0, shape[ax] - 1)
+        sl_b[npax] = slice(1, shape[ax])
+        ia = grid[tuple(sl_a)].ravel()
+        ib = grid[tuple(sl_b)].ravel()
+        ka = kg[tuple(sl_a)]
+        kb = kg[tuple(sl_b)]
+        w = 2.0 * ka * kb / (ka + kb)
+        diag[tuple(sl_a)] += w
+        diag[tuple(sl_b)] += w
+        w = w.ravel()
+        rows += [ia, ib]
+        cols += [ib, ia]
+        vals += [-w, -w]
+        # boundary (Dirichlet) contributions: first and last layer along ax
+        lo = [slice(None)] * nd
+        hi = [slice(None)] * nd
+        lo[npax] = slice(0, 1)
+        hi[npax] = slice(shape[ax] - 1, shape[ax])
+        diag[tuple(lo)] += kg[tuple(lo)]
+        diag[tuple(hi)] += kg[tuple(hi)]
+    idx = grid.ravel()
+    rows.append(idx)
+    cols.append(idx)
+    vals.append(diag.ravel())
+    return _coo_to_csr(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def laplacian_2d(nx, ny=None):
+    """5-point Dirichlet Laplacian on nx*ny nodes: diagonal 4, off-diagonal -1."""
+    ny = nx if ny is None else ny
+    return _grid_laplacian((nx, ny))
+
+
+def laplacian_3d(nx, ny=None, nz=None, jump_block=None, jump_value=1e3, seed=None):
+    """7-point Dirichlet Laplacian on nx*ny*nz nodes.
+
+    With ``jump_block=b`` the nodal coefficient is constant on b^3 blocks and is
+    1 or ``jump_value`` with probability 1/2 each (seeded), edge weights are
+    harmonic means.
+    """
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    kappa = None
+    if jump_block is not None:
+        rng = np.random.default_rng(seed)
+        bx, by, bz = (-(-nx // jump_block), -(-ny // jump_block), -(-nz // jump_block))
+        blocks = np.where(rng.random((bz, by, bx)) < 0.5, 1.0, float(jump_value))
+        z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        kappa = blocks[z // jump_block, y // jump_block, x // jump_block].ravel()
+    return _grid_laplacian((nx, ny, nz), kappa)
+
+
+# --------------------------------------------------------------------------
+# Extruded Q1 mesh with the first-order Stokes (Blatter-Pattyn) velocity form
+# --------------------------------------------------------------------------
+def _q1_reference_matrices(hx, hy, hz):
+    """Element matrices of a hx*hy*hz trilinear brick (2x2x2 Gauss).
+
+    Returns (K, M) where K (16x16) is the viscous form for mu = 1 with dof
+    ordering (local node, component) and M (8x8) is the bottom-face mass matrix
+    (only nodes with c == 0 nonzero).
+
+    Bilinear form for velocity (u, v) and test (phi, psi):
+        2 mu [ (2u_x + v_y) phi_x + (u_y + v_x)/2 phi_y + u_z/2 phi_z
+             + (u_y + v_x)/2 psi_x + (u_x + 2v_y) psi_y + v_z/2 psi_z ]
+    which is symmetric and positive semi-definite.
+    """
+    g = np.array([0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)])
+    wq = 0.5
+    local = [(a, b, c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+
+    def l(t, a):
+        return t if a else 1.0 - t
+
+    def dl(a):
+        return 1.0 if a else -1.0
+
+    K = np.zeros((16, 16))
+    vol = hx * hy * hz
+    for qx in g:
+        for qy in g:
+            for qz in g:
+                w = wq ** 3 * vol
+                grads = []
+                for (a, b, c) in local:
+                    gx = dl(a) / hx * l(qy, b) * l(qz, c)
+                    gy = l(qx, a) * dl(b) / hy * l(qz, c)
+                    gz = l(qx, a) * l(qy, b) * dl(c) / hz
+                    grads.append((gx, gy, gz))
+                for p in range(8):
+                    px, py, pz = grads[p]
+                    for q in range(8):
+                        qx_, qy_, qz_ = grads[q]
+                        # (alpha, beta) = (0,0): 4 Nq_x Np_x + Nq_y Np_y + Nq_z Np_z
+                        K[2 * p, 2 * q] += w * (4 * qx_ * px + qy_ * py + qz_ * pz)
+                        # (1,1): Nq_x Np_x + 4 Nq_y Np_y + Nq_z Np_z
+                        K[2 * p + 1, 2 * q + 1] += w * (qx_ * px + 4 * qy_ * py + qz_ * pz)
+                        # test comp 0, trial comp 1: 2 Nq_y Np_x + Nq_x Np_y
+                        K[2 * p, 2 * q + 1] += w * (2 * qy_ * px + qx_ * py)
+                        # test comp 1, trial comp 0: 2 Nq_x Np_y + Nq_y Np_x
+                        K[2 * p + 1, 2 * q] += w * (2 * qx_ * py + qy_ * px)
+    M = np.zeros((8, 8))
+    area = hx * hy
+    for qx in g:
+        for qy in g:
+            w = wq ** 2 * area
+            vals = [l(qx, a) * l(qy, b) * (1.0 if c == 0 else 0.0) for (a, b, c) in local]
+            for p in range(8):
+                for q in range(8):
+                    M[p, q] += w * vals[p] * vals[q]
+    return K, M
+
+
+def q1_extruded(ex, ey, ez, hx=1.0, hy=1.0, hz=0.01, beta=1.0, seed=1):
+    """Extruded Q1 hexahedral mesh, 2 velocity dofs per node (interleaved).
+
+    ex*ey*ez elements, (ex+1)*(ey+1)*(ez+1) nodes, node index x fastest, dof =
+    2*node + component.  Per-element viscosity mu_e = 10**U[-2, 0] (seeded).
+    A basal friction term beta * int_{z=0} (u phi + v psi) makes the form SPD.
+    Matrix entries between nodes sharing an element are stored even where the
+    value cancels (structural pattern = 27-point stencil x 2x2 dof blocks).
+    """
+    rng = np.random.default_rng(seed)
+    mu = 10.0 ** rng.uniform(-2.0, 0.0, size=(ez, ey, ex))
+    K, M = _q1_reference_matrices(hx, hy, hz)
+    Nx, Ny, Nz = ex + 1, ey + 1, ez + 1
+    nn = Nx * Ny * Nz
+    n = 2 * nn
+    local = [(a, b, c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+    lidx = {t: i for i, t in enumerate(local)}
+    offs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    # values[z, y, x, d, alpha, beta]
+    val = np.zeros((Nz, Ny, Nx, 27, 2, 2))
+    # pad mu with zeros outside the element range
+    mup = np.zeros((ez + 2, ey + 2, ex + 2))
+    mup[1:-1, 1:-1, 1:-1] = mu
+    basal = np.zeros((ez + 2, ey + 2, ex + 2))
+    basal[1, 1:-1, 1:-1] = beta  # elements in the bottom layer (ez index 0)
+    Z, Y, X = np.meshgrid(np.arange(Nz), np.arange(Ny), np.arange(Nx), indexing="ij")
+    for di, (dx, dy, dz) in enumerate(offs):
+        for (a, b, c) in local:
+            qa, qb, qc = a + dx, b + dy, c + dz
+            if not (0 <= qa <= 1 and 0 <= qb <= 1 and 0 <= qc <= 1):
+                continue
+            # element containing node p at local position (a,b,c): e = p - (a,b,c)
+            m_e = mup[Z - c + 1, Y - b + 1, X - a + 1]
+            f_e = basal[Z - c + 1, Y - b + 1, X - a + 1]
+            p = lidx[(a, b, c)]
+            q = lidx[(qa, qb, qc)]
+            for al in range(2):
+                for be in range(2):
+                    val[:, :, :, di, al, be] += m_e * K[2 * p + al, 2 * q + be]
+                    if al == be:
+                        val[:, :, :, di, al, be] += f_e * M[p, q]
+    # structural validity of each neighbour
+    valid = np.zeros((Nz, Ny, Nx, 27), dtype=bool)
+    for di, (dx, dy, dz) in enumerate(offs):
+        valid[:, :, :, di] = ((X + dx >= 0) & (X + dx < Nx) & (Y + dy >= 0) & (Y + dy < Ny)
+                              & (Z + dz >= 0) & (Z + dz < Nz))
+    node = (X + Nx * (Y + Ny * Z)).reshape(-1)
+    dnode = np.array([dx + Nx * (dy + Ny * dz) for (dx, dy, dz) in offs], dtype=np.int64)
+    valid = valid.reshape(nn, 27)
+    val = val.reshape(nn, 27, 2, 2)
+    counts = valid.sum(axis=1) * 2  # entries per dof row
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    rowptr[1::2] = counts
+    rowptr[2::2] = counts
+    rowptr = np.cumsum(rowptr)
+    nnz = int(rowptr[-1])
+    colind = np.empty(nnz, dtype=np.int32)
+    values = np.empty(nnz, dtype=np.float64)
+    # columns per node row: for each valid neighbour (sorted by node), beta 0,1
+    qnode = node[:, None] + dnode[None, :]  # (nn, 27), increasing along axis 1
+    for al in range(2):
+        cols_full = np.stack([2 * qnode, 2 * qnode + 1], axis=2)  # (nn, 27, 2)
+        vals_full = val[:, :, al, :]
+        mask = np.repeat(valid[:, :, None], 2, axis=2)
+        cflat = cols_full[mask]
+        vflat = vals_full[mask]
+        # rows 2*node+al occupy contiguous segments; masks keep row-major order
+        starts = rowptr[2 * node + al]
+        lens = counts
+        dst = np.repeat(starts - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens) + np.arange(lens.sum())
+        colind[dst] = cflat.astype(np.int32)
+        values[dst] = vflat
+    return rowptr, colind, values
+
+
+# --------------------------------------------------------------------------
+# Geometric nested dissection
+# --------------------------------------------------------------------------
+def nd_perm(shape, split_axes=None, leaf_nodes=8, dofs=1):
+    """Geometric nested dissection ordering of a node grid (x fastest).
+
+    A box is a leaf when it holds <= ``leaf_nodes`` nodes or no splittable axis
+    has extent >= 3.  Otherwise it is split along its longest splittable axis
+    (ties -> lowest axis index) at mid = lo + size//2; the order is: left part,
+    right part, then the separator plane, each plane/leaf in lexicographic
+    (x fastest) order.  With ``dofs > 1`` the dofs of a node are consecutive.
+    Returns perm with perm[new] = old.
+    """
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    if split_axes is None:
+        split_axes = tuple(range(nd))
+    strides = [1]
+    for s in shape[:-1]:
+        strides.append(strides[-1] * s)
+    out = []
+
+    def box_nodes(lo, hi):
+        rngs = [np.arange(lo[a], hi[a]) for a in range(nd)]
+        mesh = np.meshgrid(*rngs[::-1], indexing="ij")  # slowest axis first
+        idx = np.zeros(mesh[0].shape, dtype=np.int64)
+        for a in range(nd):
+            idx += mesh[nd - 1 - a] * strides[a]
+        return idx.ravel()
+
+    # iterative post-order traversal: (lo, hi, state)
+    stack = [(tuple(0 for _ in shape), shape, 0, None)]
+    while stack:
+        lo, hi, state, info = stack.pop()
+        size = [hi[a] - lo[a] for a in range(nd)]
+        if min(size) <= 0:
+            continue
+        if state == 0:
+            cand = [a for a in split_axes if size[a] >= 3]
+            if int(np.prod(size)) <= leaf_nodes or not cand:
+                out.append(box_nodes(lo, hi))
+                continue
+            ax = max(cand, key=lambda a: (size[a], -a))
+            mid = lo[ax] + size[ax] // 2
+            llo, lhi = list(lo), list(hi)
+            lhi[ax] = mid
+            rlo, rhi = list(lo), list(hi)
+            rlo[ax] = mid + 1
+            slo, shi = list(lo), list(hi)
+            slo[ax] = mid
+            shi[ax] = mid + 1
+            # push in reverse: separator (state 2), right, left
+            stack.append((tuple(slo), tuple(shi), 2, None))
+            stack.append((tuple(rlo), tuple(rhi), 0, None))
+            stack.append((tuple(llo), tuple(lhi), 0, None))
+        else:
+            out.append(box_nodes(lo, hi))
+    perm_nodes = np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
+    if dofs == 1:
+        return perm_nodes.astype(np.int32)
+    p = (perm_nodes[:, None] * dofs + np.arange(dofs)[None, :]).reshape(-1)
+    return p.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Random small SPD matrices (symbolic and numeric pins)
+# --------------------------------------------------------------------------
+def random_spd(n, density=0.1, seed=0, dense_rows=0):
+    """Random sparse SPD matrix: random symmetric pattern with a diagonal,
+    off-diagonal values U[-1,1], diagonal = row |sum| + U[0.5,1.5]."""
+    rng = np.random.default_rng(seed)
+    m = rng.random((n, n)) < density
+    m = np.triu(m, 1)
+    for r in range(min(dense_rows, n)):
+        m[r, r + 1:] = True
+    iu, ju = np.nonzero(m)
+    v = rng.uniform(-1.0, 1.0, size=len(iu))
+    rows = np.concatenate([iu, ju])
+    cols = np.concatenate([ju, iu])
+    vals = np.concatenate([v, v])
+    absrow = np.bincount(rows, weights=np.abs(vals), minlength=n)
+    d = absrow + rng.uniform(0.5, 1.5, size=n)
+    rows = np.concatenate([rows, np.arange(n)])
+    cols = np.concatenate([cols, np.arange(n)])
+    vals = np.concatenate([vals, d])
+    return _coo_to_csr(n, rows, cols, vals)
+
+
+def random_perm(n, seed=0):
+    return np.random.default_rng(seed).permutation(n).astype(np.int32)
+
+
+def rhs(n, nrhs=1, seed=0):
+    """Right-hand sides U[-1,1], shape (n,) or (n, nrhs), column-major usable."""
+    rng = np.random.default_rng(seed)
+    if nrhs == 1:
+        return rng.uniform(-1.0, 1.0, size=n)
+    return np.asfortranarray(rng.uniform(-1.0, 1.0, size=(n, nrhs)))
+
+
+def box_batch(count=512, lo=8, hi=48, seed=4, leaf_nodes=8):
+    """Batch of 7-point Laplacian boxes with sides U{lo..hi} per axis.
+
+    Returns (list of (rowptr, colind, values, perm), sides).
+    """
+    rng = np.random.default_rng(seed)
+    sides = rng.integers(lo, hi + 1, size=(count, 3))
+    out = []
+    for (a, b, c) in sides:
+        rp, ci, v = laplacian_3d(int(a), int(b), int(c))
+        perm = nd_perm((int(a), int(b), int(c)), leaf_nodes=leaf_nodes)
+        out.append((rp, ci, v, perm))
+    return out, sides
+
+
+# --------------------------------------------------------------------------
+# Named workloads
+# --------------------------------------------------------------------------
+def config1():
+    """2D 5-point Laplacian 64x64 (n=4096), geometric ND, b ~ U[-1,1] seed 0."""
+    rp, ci, v = laplacian_2d(64)
+    perm = nd_perm((64, 64))
+    return rp, ci, v, perm, rhs(64 * 64, 1, seed=0)
+
+
+def config2(ex=256, ey=256, ez=10):
+    """Extruded Q1 ice-sheet-like mesh, 2 dofs/node, ND on the horizontal plane."""
+    rp, ci, v = q1_extruded(ex, ey, ez, seed=1)
+    perm = nd_perm((ex + 1, ey + 1, ez + 1), split_axes=(0, 1), dofs=2)
+    n = len(rp) - 1
+    return rp, ci, v, perm, rhs(n, 1, seed=3)
+
+
+def config3(N=96, nrhs=1):
+    """7-point Laplacian N^3 with 8^3-block coefficient jumps {1, 1e3} (seed 2)."""
+    rp, ci, v = laplacian_3d(N, N, N, jump_block=8, jump_value=1e3, seed=2)
+    perm = nd_perm((N, N, N))
+    return rp, ci, v, perm, rhs(N ** 3, nrhs, seed=3)
+
+
+def config5(N=64, nrhs=1):
+    """Plain 7-point Laplacian N^3 (closed-form log-determinant available)."""
+    rp, ci, v = laplacian_3d(N, N, N)
+    perm = nd_perm((N, N, N))
+    return rp, ci, v, perm, rhs(N ** 3, nrhs, seed=5)

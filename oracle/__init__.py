@@ -1,0 +1,338 @@
+"""FP64 CPU oracle for the multifrontal Cholesky path -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library never does, and this
+package imports nothing from the library.
+
+What it computes (paper Sec. 5, Tacho: symbolic analysis, numerical
+factorization ``P A P^T = L L^T`` of an SPD matrix, forward/backward solve;
+the three phases of the paper's Ax=b statement in Sec. 2):
+
+* ``lower_rows`` / ``lower_cols`` -- the lower triangle of ``C = A(perm, perm)``
+  (``perm[new] = old``), duplicates summed.  Plain numpy.
+* ``etree``      -- ``parent(j) = min{i > j : L_ij != 0}`` (Liu's algorithm, C).
+* ``colcounts``  -- ``c_j = |struct(L_{*,j})|`` by row-subtree walks (C).
+* ``supernodes`` -- fundamental supernode partition (C).
+* ``factor``     -- left-looking column Cholesky, FP64 (C); optionally only the
+  columns of a descendant-closed set (exact for those columns).
+* ``solve``      -- ``x = P^T L^{-T} L^{-1} P b`` (C).
+* ``brute_symbolic`` -- dense boolean elimination on tiny inputs (pure Python),
+  an independent pin for etree / counts / nnz(L).
+* ``berr``, ``rel_fro`` -- the error measures used by the parity tests.
+
+Pins (tests/test_oracle.py): dense numpy Cholesky, the closed-form 1D
+Laplacian factor, the Dirichlet-Laplacian log-determinant, brute-force symbolic
+elimination and the etree/count invariants.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import time
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile the C oracle with the host compiler (portable flags only)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I = ctypes.c_int64
+        lib.orc_etree.argtypes = [I, P, P, P, P]
+        lib.orc_counts.argtypes = [I, P, P, P, P, P, P, P]
+        lib.orc_pattern.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_factor.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_factor.restype = ctypes.c_int64
+        lib.orc_supernodes.argtypes = [I, P, P, P, P]
+        lib.orc_supernodes.restype = ctypes.c_int64
+        lib.orc_solve.argtypes = [I, P, P, P, P, I, I]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------------------
+# Lower triangle of C = A(perm, perm)
+# ---------------------------------------------------------------------------
+def _lower_coo(rowptr, colind, values, perm):
+    n = len(rowptr) - 1
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    if perm is None:
+        iperm = np.arange(n, dtype=np.int64)
+    else:
+        perm = np.asarray(perm, dtype=np.int64)
+        iperm = np.empty(n, dtype=np.int64)
+        iperm[perm] = np.arange(n)
+    rows_old = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    i = iperm[rows_old]
+    j = iperm[np.asarray(colind, dtype=np.int64)]
+    keep = i >= j
+    v = None if values is None else np.asarray(values, dtype=np.float64)[keep]
+    return n, i[keep], j[keep], v
+
+
+def lower_rows(rowptr, colind, perm):
+    """Strict lower triangle of C by rows: (rp int64[n+1], ci int32), sorted, unique."""
+    n, i, j, _ = _lower_coo(rowptr, colind, None, perm)
+    strict = i > j
+    key = np.unique(i[strict] * n + j[strict])
+    r = key // n
+    c = (key % n).astype(np.int32)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, r + 1, 1)
+    return np.cumsum(rp), c
+
+
+def lower_cols(rowptr, colind, values, perm):
+    """Lower triangle of C (incl. diagonal) by columns, duplicates summed:
+    (Cp int64[n+1], Cr int32, Cx float64), rows ascending within a column."""
+    n, i, j, v = _lower_coo(rowptr, colind, values, perm)
+    key = j * n + i
+    order = np.argsort(key, kind="stable")
+    key = key[order]
+    v = v[order]
+    uniq, start = np.unique(key, return_index=True)
+    cx = np.add.reduceat(v, start) if len(v) else v
+    c = uniq // n
+    r = (uniq % n).astype(np.int32)
+    cp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(cp, c + 1, 1)
+    return np.cumsum(cp), r, cx
+
+
+# ---------------------------------------------------------------------------
+# Symbolic
+# ---------------------------------------------------------------------------
+def etree(n, rp, ci):
+    lib = _load()
+    parent = np.empty(n, dtype=np.int32)
+    anc = np.empty(n, dtype=np.int32)
+    lib.orc_etree(n, _p(rp), _p(ci), _p(parent), _p(anc))
+    return parent
+
+
+def counts(n, rp, ci, parent, in_s=None):
+    """(colcnt, rowcnt) restricted to columns in S (default: all)."""
+    lib = _load()
+    if in_s is None:
+        in_s = np.ones(n, dtype=np.uint8)
+    colcnt = np.empty(n, dtype=np.int64)
+    rowcnt = np.empty(n, dtype=np.int64)
+    mark = np.empty(n, dtype=np.int32)
+    lib.orc_counts(n, _p(rp), _p(ci), _p(parent), _p(in_s), _p(colcnt), _p(rowcnt), _p(mark))
+    return colcnt, rowcnt
+
+
+def colcounts(n, rp, ci, parent):
+    return counts(n, rp, ci, parent)[0]
+
+
+def supernodes(n, parent, colcnt):
+    lib = _load()
+    sup = np.empty(n + 1, dtype=np.int32)
+    nchild = np.empty(max(n, 1), dtype=np.int32)
+    ns = lib.orc_supernodes(n, _p(parent), _p(colcnt), _p(sup), _p(nchild))
+    return sup[: ns + 1].copy()
+
+
+def symbolic(rowptr, colind, perm):
+    """Dict with etree, colcounts, nnz(L), supernode partition and flops."""
+    n = len(rowptr) - 1
+    rp, ci = lower_rows(rowptr, colind, perm)
+    parent = etree(n, rp, ci)
+    cc = colcounts(n, rp, ci, parent)
+    sup = supernodes(n, parent, cc)
+    return {
+        "n": n, "parent": parent, "colcount": cc, "nnzL": int(cc.sum()),
+        "sup_ptr": sup, "flops": float(np.sum(cc.astype(np.float64) ** 2)),
+        "rows": (rp, ci),
+    }
+
+
+def brute_symbolic(rowptr, colind, perm):
+    """Dense boolean elimination on tiny inputs (n <= a few hundred).
+
+    Returns (parent, colcount).  Independent of the C routines above."""
+    n = len(rowptr) - 1
+    A = np.zeros((n, n), dtype=bool)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    A[rows, colind] = True
+    if perm is not None:
+        A = A[np.ix_(perm, perm)]
+    A = A | A.T
+    np.fill_diagonal(A, True)
+    B = np.tril(A)
+    for j in range(n):
+        below = np.nonzero(B[j + 1:, j])[0] + j + 1
+        for a in below:
+            B[a, below[below <= a]] = True
+    parent = np.full(n, -1, dtype=np.int32)
+    for j in range(n):
+        nz = np.nonzero(B[j + 1:, j])[0]
+        if len(nz):
+            parent[j] = j + 1 + nz[0]
+    return parent, B.sum(axis=0).astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Numeric
+# ---------------------------------------------------------------------------
+class Factor:
+    """L[:, S] in CSC form (Lp over all n columns; empty outside S)."""
+
+    def __init__(self, n, Lp, Li, Lx, bad_col, flops):
+        self.n, self.Lp, self.Li, self.Lx = n, Lp, Li, Lx
+        self.bad_col = bad_col
+        self.flops = flops
+
+    def column(self, j):
+        a, b = self.Lp[j], self.Lp[j + 1]
+        return self.Li[a:b], self.Lx[a:b]
+
+    def dense(self):
+        L = np.zeros((self.n, self.n))
+        for j in range(self.n):
+            r, v = self.column(j)
+            L[r, j] = v
+        return L
+
+    def logdet(self):
+        """log det C = 2 sum log L_jj (full factor)."""
+        return 2.0 * float(np.sum(np.log(self.Lx[self.Lp[:-1]])))
+
+
+def factor(rowptr, colind, values, perm, in_s=None, sym=None):
+    """Left-looking FP64 Cholesky of C = A(perm, perm); columns in S only."""
+    lib = _load()
+    n = len(rowptr) - 1
+    if sym is None:
+        rp, ci = lower_rows(rowptr, colind, perm)
+        parent = etree(n, rp, ci)
+    else:
+        rp, ci = sym["rows"]
+        parent = sym["parent"]
+    if in_s is None:
+        in_s = np.ones(n, dtype=np.uint8)
+    in_s = np.ascontiguousarray(in_s, dtype=np.uint8)
+    colcnt, rowcnt = counts(n, rp, ci, parent, in_s)
+    Lp = np.zeros(n + 1, dtype=np.int64)
+    Lp[1:] = np.cumsum(colcnt)
+    Rp = np.zeros(n + 1, dtype=np.int64)
+    Rp[1:] = np.cumsum(rowcnt)
+    Li = np.empty(int(Lp[-1]), dtype=np.int32)
+    Rk = np.empty(int(Rp[-1]), dtype=np.int32)
+    Rq = np.empty(int(Rp[-1]), dtype=np.int64)
+    mark = np.empty(n, dtype=np.int32)
+    fill = np.empty(n, dtype=np.int64)
+    lib.orc_pattern(n, _p(rp), _p(ci), _p(parent), _p(in_s), _p(Lp), _p(Li), _p(Rp),
+                    _p(Rk), _p(Rq), _p(mark), _p(fill))
+    Cp, Cr, Cx = lower_cols(rowptr, colind, values, perm)
+    Lx = np.zeros(int(Lp[-1]), dtype=np.float64)
+    x = np.zeros(n, dtype=np.float64)
+    fl = ctypes.c_double(0.0)
+    bad = lib.orc_factor(n, _p(Cp), _p(Cr), _p(Cx), _p(in_s), _p(Lp), _p(Li), _p(Lx),
+                         _p(Rp), _p(Rk), _p(Rq), _p(x), ctypes.byref(fl))
+    return Factor(n, Lp, Li, Lx, int(bad), fl.value)
+
+
+def solve(F, b, perm):
+    """x = P^T L^{-T} L^{-1} P b for b of shape (n,) or (n, nrhs)."""
+    lib = _load()
+    n = F.n
+    b = np.asarray(b, dtype=np.float64)
+    one = b.ndim == 1
+    B = b.reshape(n, -1)
+    y = np.asfortranarray(B[perm] if perm is not None else B.copy())
+    lib.orc_solve(n, _p(F.Lp), _p(F.Li), _p(F.Lx), _p(y), y.shape[1], n)
+    x = np.empty_like(y)
+    if perm is not None:
+        x[perm] = y
+    else:
+        x[:] = y
+    return x[:, 0] if one else x
+
+
+def descendant_closed(parent, roots):
+    """Mask of the union of the etree subtrees rooted at ``roots``."""
+    n = len(parent)
+    in_s = np.zeros(n, dtype=np.uint8)
+    roots = set(int(r) for r in roots)
+    # a column belongs to S iff some ancestor-or-self is a chosen root;
+    # ancestors have larger indices, so scan downwards
+    memo = np.zeros(n, dtype=np.int8)  # 0 unknown, 1 in, 2 out
+    for j in range(n - 1, -1, -1):
+        if j in roots:
+            memo[j] = 1
+        else:
+            p = parent[j]
+            memo[j] = memo[p] if p >= 0 else 2
+    in_s[memo == 1] = 1
+    return in_s
+
+
+def factor_sample(rowptr, colind, values, perm, seconds=15.0, sym=None):
+    """Time the oracle on the first J columns of the elimination order
+    (descendant-closed), growing J until the run takes about ``seconds``.
+
+    Returns (flops, elapsed_s, J)."""
+    n = len(rowptr) - 1
+    if sym is None:
+        rp, ci = lower_rows(rowptr, colind, perm)
+        sym = {"rows": (rp, ci), "parent": etree(n, rp, ci)}
+    J = max(1, n // 64)
+    while True:
+        in_s = np.zeros(n, dtype=np.uint8)
+        in_s[:J] = 1
+        t0 = time.perf_counter()
+        F = factor(rowptr, colind, values, perm, in_s=in_s, sym=sym)
+        dt = time.perf_counter() - t0
+        if dt >= seconds * 0.5 or J >= n:
+            return F.flops, dt, J
+        J = min(n, int(J * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
+
+
+# ---------------------------------------------------------------------------
+# Error measures
+# ---------------------------------------------------------------------------
+def berr(rowptr, colind, values, x, b):
+    """max over RHS columns of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)."""
+    n = len(rowptr) - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    anorm = np.max(np.bincount(rows, weights=np.abs(values), minlength=n))
+    X = np.asarray(x).reshape(n, -1)
+    Bm = np.asarray(b).reshape(n, -1)
+    worst = 0.0
+    for r in range(X.shape[1]):
+        ax = np.bincount(rows, weights=values * X[colind, r], minlength=n)
+        res = np.max(np.abs(Bm[:, r] - ax))
+        den = anorm * np.max(np.abs(X[:, r])) + np.max(np.abs(Bm[:, r]))
+        worst = max(worst, res / den)
+    return worst
+
+
+def rel_fro(Lx_test, Lx_ref):
+    """||L - L_ref||_F / ||L_ref||_F over a common pattern."""
+    d = np.asarray(Lx_test, dtype=np.float64) - np.asarray(Lx_ref, dtype=np.float64)
+    return float(np.linalg.norm(d) / np.linalg.norm(Lx_ref))

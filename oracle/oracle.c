@@ -1,0 +1,191 @@
+/*
+ * oracle.c -- plain, slow, obviously-correct CPU reference for the
+ * supernodal multifrontal Cholesky path.  TEST INFRASTRUCTURE ONLY: it is
+ * used by tests/, the smoke check and the CPU-baseline leg of the benchmark,
+ * never by the library.  It shares no code with the GPU library.
+ *
+ * Everything works on C = P A P^T (new numbering), whose lower triangle is
+ * given by the caller:
+ *   - "rows" form: strict lower part by rows (row i lists columns j < i),
+ *   - "cols" form: lower part incl. diagonal by columns (column j lists rows
+ *     i >= j, values summed over duplicates).
+ *
+ * The method (paper Sec. 5, Tacho: multifrontal Cholesky of an SPD matrix,
+ * three phases: symbolic analysis, numerical factorization, solve) reaches the
+ * unique Cholesky factor of C, so the oracle computes that definition with
+ * the textbook column-by-column (left-looking) algorithm:
+ *   etree        parent(j) = min{ i > j : L_ij != 0 }       (Liu's algorithm)
+ *   col counts   c_j = |struct(L_{*,j})| incl. diagonal     (row subtrees)
+ *   supernodes   fundamental: j+1 joins j iff parent(j) = j+1,
+ *                c_j = c_{j+1} + 1 and j is the only child of j+1
+ *   numeric      x = C[j:,j] - sum_{k: L_jk != 0} L[j:,k] L_jk;
+ *                L_jj = sqrt(x_j), L[j+1:,j] = x[j+1:] / L_jj
+ *   solve        L z = P b, L^T w = z, x = P^T w
+ *
+ * All routines can be restricted to a set S of columns closed under etree
+ * descendants (mask in_s); column j of L only depends on columns in the
+ * subtree of j, so L[:, S] is exact.  S = {0..J-1} is always closed because
+ * parent(j) > j.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Elimination tree by Liu's algorithm with path compression over the rows of
+ * the strict lower triangle.  anc: workspace of n ints. */
+void orc_etree(int64_t n, const int64_t* rp, const int32_t* ci, int32_t* parent,
+               int32_t* anc) {
+  for (int64_t i = 0; i < n; ++i) {
+    parent[i] = -1;
+    anc[i] = -1;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int32_t r = ci[p];
+      /* climb the compressed ancestor forest from r towards i */
+      while (r != -1 && r < i) {
+        int32_t next = anc[r];
+        anc[r] = (int32_t)i;
+        if (next == -1) parent[r] = (int32_t)i;
+        r = next;
+      }
+    }
+  }
+}
+
+/* Row-subtree walk: row i of L touches exactly the etree nodes on the paths
+ * from each k (C_ik != 0, k < i) up to i.  Counts per column (incl. the
+ * diagonal) and per row (off-diagonal), restricted to columns in S. */
+void orc_counts(int64_t n, const int64_t* rp, const int32_t* ci,
+                const int32_t* parent, const uint8_t* in_s, int64_t* colcnt,
+                int64_t* rowcnt, int32_t* mark) {
+  for (int64_t i = 0; i < n; ++i) {
+    colcnt[i] = 0;
+    rowcnt[i] = 0;
+    mark[i] = -1;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    mark[i] = (int32_t)i;
+    if (in_s[i]) colcnt[i] += 1;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int32_t k = ci[p];
+      while (k != -1 && in_s[k] && mark[k] != i) {
+        mark[k] = (int32_t)i;
+        colcnt[k] += 1;
+        rowcnt[i] += 1;
+        k = parent[k];
+      }
+    }
+  }
+}
+
+/* Fill the pattern of L[:, S] (Li, rows sorted ascending, diagonal first) and
+ * the row lists (for row i: columns k < i with L_ik != 0 and the position of
+ * L_ik inside column k).  Lp/Rp are prefix sums of colcnt/rowcnt. */
+void orc_pattern(int64_t n, const int64_t* rp, const int32_t* ci,
+                 const int32_t* parent, const uint8_t* in_s, const int64_t* Lp,
+                 int32_t* Li, const int64_t* Rp, int32_t* Rk, int64_t* Rq,
+                 int32_t* mark, int64_t* fill) {
+  for (int64_t i = 0; i < n; ++i) {
+    mark[i] = -1;
+    fill[i] = Lp[i];
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t rpos = Rp[i];
+    mark[i] = (int32_t)i;
+    if (in_s[i]) Li[fill[i]++] = (int32_t)i;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int32_t k = ci[p];
+      while (k != -1 && in_s[k] && mark[k] != i) {
+        mark[k] = (int32_t)i;
+        Rk[rpos] = k;
+        Rq[rpos] = fill[k];
+        ++rpos;
+        Li[fill[k]++] = (int32_t)i;
+        k = parent[k];
+      }
+    }
+  }
+}
+
+/* Left-looking numeric factorization of the columns in S, in increasing
+ * order.  Cp/Cr/Cx: lower triangle of C by columns.  x: dense workspace of n
+ * doubles, zero on entry and exit.  Returns -1 on success or the first column
+ * whose pivot is not positive (NOT SPD).  flops_done receives sum c_j^2 over
+ * the columns completed. */
+int64_t orc_factor(int64_t n, const int64_t* Cp, const int32_t* Cr,
+                   const double* Cx, const uint8_t* in_s, const int64_t* Lp,
+                   const int32_t* Li, double* Lx, const int64_t* Rp,
+                   const int32_t* Rk, const int64_t* Rq, double* x,
+                   double* flops_done) {
+  double fl = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    if (!in_s[j]) continue;
+    for (int64_t p = Cp[j]; p < Cp[j + 1]; ++p) x[Cr[p]] += Cx[p];
+    for (int64_t r = Rp[j]; r < Rp[j + 1]; ++r) {
+      int32_t k = Rk[r];
+      int64_t q = Rq[r]; /* position of L_jk in column k */
+      double ljk = Lx[q];
+      for (int64_t t = q; t < Lp[k + 1]; ++t) x[Li[t]] -= Lx[t] * ljk;
+    }
+    double d = x[j];
+    if (!(d > 0.0)) {
+      for (int64_t t = Lp[j]; t < Lp[j + 1]; ++t) x[Li[t]] = 0.0;
+      *flops_done = fl;
+      return j;
+    }
+    double ljj = sqrt(d);
+    Lx[Lp[j]] = ljj;
+    x[j] = 0.0;
+    for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) {
+      int32_t i = Li[t];
+      Lx[t] = x[i] / ljj;
+      x[i] = 0.0;
+    }
+    double c = (double)(Lp[j + 1] - Lp[j]);
+    fl += c * c;
+  }
+  *flops_done = fl;
+  return -1;
+}
+
+/* Fundamental supernodes.  sup_ptr receives the first column of every
+ * supernode followed by n; returns the number of supernodes.  nchild: n ints
+ * of workspace. */
+int64_t orc_supernodes(int64_t n, const int32_t* parent, const int64_t* colcnt,
+                       int32_t* sup_ptr, int32_t* nchild) {
+  for (int64_t j = 0; j < n; ++j) nchild[j] = 0;
+  for (int64_t j = 0; j < n; ++j)
+    if (parent[j] >= 0) nchild[parent[j]] += 1;
+  int64_t ns = 0;
+  if (n == 0) {
+    sup_ptr[0] = 0;
+    return 0;
+  }
+  sup_ptr[ns++] = 0;
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    int joins = parent[j] == j + 1 && colcnt[j] == colcnt[j + 1] + 1 &&
+                nchild[j + 1] == 1;
+    if (!joins) sup_ptr[ns++] = (int32_t)(j + 1);
+  }
+  sup_ptr[ns] = (int32_t)n;
+  return ns;
+}
+
+/* Solve L L^T w = y in place (y overwritten by w), nrhs columns with leading
+ * dimension ld.  Full factor only. */
+void orc_solve(int64_t n, const int64_t* Lp, const int32_t* Li,
+               const double* Lx, double* y, int64_t nrhs, int64_t ld) {
+  for (int64_t r = 0; r < nrhs; ++r) {
+    double* b = y + r * ld;
+    for (int64_t j = 0; j < n; ++j) { /* forward: L z = b */
+      double zj = b[j] / Lx[Lp[j]];
+      b[j] = zj;
+      for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) b[Li[t]] -= Lx[t] * zj;
+    }
+    for (int64_t j = n - 1; j >= 0; --j) { /* backward: L^T w = z */
+      double s = b[j];
+      for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) s -= Lx[t] * b[Li[t]];
+      b[j] = s / Lx[Lp[j]];
+    }
+  }
+}
