@@ -1,0 +1,352 @@
+"""Benchmark of the multifrontal Cholesky hot path on one GB300 (per rank).
+
+One step = one FP64 numeric factorization (assembly, extend-add, POTRF/TRSM/
+SYRK fronts, level by level) plus one 1-RHS forward/backward solve, on the
+extruded Q1 ice-sheet-like mesh (256 x 256 x 10 hexahedra, 2 dofs per node,
+n = 1,453,078, horizontal nested dissection).  Inputs (values, RHS) are
+resident in HBM when the timed region starts; the factor (~13 GB) is far
+larger than L2, so no flush is needed between steps.
+
+``value`` = sum_j c_j^2 (flops of the symbolic phase) * steps / time, in
+TFLOP/s, max time over ranks.  Extra keys: factor-only TFLOP/s, solve
+latency p50/p99 and solves/s, the FP32 + FP64-refinement path on the same
+matrix, the end-to-end number through the C-ABI with host buffers, the
+roofline of the dominant kernel and the oracle on the host cores.
+
+Multi-GPU (torchrun): the path does not shard, so N ranks run N independent
+replicas (weak scaling); no collective is on the data path.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "q1_extruded_256x256x10_2dof_hnd"
+METRIC = "factor TFLOP/s (sum c_j^2 / step time; step = FP64 numeric factorization + 1-RHS solve)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--size", type=int, default=256, help="horizontal elements per side")
+    p.add_argument("--layers", type=int, default=10)
+    p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def load_workload(size, layers):
+    import gen
+    rp, ci, v = gen.q1_extruded(size, size, layers, seed=1)
+    perm = gen.nd_perm((size + 1, size + 1, layers + 1), split_axes=(0, 1), dofs=2)
+    n = len(rp) - 1
+    b = gen.rhs(n, 1, seed=3)
+    return rp, ci, v, perm, b
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % index)
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def run_reference(args):
+    """The oracle on the host cores, each step a bounded sample (first J
+    columns of the elimination order) of the same matrix."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    rp, ci, v, perm, b = load_workload(args.size, args.layers)
+    n = len(rp) - 1
+    rows = oracle.lower_rows(rp, ci, perm)
+    sym = {"rows": rows, "parent": oracle.etree(n, *rows)}
+    # calibrate J so that one step is ~ per_step seconds
+    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    flops, dt, J = oracle.factor_sample(rp, ci, v, perm, seconds=per_step, sym=sym)
+    in_s = np.zeros(n, dtype=np.uint8)
+    in_s[:J] = 1
+    for _ in range(args.warmup):
+        oracle.factor(rp, ci, v, perm, in_s=in_s, sym=sym)
+    t0 = time.perf_counter()
+    fl = 0.0
+    for _ in range(args.steps):
+        F = oracle.factor(rp, ci, v, perm, in_s=in_s, sym=sym)
+        fl += F.flops
+    el = time.perf_counter() - t0
+    val = fl / el / 1e12
+    sample = "first %d of %d columns of the elimination order (descendant-closed), %.3g flops per step" % (
+        J, n, F.flops)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "l2_flush": "inputs larger than L2"},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_setup()
+    import torch
+    import paper_2506_05793_gb300 as mf
+    import gen
+    mf.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rp, ci, v, perm, b = load_workload(args.size, args.layers)
+    n = len(rp) - 1
+    opt = mf.mf_options_default()
+    opt.profile = 1  # per-launch CUDA events: per-kernel-kind device time
+    h = mf.mf_create(opt)
+    t0 = time.perf_counter()
+    s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+    t_sym = time.perf_counter() - t0
+    info = mf.mf_symbolic_get_info(s)
+    f = mf.mf_factor_create(h, s, mf.MF_FP64)
+    st = torch.cuda.current_stream(dev)
+    vd = torch.from_numpy(v).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.empty_like(bd)
+    nf_launch, ns_launch = mf.mf_factor_launch_counts(f)
+
+    def step():
+        mf.mf_factor_numeric(f, vd, stream=st, async_=True)
+        mf.mf_solve(f, bd, xd, stream=st)
+
+    for _ in range(args.warmup):
+        step()
+    mf.mf_factor_check(f, stream=st)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    mf.mf_factor_check(f, stream=st)  # status of the last step; also reads the profile
+    prof = mf.mf_factor_profile(f)
+    ms_max = max_over_ranks(ws, ms)
+    flops = info["flops"]
+    value = flops * args.steps * ws / (ms_max / 1e3) / 1e12
+    x = xd.cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    anorm = np.max(np.bincount(rows, weights=np.abs(v), minlength=n))
+    res = b - gen.csr_matvec(rp, ci, v, x)
+    berr = float(np.max(np.abs(res)) / (anorm * np.max(np.abs(x)) + np.max(np.abs(b))))
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "nnz_A": int(rp[-1]), "nnz_L": info["nnz_L"],
+                   "flops_per_factor": flops, "nsuper": info["nsuper"],
+                   "levels": info["nlevels"], "max_front": info["max_front"], "nrhs": 1,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2_flush": "inputs larger than L2 (factor %.1f GB)" % (
+                       info["factor_bytes_fp64"] / 1e9),
+                   "symbolic_s": t_sym},
+        "berr": berr,
+        "gpu_launches": int((nf_launch + ns_launch) * args.steps),
+        "clocks": clocks,
+    }
+    fac_ms = sum(p["ms"] for p in prof.values())
+    out["factor_ms_sum_of_kernels"] = fac_ms
+    out["factor_tflops_kernels"] = flops / (fac_ms / 1e3) / 1e12 if fac_ms > 0 else None
+    out["kernels"] = prof
+    # dominant kernel roofline: FP64 FMA pipe (contraction) against the
+    # measured bf16 peak times the nominal FP64 / bf16 ratio (1.25 / 2250)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    peak64 = bf16 * 1.25 / 2250.0
+    ach = prof[dom]["flops"] / (prof[dom]["ms"] / 1e3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
+    out["roofline"] = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak64,
+                       "unit": "TFLOP/s", "frac": ach / peak64, "traffic": None,
+                       "peak_source": "measured bf16 %.0f TFLOP/s x nominal FP64/bf16 1.25/2250" % bf16}
+    if rank == 0 and not args.no_extras:
+        extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info)
+    if rank == 0:
+        print(json.dumps(out))
+    mf.mf_factor_free(f)
+    mf.mf_symbolic_free(s)
+    mf.mf_destroy(h)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info):
+    import torch
+    n = len(rp) - 1
+    # solve latency (1 RHS), p50 / p99 over 200 solves
+    xd = torch.empty_like(bd)
+    for _ in range(3):
+        mf.mf_solve(f, bd, xd, stream=st)
+    lat = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
+    for a, z in ev:
+        a.record(st)
+        mf.mf_solve(f, bd, xd, stream=st)
+        z.record(st)
+    torch.cuda.synchronize()
+    lat = np.array([a.elapsed_time(z) for a, z in ev])
+    out["solve_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
+    out["solves_per_s"] = float(1e3 / np.mean(lat))
+    # end to end through the C-ABI with host buffers (values H2D, B H2D, X D2H)
+    K = 2
+    xh = np.empty(n)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        mf.mf_factor_numeric(f, v)       # host values, sync + status read
+        mf.mf_solve(f, b, xh)            # host RHS and solution
+    el = time.perf_counter() - t0
+    out["e2e"] = {"value": info["flops"] * K / el / 1e12, "unit": "TFLOP/s",
+                  "h2d_bytes_per_step": int(v.nbytes + b.nbytes),
+                  "d2h_bytes_per_step": int(xh.nbytes + 16)}
+    # FP32 factorization + FP64 refinement to berr 1e-13 on the same matrix
+    try:
+        f32 = mf.mf_factor_create(h, s, mf.MF_FP32)
+        mf.mf_factor_numeric(f32, vd, stream=st)
+        xr = torch.empty_like(bd)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        mf.mf_factor_numeric(f32, vd, stream=st, async_=True)
+        _, rep = mf.mf_solve_refined(f32, bd, xr, tol=1e-13, max_iter=30, stream=st)
+        z.record(st)
+        torch.cuda.synchronize()
+        out["fp32_ir"] = {"ms_factor_plus_refined_solve": a.elapsed_time(z), "report": rep,
+                          "fp64_ms_per_step": out["ms_per_step"]}
+        mf.mf_factor_free(f32)
+    except Exception as e:  # report, do not hide the main number
+        out["fp32_ir"] = {"error": str(e)}
+    # the oracle on the host cores, bounded sample of the same workload
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        import oracle
+        oracle.build()
+        flops, dt, J = oracle.factor_sample(rp, ci, v, out_perm(args), seconds=args.cpu_seconds)
+        out["cpu_baseline"] = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": "first %d of %d columns (descendant-closed), %.3g flops, %.1f s"
+                                         % (J, n, flops, dt)}
+
+
+def out_perm(args):
+    import gen
+    return gen.nd_perm((args.size + 1, args.size + 1, args.layers + 1), split_axes=(0, 1), dofs=2)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * mfchol.h -- C-ABI of the GB300 supernodal multifrontal sparse Cholesky.
+ *
+ * The calls follow the three phases of the paper's Ax=b statement (Sec. 2:
+ * symbolic analysis on the pattern only, numerical setup that copies the
+ * values and factors P A P^T = L L^T, solve by forward and backward
+ * substitution) and the reuse contract stated there (one analysis per
+ * pattern, repeated numerical factorizations as values change, many solves
+ * per factorization).  The factorization is Tacho's multifrontal Cholesky of
+ * an SPD matrix with level-set scheduling (paper Sec. 5); the solve is the
+ * level-set supernodal SpTRSV ("variant 1", paper Sec. 5).
+ *
+ * Conventions
+ *   - A is given as FULL symmetric CSR: rowptr (int64, n+1 entries, rowptr[0]
+ *     = 0), colind (int32, rowptr[n] entries, any order within a row,
+ *     duplicates summed), values (double, same order as colind).
+ *   - perm[new] = old, i.e. C = A(perm, perm).  NULL means identity.
+ *     Only entries (r, c) whose permuted indices satisfy iperm[r] >= iperm[c]
+ *     are read (the lower triangle of C).
+ *   - Supernodes are fundamental (no relaxed amalgamation) and are numbered
+ *     by their first column in the permuted order.
+ *   - Device pointers are plain CUDA device addresses of the current device;
+ *     stream arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).
+ *
+ * Ownership: the caller owns every array it passes; the library copies what
+ * it keeps.  Objects returned through out-parameters belong to the caller
+ * and are released with the matching *_free / mf_destroy.  Device buffers
+ * passed in are borrowed for the call and must stay valid until the work
+ * enqueued on the given stream has completed.
+ *
+ * Errors: every entry point returns an mf_status.  No entry point aborts,
+ * exits or traps.  A per-thread message is available from
+ * mf_last_error_string(); for MF_ERR_NOT_SPD the first failing column (in
+ * the permuted order) is available from mf_last_error_column().
+ */
+#ifndef MFCHOL_H
+#define MFCHOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mf_status {
+  MF_OK = 0,
+  MF_ERR_INVALID = 1,     /* malformed CSR / perm / argument */
+  MF_ERR_NOT_SPD = 2,     /* non-positive pivot; see mf_last_error_column */
+  MF_ERR_OOM = 3,         /* device allocation failed or budget exceeded */
+  MF_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  MF_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  MF_ERR_STAGNATION = 6,  /* refinement stagnated and FP64 fallback is off */
+  MF_ERR_INTERNAL = 7     /* internal consistency check failed */
+} mf_status;
+
+typedef enum mf_precision { MF_FP64 = 0, MF_FP32 = 1 } mf_precision;
+
+typedef struct mf_handle mf_handle;
+typedef struct mf_symbolic mf_symbolic;
+typedef struct mf_factor mf_factor;
+
+/* Tuning and behaviour switches.  mf_options_default fills sane values. */
+typedef struct mf_options {
+  int32_t small_front_max;  /* fronts with k+m <= this run in one CTA (<=128) */
+  int32_t use_graphs;       /* 1: capture the factorization in a CUDA graph */
+  int32_t profile;          /* 1: time every launch with CUDA events */
+  int32_t reserved0;
+  int64_t budget_bytes;     /* device bytes a factor may hold (0 = no limit) */
+} mf_options;
+
+/* Summary of a symbolic analysis. */
+typedef struct mf_symbolic_info {
+  int64_t n;
+  int64_t nnz_lower;      /* entries of the lower triangle of C (unique) */
+  int64_t nsuper;         /* fundamental supernodes */
+  int64_t nnz_L;          /* sum_j c_j, structural, incl. the diagonal */
+  double flops;           /* sum_j c_j^2 (paper-independent Cholesky count) */
+  int64_t nlevels;        /* levels of the supernodal elimination tree */
+  int64_t max_front;      /* max over supernodes of k + m */
+  int64_t max_k;          /* max supernode width */
+  int64_t factor_bytes_fp64;  /* device bytes of an FP64 factor (L + update) */
+  int64_t factor_bytes_fp32;  /* device bytes of an FP32 factor */
+} mf_symbolic_info;
+
+/* Refinement report of mf_solve_refined. */
+typedef struct mf_ir_report {
+  int32_t iterations;     /* refinement steps taken */
+  int32_t fell_back;      /* 1 if the FP64 fallback factorization was used */
+  double berr;            /* final max over RHS of the normwise backward error */
+  double berr_first;      /* backward error of the unrefined FP32 solve */
+} mf_ir_report;
+
+/* ---- library, errors --------------------------------------------------- */
+
+/* Fill *opt with defaults.  Returns MF_ERR_INVALID if opt is NULL. */
+int mf_options_default(mf_options* opt);
+
+/* Create a handle bound to the current CUDA device.  opt may be NULL
+ * (defaults).  The handle owns nothing else; destroy it last. */
+int mf_create(mf_handle** h, const mf_options* opt);
+int mf_destroy(mf_handle* h);
+
+/* Message of the last failing call on this thread ("" if none).  The
+ * pointer stays valid until the next call on this thread. */
+const char* mf_last_error_string(void);
+
+/* Permuted column of the last MF_ERR_NOT_SPD on this thread, else -1. */
+int64_t mf_last_error_column(void);
+
+/* ---- phase 1: symbolic analysis (host; paper Sec. 2 step 1) ------------- */
+
+/* Analyse the pattern of C = A(perm, perm): elimination tree (Liu),
+ * column counts (Gilbert-Ng-Peyton row-subtree leaves), fundamental
+ * supernodes, front row lists, child-to-parent relative maps, level sets and
+ * the device memory plan.  Host arrays only.  Errors: MF_ERR_INVALID for a
+ * malformed CSR (rowptr not non-decreasing, colind out of range) or a perm
+ * that is not a permutation. */
+int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr,
+                        const int32_t* colind, const int32_t* perm,
+                        mf_symbolic** s);
+
+/* Block-diagonal union of `count` independent matrices (a batch of
+ * subdomains, paper Sec. 5: many subdomain solves per GPU).  Matrix b
+ * occupies rows/cols [off_b, off_b + n_b) of the union, off_b = sum of the
+ * previous n.  perms[b] may be NULL.  The union is one symbolic object: its
+ * elimination forest has one tree per matrix and one level schedule, so a
+ * single factorization covers the whole batch. */
+int mf_symbolic_analyze_batch(mf_handle* h, int32_t count, const int64_t* ns,
+                              const int64_t* const* rowptrs,
+                              const int32_t* const* colinds,
+                              const int32_t* const* perms, mf_symbolic** s);
+
+int mf_symbolic_free(mf_symbolic* s);
+int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info);
+/* parent[j] of the column elimination tree (-1 for roots), n entries. */
+int mf_symbolic_etree(const mf_symbolic* s, int32_t* parent);
+/* c_j = |struct(L_{*,j})| including the diagonal, n entries. */
+int mf_symbolic_colcounts(const mf_symbolic* s, int64_t* counts);
+/* First column of each supernode followed by n: nsuper + 1 entries. */
+int mf_symbolic_supernodes(const mf_symbolic* s, int32_t* sup_ptr);
+/* CSC pattern of L: Lp (n+1 entries), Li (nnz_L entries, rows ascending
+ * within a column, diagonal first). */
+int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li);
+/* Supernodal elimination tree parent (-1 for roots), nsuper entries, and
+ * level of each supernode (0 = leaves), nsuper entries.  Either may be NULL. */
+int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent,
+                               int32_t* level);
+
+/* ---- phase 2: numerical factorization (device; paper Sec. 2 step 2) ----- */
+
+/* Allocate device storage for the factor of s in the given precision
+ * (MF_FP64 or MF_FP32): supernodal L panels, update matrices, the copy of
+ * the values and the device schedule.  Errors: MF_ERR_OOM if the allocation
+ * fails or exceeds the handle's budget. */
+int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec,
+                     mf_factor** f);
+
+/* Numerical factorization P A P^T = L L^T with the given values (CSR order
+ * of the analysed pattern; nnz = rowptr[n] entries; host or device pointer
+ * as values_on_device says).  Enqueued on `stream`.  Unless `async` is
+ * non-zero the call waits for the stream and returns MF_ERR_NOT_SPD (with
+ * the first failing permuted column) if a pivot was not positive.  With
+ * async != 0 it returns after enqueueing; mf_factor_check reads the status.
+ * May be called again with new values (refactorization reuses storage). */
+int mf_factor_numeric(mf_factor* f, const double* values,
+                      int32_t values_on_device, void* stream, int32_t async);
+
+/* Wait for `stream` and return the status of the last numeric call. */
+int mf_factor_check(mf_factor* f, void* stream);
+
+int mf_factor_free(mf_factor* f);
+
+/* Copy L to the host in CSC order of mf_symbolic_pattern (nnz_L doubles;
+ * FP32 factors are widened).  Synchronous. */
+int mf_factor_export_L(const mf_factor* f, double* Lx);
+
+/* Kernel launches issued by one numeric factorization / one 1-RHS solve. */
+int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches,
+                            int64_t* solve_launches);
+
+/* With profiling on (mf_options.profile), per-kernel-kind totals of the last
+ * numeric call: kinds 0 small-front, 1 assemble, 2 potrf, 3 trsm, 4 syrk.
+ * ms[kind], launches[kind] and flops[kind] (algorithmic) for 5 kinds. */
+int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches,
+                      double* flops);
+
+/* ---- phase 3: solve (device; paper Sec. 2 step 3, Sec. 5 SpTRSV) -------- */
+
+/* X = A^{-1} B for nrhs right-hand sides, column-major, FP64 at the
+ * boundary (an FP32 factor solves in FP32).  B and X are both host or both
+ * device pointers as on_device says; B may equal X.  Enqueued on stream;
+ * synchronous for host pointers. */
+int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
+             double* X, int64_t ldx, int32_t on_device, void* stream);
+
+/* Mixed-precision solve: f is an FP32 factor; the residual r = B - A X, the
+ * update X += D and the backward error
+ *   berr = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
+ * are FP64 (A = the values of the last numeric call).  Each step solves the
+ * residual scaled by 1/||r||_inf in FP32.  Stops when berr <= tol for every
+ * RHS.  Stagnation (berr not halved over two steps, or max_iter reached)
+ * triggers an FP64 factorization of the same values and an FP64 solve,
+ * unless allow_fallback is 0 (then MF_ERR_STAGNATION).  rep may be NULL. */
+int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
+                     double* X, int64_t ldx, int32_t on_device, double tol,
+                     int32_t max_iter, int32_t allow_fallback,
+                     mf_ir_report* rep, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFCHOL_H */

@@ -1,0 +1,322 @@
+"""ctypes binding of include/mfchol.h -- argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Host arrays are
+numpy arrays; device arrays are torch CUDA tensors (torch is used only for
+device memory and streams).  Matrices of right-hand sides are column-major:
+numpy arrays are converted with ``np.asfortranarray``; device tensors must
+have unit row stride (e.g. the transpose of a contiguous (nrhs, n) tensor).
+
+The library must be built (``paper_2506_05793_gb300.build.build()``); loading
+fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+MF_OK, MF_ERR_INVALID, MF_ERR_NOT_SPD, MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_TIMEOUT, \
+    MF_ERR_STAGNATION, MF_ERR_INTERNAL = range(8)
+MF_FP64, MF_FP32 = 0, 1
+FACTOR_KINDS = ("small_front", "assemble", "potrf", "trsm", "syrk")
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+class mf_options(ctypes.Structure):
+    _fields_ = [("small_front_max", _I32), ("use_graphs", _I32), ("profile", _I32),
+                ("reserved0", _I32), ("budget_bytes", _I64)]
+
+
+class mf_symbolic_info(ctypes.Structure):
+    _fields_ = [("n", _I64), ("nnz_lower", _I64), ("nsuper", _I64), ("nnz_L", _I64),
+                ("flops", _D), ("nlevels", _I64), ("max_front", _I64), ("max_k", _I64),
+                ("factor_bytes_fp64", _I64), ("factor_bytes_fp32", _I64)]
+
+
+class mf_ir_report(ctypes.Structure):
+    _fields_ = [("iterations", _I32), ("fell_back", _I32), ("berr", _D), ("berr_first", _D)]
+
+
+class MFError(RuntimeError):
+    def __init__(self, code, msg, column=-1):
+        super().__init__("mfchol error %d: %s" % (code, msg))
+        self.code = code
+        self.column = column
+
+
+_lib = None
+
+_SIGS = {
+    "mf_options_default": [_P],
+    "mf_create": [_P, _P],
+    "mf_destroy": [_P],
+    "mf_symbolic_analyze": [_P, _I64, _P, _P, _P, _P],
+    "mf_symbolic_analyze_batch": [_P, _I32, _P, _P, _P, _P, _P],
+    "mf_symbolic_free": [_P],
+    "mf_symbolic_get_info": [_P, _P],
+    "mf_symbolic_etree": [_P, _P],
+    "mf_symbolic_colcounts": [_P, _P],
+    "mf_symbolic_supernodes": [_P, _P],
+    "mf_symbolic_pattern": [_P, _P, _P],
+    "mf_symbolic_supernode_tree": [_P, _P, _P],
+    "mf_factor_create": [_P, _P, _I32, _P],
+    "mf_factor_numeric": [_P, _P, _I32, _P, _I32],
+    "mf_factor_check": [_P, _P],
+    "mf_factor_free": [_P],
+    "mf_factor_export_L": [_P, _P],
+    "mf_factor_launch_counts": [_P, _P, _P],
+    "mf_factor_profile": [_P, _P, _P, _P],
+    "mf_solve": [_P, _I32, _P, _I64, _P, _I64, _I32, _P],
+    "mf_solve_refined": [_P, _I32, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _P, _P],
+}
+
+
+def lib():
+    """Load libmfchol.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libmfchol.so is not built (%s); run __graft_entry__.build()" % LIB)
+        L = ctypes.CDLL(LIB)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.mf_last_error_string.restype = ctypes.c_char_p
+        L.mf_last_error_string.argtypes = []
+        L.mf_last_error_column.restype = _I64
+        L.mf_last_error_column.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != MF_OK:
+        L = lib()
+        raise MFError(rc, L.mf_last_error_string().decode(), int(L.mf_last_error_column()))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _is_device(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+# ---------------------------------------------------------------------------
+def mf_options_default():
+    o = mf_options()
+    _check(lib().mf_options_default(ctypes.byref(o)))
+    return o
+
+
+def mf_create(opt=None):
+    h = ctypes.c_void_p()
+    _check(lib().mf_create(ctypes.byref(h), ctypes.byref(opt) if opt is not None else None))
+    return h
+
+
+def mf_destroy(h):
+    _check(lib().mf_destroy(h))
+
+
+def mf_symbolic_analyze(h, rowptr, colind, perm=None):
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    perm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    s = ctypes.c_void_p()
+    _check(lib().mf_symbolic_analyze(h, len(rowptr) - 1, _ptr(rowptr), _ptr(colind), _ptr(perm),
+                                     ctypes.byref(s)))
+    return s
+
+
+def mf_symbolic_analyze_batch(h, mats):
+    """mats: list of (rowptr, colind, perm or None)."""
+    keep = []
+    ns = np.array([len(m[0]) - 1 for m in mats], dtype=np.int64)
+    rps = (ctypes.c_void_p * len(mats))()
+    cis = (ctypes.c_void_p * len(mats))()
+    pms = (ctypes.c_void_p * len(mats))()
+    for b, (rp, ci, pm) in enumerate(mats):
+        rp = np.ascontiguousarray(rp, dtype=np.int64)
+        ci = np.ascontiguousarray(ci, dtype=np.int32)
+        keep += [rp, ci]
+        rps[b] = rp.ctypes.data
+        cis[b] = ci.ctypes.data
+        if pm is not None:
+            pm = np.ascontiguousarray(pm, dtype=np.int32)
+            keep.append(pm)
+            pms[b] = pm.ctypes.data
+        else:
+            pms[b] = None
+    s = ctypes.c_void_p()
+    _check(lib().mf_symbolic_analyze_batch(h, len(mats), _ptr(ns), rps, cis, pms, ctypes.byref(s)))
+    return s
+
+
+def mf_symbolic_free(s):
+    _check(lib().mf_symbolic_free(s))
+
+
+def mf_symbolic_get_info(s):
+    info = mf_symbolic_info()
+    _check(lib().mf_symbolic_get_info(s, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in mf_symbolic_info._fields_}
+
+
+def mf_symbolic_etree(s):
+    n = mf_symbolic_get_info(s)["n"]
+    out = np.empty(n, dtype=np.int32)
+    _check(lib().mf_symbolic_etree(s, _ptr(out)))
+    return out
+
+
+def mf_symbolic_colcounts(s):
+    n = mf_symbolic_get_info(s)["n"]
+    out = np.empty(n, dtype=np.int64)
+    _check(lib().mf_symbolic_colcounts(s, _ptr(out)))
+    return out
+
+
+def mf_symbolic_supernodes(s):
+    ns = mf_symbolic_get_info(s)["nsuper"]
+    out = np.empty(ns + 1, dtype=np.int32)
+    _check(lib().mf_symbolic_supernodes(s, _ptr(out)))
+    return out
+
+
+def mf_symbolic_pattern(s):
+    info = mf_symbolic_get_info(s)
+    Lp = np.empty(info["n"] + 1, dtype=np.int64)
+    Li = np.empty(info["nnz_L"], dtype=np.int32)
+    _check(lib().mf_symbolic_pattern(s, _ptr(Lp), _ptr(Li)))
+    return Lp, Li
+
+
+def mf_symbolic_supernode_tree(s):
+    ns = mf_symbolic_get_info(s)["nsuper"]
+    par = np.empty(ns, dtype=np.int32)
+    lev = np.empty(ns, dtype=np.int32)
+    _check(lib().mf_symbolic_supernode_tree(s, _ptr(par), _ptr(lev)))
+    return par, lev
+
+
+def mf_factor_create(h, s, prec=MF_FP64):
+    f = ctypes.c_void_p()
+    _check(lib().mf_factor_create(h, s, prec, ctypes.byref(f)))
+    return f
+
+
+def mf_factor_numeric(f, values, stream=None, async_=False):
+    """values: float64 numpy array (host) or torch CUDA tensor (device)."""
+    dev = _is_device(values)
+    if not dev:
+        values = np.ascontiguousarray(values, dtype=np.float64)
+    _check(lib().mf_factor_numeric(f, _ptr(values), 1 if dev else 0, _stream(stream),
+                                   1 if async_ else 0))
+
+
+def mf_factor_check(f, stream=None):
+    _check(lib().mf_factor_check(f, _stream(stream)))
+
+
+def mf_factor_free(f):
+    _check(lib().mf_factor_free(f))
+
+
+def mf_factor_export_L(f, nnz_L):
+    out = np.empty(nnz_L, dtype=np.float64)
+    _check(lib().mf_factor_export_L(f, _ptr(out)))
+    return out
+
+
+def mf_factor_launch_counts(f):
+    a, b = _I64(), _I64()
+    _check(lib().mf_factor_launch_counts(f, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def mf_factor_profile(f):
+    ms = np.zeros(5)
+    n = np.zeros(5, dtype=np.int64)
+    fl = np.zeros(5)
+    _check(lib().mf_factor_profile(f, _ptr(ms), _ptr(n), _ptr(fl)))
+    return {k: {"ms": float(ms[i]), "launches": int(n[i]), "flops": float(fl[i])}
+            for i, k in enumerate(FACTOR_KINDS)}
+
+
+def _rhs_layout(B):
+    """(pointer holder, nrhs, ld, on_device, one_dim) for a column-major RHS."""
+    if _is_device(B):
+        if B.dim() == 1:
+            return B, 1, B.shape[0], 1, True
+        if B.stride(0) != 1:
+            raise ValueError("device RHS must be column-major (unit row stride)")
+        return B, B.shape[1], B.stride(1) if B.shape[1] > 1 else B.shape[0], 1, False
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        return np.ascontiguousarray(B), 1, B.shape[0], 0, True
+    B = np.asfortranarray(B)
+    return B, B.shape[1], B.shape[0], 0, False
+
+
+def _alloc_like(B, on_dev):
+    if on_dev:
+        import torch
+        if B.dim() == 1:
+            return torch.empty_like(B)
+        return torch.empty((B.shape[1], B.shape[0]), dtype=B.dtype, device=B.device).t()
+    return np.empty_like(B, order="F")
+
+
+def mf_solve(f, B, X=None, stream=None):
+    """X = A^{-1} B.  Returns X (allocated like B if not given)."""
+    Bh, nrhs, ldb, dev, _ = _rhs_layout(B)
+    if X is None:
+        X = _alloc_like(Bh, dev)
+    Xh, _, ldx, _, _ = _rhs_layout(X)
+    if dev and stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    _check(lib().mf_solve(f, nrhs, _ptr(Bh), ldb, _ptr(Xh), ldx, dev, _stream(stream)))
+    return Xh
+
+
+def mf_solve_refined(f, B, X=None, tol=1e-13, max_iter=30, allow_fallback=True, stream=None):
+    """Mixed-precision refinement (FP32 factor, FP64 residual).  Returns (X, report)."""
+    Bh, nrhs, ldb, dev, _ = _rhs_layout(B)
+    if X is None:
+        X = _alloc_like(Bh, dev)
+    Xh, _, ldx, _, _ = _rhs_layout(X)
+    if dev and stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    rep = mf_ir_report()
+    _check(lib().mf_solve_refined(f, nrhs, _ptr(Bh), ldb, _ptr(Xh), ldx, dev, tol, max_iter,
+                                  1 if allow_fallback else 0, ctypes.byref(rep), _stream(stream)))
+    return Xh, {k: getattr(rep, k) for k, _ in mf_ir_report._fields_}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding wraps plus the error helpers."""
+    return sorted(list(_SIGS) + ["mf_last_error_string", "mf_last_error_column"])

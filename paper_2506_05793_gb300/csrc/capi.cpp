@@ -1,0 +1,693 @@
+// capi.cpp -- the extern "C" boundary (include/mfchol.h): handles, symbolic
+// objects, device factors, solves and the mixed-precision refinement loop.
+//
+// Phases follow the paper's Ax=b statement (Sec. 2): symbolic analysis on
+// the host, numerical setup (copy values, factor) and solve on the device.
+// Every step of the numeric path runs in this library's kernels; there is no
+// CPU fallback.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mf_internal.h"
+
+namespace {
+thread_local std::string g_err;
+thread_local int64_t g_errcol = -1;
+}  // namespace
+
+namespace mf {
+int set_error(int code, const std::string& msg) {
+  g_err = msg;
+  if (code != MF_ERR_NOT_SPD) g_errcol = -1;
+  return code;
+}
+}  // namespace mf
+
+using mf::set_error;
+
+#define MF_CK(x)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess)                                                                \
+      return set_error(e_ == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA,       \
+                       std::string(#x) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+namespace {
+
+// Device copy of the symbolic structures; freed with the last user.
+struct DevSymOwner {
+  mf::DevSym d;
+  std::vector<void*> allocs;
+  ~DevSymOwner() {
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename V>
+  cudaError_t up(V** dst, const std::vector<V>& src) {
+    *dst = nullptr;
+    if (src.empty()) return cudaSuccess;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, src.size() * sizeof(V));
+    if (e != cudaSuccess) return e;
+    allocs.push_back(p);
+    *dst = static_cast<V*>(p);
+    return cudaMemcpy(p, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice);
+  }
+};
+
+int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
+  int dev = 0;
+  MF_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(S->dev_mu);
+  if (S->dev && S->dev_device == dev) {
+    out = std::static_pointer_cast<DevSymOwner>(S->dev);
+    return MF_OK;
+  }
+  auto o = std::make_shared<DevSymOwner>();
+  MF_CK(o->up(&o->d.sn, S->sn));
+  MF_CK(o->up(&o->d.children, S->children));
+  MF_CK(o->up(&o->d.relmap, S->relmap));
+  MF_CK(o->up(&o->d.rowidx, S->rowidx));
+  MF_CK(o->up(&o->d.acol_ptr, S->acol_ptr));
+  MF_CK(o->up(&o->d.arow, S->arow));
+  MF_CK(o->up(&o->d.asrc_ptr, S->asrc_ptr));
+  MF_CK(o->up(&o->d.asrc, S->asrc));
+  MF_CK(o->up(&o->d.items, S->items));
+  MF_CK(o->up(&o->d.perm, S->perm));
+  MF_CK(o->up(&o->d.rowptr, S->rowptr));
+  MF_CK(o->up(&o->d.colind, S->colind));
+  S->dev = o;
+  S->dev_device = dev;
+  out = o;
+  return MF_OK;
+}
+
+size_t elem_size(int prec) { return prec == MF_FP32 ? sizeof(float) : sizeof(double); }
+
+int64_t factor_bytes(const mf_symbolic* S, int prec) {
+  return (S->Lsize + S->Usize) * (int64_t)elem_size(prec) + S->nnzA * (int64_t)sizeof(double);
+}
+
+}  // namespace
+
+struct mf_factor {
+  mf_handle* h = nullptr;
+  const mf_symbolic* S = nullptr;
+  int prec = MF_FP64;
+  std::shared_ptr<DevSymOwner> ds;
+  void* L = nullptr;
+  void* U = nullptr;
+  double* vals = nullptr;
+  unsigned long long* status = nullptr;
+  unsigned long long* status_host = nullptr;
+  // solve work
+  void* Y = nullptr;
+  void* W = nullptr;
+  double* Bd = nullptr;
+  double* Xd = nullptr;
+  double* Rd = nullptr;
+  int64_t io_cap = 0;  // doubles in each of Bd/Xd/Rd
+  double* small = nullptr;  // per-RHS scalars for refinement
+  // graph of the numeric factorization
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  // profiling
+  std::vector<cudaEvent_t> ev;
+  double prof_ms[mf::K_NKINDS_FACTOR] = {0};
+  int64_t prof_n[mf::K_NKINDS_FACTOR] = {0};
+  double prof_fl[mf::K_NKINDS_FACTOR] = {0};
+  bool numeric_done = false;
+  mf_factor* fb64 = nullptr;  // FP64 fallback of the refinement loop
+
+  ~mf_factor() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    cudaFree(L);
+    cudaFree(U);
+    cudaFree(vals);
+    cudaFree(status);
+    if (status_host) cudaFreeHost(status_host);
+    cudaFree(Y);
+    cudaFree(W);
+    cudaFree(Bd);
+    cudaFree(Xd);
+    cudaFree(Rd);
+    cudaFree(small);
+    delete fb64;
+  }
+};
+
+extern "C" {
+
+int mf_options_default(mf_options* opt) {
+  if (!opt) return set_error(MF_ERR_INVALID, "opt is NULL");
+  std::memset(opt, 0, sizeof(*opt));
+  opt->small_front_max = mf::kSmallMax;
+  opt->use_graphs = 1;
+  opt->profile = 0;
+  opt->budget_bytes = 0;
+  return MF_OK;
+}
+
+int mf_create(mf_handle** h, const mf_options* opt) {
+  if (!h) return set_error(MF_ERR_INVALID, "h is NULL");
+  *h = nullptr;
+  mf_handle* H = new (std::nothrow) mf_handle();
+  if (!H) return set_error(MF_ERR_OOM, "host allocation failed");
+  if (opt) H->opt = *opt; else mf_options_default(&H->opt);
+  if (H->opt.small_front_max <= 0 || H->opt.small_front_max > mf::kSmallMax)
+    H->opt.small_front_max = mf::kSmallMax;
+  // The symbolic phase is host-only, so a handle is usable without a GPU;
+  // device calls report MF_ERR_CUDA later if no device is present.
+  if (cudaGetDevice(&H->device) != cudaSuccess) {
+    H->device = -1;
+    cudaGetLastError();
+  }
+  *h = H;
+  return MF_OK;
+}
+
+int mf_destroy(mf_handle* h) {
+  delete h;
+  return MF_OK;
+}
+
+const char* mf_last_error_string(void) { return g_err.c_str(); }
+int64_t mf_last_error_column(void) { return g_errcol; }
+
+// ---------------------------------------------------------------------------
+// Symbolic
+// ---------------------------------------------------------------------------
+int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                        const int32_t* perm, mf_symbolic** s) {
+  if (!h || !s) return set_error(MF_ERR_INVALID, "NULL handle or output");
+  *s = nullptr;
+  mf_symbolic* S = new (std::nothrow) mf_symbolic();
+  if (!S) return set_error(MF_ERR_OOM, "host allocation failed");
+  std::string err;
+  int rc;
+  try {
+    rc = mf::analyze(*S, n, rowptr, colind, perm, err);
+    if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max);
+  } catch (const std::bad_alloc&) {
+    rc = MF_ERR_OOM;
+    err = "host allocation failed";
+  }
+  if (rc != MF_OK) {
+    delete S;
+    return set_error(rc, err);
+  }
+  *s = S;
+  return MF_OK;
+}
+
+int mf_symbolic_analyze_batch(mf_handle* h, int32_t count, const int64_t* ns,
+                              const int64_t* const* rowptrs, const int32_t* const* colinds,
+                              const int32_t* const* perms, mf_symbolic** s) {
+  if (!h || !s || count < 0 || (count > 0 && (!ns || !rowptrs || !colinds)))
+    return set_error(MF_ERR_INVALID, "invalid batch arguments");
+  int64_t N = 0, NNZ = 0;
+  for (int32_t b = 0; b < count; ++b) {
+    if (ns[b] < 0 || !rowptrs[b]) return set_error(MF_ERR_INVALID, "invalid batch member");
+    N += ns[b];
+    NNZ += rowptrs[b][ns[b]];
+  }
+  if (N >= (int64_t)INT32_MAX) return set_error(MF_ERR_INVALID, "batch too large");
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci, pm;
+  try {
+    rp.reserve(N + 1);
+    ci.reserve(NNZ);
+    pm.reserve(N);
+  } catch (const std::bad_alloc&) {
+    return set_error(MF_ERR_OOM, "host allocation failed");
+  }
+  rp.push_back(0);
+  int64_t off = 0;
+  for (int32_t b = 0; b < count; ++b) {
+    const int64_t n = ns[b];
+    const int64_t* r = rowptrs[b];
+    if (r[0] != 0) return set_error(MF_ERR_INVALID, "batch member rowptr[0] != 0");
+    for (int64_t i = 0; i < n; ++i) {
+      if (r[i + 1] < r[i]) return set_error(MF_ERR_INVALID, "batch member rowptr decreasing");
+      for (int64_t p = r[i]; p < r[i + 1]; ++p) {
+        const int32_t c = colinds[b][p];
+        if (c < 0 || c >= n) return set_error(MF_ERR_INVALID, "batch member colind out of range");
+        ci.push_back((int32_t)(c + off));
+      }
+      rp.push_back((int64_t)ci.size());
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t o = (perms && perms[b]) ? perms[b][i] : (int32_t)i;
+      if (o < 0 || o >= n) return set_error(MF_ERR_INVALID, "batch member perm out of range");
+      pm.push_back((int32_t)(o + off));
+    }
+    off += n;
+  }
+  return mf_symbolic_analyze(h, N, rp.data(), ci.data(), pm.data(), s);
+}
+
+int mf_symbolic_free(mf_symbolic* s) {
+  delete s;
+  return MF_OK;
+}
+
+int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info) {
+  if (!s || !info) return set_error(MF_ERR_INVALID, "NULL argument");
+  info->n = s->n;
+  info->nnz_lower = s->nnz_lower;
+  info->nsuper = s->nsuper;
+  info->nnz_L = s->nnzL;
+  info->flops = s->flops;
+  info->nlevels = s->nlevels;
+  info->max_front = s->max_front;
+  info->max_k = s->max_k;
+  info->factor_bytes_fp64 = factor_bytes(s, MF_FP64);
+  info->factor_bytes_fp32 = factor_bytes(s, MF_FP32);
+  return MF_OK;
+}
+
+int mf_symbolic_etree(const mf_symbolic* s, int32_t* parent) {
+  if (!s || (!parent && s->n)) return set_error(MF_ERR_INVALID, "NULL argument");
+  std::copy(s->parent.begin(), s->parent.end(), parent);
+  return MF_OK;
+}
+
+int mf_symbolic_colcounts(const mf_symbolic* s, int64_t* counts) {
+  if (!s || (!counts && s->n)) return set_error(MF_ERR_INVALID, "NULL argument");
+  std::copy(s->colcount.begin(), s->colcount.end(), counts);
+  return MF_OK;
+}
+
+int mf_symbolic_supernodes(const mf_symbolic* s, int32_t* sup_ptr) {
+  if (!s || !sup_ptr) return set_error(MF_ERR_INVALID, "NULL argument");
+  if (s->n == 0) {
+    sup_ptr[0] = 0;
+    return MF_OK;
+  }
+  std::copy(s->sup_ptr.begin(), s->sup_ptr.end(), sup_ptr);
+  return MF_OK;
+}
+
+int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li) {
+  if (!s || !Lp || (!Li && s->nnzL)) return set_error(MF_ERR_INVALID, "NULL argument");
+  Lp[0] = 0;
+  int64_t pos = 0;
+  for (int64_t sn = 0; sn < s->nsuper; ++sn) {
+    const mf::SnInfo& I = s->sn[sn];
+    const int32_t* rows = s->rowidx.data() + I.rows_off;
+    const int nf = I.k + I.m;
+    for (int t = 0; t < I.k; ++t) {
+      for (int r = t; r < nf; ++r) Li[pos++] = rows[r];
+      Lp[I.first + t + 1] = pos;
+    }
+  }
+  return MF_OK;
+}
+
+int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent, int32_t* level) {
+  if (!s) return set_error(MF_ERR_INVALID, "NULL argument");
+  for (int64_t i = 0; i < s->nsuper; ++i) {
+    if (sparent) sparent[i] = s->sn[i].parent;
+    if (level) level[i] = s->slevel[i];
+  }
+  return MF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Factor
+// ---------------------------------------------------------------------------
+int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
+  if (!h || !s || !f) return set_error(MF_ERR_INVALID, "NULL argument");
+  if (prec != MF_FP64 && prec != MF_FP32) return set_error(MF_ERR_INVALID, "bad precision");
+  *f = nullptr;
+  const int64_t need = factor_bytes(s, prec);
+  if (h->opt.budget_bytes > 0 && need > h->opt.budget_bytes)
+    return set_error(MF_ERR_OOM, "factor exceeds the device budget");
+  std::unique_ptr<mf_factor> F(new (std::nothrow) mf_factor());
+  if (!F) return set_error(MF_ERR_OOM, "host allocation failed");
+  F->h = h;
+  F->S = s;
+  F->prec = prec;
+  int rc = get_devsym(s, F->ds);
+  if (rc != MF_OK) return rc;
+  const size_t es = elem_size(prec);
+  MF_CK(cudaMalloc(&F->L, std::max<int64_t>(s->Lsize, 1) * es));
+  MF_CK(cudaMalloc(&F->U, std::max<int64_t>(s->Usize, 1) * es));
+  MF_CK(cudaMalloc(&F->vals, std::max<int64_t>(s->nnzA, 1) * sizeof(double)));
+  MF_CK(cudaMalloc(&F->status, 2 * sizeof(unsigned long long)));
+  MF_CK(cudaMallocHost(&F->status_host, 2 * sizeof(unsigned long long)));
+  MF_CK(mf::factor_kernels_init(prec));
+  MF_CK(mf::solve_kernels_init(prec));
+  *f = F.release();
+  return MF_OK;
+}
+
+static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile) {
+  const mf_symbolic* S = F->S;
+  mf::FactorArgs a;
+  a.sym = F->ds->d;
+  a.vals = F->vals;
+  a.L = F->L;
+  a.U = F->U;
+  a.status = F->status;
+  MF_CK(cudaMemsetAsync(F->status, 0xff, 2 * sizeof(unsigned long long), st));
+  if (profile && F->ev.size() < 2 * S->fsched.size()) {
+    const size_t old = F->ev.size();
+    F->ev.resize(2 * S->fsched.size());
+    for (size_t i = old; i < F->ev.size(); ++i) MF_CK(cudaEventCreate(&F->ev[i]));
+  }
+  for (size_t i = 0; i < S->fsched.size(); ++i) {
+    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i], st));
+    MF_CK(mf::launch_factor(F->prec, S->fsched[i], a, st));
+    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i + 1], st));
+  }
+  return MF_OK;
+}
+
+int mf_factor_numeric(mf_factor* f, const double* values, int32_t values_on_device, void* stream,
+                      int32_t async) {
+  if (!f || (!values && f->S->nnzA)) return set_error(MF_ERR_INVALID, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const mf_symbolic* S = f->S;
+  if (S->nnzA)
+    MF_CK(cudaMemcpyAsync(f->vals, values, S->nnzA * sizeof(double),
+                          values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  const bool profile = f->h->opt.profile != 0;
+  if (f->h->opt.use_graphs && !profile) {
+    if (!f->gexec) {
+      MF_CK(cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking));
+      MF_CK(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int rc = enqueue_factor(f, f->cap_stream, false);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(f->cap_stream, &g);
+      if (rc != MF_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      MF_CK(e);
+      e = cudaGraphInstantiate(&f->gexec, g, 0);
+      cudaGraphDestroy(g);
+      MF_CK(e);
+    }
+    MF_CK(cudaGraphLaunch(f->gexec, st));
+  } else {
+    int rc = enqueue_factor(f, st, profile);
+    if (rc != MF_OK) return rc;
+  }
+  f->numeric_done = true;
+  if (async) return MF_OK;
+  return mf_factor_check(f, stream);
+}
+
+int mf_factor_check(mf_factor* f, void* stream) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MF_CK(cudaMemcpyAsync(f->status_host, f->status, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, st));
+  MF_CK(cudaStreamSynchronize(st));
+  if (f->h->opt.profile) {
+    const mf_symbolic* S = f->S;
+    for (int k = 0; k < mf::K_NKINDS_FACTOR; ++k) {
+      f->prof_ms[k] = 0;
+      f->prof_n[k] = 0;
+      f->prof_fl[k] = 0;
+    }
+    if (f->ev.size() >= 2 * S->fsched.size()) {
+      for (size_t i = 0; i < S->fsched.size(); ++i) {
+        float ms = 0.f;
+        MF_CK(cudaEventElapsedTime(&ms, f->ev[2 * i], f->ev[2 * i + 1]));
+        const int k = S->fsched[i].kind;
+        f->prof_ms[k] += ms;
+        f->prof_n[k] += 1;
+        f->prof_fl[k] += S->fsched[i].flops;
+      }
+    }
+  }
+  const unsigned long long bad = f->status_host[0];
+  if (bad != ~0ull) {
+    set_error(MF_ERR_NOT_SPD, "matrix is not positive definite");
+    g_errcol = (int64_t)bad;
+    return MF_ERR_NOT_SPD;
+  }
+  return MF_OK;
+}
+
+int mf_factor_free(mf_factor* f) {
+  delete f;
+  return MF_OK;
+}
+
+int mf_factor_export_L(const mf_factor* f, double* Lx) {
+  if (!f || (!Lx && f->S->nnzL)) return set_error(MF_ERR_INVALID, "NULL argument");
+  const mf_symbolic* S = f->S;
+  const size_t es = elem_size(f->prec);
+  std::vector<unsigned char> buf;
+  try {
+    buf.resize(S->Lsize * es);
+  } catch (const std::bad_alloc&) {
+    return set_error(MF_ERR_OOM, "host allocation failed");
+  }
+  MF_CK(cudaDeviceSynchronize());
+  if (S->Lsize) MF_CK(cudaMemcpy(buf.data(), f->L, S->Lsize * es, cudaMemcpyDeviceToHost));
+  int64_t pos = 0;
+  for (int64_t sn = 0; sn < S->nsuper; ++sn) {
+    const mf::SnInfo& I = S->sn[sn];
+    const int64_t nf = I.k + I.m;
+    for (int t = 0; t < I.k; ++t)
+      for (int64_t r = t; r < nf; ++r) {
+        const int64_t idx = I.Loff + t * nf + r;
+        Lx[pos++] = f->prec == MF_FP32 ? (double)reinterpret_cast<const float*>(buf.data())[idx]
+                                       : reinterpret_cast<const double*>(buf.data())[idx];
+      }
+  }
+  return MF_OK;
+}
+
+int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches, int64_t* solve_launches) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  if (factor_launches) *factor_launches = (int64_t)f->S->fsched.size();
+  if (solve_launches) *solve_launches = (int64_t)(f->S->fwsched.size() + f->S->bwsched.size() + 2);
+  return MF_OK;
+}
+
+int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches, double* flops) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  for (int k = 0; k < mf::K_NKINDS_FACTOR; ++k) {
+    if (ms) ms[k] = f->prof_ms[k];
+    if (launches) launches[k] = f->prof_n[k];
+    if (flops) flops[k] = f->prof_fl[k];
+  }
+  return MF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve
+// ---------------------------------------------------------------------------
+namespace {
+
+int ensure_solve_buffers(mf_factor* f) {
+  const mf_symbolic* S = f->S;
+  const size_t es = elem_size(f->prec);
+  if (!f->Y) MF_CK(cudaMalloc(&f->Y, std::max<int64_t>(S->n * mf::kSolveChunk, 1) * es));
+  if (!f->W) MF_CK(cudaMalloc(&f->W, std::max<int64_t>(S->Wsize * mf::kSolveChunk, 1) * es));
+  if (!f->small) MF_CK(cudaMalloc(&f->small, 4096 * sizeof(double)));
+  return MF_OK;
+}
+
+int ensure_io(mf_factor* f, int64_t doubles) {
+  if (doubles <= f->io_cap) return MF_OK;
+  cudaFree(f->Bd);
+  cudaFree(f->Xd);
+  cudaFree(f->Rd);
+  f->Bd = f->Xd = f->Rd = nullptr;
+  f->io_cap = 0;
+  MF_CK(cudaMalloc(&f->Bd, doubles * sizeof(double)));
+  MF_CK(cudaMalloc(&f->Xd, doubles * sizeof(double)));
+  MF_CK(cudaMalloc(&f->Rd, doubles * sizeof(double)));
+  f->io_cap = doubles;
+  return MF_OK;
+}
+
+// X (=|+=) scale * A^{-1} (inv_scale * B), device pointers, chunked RHS.
+int solve_dev(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+              const double* inv_scale, const double* scale, int accumulate, cudaStream_t st) {
+  const mf_symbolic* S = f->S;
+  int rc = ensure_solve_buffers(f);
+  if (rc != MF_OK) return rc;
+  for (int32_t c0 = 0; c0 < nrhs; c0 += mf::kSolveChunk) {
+    const int32_t cn = std::min<int32_t>(mf::kSolveChunk, nrhs - c0);
+    MF_CK(mf::launch_perm_in(f->prec, B + c0 * ldb, ldb, f->ds->d.perm, f->Y, S->n, cn,
+                             inv_scale ? inv_scale + c0 : nullptr, st));
+    mf::SolveArgs a;
+    a.sym = f->ds->d;
+    a.L = f->L;
+    a.Y = f->Y;
+    a.W = f->W;
+    a.n = S->n;
+    a.nrhs = cn;
+    for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
+    for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
+    MF_CK(mf::launch_perm_out(f->prec, f->Y, f->ds->d.perm, X + c0 * ldx, ldx, S->n, cn,
+                              scale ? scale + c0 : nullptr, accumulate, st));
+  }
+  return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+             int32_t on_device, void* stream) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  const int64_t n = f->S->n;
+  if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
+    return set_error(MF_ERR_INVALID, "invalid solve arguments");
+  if (!f->numeric_done) return set_error(MF_ERR_INVALID, "factor has no numeric values");
+  if (nrhs == 0 || n == 0) return MF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (on_device) return solve_dev(f, nrhs, B, ldb, X, ldx, nullptr, nullptr, 0, st);
+  int rc = ensure_io(f, n * (int64_t)nrhs);
+  if (rc != MF_OK) return rc;
+  MF_CK(cudaMemcpy2DAsync(f->Bd, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double),
+                          nrhs, cudaMemcpyHostToDevice, st));
+  rc = solve_dev(f, nrhs, f->Bd, n, f->Xd, n, nullptr, nullptr, 0, st);
+  if (rc != MF_OK) return rc;
+  MF_CK(cudaMemcpy2DAsync(X, ldx * sizeof(double), f->Xd, n * sizeof(double), n * sizeof(double),
+                          nrhs, cudaMemcpyDeviceToHost, st));
+  MF_CK(cudaStreamSynchronize(st));
+  return MF_OK;
+}
+
+int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X,
+                     int64_t ldx, int32_t on_device, double tol, int32_t max_iter,
+                     int32_t allow_fallback, mf_ir_report* rep, void* stream) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  const mf_symbolic* S = f->S;
+  const int64_t n = S->n;
+  if (nrhs < 0 || nrhs > 512 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
+    return set_error(MF_ERR_INVALID, "invalid refinement arguments");
+  if (!f->numeric_done) return set_error(MF_ERR_INVALID, "factor has no numeric values");
+  if (rep) std::memset(rep, 0, sizeof(*rep));
+  if (nrhs == 0 || n == 0) return MF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = ensure_io(f, n * (int64_t)nrhs);
+  if (rc != MF_OK) return rc;
+  rc = ensure_solve_buffers(f);
+  if (rc != MF_OK) return rc;
+  // device B (ld n) and X (ld n)
+  if (on_device)
+    MF_CK(cudaMemcpy2DAsync(f->Bd, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double),
+                            nrhs, cudaMemcpyDeviceToDevice, st));
+  else
+    MF_CK(cudaMemcpy2DAsync(f->Bd, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double),
+                            nrhs, cudaMemcpyHostToDevice, st));
+  double* dsm = f->small;  // [0] |A|, [1..nrhs] |b|, then rnorm, xnorm, scale, inv
+  double* d_an = dsm;
+  double* d_bn = dsm + 1;
+  double* d_rn = dsm + 1 + nrhs;
+  double* d_xn = d_rn + nrhs;
+  double* d_sc = d_xn + nrhs;
+  double* d_isc = d_sc + nrhs;
+  MF_CK(cudaMemsetAsync(dsm, 0, (1 + nrhs) * sizeof(double), st));
+  MF_CK(mf::launch_norms(f->ds->d.rowptr, f->vals, n, f->Bd, n, nrhs, d_an, st));
+  std::vector<double> hn(1 + 2 * nrhs), hs(2 * nrhs);
+  MF_CK(cudaMemcpyAsync(hn.data(), dsm, (1 + nrhs) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // x0 = solve(b)
+  rc = solve_dev(f, nrhs, f->Bd, n, f->Xd, n, nullptr, nullptr, 0, st);
+  if (rc != MF_OK) return rc;
+  MF_CK(cudaStreamSynchronize(st));
+  const double anorm = hn[0];
+  std::vector<double> bnorm(hn.begin() + 1, hn.begin() + 1 + nrhs);
+  std::vector<double> hist;
+  double berr = 0.0;
+  int it = 0;
+  bool converged = false;
+  for (;; ++it) {
+    MF_CK(cudaMemsetAsync(d_rn, 0, 2 * nrhs * sizeof(double), st));
+    MF_CK(mf::launch_residual(f->ds->d.rowptr, f->ds->d.colind, f->vals, n, f->Bd, n, f->Xd, n,
+                              f->Rd, nrhs, d_rn, d_xn, st));
+    MF_CK(cudaMemcpyAsync(hn.data() + 1, d_rn, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MF_CK(cudaStreamSynchronize(st));
+    berr = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+      const double den = anorm * hn[1 + nrhs + r] + bnorm[r];
+      const double br = den > 0 ? hn[1 + r] / den : 0.0;
+      berr = std::max(berr, br);
+    }
+    if (it == 0 && rep) rep->berr_first = berr;
+    hist.push_back(berr);
+    if (berr <= tol) {
+      converged = true;
+      break;
+    }
+    const bool stagnated =
+        it >= max_iter || (hist.size() >= 3 && berr > 0.5 * hist[hist.size() - 3]);
+    if (stagnated) break;
+    for (int r = 0; r < nrhs; ++r) {
+      const double rn = hn[1 + r];
+      hs[r] = rn;
+      hs[nrhs + r] = rn > 0 ? 1.0 / rn : 0.0;
+    }
+    MF_CK(cudaMemcpyAsync(d_sc, hs.data(), 2 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+    rc = solve_dev(f, nrhs, f->Rd, n, f->Xd, n, d_isc, d_sc, 1, st);
+    if (rc != MF_OK) return rc;
+  }
+  bool fell_back = false;
+  if (!converged) {
+    if (!allow_fallback) {
+      if (rep) {
+        rep->iterations = it;
+        rep->berr = berr;
+      }
+      return set_error(MF_ERR_STAGNATION, "iterative refinement stagnated");
+    }
+    if (!f->fb64) {
+      rc = mf_factor_create(f->h, S, MF_FP64, &f->fb64);
+      if (rc != MF_OK) return rc;
+    }
+    rc = mf_factor_numeric(f->fb64, f->vals, 1, stream, 0);
+    if (rc != MF_OK) return rc;
+    rc = solve_dev(f->fb64, nrhs, f->Bd, n, f->Xd, n, nullptr, nullptr, 0, st);
+    if (rc != MF_OK) return rc;
+    MF_CK(cudaMemsetAsync(d_rn, 0, 2 * nrhs * sizeof(double), st));
+    MF_CK(mf::launch_residual(f->ds->d.rowptr, f->ds->d.colind, f->vals, n, f->Bd, n, f->Xd, n,
+                              f->Rd, nrhs, d_rn, d_xn, st));
+    MF_CK(cudaMemcpyAsync(hn.data() + 1, d_rn, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MF_CK(cudaStreamSynchronize(st));
+    berr = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+      const double den = anorm * hn[1 + nrhs + r] + bnorm[r];
+      berr = std::max(berr, den > 0 ? hn[1 + r] / den : 0.0);
+    }
+    fell_back = true;
+  }
+  if (on_device)
+    MF_CK(cudaMemcpy2DAsync(X, ldx * sizeof(double), f->Xd, n * sizeof(double), n * sizeof(double),
+                            nrhs, cudaMemcpyDeviceToDevice, st));
+  else
+    MF_CK(cudaMemcpy2DAsync(X, ldx * sizeof(double), f->Xd, n * sizeof(double), n * sizeof(double),
+                            nrhs, cudaMemcpyDeviceToHost, st));
+  MF_CK(cudaStreamSynchronize(st));
+  if (rep) {
+    rep->iterations = it;
+    rep->fell_back = fell_back ? 1 : 0;
+    rep->berr = berr;
+  }
+  return MF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// kernels.h -- type-erased argument blocks and launchers of the device
+// kernels (factor_kernels.cu, solve_kernels.cu).  Host code in capi.cpp
+// fills these and calls the launchers; it never sees a template.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mf_internal.h"
+
+namespace mf {
+
+// Device mirror of a symbolic object (read-only during numeric work).
+struct DevSym {
+  SnInfo* sn = nullptr;
+  int32_t* children = nullptr;
+  int32_t* relmap = nullptr;
+  int32_t* rowidx = nullptr;
+  int64_t* acol_ptr = nullptr;
+  int32_t* arow = nullptr;
+  int64_t* asrc_ptr = nullptr;
+  int64_t* asrc = nullptr;
+  Item* items = nullptr;
+  int32_t* perm = nullptr;     // perm[new] = old
+  int64_t* rowptr = nullptr;   // A (original order) for the FP64 residual
+  int32_t* colind = nullptr;
+};
+
+struct FactorArgs {
+  DevSym sym;
+  const double* vals;          // A values, CSR order (device)
+  void* L;                     // T[Lsize]
+  void* U;                     // T[Usize]
+  unsigned long long* status;  // [0] = first non-positive pivot column
+};
+
+struct SolveArgs {
+  DevSym sym;
+  const void* L;  // T
+  void* Y;        // T[n * nrhs]  permuted RHS / solution
+  void* W;        // T[Wsize * nrhs] front work vectors
+  int64_t n;
+  int32_t nrhs;
+};
+
+// prec: MF_FP64 or MF_FP32.  All launchers return cudaGetLastError().
+cudaError_t factor_kernels_init(int prec);
+cudaError_t launch_factor(int prec, const Launch& L, const FactorArgs& a, cudaStream_t st);
+cudaError_t solve_kernels_init(int prec);
+cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStream_t st);
+
+// Y[i, r] = T(scale_r * B[perm[i], r]) with scale_r = inv_scale ? inv_scale[r] : 1.
+cudaError_t launch_perm_in(int prec, const double* B, int64_t ldb, const int32_t* perm,
+                           void* Y, int64_t n, int32_t nrhs, const double* inv_scale,
+                           cudaStream_t st);
+// X[perm[i], r] (=|+=) scale_r * Y[i, r]; accumulate != 0 adds.
+cudaError_t launch_perm_out(int prec, const void* Y, const int32_t* perm, double* X,
+                            int64_t ldx, int64_t n, int32_t nrhs, const double* scale,
+                            int32_t accumulate, cudaStream_t st);
+
+// FP64 residual R = B - A X (A in original order), with per-RHS maxima of
+// |R|, |X| accumulated into rnorm[r], xnorm[r] (must be zeroed before).
+cudaError_t launch_residual(const int64_t* rowptr, const int32_t* colind, const double* vals,
+                            int64_t n, const double* B, int64_t ldb, const double* X,
+                            int64_t ldx, double* R, int32_t nrhs, double* rnorm,
+                            double* xnorm, cudaStream_t st);
+// out[0] = max_i sum_j |A_ij|; out[1 + r] = max_i |B_ir|  (out zeroed before)
+cudaError_t launch_norms(const int64_t* rowptr, const double* vals, int64_t n,
+                         const double* B, int64_t ldb, int32_t nrhs, double* out,
+                         cudaStream_t st);
+
+}  // namespace mf

@@ -1,0 +1,124 @@
+// mf_internal.h -- shared host/device declarations of the GB300 multifrontal
+// Cholesky library (not part of the public C-ABI).
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mfchol.h"
+
+namespace mf {
+
+// Panel width of the blocked large-front factorization and of the blocked
+// solve, the square tile of the trailing update, rows per TRSM block, and the
+// column chunk of the large-front assembly.
+constexpr int kNB = 64;
+constexpr int kTile = 64;
+constexpr int kTrsmRows = 64;
+constexpr int kAsmCols = 32;
+constexpr int kSmallMax = 128;   // largest front (k+m) of the one-CTA kernel
+constexpr int kSolveChunk = 32;  // right-hand sides per solve pass
+
+// Per-supernode record, read by every kernel (64 bytes).
+struct SnInfo {
+  int32_t first;        // first (permuted) column
+  int32_t k;            // width (pivot columns)
+  int32_t m;            // update rows
+  int32_t nchild;       // children in the supernodal tree
+  int32_t child_begin;  // offset into the children list
+  int32_t parent;       // parent supernode or -1
+  int64_t Loff;         // L panel offset (elements), (k+m) x k column-major
+  int64_t Uoff;         // update matrix offset (elements), m x m column-major
+  int64_t rows_off;     // offset into rowidx (k+m global row indices)
+  int64_t map_off;      // offset into relmap (m positions in the parent front)
+  int64_t woff;         // offset (elements per RHS) of the solve work front
+};
+static_assert(sizeof(SnInfo) == 64, "SnInfo layout");
+
+// One work item of a batched launch.
+struct Item {
+  int32_t s, t, a, b;
+};
+
+enum Kind : int32_t {
+  K_SMALL = 0,     // fused assemble + partial Cholesky of a small front
+  K_ASSEMBLE = 1,  // zero + scatter A + extend-add of children (large fronts)
+  K_POTRF = 2,     // diagonal block Cholesky
+  K_TRSM = 3,      // panel rows * L_tt^{-T}
+  K_SYRK = 4,      // trailing lower update
+  K_NKINDS_FACTOR = 5,
+  K_FW_SMALL = 10,
+  K_FW_GATHER = 11,
+  K_FW_DIAG = 12,
+  K_FW_UPD = 13,
+  K_BW_SMALL = 14,
+  K_BW_OFFDIAG = 15,
+  K_BW_DIAG = 16,
+  K_BW_UPD = 17,
+};
+
+struct Launch {
+  int32_t kind;
+  int32_t level;
+  int32_t count;   // items (= CTAs)
+  int32_t param;   // small-front size class (max k+m) or step
+  int64_t item_off;
+  double flops;    // algorithmic flops of this launch
+};
+
+}  // namespace mf
+
+// Host-side symbolic object.
+struct mf_symbolic {
+  int64_t n = 0;
+  int64_t nnzA = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> colind;
+  std::vector<int32_t> perm, iperm;
+  std::vector<int32_t> parent;    // column etree
+  std::vector<int64_t> colcount;  // c_j
+  std::vector<int32_t> sup_ptr;   // nsuper + 1
+  std::vector<int32_t> col2sn;
+  int64_t nsuper = 0, nnzL = 0, nnz_lower = 0;
+  double flops = 0.0;
+  int32_t nlevels = 0;
+  int64_t max_front = 0, max_k = 0;
+  std::vector<mf::SnInfo> sn;
+  std::vector<int32_t> children;
+  std::vector<int32_t> rowidx;
+  std::vector<int32_t> relmap;
+  std::vector<int32_t> slevel;
+  // assembly of A into the fronts: per permuted column j, entries
+  // acol_ptr[j]..acol_ptr[j+1] with front-relative row arow[e] and source
+  // CSR positions asrc[asrc_ptr[e] .. asrc_ptr[e+1]) (duplicates summed)
+  std::vector<int64_t> acol_ptr;
+  std::vector<int32_t> arow;
+  std::vector<int64_t> asrc_ptr;
+  std::vector<int64_t> asrc;
+  int64_t Lsize = 0, Usize = 0, Wsize = 0;
+  // launch schedules
+  std::vector<mf::Item> items;
+  std::vector<mf::Launch> fsched;
+  std::vector<mf::Launch> fwsched, bwsched;
+  // device mirror, created on first use by a factor on this device
+  mutable std::mutex dev_mu;
+  mutable std::shared_ptr<void> dev;
+  mutable int dev_device = -1;
+};
+
+struct mf_handle {
+  int device = 0;
+  mf_options opt{};
+};
+
+namespace mf {
+// symbolic.cpp
+int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
+            const int32_t* perm, std::string& err);
+void build_schedules(mf_symbolic& S, int small_max);
+// error reporting (capi.cpp)
+int set_error(int code, const std::string& msg);
+}  // namespace mf

@@ -1,0 +1,614 @@
+// symbolic.cpp -- host symbolic analysis of the multifrontal Cholesky
+// (paper Sec. 2, phase 1: "symbolic analysis uses only the sparsity
+// structure"; run sequentially on one host core as the paper describes for
+// Tacho, its cost amortised over many numeric factorizations).
+//
+// Steps, all on C = A(perm, perm):
+//   1. validate the CSR and the permutation;
+//   2. strict lower triangle of C by rows and by columns;
+//   3. elimination tree (Liu's algorithm with path compression);
+//   4. postorder and column counts with the row-subtree leaf/LCA method of
+//      Gilbert, Ng and Peyton (O(nnz(A) alpha(n)), no fill-in enumeration);
+//   5. fundamental supernodes;
+//   6. front row lists by merging each supernode's A pattern with its
+//      children's update rows; child-to-parent relative maps;
+//   7. level sets of the supernodal tree (height: leaves = 0), memory plan,
+//      per-column assembly map of A into the fronts.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "mf_internal.h"
+
+namespace mf {
+
+namespace {
+
+int invalid(std::string& err, const std::string& msg) {
+  err = msg;
+  return MF_ERR_INVALID;
+}
+
+}  // namespace
+
+// Device memory of the update matrices.  U_s is written when front s is
+// factored (level(s)) and read when its parent is assembled
+// (level(parent(s))); after that level it is dead.  Blocks are placed first
+// fit in a simulated heap, level by level, so chains of thin supernodes reuse
+// the same memory instead of holding every update matrix at once.  Returns
+// the peak size (elements) and sets Uoff for every supernode.
+int64_t plan_update_memory(mf_symbolic& S) {
+  const int64_t ns = S.nsuper;
+  std::vector<std::vector<int32_t>> bylev(S.nlevels);
+  for (int64_t s = 0; s < ns; ++s) bylev[S.slevel[s]].push_back((int32_t)s);
+  std::map<int64_t, int64_t> freeb;  // offset -> size
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> release(S.nlevels + 1);
+  int64_t top = 0;
+  for (int32_t lev = 0; lev < S.nlevels; ++lev) {
+    // blocks read at level lev-1 are dead now
+    if (lev >= 1) {
+      for (const auto& b : release[lev - 1]) {
+        auto it = freeb.emplace(b.first, b.second).first;
+        auto nx = std::next(it);
+        if (nx != freeb.end() && it->first + it->second == nx->first) {
+          it->second += nx->second;
+          freeb.erase(nx);
+        }
+        if (it != freeb.begin()) {
+          auto pv = std::prev(it);
+          if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            freeb.erase(it);
+          }
+        }
+      }
+      release[lev - 1].clear();
+    }
+    std::vector<int32_t> L = bylev[lev];
+    std::sort(L.begin(), L.end(), [&](int32_t a, int32_t b) {
+      return (int64_t)S.sn[a].m * S.sn[a].m > (int64_t)S.sn[b].m * S.sn[b].m;
+    });
+    for (int32_t s : L) {
+      SnInfo& I = S.sn[s];
+      // 32-element alignment keeps every update matrix 128/256-byte aligned
+      const int64_t sz = (((int64_t)I.m * I.m) + 31) / 32 * 32;
+      if (sz == 0 || I.parent < 0) {
+        I.Uoff = 0;
+        continue;
+      }
+      int64_t off = -1;
+      for (auto it = freeb.begin(); it != freeb.end(); ++it) {
+        if (it->second >= sz) {
+          off = it->first;
+          const int64_t rest = it->second - sz;
+          freeb.erase(it);
+          if (rest > 0) freeb.emplace(off + sz, rest);
+          break;
+        }
+      }
+      if (off < 0) {
+        // grow the heap; merge with a free block that ends at the top
+        if (!freeb.empty()) {
+          auto last = std::prev(freeb.end());
+          if (last->first + last->second == top) {
+            off = last->first;
+            freeb.erase(last);
+          }
+        }
+        if (off < 0) off = top;
+        top = off + sz;
+      }
+      I.Uoff = off;
+      release[S.slevel[I.parent]].push_back({off, sz});
+    }
+  }
+  return top;
+}
+
+int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
+            const int32_t* perm, std::string& err) {
+  if (n < 0 || n >= (int64_t)INT32_MAX) return invalid(err, "n out of range");
+  if (!rowptr) return invalid(err, "rowptr is NULL");
+  if (rowptr[0] != 0) return invalid(err, "rowptr[0] != 0");
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return invalid(err, "rowptr is decreasing");
+  const int64_t nnz = rowptr[n];
+  if (nnz > 0 && !colind) return invalid(err, "colind is NULL");
+  for (int64_t p = 0; p < nnz; ++p)
+    if (colind[p] < 0 || colind[p] >= n) return invalid(err, "colind out of range");
+
+  S.n = n;
+  S.nnzA = nnz;
+  S.rowptr.assign(rowptr, rowptr + n + 1);
+  S.colind.assign(colind, colind + nnz);
+  S.perm.resize(n);
+  S.iperm.assign(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t o = perm ? perm[i] : (int32_t)i;
+    if (o < 0 || o >= n || S.iperm[o] != -1) return invalid(err, "perm is not a permutation");
+    S.perm[i] = o;
+    S.iperm[o] = (int32_t)i;
+  }
+  const std::vector<int32_t>& ip = S.iperm;
+
+  // ---- 2. strict lower triangle of C by rows (rp/ri) and columns (cp/cr)
+  std::vector<int64_t> rp(n + 1, 0), cp(n + 1, 0);
+  for (int64_t ro = 0; ro < n; ++ro) {
+    const int32_t i = ip[ro];
+    for (int64_t p = rowptr[ro]; p < rowptr[ro + 1]; ++p) {
+      const int32_t j = ip[colind[p]];
+      if (j < i) {
+        rp[i + 1]++;
+        cp[j + 1]++;
+      }
+    }
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    rp[i + 1] += rp[i];
+    cp[i + 1] += cp[i];
+  }
+  std::vector<int32_t> ri(rp[n]), cr(cp[n]);
+  {
+    std::vector<int64_t> rf(rp.begin(), rp.end() - 1), cf(cp.begin(), cp.end() - 1);
+    for (int64_t ro = 0; ro < n; ++ro) {
+      const int32_t i = ip[ro];
+      for (int64_t p = rowptr[ro]; p < rowptr[ro + 1]; ++p) {
+        const int32_t j = ip[colind[p]];
+        if (j < i) {
+          ri[rf[i]++] = j;
+          cr[cf[j]++] = i;
+        }
+      }
+    }
+  }
+
+  // ---- 3. elimination tree
+  std::vector<int32_t>& parent = S.parent;
+  parent.assign(n, -1);
+  {
+    std::vector<int32_t> anc(n, -1);
+    for (int32_t i = 0; i < n; ++i) {
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int32_t r = ri[p];
+        while (r != -1 && r < i) {
+          const int32_t nx = anc[r];
+          anc[r] = i;
+          if (nx == -1) parent[r] = i;
+          r = nx;
+        }
+      }
+    }
+  }
+
+  // ---- 4. postorder + column counts (row-subtree leaves and LCAs)
+  std::vector<int32_t> post(n);
+  {
+    std::vector<int32_t> head(n, -1), next(n, -1), stack;
+    for (int32_t j = (int32_t)n - 1; j >= 0; --j) {
+      if (parent[j] != -1) {
+        next[j] = head[parent[j]];
+        head[parent[j]] = j;
+      }
+    }
+    int32_t k = 0;
+    stack.reserve(n);
+    for (int32_t r = 0; r < n; ++r) {
+      if (parent[r] != -1) continue;
+      stack.push_back(r);
+      while (!stack.empty()) {
+        const int32_t p = stack.back();
+        const int32_t c = head[p];
+        if (c == -1) {
+          stack.pop_back();
+          post[k++] = p;
+        } else {
+          head[p] = next[c];
+          stack.push_back(c);
+        }
+      }
+    }
+    if (k != n) {
+      err = "postorder incomplete";
+      return MF_ERR_INTERNAL;
+    }
+  }
+  std::vector<int64_t> delta(n, 0);
+  {
+    std::vector<int32_t> first(n, -1), maxfirst(n, -1), prevleaf(n, -1), ancestor(n);
+    for (int32_t k = 0; k < n; ++k) {
+      int32_t j = post[k];
+      delta[j] = (first[j] == -1) ? 1 : 0;  // etree leaf: row subtree {j}
+      for (; j != -1 && first[j] == -1; j = parent[j]) first[j] = k;
+    }
+    std::iota(ancestor.begin(), ancestor.end(), 0);
+    for (int32_t k = 0; k < n; ++k) {
+      const int32_t j = post[k];
+      if (parent[j] != -1) delta[parent[j]]--;  // every row subtree ends below parent(root)
+      for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+        const int32_t i = cr[p];
+        if (first[j] <= maxfirst[i]) continue;  // j is not a leaf of row subtree i
+        maxfirst[i] = first[j];
+        const int32_t jprev = prevleaf[i];
+        prevleaf[i] = j;
+        delta[j]++;
+        if (jprev != -1) {
+          int32_t q = jprev;
+          while (q != ancestor[q]) q = ancestor[q];
+          for (int32_t s = jprev; s != q;) {
+            const int32_t sp = ancestor[s];
+            ancestor[s] = q;
+            s = sp;
+          }
+          delta[q]--;  // lca of consecutive leaves counted twice
+        }
+      }
+      if (parent[j] != -1) ancestor[j] = parent[j];
+    }
+    for (int32_t k = 0; k < n; ++k) {
+      const int32_t j = post[k];
+      if (parent[j] != -1) delta[parent[j]] += delta[j];
+    }
+  }
+  S.colcount = delta;
+  S.nnzL = 0;
+  S.flops = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    S.nnzL += S.colcount[j];
+    S.flops += (double)S.colcount[j] * (double)S.colcount[j];
+  }
+
+  // ---- 5. fundamental supernodes
+  std::vector<int32_t> nchild(n, 0);
+  for (int64_t j = 0; j < n; ++j)
+    if (parent[j] != -1) nchild[parent[j]]++;
+  S.sup_ptr.clear();
+  S.sup_ptr.push_back(0);
+  for (int64_t j = 0; j + 1 < n; ++j) {
+    const bool joins = parent[j] == j + 1 && S.colcount[j] == S.colcount[j + 1] + 1 &&
+                       nchild[j + 1] == 1;
+    if (!joins) S.sup_ptr.push_back((int32_t)(j + 1));
+  }
+  if (n > 0) S.sup_ptr.push_back((int32_t)n);
+  const int64_t ns = n > 0 ? (int64_t)S.sup_ptr.size() - 1 : 0;
+  S.nsuper = ns;
+  S.col2sn.assign(n, 0);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int32_t j = S.sup_ptr[s]; j < S.sup_ptr[s + 1]; ++j) S.col2sn[j] = (int32_t)s;
+
+  // supernodal tree and children lists (children in increasing order)
+  std::vector<int32_t> sparent(ns, -1);
+  std::vector<int32_t> schild_cnt(ns + 1, 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    const int32_t l = S.sup_ptr[s + 1] - 1;
+    const int32_t p = parent[l];
+    sparent[s] = p == -1 ? -1 : S.col2sn[p];
+    if (p != -1) {
+      if (p != S.sup_ptr[sparent[s]]) {
+        err = "child supernode does not attach to the parent's first column";
+        return MF_ERR_INTERNAL;
+      }
+      schild_cnt[sparent[s] + 1]++;
+    }
+  }
+  for (int64_t s = 0; s < ns; ++s) schild_cnt[s + 1] += schild_cnt[s];
+  S.children.assign(schild_cnt[ns], 0);
+  {
+    std::vector<int32_t> fillc(schild_cnt.begin(), schild_cnt.end() - 1);
+    for (int64_t s = 0; s < ns; ++s)
+      if (sparent[s] != -1) S.children[fillc[sparent[s]]++] = (int32_t)s;
+  }
+
+  // ---- 6. front row lists and relative maps
+  S.sn.assign(ns, SnInfo{});
+  S.slevel.assign(ns, 0);
+  S.rowidx.clear();
+  S.relmap.clear();
+  int64_t Loff = 0, Uoff = 0, woff = 0, map_off = 0;
+  S.max_front = 0;
+  S.max_k = 0;
+  S.nlevels = ns > 0 ? 1 : 0;
+  {
+    std::vector<int32_t> mark(n, -1), posn(n, -1), upd;
+    // map offsets are assigned in supernode order; the maps themselves are
+    // written when the parent is processed
+    std::vector<int64_t> map_offs(ns, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+      const int32_t f = S.sup_ptr[s], l = S.sup_ptr[s + 1] - 1, k = l - f + 1;
+      upd.clear();
+      for (int32_t j = f; j <= l; ++j)
+        for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+          const int32_t i = cr[p];
+          if (i > l && mark[i] != s) {
+            mark[i] = (int32_t)s;
+            upd.push_back(i);
+          }
+        }
+      for (int32_t ci = schild_cnt[s]; ci < schild_cnt[s + 1]; ++ci) {
+        const SnInfo& c = S.sn[S.children[ci]];
+        const int32_t* crow = S.rowidx.data() + c.rows_off + c.k;
+        for (int32_t t = 0; t < c.m; ++t) {
+          const int32_t r = crow[t];
+          if (r > l && mark[r] != s) {
+            mark[r] = (int32_t)s;
+            upd.push_back(r);
+          }
+        }
+      }
+      std::sort(upd.begin(), upd.end());
+      const int32_t m = (int32_t)upd.size();
+      if ((int64_t)k + m != S.colcount[f]) {
+        err = "front size disagrees with the column count";
+        return MF_ERR_INTERNAL;
+      }
+      SnInfo& I = S.sn[s];
+      I.first = f;
+      I.k = k;
+      I.m = m;
+      I.parent = sparent[s];
+      I.child_begin = schild_cnt[s];
+      I.nchild = schild_cnt[s + 1] - schild_cnt[s];
+      I.Loff = Loff;
+      I.Uoff = Uoff;
+      I.rows_off = (int64_t)S.rowidx.size();
+      I.map_off = map_off;
+      I.woff = woff;
+      map_offs[s] = map_off;
+      const int64_t nf = (int64_t)k + m;
+      Loff += nf * k;
+      Uoff += (int64_t)m * m;
+      woff += nf;
+      map_off += m;
+      S.max_front = std::max<int64_t>(S.max_front, nf);
+      S.max_k = std::max<int64_t>(S.max_k, k);
+      for (int32_t j = f; j <= l; ++j) S.rowidx.push_back(j);
+      for (int32_t t = 0; t < m; ++t) {
+        S.rowidx.push_back(upd[t]);
+        posn[upd[t]] = k + t;
+      }
+      // relative maps of the children into this front
+      S.relmap.resize(map_off);
+      int32_t lev = 0;
+      for (int32_t ci = schild_cnt[s]; ci < schild_cnt[s + 1]; ++ci) {
+        const int32_t c = S.children[ci];
+        const SnInfo& C = S.sn[c];
+        const int32_t* crow = S.rowidx.data() + C.rows_off + C.k;
+        int32_t* cmap = S.relmap.data() + C.map_off;
+        for (int32_t t = 0; t < C.m; ++t) {
+          const int32_t r = crow[t];
+          cmap[t] = (r <= l) ? (r - f) : posn[r];
+        }
+        lev = std::max(lev, S.slevel[c] + 1);
+      }
+      S.slevel[s] = lev;
+      S.nlevels = std::max(S.nlevels, lev + 1);
+    }
+  }
+  S.Lsize = Loff;
+  S.Wsize = woff;
+  (void)Uoff;
+  S.Usize = plan_update_memory(S);
+
+  // ---- 7. assembly map of the lower triangle of C (incl. diagonal)
+  {
+    std::vector<int64_t> ccount(n + 1, 0);
+    for (int64_t ro = 0; ro < n; ++ro) {
+      const int32_t i = ip[ro];
+      for (int64_t p = rowptr[ro]; p < rowptr[ro + 1]; ++p)
+        if (ip[colind[p]] <= i) ccount[ip[colind[p]] + 1]++;
+    }
+    for (int64_t j = 0; j < n; ++j) ccount[j + 1] += ccount[j];
+    std::vector<std::pair<int32_t, int64_t>> ent(ccount[n]);
+    {
+      std::vector<int64_t> fillp(ccount.begin(), ccount.end() - 1);
+      for (int64_t ro = 0; ro < n; ++ro) {
+        const int32_t i = ip[ro];
+        for (int64_t p = rowptr[ro]; p < rowptr[ro + 1]; ++p) {
+          const int32_t j = ip[colind[p]];
+          if (j <= i) ent[fillp[j]++] = {i, p};
+        }
+      }
+    }
+    S.acol_ptr.assign(n + 1, 0);
+    S.arow.clear();
+    S.asrc_ptr.clear();
+    S.asrc.clear();
+    S.arow.reserve(ccount[n]);
+    S.asrc_ptr.reserve(ccount[n] + 1);
+    S.asrc.reserve(ccount[n]);
+    S.asrc_ptr.push_back(0);
+    for (int64_t j = 0; j < n; ++j) {
+      std::sort(ent.begin() + ccount[j], ent.begin() + ccount[j + 1]);
+      const SnInfo& I = S.sn[S.col2sn[j]];
+      const int32_t* upd = S.rowidx.data() + I.rows_off + I.k;
+      const int32_t l = I.first + I.k - 1;
+      for (int64_t e = ccount[j]; e < ccount[j + 1]; ++e) {
+        const int32_t i = ent[e].first;
+        if (e == ccount[j] || ent[e - 1].first != i) {
+          int32_t r;
+          if (i <= l) {
+            r = i - I.first;
+          } else {
+            const int32_t* pos = std::lower_bound(upd, upd + I.m, i);
+            if (pos == upd + I.m || *pos != i) {
+              err = "entry of A outside its front";
+              return MF_ERR_INTERNAL;
+            }
+            r = I.k + (int32_t)(pos - upd);
+          }
+          S.arow.push_back(r);
+          S.asrc_ptr.push_back(S.asrc_ptr.back());
+        }
+        S.asrc.push_back(ent[e].second);
+        S.asrc_ptr.back()++;
+      }
+      S.acol_ptr[j + 1] = (int64_t)S.arow.size();
+    }
+    S.nnz_lower = (int64_t)S.arow.size();
+  }
+  return MF_OK;
+}
+
+// Launch schedules of the numeric factorization and of the solves.  Fronts
+// of one level are independent (paper Sec. 5: level-set scheduling); small
+// fronts are batched one CTA each (grouped by size class), large fronts are
+// split into column chunks (assembly), panel steps (POTRF, TRSM) and trailing
+// tiles (SYRK), each batched over all large fronts of the level.
+void build_schedules(mf_symbolic& S, int small_max) {
+  S.items.clear();
+  S.fsched.clear();
+  S.fwsched.clear();
+  S.bwsched.clear();
+  const int64_t ns = S.nsuper;
+  std::vector<std::vector<int32_t>> bylev(S.nlevels);
+  for (int64_t s = 0; s < ns; ++s) bylev[S.slevel[s]].push_back((int32_t)s);
+  const int classes[3] = {32, 64, 128};
+  auto add = [&](std::vector<Launch>& sched, int32_t kind, int32_t lev, int32_t param,
+                 const std::vector<Item>& it, double flops) {
+    if (it.empty()) return;
+    Launch L;
+    L.kind = kind;
+    L.level = lev;
+    L.count = (int32_t)it.size();
+    L.param = param;
+    L.item_off = (int64_t)S.items.size();
+    L.flops = flops;
+    S.items.insert(S.items.end(), it.begin(), it.end());
+    sched.push_back(L);
+  };
+  auto front_flops = [](int64_t nf, int64_t k) {
+    double f = 0.0;
+    for (int64_t t = 0; t < k; ++t) f += (double)(nf - t) * (double)(nf - t);
+    return f;
+  };
+  std::vector<Item> it;
+  for (int32_t lev = 0; lev < S.nlevels; ++lev) {
+    const std::vector<int32_t>& L = bylev[lev];
+    // small fronts by class
+    for (int c = 0; c < 3; ++c) {
+      const int lo = c == 0 ? 0 : classes[c - 1];
+      const int hi = std::min(classes[c], small_max);
+      if (hi <= lo) continue;
+      it.clear();
+      double fl = 0.0;
+      for (int32_t s : L) {
+        const int nf = S.sn[s].k + S.sn[s].m;
+        if (nf > lo && nf <= hi) {
+          it.push_back({s, 0, 0, 0});
+          fl += front_flops(nf, S.sn[s].k);
+        }
+      }
+      add(S.fsched, K_SMALL, lev, hi, it, fl);
+    }
+    // large fronts
+    std::vector<int32_t> G;
+    for (int32_t s : L)
+      if (S.sn[s].k + S.sn[s].m > small_max) G.push_back(s);
+    if (G.empty()) continue;
+    it.clear();
+    int32_t T = 0;
+    for (int32_t s : G) {
+      const int nf = S.sn[s].k + S.sn[s].m;
+      for (int c0 = 0; c0 < nf; c0 += kAsmCols) it.push_back({s, 0, c0, std::min(c0 + kAsmCols, nf)});
+      T = std::max<int32_t>(T, (S.sn[s].k + kNB - 1) / kNB);
+    }
+    add(S.fsched, K_ASSEMBLE, lev, 0, it, 0.0);
+    for (int32_t t = 0; t < T; ++t) {
+      std::vector<Item> ip, it3, is;
+      double fp = 0, ft = 0, fs = 0;
+      for (int32_t s : G) {
+        const int k = S.sn[s].k, nf = k + S.sn[s].m;
+        if (k <= t * kNB) continue;
+        const int b = std::min(kNB, k - t * kNB);
+        const int p0 = t * kNB + b;
+        ip.push_back({s, t, 0, 0});
+        fp += (double)b * b * b / 3.0;
+        for (int r0 = p0; r0 < nf; r0 += kTrsmRows) it3.push_back({s, t, r0, 0});
+        ft += (double)(nf - p0) * b * b;
+        const int nt = (nf - p0 + kTile - 1) / kTile;
+        for (int I = 0; I < nt; ++I)
+          for (int J = 0; J <= I; ++J) is.push_back({s, t, I, J});
+        fs += (double)(nf - p0) * (double)(nf - p0 + 1) * b;
+      }
+      add(S.fsched, K_POTRF, lev, t, ip, fp);
+      add(S.fsched, K_TRSM, lev, t, it3, ft);
+      add(S.fsched, K_SYRK, lev, t, is, fs);
+    }
+  }
+  // ---- forward solve, leaves to root
+  for (int32_t lev = 0; lev < S.nlevels; ++lev) {
+    const std::vector<int32_t>& L = bylev[lev];
+    it.clear();
+    int maxnf = 0;
+    std::vector<int32_t> G;
+    for (int32_t s : L) {
+      const int nf = S.sn[s].k + S.sn[s].m;
+      if (nf <= small_max) {
+        it.push_back({s, 0, 0, 0});
+        maxnf = std::max(maxnf, nf);
+      } else {
+        G.push_back(s);
+      }
+    }
+    add(S.fwsched, K_FW_SMALL, lev, maxnf, it, 0.0);
+    if (G.empty()) continue;
+    it.clear();
+    int32_t T = 0;
+    for (int32_t s : G) {
+      it.push_back({s, 0, 0, 0});
+      T = std::max<int32_t>(T, (S.sn[s].k + kNB - 1) / kNB);
+    }
+    add(S.fwsched, K_FW_GATHER, lev, 0, it, 0.0);
+    for (int32_t t = 0; t < T; ++t) {
+      std::vector<Item> id, iu;
+      for (int32_t s : G) {
+        const int k = S.sn[s].k, nf = k + S.sn[s].m;
+        if (k <= t * kNB) continue;
+        const int b = std::min(kNB, k - t * kNB);
+        id.push_back({s, t, 0, 0});
+        for (int r0 = t * kNB + b; r0 < nf; r0 += kTrsmRows) iu.push_back({s, t, r0, 0});
+      }
+      add(S.fwsched, K_FW_DIAG, lev, t, id, 0.0);
+      add(S.fwsched, K_FW_UPD, lev, t, iu, 0.0);
+    }
+  }
+  // ---- backward solve, root to leaves
+  for (int32_t lev = S.nlevels - 1; lev >= 0; --lev) {
+    const std::vector<int32_t>& L = bylev[lev];
+    std::vector<int32_t> G;
+    it.clear();
+    int maxnf = 0;
+    for (int32_t s : L) {
+      const int nf = S.sn[s].k + S.sn[s].m;
+      if (nf <= small_max) {
+        it.push_back({s, 0, 0, 0});
+        maxnf = std::max(maxnf, nf);
+      } else {
+        G.push_back(s);
+      }
+    }
+    if (!G.empty()) {
+      std::vector<Item> io;
+      int32_t T = 0;
+      for (int32_t s : G) {
+        for (int u0 = 0; u0 < S.sn[s].k; u0 += kNB) io.push_back({s, 0, u0, 0});
+        T = std::max<int32_t>(T, (S.sn[s].k + kNB - 1) / kNB);
+      }
+      add(S.bwsched, K_BW_OFFDIAG, lev, 0, io, 0.0);
+      for (int32_t t = T - 1; t >= 0; --t) {
+        std::vector<Item> id, iu;
+        for (int32_t s : G) {
+          const int k = S.sn[s].k;
+          if (k <= t * kNB) continue;
+          id.push_back({s, t, 0, 0});
+          for (int u0 = 0; u0 < t * kNB; u0 += kNB) iu.push_back({s, t, u0, 0});
+        }
+        add(S.bwsched, K_BW_DIAG, lev, t, id, 0.0);
+        add(S.bwsched, K_BW_UPD, lev, t, iu, 0.0);
+      }
+    }
+    add(S.bwsched, K_BW_SMALL, lev, maxnf, it, 0.0);
+  }
+}
+
+}  // namespace mf

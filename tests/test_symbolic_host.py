@@ -1,0 +1,129 @@
+"""Host symbolic analysis of the library (C-ABI, no GPU) against the oracle.
+
+Integer outputs must match bit for bit: elimination tree, column counts,
+nnz(L), fundamental supernode partition and the CSC pattern of L.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2506_05793_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def handle(mf):
+    h = mf.mf_create()
+    yield h
+    mf.mf_destroy(h)
+
+
+def check_integers(mf, handle, orc, rp, ci, perm):
+    s = mf.mf_symbolic_analyze(handle, rp, ci, perm)
+    try:
+        so = orc.symbolic(rp, ci, perm)
+        assert np.array_equal(mf.mf_symbolic_etree(s), so["parent"])
+        assert np.array_equal(mf.mf_symbolic_colcounts(s), so["colcount"])
+        assert np.array_equal(mf.mf_symbolic_supernodes(s), so["sup_ptr"])
+        info = mf.mf_symbolic_get_info(s)
+        assert info["nnz_L"] == so["nnzL"]
+        assert info["flops"] == so["flops"]
+        F = orc.factor(rp, ci, np.ones(len(ci)), perm, sym=so) if len(rp) < 400 else None
+        if F is not None:
+            Lp, Li = mf.mf_symbolic_pattern(s)
+            assert np.array_equal(Lp, F.Lp) and np.array_equal(Li, F.Li)
+        par, lev = mf.mf_symbolic_supernode_tree(s)
+        # supernodal tree: parent index larger, level strictly increasing upward
+        nz = par >= 0
+        assert np.all(par[nz] > np.nonzero(nz)[0])
+        assert np.all(lev[par[nz]] > lev[nz])
+        return info
+    finally:
+        mf.mf_symbolic_free(s)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_patterns(mf, handle, orc, seed):
+    n = [1, 2, 5, 17, 60, 150, 300, 33][seed % 8]
+    rp, ci, _ = gen.random_spd(n, 0.3 if n < 50 else 0.04, seed, dense_rows=seed % 3 == 0)
+    perm = gen.random_perm(n, seed)
+    check_integers(mf, handle, orc, rp, ci, perm if seed % 4 else None)
+
+
+@pytest.mark.parametrize("case", ["cfg1", "lap3d_jump_16", "q1_12x10x3", "lap3d_20x9x13"])
+def test_structured(mf, handle, orc, case):
+    if case == "cfg1":
+        rp, ci, v, perm, _ = gen.config1()
+    elif case == "lap3d_jump_16":
+        rp, ci, v, perm, _ = gen.config3(16)
+    elif case == "q1_12x10x3":
+        rp, ci, v = gen.q1_extruded(12, 10, 3)
+        perm = gen.nd_perm((13, 11, 4), split_axes=(0, 1), dofs=2)
+    else:
+        rp, ci, v = gen.laplacian_3d(20, 9, 13)
+        perm = gen.nd_perm((20, 9, 13))
+    check_integers(mf, handle, orc, rp, ci, perm)
+
+
+def test_invalid_inputs(mf, handle):
+    rp, ci, _ = gen.laplacian_2d(4)
+    bad = ci.copy()
+    bad[3] = 99
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_symbolic_analyze(handle, rp, bad)
+    assert e.value.code == mf.MF_ERR_INVALID
+    perm = np.arange(16, dtype=np.int32)
+    perm[0] = 1
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_symbolic_analyze(handle, rp, ci, perm)
+    assert e.value.code == mf.MF_ERR_INVALID
+    rp2 = rp.copy()
+    rp2[5] = rp2[7]
+    with pytest.raises(mf.MFError):
+        mf.mf_symbolic_analyze(handle, rp2, ci)
+
+
+def test_empty_matrix(mf, handle):
+    s = mf.mf_symbolic_analyze(handle, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32))
+    info = mf.mf_symbolic_get_info(s)
+    assert info["n"] == 0 and info["nsuper"] == 0 and info["nnz_L"] == 0
+    mf.mf_symbolic_free(s)
+
+
+def test_batch_is_block_diagonal_union(mf, handle, orc):
+    mats = []
+    for a, b, c in [(5, 6, 7), (8, 4, 3), (3, 3, 9)]:
+        rp, ci, v = gen.laplacian_3d(a, b, c)
+        mats.append((rp, ci, gen.nd_perm((a, b, c))))
+    s = mf.mf_symbolic_analyze_batch(handle, mats)
+    info = mf.mf_symbolic_get_info(s)
+    tot_nnzL = 0
+    tot_flops = 0.0
+    for rp, ci, pm in mats:
+        so = orc.symbolic(rp, ci, pm)
+        tot_nnzL += so["nnzL"]
+        tot_flops += so["flops"]
+    assert info["nnz_L"] == tot_nnzL and info["flops"] == tot_flops
+    par = mf.mf_symbolic_etree(s)
+    assert np.sum(par == -1) >= 3
+    mf.mf_symbolic_free(s)
+
+
+def test_update_memory_plan_reuses_chains(mf, handle):
+    """Update matrices of finished chains are recycled: the plan stays far
+    below holding every update matrix at once."""
+    rp, ci, v, perm, _ = gen.config3(24)
+    s = mf.mf_symbolic_analyze(handle, rp, ci, perm)
+    info = mf.mf_symbolic_get_info(s)
+    cc = mf.mf_symbolic_colcounts(s)
+    sup = mf.mf_symbolic_supernodes(s)
+    k = np.diff(sup)
+    m = cc[sup[:-1]] - k
+    all_u = float(np.sum(m.astype(np.float64) ** 2)) * 8
+    assert info["factor_bytes_fp64"] < 0.5 * all_u
+    mf.mf_symbolic_free(s)
