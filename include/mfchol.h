@@ -17,8 +17,10 @@
  *   - perm[new] = old, i.e. C = A(perm, perm).  NULL means identity.
  *     Only entries (r, c) whose permuted indices satisfy iperm[r] >= iperm[c]
  *     are read (the lower triangle of C).
- *   - Supernodes are fundamental (no relaxed amalgamation) and are numbered
- *     by their first column in the permuted order.
+ *   - Exported supernodes are fundamental (no relaxed amalgamation) and are
+ *     numbered by their first column in the permuted order.  The numeric
+ *     phase works on internal fronts (runs of supernodes merged by relaxed
+ *     amalgamation); their explicit zeros never reach exported values.
  *   - Device pointers are plain CUDA device addresses of the current device;
  *     stream arguments are cudaStream_t values passed as void* (NULL = the
  *     legacy default stream).
@@ -65,7 +67,7 @@ typedef struct mf_options {
   int32_t small_front_max;  /* fronts with k+m <= this run in one CTA (<=128) */
   int32_t use_graphs;       /* 1: capture the factorization in a CUDA graph */
   int32_t profile;          /* 1: time every launch with CUDA events */
-  int32_t reserved0;
+  int32_t relax;            /* 1: relaxed amalgamation of the internal fronts */
   int64_t budget_bytes;     /* device bytes a factor may hold (0 = no limit) */
 } mf_options;
 
@@ -76,11 +78,13 @@ typedef struct mf_symbolic_info {
   int64_t nsuper;         /* fundamental supernodes */
   int64_t nnz_L;          /* sum_j c_j, structural, incl. the diagonal */
   double flops;           /* sum_j c_j^2 (paper-independent Cholesky count) */
-  int64_t nlevels;        /* levels of the supernodal elimination tree */
-  int64_t max_front;      /* max over supernodes of k + m */
-  int64_t max_k;          /* max supernode width */
+  int64_t nlevels;        /* levels of the front tree (level-set schedule) */
+  int64_t max_front;      /* max over fronts of k + m */
+  int64_t max_k;          /* max front width */
   int64_t factor_bytes_fp64;  /* device bytes of an FP64 factor (L + update) */
   int64_t factor_bytes_fp32;  /* device bytes of an FP32 factor */
+  int64_t nfronts;        /* internal fronts after relaxed amalgamation */
+  double front_flops;     /* flops of the fronts incl. explicit zeros */
 } mf_symbolic_info;
 
 /* Refinement report of mf_solve_refined. */
@@ -143,7 +147,10 @@ int mf_symbolic_supernodes(const mf_symbolic* s, int32_t* sup_ptr);
  * within a column, diagonal first). */
 int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li);
 /* Supernodal elimination tree parent (-1 for roots), nsuper entries, and
- * level of each supernode (0 = leaves), nsuper entries.  Either may be NULL. */
+ * the level (0 = leaves) of the internal front holding each supernode,
+ * nsuper entries.  Either may be NULL.  Internal fronts are contiguous runs
+ * of supernodes merged by relaxed amalgamation (mf_options.relax); the
+ * exported etree, supernodes, counts and pattern never change with it. */
 int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent,
                                int32_t* level);
 

@@ -31,13 +31,14 @@ _D = ctypes.c_double
 
 class mf_options(ctypes.Structure):
     _fields_ = [("small_front_max", _I32), ("use_graphs", _I32), ("profile", _I32),
-                ("reserved0", _I32), ("budget_bytes", _I64)]
+                ("relax", _I32), ("budget_bytes", _I64)]
 
 
 class mf_symbolic_info(ctypes.Structure):
     _fields_ = [("n", _I64), ("nnz_lower", _I64), ("nsuper", _I64), ("nnz_L", _I64),
                 ("flops", _D), ("nlevels", _I64), ("max_front", _I64), ("max_k", _I64),
-                ("factor_bytes_fp64", _I64), ("factor_bytes_fp32", _I64)]
+                ("factor_bytes_fp64", _I64), ("factor_bytes_fp32", _I64), ("nfronts", _I64),
+                ("front_flops", _D)]
 
 
 class mf_ir_report(ctypes.Structure):

@@ -155,6 +155,7 @@ int mf_options_default(mf_options* opt) {
   opt->small_front_max = mf::kSmallMax;
   opt->use_graphs = 1;
   opt->profile = 0;
+  opt->relax = 1;
   opt->budget_bytes = 0;
   return MF_OK;
 }
@@ -196,6 +197,7 @@ int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr, const in
   if (!S) return set_error(MF_ERR_OOM, "host allocation failed");
   std::string err;
   int rc;
+  S->relax = h->opt.relax ? 1 : 0;
   try {
     rc = mf::analyze(*S, n, rowptr, colind, perm, err);
     if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max);
@@ -274,6 +276,8 @@ int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info) {
   info->max_k = s->max_k;
   info->factor_bytes_fp64 = factor_bytes(s, MF_FP64);
   info->factor_bytes_fp32 = factor_bytes(s, MF_FP32);
+  info->nfronts = (int64_t)s->sn.size();
+  info->front_flops = s->front_flops;
   return MF_OK;
 }
 
@@ -304,12 +308,12 @@ int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li) {
   Lp[0] = 0;
   int64_t pos = 0;
   for (int64_t sn = 0; sn < s->nsuper; ++sn) {
-    const mf::SnInfo& I = s->sn[sn];
-    const int32_t* rows = s->rowidx.data() + I.rows_off;
-    const int nf = I.k + I.m;
-    for (int t = 0; t < I.k; ++t) {
-      for (int r = t; r < nf; ++r) Li[pos++] = rows[r];
-      Lp[I.first + t + 1] = pos;
+    const int32_t* rows = s->fs_rowidx.data() + s->fs_rows_off[sn];
+    const int64_t nr = s->fs_rows_off[sn + 1] - s->fs_rows_off[sn];
+    const int32_t f = s->sup_ptr[sn], k = s->sup_ptr[sn + 1] - f;
+    for (int t = 0; t < k; ++t) {
+      for (int64_t r = t; r < nr; ++r) Li[pos++] = rows[r];
+      Lp[f + t + 1] = pos;
     }
   }
   return MF_OK;
@@ -318,8 +322,8 @@ int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li) {
 int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent, int32_t* level) {
   if (!s) return set_error(MF_ERR_INVALID, "NULL argument");
   for (int64_t i = 0; i < s->nsuper; ++i) {
-    if (sparent) sparent[i] = s->sn[i].parent;
-    if (level) level[i] = s->slevel[i];
+    if (sparent) sparent[i] = s->fs_parent[i];
+    if (level) level[i] = s->slevel[s->col2front[s->sup_ptr[i]]];
   }
   return MF_OK;
 }
@@ -460,16 +464,27 @@ int mf_factor_export_L(const mf_factor* f, double* Lx) {
   }
   MF_CK(cudaDeviceSynchronize());
   if (S->Lsize) MF_CK(cudaMemcpy(buf.data(), f->L, S->Lsize * es, cudaMemcpyDeviceToHost));
-  int64_t pos = 0;
-  for (int64_t sn = 0; sn < S->nsuper; ++sn) {
-    const mf::SnInfo& I = S->sn[sn];
+  // gather the fundamental pattern out of the front panels
+  std::vector<int32_t> pos(S->n, -1);
+  int64_t out = 0;
+  const float* b32 = reinterpret_cast<const float*>(buf.data());
+  const double* b64 = reinterpret_cast<const double*>(buf.data());
+  for (size_t F = 0; F < S->sn.size(); ++F) {
+    const mf::SnInfo& I = S->sn[F];
     const int64_t nf = I.k + I.m;
-    for (int t = 0; t < I.k; ++t)
-      for (int64_t r = t; r < nf; ++r) {
-        const int64_t idx = I.Loff + t * nf + r;
-        Lx[pos++] = f->prec == MF_FP32 ? (double)reinterpret_cast<const float*>(buf.data())[idx]
-                                       : reinterpret_cast<const double*>(buf.data())[idx];
+    const int32_t* frows = S->rowidx.data() + I.rows_off;
+    for (int64_t r = 0; r < nf; ++r) pos[frows[r]] = (int32_t)r;
+    for (int32_t j = I.first; j < I.first + I.k; ++j) {
+      const int32_t sn = S->col2sn[j];
+      const int32_t t = j - S->sup_ptr[sn];
+      const int32_t* rows = S->fs_rowidx.data() + S->fs_rows_off[sn];
+      const int64_t nr = S->fs_rows_off[sn + 1] - S->fs_rows_off[sn];
+      const int64_t col = I.Loff + (int64_t)(j - I.first) * nf;
+      for (int64_t r = t; r < nr; ++r) {
+        const int64_t idx = col + pos[rows[r]];
+        Lx[out++] = f->prec == MF_FP32 ? (double)b32[idx] : b64[idx];
       }
+    }
   }
   return MF_OK;
 }

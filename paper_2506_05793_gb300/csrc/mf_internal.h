@@ -80,8 +80,17 @@ struct mf_symbolic {
   std::vector<int32_t> perm, iperm;
   std::vector<int32_t> parent;    // column etree
   std::vector<int64_t> colcount;  // c_j
-  std::vector<int32_t> sup_ptr;   // nsuper + 1
+  std::vector<int32_t> sup_ptr;   // nsuper + 1 (fundamental supernodes, exported)
   std::vector<int32_t> col2sn;
+  std::vector<int32_t> fs_rowidx;    // rows of each fundamental supernode
+  std::vector<int64_t> fs_rows_off;  // nsuper + 1
+  std::vector<int32_t> fs_parent;    // fundamental supernodal tree
+  // fronts: contiguous column ranges after relaxed amalgamation; every
+  // numeric structure below (sn, rowidx, relmap, schedules) is per front
+  int32_t relax = 1;
+  std::vector<int32_t> front_ptr;  // nfronts + 1
+  std::vector<int32_t> col2front;
+  double front_flops = 0.0;        // sum over front columns of (rows)^2
   int64_t nsuper = 0, nnzL = 0, nnz_lower = 0;
   double flops = 0.0;
   int32_t nlevels = 0;

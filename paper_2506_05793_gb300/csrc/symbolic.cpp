@@ -39,7 +39,7 @@ int invalid(std::string& err, const std::string& msg) {
 // the same memory instead of holding every update matrix at once.  Returns
 // the peak size (elements) and sets Uoff for every supernode.
 int64_t plan_update_memory(mf_symbolic& S) {
-  const int64_t ns = S.nsuper;
+  const int64_t ns = (int64_t)S.sn.size();
   std::vector<std::vector<int32_t>> bylev(S.nlevels);
   for (int64_t s = 0; s < ns; ++s) bylev[S.slevel[s]].push_back((int32_t)s);
   std::map<int64_t, int64_t> freeb;  // offset -> size
@@ -292,6 +292,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
     }
   }
   for (int64_t s = 0; s < ns; ++s) schild_cnt[s + 1] += schild_cnt[s];
+  S.fs_parent = sparent;
   S.children.assign(schild_cnt[ns], 0);
   {
     std::vector<int32_t> fillc(schild_cnt.begin(), schild_cnt.end() - 1);
@@ -299,20 +300,12 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
       if (sparent[s] != -1) S.children[fillc[sparent[s]]++] = (int32_t)s;
   }
 
-  // ---- 6. front row lists and relative maps
-  S.sn.assign(ns, SnInfo{});
-  S.slevel.assign(ns, 0);
-  S.rowidx.clear();
-  S.relmap.clear();
-  int64_t Loff = 0, Uoff = 0, woff = 0, map_off = 0;
-  S.max_front = 0;
-  S.max_k = 0;
-  S.nlevels = ns > 0 ? 1 : 0;
+  // ---- 6. fundamental supernode row lists (exported pattern of L)
+  std::vector<int32_t> fs_m(ns, 0);
+  S.fs_rowidx.clear();
+  S.fs_rows_off.assign(ns + 1, 0);
   {
-    std::vector<int32_t> mark(n, -1), posn(n, -1), upd;
-    // map offsets are assigned in supernode order; the maps themselves are
-    // written when the parent is processed
-    std::vector<int64_t> map_offs(ns, 0);
+    std::vector<int32_t> mark(n, -1), upd;
     for (int64_t s = 0; s < ns; ++s) {
       const int32_t f = S.sup_ptr[s], l = S.sup_ptr[s + 1] - 1, k = l - f + 1;
       upd.clear();
@@ -325,9 +318,9 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
           }
         }
       for (int32_t ci = schild_cnt[s]; ci < schild_cnt[s + 1]; ++ci) {
-        const SnInfo& c = S.sn[S.children[ci]];
-        const int32_t* crow = S.rowidx.data() + c.rows_off + c.k;
-        for (int32_t t = 0; t < c.m; ++t) {
+        const int32_t c = S.children[ci];
+        const int32_t* crow = S.fs_rowidx.data() + S.fs_rows_off[c] + (S.sup_ptr[c + 1] - S.sup_ptr[c]);
+        for (int32_t t = 0; t < fs_m[c]; ++t) {
           const int32_t r = crow[t];
           if (r > l && mark[r] != s) {
             mark[r] = (int32_t)s;
@@ -341,55 +334,144 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
         err = "front size disagrees with the column count";
         return MF_ERR_INTERNAL;
       }
-      SnInfo& I = S.sn[s];
+      fs_m[s] = m;
+      S.fs_rows_off[s] = (int64_t)S.fs_rowidx.size();
+      for (int32_t j = f; j <= l; ++j) S.fs_rowidx.push_back(j);
+      S.fs_rowidx.insert(S.fs_rowidx.end(), upd.begin(), upd.end());
+    }
+    S.fs_rows_off[ns] = (int64_t)S.fs_rowidx.size();
+  }
+
+  // ---- 7. relaxed amalgamation of fundamental supernodes into fronts.
+  // A child whose columns end right before its parent's first column is
+  // merged into the parent when the merged front stays small or gains few
+  // explicit zeros (size thresholds 4 / 16 / 48 columns with zero fractions
+  // 0.8 / 0.1 / 0.05).  Explicit zeros stay exactly zero in the numeric
+  // phase, so the exported factor (fundamental pattern) is unchanged; the
+  // merge turns chains of thin supernodes into wide dense fronts.
+  std::vector<int32_t> fstart(ns), is_top(ns, 1);
+  {
+    std::vector<double> csum(n + 1, 0.0);
+    for (int64_t j = 0; j < n; ++j) csum[j + 1] = csum[j] + (double)S.colcount[j];
+    for (int64_t s = 0; s < ns; ++s) {
+      fstart[s] = S.sup_ptr[s];
+      if (!S.relax || fstart[s] == 0) continue;
+      const int32_t c = S.col2sn[fstart[s] - 1];
+      if (sparent[c] != s) continue;
+      const int32_t l = S.sup_ptr[s + 1] - 1;
+      const double k = (double)(l - fstart[c] + 1);
+      const double nf = k + fs_m[s];
+      const double total = k * nf - k * (k - 1) / 2.0;
+      const double zfrac = (total - (csum[l + 1] - csum[fstart[c]])) / total;
+      const bool merge = k <= 4 || (k <= 16 && zfrac < 0.8) || (k <= 48 && zfrac < 0.1) ||
+                         zfrac < 0.05;
+      if (merge) {
+        fstart[s] = fstart[c];
+        is_top[c] = 0;
+      }
+    }
+  }
+  std::vector<int32_t> tops;
+  for (int64_t s = 0; s < ns; ++s)
+    if (is_top[s]) tops.push_back((int32_t)s);
+  const int64_t nfr = (int64_t)tops.size();
+  S.front_ptr.assign(nfr + 1, 0);
+  std::vector<int32_t> fs2front(ns, -1);
+  for (int64_t F = 0; F < nfr; ++F) {
+    S.front_ptr[F] = fstart[tops[F]];
+    for (int32_t s = S.col2sn[fstart[tops[F]]]; s <= tops[F]; ++s) fs2front[s] = (int32_t)F;
+  }
+  S.front_ptr[nfr] = (int32_t)n;
+  S.col2front.assign(n, 0);
+  for (int64_t F = 0; F < nfr; ++F)
+    for (int32_t j = S.front_ptr[F]; j < S.front_ptr[F + 1]; ++j) S.col2front[j] = (int32_t)F;
+
+  // front tree and children lists (children in increasing order)
+  std::vector<int32_t> fparent(nfr, -1), fchild_cnt(nfr + 1, 0);
+  for (int64_t F = 0; F < nfr; ++F) {
+    const int32_t sp = sparent[tops[F]];
+    fparent[F] = sp < 0 ? -1 : fs2front[sp];
+    if (fparent[F] >= 0) fchild_cnt[fparent[F] + 1]++;
+  }
+  for (int64_t F = 0; F < nfr; ++F) fchild_cnt[F + 1] += fchild_cnt[F];
+  S.children.assign(fchild_cnt[nfr], 0);
+  {
+    std::vector<int32_t> fillc(fchild_cnt.begin(), fchild_cnt.end() - 1);
+    for (int64_t F = 0; F < nfr; ++F)
+      if (fparent[F] >= 0) S.children[fillc[fparent[F]]++] = (int32_t)F;
+  }
+
+  // ---- 8. front row lists, relative maps, levels
+  S.sn.assign(nfr, SnInfo{});
+  S.slevel.assign(nfr, 0);
+  S.rowidx.clear();
+  S.relmap.clear();
+  int64_t Loff = 0, woff = 0, map_off = 0;
+  S.max_front = 0;
+  S.max_k = 0;
+  S.front_flops = 0.0;
+  S.nlevels = nfr > 0 ? 1 : 0;
+  {
+    std::vector<int32_t> posn(n, -1), stamp(n, -1);
+    for (int64_t F = 0; F < nfr; ++F) {
+      const int32_t top = tops[F];
+      const int32_t f = S.front_ptr[F], l = S.front_ptr[F + 1] - 1, k = l - f + 1;
+      const int32_t m = fs_m[top];
+      const int32_t* upd = S.fs_rowidx.data() + S.fs_rows_off[top] + (S.sup_ptr[top + 1] - S.sup_ptr[top]);
+      SnInfo& I = S.sn[F];
       I.first = f;
       I.k = k;
       I.m = m;
-      I.parent = sparent[s];
-      I.child_begin = schild_cnt[s];
-      I.nchild = schild_cnt[s + 1] - schild_cnt[s];
+      I.parent = fparent[F];
+      I.child_begin = fchild_cnt[F];
+      I.nchild = fchild_cnt[F + 1] - fchild_cnt[F];
       I.Loff = Loff;
-      I.Uoff = Uoff;
+      I.Uoff = 0;
       I.rows_off = (int64_t)S.rowidx.size();
       I.map_off = map_off;
       I.woff = woff;
-      map_offs[s] = map_off;
       const int64_t nf = (int64_t)k + m;
       Loff += nf * k;
-      Uoff += (int64_t)m * m;
       woff += nf;
       map_off += m;
       S.max_front = std::max<int64_t>(S.max_front, nf);
       S.max_k = std::max<int64_t>(S.max_k, k);
+      for (int64_t t = 0; t < k; ++t) S.front_flops += (double)(nf - t) * (double)(nf - t);
       for (int32_t j = f; j <= l; ++j) S.rowidx.push_back(j);
       for (int32_t t = 0; t < m; ++t) {
         S.rowidx.push_back(upd[t]);
         posn[upd[t]] = k + t;
+        stamp[upd[t]] = (int32_t)F;
       }
-      // relative maps of the children into this front
       S.relmap.resize(map_off);
       int32_t lev = 0;
-      for (int32_t ci = schild_cnt[s]; ci < schild_cnt[s + 1]; ++ci) {
+      for (int32_t ci = fchild_cnt[F]; ci < fchild_cnt[F + 1]; ++ci) {
         const int32_t c = S.children[ci];
         const SnInfo& C = S.sn[c];
         const int32_t* crow = S.rowidx.data() + C.rows_off + C.k;
         int32_t* cmap = S.relmap.data() + C.map_off;
         for (int32_t t = 0; t < C.m; ++t) {
           const int32_t r = crow[t];
-          cmap[t] = (r <= l) ? (r - f) : posn[r];
+          if (r >= f && r <= l) {
+            cmap[t] = r - f;
+          } else if (r > l && stamp[r] == F) {
+            cmap[t] = posn[r];
+          } else {
+            err = "update row of a child front outside its parent front";
+            return MF_ERR_INTERNAL;
+          }
         }
         lev = std::max(lev, S.slevel[c] + 1);
       }
-      S.slevel[s] = lev;
+      S.slevel[F] = lev;
       S.nlevels = std::max(S.nlevels, lev + 1);
     }
   }
   S.Lsize = Loff;
   S.Wsize = woff;
-  (void)Uoff;
   S.Usize = plan_update_memory(S);
 
-  // ---- 7. assembly map of the lower triangle of C (incl. diagonal)
+  // ---- 9. assembly map of the lower triangle of C (incl. diagonal)
   {
     std::vector<int64_t> ccount(n + 1, 0);
     for (int64_t ro = 0; ro < n; ++ro) {
@@ -419,7 +501,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
     S.asrc_ptr.push_back(0);
     for (int64_t j = 0; j < n; ++j) {
       std::sort(ent.begin() + ccount[j], ent.begin() + ccount[j + 1]);
-      const SnInfo& I = S.sn[S.col2sn[j]];
+      const SnInfo& I = S.sn[S.col2front[j]];
       const int32_t* upd = S.rowidx.data() + I.rows_off + I.k;
       const int32_t l = I.first + I.k - 1;
       for (int64_t e = ccount[j]; e < ccount[j + 1]; ++e) {
@@ -459,7 +541,7 @@ void build_schedules(mf_symbolic& S, int small_max) {
   S.fsched.clear();
   S.fwsched.clear();
   S.bwsched.clear();
-  const int64_t ns = S.nsuper;
+  const int64_t ns = (int64_t)S.sn.size();
   std::vector<std::vector<int32_t>> bylev(S.nlevels);
   for (int64_t s = 0; s < ns; ++s) bylev[S.slevel[s]].push_back((int32_t)s);
   const int classes[3] = {32, 64, 128};

@@ -180,8 +180,10 @@ def test_profile_counts_flops(mf, orc):
     mf.mf_factor_numeric(f, v)
     prof = mf.mf_factor_profile(f)
     total = sum(p["flops"] for p in prof.values())
-    flops = mf.mf_symbolic_get_info(s)["flops"]
-    assert abs(total - flops) <= 0.02 * flops
+    info = mf.mf_symbolic_get_info(s)
+    # kernel flops = the fronts' work (explicit zeros of merged fronts included)
+    assert abs(total - info["front_flops"]) <= 0.02 * info["front_flops"]
+    assert info["front_flops"] >= info["flops"]
     assert all(p["ms"] >= 0 for p in prof.values())
     nf, ns = mf.mf_factor_launch_counts(f)
     assert nf == sum(p["launches"] for p in prof.values())
@@ -258,3 +260,25 @@ def test_tiny_and_diagonal(mf, handle, orc):
         rp, ci, v = A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data
         r = factor_and_compare(mf, handle, orc, rp, ci, v, None)
         assert r["relF"] <= RELF64 and r["berr"] <= BERR
+
+
+def test_relaxed_and_fundamental_fronts_agree(mf, orc):
+    """Amalgamated fronts carry explicit zeros; the exported factor equals the
+    one computed on fundamental supernodes (to rounding) and the oracle's."""
+    rp, ci, v, perm, _ = gen.config3(18)
+    F = orc.factor(rp, ci, v, perm)
+    Ls = []
+    for relax in (0, 1):
+        opt = mf.mf_options_default()
+        opt.relax = relax
+        h = mf.mf_create(opt)
+        s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+        f = mf.mf_factor_create(h, s, 0)
+        mf.mf_factor_numeric(f, v)
+        Ls.append(mf.mf_factor_export_L(f, mf.mf_symbolic_get_info(s)["nnz_L"]))
+        mf.mf_factor_free(f)
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
+    for L in Ls:
+        assert orc.rel_fro(L, F.Lx) <= RELF64
+    assert orc.rel_fro(Ls[0], Ls[1]) <= RELF64
