@@ -201,6 +201,29 @@ int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches,
 int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
              double* X, int64_t ldx, int32_t on_device, void* stream);
 
+/* Solve without allocating memory.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory on
+ * their solve path, e.g. a latency-critical serving loop (cudaMalloc can
+ * synchronize the device and takes unpredictable time) or a host program
+ * whose device memory is all handed to a pool it does not control.
+ * mf_solve allocates its work buffers on first use and stages host pointers
+ * through device copies; this call runs the same solve kernels with their
+ * work memory taken from one fixed 32 MiB device array inside the library
+ * (every GPU that loads the library holds that array until exit).  B and X
+ * are device pointers, column-major, as in mf_solve (B may equal X).  It
+ * needs (n + front work) * 8 bytes per right-hand side for an FP64 factor
+ * (4 for FP32); right-hand sides are processed in chunks that fit.  A factor
+ * too large for even one right-hand side is rejected with MF_ERR_INVALID
+ * and a message giving the bytes needed.  No cudaMalloc, cudaFree or other
+ * allocating call is made, but the first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the
+ * array, so calls whose work overlaps on the GPU (other streams, other
+ * threads) race and corrupt each other's results; serialize them.
+ * Enqueued on stream; returns without waiting. */
+int mf_solve_noalloc(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
+                     double* X, int64_t ldx, void* stream);
+
 /* Mixed-precision solve: f is an FP32 factor; the residual r = B - A X, the
  * update X += D and the backward error
  *   berr = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)

@@ -76,6 +76,7 @@ _SIGS = {
     "mf_factor_profile": [_P, _P, _P, _P],
     "mf_solve": [_P, _I32, _P, _I64, _P, _I64, _I32, _P],
     "mf_solve_refined": [_P, _I32, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _P, _P],
+    "mf_solve_noalloc": [_P, _I32, _P, _I64, _P, _I64, _P],
 }
 
 
@@ -300,6 +301,20 @@ def mf_solve(f, B, X=None, stream=None):
         import torch
         stream = torch.cuda.current_stream()
     _check(lib().mf_solve(f, nrhs, _ptr(Bh), ldb, _ptr(Xh), ldx, dev, _stream(stream)))
+    return Xh
+
+
+def mf_solve_noalloc(f, B, X, stream=None):
+    """X = A^{-1} B with device tensors B, X and no allocation (see the C
+    header); enqueued on ``stream`` (default: torch's current stream)."""
+    Bh, nrhs, ldb, dev, _ = _rhs_layout(B)
+    Xh, _, ldx, devx, _ = _rhs_layout(X)
+    if not (dev and devx):
+        raise ValueError("mf_solve_noalloc takes device tensors")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    _check(lib().mf_solve_noalloc(f, nrhs, _ptr(Bh), ldb, _ptr(Xh), ldx, _stream(stream)))
     return Xh
 
 

@@ -563,6 +563,51 @@ int solve_dev(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* 
 
 }  // namespace
 
+namespace mf {
+
+// Solve with caller-provided work memory (no allocation): Y and W of each
+// chunk of right-hand sides are carved out of `scratch`.  Used by the
+// no-allocation entry point; B and X are device pointers.
+int solve_in_scratch(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X,
+                     int64_t ldx, void* scratch, size_t scratch_bytes, cudaStream_t st) {
+  const mf_symbolic* S = f->S;
+  const size_t es = elem_size(f->prec);
+  const size_t per_rhs = (size_t)(S->n + S->Wsize) * es;
+  const size_t slack = 512;  // alignment of the W carve-out
+  if (per_rhs + slack > scratch_bytes)
+    return set_error(MF_ERR_INVALID,
+                     "problem too large for the no-allocation solve: needs " +
+                         std::to_string(per_rhs + slack) + " scratch bytes per right-hand side, "
+                         "limit " + std::to_string(scratch_bytes));
+  const int32_t chunk = (int32_t)std::min<size_t>(kSolveChunk, (scratch_bytes - slack) / per_rhs);
+  for (int32_t c0 = 0; c0 < nrhs; c0 += chunk) {
+    const int32_t cn = std::min<int32_t>(chunk, nrhs - c0);
+    unsigned char* base = static_cast<unsigned char*>(scratch);
+    void* Y = base;
+    size_t woff = ((size_t)S->n * cn * es + 255) / 256 * 256;
+    void* W = base + woff;
+    MF_CK(launch_perm_in(f->prec, B + c0 * ldb, ldb, f->ds->d.perm, Y, S->n, cn, nullptr, st));
+    SolveArgs a;
+    a.sym = f->ds->d;
+    a.L = f->L;
+    a.Y = Y;
+    a.W = W;
+    a.n = S->n;
+    a.nrhs = cn;
+    for (const Launch& L : S->fwsched) MF_CK(launch_solve(f->prec, L, a, st));
+    for (const Launch& L : S->bwsched) MF_CK(launch_solve(f->prec, L, a, st));
+    MF_CK(launch_perm_out(f->prec, Y, f->ds->d.perm, X + c0 * ldx, ldx, S->n, cn, nullptr, 0, st));
+  }
+  return MF_OK;
+}
+
+bool factor_ready(const mf_factor* f, int64_t* n) {
+  *n = f->S->n;
+  return f->numeric_done;
+}
+
+}  // namespace mf
+
 extern "C" {
 
 int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,

@@ -10,6 +10,8 @@
 
 #include "../../include/mfchol.h"
 
+typedef struct CUstream_st* cudaStream_t;
+
 namespace mf {
 
 // Panel width of the blocked large-front factorization and of the blocked
@@ -130,4 +132,8 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
 void build_schedules(mf_symbolic& S, int small_max);
 // error reporting (capi.cpp)
 int set_error(int code, const std::string& msg);
+// solve with caller-provided work memory (capi.cpp)
+int solve_in_scratch(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X,
+                     int64_t ldx, void* scratch, size_t scratch_bytes, cudaStream_t st);
+bool factor_ready(const mf_factor* f, int64_t* n);
 }  // namespace mf
