@@ -82,6 +82,9 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
   MF_CK(o->up(&o->d.asrc_ptr, S->asrc_ptr));
   MF_CK(o->up(&o->d.asrc, S->asrc));
   MF_CK(o->up(&o->d.items, S->items));
+  MF_CK(o->up(&o->d.blkoff, S->blkoff));
+  MF_CK(o->up(&o->d.ginv_ptr, S->ginv_ptr));
+  MF_CK(o->up(&o->d.ginv_src, S->ginv_src));
   MF_CK(o->up(&o->d.perm, S->perm));
   MF_CK(o->up(&o->d.rowptr, S->rowptr));
   MF_CK(o->up(&o->d.colind, S->colind));
@@ -116,6 +119,7 @@ struct mf_factor {
   double* Xd = nullptr;
   double* Rd = nullptr;
   int64_t io_cap = 0;  // doubles in each of Bd/Xd/Rd
+  int32_t* sync = nullptr;  // solve ticket counters and block flags
   double* small = nullptr;  // per-RHS scalars for refinement
   // graph of the numeric factorization
   cudaStream_t cap_stream = nullptr;
@@ -143,6 +147,7 @@ struct mf_factor {
     cudaFree(Xd);
     cudaFree(Rd);
     cudaFree(small);
+    cudaFree(sync);
     delete fb64;
   }
 };
@@ -439,6 +444,8 @@ int mf_factor_check(mf_factor* f, void* stream) {
     }
   }
   const unsigned long long bad = f->status_host[0];
+  if (f->status_host[1] != ~0ull)
+    return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
   if (bad != ~0ull) {
     set_error(MF_ERR_NOT_SPD, "matrix is not positive definite");
     g_errcol = (int64_t)bad;
@@ -493,6 +500,7 @@ int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches, int64_
   if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
   if (factor_launches) *factor_launches = (int64_t)f->S->fsched.size();
   if (solve_launches) *solve_launches = (int64_t)(f->S->fwsched.size() + f->S->bwsched.size() + 2);
+  // (a solve pass also issues one memset of its ticket counters and flags)
   return MF_OK;
 }
 
@@ -513,12 +521,41 @@ int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches, double*
 // ---------------------------------------------------------------------------
 namespace {
 
+int64_t sync_ints(const mf_symbolic* S) {
+  return 2 * (int64_t)S->nlevels + 2 * (int64_t)S->blkoff.back() + 1;
+}
+
+// Enqueue one solve pass (nrhs <= kSolveChunk) on Y/W/sync work memory.
+int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X, int64_t ldx,
+               const double* inv_scale, const double* scale, int accumulate, void* Y, void* W,
+               int32_t* sync, cudaStream_t st) {
+  const mf_symbolic* S = f->S;
+  MF_CK(cudaMemsetAsync(sync, 0, sync_ints(S) * sizeof(int32_t), st));
+  MF_CK(mf::launch_perm_in(f->prec, B, ldb, f->ds->d.perm, Y, S->n, cn, inv_scale, st));
+  mf::SolveArgs a;
+  a.sym = f->ds->d;
+  a.L = f->L;
+  a.Y = Y;
+  a.W = W;
+  a.sync = sync;
+  a.status = f->status;
+  a.n = S->n;
+  a.nrhs = cn;
+  a.nlevels = S->nlevels;
+  a.nblk = S->blkoff.back();
+  for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
+  for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
+  MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, X, ldx, S->n, cn, scale, accumulate, st));
+  return MF_OK;
+}
+
 int ensure_solve_buffers(mf_factor* f) {
   const mf_symbolic* S = f->S;
   const size_t es = elem_size(f->prec);
   if (!f->Y) MF_CK(cudaMalloc(&f->Y, std::max<int64_t>(S->n * mf::kSolveChunk, 1) * es));
   if (!f->W) MF_CK(cudaMalloc(&f->W, std::max<int64_t>(S->Wsize * mf::kSolveChunk, 1) * es));
   if (!f->small) MF_CK(cudaMalloc(&f->small, 4096 * sizeof(double)));
+  if (!f->sync) MF_CK(cudaMalloc(&f->sync, sync_ints(S) * sizeof(int32_t)));
   return MF_OK;
 }
 
@@ -544,19 +581,9 @@ int solve_dev(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* 
   if (rc != MF_OK) return rc;
   for (int32_t c0 = 0; c0 < nrhs; c0 += mf::kSolveChunk) {
     const int32_t cn = std::min<int32_t>(mf::kSolveChunk, nrhs - c0);
-    MF_CK(mf::launch_perm_in(f->prec, B + c0 * ldb, ldb, f->ds->d.perm, f->Y, S->n, cn,
-                             inv_scale ? inv_scale + c0 : nullptr, st));
-    mf::SolveArgs a;
-    a.sym = f->ds->d;
-    a.L = f->L;
-    a.Y = f->Y;
-    a.W = f->W;
-    a.n = S->n;
-    a.nrhs = cn;
-    for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
-    for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
-    MF_CK(mf::launch_perm_out(f->prec, f->Y, f->ds->d.perm, X + c0 * ldx, ldx, S->n, cn,
-                              scale ? scale + c0 : nullptr, accumulate, st));
+    rc = solve_pass(f, cn, B + c0 * ldb, ldb, X + c0 * ldx, ldx, inv_scale ? inv_scale + c0 : nullptr,
+                    scale ? scale + c0 : nullptr, accumulate, f->Y, f->W, f->sync, st);
+    if (rc != MF_OK) return rc;
   }
   return MF_OK;
 }
@@ -574,29 +601,25 @@ int solve_in_scratch(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
   const size_t es = elem_size(f->prec);
   const size_t per_rhs = (size_t)(S->n + S->Wsize) * es;
   const size_t slack = 512;  // alignment of the W carve-out
-  if (per_rhs + slack > scratch_bytes)
+  const size_t sync_bytes = ((size_t)sync_ints(S) * sizeof(int32_t) + 255) / 256 * 256;
+  if (per_rhs + slack + sync_bytes > scratch_bytes)
     return set_error(MF_ERR_INVALID,
                      "problem too large for the no-allocation solve: needs " +
-                         std::to_string(per_rhs + slack) + " scratch bytes per right-hand side, "
-                         "limit " + std::to_string(scratch_bytes));
-  const int32_t chunk = (int32_t)std::min<size_t>(kSolveChunk, (scratch_bytes - slack) / per_rhs);
+                         std::to_string(per_rhs + slack + sync_bytes) +
+                         " scratch bytes for one right-hand side, limit " +
+                         std::to_string(scratch_bytes));
+  const int32_t chunk =
+      (int32_t)std::min<size_t>(kSolveChunk, (scratch_bytes - slack - sync_bytes) / per_rhs);
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  int32_t* sync = reinterpret_cast<int32_t*>(base);
   for (int32_t c0 = 0; c0 < nrhs; c0 += chunk) {
     const int32_t cn = std::min<int32_t>(chunk, nrhs - c0);
-    unsigned char* base = static_cast<unsigned char*>(scratch);
-    void* Y = base;
-    size_t woff = ((size_t)S->n * cn * es + 255) / 256 * 256;
+    void* Y = base + sync_bytes;
+    const size_t woff = sync_bytes + ((size_t)S->n * cn * es + 255) / 256 * 256;
     void* W = base + woff;
-    MF_CK(launch_perm_in(f->prec, B + c0 * ldb, ldb, f->ds->d.perm, Y, S->n, cn, nullptr, st));
-    SolveArgs a;
-    a.sym = f->ds->d;
-    a.L = f->L;
-    a.Y = Y;
-    a.W = W;
-    a.n = S->n;
-    a.nrhs = cn;
-    for (const Launch& L : S->fwsched) MF_CK(launch_solve(f->prec, L, a, st));
-    for (const Launch& L : S->bwsched) MF_CK(launch_solve(f->prec, L, a, st));
-    MF_CK(launch_perm_out(f->prec, Y, f->ds->d.perm, X + c0 * ldx, ldx, S->n, cn, nullptr, 0, st));
+    const int rc = solve_pass(f, cn, B + c0 * ldb, ldb, X + c0 * ldx, ldx, nullptr, nullptr, 0, Y,
+                              W, sync, st);
+    if (rc != MF_OK) return rc;
   }
   return MF_OK;
 }
@@ -628,7 +651,11 @@ int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X
   if (rc != MF_OK) return rc;
   MF_CK(cudaMemcpy2DAsync(X, ldx * sizeof(double), f->Xd, n * sizeof(double), n * sizeof(double),
                           nrhs, cudaMemcpyDeviceToHost, st));
+  MF_CK(cudaMemcpyAsync(f->status_host, f->status, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, st));
   MF_CK(cudaStreamSynchronize(st));
+  if (f->status_host[1] != ~0ull)
+    return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
   return MF_OK;
 }
 

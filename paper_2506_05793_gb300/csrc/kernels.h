@@ -20,6 +20,9 @@ struct DevSym {
   int64_t* asrc_ptr = nullptr;
   int64_t* asrc = nullptr;
   Item* items = nullptr;
+  int32_t* blkoff = nullptr;   // per front: first 64-column block (solve flags)
+  int64_t* ginv_ptr = nullptr; // forward gather (inverse relative maps)
+  int64_t* ginv_src = nullptr;
   int32_t* perm = nullptr;     // perm[new] = old
   int64_t* rowptr = nullptr;   // A (original order) for the FP64 residual
   int32_t* colind = nullptr;
@@ -38,8 +41,14 @@ struct SolveArgs {
   const void* L;  // T
   void* Y;        // T[n * nrhs]  permuted RHS / solution
   void* W;        // T[Wsize * nrhs] front work vectors
+  // int32[2 * nlevels + 2 * nblk], zero before every solve: one ticket
+  // counter per level and sweep, then forward and backward block flags
+  int32_t* sync;
+  unsigned long long* status;  // status[1] receives MF_ERR_TIMEOUT
   int64_t n;
   int32_t nrhs;
+  int32_t nlevels;
+  int32_t nblk;
 };
 
 // prec: MF_FP64 or MF_FP32.  All launchers return cudaGetLastError().

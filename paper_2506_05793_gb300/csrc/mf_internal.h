@@ -52,14 +52,8 @@ enum Kind : int32_t {
   K_TRSM = 3,      // panel rows * L_tt^{-T}
   K_SYRK = 4,      // trailing lower update
   K_NKINDS_FACTOR = 5,
-  K_FW_SMALL = 10,
-  K_FW_GATHER = 11,
-  K_FW_DIAG = 12,
-  K_FW_UPD = 13,
-  K_BW_SMALL = 14,
-  K_BW_OFFDIAG = 15,
-  K_BW_DIAG = 16,
-  K_BW_UPD = 17,
+  K_FW_LEVEL = 11,   // per 64-row block: gather, GEMV with solved blocks, diagonal solve
+  K_BW_LEVEL = 12,   // per 64-column block: transposed GEMV, diagonal solve
 };
 
 struct Launch {
@@ -114,6 +108,11 @@ struct mf_symbolic {
   std::vector<mf::Item> items;
   std::vector<mf::Launch> fsched;
   std::vector<mf::Launch> fwsched, bwsched;
+  std::vector<int32_t> blkoff;     // per front: first 64-column block index
+  // forward-solve gather: entries ginv_ptr[woff+i]..[woff+i+1] of front row
+  // i are (child << 32 | row of the child front) pairs
+  std::vector<int64_t> ginv_ptr;
+  std::vector<int64_t> ginv_src;
   // device mirror, created on first use by a factor on this device
   mutable std::mutex dev_mu;
   mutable std::shared_ptr<void> dev;

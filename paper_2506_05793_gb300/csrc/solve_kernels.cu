@@ -34,6 +34,10 @@ struct SD {
   const T* L;
   T* Y;
   T* W;
+  const int32_t* blkoff;
+  const int64_t* ginv_ptr;
+  const int64_t* ginv_src;
+  unsigned long long* status;
   int64_t n;
   int nrhs;
 };
@@ -49,6 +53,10 @@ SD<T> make_sd(const SolveArgs& a) {
   d.L = static_cast<const T*>(a.L);
   d.Y = static_cast<T*>(a.Y);
   d.W = static_cast<T*>(a.W);
+  d.blkoff = a.sym.blkoff;
+  d.ginv_ptr = a.sym.ginv_ptr;
+  d.ginv_src = a.sym.ginv_src;
+  d.status = a.status;
   d.n = a.n;
   d.nrhs = a.nrhs;
   return d;
@@ -68,253 +76,320 @@ __device__ __forceinline__ T* wfront(const SD<T>& d, const SnInfo& f, int r) {
   return d.W + f.woff * d.nrhs + (int64_t)r * nf;
 }
 
+// Bounded spin: about kSpinLimit x 128 ns before a wait gives up, records
+// MF_ERR_TIMEOUT in status[1] and lets the block continue (no hang).
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The whole CTA waits until *flag != 0 (thread 0 polls with acquire loads).
+__device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* status) {
+  if (threadIdx.x == 0) {
+    int spins = 0;
+    while (ld_acquire(flag) == 0) {
+      if (++spins > kSpinLimit) {
+        atomicExch(status + 1, (unsigned long long)MF_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+  __syncthreads();
+}
+
+// Every thread fences its own writes, then one release store publishes.
+__device__ __forceinline__ void cta_publish(int* flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(flag, 1);
+}
+
+template <typename T, int R>
+constexpr size_t fw_level_smem() {
+  return ((size_t)6 * kNB * R + (size_t)kNB * (kNB + 1) + kNB) * sizeof(T);
+}
+template <typename T, int R>
+constexpr size_t bw_level_smem() {
+  return ((size_t)5 * kNB * R + (size_t)kNB * (kNB + 1) + kNB) * sizeof(T);
+}
+
 // ---------------------------------------------------------------------------
-// Forward, small supernode: gather, diagonal solve and update in shared memory.
+// Forward, one 64-row block of a front.  The block first gathers its rows of
+// the front work vector, w = [b(first..first+k); 0] + the children's update
+// entries (inverse relative maps, children in fixed order).  Pivot block p:
+//   x_p = L_pp^{-1} (w_p - sum_{a<p} L_pa x_a), written to Y and published
+//   through flag p;
+// update-row block: u = w - sum_a L_ua x_a, left in W for the parent.
+// Thread (row, g): row of the block, g = quarter of the 64 columns of L_pa.
+// The L values of block a+1 are loaded into registers while the block waits
+// for x_a, so the DRAM latency is off the critical path.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_fw_small(SD<T> d, int64_t item_off) {
+template <typename T, int R>
+__global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
+    k_fw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* F = reinterpret_cast<T*>(smem_raw);  // F[r * nf + i]
-  const SnInfo f = d.sn[d.items[item_off + blockIdx.x].s];
-  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < nf * nrhs; idx += blockDim.x) {
-    const int r = idx / nf, i = idx % nf;
-    F[idx] = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
-  }
+  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[q * R + r]
+  T* ws = xs + kNB * R;                    // ws[row * R + r]  gathered w
+  T* red = ws + kNB * R;                   // red[(g * kNB + row) * R + r]
+  T* D = red + 4 * kNB * R;                // D[c * (kNB + 1) + i] = L(r0 + i, r0 + c)
+  T* rinv = D + kNB * (kNB + 1);
+  constexpr int ld = kNB + 1;
+  __shared__ int s_item;
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
   __syncthreads();
-  for (int ci = 0; ci < f.nchild; ++ci) {
-    const SnInfo ch = d.sn[d.children[f.child_begin + ci]];
-    const int mc = ch.m;
-    const int32_t* map = d.relmap + ch.map_off;
-    for (int idx = tid; idx < mc * nrhs; idx += blockDim.x) {
-      const int r = idx / mc, ic = idx % mc;
-      F[r * nf + map[ic]] += wfront(d, ch, r)[ch.k + ic];
-    }
-    __syncthreads();
-  }
-  const T* Lp = d.L + f.Loff;
-  for (int j = 0; j < k; ++j) {
-    const T* col = Lp + (int64_t)j * nf;
-    if (tid < nrhs) F[tid * nf + j] = F[tid * nf + j] / col[j];
-    __syncthreads();
-    const int len = nf - j - 1;
-    for (int idx = tid; idx < len * nrhs; idx += blockDim.x) {
-      const int r = idx / len, i = j + 1 + idx % len;
-      F[r * nf + i] -= col[i] * F[r * nf + j];
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < nf * nrhs; idx += blockDim.x) {
-    const int r = idx / nf, i = idx % nf;
-    if (i < k) d.Y[(int64_t)r * d.n + f.first + i] = F[idx];
-    else wfront(d, f, r)[i] = F[idx];
-  }
-}
-
-// Forward, large supernode: initialise W_s and pull the children.
-template <typename T>
-__global__ void __launch_bounds__(256) k_fw_gather(SD<T> d, int64_t item_off) {
-  const SnInfo f = d.sn[d.items[item_off + blockIdx.x].s];
-  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
-  const int tid = threadIdx.x;
-  for (int64_t idx = tid; idx < (int64_t)nf * nrhs; idx += blockDim.x) {
-    const int r = (int)(idx / nf), i = (int)(idx % nf);
-    wfront(d, f, r)[i] = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
-  }
-  __syncthreads();
-  for (int ci = 0; ci < f.nchild; ++ci) {
-    const SnInfo ch = d.sn[d.children[f.child_begin + ci]];
-    const int mc = ch.m;
-    const int32_t* map = d.relmap + ch.map_off;
-    for (int64_t idx = tid; idx < (int64_t)mc * nrhs; idx += blockDim.x) {
-      const int r = (int)(idx / mc), ic = (int)(idx % mc);
-      wfront(d, f, r)[map[ic]] += wfront(d, ch, r)[ch.k + ic];
-    }
-    __syncthreads();
-  }
-}
-
-// Forward, large supernode, block t: x_t = L_tt^{-1} W[c0:c0+b]; written to
-// W and to Y.
-template <typename T>
-__global__ void __launch_bounds__(256) k_fw_diag(SD<T> d, int64_t item_off) {
-  __shared__ T X[kSolveChunk][kNB + 1];
-  const Item it = d.items[item_off + blockIdx.x];
+  const int nrhs = d.nrhs;
+  const Item it = d.items[item_off + s_item];
   const SnInfo f = d.sn[it.s];
-  const int nf = f.k + f.m, nrhs = d.nrhs;
-  const int c0 = it.t * kNB, b = min(kNB, f.k - c0);
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < b * nrhs; idx += blockDim.x) {
-    const int r = idx / b, i = idx % b;
-    X[r][i] = wfront(d, f, r)[c0 + i];
-  }
-  __syncthreads();
+  const int k = f.k, nf = k + f.m;
+  const int r0 = it.a, rows = it.b;
+  const bool pivot = it.t == 0;
+  const int tid = threadIdx.x, row = tid & 63, g = tid >> 6, lane = tid & 31, warp = tid >> 5;
+  int* fl = flags + d.blkoff[it.s];
   const T* Lp = d.L + f.Loff;
-  for (int j = 0; j < b; ++j) {
-    const T* col = Lp + (int64_t)(c0 + j) * nf + c0;
-    if (tid < nrhs) X[tid][j] = X[tid][j] / col[j];
-    __syncthreads();
-    const int len = b - j - 1;
-    for (int idx = tid; idx < len * nrhs; idx += blockDim.x) {
-      const int r = idx / len, i = j + 1 + idx % len;
-      X[r][i] -= col[i] * X[r][j];
+  T* Wf = d.W + f.woff * nrhs;
+  const int nblk = pivot ? r0 / kNB : (k + kNB - 1) / kNB;
+  // L values of block 0 (thread: column 16 g + qq of the block, its row)
+  T Lc[16];
+  const bool live = row < rows;
+  {
+    const int bs0 = min(kNB, k);
+#pragma unroll
+    for (int qq = 0; qq < 16; ++qq) {
+      const int q = g * 16 + qq;
+      Lc[qq] = (nblk > 0 && live && q < bs0) ? Lp[(int64_t)q * nf + r0 + row] : T(0);
+    }
+  }
+  // diagonal block and reciprocals of its diagonal (pivot blocks)
+  if (pivot) {
+    for (int idx = tid; idx < rows * rows; idx += blockDim.x) {
+      const int c = idx / rows, i = idx % rows;
+      if (i >= c) D[c * ld + i] = Lp[(int64_t)(r0 + c) * nf + r0 + i];
+    }
+    if (tid < rows) rinv[tid] = T(1) / Lp[(int64_t)(r0 + tid) * nf + r0 + tid];
+  }
+  // gather w for the rows of this block
+  for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
+    const int rw = idx % rows, r = idx / rows;
+    const int i = r0 + rw;
+    T w = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
+    const int64_t gi = f.woff + i;
+    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e) {
+      const int64_t src = d.ginv_src[e];
+      const SnInfo ch = d.sn[(int32_t)(src >> 32)];
+      w += d.W[ch.woff * nrhs + (int64_t)r * (ch.k + ch.m) + (int32_t)(src & 0xffffffff)];
+    }
+    ws[rw * R + r] = w;
+  }
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = T(0);
+  for (int a = 0; a < nblk; ++a) {
+    T Ln[16];
+    const bool more = a + 1 < nblk;
+    const int bsn = more ? min(kNB, k - (a + 1) * kNB) : 0;
+#pragma unroll
+    for (int qq = 0; qq < 16; ++qq) {
+      const int q = g * 16 + qq;
+      Ln[qq] = (more && live && q < bsn) ? Lp[(int64_t)((a + 1) * kNB + q) * nf + r0 + row] : T(0);
+    }
+    cta_wait(fl + a, d.status);
+    const int bsa = min(kNB, k - a * kNB);
+    for (int idx = tid; idx < bsa * nrhs; idx += blockDim.x) {
+      const int r = idx / bsa, q = idx % bsa;
+      xs[q * R + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + a * kNB + q);
     }
     __syncthreads();
+#pragma unroll
+    for (int qq = 0; qq < 16; ++qq) {
+      const int q = g * 16 + qq;
+      if (q < bsa) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r < nrhs) acc[r] = fma(Lc[qq], xs[q * R + r], acc[r]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int qq = 0; qq < 16; ++qq) Lc[qq] = Ln[qq];
   }
-  for (int idx = tid; idx < b * nrhs; idx += blockDim.x) {
-    const int r = idx / b, i = idx % b;
-    wfront(d, f, r)[c0 + i] = X[r][i];
-    d.Y[(int64_t)r * d.n + f.first + c0 + i] = X[r][i];
-  }
-}
-
-// Forward, large supernode, block t: W[rows] -= L[rows, c0:c0+b] x_t for a
-// block of kTrsmRows rows starting at it.a (one thread per row).
-template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) k_fw_upd(SD<T> d, int64_t item_off) {
-  __shared__ T X[kNB][kSolveChunk];
-  const Item it = d.items[item_off + blockIdx.x];
-  const SnInfo f = d.sn[it.s];
-  const int nf = f.k + f.m, nrhs = d.nrhs;
-  const int c0 = it.t * kNB, b = min(kNB, f.k - c0);
-  const int r0 = it.a, rows = min(kTrsmRows, nf - r0);
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < b * nrhs; idx += blockDim.x) {
-    const int r = idx / b, q = idx % b;
-    X[q][r] = wfront(d, f, r)[c0 + q];
-  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r < nrhs) red[(g * kNB + row) * R + r] = acc[r];
   __syncthreads();
-  if (tid >= rows) return;
-  T acc[kSolveChunk];
-#pragma unroll
-  for (int r = 0; r < kSolveChunk; ++r) acc[r] = T(0);
-  const T* Lp = d.L + f.Loff + (int64_t)c0 * nf + r0 + tid;
-  for (int q = 0; q < b; ++q) {
-    const T l = Lp[(int64_t)q * nf];
-#pragma unroll
-    for (int r = 0; r < kSolveChunk; ++r)
-      if (r < nrhs) acc[r] = fma(l, X[q][r], acc[r]);
+  for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
+    const int rw = idx % rows, r = idx / rows;
+    const T sum = red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
+                  red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
+    const T u = ws[rw * R + r] - sum;
+    if (pivot) xs[rw * R + r] = u;
+    else Wf[(int64_t)r * nf + r0 + rw] = u;
   }
-#pragma unroll
-  for (int r = 0; r < kSolveChunk; ++r)
-    if (r < nrhs) wfront(d, f, r)[r0 + tid] -= acc[r];
+  if (!pivot) return;
+  __syncthreads();
+  // column-oriented substitution, one warp per right-hand side; lane owns
+  // rows lane and lane + 32 of the block
+  for (int r = warp; r < nrhs; r += 8) {
+    T v0 = lane < rows ? xs[lane * R + r] : T(0);
+    T v1 = lane + 32 < rows ? xs[(lane + 32) * R + r] : T(0);
+    for (int j = 0; j < rows; ++j) {
+      const T xj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31) * rinv[j];
+      if (j < 32) {
+        if (lane == j) v0 = xj;
+        else if (lane > j && lane < rows) v0 = fma(-D[j * ld + lane], xj, v0);
+        if (lane + 32 < rows) v1 = fma(-D[j * ld + lane + 32], xj, v1);
+      } else {
+        if (lane + 32 == j) v1 = xj;
+        else if (lane + 32 > j && lane + 32 < rows) v1 = fma(-D[j * ld + lane + 32], xj, v1);
+      }
+    }
+    if (lane < rows) d.Y[(int64_t)r * d.n + f.first + r0 + lane] = v0;
+    if (lane + 32 < rows) d.Y[(int64_t)r * d.n + f.first + r0 + lane + 32] = v1;
+  }
+  cta_publish(fl + r0 / kNB);
 }
 
 // ---------------------------------------------------------------------------
-// Backward, small supernode: one CTA; warps own right-hand sides.
+// Backward, one 64-column block c of a front:
+//   x_c = L_cc^{-T} (y_c - L21[:, c]^T x(update rows) - sum_{a>c} L_ac^T x_a),
+// update rows read the final x of ancestor fronts, later blocks are awaited
+// through their flags.  Thread (col, g) holds rows 16 g .. 16 g + 15 of its
+// column of the current 64-row tile in registers; the next tile is loaded
+// while the block waits.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_bw_small(SD<T> d, int64_t item_off) {
+template <typename T, int R>
+__global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
+    k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SnInfo f = d.sn[d.items[item_off + blockIdx.x].s];
-  const int k = f.k, m = f.m, nf = k + m, nrhs = d.nrhs;
-  T* G = reinterpret_cast<T*>(smem_raw);  // G[r * k + j]
-  T* Xr = G + k * nrhs;                   // Xr[r * m + i]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const int32_t* urow = d.rowidx + f.rows_off + k;
-  for (int idx = tid; idx < k * nrhs; idx += blockDim.x) {
-    const int r = idx / k, j = idx % k;
-    G[idx] = d.Y[(int64_t)r * d.n + f.first + j];
-  }
-  for (int idx = tid; idx < m * nrhs; idx += blockDim.x) {
-    const int r = idx / m, i = idx % m;
-    Xr[idx] = d.Y[(int64_t)r * d.n + urow[i]];
-  }
+  constexpr int ld = kNB + 1;
+  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[i * R + r]
+  T* red = xs + kNB * R;                   // red[(g * kNB + c) * R + r]
+  T* Dt = red + 4 * kNB * R;               // Dt[j * ld + c] = L(c0 + j, c0 + c)
+  T* rinv = Dt + kNB * ld;
+  __shared__ int s_item;
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
   __syncthreads();
+  const int nrhs = d.nrhs;
+  const Item it = d.items[item_off + s_item];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m;
+  const int c0 = it.a, bs = it.b;
+  const int tid = threadIdx.x, col = tid & 63, g = tid >> 6, lane = tid & 31, warp = tid >> 5;
+  int* fl = flags + d.blkoff[it.s];
   const T* Lp = d.L + f.Loff;
-  if (m > 0) {
-    for (int p = warp; p < k * nrhs; p += nw) {
-      const int r = p / k, j = p % k;
-      const T* col = Lp + (int64_t)j * nf + k;
-      T s = T(0);
-      for (int i = lane; i < m; i += 32) s = fma(col[i], Xr[r * m + i], s);
-      s = warp_sum(s);
-      if (lane == 0) G[r * k + j] -= s;
+  const bool live = col < bs;
+  const T* Lcol = Lp + (int64_t)(c0 + (live ? col : 0)) * nf;
+  const int32_t* frow = d.rowidx + f.rows_off;
+  const int PB = (k + kNB - 1) / kNB;
+  // tiles: update rows first (no waiting), then later pivot blocks, last first
+  const int ntu = (nf - k + kNB - 1) / kNB;
+  const int ntiles = ntu + (PB - 1 - c0 / kNB);
+  T Lc[16];
+  {
+    int i0 = 0, ti = 0;
+    if (ntiles > 0) {
+      if (ntu > 0) {
+        i0 = k;
+        ti = min(kNB, nf - k);
+      } else {
+        i0 = (PB - 1) * kNB;
+        ti = min(kNB, k - i0);
+      }
+    }
+#pragma unroll
+    for (int ii = 0; ii < 16; ++ii) {
+      const int i = g * 16 + ii;
+      Lc[ii] = (live && i < ti) ? Lcol[i0 + i] : T(0);
+    }
+  }
+  for (int idx = tid; idx < bs * bs; idx += blockDim.x) {
+    const int c = idx / bs, j = idx % bs;
+    if (j >= c) Dt[j * ld + c] = Lp[(int64_t)(c0 + c) * nf + c0 + j];
+  }
+  if (tid < bs) rinv[tid] = T(1) / Lp[(int64_t)(c0 + tid) * nf + c0 + tid];
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = T(0);
+  for (int tI = 0; tI < ntiles; ++tI) {
+    const bool upd = tI < ntu;
+    const int i0 = upd ? k + tI * kNB : (PB - 1 - (tI - ntu)) * kNB;
+    const int ti = upd ? min(kNB, nf - i0) : min(kNB, k - i0);
+    T Ln[16];
+    {
+      int n0 = 0, nt = 0;
+      if (tI + 1 < ntiles) {
+        if (tI + 1 < ntu) {
+          n0 = k + (tI + 1) * kNB;
+          nt = min(kNB, nf - n0);
+        } else {
+          n0 = (PB - 1 - (tI + 1 - ntu)) * kNB;
+          nt = min(kNB, k - n0);
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < 16; ++ii) {
+        const int i = g * 16 + ii;
+        Ln[ii] = (live && i < nt) ? Lcol[n0 + i] : T(0);
+      }
+    }
+    if (!upd) cta_wait(fl + i0 / kNB, d.status);
+    for (int idx = tid; idx < ti * nrhs; idx += blockDim.x) {
+      const int i = idx % ti, r = idx / ti;
+      xs[i * R + r] = upd ? d.Y[(int64_t)r * d.n + frow[i0 + i]]
+                          : __ldcg(d.Y + (int64_t)r * d.n + f.first + i0 + i);
     }
     __syncthreads();
-  }
-  for (int r = warp; r < nrhs; r += nw) {
-    T* g = G + r * k;
-    for (int j = k - 1; j >= 0; --j) {
-      const T* col = Lp + (int64_t)j * nf;
-      T s = T(0);
-      for (int i = j + 1 + lane; i < k; i += 32) s = fma(col[i], g[i], s);
-      s = warp_sum(s);
-      if (lane == 0) g[j] = (g[j] - s) / col[j];
-      __syncwarp();
+#pragma unroll
+    for (int ii = 0; ii < 16; ++ii) {
+      const int i = g * 16 + ii;
+      if (i < ti) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r < nrhs) acc[r] = fma(Lc[ii], xs[i * R + r], acc[r]);
+      }
     }
+    __syncthreads();
+#pragma unroll
+    for (int ii = 0; ii < 16; ++ii) Lc[ii] = Ln[ii];
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r < nrhs) red[(g * kNB + col) * R + r] = acc[r];
+  __syncthreads();
+  for (int idx = tid; idx < bs * nrhs; idx += blockDim.x) {
+    const int c = idx % bs, r = idx / bs;
+    const T sum = red[(0 * kNB + c) * R + r] + red[(1 * kNB + c) * R + r] +
+                  red[(2 * kNB + c) * R + r] + red[(3 * kNB + c) * R + r];
+    xs[c * R + r] = d.Y[(int64_t)r * d.n + f.first + c0 + c] - sum;
   }
   __syncthreads();
-  for (int idx = tid; idx < k * nrhs; idx += blockDim.x) {
-    const int r = idx / k, j = idx % k;
-    d.Y[(int64_t)r * d.n + f.first + j] = G[idx];
-  }
-}
-
-// Backward, large supernode: g[u-block] = y - L21[:, u-block]^T x(rows) into W.
-template <typename T>
-__global__ void __launch_bounds__(256) k_bw_offdiag(SD<T> d, int64_t item_off) {
-  const Item it = d.items[item_off + blockIdx.x];
-  const SnInfo f = d.sn[it.s];
-  const int k = f.k, m = f.m, nf = k + m, nrhs = d.nrhs;
-  const int u0 = it.a, ub = min(kNB, k - u0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int32_t* urow = d.rowidx + f.rows_off + k;
-  const T* Lp = d.L + f.Loff;
-  for (int p = warp; p < ub * nrhs; p += nw) {
-    const int r = p / ub, j = u0 + p % ub;
-    const T* col = Lp + (int64_t)j * nf + k;
-    const T* y = d.Y + (int64_t)r * d.n;
-    T s = T(0);
-    for (int i = lane; i < m; i += 32) s = fma(col[i], y[urow[i]], s);
-    s = warp_sum(s);
-    if (lane == 0) wfront(d, f, r)[j] = y[f.first + j] - s;
-  }
-}
-
-// Backward, large supernode, block t: x_t = L_tt^{-T} g_t (warp per RHS).
-template <typename T>
-__global__ void __launch_bounds__(256) k_bw_diag(SD<T> d, int64_t item_off) {
-  const Item it = d.items[item_off + blockIdx.x];
-  const SnInfo f = d.sn[it.s];
-  const int nf = f.k + f.m, nrhs = d.nrhs;
-  const int c0 = it.t * kNB, b = min(kNB, f.k - c0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T* Lp = d.L + f.Loff;
-  for (int r = warp; r < nrhs; r += nw) {
-    T* g = wfront(d, f, r) + c0;
-    for (int j = b - 1; j >= 0; --j) {
-      const T* col = Lp + (int64_t)(c0 + j) * nf + c0;
-      T s = T(0);
-      for (int i = j + 1 + lane; i < b; i += 32) s = fma(col[i], g[i], s);
-      s = warp_sum(s);
-      if (lane == 0) g[j] = (g[j] - s) / col[j];
-      __syncwarp();
+  // right-looking substitution with L_cc^T, one warp per right-hand side;
+  // lane owns columns lane and lane + 32 of the block
+  for (int r = warp; r < nrhs; r += 8) {
+    T v0 = lane < bs ? xs[lane * R + r] : T(0);
+    T v1 = lane + 32 < bs ? xs[(lane + 32) * R + r] : T(0);
+    for (int j = bs - 1; j >= 0; --j) {
+      const T xj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31) * rinv[j];
+      if (j < 32) {
+        if (lane == j) v0 = xj;
+        else if (lane < j) v0 = fma(-Dt[j * ld + lane], xj, v0);
+      } else {
+        if (lane + 32 == j) v1 = xj;
+        else if (lane + 32 < j) v1 = fma(-Dt[j * ld + lane + 32], xj, v1);
+        v0 = fma(-Dt[j * ld + lane], xj, v0);
+      }
     }
-    for (int i = lane; i < b; i += 32) d.Y[(int64_t)r * d.n + f.first + c0 + i] = g[i];
+    if (lane < bs) d.Y[(int64_t)r * d.n + f.first + c0 + lane] = v0;
+    if (lane + 32 < bs) d.Y[(int64_t)r * d.n + f.first + c0 + lane + 32] = v1;
   }
-}
-
-// Backward, large supernode, block t: g[u-block] -= L[t-block, u-block]^T x_t.
-template <typename T>
-__global__ void __launch_bounds__(256) k_bw_upd(SD<T> d, int64_t item_off) {
-  const Item it = d.items[item_off + blockIdx.x];
-  const SnInfo f = d.sn[it.s];
-  const int nf = f.k + f.m, nrhs = d.nrhs;
-  const int c0 = it.t * kNB, b = min(kNB, f.k - c0);
-  const int u0 = it.a, ub = min(kNB, c0 - u0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T* Lp = d.L + f.Loff;
-  for (int p = warp; p < ub * nrhs; p += nw) {
-    const int r = p / ub, j = u0 + p % ub;
-    const T* col = Lp + (int64_t)j * nf + c0;
-    T* g = wfront(d, f, r);
-    T s = T(0);
-    for (int i = lane; i < b; i += 32) s = fma(col[i], g[c0 + i], s);
-    s = warp_sum(s);
-    if (lane == 0) g[j] -= s;
-  }
+  cta_publish(fl + c0 / kNB);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,44 +461,40 @@ __global__ void k_norms(const int64_t* rowptr, const double* vals, int64_t n, co
   }
 }
 
+template <typename T, int R>
+cudaError_t init_r() {
+  cudaError_t e = cudaFuncSetAttribute(k_fw_level<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fw_level_smem<T, R>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_bw_level<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bw_level_smem<T, R>());
+}
+
 template <typename T>
 cudaError_t init_t() {
-  return cudaFuncSetAttribute(k_fw_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSmallMax * kSolveChunk * (int)sizeof(T));
+  cudaError_t e = init_r<T, 1>();
+  if (e == cudaSuccess) e = init_r<T, 8>();
+  if (e == cudaSuccess) e = init_r<T, kSolveChunk>();
+  return e;
+}
+
+template <typename T, int R>
+void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
+  const SD<T> d = make_sd<T>(a);
+  if (L.kind == K_FW_LEVEL)
+    k_fw_level<T, R><<<L.count, 256, fw_level_smem<T, R>(), st>>>(
+        d, L.item_off, a.sync + 2 * L.level, a.sync + 2 * a.nlevels);
+  else
+    k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(
+        d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
 }
 
 template <typename T>
 cudaError_t launch_t(const Launch& L, const SolveArgs& a, cudaStream_t st) {
-  const SD<T> d = make_sd<T>(a);
-  const dim3 grid(L.count);
-  switch (L.kind) {
-    case K_FW_SMALL:
-      k_fw_small<T><<<grid, 256, (size_t)L.param * a.nrhs * sizeof(T), st>>>(d, L.item_off);
-      break;
-    case K_FW_GATHER:
-      k_fw_gather<T><<<grid, 256, 0, st>>>(d, L.item_off);
-      break;
-    case K_FW_DIAG:
-      k_fw_diag<T><<<grid, 256, 0, st>>>(d, L.item_off);
-      break;
-    case K_FW_UPD:
-      k_fw_upd<T><<<grid, kTrsmRows, 0, st>>>(d, L.item_off);
-      break;
-    case K_BW_SMALL:
-      k_bw_small<T><<<grid, 256, (size_t)L.param * a.nrhs * sizeof(T), st>>>(d, L.item_off);
-      break;
-    case K_BW_OFFDIAG:
-      k_bw_offdiag<T><<<grid, 256, 0, st>>>(d, L.item_off);
-      break;
-    case K_BW_DIAG:
-      k_bw_diag<T><<<grid, 256, 0, st>>>(d, L.item_off);
-      break;
-    case K_BW_UPD:
-      k_bw_upd<T><<<grid, 256, 0, st>>>(d, L.item_off);
-      break;
-    default:
-      return cudaErrorInvalidValue;
-  }
+  if (L.kind != K_FW_LEVEL && L.kind != K_BW_LEVEL) return cudaErrorInvalidValue;
+  if (a.nrhs <= 1) launch_r<T, 1>(L, a, st);
+  else if (a.nrhs <= 8) launch_r<T, 8>(L, a, st);
+  else launch_r<T, kSolveChunk>(L, a, st);
   return cudaGetLastError();
 }
 

@@ -470,6 +470,33 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
   S.Lsize = Loff;
   S.Wsize = woff;
   S.Usize = plan_update_memory(S);
+  // inverse of the relative maps for the forward solve: for every front row
+  // (global index woff + i) the children's update entries that add into it,
+  // children in increasing order (deterministic sums)
+  S.ginv_ptr.assign(S.Wsize + 1, 0);
+  for (int64_t F = 0; F < nfr; ++F) {
+    const SnInfo& P = S.sn[F];
+    for (int32_t ci = P.child_begin; ci < P.child_begin + P.nchild; ++ci) {
+      const SnInfo& C = S.sn[S.children[ci]];
+      const int32_t* cmap = S.relmap.data() + C.map_off;
+      for (int32_t t = 0; t < C.m; ++t) S.ginv_ptr[P.woff + cmap[t] + 1]++;
+    }
+  }
+  for (int64_t i = 0; i < S.Wsize; ++i) S.ginv_ptr[i + 1] += S.ginv_ptr[i];
+  S.ginv_src.assign(S.ginv_ptr[S.Wsize], 0);
+  {
+    std::vector<int64_t> fillg(S.ginv_ptr.begin(), S.ginv_ptr.end() - 1);
+    for (int64_t F = 0; F < nfr; ++F) {
+      const SnInfo& P = S.sn[F];
+      for (int32_t ci = P.child_begin; ci < P.child_begin + P.nchild; ++ci) {
+        const int32_t c = S.children[ci];
+        const SnInfo& C = S.sn[c];
+        const int32_t* cmap = S.relmap.data() + C.map_off;
+        for (int32_t t = 0; t < C.m; ++t)
+          S.ginv_src[fillg[P.woff + cmap[t]]++] = ((int64_t)c << 32) | (uint32_t)(C.k + t);
+      }
+    }
+  }
 
   // ---- 9. assembly map of the lower triangle of C (incl. diagonal)
   {
@@ -617,79 +644,32 @@ void build_schedules(mf_symbolic& S, int small_max) {
       add(S.fsched, K_SYRK, lev, t, is, fs);
     }
   }
-  // ---- forward solve, leaves to root
+  // ---- solves: one sync-free launch per level and sweep.  Items are the
+  // 64-row blocks of every front of the level (forward: pivot blocks in
+  // order, then update-row blocks; backward: pivot column blocks in reverse
+  // order).  Items are taken in ticket order, so a block only waits on
+  // blocks with earlier tickets.
+  S.blkoff.assign(ns + 1, 0);
+  for (int64_t s = 0; s < ns; ++s) S.blkoff[s + 1] = S.blkoff[s] + (S.sn[s].k + kNB - 1) / kNB;
   for (int32_t lev = 0; lev < S.nlevels; ++lev) {
     const std::vector<int32_t>& L = bylev[lev];
     it.clear();
-    int maxnf = 0;
-    std::vector<int32_t> G;
     for (int32_t s : L) {
-      const int nf = S.sn[s].k + S.sn[s].m;
-      if (nf <= small_max) {
-        it.push_back({s, 0, 0, 0});
-        maxnf = std::max(maxnf, nf);
-      } else {
-        G.push_back(s);
-      }
+      const int k = S.sn[s].k, m = S.sn[s].m;
+      for (int r0 = 0; r0 < k; r0 += kNB) it.push_back({s, 0, r0, std::min(kNB, k - r0)});
+      for (int r0 = 0; r0 < m; r0 += kNB) it.push_back({s, 1, k + r0, std::min(kNB, m - r0)});
     }
-    add(S.fwsched, K_FW_SMALL, lev, maxnf, it, 0.0);
-    if (G.empty()) continue;
-    it.clear();
-    int32_t T = 0;
-    for (int32_t s : G) {
-      it.push_back({s, 0, 0, 0});
-      T = std::max<int32_t>(T, (S.sn[s].k + kNB - 1) / kNB);
-    }
-    add(S.fwsched, K_FW_GATHER, lev, 0, it, 0.0);
-    for (int32_t t = 0; t < T; ++t) {
-      std::vector<Item> id, iu;
-      for (int32_t s : G) {
-        const int k = S.sn[s].k, nf = k + S.sn[s].m;
-        if (k <= t * kNB) continue;
-        const int b = std::min(kNB, k - t * kNB);
-        id.push_back({s, t, 0, 0});
-        for (int r0 = t * kNB + b; r0 < nf; r0 += kTrsmRows) iu.push_back({s, t, r0, 0});
-      }
-      add(S.fwsched, K_FW_DIAG, lev, t, id, 0.0);
-      add(S.fwsched, K_FW_UPD, lev, t, iu, 0.0);
-    }
+    add(S.fwsched, K_FW_LEVEL, lev, 0, it, 0.0);
   }
-  // ---- backward solve, root to leaves
   for (int32_t lev = S.nlevels - 1; lev >= 0; --lev) {
     const std::vector<int32_t>& L = bylev[lev];
-    std::vector<int32_t> G;
     it.clear();
-    int maxnf = 0;
     for (int32_t s : L) {
-      const int nf = S.sn[s].k + S.sn[s].m;
-      if (nf <= small_max) {
-        it.push_back({s, 0, 0, 0});
-        maxnf = std::max(maxnf, nf);
-      } else {
-        G.push_back(s);
-      }
+      const int k = S.sn[s].k;
+      for (int c0 = ((k - 1) / kNB) * kNB; c0 >= 0; c0 -= kNB)
+        it.push_back({s, 0, c0, std::min(kNB, k - c0)});
     }
-    if (!G.empty()) {
-      std::vector<Item> io;
-      int32_t T = 0;
-      for (int32_t s : G) {
-        for (int u0 = 0; u0 < S.sn[s].k; u0 += kNB) io.push_back({s, 0, u0, 0});
-        T = std::max<int32_t>(T, (S.sn[s].k + kNB - 1) / kNB);
-      }
-      add(S.bwsched, K_BW_OFFDIAG, lev, 0, io, 0.0);
-      for (int32_t t = T - 1; t >= 0; --t) {
-        std::vector<Item> id, iu;
-        for (int32_t s : G) {
-          const int k = S.sn[s].k;
-          if (k <= t * kNB) continue;
-          id.push_back({s, t, 0, 0});
-          for (int u0 = 0; u0 < t * kNB; u0 += kNB) iu.push_back({s, t, u0, 0});
-        }
-        add(S.bwsched, K_BW_DIAG, lev, t, id, 0.0);
-        add(S.bwsched, K_BW_UPD, lev, t, iu, 0.0);
-      }
-    }
-    add(S.bwsched, K_BW_SMALL, lev, maxnf, it, 0.0);
+    add(S.bwsched, K_BW_LEVEL, lev, 0, it, 0.0);
   }
 }
 
