@@ -34,7 +34,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "q1_extruded_256x256x10_2dof_hnd"
 METRIC = "factor TFLOP/s (sum c_j^2 / step time; step = FP64 numeric factorization + 1-RHS solve)"
 
 
@@ -44,20 +43,38 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--size", type=int, default=256, help="horizontal elements per side")
+    p.add_argument("--workload", default="q1", choices=["q1", "lap3d"],
+                   help="q1: extruded Q1 ice-sheet mesh (default); lap3d: 7-point Laplacian size^3 "
+                        "(small cases for profiling)")
+    p.add_argument("--size", type=int, default=None,
+                   help="q1: horizontal elements per side (256); lap3d: grid side (48)")
     p.add_argument("--layers", type=int, default=10)
+    p.add_argument("--prec", default="fp64", choices=["fp64", "fp32"],
+                   help="precision of the timed factorization + solve (fp64 is the benchmark; "
+                        "fp32 runs the tensor-core path, for profiling)")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
 
 
-def load_workload(size, layers):
+def load_workload(args):
     import gen
-    rp, ci, v = gen.q1_extruded(size, size, layers, seed=1)
-    perm = gen.nd_perm((size + 1, size + 1, layers + 1), split_axes=(0, 1), dofs=2)
+    if args.workload == "lap3d":
+        rp, ci, v = gen.laplacian_3d(args.size)
+        perm = gen.nd_perm((args.size,) * 3)
+    else:
+        rp, ci, v = gen.q1_extruded(args.size, args.size, args.layers, seed=1)
+        perm = gen.nd_perm((args.size + 1, args.size + 1, args.layers + 1), split_axes=(0, 1),
+                           dofs=2)
     n = len(rp) - 1
     b = gen.rhs(n, 1, seed=3)
     return rp, ci, v, perm, b
+
+
+def workload_name(args):
+    if args.workload == "lap3d":
+        return "laplacian7_%d^3_nd" % args.size
+    return "q1_extruded_%dx%dx%d_2dof_hnd" % (args.size, args.size, args.layers)
 
 
 def dist_setup():
@@ -147,7 +164,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    rp, ci, v, perm, b = load_workload(args.size, args.layers)
+    rp, ci, v, perm, b = load_workload(args)
     n = len(rp) - 1
     rows = oracle.lower_rows(rp, ci, perm)
     sym = {"rows": rows, "parent": oracle.etree(n, *rows)}
@@ -172,7 +189,7 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "l2_flush": "inputs larger than L2"},
+        "config": {"workload": workload_name(args), "n": n, "l2_flush": "inputs larger than L2"},
         "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -182,6 +199,8 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.size is None:
+        args.size = 48 if args.workload == "lap3d" else 256
     if args.impl == "reference":
         run_reference(args)
         return
@@ -192,7 +211,7 @@ def main():
     mf.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    rp, ci, v, perm, b = load_workload(args.size, args.layers)
+    rp, ci, v, perm, b = load_workload(args)
     n = len(rp) - 1
     opt = mf.mf_options_default()
     opt.profile = 1  # per-launch CUDA events: per-kernel-kind device time
@@ -201,7 +220,7 @@ def main():
     s = mf.mf_symbolic_analyze(h, rp, ci, perm)
     t_sym = time.perf_counter() - t0
     info = mf.mf_symbolic_get_info(s)
-    f = mf.mf_factor_create(h, s, mf.MF_FP64)
+    f = mf.mf_factor_create(h, s, mf.MF_FP32 if args.prec == "fp32" else mf.MF_FP64)
     st = torch.cuda.current_stream(dev)
     vd = torch.from_numpy(v).to(dev)
     bd = torch.from_numpy(b).to(dev)
@@ -244,9 +263,11 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "fp32" else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "nnz_A": int(rp[-1]), "nnz_L": info["nnz_L"],
+        "config": {"workload": workload_name(args), "n": n, "nnz_A": int(rp[-1]),
+                   "nnz_L": info["nnz_L"],
                    "flops_per_factor": flops, "nsuper": info["nsuper"],
                    "levels": info["nlevels"], "max_front": info["max_front"], "nrhs": 1,
                    "parallelism": "replicas" if ws > 1 else "single",
@@ -276,7 +297,7 @@ def main():
                        "unit": "TFLOP/s", "frac": ach / peak64, "traffic": None,
                        "peak_source": "measured bf16 %.0f TFLOP/s x nominal FP64/bf16 1.25/2250" % bf16}
     if rank == 0 and not args.no_extras:
-        extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info)
+        extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm)
     if rank == 0:
         print(json.dumps(out))
     mf.mf_factor_free(f)
@@ -287,7 +308,7 @@ def main():
         dist.destroy_process_group()
 
 
-def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info):
+def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm):
     import torch
     n = len(rp) - 1
     # solve latency (1 RHS), p50 / p99 over 200 solves
@@ -336,16 +357,11 @@ def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info):
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:
         import oracle
         oracle.build()
-        flops, dt, J = oracle.factor_sample(rp, ci, v, out_perm(args), seconds=args.cpu_seconds)
+        flops, dt, J = oracle.factor_sample(rp, ci, v, perm, seconds=args.cpu_seconds)
         out["cpu_baseline"] = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": 1,
                                "kind": "oracle",
                                "sample": "first %d of %d columns (descendant-closed), %.3g flops, %.1f s"
                                          % (J, n, flops, dt)}
-
-
-def out_perm(args):
-    import gen
-    return gen.nd_perm((args.size + 1, args.size + 1, args.layers + 1), split_axes=(0, 1), dofs=2)
 
 
 if __name__ == "__main__":

@@ -69,6 +69,9 @@ typedef struct mf_options {
   int32_t profile;          /* 1: time every launch with CUDA events */
   int32_t relax;            /* 1: relaxed amalgamation of the internal fronts */
   int64_t budget_bytes;     /* device bytes a factor may hold (0 = no limit) */
+  int32_t tc;               /* 1: FP32 trailing updates on tcgen05 tensor cores
+                               (split-TF32, FP32 accuracy); 0: FP32 FMA */
+  int32_t reserved0;
 } mf_options;
 
 /* Summary of a symbolic analysis. */
@@ -187,8 +190,9 @@ int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches,
                             int64_t* solve_launches);
 
 /* With profiling on (mf_options.profile), per-kernel-kind totals of the last
- * numeric call: kinds 0 small-front, 1 assemble, 2 potrf, 3 trsm, 4 syrk.
- * ms[kind], launches[kind] and flops[kind] (algorithmic) for 5 kinds. */
+ * numeric call: kinds 0 small-front, 1 assemble, 2 potrf, 3 trsm, 4 syrk,
+ * 5 syrk on tensor cores.  ms[kind], launches[kind] and flops[kind]
+ * (algorithmic) for 6 kinds. */
 int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches,
                       double* flops);
 

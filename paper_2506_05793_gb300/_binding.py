@@ -21,7 +21,7 @@ from .build import LIB
 MF_OK, MF_ERR_INVALID, MF_ERR_NOT_SPD, MF_ERR_OOM, MF_ERR_CUDA, MF_ERR_TIMEOUT, \
     MF_ERR_STAGNATION, MF_ERR_INTERNAL = range(8)
 MF_FP64, MF_FP32 = 0, 1
-FACTOR_KINDS = ("small_front", "assemble", "potrf", "trsm", "syrk")
+FACTOR_KINDS = ("small_front", "assemble", "potrf", "trsm", "syrk", "syrk_tc")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -31,7 +31,7 @@ _D = ctypes.c_double
 
 class mf_options(ctypes.Structure):
     _fields_ = [("small_front_max", _I32), ("use_graphs", _I32), ("profile", _I32),
-                ("relax", _I32), ("budget_bytes", _I64)]
+                ("relax", _I32), ("budget_bytes", _I64), ("tc", _I32), ("reserved0", _I32)]
 
 
 class mf_symbolic_info(ctypes.Structure):
@@ -259,9 +259,9 @@ def mf_factor_launch_counts(f):
 
 
 def mf_factor_profile(f):
-    ms = np.zeros(5)
-    n = np.zeros(5, dtype=np.int64)
-    fl = np.zeros(5)
+    ms = np.zeros(6)
+    n = np.zeros(6, dtype=np.int64)
+    fl = np.zeros(6)
     _check(lib().mf_factor_profile(f, _ptr(ms), _ptr(n), _ptr(fl)))
     return {k: {"ms": float(ms[i]), "launches": int(n[i]), "flops": float(fl[i])}
             for i, k in enumerate(FACTOR_KINDS)}

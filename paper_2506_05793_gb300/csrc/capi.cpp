@@ -83,6 +83,8 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
   MF_CK(o->up(&o->d.asrc, S->asrc));
   MF_CK(o->up(&o->d.items, S->items));
   MF_CK(o->up(&o->d.blkoff, S->blkoff));
+  MF_CK(o->up(&o->d.soff, S->soff));
+  MF_CK(o->up(&o->d.arange, S->arange));
   MF_CK(o->up(&o->d.ginv_ptr, S->ginv_ptr));
   MF_CK(o->up(&o->d.ginv_src, S->ginv_src));
   MF_CK(o->up(&o->d.perm, S->perm));
@@ -97,7 +99,9 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
 size_t elem_size(int prec) { return prec == MF_FP32 ? sizeof(float) : sizeof(double); }
 
 int64_t factor_bytes(const mf_symbolic* S, int prec) {
-  return (S->Lsize + S->Usize) * (int64_t)elem_size(prec) + S->nnzA * (int64_t)sizeof(double);
+  return (S->Lsize + S->Usize + S->max_large * mf::kNB * mf::kNB + S->nnz_lower) *
+             (int64_t)elem_size(prec) +
+         S->nnzA * (int64_t)sizeof(double);
 }
 
 }  // namespace
@@ -120,6 +124,10 @@ struct mf_factor {
   double* Rd = nullptr;
   int64_t io_cap = 0;  // doubles in each of Bd/Xd/Rd
   int32_t* sync = nullptr;  // solve ticket counters and block flags
+  bool tc = false;          // FP32 trailing updates on tcgen05 tensor cores
+  float* split = nullptr;   // tf32 hi/lo staging rows of the panels
+  void* dinv = nullptr;     // inverses of the current diagonal blocks (scratch)
+  void* av = nullptr;       // lower entries of C in assembly order (T)
   double* small = nullptr;  // per-RHS scalars for refinement
   // graph of the numeric factorization
   cudaStream_t cap_stream = nullptr;
@@ -148,6 +156,9 @@ struct mf_factor {
     cudaFree(Rd);
     cudaFree(small);
     cudaFree(sync);
+    cudaFree(split);
+    cudaFree(dinv);
+    cudaFree(av);
     delete fb64;
   }
 };
@@ -161,6 +172,7 @@ int mf_options_default(mf_options* opt) {
   opt->use_graphs = 1;
   opt->profile = 0;
   opt->relax = 1;
+  opt->tc = 1;
   opt->budget_bytes = 0;
   return MF_OK;
 }
@@ -356,8 +368,16 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   MF_CK(cudaMalloc(&F->vals, std::max<int64_t>(s->nnzA, 1) * sizeof(double)));
   MF_CK(cudaMalloc(&F->status, 2 * sizeof(unsigned long long)));
   MF_CK(cudaMallocHost(&F->status_host, 2 * sizeof(unsigned long long)));
+  MF_CK(cudaMemset(F->status, 0xff, 2 * sizeof(unsigned long long)));
+  MF_CK(cudaMalloc(&F->dinv, std::max<int64_t>(s->max_large, 1) * mf::kNB * mf::kNB * es));
+  MF_CK(cudaMalloc(&F->av, std::max<int64_t>(s->nnz_lower, 1) * es));
   MF_CK(mf::factor_kernels_init(prec));
   MF_CK(mf::solve_kernels_init(prec));
+  if (prec == MF_FP32 && h->opt.tc) {
+    F->tc = true;
+    MF_CK(mf::factor_tc_init());
+    MF_CK(cudaMalloc(&F->split, std::max<int64_t>(s->split_rows, 1) * 128 * sizeof(float)));
+  }
   *f = F.release();
   return MF_OK;
 }
@@ -370,15 +390,20 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile) {
   a.L = F->L;
   a.U = F->U;
   a.status = F->status;
+  a.split = F->tc ? F->split : nullptr;
+  a.dinv = F->dinv;
+  a.av = F->av;
+  const std::vector<mf::Launch>& sched = F->tc ? S->fsched_tc : S->fsched;
   MF_CK(cudaMemsetAsync(F->status, 0xff, 2 * sizeof(unsigned long long), st));
-  if (profile && F->ev.size() < 2 * S->fsched.size()) {
+  MF_CK(mf::launch_gather_values(F->prec, a, S->nnz_lower, st));
+  if (profile && F->ev.size() < 2 * sched.size()) {
     const size_t old = F->ev.size();
-    F->ev.resize(2 * S->fsched.size());
+    F->ev.resize(2 * sched.size());
     for (size_t i = old; i < F->ev.size(); ++i) MF_CK(cudaEventCreate(&F->ev[i]));
   }
-  for (size_t i = 0; i < S->fsched.size(); ++i) {
+  for (size_t i = 0; i < sched.size(); ++i) {
     if (profile) MF_CK(cudaEventRecord(F->ev[2 * i], st));
-    MF_CK(mf::launch_factor(F->prec, S->fsched[i], a, st));
+    MF_CK(mf::launch_factor(F->prec, sched[i], a, st));
     if (profile) MF_CK(cudaEventRecord(F->ev[2 * i + 1], st));
   }
   return MF_OK;
@@ -426,20 +451,20 @@ int mf_factor_check(mf_factor* f, void* stream) {
                         cudaMemcpyDeviceToHost, st));
   MF_CK(cudaStreamSynchronize(st));
   if (f->h->opt.profile) {
-    const mf_symbolic* S = f->S;
+    const std::vector<mf::Launch>& sched = f->tc ? f->S->fsched_tc : f->S->fsched;
     for (int k = 0; k < mf::K_NKINDS_FACTOR; ++k) {
       f->prof_ms[k] = 0;
       f->prof_n[k] = 0;
       f->prof_fl[k] = 0;
     }
-    if (f->ev.size() >= 2 * S->fsched.size()) {
-      for (size_t i = 0; i < S->fsched.size(); ++i) {
+    if (f->ev.size() >= 2 * sched.size()) {
+      for (size_t i = 0; i < sched.size(); ++i) {
         float ms = 0.f;
         MF_CK(cudaEventElapsedTime(&ms, f->ev[2 * i], f->ev[2 * i + 1]));
-        const int k = S->fsched[i].kind;
+        const int k = sched[i].kind;
         f->prof_ms[k] += ms;
         f->prof_n[k] += 1;
-        f->prof_fl[k] += S->fsched[i].flops;
+        f->prof_fl[k] += sched[i].flops;
       }
     }
   }
@@ -498,7 +523,9 @@ int mf_factor_export_L(const mf_factor* f, double* Lx) {
 
 int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches, int64_t* solve_launches) {
   if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
-  if (factor_launches) *factor_launches = (int64_t)f->S->fsched.size();
+  // + 1: the gather of the values into assembly order
+  if (factor_launches)
+    *factor_launches = (int64_t)(f->tc ? f->S->fsched_tc.size() : f->S->fsched.size()) + 1;
   if (solve_launches) *solve_launches = (int64_t)(f->S->fwsched.size() + f->S->bwsched.size() + 2);
   // (a solve pass also issues one memset of its ticket counters and flags)
   return MF_OK;

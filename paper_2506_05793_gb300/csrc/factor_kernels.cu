@@ -35,9 +35,14 @@ struct FD {
   const int64_t* asrc;
   const Item* items;
   const double* vals;
+  const T* av;
+  const Item* arange;
   T* L;
   T* U;
   unsigned long long* status;
+  const int64_t* soff;
+  float* split;
+  T* dinv;
 };
 
 template <typename T>
@@ -52,9 +57,14 @@ FD<T> make_fd(const FactorArgs& a) {
   d.asrc = a.sym.asrc;
   d.items = a.sym.items;
   d.vals = a.vals;
+  d.av = static_cast<const T*>(a.av);
+  d.arange = a.sym.arange;
   d.L = static_cast<T*>(a.L);
   d.U = static_cast<T*>(a.U);
   d.status = a.status;
+  d.soff = a.sym.soff;
+  d.split = a.split;
+  d.dinv = static_cast<T*>(a.dinv);
   return d;
 }
 
@@ -68,23 +78,6 @@ __device__ __forceinline__ T* front_col(const FD<T>& d, const SnInfo& f, int c) 
 
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
-
-// Sum of the (possibly duplicated) CSR entries of one front entry.
-template <typename T>
-__device__ __forceinline__ T a_entry(const FD<T>& d, int64_t e) {
-  double v = 0.0;
-  for (int64_t p = d.asrc_ptr[e]; p < d.asrc_ptr[e + 1]; ++p) v += d.vals[d.asrc[p]];
-  return T(v);
-}
-
-__device__ __forceinline__ int lower_bound_i32(const int32_t* a, int n, int key) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (a[mid] < key) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
 
 // Unblocked right-looking partial Cholesky of the first `k` columns of an
 // n x n lower-triangular block held column-major in shared memory (ld).
@@ -127,7 +120,7 @@ __global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) 
   for (int c = warp; c < k; c += nw) {
     const int g = f.first + c;
     for (int64_t e = d.acol_ptr[g] + lane; e < d.acol_ptr[g + 1]; e += 32)
-      F[c * nf + d.arow[e]] = a_entry(d, e);
+      F[c * nf + d.arow[e]] = d.av[e];
   }
   __syncthreads();
   for (int ci = 0; ci < f.nchild; ++ci) {
@@ -172,15 +165,14 @@ __global__ void __launch_bounds__(256) k_assemble(FD<T> d, int64_t item_off) {
     T* col = front_col(d, f, c);
     const int g = f.first + c;
     for (int64_t e = d.acol_ptr[g] + lane; e < d.acol_ptr[g + 1]; e += 32)
-      col[d.arow[e]] = a_entry(d, e);
+      col[d.arow[e]] = d.av[e];
   }
   __syncthreads();
-  for (int ci = 0; ci < f.nchild; ++ci) {
-    const SnInfo ch = d.sn[d.children[f.child_begin + ci]];
+  for (const Item* rg = d.arange + it.t; rg->s >= 0; ++rg) {
+    const SnInfo ch = d.sn[rg->s];
     const int mc = ch.m;
     const int32_t* map = d.relmap + ch.map_off;
-    const int lo = lower_bound_i32(map, mc, c0);
-    const int hi = lower_bound_i32(map, mc, c1);
+    const int lo = rg->t, hi = rg->a;
     const T* Uc = d.U + ch.Uoff;
     for (int jc = lo + warp; jc < hi; jc += nw) {
       T* col = front_col(d, f, map[jc]);
@@ -191,47 +183,264 @@ __global__ void __launch_bounds__(256) k_assemble(FD<T> d, int64_t item_off) {
   }
 }
 
+// Diagonal block of panel step c0 (b x b, padded with the identity to 64 x 64)
+// into shared memory D (column-major, leading dimension ld).  Every thread
+// issues all its global loads before the first shared store, so the DRAM
+// latency is paid once, not once per element.
+template <typename T, int NT>
+__device__ __forceinline__ void load_diag_block(const FD<T>& d, const SnInfo& f, int c0, int b,
+                                                T* D, int ld) {
+  constexpr int PER = kNB * kNB / NT;
+  const int64_t nf = (int64_t)f.k + f.m;
+  const T* base = d.L + f.Loff + (int64_t)c0 * nf + c0;
+  T v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int idx = threadIdx.x + u * NT, c = idx / kNB, i = idx % kNB;
+    v[u] = (i < b && c < b) ? (i >= c ? base[(int64_t)c * nf + i] : T(0)) : (i == c ? T(1) : T(0));
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int idx = threadIdx.x + u * NT;
+    D[(idx / kNB) * ld + (idx % kNB)] = v[u];
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Large fronts, panel step t: Cholesky of the b x b diagonal block.
+// One warp: Cholesky and inverse of the 32 x 32 lower block at D (column-major,
+// leading dimension ld) entirely in registers.  Lane i keeps row i of the
+// block; the rank-1 updates and the substitution for the inverse take the
+// other rows' values by shuffles.  L overwrites D (upper part zero), the
+// inverse goes to Y (same layout).  Pivots beyond `nvalid` are padding.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
-  __shared__ T D[kNB * (kNB + 1)];
+__device__ __noinline__ void warp_chol_inv32(T* D, T* Y, int ld, int nvalid, int64_t col0,
+                                             unsigned long long* status) {
+  constexpr unsigned full = 0xffffffffu;
+  const int i = threadIdx.x & 31;
+  T r[32];
+  T myinv = T(0);  // 1 / L(i, i), kept for the inverse
+#pragma unroll
+  for (int c = 0; c < 32; ++c) r[c] = i >= c ? D[c * ld + i] : T(0);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const T piv = __shfl_sync(full, r[j], j);
+    if (i == 0 && j < nvalid && !(piv > T(0))) atomicMin(status, (unsigned long long)(col0 + j));
+    const T ljj = dsqrt(piv);
+    const T rinv = T(1) / ljj;
+    if (i == j) myinv = rinv;
+    r[j] = i == j ? ljj : (i > j ? r[j] * rinv : T(0));
+#pragma unroll
+    for (int c = j + 1; c < 32; ++c) {
+      const T lc = __shfl_sync(full, r[j], c);
+      if (i >= c) r[c] = fma(-r[j], lc, r[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 32; ++c) D[c * ld + i] = r[c];
+  // inverse: lane i solves L y = e_i (column i of L^{-1})
+  T y[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    T s = k == i ? T(1) : T(0);
+#pragma unroll
+    for (int m = 0; m < k; ++m) s = fma(-__shfl_sync(full, r[m], k), y[m], s);
+    y[k] = s * __shfl_sync(full, myinv, k);
+  }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) Y[i * ld + k] = y[k];
+}
+
+// ---------------------------------------------------------------------------
+// Large fronts, panel step t: Cholesky of the b x b diagonal block and the
+// inverse of its factor, as 2 x 2 blocks of 32 (128 threads):
+//   warp 0: L11, Y11 = L11^{-1}      all: L21 = A21 Y11^T
+//   all:    A22 -= L21 L21^T         warp 0: L22, Y22 = L22^{-1}
+//   all:    Y21 = -Y22 (L21 Y11)
+// A block with b < 64 is padded with the identity, so its factor and inverse
+// are padded the same way.  The inverse goes to the scratch dinv (64 x 64,
+// column-major, slot = position of the front in its level, item field b).
+// ---------------------------------------------------------------------------
+template <typename T>
+constexpr size_t potrf_blk_smem() {
+  return (size_t)(2 * kNB * (kNB + 1) + 32 * 33) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_potrf_blk(FD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ld = kNB + 1;
+  T* D = reinterpret_cast<T*>(smem_raw);  // D[c * ld + i] = A(i, c), then L(i, c)
+  T* Y = D + kNB * ld;                    // Y[c * ld + i] = L^{-1}(i, c)
+  T* Tm = Y + kNB * ld;                   // Tm[c * 33 + i] = (L21 Y11)(32 + i, c)
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int c0 = it.t * kNB;
   const int b = min(kNB, f.k - c0);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  constexpr int ld = kNB + 1;
-  for (int c = warp; c < b; c += nw) {
-    const T* col = front_col(d, f, c0 + c) + c0;
-    for (int r = c + lane; r < b; r += 32) D[c * ld + r] = col[r];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  load_diag_block<T, 128>(d, f, c0, b, D, ld);
+  for (int idx = tid; idx < kNB * ld; idx += blockDim.x) Y[idx] = T(0);
+  __syncthreads();
+  if (warp == 0) warp_chol_inv32(D, Y, ld, min(b, 32), f.first + c0, d.status);
+  __syncthreads();
+  const int i2 = 32 + lane;  // row of the lower block rows handled by this thread
+  {
+    // L21(i, c) = sum_{k <= c} A21(i, k) Y11(c, k); c = warp + 4 q
+    T x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = warp + 4 * q;
+      T s = T(0);
+      for (int k = 0; k <= c; ++k) s = fma(D[k * ld + i2], Y[k * ld + c], s);
+      x[q] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) D[(warp + 4 * q) * ld + i2] = x[q];
   }
   __syncthreads();
-  smem_partial_chol(D, ld, b, b, f.first + c0, d.status);
-  for (int c = warp; c < b; c += nw) {
-    T* col = front_col(d, f, c0 + c) + c0;
-    for (int r = c + lane; r < b; r += 32) col[r] = D[c * ld + r];
+  // A22 -= L21 L21^T (lower), c = 32 + warp + 4 q
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = 32 + warp + 4 * q;
+    if (i2 >= c) {
+      T s = D[c * ld + i2];
+      for (int k = 0; k < 32; ++k) s = fma(-D[k * ld + i2], D[k * ld + c], s);
+      D[c * ld + i2] = s;
+    }
+  }
+  __syncthreads();
+  if (warp == 0)
+    warp_chol_inv32(D + 32 * ld + 32, Y + 32 * ld + 32, ld, max(0, min(b - 32, 32)),
+                    f.first + c0 + 32, d.status);
+  __syncthreads();
+  // Tm = L21 Y11: Tm(i, c) = sum_{k >= c} L21(i, k) Y11(k, c)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = warp + 4 * q;
+    T s = T(0);
+    for (int k = c; k < 32; ++k) s = fma(D[k * ld + i2], Y[c * ld + k], s);
+    Tm[c * 33 + lane] = s;
+  }
+  __syncthreads();
+  // Y21 = -Y22 Tm: Y21(i, c) = -sum_{m <= i} Y22(i, m) Tm(m, c)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int c = warp + 4 * q;
+    T s = T(0);
+    for (int m = 0; m <= lane; ++m) s = fma(Y[(32 + m) * ld + i2], Tm[c * 33 + m], s);
+    Y[c * ld + i2] = -s;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < b * b; idx += blockDim.x) {
+    const int c = idx / b, i = idx % b;
+    if (i >= c) front_col(d, f, c0 + c)[c0 + i] = D[c * ld + i];
+  }
+  T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, i = idx % kNB;
+    Dv[c * kNB + i] = Y[c * ld + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 variant of the diagonal-block kernel (256 threads): the block sits in
+// shared memory; per column one thread takes the square root and reciprocal
+// (FP64 square root and division are costly on this part); the trailing
+// update walks a table of the lower triangle ordered by column from the
+// right, so at column j its first (63 - j)(64 - j) / 2 entries are the live
+// elements and the FMAs spread over all four FP64 pipes of the SM.  The
+// inverse is formed the same way, right-looking by rows.
+// ---------------------------------------------------------------------------
+template <typename T>
+constexpr size_t potrf_smem() {
+  return (size_t)2 * kNB * (kNB + 1) * sizeof(T) + kNB * (kNB + 1) / 2 * sizeof(uint16_t);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*D)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // A(i, c), then L(i, c)
+  T(*Y)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));
+  // lower-triangle entries (i << 8 | c), columns 63, 62, ...
+  uint16_t* tri = reinterpret_cast<uint16_t*>(smem_raw + (size_t)2 * kNB * (kNB + 1) * sizeof(T));
+  __shared__ T s_r;
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int c0 = it.t * kNB;
+  const int b = min(kNB, f.k - c0);
+  const int tid = threadIdx.x;
+  load_diag_block<T, 256>(d, f, c0, b, &D[0][0], kNB + 1);
+  for (int e = tid; e < kNB * (kNB + 1) / 2; e += blockDim.x) {
+    int m = 1;  // column c = 64 - m holds m elements
+    while ((m * (m + 1)) / 2 <= e) ++m;
+    const int c = kNB - m, o = e - (m * (m - 1)) / 2;
+    tri[e] = (uint16_t)(((c + o) << 8) | c);
+  }
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, i = idx % kNB;
+    Y[c][i] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = 0; j < kNB; ++j) {
+    if (tid == 0) {
+      const T piv = D[j][j];
+      if (j < b && !(piv > T(0))) atomicMin(d.status, (unsigned long long)(f.first + c0 + j));
+      const T ljj = dsqrt(piv);
+      D[j][j] = ljj;
+      s_r = T(1) / ljj;
+    }
+    __syncthreads();
+    const T r = s_r;
+    for (int i = j + 1 + tid; i < kNB; i += blockDim.x) D[j][i] *= r;
+    __syncthreads();
+    const int live = ((kNB - 1 - j) * (kNB - j)) / 2;
+    for (int e = tid; e < live; e += blockDim.x) {
+      const int ic = tri[e], i = ic >> 8, c = ic & 255;
+      D[c][i] = fma(-D[j][i], D[j][c], D[c][i]);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < b * b; idx += blockDim.x) {
+    const int c = idx / b, i = idx % b;
+    if (i >= c) front_col(d, f, c0 + c)[c0 + i] = D[c][i];
+  }
+  for (int p = 0; p < kNB; ++p) {
+    if (tid == 0) s_r = T(1) / D[p][p];
+    __syncthreads();
+    const T r = s_r;
+    for (int c = tid; c <= p; c += blockDim.x) Y[c][p] *= r;
+    __syncthreads();
+    const int w = p + 1, cnt = (kNB - 1 - p) * w;
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      const int i = p + 1 + e / w, c = e % w;
+      Y[c][i] = fma(-D[p][i], Y[c][p], Y[c][i]);
+    }
+    __syncthreads();
+  }
+  T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, i = idx % kNB;
+    Dv[c * kNB + i] = Y[c][i];
   }
 }
 
 // ---------------------------------------------------------------------------
 // Large fronts, panel step t: rows [r0, r0 + kTrsmRows) of the panel below
-// the diagonal block, X = A L_tt^{-T}; one thread per row.
+// the diagonal block, X = A L_tt^{-T} as a product with the inverse from
+// k_potrf.  Thread (r, g) computes X(r, j) for j = 16 g .. 16 g + 15.
 // ---------------------------------------------------------------------------
 template <typename T>
 constexpr size_t trsm_smem() {
-  return (size_t)(kNB * (kNB + 1) + kNB * (kTrsmRows + 1) + kNB) * sizeof(T);
+  return (size_t)2 * kNB * (kNB + 1) * sizeof(T);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) k_trsm(FD<T> d, int64_t item_off) {
+__global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*D)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // D[c][r] = L_tt(r, c)
-  T(*X)[kTrsmRows + 1] = reinterpret_cast<T(*)[kTrsmRows + 1]>(
-      smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));          // X[c][row]
-  T* rinv = reinterpret_cast<T*>(smem_raw + (size_t)(kNB * (kNB + 1) + kNB * (kTrsmRows + 1)) *
-                                                sizeof(T));
+  T(*As)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // As[c][r] = A(r0 + r, c0 + c)
+  T(*Li)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(
+      smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));          // Li[c][j] = Linv(j, c)
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int nf = f.k + f.m;
@@ -239,22 +448,63 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm(FD<T> d, int64_t item_off) {
   const int b = min(kNB, f.k - c0);
   const int r0 = it.a;
   const int rows = min(kTrsmRows, nf - r0);
-  const int tid = threadIdx.x;
-  for (int c = 0; c < b; ++c) {
-    const T* col = front_col(d, f, c0 + c);
-    if (tid < b && tid >= c) D[c][tid] = col[c0 + tid];
-    if (tid < rows) X[c][tid] = col[r0 + tid];
+  const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
+  const T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
+  {
+    // all global loads of this thread in flight before the first shared store
+    constexpr int PER = kNB * kNB / 256;
+    const T* P = d.L + f.Loff + (int64_t)c0 * nf + r0;
+    T va[PER], vl[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * 256, c = idx / kNB, rr = idx % kNB;
+      va[u] = (c < b && rr < rows) ? P[(int64_t)c * nf + rr] : T(0);
+      vl[u] = Dv[idx];
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int idx = tid + u * 256, c = idx / kNB, rr = idx % kNB;
+      As[c][rr] = va[u];
+      Li[c][rr] = vl[u];
+    }
   }
   __syncthreads();
-  if (tid < b) rinv[tid] = T(1) / D[tid][tid];
-  __syncthreads();
-  if (tid < rows) {
-    for (int j = 0; j < b; ++j) {
-      T x = X[j][tid];
-      for (int i = 0; i < j; ++i) x -= X[i][tid] * D[i][j];
-      X[j][tid] = x * rinv[j];
+  // thread (r, g): row r, the 16 contiguous columns j = 16 g + q; the product
+  // is triangular (c <= j), so c stops at the thread's last column
+  T x[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) x[q] = T(0);
+  const int jlast = 16 * g + 15;
+  for (int c = 0; c <= jlast; ++c) {
+    const T a = As[c][r];
+    const T* lrow = &Li[c][16 * g];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = fma(a, lrow[q], x[q]);
+  }
+  if (r < rows) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = 16 * g + q;
+      if (j < b) front_col(d, f, c0 + j)[r0 + r] = x[q];
     }
-    for (int c = 0; c < b; ++c) front_col(d, f, c0 + c)[r0 + tid] = X[c][tid];
+  }
+  if (d.split != nullptr) {
+    // FP32 tensor-core path: tf32 hi / lo split of the solved rows, row-major
+    // (64 hi then 64 lo floats per row), zero beyond the panel width b
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) As[16 * g + q][r] = (16 * g + q) < b ? x[q] : T(0);
+    __syncthreads();
+    float* out = d.split + (d.soff[it.s] + r0) * 128;
+    for (int idx = tid; idx < rows * kNB; idx += blockDim.x) {
+      const int rw = idx / kNB, c = idx % kNB;
+      const float xv = (float)As[c][rw];
+      uint32_t hb;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xv));
+      const float hi = __uint_as_float(hb);
+      out[(int64_t)rw * 128 + c] = hi;
+      out[(int64_t)rw * 128 + kNB + c] = xv - hi;
+    }
   }
 }
 
@@ -305,16 +555,40 @@ __global__ void __launch_bounds__(256) k_syrk(FD<T> d, int64_t item_off) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
   }
+  // two-phase read-modify-write: all 16 loads in flight before any store
+  T* p[4][4];
+  T cur[4][4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = rJ + tc + 16 * j;
-    if (c >= nf) continue;
-    T* col = front_col(d, f, c);
+    T* col = c < nf ? front_col(d, f, c) : nullptr;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = rI + tr + 16 * i;
-      if (r < nf && r >= c) col[r] -= acc[i][j];
+      p[i][j] = (col && r < nf && r >= c) ? col + r : nullptr;
     }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cur[i][j] = p[i][j] ? *p[i][j] : T(0);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (p[i][j]) *p[i][j] = cur[i][j] - acc[i][j];
+}
+
+// av[e] = T(sum of the CSR values of lower entry e): one pass per numeric
+// call, so the assembly kernels read values in their own order.
+template <typename T>
+__global__ void k_gather_values(const int64_t* asrc_ptr, const int64_t* asrc, const double* vals,
+                                T* av, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int64_t p = asrc_ptr[e]; p < asrc_ptr[e + 1]; ++p) v += vals[asrc[p]];
+    av[e] = T(v);
   }
 }
 
@@ -325,6 +599,12 @@ cudaError_t init_t() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)potrf_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_potrf_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)potrf_blk_smem<T>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)syrk_smem<T>());
@@ -342,14 +622,19 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
       k_assemble<T><<<grid, 256, 0, st>>>(d, L.item_off);
       break;
     case K_POTRF:
-      k_potrf<T><<<grid, 256, 0, st>>>(d, L.item_off);
+      if constexpr (sizeof(T) == 4)
+        k_potrf_blk<T><<<grid, 128, potrf_blk_smem<T>(), st>>>(d, L.item_off);
+      else
+        k_potrf<T><<<grid, 256, potrf_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_TRSM:
-      k_trsm<T><<<grid, kTrsmRows, trsm_smem<T>(), st>>>(d, L.item_off);
+      k_trsm<T><<<grid, 256, trsm_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_SYRK:
       k_syrk<T><<<grid, 256, syrk_smem<T>(), st>>>(d, L.item_off);
       break;
+    case K_SYRK_TC:
+      return launch_syrk_tc(L, a, st);
     default:
       return cudaErrorInvalidValue;
   }
@@ -360,6 +645,19 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
 
 cudaError_t factor_kernels_init(int prec) {
   return prec == MF_FP32 ? init_t<float>() : init_t<double>();
+}
+
+cudaError_t launch_gather_values(int prec, const FactorArgs& a, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  if (prec == MF_FP32)
+    k_gather_values<float><<<(int)g, 256, 0, st>>>(a.sym.asrc_ptr, a.sym.asrc, a.vals,
+                                                   static_cast<float*>(a.av), n);
+  else
+    k_gather_values<double><<<(int)g, 256, 0, st>>>(a.sym.asrc_ptr, a.sym.asrc, a.vals,
+                                                    static_cast<double*>(a.av), n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_factor(int prec, const Launch& L, const FactorArgs& a, cudaStream_t st) {

@@ -21,6 +21,8 @@ struct DevSym {
   int64_t* asrc = nullptr;
   Item* items = nullptr;
   int32_t* blkoff = nullptr;   // per front: first 64-column block (solve flags)
+  int64_t* soff = nullptr;     // per front: first row in the split buffer
+  Item* arange = nullptr;      // assembly chunks: (child, lo, hi) ranges, sentinel -1
   int64_t* ginv_ptr = nullptr; // forward gather (inverse relative maps)
   int64_t* ginv_src = nullptr;
   int32_t* perm = nullptr;     // perm[new] = old
@@ -31,9 +33,16 @@ struct DevSym {
 struct FactorArgs {
   DevSym sym;
   const double* vals;          // A values, CSR order (device)
+  void* av;                    // T[nnz_lower]: lower entries of C in assembly order
   void* L;                     // T[Lsize]
   void* U;                     // T[Usize]
   unsigned long long* status;  // [0] = first non-positive pivot column
+  // FP32 tensor-core path: per panel row 64 tf32 "hi" then 64 "lo" floats
+  // (row soff[front] + front row); nullptr elsewhere
+  float* split;
+  // per large front of the level (slot in item field b): 64 x 64 inverse of
+  // the current diagonal block of the factor, T
+  void* dinv;
 };
 
 struct SolveArgs {
@@ -54,6 +63,11 @@ struct SolveArgs {
 // prec: MF_FP64 or MF_FP32.  All launchers return cudaGetLastError().
 cudaError_t factor_kernels_init(int prec);
 cudaError_t launch_factor(int prec, const Launch& L, const FactorArgs& a, cudaStream_t st);
+// av[e] = sum of the CSR values of lower entry e (duplicates summed), cast to T
+cudaError_t launch_gather_values(int prec, const FactorArgs& a, int64_t nnz_lower, cudaStream_t st);
+// tcgen05 FP32 trailing update (factor_tc.cu)
+cudaError_t factor_tc_init();
+cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st);
 cudaError_t solve_kernels_init(int prec);
 cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStream_t st);
 

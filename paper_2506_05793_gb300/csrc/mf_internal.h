@@ -19,6 +19,7 @@ namespace mf {
 // column chunk of the large-front assembly.
 constexpr int kNB = 64;
 constexpr int kTile = 64;
+constexpr int kTcTile = 128;  // square tile of the tensor-core trailing update
 constexpr int kTrsmRows = 64;
 constexpr int kAsmCols = 32;
 constexpr int kSmallMax = 128;   // largest front (k+m) of the one-CTA kernel
@@ -51,7 +52,8 @@ enum Kind : int32_t {
   K_POTRF = 2,     // diagonal block Cholesky
   K_TRSM = 3,      // panel rows * L_tt^{-T}
   K_SYRK = 4,      // trailing lower update
-  K_NKINDS_FACTOR = 5,
+  K_SYRK_TC = 5,   // FP32 trailing update on tcgen05 tensor cores (128 x 128)
+  K_NKINDS_FACTOR = 6,
   K_FW_LEVEL = 11,   // per 64-row block: gather, GEMV with solved blocks, diagonal solve
   K_BW_LEVEL = 12,   // per 64-column block: transposed GEMV, diagonal solve
 };
@@ -107,6 +109,11 @@ struct mf_symbolic {
   // launch schedules
   std::vector<mf::Item> items;
   std::vector<mf::Launch> fsched;
+  std::vector<mf::Launch> fsched_tc;  // FP32 with tensor-core trailing updates
+  std::vector<int64_t> soff;          // per front: first row in the split buffer
+  int64_t split_rows = 0;
+  int64_t max_large = 0;              // most large fronts in one level
+  std::vector<mf::Item> arange;       // assembly: (child, lo, hi, 0) lists per chunk
   std::vector<mf::Launch> fwsched, bwsched;
   std::vector<int32_t> blkoff;     // per front: first 64-column block index
   // forward-solve gather: entries ginv_ptr[woff+i]..[woff+i+1] of front row

@@ -169,11 +169,20 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   }
   // diagonal block and reciprocals of its diagonal (pivot blocks)
   if (pivot) {
-    for (int idx = tid; idx < rows * rows; idx += blockDim.x) {
-      const int c = idx / rows, i = idx % rows;
-      if (i >= c) D[c * ld + i] = Lp[(int64_t)(r0 + c) * nf + r0 + i];
+    // all global loads of the diagonal block in flight before the stores
+    T v[kNB * kNB / 256];
+    const T* P = Lp + (int64_t)r0 * nf + r0;
+#pragma unroll
+    for (int u = 0; u < kNB * kNB / 256; ++u) {
+      const int idx = tid + u * 256, c = idx / kNB, i = idx % kNB;
+      v[u] = (c < rows && i < rows && i >= c) ? P[(int64_t)c * nf + i] : T(0);
     }
-    if (tid < rows) rinv[tid] = T(1) / Lp[(int64_t)(r0 + tid) * nf + r0 + tid];
+#pragma unroll
+    for (int u = 0; u < kNB * kNB / 256; ++u) {
+      const int idx = tid + u * 256;
+      D[(idx / kNB) * ld + (idx % kNB)] = v[u];
+    }
+    if (tid < rows) rinv[tid] = T(1) / P[(int64_t)tid * nf + tid];
   }
   // gather w for the rows of this block
   for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
@@ -309,11 +318,22 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
       Lc[ii] = (live && i < ti) ? Lcol[i0 + i] : T(0);
     }
   }
-  for (int idx = tid; idx < bs * bs; idx += blockDim.x) {
-    const int c = idx / bs, j = idx % bs;
-    if (j >= c) Dt[j * ld + c] = Lp[(int64_t)(c0 + c) * nf + c0 + j];
+  {
+    // all global loads of the diagonal block in flight before the stores
+    T v[kNB * kNB / 256];
+    const T* P = Lp + (int64_t)c0 * nf + c0;
+#pragma unroll
+    for (int u = 0; u < kNB * kNB / 256; ++u) {
+      const int idx = tid + u * 256, c = idx / kNB, j = idx % kNB;
+      v[u] = (c < bs && j < bs && j >= c) ? P[(int64_t)c * nf + j] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kNB * kNB / 256; ++u) {
+      const int idx = tid + u * 256;
+      Dt[(idx % kNB) * ld + idx / kNB] = v[u];
+    }
+    if (tid < bs) rinv[tid] = T(1) / P[(int64_t)tid * nf + tid];
   }
-  if (tid < bs) rinv[tid] = T(1) / Lp[(int64_t)(c0 + tid) * nf + c0 + tid];
   T acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = T(0);

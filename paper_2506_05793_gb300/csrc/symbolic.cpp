@@ -565,7 +565,12 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
 // tiles (SYRK), each batched over all large fronts of the level.
 void build_schedules(mf_symbolic& S, int small_max) {
   S.items.clear();
+  S.arange.clear();
   S.fsched.clear();
+  S.fsched_tc.clear();
+  S.soff.assign(S.sn.size(), 0);
+  S.split_rows = 0;
+  S.max_large = 0;
   S.fwsched.clear();
   S.bwsched.clear();
   const int64_t ns = (int64_t)S.sn.size();
@@ -608,6 +613,7 @@ void build_schedules(mf_symbolic& S, int small_max) {
         }
       }
       add(S.fsched, K_SMALL, lev, hi, it, fl);
+      add(S.fsched_tc, K_SMALL, lev, hi, it, fl);
     }
     // large fronts
     std::vector<int32_t> G;
@@ -617,31 +623,64 @@ void build_schedules(mf_symbolic& S, int small_max) {
     it.clear();
     int32_t T = 0;
     for (int32_t s : G) {
-      const int nf = S.sn[s].k + S.sn[s].m;
-      for (int c0 = 0; c0 < nf; c0 += kAsmCols) it.push_back({s, 0, c0, std::min(c0 + kAsmCols, nf)});
-      T = std::max<int32_t>(T, (S.sn[s].k + kNB - 1) / kNB);
+      const SnInfo& P = S.sn[s];
+      const int nf = P.k + P.m;
+      for (int c0 = 0; c0 < nf; c0 += kAsmCols) {
+        const int c1 = std::min(c0 + kAsmCols, nf);
+        // children whose update columns land in [c0, c1): (child, lo, hi)
+        // ranges of their columns, closed by a sentinel
+        const int32_t off = (int32_t)S.arange.size();
+        for (int32_t ci = P.child_begin; ci < P.child_begin + P.nchild; ++ci) {
+          const int32_t c = S.children[ci];
+          const SnInfo& C = S.sn[c];
+          const int32_t* map = S.relmap.data() + C.map_off;
+          const int32_t lo = (int32_t)(std::lower_bound(map, map + C.m, c0) - map);
+          const int32_t hi = (int32_t)(std::lower_bound(map, map + C.m, c1) - map);
+          if (hi > lo) S.arange.push_back({c, lo, hi, 0});
+        }
+        S.arange.push_back({-1, 0, 0, 0});
+        it.push_back({s, off, c0, c1});
+      }
+      T = std::max<int32_t>(T, (P.k + kNB - 1) / kNB);
     }
     add(S.fsched, K_ASSEMBLE, lev, 0, it, 0.0);
+    add(S.fsched_tc, K_ASSEMBLE, lev, 0, it, 0.0);
+    // rows of the split buffer: the level's large fronts side by side
+    int64_t srow = 0;
+    for (int32_t s : G) {
+      S.soff[s] = srow;
+      srow += S.sn[s].k + S.sn[s].m;
+    }
+    S.split_rows = std::max(S.split_rows, srow);
+    S.max_large = std::max<int64_t>(S.max_large, (int64_t)G.size());
     for (int32_t t = 0; t < T; ++t) {
-      std::vector<Item> ip, it3, is;
+      std::vector<Item> ip, it3, is, itc;
       double fp = 0, ft = 0, fs = 0;
-      for (int32_t s : G) {
+      for (size_t gi = 0; gi < G.size(); ++gi) {
+        const int32_t s = G[gi];
+        const int lpos = (int)gi;  // slot of the front's diagonal-block inverse
         const int k = S.sn[s].k, nf = k + S.sn[s].m;
         if (k <= t * kNB) continue;
         const int b = std::min(kNB, k - t * kNB);
         const int p0 = t * kNB + b;
-        ip.push_back({s, t, 0, 0});
+        ip.push_back({s, t, 0, lpos});
         fp += (double)b * b * b / 3.0;
-        for (int r0 = p0; r0 < nf; r0 += kTrsmRows) it3.push_back({s, t, r0, 0});
+        for (int r0 = p0; r0 < nf; r0 += kTrsmRows) it3.push_back({s, t, r0, lpos});
         ft += (double)(nf - p0) * b * b;
         const int nt = (nf - p0 + kTile - 1) / kTile;
         for (int I = 0; I < nt; ++I)
           for (int J = 0; J <= I; ++J) is.push_back({s, t, I, J});
+        const int nt2 = (nf - p0 + kTcTile - 1) / kTcTile;
+        for (int I = 0; I < nt2; ++I)
+          for (int J = 0; J <= I; ++J) itc.push_back({s, t, I, J});
         fs += (double)(nf - p0) * (double)(nf - p0 + 1) * b;
       }
       add(S.fsched, K_POTRF, lev, t, ip, fp);
       add(S.fsched, K_TRSM, lev, t, it3, ft);
       add(S.fsched, K_SYRK, lev, t, is, fs);
+      add(S.fsched_tc, K_POTRF, lev, t, ip, fp);
+      add(S.fsched_tc, K_TRSM, lev, t, it3, ft);
+      add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fs);
     }
   }
   // ---- solves: one sync-free launch per level and sweep.  Items are the

@@ -186,7 +186,7 @@ def test_profile_counts_flops(mf, orc):
     assert info["front_flops"] >= info["flops"]
     assert all(p["ms"] >= 0 for p in prof.values())
     nf, ns = mf.mf_factor_launch_counts(f)
-    assert nf == sum(p["launches"] for p in prof.values())
+    assert nf == sum(p["launches"] for p in prof.values()) + 1  # + the value gather
     mf.mf_factor_free(f)
     mf.mf_symbolic_free(s)
     mf.mf_destroy(h)
@@ -282,3 +282,43 @@ def test_relaxed_and_fundamental_fronts_agree(mf, orc):
     for L in Ls:
         assert orc.rel_fro(L, F.Lx) <= RELF64
     assert orc.rel_fro(Ls[0], Ls[1]) <= RELF64
+
+
+@pytest.mark.parametrize("case", ["dense_200", "dense_333", "lap3d_jump_20", "q1_14x12x4"])
+def test_fp32_tensor_core_update(mf, orc, case):
+    """FP32 factor with the tcgen05 split-TF32 trailing update agrees with the
+    FP32 FMA path and with the FP64 oracle to FP32 accuracy."""
+    import scipy.sparse as sp
+    if case.startswith("dense"):
+        n = int(case.split("_")[1])
+        rng = np.random.default_rng(n)
+        M = rng.standard_normal((n, n))
+        A = sp.csr_matrix(M @ M.T + n * np.eye(n))
+        rp, ci, v, perm = A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data, None
+    elif case == "lap3d_jump_20":
+        rp, ci, v, perm, _ = gen.config3(20)
+    else:
+        rp, ci, v = gen.q1_extruded(14, 12, 4, seed=3)
+        perm = gen.nd_perm((15, 13, 5), split_axes=(0, 1), dofs=2)
+    F = orc.factor(rp, ci, v, perm)
+    out = {}
+    for tc in (0, 1):
+        opt = mf.mf_options_default()
+        opt.tc = tc
+        opt.profile = 1
+        h = mf.mf_create(opt)
+        s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+        f = mf.mf_factor_create(h, s, 1)
+        mf.mf_factor_numeric(f, v)
+        out[tc] = mf.mf_factor_export_L(f, mf.mf_symbolic_get_info(s)["nnz_L"])
+        prof = mf.mf_factor_profile(f)
+        if tc:
+            assert prof["syrk_tc"]["launches"] > 0 and prof["syrk"]["launches"] == 0
+        mf.mf_factor_free(f)
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
+    r_fma = orc.rel_fro(out[0], F.Lx)
+    r_tc = orc.rel_fro(out[1], F.Lx)
+    assert r_fma <= 5e-4 and r_tc <= 5e-4
+    # split-TF32 keeps FP32 accuracy: within a small factor of the FMA path
+    assert r_tc <= 4.0 * r_fma + 1e-6
