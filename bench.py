@@ -43,15 +43,21 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="q1", choices=["q1", "lap3d"],
+    p.add_argument("--workload", default="q1", choices=["q1", "lap3d", "batch"],
                    help="q1: extruded Q1 ice-sheet mesh (default); lap3d: 7-point Laplacian size^3 "
-                        "(small cases for profiling)")
+                        "(small cases for profiling); batch: 512 7-point Laplacian boxes with "
+                        "sides U{8..48} (seed 4) as one block-diagonal forest")
     p.add_argument("--size", type=int, default=None,
                    help="q1: horizontal elements per side (256); lap3d: grid side (48)")
     p.add_argument("--layers", type=int, default=10)
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32"],
                    help="precision of the timed factorization + solve (fp64 is the benchmark; "
                         "fp32 runs the tensor-core path, for profiling)")
+    p.add_argument("--ir", action="store_true",
+                   help="step = FP32 factorization + solve refined in FP64 to berr 1e-13")
+    p.add_argument("--autotune", action="store_true",
+                   help="pick relaxation / small-front limit / tensor cores with mf_autotune first")
+    p.add_argument("--count", type=int, default=512, help="batch: number of boxes")
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
@@ -62,6 +68,11 @@ def load_workload(args):
     if args.workload == "lap3d":
         rp, ci, v = gen.laplacian_3d(args.size)
         perm = gen.nd_perm((args.size,) * 3)
+    elif args.workload == "batch":
+        mats, _ = gen.box_batch(args.count, 8, 48, seed=4)
+        rp, ci, v = gen.block_diag_csr([(a, b, c) for a, b, c, _ in mats])
+        offs = np.cumsum([0] + [len(m[0]) - 1 for m in mats])
+        perm = np.concatenate([m[3] + o for m, o in zip(mats, offs[:-1])]).astype(np.int32)
     else:
         rp, ci, v = gen.q1_extruded(args.size, args.size, args.layers, seed=1)
         perm = gen.nd_perm((args.size + 1, args.size + 1, args.layers + 1), split_axes=(0, 1),
@@ -74,6 +85,8 @@ def load_workload(args):
 def workload_name(args):
     if args.workload == "lap3d":
         return "laplacian7_%d^3_nd" % args.size
+    if args.workload == "batch":
+        return "batch_%d_laplacian7_boxes_8-48_seed4" % args.count
     return "q1_extruded_%dx%dx%d_2dof_hnd" % (args.size, args.size, args.layers)
 
 
@@ -96,13 +109,21 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x):
+    """Max of a host float over all ranks (NCCL on GPUs, gloo on CPU)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(units_per_rank, steps, ws, ms_max):
+    """Whole-job throughput: every rank processes `units_per_rank` per step
+    (independent replicas, weak scaling); the slowest rank sets the time."""
+    return units_per_rank * steps * ws / (ms_max / 1e3)
 
 
 class ClockSampler:
@@ -213,14 +234,24 @@ def main():
     dev = torch.device("cuda", local)
     rp, ci, v, perm, b = load_workload(args)
     n = len(rp) - 1
+    if args.ir:
+        args.prec = "fp32"
+    prec = mf.MF_FP32 if args.prec == "fp32" else mf.MF_FP64
     opt = mf.mf_options_default()
+    tuned = None
+    if args.autotune:
+        h0 = mf.mf_create()
+        opt, tuned_ms = mf.mf_autotune(h0, rp, ci, perm, v, prec=prec, reps=2)
+        mf.mf_destroy(h0)
+        tuned = {"relax": opt.relax, "small_front_max": opt.small_front_max, "tc": opt.tc,
+                 "ms": tuned_ms}
     opt.profile = 1  # per-launch CUDA events: per-kernel-kind device time
     h = mf.mf_create(opt)
     t0 = time.perf_counter()
     s = mf.mf_symbolic_analyze(h, rp, ci, perm)
     t_sym = time.perf_counter() - t0
     info = mf.mf_symbolic_get_info(s)
-    f = mf.mf_factor_create(h, s, mf.MF_FP32 if args.prec == "fp32" else mf.MF_FP64)
+    f = mf.mf_factor_create(h, s, prec)
     st = torch.cuda.current_stream(dev)
     vd = torch.from_numpy(v).to(dev)
     bd = torch.from_numpy(b).to(dev)
@@ -229,7 +260,10 @@ def main():
 
     def step():
         mf.mf_factor_numeric(f, vd, stream=st, async_=True)
-        mf.mf_solve(f, bd, xd, stream=st)
+        if args.ir:
+            mf.mf_solve_refined(f, bd, xd, tol=1e-13, max_iter=30, stream=st)
+        else:
+            mf.mf_solve(f, bd, xd, stream=st)
 
     for _ in range(args.warmup):
         step()
@@ -253,7 +287,7 @@ def main():
     prof = mf.mf_factor_profile(f)
     ms_max = max_over_ranks(ws, ms)
     flops = info["flops"]
-    value = flops * args.steps * ws / (ms_max / 1e3) / 1e12
+    value = job_value(flops, args.steps, ws, ms_max) / 1e12
     x = xd.cpu().numpy()
     rows = np.repeat(np.arange(n), np.diff(rp))
     anorm = np.max(np.bincount(rows, weights=np.abs(v), minlength=n))
@@ -275,6 +309,9 @@ def main():
                        info["factor_bytes_fp64"] / 1e9),
                    "symbolic_s": t_sym},
         "berr": berr,
+        "step": ("FP32 factor + FP64-refined solve to berr 1e-13" if args.ir else
+                 "%s factor + %s solve" % (args.prec.upper(), args.prec.upper())),
+        "autotune": tuned,
         "gpu_launches": int((nf_launch + ns_launch) * args.steps),
         "clocks": clocks,
     }

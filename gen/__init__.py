@@ -324,47 +324,50 @@ def nd_perm(shape, split_axes=None, leaf_nodes=8, dofs=1):
     nd = len(shape)
     if split_axes is None:
         split_axes = tuple(range(nd))
-    strides = [1]
-    for s in shape[:-1]:
-        strides.append(strides[-1] * s)
-    out = []
+    cache = {}
 
-    def box_nodes(lo, hi):
-        rngs = [np.arange(lo[a], hi[a]) for a in range(nd)]
-        mesh = np.meshgrid(*rngs[::-1], indexing="ij")  # slowest axis first
-        idx = np.zeros(mesh[0].shape, dtype=np.int64)
-        for a in range(nd):
-            idx += mesh[nd - 1 - a] * strides[a]
-        return idx.ravel()
+    def lex(sz):
+        """Node indices of a box of size sz in its own numbering (x fastest)."""
+        return np.arange(int(np.prod(sz)), dtype=np.int64)
 
-    # iterative post-order traversal: (lo, hi, state)
-    stack = [(tuple(0 for _ in shape), shape, 0, None)]
-    while stack:
-        lo, hi, state, info = stack.pop()
-        size = [hi[a] - lo[a] for a in range(nd)]
-        if min(size) <= 0:
-            continue
-        if state == 0:
-            cand = [a for a in split_axes if size[a] >= 3]
-            if int(np.prod(size)) <= leaf_nodes or not cand:
-                out.append(box_nodes(lo, hi))
-                continue
-            ax = max(cand, key=lambda a: (size[a], -a))
-            mid = lo[ax] + size[ax] // 2
-            llo, lhi = list(lo), list(hi)
-            lhi[ax] = mid
-            rlo, rhi = list(lo), list(hi)
-            rlo[ax] = mid + 1
-            slo, shi = list(lo), list(hi)
-            slo[ax] = mid
-            shi[ax] = mid + 1
-            # push in reverse: separator (state 2), right, left
-            stack.append((tuple(slo), tuple(shi), 2, None))
-            stack.append((tuple(rlo), tuple(rhi), 0, None))
-            stack.append((tuple(llo), tuple(lhi), 0, None))
+    def local_order(sz):
+        # order of the nodes of a box of size sz, as indices of the box's own
+        # lexicographic numbering; depends only on the box size
+        if sz in cache:
+            return cache[sz]
+        cand = [a for a in split_axes if sz[a] >= 3]
+        if int(np.prod(sz)) <= leaf_nodes or not cand or min(sz) <= 0:
+            out = lex(sz)
         else:
-            out.append(box_nodes(lo, hi))
-    perm_nodes = np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
+            ax = max(cand, key=lambda a: (sz[a], -a))
+            mid = sz[ax] // 2
+            strides = [1]
+            for d in sz[:-1]:
+                strides.append(strides[-1] * d)
+            parts = []
+            for lo, hi in ((0, mid), (mid + 1, sz[ax]), (mid, mid + 1)):
+                sub = list(sz)
+                sub[ax] = hi - lo
+                sub = tuple(sub)
+                if min(sub) <= 0:
+                    continue
+                # coordinates of the sub-box's nodes in its own numbering
+                o = local_order(sub) if (lo, hi) != (mid, mid + 1) else lex(sub)
+                coords = []
+                rem = o
+                for d in range(nd):
+                    coords.append(rem % sub[d])
+                    rem = rem // sub[d]
+                coords[ax] = coords[ax] + lo
+                idx = np.zeros(len(o), dtype=np.int64)
+                for d in range(nd):
+                    idx += coords[d] * strides[d]
+                parts.append(idx)
+            out = np.concatenate(parts) if parts else lex(sz)
+        cache[sz] = out
+        return out
+
+    perm_nodes = local_order(shape) if int(np.prod(shape)) > 0 else np.zeros(0, dtype=np.int64)
     if dofs == 1:
         return perm_nodes.astype(np.int32)
     p = (perm_nodes[:, None] * dofs + np.arange(dofs)[None, :]).reshape(-1)

@@ -157,6 +157,20 @@ int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li);
 int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent,
                                int32_t* level);
 
+/* Autotuner (no paper counterpart; the paper tunes by hand).  Times the
+ * numeric factorization of the given matrix and values in precision prec
+ * for every combination of: relaxed amalgamation on/off, small-front limit
+ * 32/64/128 (which fronts go to the one-CTA kernel vs the tiled kernels)
+ * and, for MF_FP32, tensor-core or FMA trailing updates.  Each candidate is
+ * factored once to warm up, then `reps` times (CUDA events, the factor's
+ * own graph).  *best receives h's options with the fastest combination and
+ * *best_ms its mean time.  Values: host or device pointer as
+ * values_on_device says.  Errors as mf_symbolic_analyze / mf_factor_*. */
+int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr,
+                const int32_t* colind, const int32_t* perm,
+                const double* values, int32_t values_on_device, int32_t prec,
+                int32_t reps, mf_options* best, double* best_ms);
+
 /* ---- phase 2: numerical factorization (device; paper Sec. 2 step 2) ----- */
 
 /* Allocate device storage for the factor of s in the given precision
@@ -240,6 +254,59 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
                      double* X, int64_t ldx, int32_t on_device, double tol,
                      int32_t max_iter, int32_t allow_fallback,
                      mf_ir_report* rep, void* stream);
+
+/* ---- serving loop (no paper counterpart beyond Sec. 5's many subdomain
+ * solves per GPU; continuous batching of factor and solve requests) ----- */
+
+typedef struct mf_server mf_server;
+
+typedef struct mf_server_stats {
+  int64_t completed;
+  int64_t failed;
+  double p50_ms;          /* request latency, submit to completion */
+  double p99_ms;
+  double mean_ms;
+  double solves_per_s;    /* completed solves over the served span */
+  int64_t resident_bytes; /* device bytes of resident or in-flight factors */
+  int64_t peak_resident_bytes;
+} mf_server_stats;
+
+/* Start `workers` worker threads (each with its own CUDA stream on the
+ * current device).  Factor requests are admitted while the device bytes of
+ * resident and in-flight factors stay within budget_bytes (0 = no limit).
+ * h must outlive the server. */
+int mf_server_create(mf_handle* h, int32_t workers, int64_t budget_bytes,
+                     mf_server** sv);
+
+/* Queue a factor request: factor s with `values` (host, CSR order) in
+ * precision prec, keep the factor resident, and solve nrhs host right-hand
+ * sides B into X (nrhs may be 0).  FP32 factors solve with FP64 refinement to
+ * berr 1e-13.  s, values, B and X must stay valid until the request is done.
+ * *req identifies the request, *factor_id the resident factor.  Errors:
+ * MF_ERR_OOM if the factor can never fit the budget. */
+int mf_server_submit_factor(mf_server* sv, const mf_symbolic* s,
+                            const double* values, int32_t prec, int32_t nrhs,
+                            const double* B, int64_t ldb, double* X,
+                            int64_t ldx, int64_t* req, int64_t* factor_id);
+
+/* Queue a solve of nrhs host right-hand sides against a resident (or still
+ * queued) factor.  Requests on one factor run one at a time; other requests
+ * proceed meanwhile. */
+int mf_server_submit_solve(mf_server* sv, int64_t factor_id, int32_t nrhs,
+                           const double* B, int64_t ldb, double* X,
+                           int64_t ldx, int64_t* req);
+
+/* Completion state of a request (done flag, mf_status, latency in ms). */
+int mf_server_poll(mf_server* sv, int64_t req, int32_t* done, int32_t* status,
+                   double* latency_ms);
+/* Block until the request is done. */
+int mf_server_wait(mf_server* sv, int64_t req, int32_t* status,
+                   double* latency_ms);
+/* Free a resident factor (deferred until no request uses it). */
+int mf_server_release_factor(mf_server* sv, int64_t factor_id);
+int mf_server_get_stats(mf_server* sv, mf_server_stats* out);
+/* Finish the queued requests, join the workers, free resident factors. */
+int mf_server_free(mf_server* sv);
 
 #ifdef __cplusplus
 }

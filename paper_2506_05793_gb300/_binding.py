@@ -45,6 +45,12 @@ class mf_ir_report(ctypes.Structure):
     _fields_ = [("iterations", _I32), ("fell_back", _I32), ("berr", _D), ("berr_first", _D)]
 
 
+class mf_server_stats(ctypes.Structure):
+    _fields_ = [("completed", _I64), ("failed", _I64), ("p50_ms", _D), ("p99_ms", _D),
+                ("mean_ms", _D), ("solves_per_s", _D), ("resident_bytes", _I64),
+                ("peak_resident_bytes", _I64)]
+
+
 class MFError(RuntimeError):
     def __init__(self, code, msg, column=-1):
         super().__init__("mfchol error %d: %s" % (code, msg))
@@ -77,6 +83,15 @@ _SIGS = {
     "mf_solve": [_P, _I32, _P, _I64, _P, _I64, _I32, _P],
     "mf_solve_refined": [_P, _I32, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _P, _P],
     "mf_solve_noalloc": [_P, _I32, _P, _I64, _P, _I64, _P],
+    "mf_autotune": [_P, _I64, _P, _P, _P, _P, _I32, _I32, _I32, _P, _P],
+    "mf_server_create": [_P, _I32, _I64, _P],
+    "mf_server_submit_factor": [_P, _P, _P, _I32, _I32, _P, _I64, _P, _I64, _P, _P],
+    "mf_server_submit_solve": [_P, _I64, _I32, _P, _I64, _P, _I64, _P],
+    "mf_server_poll": [_P, _I64, _P, _P, _P],
+    "mf_server_wait": [_P, _I64, _P, _P],
+    "mf_server_release_factor": [_P, _I64],
+    "mf_server_get_stats": [_P, _P],
+    "mf_server_free": [_P],
 }
 
 
@@ -223,6 +238,22 @@ def mf_symbolic_supernode_tree(s):
     return par, lev
 
 
+def mf_autotune(h, rowptr, colind, perm, values, prec=MF_FP64, reps=2):
+    """Fastest options for this matrix (see the C header).  Returns (mf_options, ms)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    perm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    dev = _is_device(values)
+    if not dev:
+        values = np.ascontiguousarray(values, dtype=np.float64)
+    best = mf_options()
+    ms = ctypes.c_double()
+    _check(lib().mf_autotune(h, len(rowptr) - 1, _ptr(rowptr), _ptr(colind), _ptr(perm),
+                             _ptr(values), 1 if dev else 0, prec, reps, ctypes.byref(best),
+                             ctypes.byref(ms)))
+    return best, ms.value
+
+
 def mf_factor_create(h, s, prec=MF_FP64):
     f = ctypes.c_void_p()
     _check(lib().mf_factor_create(h, s, prec, ctypes.byref(f)))
@@ -331,6 +362,74 @@ def mf_solve_refined(f, B, X=None, tol=1e-13, max_iter=30, allow_fallback=True, 
     _check(lib().mf_solve_refined(f, nrhs, _ptr(Bh), ldb, _ptr(Xh), ldx, dev, tol, max_iter,
                                   1 if allow_fallback else 0, ctypes.byref(rep), _stream(stream)))
     return Xh, {k: getattr(rep, k) for k, _ in mf_ir_report._fields_}
+
+
+# ---------------------------------------------------------------------------
+# serving loop.  Host arrays handed to a request are kept alive by the
+# binding until the request is waited on.
+_keep = {}
+
+
+def mf_server_create(h, workers=4, budget_bytes=0):
+    sv = ctypes.c_void_p()
+    _check(lib().mf_server_create(h, workers, budget_bytes, ctypes.byref(sv)))
+    return sv
+
+
+def mf_server_submit_factor(sv, s, values, prec, B=None, X=None):
+    """Returns (req, factor_id, X); B/X column-major host arrays or None."""
+    values = np.ascontiguousarray(values, dtype=np.float64)
+    nrhs, ldb = 0, 1
+    if B is not None:
+        B = np.asfortranarray(np.asarray(B, dtype=np.float64).reshape(B.shape[0], -1))
+        nrhs, ldb = B.shape[1], B.shape[0]
+        if X is None:
+            X = np.empty_like(B, order="F")
+    req, fid = _I64(), _I64()
+    _check(lib().mf_server_submit_factor(sv, s, _ptr(values), prec, nrhs, _ptr(B), ldb, _ptr(X),
+                                         ldb, ctypes.byref(req), ctypes.byref(fid)))
+    _keep[(sv.value, req.value)] = (values, B, X)
+    return req.value, fid.value, X
+
+
+def mf_server_submit_solve(sv, factor_id, B, X=None):
+    B = np.asfortranarray(np.asarray(B, dtype=np.float64).reshape(B.shape[0], -1))
+    if X is None:
+        X = np.empty_like(B, order="F")
+    req = _I64()
+    _check(lib().mf_server_submit_solve(sv, factor_id, B.shape[1], _ptr(B), B.shape[0], _ptr(X),
+                                        B.shape[0], ctypes.byref(req)))
+    _keep[(sv.value, req.value)] = (B, X)
+    return req.value, X
+
+
+def mf_server_poll(sv, req):
+    d, st, ms = _I32(), _I32(), _D()
+    _check(lib().mf_server_poll(sv, req, ctypes.byref(d), ctypes.byref(st), ctypes.byref(ms)))
+    return bool(d.value), st.value, ms.value
+
+
+def mf_server_wait(sv, req):
+    st, ms = _I32(), _D()
+    _check(lib().mf_server_wait(sv, req, ctypes.byref(st), ctypes.byref(ms)))
+    _keep.pop((sv.value, req), None)
+    return st.value, ms.value
+
+
+def mf_server_release_factor(sv, factor_id):
+    _check(lib().mf_server_release_factor(sv, factor_id))
+
+
+def mf_server_get_stats(sv):
+    out = mf_server_stats()
+    _check(lib().mf_server_get_stats(sv, ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in mf_server_stats._fields_}
+
+
+def mf_server_free(sv):
+    _check(lib().mf_server_free(sv))
+    for key in [k for k in _keep if k[0] == sv.value]:
+        del _keep[key]
 
 
 def exported_symbols():

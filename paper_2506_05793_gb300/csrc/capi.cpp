@@ -322,6 +322,11 @@ int mf_symbolic_supernodes(const mf_symbolic* s, int32_t* sup_ptr) {
 
 int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li) {
   if (!s || !Lp || (!Li && s->nnzL)) return set_error(MF_ERR_INVALID, "NULL argument");
+  try {
+    mf::ensure_fundamental_rows(*s);
+  } catch (const std::bad_alloc&) {
+    return set_error(MF_ERR_OOM, "host allocation failed");
+  }
   Lp[0] = 0;
   int64_t pos = 0;
   for (int64_t sn = 0; sn < s->nsuper; ++sn) {
@@ -494,6 +499,11 @@ int mf_factor_export_L(const mf_factor* f, double* Lx) {
   } catch (const std::bad_alloc&) {
     return set_error(MF_ERR_OOM, "host allocation failed");
   }
+  try {
+    mf::ensure_fundamental_rows(*S);
+  } catch (const std::bad_alloc&) {
+    return set_error(MF_ERR_OOM, "host allocation failed");
+  }
   MF_CK(cudaDeviceSynchronize());
   if (S->Lsize) MF_CK(cudaMemcpy(buf.data(), f->L, S->Lsize * es, cudaMemcpyDeviceToHost));
   // gather the fundamental pattern out of the front panels
@@ -542,6 +552,77 @@ int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches, double*
 }
 
 }  // extern "C"
+
+int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                const int32_t* perm, const double* values, int32_t values_on_device, int32_t prec,
+                int32_t reps, mf_options* best, double* best_ms) {
+  if (!h || !best || !best_ms || reps < 1) return set_error(MF_ERR_INVALID, "invalid autotune arguments");
+  if (prec != MF_FP64 && prec != MF_FP32) return set_error(MF_ERR_INVALID, "bad precision");
+  *best = h->opt;
+  *best_ms = -1.0;
+  cudaStream_t st = nullptr;
+  MF_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MF_CK(cudaEventCreate(&e0));
+  MF_CK(cudaEventCreate(&e1));
+  int rc = MF_OK;
+  const int smalls[3] = {mf::kSmallMax, 64, 32};
+  for (int relax = 1; relax >= 0 && rc == MF_OK; --relax) {
+    mf_handle tmp = *h;
+    tmp.opt.relax = relax;
+    tmp.opt.profile = 0;
+    tmp.opt.use_graphs = 1;
+    mf_symbolic* S = nullptr;
+    rc = mf_symbolic_analyze(&tmp, n, rowptr, colind, perm, &S);
+    if (rc != MF_OK) break;
+    for (int si = 0; si < 3 && rc == MF_OK; ++si) {
+      try {
+        mf::build_schedules(*S, smalls[si]);
+      } catch (const std::bad_alloc&) {
+        rc = set_error(MF_ERR_OOM, "host allocation failed");
+        break;
+      }
+      {
+        std::lock_guard<std::mutex> lk(S->dev_mu);  // schedules changed: new device copy
+        S->dev.reset();
+        S->dev_device = -1;
+      }
+      const int ntc = prec == MF_FP32 ? 2 : 1;
+      for (int tci = 0; tci < ntc && rc == MF_OK; ++tci) {
+        tmp.opt.small_front_max = smalls[si];
+        tmp.opt.tc = prec == MF_FP32 ? 1 - tci : h->opt.tc;
+        mf_factor* f = nullptr;
+        rc = mf_factor_create(&tmp, S, prec, &f);
+        if (rc != MF_OK) break;
+        rc = mf_factor_numeric(f, values, values_on_device, st, 0);
+        float ms = 0.f;
+        if (rc == MF_OK) {
+          cudaEventRecord(e0, st);
+          for (int r = 0; r < reps && rc == MF_OK; ++r) rc = mf_factor_numeric(f, values, values_on_device, st, 1);
+          cudaEventRecord(e1, st);
+          if (rc == MF_OK) rc = mf_factor_check(f, st);
+          if (rc == MF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            rc = set_error(MF_ERR_CUDA, "cudaEventElapsedTime failed");
+        }
+        mf_factor_free(f);
+        if (rc != MF_OK) break;
+        const double mean = (double)ms / reps;
+        if (*best_ms < 0 || mean < *best_ms) {
+          *best_ms = mean;
+          *best = h->opt;
+          best->relax = relax;
+          best->small_front_max = smalls[si];
+          best->tc = tmp.opt.tc;
+        }
+      }
+    }
+    mf_symbolic_free(S);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  return rc;
+}
 
 // ---------------------------------------------------------------------------
 // Solve

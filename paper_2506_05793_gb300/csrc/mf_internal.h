@@ -80,8 +80,10 @@ struct mf_symbolic {
   std::vector<int64_t> colcount;  // c_j
   std::vector<int32_t> sup_ptr;   // nsuper + 1 (fundamental supernodes, exported)
   std::vector<int32_t> col2sn;
-  std::vector<int32_t> fs_rowidx;    // rows of each fundamental supernode
-  std::vector<int64_t> fs_rows_off;  // nsuper + 1
+  std::vector<int32_t> fs_rowidx;    // rows of each fundamental supernode (lazy)
+  std::vector<int64_t> fs_rows_off;  // nsuper + 1 (empty until first needed)
+  std::vector<int64_t> low_cp;       // strict lower triangle of C by columns
+  std::vector<int32_t> low_cr;
   std::vector<int32_t> fs_parent;    // fundamental supernodal tree
   // fronts: contiguous column ranges after relaxed amalgamation; every
   // numeric structure below (sn, rowidx, relmap, schedules) is per front
@@ -136,6 +138,7 @@ namespace mf {
 int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
             const int32_t* perm, std::string& err);
 void build_schedules(mf_symbolic& S, int small_max);
+void ensure_fundamental_rows(const mf_symbolic& S);
 // error reporting (capi.cpp)
 int set_error(int code, const std::string& msg);
 // solve with caller-provided work memory (capi.cpp)

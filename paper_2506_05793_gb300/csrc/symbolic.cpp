@@ -15,8 +15,12 @@
 //   7. level sets of the supernodal tree (height: leaves = 0), memory plan,
 //      per-column assembly map of A into the fronts.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <set>
 #include <numeric>
 
 #include "mf_internal.h"
@@ -24,6 +28,19 @@
 namespace mf {
 
 namespace {
+
+// Phase timings of the analysis on stderr when MF_SYMBOLIC_TIMING is set.
+struct PhaseTimer {
+  bool on = std::getenv("MF_SYMBOLIC_TIMING") != nullptr;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  void mark(const char* what) {
+    if (!on) return;
+    const auto t1 = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[mf symbolic] %-28s %8.3f s\n", what,
+                 std::chrono::duration<double>(t1 - t0).count());
+    t0 = t1;
+  }
+};
 
 int invalid(std::string& err, const std::string& msg) {
   err = msg;
@@ -34,34 +51,42 @@ int invalid(std::string& err, const std::string& msg) {
 
 // Device memory of the update matrices.  U_s is written when front s is
 // factored (level(s)) and read when its parent is assembled
-// (level(parent(s))); after that level it is dead.  Blocks are placed first
-// fit in a simulated heap, level by level, so chains of thin supernodes reuse
-// the same memory instead of holding every update matrix at once.  Returns
-// the peak size (elements) and sets Uoff for every supernode.
+// (level(parent(s))); after that level it is dead.  Blocks are placed best fit
+// in a simulated heap, level by level (free blocks indexed by offset for
+// coalescing and by size for the fit), so chains of thin fronts reuse the same
+// memory instead of holding every update matrix at once.  Returns the peak
+// size (elements) and sets Uoff for every front.
 int64_t plan_update_memory(mf_symbolic& S) {
   const int64_t ns = (int64_t)S.sn.size();
   std::vector<std::vector<int32_t>> bylev(S.nlevels);
   for (int64_t s = 0; s < ns; ++s) bylev[S.slevel[s]].push_back((int32_t)s);
-  std::map<int64_t, int64_t> freeb;  // offset -> size
+  std::map<int64_t, int64_t> by_off;              // offset -> size
+  std::set<std::pair<int64_t, int64_t>> by_size;   // (size, offset)
+  auto erase_size = [&](int64_t size, int64_t off) { by_size.erase({size, off}); };
   std::vector<std::vector<std::pair<int64_t, int64_t>>> release(S.nlevels + 1);
   int64_t top = 0;
   for (int32_t lev = 0; lev < S.nlevels; ++lev) {
     // blocks read at level lev-1 are dead now
     if (lev >= 1) {
-      for (const auto& b : release[lev - 1]) {
-        auto it = freeb.emplace(b.first, b.second).first;
-        auto nx = std::next(it);
-        if (nx != freeb.end() && it->first + it->second == nx->first) {
-          it->second += nx->second;
-          freeb.erase(nx);
+      for (const auto& blk : release[lev - 1]) {
+        int64_t off = blk.first, size = blk.second;
+        auto nx = by_off.lower_bound(off);
+        if (nx != by_off.end() && off + size == nx->first) {
+          size += nx->second;
+          erase_size(nx->second, nx->first);
+          nx = by_off.erase(nx);
         }
-        if (it != freeb.begin()) {
-          auto pv = std::prev(it);
-          if (pv->first + pv->second == it->first) {
-            pv->second += it->second;
-            freeb.erase(it);
+        if (nx != by_off.begin()) {
+          auto pv = std::prev(nx);
+          if (pv->first + pv->second == off) {
+            off = pv->first;
+            size += pv->second;
+            erase_size(pv->second, pv->first);
+            by_off.erase(pv);
           }
         }
+        by_off.emplace(off, size);
+        by_size.insert({size, off});
       }
       release[lev - 1].clear();
     }
@@ -78,25 +103,27 @@ int64_t plan_update_memory(mf_symbolic& S) {
         continue;
       }
       int64_t off = -1;
-      for (auto it = freeb.begin(); it != freeb.end(); ++it) {
-        if (it->second >= sz) {
-          off = it->first;
-          const int64_t rest = it->second - sz;
-          freeb.erase(it);
-          if (rest > 0) freeb.emplace(off + sz, rest);
-          break;
+      auto fit = by_size.lower_bound({sz, (int64_t)-1});
+      if (fit != by_size.end()) {
+        const int64_t bsize = fit->first;
+        off = fit->second;
+        by_size.erase(fit);
+        by_off.erase(off);
+        if (bsize > sz) {
+          by_off.emplace(off + sz, bsize - sz);
+          by_size.insert({bsize - sz, off + sz});
         }
-      }
-      if (off < 0) {
-        // grow the heap; merge with a free block that ends at the top
-        if (!freeb.empty()) {
-          auto last = std::prev(freeb.end());
+      } else {
+        // grow the heap, absorbing a free block that ends at the top
+        off = top;
+        if (!by_off.empty()) {
+          auto last = std::prev(by_off.end());
           if (last->first + last->second == top) {
             off = last->first;
-            freeb.erase(last);
+            erase_size(last->second, last->first);
+            by_off.erase(last);
           }
         }
-        if (off < 0) off = top;
         top = off + sz;
       }
       I.Uoff = off;
@@ -118,6 +145,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
   for (int64_t p = 0; p < nnz; ++p)
     if (colind[p] < 0 || colind[p] >= n) return invalid(err, "colind out of range");
 
+  PhaseTimer timer;
   S.n = n;
   S.nnzA = nnz;
   S.rowptr.assign(rowptr, rowptr + n + 1);
@@ -163,6 +191,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
     }
   }
 
+  timer.mark("lower triangle");
   // ---- 3. elimination tree
   std::vector<int32_t>& parent = S.parent;
   parent.assign(n, -1);
@@ -181,6 +210,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
     }
   }
 
+  timer.mark("etree");
   // ---- 4. postorder + column counts (row-subtree leaves and LCAs)
   std::vector<int32_t> post(n);
   {
@@ -250,6 +280,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
       if (parent[j] != -1) delta[parent[j]] += delta[j];
     }
   }
+  timer.mark("column counts");
   S.colcount = delta;
   S.nnzL = 0;
   S.flops = 0.0;
@@ -300,47 +331,13 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
       if (sparent[s] != -1) S.children[fillc[sparent[s]]++] = (int32_t)s;
   }
 
-  // ---- 6. fundamental supernode row lists (exported pattern of L)
+  timer.mark("supernodes");
+  // update rows of each fundamental supernode: m_s = c_first - k_s
   std::vector<int32_t> fs_m(ns, 0);
+  for (int64_t s = 0; s < ns; ++s)
+    fs_m[s] = (int32_t)(S.colcount[S.sup_ptr[s]] - (S.sup_ptr[s + 1] - S.sup_ptr[s]));
   S.fs_rowidx.clear();
-  S.fs_rows_off.assign(ns + 1, 0);
-  {
-    std::vector<int32_t> mark(n, -1), upd;
-    for (int64_t s = 0; s < ns; ++s) {
-      const int32_t f = S.sup_ptr[s], l = S.sup_ptr[s + 1] - 1, k = l - f + 1;
-      upd.clear();
-      for (int32_t j = f; j <= l; ++j)
-        for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
-          const int32_t i = cr[p];
-          if (i > l && mark[i] != s) {
-            mark[i] = (int32_t)s;
-            upd.push_back(i);
-          }
-        }
-      for (int32_t ci = schild_cnt[s]; ci < schild_cnt[s + 1]; ++ci) {
-        const int32_t c = S.children[ci];
-        const int32_t* crow = S.fs_rowidx.data() + S.fs_rows_off[c] + (S.sup_ptr[c + 1] - S.sup_ptr[c]);
-        for (int32_t t = 0; t < fs_m[c]; ++t) {
-          const int32_t r = crow[t];
-          if (r > l && mark[r] != s) {
-            mark[r] = (int32_t)s;
-            upd.push_back(r);
-          }
-        }
-      }
-      std::sort(upd.begin(), upd.end());
-      const int32_t m = (int32_t)upd.size();
-      if ((int64_t)k + m != S.colcount[f]) {
-        err = "front size disagrees with the column count";
-        return MF_ERR_INTERNAL;
-      }
-      fs_m[s] = m;
-      S.fs_rows_off[s] = (int64_t)S.fs_rowidx.size();
-      for (int32_t j = f; j <= l; ++j) S.fs_rowidx.push_back(j);
-      S.fs_rowidx.insert(S.fs_rowidx.end(), upd.begin(), upd.end());
-    }
-    S.fs_rows_off[ns] = (int64_t)S.fs_rowidx.size();
-  }
+  S.fs_rows_off.clear();
 
   // ---- 7. relaxed amalgamation of fundamental supernodes into fronts.
   // A child whose columns end right before its parent's first column is
@@ -401,6 +398,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
       if (fparent[F] >= 0) S.children[fillc[fparent[F]]++] = (int32_t)F;
   }
 
+  timer.mark("amalgamation + front tree");
   // ---- 8. front row lists, relative maps, levels
   S.sn.assign(nfr, SnInfo{});
   S.slevel.assign(nfr, 0);
@@ -412,12 +410,38 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
   S.front_flops = 0.0;
   S.nlevels = nfr > 0 ? 1 : 0;
   {
-    std::vector<int32_t> posn(n, -1), stamp(n, -1);
+    std::vector<int32_t> posn(n, -1), stamp(n, -1), mark(n, -1), upd;
     for (int64_t F = 0; F < nfr; ++F) {
       const int32_t top = tops[F];
       const int32_t f = S.front_ptr[F], l = S.front_ptr[F + 1] - 1, k = l - f + 1;
-      const int32_t m = fs_m[top];
-      const int32_t* upd = S.fs_rowidx.data() + S.fs_rows_off[top] + (S.sup_ptr[top + 1] - S.sup_ptr[top]);
+      // update rows: entries of C below the front's columns, plus the
+      // children's update rows below them (the multifrontal structure)
+      upd.clear();
+      for (int32_t j = f; j <= l; ++j)
+        for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+          const int32_t i = cr[p];
+          if (i > l && mark[i] != F) {
+            mark[i] = (int32_t)F;
+            upd.push_back(i);
+          }
+        }
+      for (int32_t ci = fchild_cnt[F]; ci < fchild_cnt[F + 1]; ++ci) {
+        const SnInfo& C = S.sn[S.children[ci]];
+        const int32_t* crow = S.rowidx.data() + C.rows_off + C.k;
+        for (int32_t t = 0; t < C.m; ++t) {
+          const int32_t r = crow[t];
+          if (r > l && mark[r] != F) {
+            mark[r] = (int32_t)F;
+            upd.push_back(r);
+          }
+        }
+      }
+      std::sort(upd.begin(), upd.end());
+      const int32_t m = (int32_t)upd.size();
+      if (m != fs_m[top]) {
+        err = "front update rows disagree with the column counts";
+        return MF_ERR_INTERNAL;
+      }
       SnInfo& I = S.sn[F];
       I.first = f;
       I.k = k;
@@ -467,9 +491,13 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
       S.nlevels = std::max(S.nlevels, lev + 1);
     }
   }
+  timer.mark("front rows + maps");
   S.Lsize = Loff;
   S.Wsize = woff;
   S.Usize = plan_update_memory(S);
+  S.low_cp = std::move(cp);
+  S.low_cr = std::move(cr);
+  timer.mark("update-memory plan");
   // inverse of the relative maps for the forward solve: for every front row
   // (global index woff + i) the children's update entries that add into it,
   // children in increasing order (deterministic sums)
@@ -498,23 +526,31 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
     }
   }
 
-  // ---- 9. assembly map of the lower triangle of C (incl. diagonal)
+  timer.mark("gather maps");
+  // ---- 9. assembly map of the lower triangle of C (incl. diagonal).  Rows
+  // are visited in increasing permuted order, so each column's entries come
+  // out sorted by row with duplicates adjacent; front-relative rows come from
+  // a per-front position marker.
   {
     std::vector<int64_t> ccount(n + 1, 0);
-    for (int64_t ro = 0; ro < n; ++ro) {
-      const int32_t i = ip[ro];
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t ro = S.perm[i];
       for (int64_t p = rowptr[ro]; p < rowptr[ro + 1]; ++p)
         if (ip[colind[p]] <= i) ccount[ip[colind[p]] + 1]++;
     }
     for (int64_t j = 0; j < n; ++j) ccount[j + 1] += ccount[j];
-    std::vector<std::pair<int32_t, int64_t>> ent(ccount[n]);
+    std::vector<int32_t> erow(ccount[n]);
+    std::vector<int64_t> esrc(ccount[n]);
     {
       std::vector<int64_t> fillp(ccount.begin(), ccount.end() - 1);
-      for (int64_t ro = 0; ro < n; ++ro) {
-        const int32_t i = ip[ro];
+      for (int64_t i = 0; i < n; ++i) {
+        const int32_t ro = S.perm[i];
         for (int64_t p = rowptr[ro]; p < rowptr[ro + 1]; ++p) {
           const int32_t j = ip[colind[p]];
-          if (j <= i) ent[fillp[j]++] = {i, p};
+          if (j <= i) {
+            erow[fillp[j]] = (int32_t)i;
+            esrc[fillp[j]++] = p;
+          }
         }
       }
     }
@@ -526,35 +562,32 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
     S.asrc_ptr.reserve(ccount[n] + 1);
     S.asrc.reserve(ccount[n]);
     S.asrc_ptr.push_back(0);
-    for (int64_t j = 0; j < n; ++j) {
-      std::sort(ent.begin() + ccount[j], ent.begin() + ccount[j + 1]);
-      const SnInfo& I = S.sn[S.col2front[j]];
-      const int32_t* upd = S.rowidx.data() + I.rows_off + I.k;
-      const int32_t l = I.first + I.k - 1;
-      for (int64_t e = ccount[j]; e < ccount[j + 1]; ++e) {
-        const int32_t i = ent[e].first;
-        if (e == ccount[j] || ent[e - 1].first != i) {
-          int32_t r;
-          if (i <= l) {
-            r = i - I.first;
-          } else {
-            const int32_t* pos = std::lower_bound(upd, upd + I.m, i);
-            if (pos == upd + I.m || *pos != i) {
+    std::vector<int32_t> posn(n, -1);
+    for (int64_t F = 0; F < (int64_t)S.sn.size(); ++F) {
+      const SnInfo& I = S.sn[F];
+      const int32_t* frows = S.rowidx.data() + I.rows_off;
+      for (int32_t r = 0; r < I.k + I.m; ++r) posn[frows[r]] = r;
+      for (int32_t j = I.first; j < I.first + I.k; ++j) {
+        for (int64_t e = ccount[j]; e < ccount[j + 1]; ++e) {
+          const int32_t i = erow[e];
+          if (e == ccount[j] || erow[e - 1] != i) {
+            const int32_t r = posn[i];
+            if (r < 0 || frows[r] != i) {
               err = "entry of A outside its front";
               return MF_ERR_INTERNAL;
             }
-            r = I.k + (int32_t)(pos - upd);
+            S.arow.push_back(r);
+            S.asrc_ptr.push_back(S.asrc_ptr.back());
           }
-          S.arow.push_back(r);
-          S.asrc_ptr.push_back(S.asrc_ptr.back());
+          S.asrc.push_back(esrc[e]);
+          S.asrc_ptr.back()++;
         }
-        S.asrc.push_back(ent[e].second);
-        S.asrc_ptr.back()++;
+        S.acol_ptr[j + 1] = (int64_t)S.arow.size();
       }
-      S.acol_ptr[j + 1] = (int64_t)S.arow.size();
     }
     S.nnz_lower = (int64_t)S.arow.size();
   }
+  timer.mark("assembly map");
   return MF_OK;
 }
 
@@ -710,6 +743,62 @@ void build_schedules(mf_symbolic& S, int small_max) {
     }
     add(S.bwsched, K_BW_LEVEL, lev, 0, it, 0.0);
   }
+}
+
+// Row lists of the fundamental supernodes (the exported pattern of L), built
+// on first request: column j's lower entries of C plus the children's update
+// rows, merged per supernode in increasing order.
+void ensure_fundamental_rows(const mf_symbolic& Sc) {
+  std::lock_guard<std::mutex> lk(Sc.dev_mu);
+  if (!Sc.fs_rows_off.empty() || Sc.nsuper == 0) return;
+  mf_symbolic& S = const_cast<mf_symbolic&>(Sc);
+  const int64_t n = S.n, ns = S.nsuper;
+  std::vector<int32_t> schild_cnt(ns + 1, 0), children;
+  for (int64_t s = 0; s < ns; ++s)
+    if (S.fs_parent[s] >= 0) schild_cnt[S.fs_parent[s] + 1]++;
+  for (int64_t s = 0; s < ns; ++s) schild_cnt[s + 1] += schild_cnt[s];
+  children.assign(schild_cnt[ns], 0);
+  {
+    std::vector<int32_t> fillc(schild_cnt.begin(), schild_cnt.end() - 1);
+    for (int64_t s = 0; s < ns; ++s)
+      if (S.fs_parent[s] >= 0) children[fillc[S.fs_parent[s]]++] = (int32_t)s;
+  }
+  std::vector<int32_t> mark(n, -1), upd;
+  std::vector<int32_t> fs_m(ns, 0);
+  S.fs_rows_off.assign(ns + 1, 0);
+  S.fs_rowidx.clear();
+  int64_t total = 0;
+  for (int64_t s = 0; s < ns; ++s) total += S.colcount[S.sup_ptr[s]];
+  S.fs_rowidx.reserve(total);
+  for (int64_t s = 0; s < ns; ++s) {
+    const int32_t f = S.sup_ptr[s], l = S.sup_ptr[s + 1] - 1;
+    upd.clear();
+    for (int32_t j = f; j <= l; ++j)
+      for (int64_t p = S.low_cp[j]; p < S.low_cp[j + 1]; ++p) {
+        const int32_t i = S.low_cr[p];
+        if (i > l && mark[i] != s) {
+          mark[i] = (int32_t)s;
+          upd.push_back(i);
+        }
+      }
+    for (int32_t ci = schild_cnt[s]; ci < schild_cnt[s + 1]; ++ci) {
+      const int32_t c = children[ci];
+      const int32_t* crow = S.fs_rowidx.data() + S.fs_rows_off[c] + (S.sup_ptr[c + 1] - S.sup_ptr[c]);
+      for (int32_t t = 0; t < fs_m[c]; ++t) {
+        const int32_t r = crow[t];
+        if (r > l && mark[r] != s) {
+          mark[r] = (int32_t)s;
+          upd.push_back(r);
+        }
+      }
+    }
+    std::sort(upd.begin(), upd.end());
+    fs_m[s] = (int32_t)upd.size();
+    S.fs_rows_off[s] = (int64_t)S.fs_rowidx.size();
+    for (int32_t j = f; j <= l; ++j) S.fs_rowidx.push_back(j);
+    S.fs_rowidx.insert(S.fs_rowidx.end(), upd.begin(), upd.end());
+  }
+  S.fs_rows_off[ns] = (int64_t)S.fs_rowidx.size();
 }
 
 }  // namespace mf
