@@ -302,7 +302,8 @@ int mf_server_poll(mf_server* sv, int64_t req, int32_t* done, int32_t* status,
 /* Block until the request is done. */
 int mf_server_wait(mf_server* sv, int64_t req, int32_t* status,
                    double* latency_ms);
-/* Free a resident factor (deferred until no request uses it). */
+/* Free a resident factor; deferred until no running or queued request uses
+ * it (solve requests submitted before the release still run). */
 int mf_server_release_factor(mf_server* sv, int64_t factor_id);
 int mf_server_get_stats(mf_server* sv, mf_server_stats* out);
 /* Finish the queued requests, join the workers, free resident factors. */

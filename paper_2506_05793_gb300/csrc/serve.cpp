@@ -179,7 +179,7 @@ struct mf_server {
         auto fr = factors.find(rq.factor_id);
         if (fr != factors.end()) {
           fr->second.busy = false;
-          if (fr->second.release) {
+          if (fr->second.release && !queued_for(rq.factor_id)) {
             to_free.push_back(fr->second.f);
             reserved -= fr->second.bytes;
             factors.erase(fr);
@@ -204,6 +204,12 @@ struct mf_server {
       cv.notify_all();
     }
     cudaStreamDestroy(st);
+  }
+
+  // a queued request still needs this factor (under mu)
+  bool queued_for(int64_t id) const {
+    return std::any_of(queue.begin(), queue.end(),
+                       [&](const Request& q) { return q.factor_id == id; });
   }
 
   int32_t factors_prec(int64_t id) {
@@ -348,8 +354,8 @@ int mf_server_release_factor(mf_server* sv, int64_t factor_id) {
     std::lock_guard<std::mutex> lk(sv->mu);
     auto fr = sv->factors.find(factor_id);
     if (fr == sv->factors.end()) return mf::set_error(MF_ERR_INVALID, "unknown factor");
-    if (fr->second.busy || !fr->second.ready) {
-      fr->second.release = true;  // freed by the worker that finishes with it
+    if (fr->second.busy || !fr->second.ready || sv->queued_for(factor_id)) {
+      fr->second.release = true;  // freed after its last queued request
       return MF_OK;
     }
     f = fr->second.f;
