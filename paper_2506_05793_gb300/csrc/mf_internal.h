@@ -24,6 +24,7 @@ constexpr int kTrsmRows = 64;
 constexpr int kAsmCols = 32;
 constexpr int kSmallMax = 128;   // largest front (k+m) of the one-CTA kernel
 constexpr int kSolveChunk = 32;  // right-hand sides per solve pass
+constexpr int kWarpSolve = 512;  // fronts this small are solved by one warp
 
 // Per-supernode record, read by every kernel (64 bytes).
 struct SnInfo {
@@ -56,6 +57,8 @@ enum Kind : int32_t {
   K_NKINDS_FACTOR = 6,
   K_FW_LEVEL = 11,   // per 64-row block: gather, GEMV with solved blocks, diagonal solve
   K_BW_LEVEL = 12,   // per 64-column block: transposed GEMV, diagonal solve
+  K_FW_WARP = 13,    // one warp per front with k + m <= kWarpSolve (forward)
+  K_BW_WARP = 14,    // one warp per front with k + m <= kWarpSolve (backward)
 };
 
 struct Launch {
@@ -119,7 +122,7 @@ struct mf_symbolic {
   std::vector<mf::Launch> fwsched, bwsched;
   std::vector<int32_t> blkoff;     // per front: first 64-column block index
   // forward-solve gather: entries ginv_ptr[woff+i]..[woff+i+1] of front row
-  // i are (child << 32 | row of the child front) pairs
+  // i are the global work-vector rows (child woff + child row) added into it
   std::vector<int64_t> ginv_ptr;
   std::vector<int64_t> ginv_src;
   // device mirror, created on first use by a factor on this device

@@ -69,13 +69,6 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// W_s pointer for rhs r: element i of the front work vector is Ws(r)[i].
-template <typename T>
-__device__ __forceinline__ T* wfront(const SD<T>& d, const SnInfo& f, int r) {
-  const int64_t nf = (int64_t)f.k + f.m;
-  return d.W + f.woff * d.nrhs + (int64_t)r * nf;
-}
-
 // Bounded spin: about kSpinLimit x 128 ns before a wait gives up, records
 // MF_ERR_TIMEOUT in status[1] and lets the block continue (no hang).
 constexpr int kSpinLimit = 1 << 22;
@@ -143,7 +136,7 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   T* rinv = D + kNB * (kNB + 1);
   constexpr int ld = kNB + 1;
   __shared__ int s_item;
-  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+  if (threadIdx.x == 0) s_item = counter ? atomicAdd(counter, 1) : (int)blockIdx.x;
   __syncthreads();
   const int nrhs = d.nrhs;
   const Item it = d.items[item_off + s_item];
@@ -186,15 +179,12 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   }
   // gather w for the rows of this block
   for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
-    const int rw = idx % rows, r = idx / rows;
+    const int rw = idx / nrhs, r = idx % nrhs;
     const int i = r0 + rw;
     T w = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
     const int64_t gi = f.woff + i;
-    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e) {
-      const int64_t src = d.ginv_src[e];
-      const SnInfo ch = d.sn[(int32_t)(src >> 32)];
-      w += d.W[ch.woff * nrhs + (int64_t)r * (ch.k + ch.m) + (int32_t)(src & 0xffffffff)];
-    }
+    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e)
+      w += d.W[d.ginv_src[e] * nrhs + r];
     ws[rw * R + r] = w;
   }
   T acc[R];
@@ -234,12 +224,12 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
     if (r < nrhs) red[(g * kNB + row) * R + r] = acc[r];
   __syncthreads();
   for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
-    const int rw = idx % rows, r = idx / rows;
+    const int rw = idx / nrhs, r = idx % nrhs;
     const T sum = red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
                   red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
     const T u = ws[rw * R + r] - sum;
     if (pivot) xs[rw * R + r] = u;
-    else Wf[(int64_t)r * nf + r0 + rw] = u;
+    else Wf[(int64_t)(r0 + rw) * nrhs + r] = u;
   }
   if (!pivot) return;
   __syncthreads();
@@ -413,6 +403,290 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
 }
 
 // ---------------------------------------------------------------------------
+// Fronts with k + m <= 64: one warp per front (8 per CTA), few registers so
+// that many fronts are in flight.  Lane l owns front rows l and l + 32.  The
+// work vector of front s lives in W[(woff_s + i) * nrhs + r].
+// Forward: gather w, then for each pivot j: x_j = w_j / L_jj and
+// w_i -= L_ij x_j below it (the next column is loaded while this one is used).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int64_t count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w_id = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w_id >= count) return;
+  const SnInfo f = d.sn[d.items[item_off + w_id].s];
+  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
+  const T* Lp = d.L + f.Loff;
+  const int i0 = lane, i1 = lane + 32;
+  const T rd0 = i0 < k ? T(1) / Lp[(int64_t)i0 * nf + i0] : T(0);
+  const T rd1 = i1 < k ? T(1) / Lp[(int64_t)i1 * nf + i1] : T(0);
+  for (int r = 0; r < nrhs; ++r) {
+    T w[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      T v = T(0);
+      if (i < nf) {
+        v = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
+        const int64_t gi = f.woff + i;
+        for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e)
+          v += d.W[d.ginv_src[e] * nrhs + r];
+      }
+      w[h] = v;
+    }
+    T c0 = i0 < nf ? Lp[i0] : T(0), c1 = i1 < nf ? Lp[i1] : T(0);
+    for (int j = 0; j < k; ++j) {
+      T n0 = T(0), n1 = T(0);
+      if (j + 1 < k) {
+        const T* nc = Lp + (int64_t)(j + 1) * nf;
+        n0 = i0 < nf ? nc[i0] : T(0);
+        n1 = i1 < nf ? nc[i1] : T(0);
+      }
+      const T rj = __shfl_sync(0xffffffffu, j < 32 ? rd0 : rd1, j & 31);
+      const T xj = __shfl_sync(0xffffffffu, j < 32 ? w[0] : w[1], j & 31) * rj;
+      if (i0 == j) w[0] = xj;
+      else if (i0 > j) w[0] = fma(-c0, xj, w[0]);
+      if (i1 == j) w[1] = xj;
+      else if (i1 > j) w[1] = fma(-c1, xj, w[1]);
+      c0 = n0;
+      c1 = n1;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      if (i < k) d.Y[(int64_t)r * d.n + f.first + i] = w[h];
+      else if (i < nf) d.W[(f.woff + i) * nrhs + r] = w[h];
+    }
+  }
+}
+
+// Backward, one warp per front with k + m <= 64: for j = k-1 .. 0,
+//   x_j = (y_j - sum_{i > j} L_ij x_i) / L_jj,
+// x_i being the ancestors' final values for the update rows and the values
+// just solved for the pivot rows; one warp reduction per column.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bw_tiny(SD<T> d, int64_t item_off, int64_t count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w_id = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (w_id >= count) return;
+  const SnInfo f = d.sn[d.items[item_off + w_id].s];
+  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
+  const T* Lp = d.L + f.Loff;
+  const int32_t* frow = d.rowidx + f.rows_off;
+  const int i0 = lane, i1 = lane + 32;
+  const T rd0 = i0 < k ? T(1) / Lp[(int64_t)i0 * nf + i0] : T(0);
+  const T rd1 = i1 < k ? T(1) / Lp[(int64_t)i1 * nf + i1] : T(0);
+  for (int r = 0; r < nrhs; ++r) {
+    const T* yr = d.Y + (int64_t)r * d.n;
+    T x0 = i0 < nf ? (i0 < k ? T(0) : yr[frow[i0]]) : T(0);
+    T x1 = i1 < nf ? (i1 < k ? T(0) : yr[frow[i1]]) : T(0);
+    const T y0 = i0 < k ? yr[f.first + i0] : T(0);
+    const T y1 = i1 < k ? yr[f.first + i1] : T(0);
+    T c0 = T(0), c1 = T(0);
+    if (k > 0) {
+      const T* col = Lp + (int64_t)(k - 1) * nf;
+      c0 = i0 < nf ? col[i0] : T(0);
+      c1 = i1 < nf ? col[i1] : T(0);
+    }
+    for (int j = k - 1; j >= 0; --j) {
+      T n0 = T(0), n1 = T(0);
+      if (j > 0) {
+        const T* nc = Lp + (int64_t)(j - 1) * nf;
+        n0 = i0 < nf ? nc[i0] : T(0);
+        n1 = i1 < nf ? nc[i1] : T(0);
+      }
+      T p = (i0 > j ? c0 * x0 : T(0)) + (i1 > j ? c1 * x1 : T(0));
+      p = warp_sum(p);
+      const T yj = __shfl_sync(0xffffffffu, j < 32 ? y0 : y1, j & 31);
+      const T rj = __shfl_sync(0xffffffffu, j < 32 ? rd0 : rd1, j & 31);
+      const T xj = (yj - p) * rj;
+      if (i0 == j) x0 = xj;
+      if (i1 == j) x1 = xj;
+      c0 = n0;
+      c1 = n1;
+    }
+    if (i0 < k) d.Y[(int64_t)r * d.n + f.first + i0] = x0;
+    if (i1 < k) d.Y[(int64_t)r * d.n + f.first + i1] = x1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fronts with 64 < k + m <= 32 H: one warp per front (8 per CTA), no flags;
+// the front's work vector is staged in shared memory.  Forward, per block of
+// 32 pivots [jb, jb + 32): the 32 x 32 triangle is solved in registers (lane
+// l owns row jb + l, one shuffle per pivot), then the rows below take
+// w_i -= sum_jj L(i, jb + jj) x_jj with all 32 loads of a row issued
+// together.  Rows of earlier blocks are not read again.
+// ---------------------------------------------------------------------------
+template <typename T, int H>
+__global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, int64_t count) {
+  constexpr int LB = sizeof(T) == 8 ? 16 : 32;  // L loads issued together
+  __shared__ T ws_all[8 * 32 * H];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t w_id = (int64_t)blockIdx.x * 8 + wq;
+  if (w_id >= count) return;
+  T* ws = ws_all + wq * 32 * H;
+  const SnInfo f = d.sn[d.items[item_off + w_id].s];
+  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
+  const T* Lp = d.L + f.Loff;
+  for (int r = 0; r < nrhs; ++r) {
+    __syncwarp();
+    {
+      int64_t e0[H], e1[H];
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const int i = lane + 32 * h;
+        e0[h] = i < nf ? d.ginv_ptr[f.woff + i] : 0;
+        e1[h] = i < nf ? d.ginv_ptr[f.woff + i + 1] : 0;
+      }
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const int i = lane + 32 * h;
+        T v = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
+        for (int64_t e = e0[h]; e < e1[h]; ++e) v += d.W[d.ginv_src[e] * nrhs + r];
+        ws[i] = v;
+      }
+    }
+    __syncwarp();
+    for (int jb = 0; jb < k; jb += 32) {
+      const int bc = min(32, k - jb);
+      // rows jb + lane of columns jb .. jb + bc (indices clamped into the
+      // front so every load is valid and all of them issue together)
+      const int ir = min(jb + lane, nf - 1);
+      T dl[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) dl[jj] = Lp[(int64_t)(jb + min(jj, bc - 1)) * nf + ir];
+      const int id = jb + min(lane, bc - 1);
+      const T rdb = lane < bc ? T(1) / Lp[(int64_t)id * nf + id] : T(0);
+      T v = ws[jb + lane];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        if (jj < bc) {
+          const T xj = __shfl_sync(0xffffffffu, v * rdb, jj);
+          if (lane == jj) v = xj;
+          else if (lane > jj) v = fma(-dl[jj], xj, v);
+        }
+      }
+      if (jb + lane < nf) ws[jb + lane] = v;
+      __syncwarp();
+      // later rows: w_i -= sum_jj L(i, jb + jj) x_jj (x_jj = ws[jb + jj])
+      for (int i = jb + 32 + lane; i < nf + lane; i += 32) {
+        const int ic = min(i, nf - 1);
+        T u = ws[ic];
+#pragma unroll
+        for (int q0 = 0; q0 < 32; q0 += LB) {
+          T lv[LB];
+#pragma unroll
+          for (int q = 0; q < LB; ++q) lv[q] = Lp[(int64_t)(jb + min(q0 + q, bc - 1)) * nf + ic];
+#pragma unroll
+          for (int q = 0; q < LB; ++q)
+            if (q0 + q < bc) u = fma(-lv[q], ws[jb + q0 + q], u);
+        }
+        if (i < nf) ws[i] = u;
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = lane + 32 * h;
+      if (i < k) d.Y[(int64_t)r * d.n + f.first + i] = ws[i];
+      else if (i < nf) d.W[(f.woff + i) * nrhs + r] = ws[i];
+    }
+  }
+}
+
+// Sum over the warp of 32 per-lane vectors: lane l returns sum_lanes p[l].
+// Five halving exchange steps (31 shuffles) instead of 32 reductions.
+template <typename T>
+__device__ __forceinline__ T transpose_sum32(T (&p)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int jj = 0; jj < o; ++jj) {
+      const T send = hi ? p[jj] : p[jj + o];
+      const T keep = hi ? p[jj + o] : p[jj];
+      p[jj] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return p[0];
+}
+
+// Backward, one warp per front, pivot columns in blocks of 32 from the last:
+//   x_j = (y_j - sum_{i > j} L_ij x_i) / L_jj.
+// x of the update rows (ancestors' final values) and of solved pivot rows
+// sit in shared memory.  For block [j0, j0 + 32): lanes own rows to form the
+// sums over rows i >= j0 + 32 (coalesced L reads), a transposed reduction
+// hands column j0 + l's sum to lane l, and the triangle of the diagonal
+// block is solved with lane l owning column j0 + l (one shuffle per pivot).
+// ---------------------------------------------------------------------------
+template <typename T, int H>
+__global__ void __launch_bounds__(256, 2) k_bw_warp(SD<T> d, int64_t item_off, int64_t count) {
+  constexpr int LB = sizeof(T) == 8 ? 16 : 32;
+  __shared__ T xs_all[8 * 32 * H];
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int64_t w_id = (int64_t)blockIdx.x * 8 + wq;
+  if (w_id >= count) return;
+  T* xs = xs_all + wq * 32 * H;
+  const SnInfo f = d.sn[d.items[item_off + w_id].s];
+  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
+  const T* Lp = d.L + f.Loff;
+  const int32_t* frow = d.rowidx + f.rows_off;
+  for (int r = 0; r < nrhs; ++r) {
+    const T* yr = d.Y + (int64_t)r * d.n;
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int i = lane + 32 * h;
+      if (i >= k && i < nf) xs[i] = yr[frow[i]];
+    }
+    __syncwarp();
+    for (int b = (k - 1) >> 5; b >= 0; --b) {
+      const int j0 = 32 * b, bc = min(32, k - j0);
+      T p[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) p[jj] = T(0);
+      for (int i = j0 + bc + lane; i < nf; i += 32) {
+        const T xi = xs[i];
+#pragma unroll
+        for (int q0 = 0; q0 < 32; q0 += LB) {
+          T lv[LB];
+#pragma unroll
+          for (int q = 0; q < LB; ++q) lv[q] = Lp[(int64_t)(j0 + min(q0 + q, bc - 1)) * nf + i];
+#pragma unroll
+          for (int q = 0; q < LB; ++q) p[q0 + q] = fma(lv[q], xi, p[q0 + q]);
+        }
+      }
+      T acc = transpose_sum32(p, lane);
+      const bool own = lane < bc;
+      const int j = j0 + min(lane, bc - 1);
+      T lc[32];
+#pragma unroll
+      for (int ii = 0; ii < 32; ++ii) lc[ii] = Lp[(int64_t)j * nf + j0 + min(ii, bc - 1)];
+#pragma unroll
+      for (int ii = 0; ii < 32; ++ii)
+        if (!(own && ii > lane && ii < bc)) lc[ii] = T(0);
+      const T yv = own ? yr[f.first + j] : T(0);
+      const T rinv = own ? T(1) / Lp[(int64_t)j * nf + j] : T(0);
+      T xj = T(0);
+#pragma unroll
+      for (int ii = 31; ii >= 0; --ii) {
+        if (ii < bc) {
+          const T xi = __shfl_sync(0xffffffffu, (yv - acc) * rinv, ii);
+          if (lane == ii) xj = xi;
+          acc = fma(lc[ii], xi, acc);
+        }
+      }
+      if (own) {
+        xs[j] = xj;
+        d.Y[(int64_t)r * d.n + f.first + j] = xj;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Permutations and FP64 residual kernels.
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -501,16 +775,40 @@ cudaError_t init_t() {
 template <typename T, int R>
 void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   const SD<T> d = make_sd<T>(a);
-  if (L.kind == K_FW_LEVEL)
+  if (L.kind == K_FW_LEVEL)  // param 1: update-row blocks, all pivots done
     k_fw_level<T, R><<<L.count, 256, fw_level_smem<T, R>(), st>>>(
-        d, L.item_off, a.sync + 2 * L.level, a.sync + 2 * a.nlevels);
+        d, L.item_off, L.param ? nullptr : a.sync + 2 * L.level, a.sync + 2 * a.nlevels);
   else
     k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(
         d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
 }
 
+template <typename T, int H>
+void launch_warp(bool fw, const Launch& L, const SolveArgs& a, cudaStream_t st) {
+  const SD<T> d = make_sd<T>(a);
+  const int blocks = (int)((L.count + 7) / 8);
+  if constexpr (H == 2) {
+    if (fw) k_fw_tiny<T><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    else k_bw_tiny<T><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+  } else {
+    if (fw) k_fw_warp<T, H><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    else k_bw_warp<T, H><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+  }
+}
+
 template <typename T>
 cudaError_t launch_t(const Launch& L, const SolveArgs& a, cudaStream_t st) {
+  if (L.kind == K_FW_WARP || L.kind == K_BW_WARP) {
+    const bool fw = L.kind == K_FW_WARP;
+    switch (L.param) {
+      case 2: launch_warp<T, 2>(fw, L, a, st); break;
+      case 4: launch_warp<T, 4>(fw, L, a, st); break;
+      case 8: launch_warp<T, 8>(fw, L, a, st); break;
+      case 16: launch_warp<T, 16>(fw, L, a, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   if (L.kind != K_FW_LEVEL && L.kind != K_BW_LEVEL) return cudaErrorInvalidValue;
   if (a.nrhs <= 1) launch_r<T, 1>(L, a, st);
   else if (a.nrhs <= 8) launch_r<T, 8>(L, a, st);

@@ -499,8 +499,9 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
   S.low_cr = std::move(cr);
   timer.mark("update-memory plan");
   // inverse of the relative maps for the forward solve: for every front row
-  // (global index woff + i) the children's update entries that add into it,
-  // children in increasing order (deterministic sums)
+  // (global index woff + i) the global rows (child woff + child row) of the
+  // children's update entries that add into it, children in increasing order
+  // (deterministic sums)
   S.ginv_ptr.assign(S.Wsize + 1, 0);
   for (int64_t F = 0; F < nfr; ++F) {
     const SnInfo& P = S.sn[F];
@@ -521,7 +522,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
         const SnInfo& C = S.sn[c];
         const int32_t* cmap = S.relmap.data() + C.map_off;
         for (int32_t t = 0; t < C.m; ++t)
-          S.ginv_src[fillg[P.woff + cmap[t]]++] = ((int64_t)c << 32) | (uint32_t)(C.k + t);
+          S.ginv_src[fillg[P.woff + cmap[t]]++] = C.woff + C.k + t;
       }
     }
   }
@@ -716,31 +717,78 @@ void build_schedules(mf_symbolic& S, int small_max) {
       add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fs);
     }
   }
-  // ---- solves: one sync-free launch per level and sweep.  Items are the
-  // 64-row blocks of every front of the level (forward: pivot blocks in
-  // order, then update-row blocks; backward: pivot column blocks in reverse
-  // order).  Items are taken in ticket order, so a block only waits on
-  // blocks with earlier tickets.
+  // ---- solves.  Per level and sweep, fronts with k + m <= kWarpSolve go to
+  // the one-warp kernels (no flags, one launch per row class, 32 H rows with
+  // H = 2, 4, 8, 16) unless the class is too sparse to fill the GPU and the
+  // front has a long pivot chain (k > 64); all other fronts are split into
+  // 64-row blocks for the sync-free level kernel.  Level-kernel items are
+  // taken in ticket order, so a block only waits on blocks with earlier
+  // tickets; they are ordered by depth in their front's chain (every
+  // front's first block, then every front's second, ...), so the resident
+  // blocks are the frontier of all chains rather than the tail of a few.
   S.blkoff.assign(ns + 1, 0);
   for (int64_t s = 0; s < ns; ++s) S.blkoff[s + 1] = S.blkoff[s] + (S.sn[s].k + kNB - 1) / kNB;
-  for (int32_t lev = 0; lev < S.nlevels; ++lev) {
-    const std::vector<int32_t>& L = bylev[lev];
-    it.clear();
+  constexpr size_t kWarpMinFronts = 2048;
+  auto warp_class = [](int nf) { return nf <= 64 ? 0 : nf <= 128 ? 1 : nf <= 256 ? 2 : 3; };
+  // split a level's fronts into warp classes and level-kernel fronts
+  auto split_level = [&](const std::vector<int32_t>& L, std::vector<Item> (&wcls)[4],
+                         std::vector<int32_t>& big) {
+    std::vector<int32_t> cls[4];
+    big.clear();
     for (int32_t s : L) {
-      const int k = S.sn[s].k, m = S.sn[s].m;
-      for (int r0 = 0; r0 < k; r0 += kNB) it.push_back({s, 0, r0, std::min(kNB, k - r0)});
-      for (int r0 = 0; r0 < m; r0 += kNB) it.push_back({s, 1, k + r0, std::min(kNB, m - r0)});
+      const int nf = S.sn[s].k + S.sn[s].m;
+      if (nf <= kWarpSolve) cls[warp_class(nf)].push_back(s);
+      else big.push_back(s);
     }
+    for (int c = 0; c < 4; ++c) {
+      wcls[c].clear();
+      const bool sparse = cls[c].size() < kWarpMinFronts;
+      for (int32_t s : cls[c]) {
+        if (sparse && S.sn[s].k > 2 * 32) big.push_back(s);
+        else wcls[c].push_back({s, 0, 0, 0});
+      }
+    }
+  };
+  std::vector<std::vector<Item>> bydepth;
+  auto flatten = [&](std::vector<Item>& out) {
+    out.clear();
+    for (auto& v : bydepth) {
+      out.insert(out.end(), v.begin(), v.end());
+      v.clear();
+    }
+  };
+  std::vector<Item> wcls[4], upd;
+  std::vector<int32_t> big;
+  for (int32_t lev = 0; lev < S.nlevels; ++lev) {
+    split_level(bylev[lev], wcls, big);
+    upd.clear();
+    for (int32_t s : big) {
+      const int k = S.sn[s].k, m = S.sn[s].m;
+      for (int r0 = 0, dpt = 0; r0 < k; r0 += kNB, ++dpt) {
+        if ((int)bydepth.size() <= dpt) bydepth.resize(dpt + 1);
+        bydepth[dpt].push_back({s, 0, r0, std::min(kNB, k - r0)});
+      }
+      for (int r0 = 0; r0 < m; r0 += kNB) upd.push_back({s, 1, k + r0, std::min(kNB, m - r0)});
+    }
+    flatten(it);
+    for (int c = 0; c < 4; ++c) add(S.fwsched, K_FW_WARP, lev, 2 << c, wcls[c], 0.0);
+    // pivot blocks (flag chains within a front), then the update-row blocks
+    // of the level, which then never wait
     add(S.fwsched, K_FW_LEVEL, lev, 0, it, 0.0);
+    add(S.fwsched, K_FW_LEVEL, lev, 1, upd, 0.0);
   }
   for (int32_t lev = S.nlevels - 1; lev >= 0; --lev) {
-    const std::vector<int32_t>& L = bylev[lev];
-    it.clear();
-    for (int32_t s : L) {
+    split_level(bylev[lev], wcls, big);
+    for (int32_t s : big) {
       const int k = S.sn[s].k;
-      for (int c0 = ((k - 1) / kNB) * kNB; c0 >= 0; c0 -= kNB)
-        it.push_back({s, 0, c0, std::min(kNB, k - c0)});
+      int dpt = 0;
+      for (int c0 = ((k - 1) / kNB) * kNB; c0 >= 0; c0 -= kNB, ++dpt) {
+        if ((int)bydepth.size() <= dpt) bydepth.resize(dpt + 1);
+        bydepth[dpt].push_back({s, 0, c0, std::min(kNB, k - c0)});
+      }
     }
+    flatten(it);
+    for (int c = 0; c < 4; ++c) add(S.bwsched, K_BW_WARP, lev, 2 << c, wcls[c], 0.0);
     add(S.bwsched, K_BW_LEVEL, lev, 0, it, 0.0);
   }
 }
