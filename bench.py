@@ -43,12 +43,14 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="q1", choices=["q1", "lap3d", "batch", "serve"],
+    p.add_argument("--workload", default="q1", choices=["q1", "lap3d", "jump3d", "batch", "serve"],
                    help="q1: extruded Q1 ice-sheet mesh (default); lap3d: 7-point Laplacian size^3 "
-                        "(small cases for profiling); batch: 512 7-point Laplacian boxes with "
-                        "sides U{8..48} (seed 4) as one block-diagonal forest")
+                        "(small cases for profiling); jump3d: 7-point Laplacian size^3 with "
+                        "coefficients 1 / 1e3 on 8^3 blocks (seed 2); batch: 512 7-point Laplacian "
+                        "boxes with sides U{8..48} (seed 4) as one block-diagonal forest")
     p.add_argument("--size", type=int, default=None,
-                   help="q1: horizontal elements per side (256); lap3d: grid side (48)")
+                   help="q1: horizontal elements per side (256); lap3d: grid side (48); "
+                        "jump3d: grid side (96)")
     p.add_argument("--layers", type=int, default=10)
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32"],
                    help="precision of the timed factorization + solve (fp64 is the benchmark; "
@@ -58,6 +60,7 @@ def parse():
     p.add_argument("--autotune", action="store_true",
                    help="pick relaxation / small-front limit / tensor cores with mf_autotune first")
     p.add_argument("--count", type=int, default=512, help="batch: number of boxes")
+    p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per solve")
     p.add_argument("--serve-rates", default="25,100,400",
                    help="serve: Poisson arrival rates (requests/s) to sweep")
     p.add_argument("--serve-requests", type=int, default=240, help="serve: requests per rate")
@@ -72,6 +75,9 @@ def load_workload(args):
     if args.workload == "lap3d":
         rp, ci, v = gen.laplacian_3d(args.size)
         perm = gen.nd_perm((args.size,) * 3)
+    elif args.workload == "jump3d":
+        rp, ci, v = gen.laplacian_3d(args.size, jump_block=8, jump_value=1e3, seed=2)
+        perm = gen.nd_perm((args.size,) * 3)
     elif args.workload == "batch":
         mats, _ = gen.box_batch(args.count, 8, 48, seed=4)
         rp, ci, v = gen.block_diag_csr([(a, b, c) for a, b, c, _ in mats])
@@ -82,13 +88,15 @@ def load_workload(args):
         perm = gen.nd_perm((args.size + 1, args.size + 1, args.layers + 1), split_axes=(0, 1),
                            dofs=2)
     n = len(rp) - 1
-    b = gen.rhs(n, 1, seed=3)
+    b = gen.rhs(n, args.nrhs, seed=3)
     return rp, ci, v, perm, b
 
 
 def workload_name(args):
     if args.workload == "lap3d":
         return "laplacian7_%d^3_nd" % args.size
+    if args.workload == "jump3d":
+        return "laplacian7_%d^3_jump1e3_8^3blocks_nd" % args.size
     if args.workload == "batch":
         return "batch_%d_laplacian7_boxes_8-48_seed4" % args.count
     return "q1_extruded_%dx%dx%d_2dof_hnd" % (args.size, args.size, args.layers)
@@ -294,7 +302,7 @@ def main():
         run_serve(args)
         return
     if args.size is None:
-        args.size = 48 if args.workload == "lap3d" else 256
+        args.size = {"lap3d": 48, "jump3d": 96}.get(args.workload, 256)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -364,8 +372,10 @@ def main():
     x = xd.cpu().numpy()
     rows = np.repeat(np.arange(n), np.diff(rp))
     anorm = np.max(np.bincount(rows, weights=np.abs(v), minlength=n))
-    res = b - gen.csr_matvec(rp, ci, v, x)
-    berr = float(np.max(np.abs(res)) / (anorm * np.max(np.abs(x)) + np.max(np.abs(b))))
+    res = (b - gen.csr_matvec(rp, ci, v, x)).reshape(n, -1)
+    xx, bb = x.reshape(n, -1), b.reshape(n, -1)
+    berr = float(np.max(np.max(np.abs(res), axis=0) /
+                        (anorm * np.max(np.abs(xx), axis=0) + np.max(np.abs(bb), axis=0))))
 
     out = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
@@ -376,7 +386,7 @@ def main():
         "config": {"workload": workload_name(args), "n": n, "nnz_A": int(rp[-1]),
                    "nnz_L": info["nnz_L"],
                    "flops_per_factor": flops, "nsuper": info["nsuper"],
-                   "levels": info["nlevels"], "max_front": info["max_front"], "nrhs": 1,
+                   "levels": info["nlevels"], "max_front": info["max_front"], "nrhs": args.nrhs,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2_flush": "inputs larger than L2 (factor %.1f GB)" % (
                        info["factor_bytes_fp64"] / 1e9),
@@ -430,7 +440,7 @@ def main():
 def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm):
     import torch
     n = len(rp) - 1
-    # solve latency (1 RHS), p50 / p99 over 200 solves
+    # solve latency (nrhs right-hand sides), p50 / p99 over 200 solves
     xd = torch.empty_like(bd)
     for _ in range(3):
         mf.mf_solve(f, bd, xd, stream=st)
@@ -444,9 +454,10 @@ def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm):
     lat = np.array([a.elapsed_time(z) for a, z in ev])
     out["solve_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
     out["solves_per_s"] = float(1e3 / np.mean(lat))
+    out["solve_nrhs"] = args.nrhs
     # end to end through the C-ABI with host buffers (values H2D, B H2D, X D2H)
     K = 2
-    xh = np.empty(n)
+    xh = np.empty_like(b, order="F")
     t0 = time.perf_counter()
     for _ in range(K):
         mf.mf_factor_numeric(f, v)       # host values, sync + status read

@@ -92,6 +92,7 @@ _SIGS = {
     "mf_server_release_factor": [_P, _I64],
     "mf_server_get_stats": [_P, _P],
     "mf_server_free": [_P],
+    "mf_diag_wait_timeout": [_I32, _P],
 }
 
 
@@ -296,6 +297,12 @@ def mf_factor_profile(f):
     _check(lib().mf_factor_profile(f, _ptr(ms), _ptr(n), _ptr(fl)))
     return {k: {"ms": float(ms[i]), "launches": int(n[i]), "flops": float(fl[i])}
             for i, k in enumerate(FACTOR_KINDS)}
+
+
+def mf_diag_wait_timeout(polls=1 << 14, stream=None):
+    """Run the solve's bounded device wait on a flag nothing sets; returns the
+    status code (MF_ERR_TIMEOUT expected) instead of raising."""
+    return int(lib().mf_diag_wait_timeout(polls, _stream(stream)))
 
 
 def _rhs_layout(B):

@@ -551,6 +551,28 @@ int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches, double*
   return MF_OK;
 }
 
+int mf_diag_wait_timeout(int32_t polls, void* stream) {
+  if (polls < 1) return set_error(MF_ERR_INVALID, "polls must be positive");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* buf = nullptr;
+  MF_CK(cudaMalloc(&buf, 256));
+  int rc = MF_OK;
+  unsigned long long host[2] = {0, 0};
+  int* flag = static_cast<int*>(buf);
+  unsigned long long* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(buf) + 128);
+  cudaError_t e = cudaMemsetAsync(buf, 0, 256, st);
+  if (e == cudaSuccess) e = mf::launch_wait_probe(flag, status, polls, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, status, sizeof(host), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) return set_error(MF_ERR_CUDA, std::string("wait probe: ") + cudaGetErrorString(e));
+  if (host[1] == (unsigned long long)MF_ERR_TIMEOUT)
+    rc = set_error(MF_ERR_TIMEOUT, "device wait gave up after " + std::to_string(polls) + " polls");
+  else
+    rc = set_error(MF_ERR_INTERNAL, "wait probe returned without a timeout record");
+  return rc;
+}
+
 }  // extern "C"
 
 int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* colind,

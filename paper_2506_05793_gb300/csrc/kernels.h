@@ -70,6 +70,8 @@ cudaError_t factor_tc_init();
 cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st);
 cudaError_t solve_kernels_init(int prec);
 cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStream_t st);
+cudaError_t launch_wait_probe(const int* flag, unsigned long long* status, int limit,
+                              cudaStream_t st);
 
 // Y[i, r] = T(scale_r * B[perm[i], r]) with scale_r = inv_scale ? inv_scale[r] : 1.
 cudaError_t launch_perm_in(int prec, const double* B, int64_t ldb, const int32_t* perm,

@@ -59,6 +59,8 @@ enum Kind : int32_t {
   K_BW_LEVEL = 12,   // per 64-column block: transposed GEMV, diagonal solve
   K_FW_WARP = 13,    // one warp per front with k + m <= kWarpSolve (forward)
   K_BW_WARP = 14,    // one warp per front with k + m <= kWarpSolve (backward)
+  K_FW_GEMV = 15,    // per 64 update rows: w -= L21 x1 (after the level's pivots)
+  K_BW_GEMV = 16,    // per 64 pivot columns: y -= L21^T x2 (before the chains)
 };
 
 struct Launch {

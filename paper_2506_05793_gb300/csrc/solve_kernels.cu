@@ -84,11 +84,12 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 // The whole CTA waits until *flag != 0 (thread 0 polls with acquire loads).
-__device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* status) {
+__device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* status,
+                                         int limit = kSpinLimit) {
   if (threadIdx.x == 0) {
     int spins = 0;
     while (ld_acquire(flag) == 0) {
-      if (++spins > kSpinLimit) {
+      if (++spins > limit) {
         atomicExch(status + 1, (unsigned long long)MF_ERR_TIMEOUT);
         break;
       }
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
 // ---------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
-    k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
+    k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags, int upd_done) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ld = kNB + 1;
   T* xs = reinterpret_cast<T*>(smem_raw);  // xs[i * R + r]
@@ -287,8 +288,9 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   const T* Lcol = Lp + (int64_t)(c0 + (live ? col : 0)) * nf;
   const int32_t* frow = d.rowidx + f.rows_off;
   const int PB = (k + kNB - 1) / kNB;
-  // tiles: update rows first (no waiting), then later pivot blocks, last first
-  const int ntu = (nf - k + kNB - 1) / kNB;
+  // tiles: update rows first (no waiting; skipped when k_bw_gemv has already
+  // subtracted them from y), then later pivot blocks, last first
+  const int ntu = upd_done ? 0 : (nf - k + kNB - 1) / kNB;
   const int ntiles = ntu + (PB - 1 - c0 / kNB);
   T Lc[16];
   {
@@ -400,6 +402,136 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
     if (lane + 32 < bs) d.Y[(int64_t)r * d.n + f.first + c0 + lane + 32] = v1;
   }
   cta_publish(fl + c0 / kNB);
+}
+
+// ---------------------------------------------------------------------------
+// Streaming products of the large fronts, run after every pivot of the level
+// (forward) or before any (backward), so they never wait.  Shared memory
+// holds kGemvStage staged values plus the per-block partial sums.
+// ---------------------------------------------------------------------------
+constexpr int kGemvStage = 4096;
+
+template <typename T, int R>
+constexpr size_t gemv_smem() {
+  return ((size_t)kGemvStage + (size_t)4 * kNB * R) * sizeof(T);
+}
+
+// Forward, one 64-row block of update rows of a front:
+//   W(rows) = w(rows) - L21(rows, :) x1,
+// x1 = the front's solved pivots (in Y), staged in chunks of kGemvStage / R
+// columns.  Thread (row, g) takes columns g, g + 4, ...; a warp reads 32
+// consecutive rows of one column.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_fw_gemv(SD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sx = reinterpret_cast<T*>(smem_raw);  // sx[j * R + r]
+  T* red = sx + kGemvStage;                // red[(g * kNB + row) * R + r]
+  constexpr int CH = kGemvStage / R;
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
+  const int r0 = it.a, rows = it.b;
+  const int tid = threadIdx.x, row = tid & 63, g = tid >> 6;
+  const bool live = row < rows;
+  const T* Lr = d.L + f.Loff + r0 + (live ? row : 0);
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = T(0);
+  for (int j0 = 0; j0 < k; j0 += CH) {
+    const int cl = min(CH, k - j0);
+    __syncthreads();
+    for (int idx = tid; idx < cl * nrhs; idx += blockDim.x) {
+      const int j = idx % cl, r = idx / cl;
+      sx[j * R + r] = d.Y[(int64_t)r * d.n + f.first + j0 + j];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int j = g; j < cl; j += 4) {
+      const T l = Lr[(int64_t)(j0 + j) * nf];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (r < nrhs) acc[r] = fma(l, sx[j * R + r], acc[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r < nrhs) red[(g * kNB + row) * R + r] = acc[r];
+  __syncthreads();
+  for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
+    const int rw = idx / nrhs, r = idx % nrhs;
+    const int i = r0 + rw;
+    T w = T(0);
+    const int64_t gi = f.woff + i;
+    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e)
+      w += d.W[d.ginv_src[e] * nrhs + r];
+    const T sum = red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
+                  red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
+    d.W[gi * nrhs + r] = w - sum;
+  }
+}
+
+// Backward, one 64-column block [c0, c0 + bs) of a front:
+//   y(c0 + c) -= L21(:, c0 + c)^T x2,
+// x2 = the final x of the front's update rows (ancestors), staged in chunks
+// of kGemvStage / R rows.  Each warp streams CW columns at a time, lanes
+// along the rows (coalesced), and reduces each column with a warp sum.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_bw_gemv(SD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[i * R + r]
+  T* part = xs + kGemvStage;               // part[c * R + r]
+  constexpr int CH = kGemvStage / R;
+  constexpr int CW = R == 1 ? 8 : (R <= 8 ? 2 : 1);
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, m = f.m, nf = k + m, nrhs = d.nrhs;
+  const int c0 = it.a, bs = it.b;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* Lp = d.L + f.Loff;
+  const int32_t* frow = d.rowidx + f.rows_off + k;
+  for (int idx = tid; idx < kNB * R; idx += blockDim.x) part[idx] = T(0);
+  for (int i0 = 0; i0 < m; i0 += CH) {
+    const int ch = min(CH, m - i0);
+    __syncthreads();
+    for (int idx = tid; idx < ch * nrhs; idx += blockDim.x) {
+      const int i = idx % ch, r = idx / ch;
+      xs[i * R + r] = d.Y[(int64_t)r * d.n + frow[i0 + i]];
+    }
+    __syncthreads();
+    for (int cb = warp * CW; cb < bs; cb += 8 * CW) {
+      T a[CW][R];
+#pragma unroll
+      for (int q = 0; q < CW; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) a[q][r] = T(0);
+      const T* Lc = Lp + (int64_t)(c0 + cb) * nf + k + i0;
+#pragma unroll 2
+      for (int i = lane; i < ch; i += 32) {
+        T l[CW];
+#pragma unroll
+        for (int q = 0; q < CW; ++q) l[q] = cb + q < bs ? Lc[(int64_t)q * nf + i] : T(0);
+#pragma unroll
+        for (int q = 0; q < CW; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (r < nrhs) a[q][r] = fma(l[q], xs[i * R + r], a[q][r]);
+      }
+#pragma unroll
+      for (int q = 0; q < CW; ++q)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (r < nrhs) {
+            const T sum = warp_sum(a[q][r]);
+            if (lane == 0 && cb + q < bs) part[(cb + q) * R + r] += sum;
+          }
+        }
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < bs * nrhs; idx += blockDim.x) {
+    const int c = idx / nrhs, r = idx % nrhs;
+    d.Y[(int64_t)r * d.n + f.first + c0 + c] -= part[c * R + r];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -686,6 +818,12 @@ __global__ void __launch_bounds__(256, 2) k_bw_warp(SD<T> d, int64_t item_off, i
   }
 }
 
+// Diagnostic: the solve's bounded wait on a flag that nothing sets.  Gives
+// up after `limit` polls and records MF_ERR_TIMEOUT in status[1].
+__global__ void k_wait_probe(const int* flag, unsigned long long* status, int limit) {
+  cta_wait(flag, status, limit);
+}
+
 // ---------------------------------------------------------------------------
 // Permutations and FP64 residual kernels.
 // ---------------------------------------------------------------------------
@@ -759,9 +897,16 @@ template <typename T, int R>
 cudaError_t init_r() {
   cudaError_t e = cudaFuncSetAttribute(k_fw_level<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)fw_level_smem<T, R>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_bw_level<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bw_level_smem<T, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bw_level<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bw_level_smem<T, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fw_gemv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gemv_smem<T, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_bw_gemv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gemv_smem<T, R>());
+  return e;
 }
 
 template <typename T>
@@ -775,12 +920,16 @@ cudaError_t init_t() {
 template <typename T, int R>
 void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   const SD<T> d = make_sd<T>(a);
-  if (L.kind == K_FW_LEVEL)  // param 1: update-row blocks, all pivots done
+  if (L.kind == K_FW_LEVEL)
     k_fw_level<T, R><<<L.count, 256, fw_level_smem<T, R>(), st>>>(
-        d, L.item_off, L.param ? nullptr : a.sync + 2 * L.level, a.sync + 2 * a.nlevels);
-  else
+        d, L.item_off, a.sync + 2 * L.level, a.sync + 2 * a.nlevels);
+  else if (L.kind == K_BW_LEVEL)  // param 1: k_bw_gemv did the update rows
     k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(
-        d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
+        d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk, L.param);
+  else if (L.kind == K_FW_GEMV)
+    k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
+  else
+    k_bw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
 }
 
 template <typename T, int H>
@@ -809,7 +958,8 @@ cudaError_t launch_t(const Launch& L, const SolveArgs& a, cudaStream_t st) {
     }
     return cudaGetLastError();
   }
-  if (L.kind != K_FW_LEVEL && L.kind != K_BW_LEVEL) return cudaErrorInvalidValue;
+  if (L.kind != K_FW_LEVEL && L.kind != K_BW_LEVEL && L.kind != K_FW_GEMV && L.kind != K_BW_GEMV)
+    return cudaErrorInvalidValue;
   if (a.nrhs <= 1) launch_r<T, 1>(L, a, st);
   else if (a.nrhs <= 8) launch_r<T, 8>(L, a, st);
   else launch_r<T, kSolveChunk>(L, a, st);
@@ -826,6 +976,12 @@ int grid_for(int64_t total) {
 
 cudaError_t solve_kernels_init(int prec) {
   return prec == MF_FP32 ? init_t<float>() : init_t<double>();
+}
+
+cudaError_t launch_wait_probe(const int* flag, unsigned long long* status, int limit,
+                              cudaStream_t st) {
+  k_wait_probe<<<1, 64, 0, st>>>(flag, status, limit);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStream_t st) {

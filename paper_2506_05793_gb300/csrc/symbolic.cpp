@@ -773,9 +773,9 @@ void build_schedules(mf_symbolic& S, int small_max) {
     flatten(it);
     for (int c = 0; c < 4; ++c) add(S.fwsched, K_FW_WARP, lev, 2 << c, wcls[c], 0.0);
     // pivot blocks (flag chains within a front), then the update-row blocks
-    // of the level, which then never wait
+    // of the level as a streaming product that never waits
     add(S.fwsched, K_FW_LEVEL, lev, 0, it, 0.0);
-    add(S.fwsched, K_FW_LEVEL, lev, 1, upd, 0.0);
+    add(S.fwsched, K_FW_GEMV, lev, 0, upd, 0.0);
   }
   for (int32_t lev = S.nlevels - 1; lev >= 0; --lev) {
     split_level(bylev[lev], wcls, big);
@@ -788,8 +788,14 @@ void build_schedules(mf_symbolic& S, int small_max) {
       }
     }
     flatten(it);
+    upd.clear();
+    for (const Item& x : it)
+      if (S.sn[x.s].m > 0) upd.push_back(x);
     for (int c = 0; c < 4; ++c) add(S.bwsched, K_BW_WARP, lev, 2 << c, wcls[c], 0.0);
-    add(S.bwsched, K_BW_LEVEL, lev, 0, it, 0.0);
+    // update-row products of every column block first (no waiting), then the
+    // flag-chained triangles
+    add(S.bwsched, K_BW_GEMV, lev, 0, upd, 0.0);
+    add(S.bwsched, K_BW_LEVEL, lev, 1, it, 0.0);
   }
 }
 
