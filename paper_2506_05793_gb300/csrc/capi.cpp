@@ -126,6 +126,7 @@ struct mf_factor {
   int32_t* sync = nullptr;  // solve ticket counters and block flags
   bool tc = false;          // FP32 trailing updates on tcgen05 tensor cores
   float* split = nullptr;   // tf32 hi/lo staging rows of the panels
+  alignas(128) unsigned char split_map[128];  // TMA tensor map over split
   void* dinv = nullptr;     // inverses of the current diagonal blocks (scratch)
   void* av = nullptr;       // lower entries of C in assembly order (T)
   double* small = nullptr;  // per-RHS scalars for refinement
@@ -381,7 +382,12 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   if (prec == MF_FP32 && h->opt.tc) {
     F->tc = true;
     MF_CK(mf::factor_tc_init());
-    MF_CK(cudaMalloc(&F->split, std::max<int64_t>(s->split_rows, 1) * 128 * sizeof(float)));
+    const int64_t srows = std::max<int64_t>(s->split_rows, 1);
+    MF_CK(cudaMalloc(&F->split, srows * 128 * sizeof(float)));
+    // rows past a front are read (and discarded) by the tile kernel: keep
+    // them finite
+    MF_CK(cudaMemset(F->split, 0, srows * 128 * sizeof(float)));
+    MF_CK(mf::make_split_map(F->split, srows, F->split_map));
   }
   *f = F.release();
   return MF_OK;
@@ -396,6 +402,7 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile) {
   a.U = F->U;
   a.status = F->status;
   a.split = F->tc ? F->split : nullptr;
+  a.split_map = F->tc ? F->split_map : nullptr;
   a.dinv = F->dinv;
   a.av = F->av;
   const std::vector<mf::Launch>& sched = F->tc ? S->fsched_tc : S->fsched;

@@ -207,221 +207,92 @@ __device__ __forceinline__ void load_diag_block(const FD<T>& d, const SnInfo& f,
 }
 
 // ---------------------------------------------------------------------------
-// One warp: Cholesky and inverse of the 32 x 32 lower block at D (column-major,
-// leading dimension ld) entirely in registers.  Lane i keeps row i of the
-// block; the rank-1 updates and the substitution for the inverse take the
-// other rows' values by shuffles.  L overwrites D (upper part zero), the
-// inverse goes to Y (same layout).  Pivots beyond `nvalid` are padding.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __noinline__ void warp_chol_inv32(T* D, T* Y, int ld, int nvalid, int64_t col0,
-                                             unsigned long long* status) {
-  constexpr unsigned full = 0xffffffffu;
-  const int i = threadIdx.x & 31;
-  T r[32];
-  T myinv = T(0);  // 1 / L(i, i), kept for the inverse
-#pragma unroll
-  for (int c = 0; c < 32; ++c) r[c] = i >= c ? D[c * ld + i] : T(0);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const T piv = __shfl_sync(full, r[j], j);
-    if (i == 0 && j < nvalid && !(piv > T(0))) atomicMin(status, (unsigned long long)(col0 + j));
-    const T ljj = dsqrt(piv);
-    const T rinv = T(1) / ljj;
-    if (i == j) myinv = rinv;
-    r[j] = i == j ? ljj : (i > j ? r[j] * rinv : T(0));
-#pragma unroll
-    for (int c = j + 1; c < 32; ++c) {
-      const T lc = __shfl_sync(full, r[j], c);
-      if (i >= c) r[c] = fma(-r[j], lc, r[c]);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 32; ++c) D[c * ld + i] = r[c];
-  // inverse: lane i solves L y = e_i (column i of L^{-1})
-  T y[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    T s = k == i ? T(1) : T(0);
-#pragma unroll
-    for (int m = 0; m < k; ++m) s = fma(-__shfl_sync(full, r[m], k), y[m], s);
-    y[k] = s * __shfl_sync(full, myinv, k);
-  }
-#pragma unroll
-  for (int k = 0; k < 32; ++k) Y[i * ld + k] = y[k];
-}
-
-// ---------------------------------------------------------------------------
-// Large fronts, panel step t: Cholesky of the b x b diagonal block and the
-// inverse of its factor, as 2 x 2 blocks of 32 (128 threads):
-//   warp 0: L11, Y11 = L11^{-1}      all: L21 = A21 Y11^T
-//   all:    A22 -= L21 L21^T         warp 0: L22, Y22 = L22^{-1}
-//   all:    Y21 = -Y22 (L21 Y11)
-// A block with b < 64 is padded with the identity, so its factor and inverse
-// are padded the same way.  The inverse goes to the scratch dinv (64 x 64,
-// column-major, slot = position of the front in its level, item field b).
-// ---------------------------------------------------------------------------
-template <typename T>
-constexpr size_t potrf_blk_smem() {
-  return (size_t)(2 * kNB * (kNB + 1) + 32 * 33) * sizeof(T);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(128) k_potrf_blk(FD<T> d, int64_t item_off) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int ld = kNB + 1;
-  T* D = reinterpret_cast<T*>(smem_raw);  // D[c * ld + i] = A(i, c), then L(i, c)
-  T* Y = D + kNB * ld;                    // Y[c * ld + i] = L^{-1}(i, c)
-  T* Tm = Y + kNB * ld;                   // Tm[c * 33 + i] = (L21 Y11)(32 + i, c)
-  const Item it = d.items[item_off + blockIdx.x];
-  const SnInfo f = d.sn[it.s];
-  const int c0 = it.t * kNB;
-  const int b = min(kNB, f.k - c0);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_diag_block<T, 128>(d, f, c0, b, D, ld);
-  for (int idx = tid; idx < kNB * ld; idx += blockDim.x) Y[idx] = T(0);
-  __syncthreads();
-  if (warp == 0) warp_chol_inv32(D, Y, ld, min(b, 32), f.first + c0, d.status);
-  __syncthreads();
-  const int i2 = 32 + lane;  // row of the lower block rows handled by this thread
-  {
-    // L21(i, c) = sum_{k <= c} A21(i, k) Y11(c, k); c = warp + 4 q
-    T x[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = warp + 4 * q;
-      T s = T(0);
-      for (int k = 0; k <= c; ++k) s = fma(D[k * ld + i2], Y[k * ld + c], s);
-      x[q] = s;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 8; ++q) D[(warp + 4 * q) * ld + i2] = x[q];
-  }
-  __syncthreads();
-  // A22 -= L21 L21^T (lower), c = 32 + warp + 4 q
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = 32 + warp + 4 * q;
-    if (i2 >= c) {
-      T s = D[c * ld + i2];
-      for (int k = 0; k < 32; ++k) s = fma(-D[k * ld + i2], D[k * ld + c], s);
-      D[c * ld + i2] = s;
-    }
-  }
-  __syncthreads();
-  if (warp == 0)
-    warp_chol_inv32(D + 32 * ld + 32, Y + 32 * ld + 32, ld, max(0, min(b - 32, 32)),
-                    f.first + c0 + 32, d.status);
-  __syncthreads();
-  // Tm = L21 Y11: Tm(i, c) = sum_{k >= c} L21(i, k) Y11(k, c)
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = warp + 4 * q;
-    T s = T(0);
-    for (int k = c; k < 32; ++k) s = fma(D[k * ld + i2], Y[c * ld + k], s);
-    Tm[c * 33 + lane] = s;
-  }
-  __syncthreads();
-  // Y21 = -Y22 Tm: Y21(i, c) = -sum_{m <= i} Y22(i, m) Tm(m, c)
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int c = warp + 4 * q;
-    T s = T(0);
-    for (int m = 0; m <= lane; ++m) s = fma(Y[(32 + m) * ld + i2], Tm[c * 33 + m], s);
-    Y[c * ld + i2] = -s;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < b * b; idx += blockDim.x) {
-    const int c = idx / b, i = idx % b;
-    if (i >= c) front_col(d, f, c0 + c)[c0 + i] = D[c * ld + i];
-  }
-  T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
-  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
-    const int c = idx / kNB, i = idx % kNB;
-    Dv[c * kNB + i] = Y[c * ld + i];
-  }
-}
-
-// ---------------------------------------------------------------------------
-// FP64 variant of the diagonal-block kernel (256 threads): the block sits in
-// shared memory; per column one thread takes the square root and reciprocal
-// (FP64 square root and division are costly on this part); the trailing
-// update walks a table of the lower triangle ordered by column from the
-// right, so at column j its first (63 - j)(64 - j) / 2 entries are the live
-// elements and the FMAs spread over all four FP64 pipes of the SM.  The
-// inverse is formed the same way, right-looking by rows.
+// Large fronts, panel step t: Cholesky factor and inverse of the b x b
+// diagonal block (b <= 64, padded with the identity to 64 x 64), one CTA of
+// 256 threads per front, compact loops (the kernel runs once per panel step
+// on the critical path, so its code must stay small enough to fetch fast).
+//
+// Factor, right-looking in the L D L^T form: at step j every thread reads the
+// pivot d_j = D(j, j) and, for its row i > j, updates
+//   D(i, c) -= D(i, j) D(c, j) / d_j        for j < c <= i,
+// one barrier per step (column j itself is not modified in step j).  Then
+// L(j, j) = sqrt(d_j) and L(i, j) = D(i, j) / sqrt(d_j).
+// Inverse: thread c solves L y = e_c by substitution (independent columns,
+// no barriers), y(i) = -(sum_{c <= k < i} L(i, k) y(k)) / L(i, i).
 // ---------------------------------------------------------------------------
 template <typename T>
 constexpr size_t potrf_smem() {
-  return (size_t)2 * kNB * (kNB + 1) * sizeof(T) + kNB * (kNB + 1) / 2 * sizeof(uint16_t);
+  return ((size_t)2 * kNB * (kNB + 1) + 2 * kNB) * sizeof(T);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*D)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // A(i, c), then L(i, c)
-  T(*Y)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));
-  // lower-triangle entries (i << 8 | c), columns 63, 62, ...
-  uint16_t* tri = reinterpret_cast<uint16_t*>(smem_raw + (size_t)2 * kNB * (kNB + 1) * sizeof(T));
-  __shared__ T s_r;
+  constexpr int ld = kNB + 1;
+  T* D = reinterpret_cast<T*>(smem_raw);  // D[c * ld + i] = A(i, c), then L(i, c)
+  T* Y = D + kNB * ld;                    // Y[c * ld + i] = L^{-1}(i, c)
+  T* sq = Y + kNB * ld;                   // sqrt(d_c)
+  T* rsq = sq + kNB;                      // 1 / sqrt(d_c)
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int c0 = it.t * kNB;
   const int b = min(kNB, f.k - c0);
-  const int tid = threadIdx.x;
-  load_diag_block<T, 256>(d, f, c0, b, &D[0][0], kNB + 1);
-  for (int e = tid; e < kNB * (kNB + 1) / 2; e += blockDim.x) {
-    int m = 1;  // column c = 64 - m holds m elements
-    while ((m * (m + 1)) / 2 <= e) ++m;
-    const int c = kNB - m, o = e - (m * (m - 1)) / 2;
-    tri[e] = (uint16_t)(((c + o) << 8) | c);
+  const int tid = threadIdx.x, lane = tid & 31;
+  load_diag_block<T, 256>(d, f, c0, b, D, ld);
+  for (int idx = tid; idx < kNB * ld; idx += blockDim.x) Y[idx] = T(0);
+  __syncthreads();
+  const int i = tid & (kNB - 1), q = tid >> 6;
+  for (int j = 0; j < kNB; ++j) {
+    const T piv = D[j * ld + j];
+    if (tid == 0 && j < b && !(piv > T(0)))
+      atomicMin(d.status, (unsigned long long)(f.first + c0 + j));
+    T rp = T(0);
+    if (lane == 0) rp = T(1) / piv;
+    rp = __shfl_sync(0xffffffffu, rp, 0);
+    if (i > j) {
+      const T lij = D[j * ld + i] * rp;
+      for (int c = j + 1 + q; c <= i; c += 4) D[c * ld + i] = fma(-lij, D[j * ld + c], D[c * ld + i]);
+    }
+    __syncthreads();
   }
-  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
-    const int c = idx / kNB, i = idx % kNB;
-    Y[c][i] = (i == c) ? T(1) : T(0);
+  if (tid < kNB) {
+    const T s = dsqrt(D[tid * ld + tid]);
+    sq[tid] = s;
+    rsq[tid] = T(1) / s;
   }
   __syncthreads();
-  for (int j = 0; j < kNB; ++j) {
-    if (tid == 0) {
-      const T piv = D[j][j];
-      if (j < b && !(piv > T(0))) atomicMin(d.status, (unsigned long long)(f.first + c0 + j));
-      const T ljj = dsqrt(piv);
-      D[j][j] = ljj;
-      s_r = T(1) / ljj;
-    }
-    __syncthreads();
-    const T r = s_r;
-    for (int i = j + 1 + tid; i < kNB; i += blockDim.x) D[j][i] *= r;
-    __syncthreads();
-    const int live = ((kNB - 1 - j) * (kNB - j)) / 2;
-    for (int e = tid; e < live; e += blockDim.x) {
-      const int ic = tri[e], i = ic >> 8, c = ic & 255;
-      D[c][i] = fma(-D[j][i], D[j][c], D[c][i]);
-    }
-    __syncthreads();
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, r = idx % kNB;
+    if (r > c) D[c * ld + r] *= rsq[c];
+    else if (r == c) D[c * ld + r] = sq[c];
   }
+  __syncthreads();
+  if (tid < kNB) {
+    const int c = tid;
+    T* yc = Y + c * ld;
+    yc[c] = rsq[c];
+    for (int r = c + 1; r < kNB; ++r) {
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+      int k = c;
+      for (; k + 3 < r; k += 4) {
+        s0 = fma(D[k * ld + r], yc[k], s0);
+        s1 = fma(D[(k + 1) * ld + r], yc[k + 1], s1);
+        s2 = fma(D[(k + 2) * ld + r], yc[k + 2], s2);
+        s3 = fma(D[(k + 3) * ld + r], yc[k + 3], s3);
+      }
+      for (; k < r; ++k) s0 = fma(D[k * ld + r], yc[k], s0);
+      yc[r] = -((s0 + s1) + (s2 + s3)) * rsq[r];
+    }
+  }
+  __syncthreads();
   for (int idx = tid; idx < b * b; idx += blockDim.x) {
-    const int c = idx / b, i = idx % b;
-    if (i >= c) front_col(d, f, c0 + c)[c0 + i] = D[c][i];
-  }
-  for (int p = 0; p < kNB; ++p) {
-    if (tid == 0) s_r = T(1) / D[p][p];
-    __syncthreads();
-    const T r = s_r;
-    for (int c = tid; c <= p; c += blockDim.x) Y[c][p] *= r;
-    __syncthreads();
-    const int w = p + 1, cnt = (kNB - 1 - p) * w;
-    for (int e = tid; e < cnt; e += blockDim.x) {
-      const int i = p + 1 + e / w, c = e % w;
-      Y[c][i] = fma(-D[p][i], Y[c][p], Y[c][i]);
-    }
-    __syncthreads();
+    const int c = idx / b, r = idx % b;
+    if (r >= c) front_col(d, f, c0 + c)[c0 + r] = D[c * ld + r];
   }
   T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
   for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
-    const int c = idx / kNB, i = idx % kNB;
-    Dv[c * kNB + i] = Y[c][i];
+    const int c = idx / kNB, r = idx % kNB;
+    Dv[c * kNB + r] = Y[c * ld + r];
   }
 }
 
@@ -603,9 +474,6 @@ cudaError_t init_t() {
   e = cudaFuncSetAttribute(k_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)potrf_smem<T>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_potrf_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)potrf_blk_smem<T>());
-  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)syrk_smem<T>());
 }
@@ -622,10 +490,7 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
       k_assemble<T><<<grid, 256, 0, st>>>(d, L.item_off);
       break;
     case K_POTRF:
-      if constexpr (sizeof(T) == 4)
-        k_potrf_blk<T><<<grid, 128, potrf_blk_smem<T>(), st>>>(d, L.item_off);
-      else
-        k_potrf<T><<<grid, 256, potrf_smem<T>(), st>>>(d, L.item_off);
+      k_potrf<T><<<grid, 256, potrf_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_TRSM:
       k_trsm<T><<<grid, 256, trsm_smem<T>(), st>>>(d, L.item_off);

@@ -11,18 +11,22 @@
 //
 // One CTA (128 threads) computes one 128 x 128 tile (I, J), I >= J:
 //   - the 64-wide K range is staged in two halves of 32 through one 64 KB
-//     shared-memory buffer (so three CTAs fit on an SM and overlap); each half
-//     is copied with cp.async in the canonical K-major 128-byte-swizzle layout
-//     (8-row atoms of 8 x 16-byte units, unit u of row r stored at u ^ (r & 7));
+//     shared-memory buffer (so three CTAs fit on an SM and overlap); one thread
+//     copies each half with TMA (a tensor map over the staging buffer, boxes
+//     of 128 rows x 32 floats with 128-byte swizzle), which writes the
+//     canonical K-major layout the MMA descriptors expect (8-row atoms of
+//     8 x 16-byte units, unit u of row r stored at u ^ (r & 7));
 //   - one elected thread issues 12 tcgen05.mma per half (3 products x 4
 //     k-steps of 8) into a 128 x 128 FP32 accumulator in tensor memory and
 //     commits them to an mbarrier (phase 0, then phase 1);
 //   - after a bounded wait, each warp reads its 32 accumulator lanes with
 //     tcgen05.ld and subtracts them from the lower part of the tile in HBM,
 //     loading the next 32 columns' old values before storing the current.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "kernels.h"
 
@@ -56,23 +60,21 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes)
-               : "memory");
+
+// TMA copy of one 128-row x 32-float box of the staging buffer (element
+// column x, row y) into shared memory at dst; completion is counted on mbar.
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* map, int x, int64_t y,
+                                        uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"((int)y), "r"(mbar)
+      : "memory");
 }
 
-// Copy K-half h (k in [32 h, 32 h + 32)) of 128 staging rows (row R0 + r) into
-// the swizzled hi and lo chunks; rows at or beyond `valid` are zero-filled.
-__device__ __forceinline__ void load_half(const float* split, int64_t R0, int valid, int h,
-                                          uint32_t hi_base, uint32_t lo_base) {
-  for (int idx = threadIdx.x; idx < 128 * 16; idx += blockDim.x) {
-    const int r = idx >> 4, U = idx & 15;
-    const int part = U >> 3, u = U & 7;
-    const uint32_t dst = (part ? lo_base : hi_base) + r * 128 + ((u ^ (r & 7)) << 4);
-    const bool ok = r < valid;
-    const float* src = split + (ok ? (R0 + r) * 128 + part * 64 + h * 32 + u * 4 : 0);
-    cp_async16(dst, src, ok ? 16 : 0);
-  }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+               : "memory");
 }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
@@ -108,15 +110,19 @@ struct TcArgs {
   unsigned long long* status;
 };
 
-__global__ void __launch_bounds__(128, 3) k_syrk_tc(TcArgs<float> d, int64_t item_off) {
+__global__ void __launch_bounds__(128, 3)
+    k_syrk_tc(TcArgs<float> d, const __grid_constant__ CUtensorMap smap, int64_t item_off) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned operand chunks: A hi, A lo, B hi, B lo (one K-half each)
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
   unsigned char* gbase = smem_raw + (sbase - smem_u32(smem_raw));
   const uint32_t a_hi = sbase, a_lo = sbase + kOpBytes;
   const uint32_t b_hi = sbase + 2 * kOpBytes, b_lo = sbase + 3 * kOpBytes;
+  // one single-use barrier per event (TMA of half 0 / 1, MMAs of half 0 / 1),
+  // each waited once on phase 0: a thread that reaches its wait late can
+  // never mistake a later phase for the one it waits for
   uint64_t* mbar = reinterpret_cast<uint64_t*>(gbase + 4 * kOpBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + 4 * kOpBytes + 8);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + 4 * kOpBytes + 32);
 
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(TcArgs<float> d, int64_t ite
   const bool diag = it.a == it.b;
   const int64_t R0 = d.soff[it.s];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t mb = smem_u32(mbar);
+  const uint32_t mb0 = smem_u32(mbar);  // + 8 h: MMAs of half h; + 16 + 8 h: TMA of half h
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -138,21 +144,86 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(TcArgs<float> d, int64_t ite
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+    for (int q = 0; q < 4; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0 + 8 * q) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int i = warp * 32 + lane;  // accumulator lane = row of the tile
+  const int r = rI + i;
+  const bool rowok = r < nf;
+  // element (r, c) of the front: L panel for c < k, update matrix beyond.
+  // Per 32-column chunk one base pointer and a column stride; a chunk that
+  // straddles k takes the per-column path.
+  auto col_ptr = [&](int c) -> float* {
+    if (c < f.k) return d.L + f.Loff + (int64_t)c * nf + r;
+    return d.U + f.Uoff + (int64_t)(c - f.k) * f.m + (r - f.k);
+  };
+  auto chunk_load = [&](int cbase, float (&out)[32]) {
+    const int lim = rowok ? min(min(32, nf - cbase), r - cbase + 1) : 0;  // valid j < lim
+    if (cbase + 32 <= f.k || cbase >= f.k) {
+      const bool inL = cbase < f.k;
+      const int64_t ld = inL ? nf : f.m;
+      const float* p = inL ? d.L + f.Loff + (int64_t)cbase * nf + r
+                           : d.U + f.Uoff + (int64_t)(cbase - f.k) * f.m + (r - f.k);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[j] = j < lim ? p[j * ld] : 0.0f;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[j] = j < lim ? *col_ptr(cbase + j) : 0.0f;
+    }
+  };
+  auto chunk_store = [&](int cbase, const float (&cur)[32], const uint32_t (&v)[32]) {
+    const int lim = rowok ? min(min(32, nf - cbase), r - cbase + 1) : 0;
+    if (cbase + 32 <= f.k || cbase >= f.k) {
+      const bool inL = cbase < f.k;
+      const int64_t ld = inL ? nf : f.m;
+      float* p = inL ? d.L + f.Loff + (int64_t)cbase * nf + r
+                     : d.U + f.Uoff + (int64_t)(cbase - f.k) * f.m + (r - f.k);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < lim) p[j * ld] = cur[j] - __uint_as_float(v[j]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < lim) *col_ptr(cbase + j) = cur[j] - __uint_as_float(v[j]);
+    }
+  };
+  // the tile of C goes to L2 while the operands load and multiply: thread t
+  // prefetches the rows of column rJ + t that the epilogue will touch
+  {
+    const int c = rJ + tid;
+    const int lo = max(rI, c), hi = min(rI + kTcM, nf);
+    if (c < nf && lo < hi) {
+      const float* p = c < f.k ? d.L + f.Loff + (int64_t)c * nf + lo
+                               : d.U + f.Uoff + (int64_t)(c - f.k) * f.m + (lo - f.k);
+      for (int o = 0; o < hi - lo; o += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + o));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p + (hi - lo - 1)));
+    }
+  }
+  float cur[32];
+  chunk_load(rJ, cur);
   const uint32_t bh = diag ? a_hi : b_hi, bl = diag ? a_lo : b_lo;
   bool ok = true;
-  uint32_t tmem = 0;
   for (int h = 0; h < 2; ++h) {
-    load_half(d.split, R0 + rI, nf - rI, h, a_hi, a_lo);
-    if (!diag) load_half(d.split, R0 + rJ, nf - rJ, h, b_hi, b_lo);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    tmem = *tmem_slot;
+    const uint32_t mb = mb0 + 8 * h, mbt = mb0 + 16 + 8 * h;
+    // rows of the staging buffer beyond the front belong to other fronts (or
+    // are zero); they only reach accumulator rows / columns that the
+    // epilogue discards
+    if (tid == 0) {
+      mbar_expect_tx(mbt, (diag ? 2u : 4u) * (uint32_t)kOpBytes);
+      tma_box(a_hi, &smap, h * 32, R0 + rI, mbt);
+      tma_box(a_lo, &smap, 64 + h * 32, R0 + rI, mbt);
+      if (!diag) {
+        tma_box(b_hi, &smap, h * 32, R0 + rJ, mbt);
+        tma_box(b_lo, &smap, 64 + h * 32, R0 + rJ, mbt);
+      }
+    }
+    ok = ok && mbar_wait(mbt, 0u);
+    if (!ok) break;
     if (tid == 0) {
       // small terms first: lo*hi, hi*lo, then hi*hi; 4 k-steps of 8 each
       const uint32_t as[3] = {a_lo, a_hi, a_hi};
@@ -167,28 +238,16 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(TcArgs<float> d, int64_t ite
     }
     // the MMAs of this half must finish reading shared memory (and, for the
     // second half, writing the accumulator) before anyone goes on
-    ok = ok && mbar_wait(mb, (uint32_t)h);
+    ok = ok && mbar_wait(mb, 0u);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (!ok) break;
   }
   if (!ok) {
     if (lane == 0) atomicExch(d.status + 1, (unsigned long long)MF_ERR_TIMEOUT);
   } else {
-    const int i = warp * 32 + lane;  // accumulator lane = row of the tile
-    const int r = rI + i;
-    const bool rowok = r < nf;
-    // element (r, c) of the front: L panel for c < k, update matrix beyond
-    auto addr = [&](int c) -> float* {
-      if (c < f.k) return d.L + f.Loff + (int64_t)c * nf + r;
-      return d.U + (f.Uoff + (int64_t)(c - f.k) * f.m + (r - f.k));
-    };
-    float cur[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int c = rJ + j;
-      cur[j] = (rowok && c < nf && r >= c) ? *addr(c) : 0.0f;
-    }
     for (int cb = 0; cb < kTcN / 32; ++cb) {
+      const int cbase = rJ + cb * 32;
+      if (cbase >= nf) break;  // same for the whole CTA
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32);
       asm volatile(
@@ -204,17 +263,9 @@ __global__ void __launch_bounds__(128, 3) k_syrk_tc(TcArgs<float> d, int64_t ite
           : "memory");
       // the next chunk's old values are loaded before this chunk is stored
       float nxt[32];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = rJ + (cb + 1) * 32 + j;
-        nxt[j] = (cb < 3 && rowok && c < nf && r >= c) ? *addr(c) : 0.0f;
-      }
+      if (cb + 1 < kTcN / 32 && cbase + 32 < nf) chunk_load(cbase + 32, nxt);
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = rJ + cb * 32 + j;
-        if (rowok && c < nf && r >= c) *addr(c) = cur[j] - __uint_as_float(v[j]);
-      }
+      chunk_store(cbase, cur, v);
 #pragma unroll
       for (int j = 0; j < 32; ++j) cur[j] = nxt[j];
     }
@@ -235,8 +286,39 @@ cudaError_t factor_tc_init() {
   return cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
 }
 
+cudaError_t make_split_map(float* split, int64_t rows, void* map_out) {
+  typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<EncodeFn>(fn);
+  }
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {128, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {128 * sizeof(float)};
+  const cuuint32_t box[2] = {32, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, split, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  std::memcpy(map_out, &m, sizeof(m));
+  return cudaSuccess;
+}
+
 cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st) {
   if (L.count <= 0) return cudaSuccess;
+  if (!a.split_map) return cudaErrorInvalidValue;
+  CUtensorMap m;
+  std::memcpy(&m, a.split_map, sizeof(m));
   TcArgs<float> d;
   d.sn = a.sym.sn;
   d.items = a.sym.items;
@@ -245,7 +327,7 @@ cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st
   d.L = static_cast<float*>(a.L);
   d.U = static_cast<float*>(a.U);
   d.status = a.status;
-  k_syrk_tc<<<L.count, 128, kTcSmem, st>>>(d, L.item_off);
+  k_syrk_tc<<<L.count, 128, kTcSmem, st>>>(d, m, L.item_off);
   return cudaGetLastError();
 }
 
