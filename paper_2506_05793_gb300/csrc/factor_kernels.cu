@@ -209,90 +209,184 @@ __device__ __forceinline__ void load_diag_block(const FD<T>& d, const SnInfo& f,
 // ---------------------------------------------------------------------------
 // Large fronts, panel step t: Cholesky factor and inverse of the b x b
 // diagonal block (b <= 64, padded with the identity to 64 x 64), one CTA of
-// 256 threads per front, compact loops (the kernel runs once per panel step
-// on the critical path, so its code must stay small enough to fetch fast).
+// 256 threads per front.  The kernel sits on the critical path of every
+// panel step, so it is blocked for few barriers, keeps every warp's work
+// uniform (an FP64 warp instruction costs the same with 1 or 32 lanes
+// active) and is written as compact loops.
 //
-// Factor, right-looking in the L D L^T form: at step j every thread reads the
-// pivot d_j = D(j, j) and, for its row i > j, updates
-//   D(i, c) -= D(i, j) D(c, j) / d_j        for j < c <= i,
-// one barrier per step (column j itself is not modified in step j).  Then
-// L(j, j) = sqrt(d_j) and L(i, j) = D(i, j) / sqrt(d_j).
-// Inverse: thread c solves L y = e_c by substitution (independent columns,
-// no barriers), y(i) = -(sum_{c <= k < i} L(i, k) y(k)) / L(i, i).
+// Factor, by 16-column blocks B (rows/columns j0 .. j0 + 15):
+//   (a) one warp: L_BB = chol(A_BB) and its inverse Y_BB (column
+//       substitution, lane c solves L_BB y = e_c);
+//   (b) rows below: L_iB = A_iB Y_BB^T;
+//   (c) trailing lower part: A_ic -= L_iB L_cB^T (triangle enumerated evenly
+//       over the threads).
+// Inverse: the off-diagonal blocks by distance d = i - j = 1, 2, 3:
+//   Y_ij = -Y_ii (sum_{k=j}^{i-1} L_ik Y_kj).
 // ---------------------------------------------------------------------------
+constexpr int kPB = 16;  // block size inside the diagonal-block kernel
+
 template <typename T>
 constexpr size_t potrf_smem() {
-  return ((size_t)2 * kNB * (kNB + 1) + 2 * kNB) * sizeof(T);
+  return ((size_t)2 * kNB * (kNB + 1) + (size_t)3 * kPB * (kPB + 1)) * sizeof(T);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int ld = kNB + 1;
-  T* D = reinterpret_cast<T*>(smem_raw);  // D[c * ld + i] = A(i, c), then L(i, c)
-  T* Y = D + kNB * ld;                    // Y[c * ld + i] = L^{-1}(i, c)
-  T* sq = Y + kNB * ld;                   // sqrt(d_c)
-  T* rsq = sq + kNB;                      // 1 / sqrt(d_c)
+  constexpr int ld = kNB + 1, tld = kPB + 1;
+  T* D = reinterpret_cast<T*>(smem_raw);  // D[c * ld + r] = A(r, c), then L(r, c)
+  T* Y = D + kNB * ld;                    // Y[c * ld + r] = L^{-1}(r, c)
+  T* Tm = Y + kNB * ld;                   // Tm[(m * kPB + c) * tld + r]: block products
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int c0 = it.t * kNB;
   const int b = min(kNB, f.k - c0);
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   load_diag_block<T, 256>(d, f, c0, b, D, ld);
   for (int idx = tid; idx < kNB * ld; idx += blockDim.x) Y[idx] = T(0);
   __syncthreads();
-  const int i = tid & (kNB - 1), q = tid >> 6;
-  for (int j = 0; j < kNB; ++j) {
-    const T piv = D[j * ld + j];
-    if (tid == 0 && j < b && !(piv > T(0)))
-      atomicMin(d.status, (unsigned long long)(f.first + c0 + j));
-    T rp = T(0);
-    if (lane == 0) rp = T(1) / piv;
-    rp = __shfl_sync(0xffffffffu, rp, 0);
-    if (i > j) {
-      const T lij = D[j * ld + i] * rp;
-      for (int c = j + 1 + q; c <= i; c += 4) D[c * ld + i] = fma(-lij, D[j * ld + c], D[c * ld + i]);
+  for (int j0 = 0; j0 < kNB; j0 += kPB) {
+    // (a) diagonal block: lane r < 16 owns row j0 + r
+    if (warp == 0) {
+      const int r = lane;
+      for (int t = 0; t < kPB; ++t) {
+        T* col = D + (j0 + t) * ld + j0;
+        const T piv = col[t];
+        if (r == 0 && j0 + t < b && !(piv > T(0)))
+          atomicMin(d.status, (unsigned long long)(f.first + c0 + j0 + t));
+        const T ljj = dsqrt(piv);
+        const T rinv = T(1) / ljj;
+        __syncwarp();  // the pivot has been read
+        if (r == t) col[t] = ljj;
+        else if (r > t && r < kPB) col[r] *= rinv;  // each lane scales its own entry
+        __syncwarp();
+        if (r > t && r < kPB) {
+          // all loads first (fixed trip count, so they issue together)
+          const T lr = col[r];
+          T lc[kPB], dv[kPB];
+#pragma unroll
+          for (int c = 0; c < kPB; ++c) {
+            lc[c] = col[c];
+            dv[c] = D[(j0 + c) * ld + j0 + r];
+          }
+#pragma unroll
+          for (int c = 0; c < kPB; ++c)
+            if (c > t && c <= r) D[(j0 + c) * ld + j0 + r] = fma(-lr, lc[c], dv[c]);
+        }
+        __syncwarp();
+      }
+      // inverse of L_BB: lane c < 16 solves L_BB y = e_c, right-looking with
+      // y in registers; the reciprocals of the diagonal are computed once
+      const T rdl = T(1) / D[(j0 + (lane & (kPB - 1))) * ld + j0 + (lane & (kPB - 1))];
+      const int c = lane & (kPB - 1);
+      T acc[kPB], y[kPB];
+#pragma unroll
+      for (int q = 0; q < kPB; ++q) acc[q] = T(0);
+#pragma unroll
+      for (int q = 0; q < kPB; ++q) {
+        const T rq = __shfl_sync(0xffffffffu, rdl, q);
+        y[q] = q < c ? T(0) : ((q == c ? T(1) : T(0)) + acc[q]) * rq;
+#pragma unroll
+        for (int q2 = q + 1; q2 < kPB; ++q2) acc[q2] = fma(-D[(j0 + q) * ld + j0 + q2], y[q], acc[q2]);
+      }
+      if (lane < kPB) {
+#pragma unroll
+        for (int q = 0; q < kPB; ++q) Y[(j0 + c) * ld + j0 + q] = y[q];
+      }
+    }
+    __syncthreads();
+    const int base = j0 + kPB, n2 = kNB - base;
+    if (n2 == 0) break;
+    // (b) L_iB = A_iB Y_BB^T for rows i >= base: element e -> (i, t)
+    {
+      T v[3];
+      for (int q = 0; q < 3; ++q) {
+        const int e = tid + q * 256;
+        v[q] = T(0);
+        if (e < n2 * kPB) {
+          const int i = base + e / kPB, t = e % kPB;
+          T av[kPB], yv[kPB];
+#pragma unroll
+          for (int k = 0; k < kPB; ++k) {
+            av[k] = D[(j0 + k) * ld + i];
+            yv[k] = Y[(j0 + k) * ld + j0 + t];  // zero for k > t
+          }
+          T s = T(0);
+#pragma unroll
+          for (int k = 0; k < kPB; ++k) s = fma(av[k], yv[k], s);
+          v[q] = s;
+        }
+      }
+      __syncthreads();
+      for (int q = 0; q < 3; ++q) {
+        const int e = tid + q * 256;
+        if (e < n2 * kPB) D[(j0 + e % kPB) * ld + base + e / kPB] = v[q];
+      }
+      __syncthreads();
+    }
+    // (c) trailing lower part: element e of the n2 x n2 triangle -> (i, c)
+    const int E = n2 * (n2 + 1) / 2;
+    for (int e = tid; e < E; e += blockDim.x) {
+      int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while (i * (i + 1) / 2 > e) --i;
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      const int c = e - i * (i + 1) / 2;
+      T li[kPB], lc[kPB];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        li[t] = D[(j0 + t) * ld + base + i];
+        lc[t] = D[(j0 + t) * ld + base + c];
+      }
+      T s = D[(base + c) * ld + base + i];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) s = fma(-li[t], lc[t], s);
+      D[(base + c) * ld + base + i] = s;
     }
     __syncthreads();
   }
-  if (tid < kNB) {
-    const T s = dsqrt(D[tid * ld + tid]);
-    sq[tid] = s;
-    rsq[tid] = T(1) / s;
-  }
-  __syncthreads();
-  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
-    const int c = idx / kNB, r = idx % kNB;
-    if (r > c) D[c * ld + r] *= rsq[c];
-    else if (r == c) D[c * ld + r] = sq[c];
-  }
-  __syncthreads();
-  if (tid < kNB) {
-    const int c = tid;
-    T* yc = Y + c * ld;
-    yc[c] = rsq[c];
-    for (int r = c + 1; r < kNB; ++r) {
-      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-      int k = c;
-      for (; k + 3 < r; k += 4) {
-        s0 = fma(D[k * ld + r], yc[k], s0);
-        s1 = fma(D[(k + 1) * ld + r], yc[k + 1], s1);
-        s2 = fma(D[(k + 2) * ld + r], yc[k + 2], s2);
-        s3 = fma(D[(k + 3) * ld + r], yc[k + 3], s3);
+  // off-diagonal blocks of the inverse, by block distance
+  const int r = tid & (kPB - 1), c = tid >> 4;  // element (r, c) of a 16 x 16 block
+  for (int dd = 1; dd < kNB / kPB; ++dd) {
+    const int nb = kNB / kPB - dd;
+    for (int m = 0; m < nb; ++m) {
+      const int bi = m + dd, bj = m;
+      T s = T(0);
+      for (int kb = bj; kb < bi; ++kb) {
+        T lv[kPB], yv[kPB];
+#pragma unroll
+        for (int t = 0; t < kPB; ++t) {
+          lv[t] = D[(kb * kPB + t) * ld + bi * kPB + r];
+          yv[t] = Y[(bj * kPB + c) * ld + kb * kPB + t];
+        }
+#pragma unroll
+        for (int t = 0; t < kPB; ++t) s = fma(lv[t], yv[t], s);
       }
-      for (; k < r; ++k) s0 = fma(D[k * ld + r], yc[k], s0);
-      yc[r] = -((s0 + s1) + (s2 + s3)) * rsq[r];
+      Tm[(m * kPB + c) * tld + r] = s;
     }
+    __syncthreads();
+    for (int m = 0; m < nb; ++m) {
+      const int bi = m + dd, bj = m;
+      T yv[kPB], tv[kPB];
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) {
+        yv[t] = Y[(bi * kPB + t) * ld + bi * kPB + r];  // zero for t > r
+        tv[t] = Tm[(m * kPB + c) * tld + t];
+      }
+      T s = T(0);
+#pragma unroll
+      for (int t = 0; t < kPB; ++t) s = fma(yv[t], tv[t], s);
+      Y[(bj * kPB + c) * ld + bi * kPB + r] = -s;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int idx = tid; idx < b * b; idx += blockDim.x) {
-    const int c = idx / b, r = idx % b;
-    if (r >= c) front_col(d, f, c0 + c)[c0 + r] = D[c * ld + r];
+    const int cc = idx / b, rr = idx % b;
+    if (rr >= cc) front_col(d, f, c0 + cc)[c0 + rr] = D[cc * ld + rr];
   }
   T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
   for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
-    const int c = idx / kNB, r = idx % kNB;
-    Dv[c * kNB + r] = Y[c * ld + r];
+    const int cc = idx / kNB, rr = idx % kNB;
+    Dv[cc * kNB + rr] = Y[cc * ld + rr];
   }
 }
 
