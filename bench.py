@@ -188,6 +188,36 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# DRAM traffic of the dominant FP64 kernel, from one ncu pass
+# (dram__bytes_read.sum + dram__bytes_write.sum) over all 377 k_syrk launches
+# of one FP64 factorization of the default Q1 workload: 230.9 GB read +
+# 199.0 GB written.  Reported per launch, like `achieved`; valid only while
+# the kernel's source text is the one measured (SHA-1 below).
+SYRK_TRAFFIC = {"workload": "q1_extruded_256x256x10_2dof_hnd", "prec": "fp64",
+                "bytes_per_launch": (230.88e9 + 198.97e9) / 377,
+                "source_sha1": "59cc60931be4e84f3320740ff8aa588657291de9"}
+
+
+def kernel_source_sha1(path, signature):
+    """SHA-1 of a kernel's text: from `signature` to its closing brace."""
+    import hashlib
+    try:
+        src = open(path).read()
+        i = src.index(signature)
+        j = src.index("{", i)
+    except (OSError, ValueError):
+        return None
+    depth = 0
+    for k in range(j, len(src)):
+        if src[k] == "{":
+            depth += 1
+        elif src[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return hashlib.sha1(src[i:k + 1].encode()).hexdigest()
+    return None
+
+
 def run_reference(args):
     """The oracle on the host cores, each step a bounded sample (first J
     columns of the elimination order) of the same matrix."""
@@ -423,8 +453,15 @@ def main():
     else:
         peak = bf16 * 1.25 / 2250.0
         src = "measured bf16 %.0f TFLOP/s x nominal FP64/bf16 1.25/2250" % bf16
+    traffic = None
+    if (dom == "syrk" and args.prec == "fp64" and workload_name(args) == SYRK_TRAFFIC["workload"]
+            and kernel_source_sha1(os.path.join(ROOT, "paper_2506_05793_gb300", "csrc",
+                                                "factor_kernels.cu"), "k_syrk(FD<T> d")
+            == SYRK_TRAFFIC["source_sha1"]):
+        traffic = SYRK_TRAFFIC["bytes_per_launch"]
     out["roofline"] = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak,
-                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_source": src}
+                       "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                       "peak_source": src}
     if rank == 0 and not args.no_extras:
         extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm)
     if rank == 0:
