@@ -534,6 +534,64 @@ __global__ void __launch_bounds__(256) k_bw_gemv(SD<T> d, int64_t item_off) {
   }
 }
 
+// Backward update-row sums for several right-hand sides (R >= 8): the block
+// [c0, c0 + bs) of a front takes Y(c0 + c, r) -= (L21^T X2)(c, r) as a small
+// GEMM over chunks of kBwRows update rows.  The chunk of L21 is staged
+// transposed in shared memory (coalesced loads, padded rows), the chunk of
+// X2 row-major; thread (c, g) accumulates column c for right-hand sides
+// g, g + 4, ... (the X2 reads are warp broadcasts).
+constexpr int kBwRows = 64;
+
+template <typename T, int R>
+constexpr size_t bw_gemm_smem() {
+  return ((size_t)kNB * (kBwRows + 1) + (size_t)kBwRows * R) * sizeof(T);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_bw_gemm(SD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int lds = kBwRows + 1;
+  constexpr int RG = R / 4;                 // right-hand sides per thread
+  T* Ls = reinterpret_cast<T*>(smem_raw);   // Ls[c * lds + i] = L21(i0 + i, c0 + c)
+  T* xs = Ls + kNB * lds;                   // xs[i * R + r] = X2(i0 + i, r)
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, m = f.m, nf = k + m, nrhs = d.nrhs;
+  const int c0 = it.a, bs = it.b;
+  const int tid = threadIdx.x, c = tid & (kNB - 1), g = tid >> 6;
+  const T* Lp = d.L + f.Loff;
+  const int32_t* frow = d.rowidx + f.rows_off + k;
+  T acc[RG];
+#pragma unroll
+  for (int q = 0; q < RG; ++q) acc[q] = T(0);
+  for (int i0 = 0; i0 < m; i0 += kBwRows) {
+    const int ch = min(kBwRows, m - i0);
+    __syncthreads();
+    for (int idx = tid; idx < kNB * kBwRows; idx += blockDim.x) {
+      const int cc = idx / kBwRows, i = idx % kBwRows;
+      Ls[cc * lds + i] = (cc < bs && i < ch) ? Lp[(int64_t)(c0 + cc) * nf + k + i0 + i] : T(0);
+    }
+    for (int idx = tid; idx < kBwRows * nrhs; idx += blockDim.x) {
+      const int i = idx % kBwRows, r = idx / kBwRows;
+      xs[i * R + r] = i < ch ? d.Y[(int64_t)r * d.n + frow[i0 + i]] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < kBwRows; ++i) {
+      const T l = Ls[c * lds + i];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) acc[q] = fma(l, xs[i * R + g + 4 * q], acc[q]);
+    }
+  }
+  if (c < bs) {
+#pragma unroll
+    for (int q = 0; q < RG; ++q) {
+      const int r = g + 4 * q;
+      if (r < nrhs) d.Y[(int64_t)r * d.n + f.first + c0 + c] -= acc[q];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Fronts with k + m <= 64: one warp per front (8 per CTA), few registers so
 // that many fronts are in flight.  Lane l owns front rows l and l + 32.  The
@@ -906,6 +964,11 @@ cudaError_t init_r() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_bw_gemv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)gemv_smem<T, R>());
+  if constexpr (R >= 8) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bw_gemm<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bw_gemm_smem<T, R>());
+  }
   return e;
 }
 
@@ -928,6 +991,8 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
         d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk, L.param);
   else if (L.kind == K_FW_GEMV)
     k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
+  else if constexpr (R >= 8)
+    k_bw_gemm<T, R><<<L.count, 256, bw_gemm_smem<T, R>(), st>>>(d, L.item_off);
   else
     k_bw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
 }
