@@ -383,10 +383,10 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
     F->tc = true;
     MF_CK(mf::factor_tc_init());
     const int64_t srows = std::max<int64_t>(s->split_rows, 1);
-    MF_CK(cudaMalloc(&F->split, srows * 128 * sizeof(float)));
+    MF_CK(cudaMalloc(&F->split, srows * 256 * sizeof(float)));
     // rows past a front are read (and discarded) by the tile kernel: keep
     // them finite
-    MF_CK(cudaMemset(F->split, 0, srows * 128 * sizeof(float)));
+    MF_CK(cudaMemset(F->split, 0, srows * 256 * sizeof(float)));
     MF_CK(mf::make_split_map(F->split, srows, F->split_map));
   }
   *f = F.release();

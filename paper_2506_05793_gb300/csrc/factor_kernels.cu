@@ -455,20 +455,21 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
   }
   if (d.split != nullptr) {
     // FP32 tensor-core path: tf32 hi / lo split of the solved rows, row-major
-    // (64 hi then 64 lo floats per row), zero beyond the panel width b
+    // rows of 256 floats holding two panels (slot = step parity, each 64 hi
+    // then 64 lo floats), zero beyond the panel width b
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 16; ++q) As[16 * g + q][r] = (16 * g + q) < b ? x[q] : T(0);
     __syncthreads();
-    float* out = d.split + (d.soff[it.s] + r0) * 128;
+    float* out = d.split + (d.soff[it.s] + r0) * 256 + (it.t & 1) * 128;
     for (int idx = tid; idx < rows * kNB; idx += blockDim.x) {
       const int rw = idx / kNB, c = idx % kNB;
       const float xv = (float)As[c][rw];
       uint32_t hb;
       asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xv));
       const float hi = __uint_as_float(hb);
-      out[(int64_t)rw * 128 + c] = hi;
-      out[(int64_t)rw * 128 + kNB + c] = xv - hi;
+      out[(int64_t)rw * 256 + c] = hi;
+      out[(int64_t)rw * 256 + kNB + c] = xv - hi;
     }
   }
 }

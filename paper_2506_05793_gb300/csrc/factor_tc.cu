@@ -7,7 +7,13 @@
 // tensor cores each panel value is split, p = hi + lo with hi = tf32(p) and
 // lo = p - hi, and C -= hi hi^T + hi lo^T + lo hi^T (the lo lo^T term is
 // below FP32 rounding).  The TRSM kernel writes hi and lo of every panel row
-// into a row-major staging buffer (128 floats per row: 64 hi, 64 lo).
+// into a row-major staging buffer (256 floats per row: two panel slots of
+// 64 hi then 64 lo, the slot being the panel step's parity).
+//
+// Panels are paired to halve the traffic of the trailing matrix: after an
+// even panel t only the next panel's 64 columns are updated (mode 1), and
+// after panel t + 1 both panels update the rest in one pass with K = 128
+// (mode 2); a front ending on an even panel updates normally (mode 0).
 //
 // One CTA (128 threads) computes one 128 x 128 tile (I, J), I >= J:
 //   - the 64-wide K range is staged in two halves of 32 through one 64 KB
@@ -37,7 +43,7 @@ constexpr int kTcM = 128;
 constexpr int kTcN = 128;
 constexpr uint32_t kTmemCols = 128;
 constexpr int kOpBytes = 128 * 128;  // one 128-row x 32-float swizzled K-chunk
-constexpr size_t kTcSmem = 4 * (size_t)kOpBytes + 1024 + 64;
+constexpr size_t kTcSmem = 4 * (size_t)kOpBytes + 1024 + 128;
 constexpr long long kMbarSpin = 1ll << 22;  // try_wait polls before giving up
 
 // instruction descriptor: D = F32, A = B = TF32, both K-major, M = N = 128
@@ -118,23 +124,30 @@ __global__ void __launch_bounds__(128, 3)
   unsigned char* gbase = smem_raw + (sbase - smem_u32(smem_raw));
   const uint32_t a_hi = sbase, a_lo = sbase + kOpBytes;
   const uint32_t b_hi = sbase + 2 * kOpBytes, b_lo = sbase + 3 * kOpBytes;
-  // one single-use barrier per event (TMA of half 0 / 1, MMAs of half 0 / 1),
-  // each waited once on phase 0: a thread that reaches its wait late can
-  // never mistake a later phase for the one it waits for
+  // one single-use barrier per event (MMAs of quarter q at + 8 q, TMA of
+  // quarter q at + 32 + 8 q), each waited once on phase 0: a thread that
+  // reaches its wait late can never mistake a later phase for its own
   uint64_t* mbar = reinterpret_cast<uint64_t*>(gbase + 4 * kOpBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + 4 * kOpBytes + 32);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + 4 * kOpBytes + 64);
 
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int nf = f.k + f.m;
-  const int c0 = it.t * kNB;
+  // mode 0: panel tt on the trailing matrix; 1: panel tt on the next panel's
+  // columns only (strip); 2: panels tt and tt + 1 together (K = 128) on the
+  // trailing matrix beyond panel tt + 1
+  const int tt = it.t & 0xffffff, mode = it.t >> 24;
+  const int tl = mode == 2 ? tt + 1 : tt;  // last panel applied
+  const int c0 = tl * kNB;
   const int b = min(kNB, f.k - c0);
   const int p0 = c0 + b;
   const int rI = p0 + it.a * kTcM, rJ = p0 + it.b * kTcN;
+  const int cmax = mode == 1 ? min(f.k, p0 + kNB) : nf;  // columns updated: [p0, cmax)
+  const int nq = mode == 2 ? 4 : 2;                      // K quarters of 32
   const bool diag = it.a == it.b;
   const int64_t R0 = d.soff[it.s];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t mb0 = smem_u32(mbar);  // + 8 h: MMAs of half h; + 16 + 8 h: TMA of half h
+  const uint32_t mb0 = smem_u32(mbar);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -144,7 +157,7 @@ __global__ void __launch_bounds__(128, 3)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < 8; ++q)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0 + 8 * q) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -163,7 +176,7 @@ __global__ void __launch_bounds__(128, 3)
     return d.U + f.Uoff + (int64_t)(c - f.k) * f.m + (r - f.k);
   };
   auto chunk_load = [&](int cbase, float (&out)[32]) {
-    const int lim = rowok ? min(min(32, nf - cbase), r - cbase + 1) : 0;  // valid j < lim
+    const int lim = rowok ? min(min(32, cmax - cbase), r - cbase + 1) : 0;  // valid j < lim
     if (cbase + 32 <= f.k || cbase >= f.k) {
       const bool inL = cbase < f.k;
       const int64_t ld = inL ? nf : f.m;
@@ -177,7 +190,7 @@ __global__ void __launch_bounds__(128, 3)
     }
   };
   auto chunk_store = [&](int cbase, const float (&cur)[32], const uint32_t (&v)[32]) {
-    const int lim = rowok ? min(min(32, nf - cbase), r - cbase + 1) : 0;
+    const int lim = rowok ? min(min(32, cmax - cbase), r - cbase + 1) : 0;
     if (cbase + 32 <= f.k || cbase >= f.k) {
       const bool inL = cbase < f.k;
       const int64_t ld = inL ? nf : f.m;
@@ -197,7 +210,7 @@ __global__ void __launch_bounds__(128, 3)
   {
     const int c = rJ + tid;
     const int lo = max(rI, c), hi = min(rI + kTcM, nf);
-    if (c < nf && lo < hi) {
+    if (c < cmax && lo < hi) {
       const float* p = c < f.k ? d.L + f.Loff + (int64_t)c * nf + lo
                                : d.U + f.Uoff + (int64_t)(c - f.k) * f.m + (lo - f.k);
       for (int o = 0; o < hi - lo; o += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + o));
@@ -208,18 +221,21 @@ __global__ void __launch_bounds__(128, 3)
   chunk_load(rJ, cur);
   const uint32_t bh = diag ? a_hi : b_hi, bl = diag ? a_lo : b_lo;
   bool ok = true;
-  for (int h = 0; h < 2; ++h) {
-    const uint32_t mb = mb0 + 8 * h, mbt = mb0 + 16 + 8 * h;
+  for (int q = 0; q < nq; ++q) {
+    const uint32_t mb = mb0 + 8 * q, mbt = mb0 + 32 + 8 * q;
+    const int h = q & 1;                                           // half of a panel
+    const int slot = (mode == 2 ? tt + (q >> 1) : tt) & 1;        // staging slot of the panel
+    const int x0 = slot * 128 + h * 32;
     // rows of the staging buffer beyond the front belong to other fronts (or
     // are zero); they only reach accumulator rows / columns that the
     // epilogue discards
     if (tid == 0) {
       mbar_expect_tx(mbt, (diag ? 2u : 4u) * (uint32_t)kOpBytes);
-      tma_box(a_hi, &smap, h * 32, R0 + rI, mbt);
-      tma_box(a_lo, &smap, 64 + h * 32, R0 + rI, mbt);
+      tma_box(a_hi, &smap, x0, R0 + rI, mbt);
+      tma_box(a_lo, &smap, x0 + 64, R0 + rI, mbt);
       if (!diag) {
-        tma_box(b_hi, &smap, h * 32, R0 + rJ, mbt);
-        tma_box(b_lo, &smap, 64 + h * 32, R0 + rJ, mbt);
+        tma_box(b_hi, &smap, x0, R0 + rJ, mbt);
+        tma_box(b_lo, &smap, x0 + 64, R0 + rJ, mbt);
       }
     }
     ok = ok && mbar_wait(mbt, 0u);
@@ -231,7 +247,7 @@ __global__ void __launch_bounds__(128, 3)
       for (int term = 0; term < 3; ++term)
         for (int ks = 0; ks < 4; ++ks)
           mma_tf32(tmem, sdesc_sw128(as[term] + ks * 32), sdesc_sw128(bs[term] + ks * 32),
-                   (h | term | ks) != 0);
+                   (q | term | ks) != 0);
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb)
           : "memory");
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(128, 3)
   } else {
     for (int cb = 0; cb < kTcN / 32; ++cb) {
       const int cbase = rJ + cb * 32;
-      if (cbase >= nf) break;  // same for the whole CTA
+      if (cbase >= cmax) break;  // same for the whole CTA
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32);
       asm volatile(
@@ -263,7 +279,7 @@ __global__ void __launch_bounds__(128, 3)
           : "memory");
       // the next chunk's old values are loaded before this chunk is stored
       float nxt[32];
-      if (cb + 1 < kTcN / 32 && cbase + 32 < nf) chunk_load(cbase + 32, nxt);
+      if (cb + 1 < kTcN / 32 && cbase + 32 < cmax) chunk_load(cbase + 32, nxt);
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
       chunk_store(cbase, cur, v);
 #pragma unroll
@@ -302,8 +318,8 @@ cudaError_t make_split_map(float* split, int64_t rows, void* map_out) {
     encode = reinterpret_cast<EncodeFn>(fn);
   }
   CUtensorMap m;
-  const cuuint64_t dims[2] = {128, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {128 * sizeof(float)};
+  const cuuint64_t dims[2] = {256, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {256 * sizeof(float)};
   const cuuint32_t box[2] = {32, 128};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, split, dims, strides, box, estr,

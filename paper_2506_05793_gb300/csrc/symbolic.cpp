@@ -22,6 +22,7 @@
 #include <map>
 #include <set>
 #include <numeric>
+#include <unordered_map>
 
 #include "mf_internal.h"
 
@@ -687,9 +688,10 @@ void build_schedules(mf_symbolic& S, int small_max) {
     }
     S.split_rows = std::max(S.split_rows, srow);
     S.max_large = std::max<int64_t>(S.max_large, (int64_t)G.size());
+    std::unordered_map<int32_t, double> fpair;  // panel t's deferred flops
     for (int32_t t = 0; t < T; ++t) {
       std::vector<Item> ip, it3, is, itc;
-      double fp = 0, ft = 0, fs = 0;
+      double fp = 0, ft = 0, fs = 0, fstc = 0;
       for (size_t gi = 0; gi < G.size(); ++gi) {
         const int32_t s = G[gi];
         const int lpos = (int)gi;  // slot of the front's diagonal-block inverse
@@ -704,17 +706,35 @@ void build_schedules(mf_symbolic& S, int small_max) {
         const int nt = (nf - p0 + kTile - 1) / kTile;
         for (int I = 0; I < nt; ++I)
           for (int J = 0; J <= I; ++J) is.push_back({s, t, I, J});
+        // tensor-core path: panels are paired.  Even step t with a next
+        // panel: update only the next panel's 64 columns (strip, mode 1);
+        // odd step t: update everything beyond panel t with both panels at
+        // once (K = 128, mode 2, item carries the first panel t - 1).  An
+        // even last step updates its trailing matrix alone (mode 0).
         const int nt2 = (nf - p0 + kTcTile - 1) / kTcTile;
-        for (int I = 0; I < nt2; ++I)
-          for (int J = 0; J <= I; ++J) itc.push_back({s, t, I, J});
-        fs += (double)(nf - p0) * (double)(nf - p0 + 1) * b;
+        const double full = (double)(nf - p0) * (double)(nf - p0 + 1) * b;
+        if ((t & 1) == 0 && (t + 1) * kNB < k) {
+          const int b1 = std::min(kNB, k - (t + 1) * kNB);
+          for (int I = 0; I < nt2; ++I) itc.push_back({s, t | (1 << 24), I, 0});
+          fstc += 2.0 * ((double)b1 * (nf - p0) - (double)b1 * (b1 - 1) / 2.0) * b;
+          fpair[s] = full - 2.0 * ((double)b1 * (nf - p0) - (double)b1 * (b1 - 1) / 2.0) * b;
+        } else if ((t & 1) == 0) {
+          for (int I = 0; I < nt2; ++I)
+            for (int J = 0; J <= I; ++J) itc.push_back({s, t, I, J});
+          fstc += full;
+        } else {
+          for (int I = 0; I < nt2; ++I)
+            for (int J = 0; J <= I; ++J) itc.push_back({s, (t - 1) | (2 << 24), I, J});
+          fstc += full + fpair[s];
+        }
+        fs += full;
       }
       add(S.fsched, K_POTRF, lev, t, ip, fp);
       add(S.fsched, K_TRSM, lev, t, it3, ft);
       add(S.fsched, K_SYRK, lev, t, is, fs);
       add(S.fsched_tc, K_POTRF, lev, t, ip, fp);
       add(S.fsched_tc, K_TRSM, lev, t, it3, ft);
-      add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fs);
+      add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fstc);
     }
   }
   // ---- solves.  Per level and sweep, fronts with k + m <= kWarpSolve go to

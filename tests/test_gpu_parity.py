@@ -284,7 +284,7 @@ def test_relaxed_and_fundamental_fronts_agree(mf, orc):
     assert orc.rel_fro(Ls[0], Ls[1]) <= RELF64
 
 
-@pytest.mark.parametrize("case", ["dense_200", "dense_333", "lap3d_jump_20", "q1_14x12x4"])
+@pytest.mark.parametrize("case", ["dense_150", "dense_200", "dense_333", "lap3d_jump_20", "q1_14x12x4"])
 def test_fp32_tensor_core_update(mf, orc, case):
     """FP32 factor with the tcgen05 split-TF32 trailing update agrees with the
     FP32 FMA path and with the FP64 oracle to FP32 accuracy."""
