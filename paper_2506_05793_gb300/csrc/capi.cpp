@@ -98,10 +98,14 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
 
 size_t elem_size(int prec) { return prec == MF_FP32 ? sizeof(float) : sizeof(double); }
 
+// Device bytes of one factor: L, update matrices, diagonal-block inverses,
+// values in assembly order and the CSR values; FP32 adds the tensor-core
+// staging rows (two panels of 64 hi + 64 lo floats per row).
 int64_t factor_bytes(const mf_symbolic* S, int prec) {
   return (S->Lsize + S->Usize + S->max_large * mf::kNB * mf::kNB + S->nnz_lower) *
              (int64_t)elem_size(prec) +
-         S->nnzA * (int64_t)sizeof(double);
+         S->nnzA * (int64_t)sizeof(double) +
+         (prec == MF_FP32 ? std::max<int64_t>(S->split_rows, 1) * 256 * (int64_t)sizeof(float) : 0);
 }
 
 }  // namespace
