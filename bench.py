@@ -61,6 +61,8 @@ def parse():
                    help="pick relaxation / small-front limit / tensor cores with mf_autotune first")
     p.add_argument("--count", type=int, default=512, help="batch: number of boxes")
     p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per solve")
+    p.add_argument("--sptrsv", type=int, default=2, choices=[1, 2],
+                   help="pivot-block solve: 1 substitution, 2 stored diagonal-block inverses")
     p.add_argument("--serve-rates", default="25,100,400",
                    help="serve: Poisson arrival rates (requests/s) to sweep")
     p.add_argument("--serve-requests", type=int, default=240, help="serve: requests per rate")
@@ -357,6 +359,7 @@ def main():
         tuned = {"relax": opt.relax, "small_front_max": opt.small_front_max, "tc": opt.tc,
                  "ms": tuned_ms}
     opt.profile = 1  # per-launch CUDA events: per-kernel-kind device time
+    opt.sptrsv = args.sptrsv
     h = mf.mf_create(opt)
     t0 = time.perf_counter()
     s = mf.mf_symbolic_analyze(h, rp, ci, perm)
@@ -417,6 +420,7 @@ def main():
                    "nnz_L": info["nnz_L"],
                    "flops_per_factor": flops, "nsuper": info["nsuper"],
                    "levels": info["nlevels"], "max_front": info["max_front"], "nrhs": args.nrhs,
+                   "sptrsv": args.sptrsv,
                    "parallelism": "replicas" if ws > 1 else "single",
                    "l2_flush": "inputs larger than L2 (factor %.1f GB)" % (
                        info["factor_bytes_fp64"] / 1e9),

@@ -71,7 +71,13 @@ typedef struct mf_options {
   int64_t budget_bytes;     /* device bytes a factor may hold (0 = no limit) */
   int32_t tc;               /* 1: FP32 trailing updates on tcgen05 tensor cores
                                (split-TF32, FP32 accuracy); 0: FP32 FMA */
-  int32_t reserved0;
+  int32_t sptrsv;           /* solve of the large fronts' pivot blocks (Sec. 5,
+                               SpTRSV variants): 1 = substitution with the
+                               64 x 64 diagonal blocks; 2 = product with their
+                               inverses, kept from the factorization (default;
+                               more memory: 64 x 64 values per 64 pivot columns
+                               of every large front, about 5% of the factor).
+                               Fixed at symbolic analysis. */
 } mf_options;
 
 /* Summary of a symbolic analysis. */

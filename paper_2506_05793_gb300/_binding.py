@@ -31,7 +31,7 @@ _D = ctypes.c_double
 
 class mf_options(ctypes.Structure):
     _fields_ = [("small_front_max", _I32), ("use_graphs", _I32), ("profile", _I32),
-                ("relax", _I32), ("budget_bytes", _I64), ("tc", _I32), ("reserved0", _I32)]
+                ("relax", _I32), ("budget_bytes", _I64), ("tc", _I32), ("sptrsv", _I32)]
 
 
 class mf_symbolic_info(ctypes.Structure):

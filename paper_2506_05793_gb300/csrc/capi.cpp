@@ -84,6 +84,7 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
   MF_CK(o->up(&o->d.items, S->items));
   MF_CK(o->up(&o->d.blkoff, S->blkoff));
   MF_CK(o->up(&o->d.soff, S->soff));
+  MF_CK(o->up(&o->d.ioff, S->ioff));
   MF_CK(o->up(&o->d.arange, S->arange));
   MF_CK(o->up(&o->d.ginv_ptr, S->ginv_ptr));
   MF_CK(o->up(&o->d.ginv_src, S->ginv_src));
@@ -102,7 +103,8 @@ size_t elem_size(int prec) { return prec == MF_FP32 ? sizeof(float) : sizeof(dou
 // values in assembly order and the CSR values; FP32 adds the tensor-core
 // staging rows (two panels of 64 hi + 64 lo floats per row).
 int64_t factor_bytes(const mf_symbolic* S, int prec) {
-  return (S->Lsize + S->Usize + S->max_large * mf::kNB * mf::kNB + S->nnz_lower) *
+  const int64_t inv_slots = S->keep_inv ? S->ninv : S->max_large;
+  return (S->Lsize + S->Usize + inv_slots * mf::kNB * mf::kNB + S->nnz_lower) *
              (int64_t)elem_size(prec) +
          S->nnzA * (int64_t)sizeof(double) +
          (prec == MF_FP32 ? std::max<int64_t>(S->split_rows, 1) * 256 * (int64_t)sizeof(float) : 0);
@@ -177,6 +179,7 @@ int mf_options_default(mf_options* opt) {
   opt->use_graphs = 1;
   opt->profile = 0;
   opt->relax = 1;
+  opt->sptrsv = 2;
   opt->tc = 1;
   opt->budget_bytes = 0;
   return MF_OK;
@@ -220,6 +223,7 @@ int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr, const in
   std::string err;
   int rc;
   S->relax = h->opt.relax ? 1 : 0;
+  S->keep_inv = h->opt.sptrsv == 2;
   try {
     rc = mf::analyze(*S, n, rowptr, colind, perm, err);
     if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max);
@@ -379,7 +383,10 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   MF_CK(cudaMalloc(&F->status, 2 * sizeof(unsigned long long)));
   MF_CK(cudaMallocHost(&F->status_host, 2 * sizeof(unsigned long long)));
   MF_CK(cudaMemset(F->status, 0xff, 2 * sizeof(unsigned long long)));
-  MF_CK(cudaMalloc(&F->dinv, std::max<int64_t>(s->max_large, 1) * mf::kNB * mf::kNB * es));
+  // diagonal-block inverses: one slot per large front of a level, or one per
+  // 64 pivot columns of every large front when the solve uses them
+  const int64_t inv_slots = s->keep_inv ? s->ninv : s->max_large;
+  MF_CK(cudaMalloc(&F->dinv, std::max<int64_t>(inv_slots, 1) * mf::kNB * mf::kNB * es));
   MF_CK(cudaMalloc(&F->av, std::max<int64_t>(s->nnz_lower, 1) * es));
   MF_CK(mf::factor_kernels_init(prec));
   MF_CK(mf::solve_kernels_init(prec));
@@ -684,6 +691,7 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.nrhs = cn;
   a.nlevels = S->nlevels;
   a.nblk = S->blkoff.back();
+  a.dinv = S->keep_inv ? f->dinv : nullptr;
   for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, X, ldx, S->n, cn, scale, accumulate, st));

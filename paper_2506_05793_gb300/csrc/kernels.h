@@ -22,6 +22,7 @@ struct DevSym {
   Item* items = nullptr;
   int32_t* blkoff = nullptr;   // per front: first 64-column block (solve flags)
   int64_t* soff = nullptr;     // per front: first row in the split buffer
+  int64_t* ioff = nullptr;     // per front: first diagonal-block inverse slot (or -1)
   Item* arange = nullptr;      // assembly chunks: (child, lo, hi) ranges, sentinel -1
   int64_t* ginv_ptr = nullptr; // forward gather (inverse relative maps)
   int64_t* ginv_src = nullptr;
@@ -55,6 +56,9 @@ struct SolveArgs {
   // counter per level and sweep, then forward and backward block flags
   int32_t* sync;
   unsigned long long* status;  // status[1] receives MF_ERR_TIMEOUT
+  // diagonal-block inverses of the large fronts (slots sym.ioff), or nullptr
+  // to solve the pivot blocks by substitution
+  const void* dinv = nullptr;
   int64_t n;
   int32_t nrhs;
   int32_t nlevels;

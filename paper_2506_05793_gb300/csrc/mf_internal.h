@@ -120,6 +120,11 @@ struct mf_symbolic {
   std::vector<int64_t> soff;          // per front: first row in the split buffer
   int64_t split_rows = 0;
   int64_t max_large = 0;              // most large fronts in one level
+  // diagonal-block inverses kept for the solve (SpTRSV variant 2): slot of
+  // the first 64-column block of each large front (-1 elsewhere), slot count
+  bool keep_inv = false;
+  std::vector<int64_t> ioff;
+  int64_t ninv = 0;
   std::vector<mf::Item> arange;       // assembly: (child, lo, hi, 0) lists per chunk
   std::vector<mf::Launch> fwsched, bwsched;
   std::vector<int32_t> blkoff;     // per front: first 64-column block index

@@ -37,6 +37,8 @@ struct SD {
   const int32_t* blkoff;
   const int64_t* ginv_ptr;
   const int64_t* ginv_src;
+  const T* dinv;         // diagonal-block inverses (SpTRSV variant 2) or nullptr
+  const int64_t* ioff;   // per front: first inverse slot, -1 if none
   unsigned long long* status;
   int64_t n;
   int nrhs;
@@ -56,6 +58,8 @@ SD<T> make_sd(const SolveArgs& a) {
   d.blkoff = a.sym.blkoff;
   d.ginv_ptr = a.sym.ginv_ptr;
   d.ginv_src = a.sym.ginv_src;
+  d.dinv = static_cast<const T*>(a.dinv);
+  d.ioff = a.sym.ioff;
   d.status = a.status;
   d.n = a.n;
   d.nrhs = a.nrhs;
@@ -161,8 +165,24 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
       Lc[qq] = (nblk > 0 && live && q < bs0) ? Lp[(int64_t)q * nf + r0 + row] : T(0);
     }
   }
-  // diagonal block and reciprocals of its diagonal (pivot blocks)
-  if (pivot) {
+  // pivot blocks: the inverse of the diagonal block when it was kept
+  // (SpTRSV variant 2), else the diagonal block and the reciprocals of its
+  // diagonal for the substitution
+  const int64_t islot = (pivot && d.dinv != nullptr) ? d.ioff[it.s] : -1;
+  if (islot >= 0) {
+    T v[kNB * kNB / 256];
+    const T* Q = d.dinv + (islot + r0 / kNB) * (int64_t)(kNB * kNB);
+#pragma unroll
+    for (int u = 0; u < kNB * kNB / 256; ++u) {
+      const int idx = tid + u * 256, c = idx / kNB, i = idx % kNB;
+      v[u] = (c < rows && i < rows) ? Q[idx] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kNB * kNB / 256; ++u) {
+      const int idx = tid + u * 256;
+      D[(idx / kNB) * ld + (idx % kNB)] = v[u];
+    }
+  } else if (pivot) {
     // all global loads of the diagonal block in flight before the stores
     T v[kNB * kNB / 256];
     const T* P = Lp + (int64_t)r0 * nf + r0;
@@ -234,6 +254,34 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   }
   if (!pivot) return;
   __syncthreads();
+  if (islot >= 0) {
+    // x = L_pp^{-1} u: thread (row, g) sums 16 columns, four partial sums
+    T a2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a2[r] = T(0);
+#pragma unroll
+    for (int qq = 0; qq < 16; ++qq) {
+      const int c = g * 16 + qq;
+      if (c < rows) {
+        const T dv = D[c * ld + row];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r < nrhs) a2[r] = fma(dv, xs[c * R + r], a2[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r < nrhs) red[(g * kNB + row) * R + r] = a2[r];
+    __syncthreads();
+    for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
+      const int rw = idx / nrhs, r = idx % nrhs;
+      d.Y[(int64_t)r * d.n + f.first + r0 + rw] =
+          red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
+          red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
+    }
+    cta_publish(fl + r0 / kNB);
+    return;
+  }
   // column-oriented substitution, one warp per right-hand side; lane owns
   // rows lane and lane + 32 of the block
   for (int r = warp; r < nrhs; r += 8) {
@@ -310,21 +358,26 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
       Lc[ii] = (live && i < ti) ? Lcol[i0 + i] : T(0);
     }
   }
+  // Dt[j * ld + c] = (j, c) entry of the diagonal block, or of its inverse
+  // when that was kept (SpTRSV variant 2)
+  const int64_t islot = d.dinv != nullptr ? d.ioff[it.s] : -1;
   {
     // all global loads of the diagonal block in flight before the stores
     T v[kNB * kNB / 256];
     const T* P = Lp + (int64_t)c0 * nf + c0;
+    const T* Q = islot >= 0 ? d.dinv + (islot + c0 / kNB) * (int64_t)(kNB * kNB) : nullptr;
 #pragma unroll
     for (int u = 0; u < kNB * kNB / 256; ++u) {
       const int idx = tid + u * 256, c = idx / kNB, j = idx % kNB;
-      v[u] = (c < bs && j < bs && j >= c) ? P[(int64_t)c * nf + j] : T(0);
+      const bool in = c < bs && j < bs && j >= c;
+      v[u] = in ? (Q ? Q[idx] : P[(int64_t)c * nf + j]) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kNB * kNB / 256; ++u) {
       const int idx = tid + u * 256;
       Dt[(idx % kNB) * ld + idx / kNB] = v[u];
     }
-    if (tid < bs) rinv[tid] = T(1) / P[(int64_t)tid * nf + tid];
+    if (islot < 0 && tid < bs) rinv[tid] = T(1) / P[(int64_t)tid * nf + tid];
   }
   T acc[R];
 #pragma unroll
@@ -382,6 +435,35 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
     xs[c * R + r] = d.Y[(int64_t)r * d.n + f.first + c0 + c] - sum;
   }
   __syncthreads();
+  if (islot >= 0) {
+    // x = L_cc^{-T} v: thread (col, g) sums rows 16 g .. 16 g + 15 of
+    // column col of the inverse, four partial sums
+    T a2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a2[r] = T(0);
+#pragma unroll
+    for (int qq = 0; qq < 16; ++qq) {
+      const int j = g * 16 + qq;
+      if (j < bs) {
+        const T dv = Dt[j * ld + col];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if (r < nrhs) a2[r] = fma(dv, xs[j * R + r], a2[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r < nrhs) red[(g * kNB + col) * R + r] = a2[r];
+    __syncthreads();
+    for (int idx = tid; idx < bs * nrhs; idx += blockDim.x) {
+      const int c = idx / nrhs, r = idx % nrhs;
+      d.Y[(int64_t)r * d.n + f.first + c0 + c] =
+          red[(0 * kNB + c) * R + r] + red[(1 * kNB + c) * R + r] +
+          red[(2 * kNB + c) * R + r] + red[(3 * kNB + c) * R + r];
+    }
+    cta_publish(fl + c0 / kNB);
+    return;
+  }
   // right-looking substitution with L_cc^T, one warp per right-hand side;
   // lane owns columns lane and lane + 32 of the block
   for (int r = warp; r < nrhs; r += 8) {

@@ -606,6 +606,8 @@ void build_schedules(mf_symbolic& S, int small_max) {
   S.soff.assign(S.sn.size(), 0);
   S.split_rows = 0;
   S.max_large = 0;
+  S.ioff.assign(S.sn.size(), -1);
+  S.ninv = 0;
   S.fwsched.clear();
   S.bwsched.clear();
   const int64_t ns = (int64_t)S.sn.size();
@@ -688,13 +690,19 @@ void build_schedules(mf_symbolic& S, int small_max) {
     }
     S.split_rows = std::max(S.split_rows, srow);
     S.max_large = std::max<int64_t>(S.max_large, (int64_t)G.size());
+    if (S.keep_inv)
+      for (int32_t s : G) {
+        S.ioff[s] = S.ninv;
+        S.ninv += (S.sn[s].k + kNB - 1) / kNB;
+      }
     std::unordered_map<int32_t, double> fpair;  // panel t's deferred flops
     for (int32_t t = 0; t < T; ++t) {
       std::vector<Item> ip, it3, is, itc;
       double fp = 0, ft = 0, fs = 0, fstc = 0;
       for (size_t gi = 0; gi < G.size(); ++gi) {
         const int32_t s = G[gi];
-        const int lpos = (int)gi;  // slot of the front's diagonal-block inverse
+        // slot of the diagonal-block inverse: per level, or kept per block
+        const int lpos = S.keep_inv ? (int)(S.ioff[s] + t) : (int)gi;
         const int k = S.sn[s].k, nf = k + S.sn[s].m;
         if (k <= t * kNB) continue;
         const int b = std::min(kNB, k - t * kNB);
