@@ -120,15 +120,15 @@ constexpr size_t bw_level_smem() {
 }
 
 // ---------------------------------------------------------------------------
-// Forward, one 64-row block of a front.  The block first gathers its rows of
-// the front work vector, w = [b(first..first+k); 0] + the children's update
-// entries (inverse relative maps, children in fixed order).  Pivot block p:
-//   x_p = L_pp^{-1} (w_p - sum_{a<p} L_pa x_a), written to Y and published
-//   through flag p;
-// update-row block: u = w - sum_a L_ua x_a, left in W for the parent.
-// Thread (row, g): row of the block, g = quarter of the 64 columns of L_pa.
-// The L values of block a+1 are loaded into registers while the block waits
-// for x_a, so the DRAM latency is off the critical path.
+// Forward, one 64-row pivot block p of a large front (the update rows of
+// the level run afterwards in k_fw_gemv).  The block gathers its rows of the
+// front work vector, w = b(first..) + the children's update entries (inverse
+// relative maps, children in fixed order), then
+//   x_p = L_pp^{-1} (w_p - sum_{a<p} L_pa x_a),
+// written to Y and published through flag p; earlier blocks are awaited
+// through their flags.  Thread (row, g): row of the block, g = quarter of the
+// 64 columns of L_pa.  The L values of block a+1 are loaded into registers
+// while the block waits for x_a, so the DRAM latency is off the critical path.
 // ---------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
@@ -141,19 +141,17 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   T* rinv = D + kNB * (kNB + 1);
   constexpr int ld = kNB + 1;
   __shared__ int s_item;
-  if (threadIdx.x == 0) s_item = counter ? atomicAdd(counter, 1) : (int)blockIdx.x;
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
   __syncthreads();
   const int nrhs = d.nrhs;
   const Item it = d.items[item_off + s_item];
   const SnInfo f = d.sn[it.s];
   const int k = f.k, nf = k + f.m;
   const int r0 = it.a, rows = it.b;
-  const bool pivot = it.t == 0;
   const int tid = threadIdx.x, row = tid & 63, g = tid >> 6, lane = tid & 31, warp = tid >> 5;
   int* fl = flags + d.blkoff[it.s];
   const T* Lp = d.L + f.Loff;
-  T* Wf = d.W + f.woff * nrhs;
-  const int nblk = pivot ? r0 / kNB : (k + kNB - 1) / kNB;
+  const int nblk = r0 / kNB;  // earlier pivot blocks of the front
   // L values of block 0 (thread: column 16 g + qq of the block, its row)
   T Lc[16];
   const bool live = row < rows;
@@ -168,7 +166,7 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   // pivot blocks: the inverse of the diagonal block when it was kept
   // (SpTRSV variant 2), else the diagonal block and the reciprocals of its
   // diagonal for the substitution
-  const int64_t islot = (pivot && d.dinv != nullptr) ? d.ioff[it.s] : -1;
+  const int64_t islot = d.dinv != nullptr ? d.ioff[it.s] : -1;
   if (islot >= 0) {
     T v[kNB * kNB / 256];
     const T* Q = d.dinv + (islot + r0 / kNB) * (int64_t)(kNB * kNB);
@@ -182,7 +180,7 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
       const int idx = tid + u * 256;
       D[(idx / kNB) * ld + (idx % kNB)] = v[u];
     }
-  } else if (pivot) {
+  } else {
     // all global loads of the diagonal block in flight before the stores
     T v[kNB * kNB / 256];
     const T* P = Lp + (int64_t)r0 * nf + r0;
@@ -248,11 +246,8 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
     const int rw = idx / nrhs, r = idx % nrhs;
     const T sum = red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
                   red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
-    const T u = ws[rw * R + r] - sum;
-    if (pivot) xs[rw * R + r] = u;
-    else Wf[(int64_t)(r0 + rw) * nrhs + r] = u;
+    xs[rw * R + r] = ws[rw * R + r] - sum;
   }
-  if (!pivot) return;
   __syncthreads();
   if (islot >= 0) {
     // x = L_pp^{-1} u: thread (row, g) sums 16 columns, four partial sums
@@ -305,16 +300,16 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
 }
 
 // ---------------------------------------------------------------------------
-// Backward, one 64-column block c of a front:
-//   x_c = L_cc^{-T} (y_c - L21[:, c]^T x(update rows) - sum_{a>c} L_ac^T x_a),
-// update rows read the final x of ancestor fronts, later blocks are awaited
-// through their flags.  Thread (col, g) holds rows 16 g .. 16 g + 15 of its
-// column of the current 64-row tile in registers; the next tile is loaded
-// while the block waits.
+// Backward, one 64-column pivot block c of a large front:
+//   x_c = L_cc^{-T} (y'_c - sum_{a>c} L_ac^T x_a),
+// y' = y - L21[:, c]^T x(update rows), already formed by k_bw_gemv /
+// k_bw_gemm; later blocks are awaited through their flags.  Thread (col, g)
+// holds rows 16 g .. 16 g + 15 of its column of the current 64-row tile in
+// registers; the next tile is loaded while the block waits.
 // ---------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
-    k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags, int upd_done) {
+    k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ld = kNB + 1;
   T* xs = reinterpret_cast<T*>(smem_raw);  // xs[i * R + r]
@@ -334,23 +329,16 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   const T* Lp = d.L + f.Loff;
   const bool live = col < bs;
   const T* Lcol = Lp + (int64_t)(c0 + (live ? col : 0)) * nf;
-  const int32_t* frow = d.rowidx + f.rows_off;
   const int PB = (k + kNB - 1) / kNB;
-  // tiles: update rows first (no waiting; skipped when k_bw_gemv has already
-  // subtracted them from y), then later pivot blocks, last first
-  const int ntu = upd_done ? 0 : (nf - k + kNB - 1) / kNB;
-  const int ntiles = ntu + (PB - 1 - c0 / kNB);
+  // tiles: the later pivot blocks of the front, last first (the update rows
+  // were subtracted from y by k_bw_gemv / k_bw_gemm)
+  const int ntiles = PB - 1 - c0 / kNB;
   T Lc[16];
   {
     int i0 = 0, ti = 0;
     if (ntiles > 0) {
-      if (ntu > 0) {
-        i0 = k;
-        ti = min(kNB, nf - k);
-      } else {
-        i0 = (PB - 1) * kNB;
-        ti = min(kNB, k - i0);
-      }
+      i0 = (PB - 1) * kNB;
+      ti = min(kNB, k - i0);
     }
 #pragma unroll
     for (int ii = 0; ii < 16; ++ii) {
@@ -383,20 +371,14 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = T(0);
   for (int tI = 0; tI < ntiles; ++tI) {
-    const bool upd = tI < ntu;
-    const int i0 = upd ? k + tI * kNB : (PB - 1 - (tI - ntu)) * kNB;
-    const int ti = upd ? min(kNB, nf - i0) : min(kNB, k - i0);
+    const int i0 = (PB - 1 - tI) * kNB;
+    const int ti = min(kNB, k - i0);
     T Ln[16];
     {
       int n0 = 0, nt = 0;
       if (tI + 1 < ntiles) {
-        if (tI + 1 < ntu) {
-          n0 = k + (tI + 1) * kNB;
-          nt = min(kNB, nf - n0);
-        } else {
-          n0 = (PB - 1 - (tI + 1 - ntu)) * kNB;
-          nt = min(kNB, k - n0);
-        }
+        n0 = (PB - 2 - tI) * kNB;
+        nt = min(kNB, k - n0);
       }
 #pragma unroll
       for (int ii = 0; ii < 16; ++ii) {
@@ -404,11 +386,10 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
         Ln[ii] = (live && i < nt) ? Lcol[n0 + i] : T(0);
       }
     }
-    if (!upd) cta_wait(fl + i0 / kNB, d.status);
+    cta_wait(fl + i0 / kNB, d.status);
     for (int idx = tid; idx < ti * nrhs; idx += blockDim.x) {
       const int i = idx % ti, r = idx / ti;
-      xs[i * R + r] = upd ? d.Y[(int64_t)r * d.n + frow[i0 + i]]
-                          : __ldcg(d.Y + (int64_t)r * d.n + f.first + i0 + i);
+      xs[i * R + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + i0 + i);
     }
     __syncthreads();
 #pragma unroll
@@ -1068,9 +1049,9 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   if (L.kind == K_FW_LEVEL)
     k_fw_level<T, R><<<L.count, 256, fw_level_smem<T, R>(), st>>>(
         d, L.item_off, a.sync + 2 * L.level, a.sync + 2 * a.nlevels);
-  else if (L.kind == K_BW_LEVEL)  // param 1: k_bw_gemv did the update rows
+  else if (L.kind == K_BW_LEVEL)
     k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(
-        d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk, L.param);
+        d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
   else if (L.kind == K_FW_GEMV)
     k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
   else if constexpr (R >= 8)
