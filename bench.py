@@ -434,6 +434,9 @@ def main():
     }
     fac_ms = sum(p["ms"] for p in prof.values())
     out["factor_ms_sum_of_kernels"] = fac_ms
+    out["kernels_note"] = ("per-kind sums of per-launch CUDA-event times; lookahead runs bulk "
+                           "updates on a second stream, so kinds overlap and the sum can exceed "
+                           "the step")
     out["factor_tflops_kernels"] = flops / (fac_ms / 1e3) / 1e12 if fac_ms > 0 else None
     out["kernels"] = prof
     # dominant kernel roofline: FP64 FMA pipe (contraction) against the

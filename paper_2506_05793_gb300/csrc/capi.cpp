@@ -107,7 +107,10 @@ int64_t factor_bytes(const mf_symbolic* S, int prec) {
   return (S->Lsize + S->Usize + inv_slots * mf::kNB * mf::kNB + S->nnz_lower) *
              (int64_t)elem_size(prec) +
          S->nnzA * (int64_t)sizeof(double) +
-         (prec == MF_FP32 ? std::max<int64_t>(S->split_rows, 1) * 256 * (int64_t)sizeof(float) : 0);
+         (prec == MF_FP32 ? (std::max<int64_t>(S->split_rows, 1) * 256 +
+                             std::max<int64_t>(S->split_rows_b, 1) * 512) *
+                                (int64_t)sizeof(float)
+                          : 0);
 }
 
 }  // namespace
@@ -132,7 +135,15 @@ struct mf_factor {
   int32_t* sync = nullptr;  // solve ticket counters and block flags
   bool tc = false;          // FP32 trailing updates on tcgen05 tensor cores
   float* split = nullptr;   // tf32 hi/lo staging rows of the panels
-  alignas(128) unsigned char split_map[128];  // TMA tensor map over split
+  float* split_b = nullptr; // four-slot staging rows of lookahead levels
+  alignas(128) unsigned char split_map[128];    // TMA tensor map over split
+  alignas(128) unsigned char split_map_b[128];  // TMA tensor map over split_b
+  // enqueue_factor runs on two internal streams forked from the caller's:
+  // the critical path (panels, first tile columns) at high priority and the
+  // lookahead bulk updates at low priority, so that freed SM slots go to the
+  // critical path first
+  cudaStream_t crit = nullptr, side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_side = nullptr, ev_in = nullptr, ev_out = nullptr;
   void* dinv = nullptr;     // inverses of the current diagonal blocks (scratch)
   void* av = nullptr;       // lower entries of C in assembly order (T)
   double* small = nullptr;  // per-RHS scalars for refinement
@@ -164,6 +175,13 @@ struct mf_factor {
     cudaFree(small);
     cudaFree(sync);
     cudaFree(split);
+    cudaFree(split_b);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_side) cudaEventDestroy(ev_side);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (side) cudaStreamDestroy(side);
+    if (crit) cudaStreamDestroy(crit);
     cudaFree(dinv);
     cudaFree(av);
     delete fb64;
@@ -394,11 +412,15 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
     F->tc = true;
     MF_CK(mf::factor_tc_init());
     const int64_t srows = std::max<int64_t>(s->split_rows, 1);
+    const int64_t srows_b = std::max<int64_t>(s->split_rows_b, 1);
     MF_CK(cudaMalloc(&F->split, srows * 256 * sizeof(float)));
+    MF_CK(cudaMalloc(&F->split_b, srows_b * 512 * sizeof(float)));
     // rows past a front are read (and discarded) by the tile kernel: keep
     // them finite
     MF_CK(cudaMemset(F->split, 0, srows * 256 * sizeof(float)));
-    MF_CK(mf::make_split_map(F->split, srows, F->split_map));
+    MF_CK(cudaMemset(F->split_b, 0, srows_b * 512 * sizeof(float)));
+    MF_CK(mf::make_split_map(F->split, srows, 256, F->split_map));
+    MF_CK(mf::make_split_map(F->split_b, srows_b, 512, F->split_map_b));
   }
   *f = F.release();
   return MF_OK;
@@ -413,7 +435,9 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile) {
   a.U = F->U;
   a.status = F->status;
   a.split = F->tc ? F->split : nullptr;
+  a.split_b = F->tc ? F->split_b : nullptr;
   a.split_map = F->tc ? F->split_map : nullptr;
+  a.split_map_b = F->tc ? F->split_map_b : nullptr;
   a.dinv = F->dinv;
   a.av = F->av;
   const std::vector<mf::Launch>& sched = F->tc ? S->fsched_tc : S->fsched;
@@ -424,11 +448,46 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile) {
     F->ev.resize(2 * sched.size());
     for (size_t i = old; i < F->ev.size(); ++i) MF_CK(cudaEventCreate(&F->ev[i]));
   }
-  for (size_t i = 0; i < sched.size(); ++i) {
-    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i], st));
-    MF_CK(mf::launch_factor(F->prec, sched[i], a, st));
-    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i + 1], st));
+  if (!F->side) {
+    int lo = 0, hi = 0;
+    MF_CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    MF_CK(cudaStreamCreateWithPriority(&F->crit, cudaStreamNonBlocking, hi));
+    MF_CK(cudaStreamCreateWithPriority(&F->side, cudaStreamNonBlocking, lo));
+    for (cudaEvent_t* e : {&F->ev_fork, &F->ev_side, &F->ev_in, &F->ev_out})
+      MF_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
+  // the schedule runs on crit, lookahead launches on side (forked from
+  // crit); crit joins side when a launch asks, at every change of level and
+  // at the end, and st waits for crit, so the factorization as a whole stays
+  // ordered on st
+  MF_CK(cudaEventRecord(F->ev_in, st));
+  MF_CK(cudaStreamWaitEvent(F->crit, F->ev_in, 0));
+  bool pending = false;
+  int32_t level = -1;
+  for (size_t i = 0; i < sched.size(); ++i) {
+    const mf::Launch& L = sched[i];
+    if (pending && (L.join || L.level != level)) {
+      MF_CK(cudaStreamWaitEvent(F->crit, F->ev_side, 0));
+      pending = false;
+    }
+    level = L.level;
+    cudaStream_t ls = F->crit;
+    if (L.side) {
+      MF_CK(cudaEventRecord(F->ev_fork, F->crit));
+      MF_CK(cudaStreamWaitEvent(F->side, F->ev_fork, 0));
+      ls = F->side;
+    }
+    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i], ls));
+    MF_CK(mf::launch_factor(F->prec, L, a, ls));
+    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i + 1], ls));
+    if (L.side) {
+      MF_CK(cudaEventRecord(F->ev_side, F->side));
+      pending = true;
+    }
+  }
+  if (pending) MF_CK(cudaStreamWaitEvent(F->crit, F->ev_side, 0));
+  MF_CK(cudaEventRecord(F->ev_out, F->crit));
+  MF_CK(cudaStreamWaitEvent(st, F->ev_out, 0));
   return MF_OK;
 }
 
@@ -453,7 +512,8 @@ int mf_factor_numeric(mf_factor* f, const double* values, int32_t values_on_devi
         return rc;
       }
       MF_CK(e);
-      e = cudaGraphInstantiate(&f->gexec, g, 0);
+      // per-node priorities keep the critical path ahead of the bulk updates
+      e = cudaGraphInstantiate(&f->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
       cudaGraphDestroy(g);
       MF_CK(e);
     }

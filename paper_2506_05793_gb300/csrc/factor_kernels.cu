@@ -41,7 +41,8 @@ struct FD {
   T* U;
   unsigned long long* status;
   const int64_t* soff;
-  float* split;
+  float* split;    // staging area 0: rows of 256 floats (two panel slots)
+  float* split_b;  // staging area 1: rows of 512 floats (four slots, lookahead levels)
   T* dinv;
 };
 
@@ -64,6 +65,7 @@ FD<T> make_fd(const FactorArgs& a) {
   d.status = a.status;
   d.soff = a.sym.soff;
   d.split = a.split;
+  d.split_b = a.split_b;
   d.dinv = static_cast<T*>(a.dinv);
   return d;
 }
@@ -455,21 +457,26 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
   }
   if (d.split != nullptr) {
     // FP32 tensor-core path: tf32 hi / lo split of the solved rows, row-major
-    // rows of 256 floats holding two panels (slot = step parity, each 64 hi
-    // then 64 lo floats), zero beyond the panel width b
+    // staging rows holding two panel slots (area 0, slot = step parity) or
+    // four (area 1, lookahead levels, slot = step mod 4), each slot 64 hi
+    // then 64 lo floats; zero beyond the panel width b
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 16; ++q) As[16 * g + q][r] = (16 * g + q) < b ? x[q] : T(0);
     __syncthreads();
-    float* out = d.split + (d.soff[it.s] + r0) * 256 + (it.t & 1) * 128;
+    const int64_t so = d.soff[it.s];
+    const bool area1 = (so >> kSoffAreaShift) != 0;
+    const int64_t srow = so & (((int64_t)1 << kSoffAreaShift) - 1);
+    const int sw = area1 ? 512 : 256;
+    float* out = (area1 ? d.split_b : d.split) + (srow + r0) * sw + (it.t & (area1 ? 3 : 1)) * 128;
     for (int idx = tid; idx < rows * kNB; idx += blockDim.x) {
       const int rw = idx / kNB, c = idx % kNB;
       const float xv = (float)As[c][rw];
       uint32_t hb;
       asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(xv));
       const float hi = __uint_as_float(hb);
-      out[(int64_t)rw * 256 + c] = hi;
-      out[(int64_t)rw * 256 + kNB + c] = xv - hi;
+      out[(int64_t)rw * sw + c] = hi;
+      out[(int64_t)rw * sw + kNB + c] = xv - hi;
     }
   }
 }

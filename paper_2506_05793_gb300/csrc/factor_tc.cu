@@ -117,7 +117,8 @@ struct TcArgs {
 };
 
 __global__ void __launch_bounds__(128, 3)
-    k_syrk_tc(TcArgs<float> d, const __grid_constant__ CUtensorMap smap, int64_t item_off) {
+    k_syrk_tc(TcArgs<float> d, const __grid_constant__ CUtensorMap smap0,
+              const __grid_constant__ CUtensorMap smap1, int area, int64_t item_off) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned operand chunks: A hi, A lo, B hi, B lo (one K-half each)
   const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -145,7 +146,10 @@ __global__ void __launch_bounds__(128, 3)
   const int cmax = mode == 1 ? min(f.k, p0 + kNB) : nf;  // columns updated: [p0, cmax)
   const int nq = mode == 2 ? 4 : 2;                      // K quarters of 32
   const bool diag = it.a == it.b;
-  const int64_t R0 = d.soff[it.s];
+  // staging rows: area 0 holds two panel slots per row, area 1 four
+  const int64_t R0 = d.soff[it.s] & (((int64_t)1 << kSoffAreaShift) - 1);
+  const CUtensorMap* smap = area ? &smap1 : &smap0;
+  const int smask = area ? 3 : 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mb0 = smem_u32(mbar);
 
@@ -224,18 +228,18 @@ __global__ void __launch_bounds__(128, 3)
   for (int q = 0; q < nq; ++q) {
     const uint32_t mb = mb0 + 8 * q, mbt = mb0 + 32 + 8 * q;
     const int h = q & 1;                                           // half of a panel
-    const int slot = (mode == 2 ? tt + (q >> 1) : tt) & 1;        // staging slot of the panel
+    const int slot = (mode == 2 ? tt + (q >> 1) : tt) & smask;    // staging slot of the panel
     const int x0 = slot * 128 + h * 32;
     // rows of the staging buffer beyond the front belong to other fronts (or
     // are zero); they only reach accumulator rows / columns that the
     // epilogue discards
     if (tid == 0) {
       mbar_expect_tx(mbt, (diag ? 2u : 4u) * (uint32_t)kOpBytes);
-      tma_box(a_hi, &smap, x0, R0 + rI, mbt);
-      tma_box(a_lo, &smap, x0 + 64, R0 + rI, mbt);
+      tma_box(a_hi, smap, x0, R0 + rI, mbt);
+      tma_box(a_lo, smap, x0 + 64, R0 + rI, mbt);
       if (!diag) {
-        tma_box(b_hi, &smap, x0, R0 + rJ, mbt);
-        tma_box(b_lo, &smap, x0 + 64, R0 + rJ, mbt);
+        tma_box(b_hi, smap, x0, R0 + rJ, mbt);
+        tma_box(b_lo, smap, x0 + 64, R0 + rJ, mbt);
       }
     }
     ok = ok && mbar_wait(mbt, 0u);
@@ -302,7 +306,7 @@ cudaError_t factor_tc_init() {
   return cudaFuncSetAttribute(k_syrk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
 }
 
-cudaError_t make_split_map(float* split, int64_t rows, void* map_out) {
+cudaError_t make_split_map(float* split, int64_t rows, int width, void* map_out) {
   typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -318,8 +322,8 @@ cudaError_t make_split_map(float* split, int64_t rows, void* map_out) {
     encode = reinterpret_cast<EncodeFn>(fn);
   }
   CUtensorMap m;
-  const cuuint64_t dims[2] = {256, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {256 * sizeof(float)};
+  const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)width * sizeof(float)};
   const cuuint32_t box[2] = {32, 128};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, split, dims, strides, box, estr,
@@ -332,9 +336,10 @@ cudaError_t make_split_map(float* split, int64_t rows, void* map_out) {
 
 cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st) {
   if (L.count <= 0) return cudaSuccess;
-  if (!a.split_map) return cudaErrorInvalidValue;
-  CUtensorMap m;
-  std::memcpy(&m, a.split_map, sizeof(m));
+  if (!a.split_map || !a.split_map_b) return cudaErrorInvalidValue;
+  CUtensorMap m0, m1;
+  std::memcpy(&m0, a.split_map, sizeof(m0));
+  std::memcpy(&m1, a.split_map_b, sizeof(m1));
   TcArgs<float> d;
   d.sn = a.sym.sn;
   d.items = a.sym.items;
@@ -343,7 +348,7 @@ cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st
   d.L = static_cast<float*>(a.L);
   d.U = static_cast<float*>(a.U);
   d.status = a.status;
-  k_syrk_tc<<<L.count, 128, kTcSmem, st>>>(d, m, L.item_off);
+  k_syrk_tc<<<L.count, 128, kTcSmem, st>>>(d, m0, m1, (int)L.area, L.item_off);
   return cudaGetLastError();
 }
 

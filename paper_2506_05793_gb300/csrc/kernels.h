@@ -41,7 +41,9 @@ struct FactorArgs {
   // FP32 tensor-core path: per panel row 64 tf32 "hi" then 64 "lo" floats
   // (row soff[front] + front row); nullptr elsewhere
   float* split;
-  const void* split_map;  // host copy of the TMA tensor map over split (128 bytes)
+  float* split_b;           // four-slot staging rows of lookahead levels
+  const void* split_map;    // host copy of the TMA tensor map over split (128 bytes)
+  const void* split_map_b;  // same over split_b
   // per large front of the level (slot in item field b): 64 x 64 inverse of
   // the current diagonal block of the factor, T
   void* dinv;
@@ -73,9 +75,9 @@ cudaError_t launch_gather_values(int prec, const FactorArgs& a, int64_t nnz_lowe
 // tcgen05 FP32 trailing update (factor_tc.cu)
 cudaError_t factor_tc_init();
 cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st);
-// tensor map (128 bytes, written to map_out) over a split staging buffer of
-// `rows` rows of 128 floats
-cudaError_t make_split_map(float* split, int64_t rows, void* map_out);
+// tensor map (128 bytes, written to map_out) over a staging buffer of
+// `rows` rows of `width` floats (256 or 512)
+cudaError_t make_split_map(float* split, int64_t rows, int width, void* map_out);
 cudaError_t solve_kernels_init(int prec);
 cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStream_t st);
 cudaError_t launch_wait_probe(const int* flag, unsigned long long* status, int limit,

@@ -70,7 +70,19 @@ struct Launch {
   int32_t param;   // small-front size class (max k+m) or step
   int64_t item_off;
   double flops;    // algorithmic flops of this launch
+  // lookahead on levels with few large fronts: `side` launches run on a
+  // second stream, overlapping the next panels' factorization; `join` makes
+  // the main stream wait for the side stream first.  `area` selects the
+  // tensor-core staging area (0: two panel slots, 1: four).
+  int8_t side = 0;
+  int8_t join = 0;
+  int8_t area = 0;
 };
+
+// levels with at most this many large fronts factor with lookahead
+constexpr int kLookaheadFronts = 16;
+// split-buffer offsets carry the staging area in bit 48 and up
+constexpr int kSoffAreaShift = 48;
 
 }  // namespace mf
 
@@ -118,7 +130,8 @@ struct mf_symbolic {
   std::vector<mf::Launch> fsched;
   std::vector<mf::Launch> fsched_tc;  // FP32 with tensor-core trailing updates
   std::vector<int64_t> soff;          // per front: first row in the split buffer
-  int64_t split_rows = 0;
+  int64_t split_rows = 0;    // staging rows of area 0 (2 panel slots per row)
+  int64_t split_rows_b = 0;  // staging rows of area 1 (4 slots, lookahead levels)
   int64_t max_large = 0;              // most large fronts in one level
   // diagonal-block inverses kept for the solve (SpTRSV variant 2): slot of
   // the first 64-column block of each large front (-1 elsewhere), slot count

@@ -605,6 +605,7 @@ void build_schedules(mf_symbolic& S, int small_max) {
   S.fsched_tc.clear();
   S.soff.assign(S.sn.size(), 0);
   S.split_rows = 0;
+  S.split_rows_b = 0;
   S.max_large = 0;
   S.ioff.assign(S.sn.size(), -1);
   S.ninv = 0;
@@ -615,7 +616,8 @@ void build_schedules(mf_symbolic& S, int small_max) {
   for (int64_t s = 0; s < ns; ++s) bylev[S.slevel[s]].push_back((int32_t)s);
   const int classes[3] = {32, 64, 128};
   auto add = [&](std::vector<Launch>& sched, int32_t kind, int32_t lev, int32_t param,
-                 const std::vector<Item>& it, double flops) {
+                 const std::vector<Item>& it, double flops, int side = 0, int join = 0,
+                 int area = 0) {
     if (it.empty()) return;
     Launch L;
     L.kind = kind;
@@ -624,6 +626,9 @@ void build_schedules(mf_symbolic& S, int small_max) {
     L.param = param;
     L.item_off = (int64_t)S.items.size();
     L.flops = flops;
+    L.side = (int8_t)side;
+    L.join = (int8_t)join;
+    L.area = (int8_t)area;
     S.items.insert(S.items.end(), it.begin(), it.end());
     sched.push_back(L);
   };
@@ -682,13 +687,16 @@ void build_schedules(mf_symbolic& S, int small_max) {
     }
     add(S.fsched, K_ASSEMBLE, lev, 0, it, 0.0);
     add(S.fsched_tc, K_ASSEMBLE, lev, 0, it, 0.0);
-    // rows of the split buffer: the level's large fronts side by side
+    // rows of the split buffer: the level's large fronts side by side, in
+    // the four-slot area on lookahead levels
+    const bool la = (int)G.size() <= kLookaheadFronts;
     int64_t srow = 0;
     for (int32_t s : G) {
-      S.soff[s] = srow;
+      S.soff[s] = srow | (la ? (int64_t)1 << kSoffAreaShift : 0);
       srow += S.sn[s].k + S.sn[s].m;
     }
-    S.split_rows = std::max(S.split_rows, srow);
+    if (la) S.split_rows_b = std::max(S.split_rows_b, srow);
+    else S.split_rows = std::max(S.split_rows, srow);
     S.max_large = std::max<int64_t>(S.max_large, (int64_t)G.size());
     if (S.keep_inv)
       for (int32_t s : G) {
@@ -699,6 +707,7 @@ void build_schedules(mf_symbolic& S, int small_max) {
     for (int32_t t = 0; t < T; ++t) {
       std::vector<Item> ip, it3, is, itc;
       double fp = 0, ft = 0, fs = 0, fstc = 0;
+      bool normal_tc = false;  // a tensor-core front takes a plain update this step
       for (size_t gi = 0; gi < G.size(); ++gi) {
         const int32_t s = G[gi];
         // slot of the diagonal-block inverse: per level, or kept per block
@@ -730,6 +739,7 @@ void build_schedules(mf_symbolic& S, int small_max) {
           for (int I = 0; I < nt2; ++I)
             for (int J = 0; J <= I; ++J) itc.push_back({s, t, I, J});
           fstc += full;
+          normal_tc = true;
         } else {
           for (int I = 0; I < nt2; ++I)
             for (int J = 0; J <= I; ++J) itc.push_back({s, (t - 1) | (2 << 24), I, J});
@@ -739,10 +749,36 @@ void build_schedules(mf_symbolic& S, int small_max) {
       }
       add(S.fsched, K_POTRF, lev, t, ip, fp);
       add(S.fsched, K_TRSM, lev, t, it3, ft);
-      add(S.fsched, K_SYRK, lev, t, is, fs);
-      add(S.fsched_tc, K_POTRF, lev, t, ip, fp);
-      add(S.fsched_tc, K_TRSM, lev, t, it3, ft);
-      add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fstc);
+      add(S.fsched_tc, K_POTRF, lev, t, ip, fp, 0, 0, la);
+      add(S.fsched_tc, K_TRSM, lev, t, it3, ft, 0, 0, la);
+      if (!la) {
+        add(S.fsched, K_SYRK, lev, t, is, fs);
+        add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fstc);
+        continue;
+      }
+      // lookahead: the first tile column of a trailing update (the next
+      // panel's columns) runs on the main stream after the side stream has
+      // finished the previous bulk; the other tiles run on the side stream
+      // while the next panel is factored.  The flop split is by tile count.
+      auto split_j0 = [](const std::vector<Item>& v, std::vector<Item>& a, std::vector<Item>& b) {
+        for (const Item& x : v) (x.b == 0 ? a : b).push_back(x);
+      };
+      {
+        std::vector<Item> a, b;
+        split_j0(is, a, b);
+        const double fa = is.empty() ? 0.0 : fs * (double)a.size() / (double)is.size();
+        add(S.fsched, K_SYRK, lev, t, a, fa, 0, 1);
+        add(S.fsched, K_SYRK, lev, t, b, fs - fa, 1, 0);
+      }
+      if ((t & 1) == 1) {  // pair step
+        std::vector<Item> a, b;
+        split_j0(itc, a, b);
+        const double fa = itc.empty() ? 0.0 : fstc * (double)a.size() / (double)itc.size();
+        add(S.fsched_tc, K_SYRK_TC, lev, t, a, fa, 0, 1, 1);
+        add(S.fsched_tc, K_SYRK_TC, lev, t, b, fstc - fa, 1, 0, 1);
+      } else {  // strips touch only the next panel; a plain update waits
+        add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fstc, 0, normal_tc ? 1 : 0, 1);
+      }
     }
   }
   // ---- solves.  Per level and sweep, fronts with k + m <= kWarpSolve go to
