@@ -80,7 +80,7 @@ struct Launch {
 };
 
 // levels with at most this many large fronts factor with lookahead
-constexpr int kLookaheadFronts = 16;
+constexpr int kLookaheadFronts = 64;
 // split-buffer offsets carry the staging area in bit 48 and up
 constexpr int kSoffAreaShift = 48;
 

@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
 // ---------------------------------------------------------------------------
 // Backward, one 64-column pivot block c of a large front:
 //   x_c = L_cc^{-T} (y'_c - sum_{a>c} L_ac^T x_a),
-// y' = y - L21[:, c]^T x(update rows), already formed by k_bw_gemv /
+// y' = y - L21[:, c]^T x(update rows), already formed by k_bw_gemv1 /
 // k_bw_gemm; later blocks are awaited through their flags.  Thread (col, g)
 // holds rows 16 g .. 16 g + 15 of its column of the current 64-row tile in
 // registers; the next tile is loaded while the block waits.
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   const T* Lcol = Lp + (int64_t)(c0 + (live ? col : 0)) * nf;
   const int PB = (k + kNB - 1) / kNB;
   // tiles: the later pivot blocks of the front, last first (the update rows
-  // were subtracted from y by k_bw_gemv / k_bw_gemm)
+  // were subtracted from y by k_bw_gemv1 / k_bw_gemm)
   const int ntiles = PB - 1 - c0 / kNB;
   T Lc[16];
   {
@@ -533,67 +533,84 @@ __global__ void __launch_bounds__(256) k_fw_gemv(SD<T> d, int64_t item_off) {
   }
 }
 
-// Backward, one 64-column block [c0, c0 + bs) of a front:
-//   y(c0 + c) -= L21(:, c0 + c)^T x2,
-// x2 = the final x of the front's update rows (ancestors), staged in chunks
-// of kGemvStage / R rows.  Each warp streams CW columns at a time, lanes
-// along the rows (coalesced), and reduces each column with a warp sum.
-template <typename T, int R>
-__global__ void __launch_bounds__(256) k_bw_gemv(SD<T> d, int64_t item_off) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[i * R + r]
-  T* part = xs + kGemvStage;               // part[c * R + r]
-  constexpr int CH = kGemvStage / R;
-  constexpr int CW = R == 1 ? 8 : (R <= 8 ? 2 : 1);
-  const Item it = d.items[item_off + blockIdx.x];
+// One right-hand side, four CTAs per item (more CTAs for the few, tall
+// fronts of the upper levels).  Forward: CTA (item, sub) takes rows
+// r0 + 16 sub .. + 16 of the item's 64 update rows, thread (row, g) sums the
+// columns j = g (mod 16); the 16 partial sums of a row are added in a fixed
+// order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fw_gemv1(SD<T> d, int64_t item_off) {
+  __shared__ T red[16][17];
+  const int sub = blockIdx.x & 3;
+  const Item it = d.items[item_off + (blockIdx.x >> 2)];
+  const int rows = min(16, it.b - 16 * sub);
+  if (rows <= 0) return;  // whole CTA
   const SnInfo f = d.sn[it.s];
-  const int k = f.k, m = f.m, nf = k + m, nrhs = d.nrhs;
-  const int c0 = it.a, bs = it.b;
+  const int k = f.k, nf = k + f.m;
+  const int r0 = it.a + 16 * sub;
+  const int tid = threadIdx.x, row = tid & 15, g = tid >> 4;
+  const bool live = row < rows;
+  const T* Lr = d.L + f.Loff + r0 + (live ? row : 0);
+  const T* yx = d.Y + f.first;  // the front's solved pivots
+  T a0 = T(0), a1 = T(0);
+  int j = g;
+  for (; j + 16 < k; j += 32) {
+    a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
+    a1 = fma(Lr[(int64_t)(j + 16) * nf], yx[j + 16], a1);
+  }
+  if (j < k) a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
+  red[g][row] = a0 + a1;
+  __syncthreads();
+  if (tid < rows) {
+    T sum = T(0);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) sum += red[q][tid];
+    const int64_t gi = f.woff + r0 + tid;
+    T w = T(0);
+    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e) w += d.W[d.ginv_src[e]];
+    d.W[gi] = w - sum;
+  }
+}
+
+// Backward, one right-hand side: CTA (item, sub) takes columns
+// c0 + 16 sub .. + 16 of the item's 64; its eight warps split the update
+// rows (lane-consecutive rows, coalesced), each lane keeps 16 column sums,
+// and the warps' sums are added in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bw_gemv1(SD<T> d, int64_t item_off) {
+  __shared__ T red[8][16];
+  const int sub = blockIdx.x & 3;
+  const Item it = d.items[item_off + (blockIdx.x >> 2)];
+  const int nc = min(16, it.b - 16 * sub);
+  if (nc <= 0) return;  // whole CTA
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, m = f.m, nf = k + m;
+  const int c0 = it.a + 16 * sub;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T* Lp = d.L + f.Loff;
+  const T* Lb = d.L + f.Loff + (int64_t)c0 * nf + k;
   const int32_t* frow = d.rowidx + f.rows_off + k;
-  for (int idx = tid; idx < kNB * R; idx += blockDim.x) part[idx] = T(0);
-  for (int i0 = 0; i0 < m; i0 += CH) {
-    const int ch = min(CH, m - i0);
-    __syncthreads();
-    for (int idx = tid; idx < ch * nrhs; idx += blockDim.x) {
-      const int i = idx % ch, r = idx / ch;
-      xs[i * R + r] = d.Y[(int64_t)r * d.n + frow[i0 + i]];
-    }
-    __syncthreads();
-    for (int cb = warp * CW; cb < bs; cb += 8 * CW) {
-      T a[CW][R];
+  T acc[16];
 #pragma unroll
-      for (int q = 0; q < CW; ++q)
+  for (int q = 0; q < 16; ++q) acc[q] = T(0);
+  for (int i = warp * 32 + lane; i < m; i += 256) {
+    const T xi = d.Y[frow[i]];
+    T lv[16];
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[q][r] = T(0);
-      const T* Lc = Lp + (int64_t)(c0 + cb) * nf + k + i0;
-#pragma unroll 2
-      for (int i = lane; i < ch; i += 32) {
-        T l[CW];
+    for (int q = 0; q < 16; ++q) lv[q] = q < nc ? Lb[(int64_t)q * nf + i] : T(0);
 #pragma unroll
-        for (int q = 0; q < CW; ++q) l[q] = cb + q < bs ? Lc[(int64_t)q * nf + i] : T(0);
+    for (int q = 0; q < 16; ++q) acc[q] = fma(lv[q], xi, acc[q]);
+  }
 #pragma unroll
-        for (int q = 0; q < CW; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            if (r < nrhs) a[q][r] = fma(l[q], xs[i * R + r], a[q][r]);
-      }
-#pragma unroll
-      for (int q = 0; q < CW; ++q)
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (r < nrhs) {
-            const T sum = warp_sum(a[q][r]);
-            if (lane == 0 && cb + q < bs) part[(cb + q) * R + r] += sum;
-          }
-        }
-    }
+  for (int q = 0; q < 16; ++q) {
+    const T v = warp_sum(acc[q]);
+    if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
-  for (int idx = tid; idx < bs * nrhs; idx += blockDim.x) {
-    const int c = idx / nrhs, r = idx % nrhs;
-    d.Y[(int64_t)r * d.n + f.first + c0 + c] -= part[c * R + r];
+  if (tid < nc) {
+    T sum = T(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += red[w][tid];
+    d.Y[f.first + c0 + tid] -= sum;
   }
 }
 
@@ -1024,9 +1041,6 @@ cudaError_t init_r() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fw_gemv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)gemv_smem<T, R>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_bw_gemv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)gemv_smem<T, R>());
   if constexpr (R >= 8) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_bw_gemm<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1052,12 +1066,14 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   else if (L.kind == K_BW_LEVEL)
     k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(
         d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
-  else if (L.kind == K_FW_GEMV)
-    k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
+  else if (L.kind == K_FW_GEMV) {
+    if constexpr (R == 1) k_fw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
+    else k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
+  }
   else if constexpr (R >= 8)
     k_bw_gemm<T, R><<<L.count, 256, bw_gemm_smem<T, R>(), st>>>(d, L.item_off);
   else
-    k_bw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
+    k_bw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
 }
 
 template <typename T, int H>
