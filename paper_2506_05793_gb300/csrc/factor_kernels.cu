@@ -245,9 +245,16 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
   const int b = min(kNB, f.k - c0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   load_diag_block<T, 256>(d, f, c0, b, D, ld);
-  for (int idx = tid; idx < kNB * ld; idx += blockDim.x) Y[idx] = T(0);
+  // only the 16-column blocks holding real pivots are factored and
+  // inverted; beyond them the padded block is the identity, and so is its
+  // inverse
+  const int nbk = (b + kPB - 1) / kPB, bend = nbk * kPB;
+  for (int idx = tid; idx < kNB * ld; idx += blockDim.x) {
+    const int c = idx / ld, r = idx % ld;
+    Y[idx] = (c >= bend && r == c) ? T(1) : T(0);
+  }
   __syncthreads();
-  for (int j0 = 0; j0 < kNB; j0 += kPB) {
+  for (int j0 = 0; j0 < bend; j0 += kPB) {
     // (a) diagonal block: lane r < 16 owns row j0 + r
     if (warp == 0) {
       const int r = lane;
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
       }
     }
     __syncthreads();
-    const int base = j0 + kPB, n2 = kNB - base;
+    const int base = j0 + kPB, n2 = bend - base;
     if (n2 == 0) break;
     // (b) L_iB = A_iB Y_BB^T for rows i >= base: element e -> (i, t)
     {
@@ -348,8 +355,8 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
   }
   // off-diagonal blocks of the inverse, by block distance
   const int r = tid & (kPB - 1), c = tid >> 4;  // element (r, c) of a 16 x 16 block
-  for (int dd = 1; dd < kNB / kPB; ++dd) {
-    const int nb = kNB / kPB - dd;
+  for (int dd = 1; dd < nbk; ++dd) {
+    const int nb = nbk - dd;
     for (int m = 0; m < nb; ++m) {
       const int bi = m + dd, bj = m;
       T s = T(0);
