@@ -66,7 +66,8 @@ typedef struct mf_factor mf_factor;
 typedef struct mf_options {
   int32_t small_front_max;  /* fronts with k+m <= this run in one CTA (<=128) */
   int32_t use_graphs;       /* 1: capture the factorization in a CUDA graph */
-  int32_t profile;          /* 1: time every launch with CUDA events */
+  int32_t profile;          /* 1: time every launch with CUDA events (recorded
+                               inside the CUDA graph when graphs are on) */
   int32_t relax;            /* 1: relaxed amalgamation of the internal fronts */
   int64_t budget_bytes;     /* device bytes a factor may hold (0 = no limit) */
   int32_t tc;               /* 1: FP32 trailing updates on tcgen05 tensor cores

@@ -426,7 +426,10 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   return MF_OK;
 }
 
-static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile) {
+// Enqueue the numeric factorization on st.  With `capturing` the calls are
+// being recorded into a CUDA graph: profile events then become event-record
+// nodes of the graph, so per-launch timing also works for graph replays.
+static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capturing) {
   const mf_symbolic* S = F->S;
   mf::FactorArgs a;
   a.sym = F->ds->d;
@@ -477,9 +480,10 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile) {
       MF_CK(cudaStreamWaitEvent(F->side, F->ev_fork, 0));
       ls = F->side;
     }
-    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i], ls));
+    const unsigned rec = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (profile) MF_CK(cudaEventRecordWithFlags(F->ev[2 * i], ls, rec));
     MF_CK(mf::launch_factor(F->prec, L, a, ls));
-    if (profile) MF_CK(cudaEventRecord(F->ev[2 * i + 1], ls));
+    if (profile) MF_CK(cudaEventRecordWithFlags(F->ev[2 * i + 1], ls, rec));
     if (L.side) {
       MF_CK(cudaEventRecord(F->ev_side, F->side));
       pending = true;
@@ -500,11 +504,11 @@ int mf_factor_numeric(mf_factor* f, const double* values, int32_t values_on_devi
     MF_CK(cudaMemcpyAsync(f->vals, values, S->nnzA * sizeof(double),
                           values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   const bool profile = f->h->opt.profile != 0;
-  if (f->h->opt.use_graphs && !profile) {
+  if (f->h->opt.use_graphs) {
     if (!f->gexec) {
       MF_CK(cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking));
       MF_CK(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
-      int rc = enqueue_factor(f, f->cap_stream, false);
+      int rc = enqueue_factor(f, f->cap_stream, profile, true);
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamEndCapture(f->cap_stream, &g);
       if (rc != MF_OK) {
@@ -519,7 +523,7 @@ int mf_factor_numeric(mf_factor* f, const double* values, int32_t values_on_devi
     }
     MF_CK(cudaGraphLaunch(f->gexec, st));
   } else {
-    int rc = enqueue_factor(f, st, profile);
+    int rc = enqueue_factor(f, st, profile, false);
     if (rc != MF_OK) return rc;
   }
   f->numeric_done = true;

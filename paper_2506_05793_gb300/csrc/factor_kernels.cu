@@ -444,12 +444,13 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
   }
   __syncthreads();
   // thread (r, g): row r, the 16 contiguous columns j = 16 g + q; the product
-  // is triangular (c <= j), so c stops at the thread's last column
+  // is triangular (c <= j), so c stops at the thread's last column, and at
+  // the panel width b (A is zero beyond it; columns j >= b stay zero)
   T x[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) x[q] = T(0);
-  const int jlast = 16 * g + 15;
-  for (int c = 0; c <= jlast; ++c) {
+  const int cend = 16 * g < b ? min(16 * g + 15, b - 1) : -1;
+  for (int c = 0; c <= cend; ++c) {
     const T a = As[c][r];
     const T* lrow = &Li[c][16 * g];
 #pragma unroll

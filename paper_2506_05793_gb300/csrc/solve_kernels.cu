@@ -992,15 +992,24 @@ __global__ void k_perm_out(const T* Y, const int32_t* perm, double* X, int64_t l
   }
 }
 
-// atomic max for non-negative doubles through their IEEE bit patterns
+// atomic max for non-negative doubles through their IEEE bit patterns (the
+// order of non-negative doubles is that of their bits); shared or global
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// The max-norms are reduced per block in shared memory first, then one
+// global atomic per block and value: a global atomic per row would serialize
+// millions of updates on the same address.
+
 // one warp per row: r = b - A x, plus max |r| and max |x| per RHS
+// (dynamic shared memory: 2 nrhs doubles)
 __global__ void k_residual(const int64_t* rowptr, const int32_t* colind, const double* vals,
                            int64_t n, const double* B, int64_t ldb, const double* X, int64_t ldx,
                            double* R, int nrhs, double* rnorm, double* xnorm) {
+  extern __shared__ double smax[];  // [0, nrhs): |r|, [nrhs, 2 nrhs): |x|
+  for (int i = threadIdx.x; i < 2 * nrhs; i += blockDim.x) smax[i] = 0.0;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1013,22 +1022,36 @@ __global__ void k_residual(const int64_t* rowptr, const int32_t* colind, const d
       if (lane == 0) {
         const double res = B[r * ldb + row] - s;
         R[r * n + row] = res;
-        atomic_max_nonneg(&rnorm[r], fabs(res));
-        atomic_max_nonneg(&xnorm[r], fabs(x[row]));
+        atomic_max_nonneg(&smax[r], fabs(res));
+        atomic_max_nonneg(&smax[nrhs + r], fabs(x[row]));
       }
     }
   }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+    atomic_max_nonneg(&rnorm[r], smax[r]);
+    atomic_max_nonneg(&xnorm[r], smax[nrhs + r]);
+  }
 }
 
+// max row sum of |A| into out[0], max |b_r| into out[1 + r]
+// (dynamic shared memory: 1 + nrhs doubles)
 __global__ void k_norms(const int64_t* rowptr, const double* vals, int64_t n, const double* B,
                         int64_t ldb, int nrhs, double* out) {
+  extern __shared__ double smax[];
+  for (int i = threadIdx.x; i < 1 + nrhs; i += blockDim.x) smax[i] = 0.0;
+  __syncthreads();
+  double amax = 0.0;
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
        row += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int64_t p = rowptr[row]; p < rowptr[row + 1]; ++p) s += fabs(vals[p]);
-    atomic_max_nonneg(&out[0], s);
-    for (int r = 0; r < nrhs; ++r) atomic_max_nonneg(&out[1 + r], fabs(B[r * ldb + row]));
+    amax = fmax(amax, s);
+    for (int r = 0; r < nrhs; ++r) atomic_max_nonneg(&smax[1 + r], fabs(B[r * ldb + row]));
   }
+  atomic_max_nonneg(&smax[0], amax);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 1 + nrhs; i += blockDim.x) atomic_max_nonneg(&out[i], smax[i]);
 }
 
 template <typename T, int R>
@@ -1163,13 +1186,15 @@ cudaError_t launch_residual(const int64_t* rowptr, const int32_t* colind, const 
   int64_t g = (n * 32 + 255) / 256;
   if (g > 152 * 32) g = 152 * 32;
   if (g < 1) g = 1;
-  k_residual<<<(int)g, 256, 0, st>>>(rowptr, colind, vals, n, B, ldb, X, ldx, R, nrhs, rnorm, xnorm);
+  k_residual<<<(int)g, 256, 2 * (size_t)nrhs * sizeof(double), st>>>(rowptr, colind, vals, n, B, ldb,
+                                                                      X, ldx, R, nrhs, rnorm, xnorm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_norms(const int64_t* rowptr, const double* vals, int64_t n, const double* B,
                          int64_t ldb, int32_t nrhs, double* out, cudaStream_t st) {
-  k_norms<<<grid_for(n), 256, 0, st>>>(rowptr, vals, n, B, ldb, nrhs, out);
+  k_norms<<<grid_for(n), 256, (1 + (size_t)nrhs) * sizeof(double), st>>>(rowptr, vals, n, B, ldb,
+                                                                         nrhs, out);
   return cudaGetLastError();
 }
 
