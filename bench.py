@@ -191,12 +191,13 @@ class ClockSampler:
 
 
 # DRAM traffic of the dominant FP64 kernel, from one ncu pass
-# (dram__bytes_read.sum + dram__bytes_write.sum) over all 377 k_syrk launches
-# of one FP64 factorization of the default Q1 workload: 230.9 GB read +
-# 199.0 GB written.  Reported per launch, like `achieved`; valid only while
-# the kernel's source text is the one measured (SHA-1 below).
+# (dram__bytes_read.sum + dram__bytes_write.sum) over all 717 k_syrk launches
+# of one FP64 factorization of the default Q1 workload: 234.5 GB read +
+# 195.6 GB written.  Reported per launch, like `achieved`; valid only while
+# the kernel's source text is the one measured (SHA-1 below) and the
+# factorization issues the same number of launches.
 SYRK_TRAFFIC = {"workload": "q1_extruded_256x256x10_2dof_hnd", "prec": "fp64",
-                "bytes_per_launch": (230.88e9 + 198.97e9) / 377,
+                "launches": 717, "bytes_per_launch": (234.48e9 + 195.60e9) / 717,
                 "source_sha1": "59cc60931be4e84f3320740ff8aa588657291de9"}
 
 
@@ -462,6 +463,7 @@ def main():
         src = "measured bf16 %.0f TFLOP/s x nominal FP64/bf16 1.25/2250" % bf16
     traffic = None
     if (dom == "syrk" and args.prec == "fp64" and workload_name(args) == SYRK_TRAFFIC["workload"]
+            and prof["syrk"]["launches"] == SYRK_TRAFFIC["launches"]
             and kernel_source_sha1(os.path.join(ROOT, "paper_2506_05793_gb300", "csrc",
                                                 "factor_kernels.cu"), "k_syrk(FD<T> d")
             == SYRK_TRAFFIC["source_sha1"]):
