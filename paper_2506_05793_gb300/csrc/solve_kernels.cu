@@ -103,11 +103,14 @@ __device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* st
   __syncthreads();
 }
 
-// Every thread fences its own writes, then one release store publishes.
+// The CTA barrier orders every thread's writes before thread 0, whose
+// fence and release store publish them at GPU scope (release is cumulative).
 __device__ __forceinline__ void cta_publish(int* flag) {
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) st_release(flag, 1);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flag, 1);
+  }
 }
 
 template <typename T, int R>
@@ -367,6 +370,15 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
     }
     if (islot < 0 && tid < bs) rinv[tid] = T(1) / P[(int64_t)tid * nf + tid];
   }
+  // the block's own y' (final before this launch) is loaded up front, off the
+  // critical path of the chain
+  constexpr int YP = (kNB * R + 255) / 256;
+  T ypre[YP];
+#pragma unroll
+  for (int u = 0; u < YP; ++u) {
+    const int idx = tid + 256 * u;
+    ypre[u] = idx < bs * nrhs ? d.Y[(int64_t)(idx / bs) * d.n + f.first + c0 + idx % bs] : T(0);
+  }
   T acc[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = T(0);
@@ -409,11 +421,14 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
   for (int r = 0; r < R; ++r)
     if (r < nrhs) red[(g * kNB + col) * R + r] = acc[r];
   __syncthreads();
-  for (int idx = tid; idx < bs * nrhs; idx += blockDim.x) {
+#pragma unroll
+  for (int u = 0; u < YP; ++u) {
+    const int idx = tid + 256 * u;
+    if (idx >= bs * nrhs) break;
     const int c = idx % bs, r = idx / bs;
     const T sum = red[(0 * kNB + c) * R + r] + red[(1 * kNB + c) * R + r] +
                   red[(2 * kNB + c) * R + r] + red[(3 * kNB + c) * R + r];
-    xs[c * R + r] = d.Y[(int64_t)r * d.n + f.first + c0 + c] - sum;
+    xs[c * R + r] = ypre[u] - sum;
   }
   __syncthreads();
   if (islot >= 0) {
