@@ -134,7 +134,7 @@ constexpr size_t bw_level_smem() {
 // while the block waits for x_a, so the DRAM latency is off the critical path.
 // ---------------------------------------------------------------------------
 template <typename T, int R>
-__global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
+__global__ void __launch_bounds__(256, 2)
     k_fw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);  // xs[q * R + r]
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
 // registers; the next tile is loaded while the block waits.
 // ---------------------------------------------------------------------------
 template <typename T, int R>
-__global__ void __launch_bounds__(256, R > 8 ? 1 : 2)
+__global__ void __launch_bounds__(256, 2)
     k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ld = kNB + 1;
