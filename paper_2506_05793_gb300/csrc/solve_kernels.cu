@@ -113,13 +113,50 @@ __device__ __forceinline__ void cta_publish(int* flag) {
   }
 }
 
+// Row pitches of the per-RHS shared arrays: padded so that lanes stepping
+// through rows do not hit the same bank (xs rows stay 16-byte aligned).
+template <int R>
+constexpr int xs_pitch() { return R == 1 ? 1 : R + 4; }
+template <int R>
+constexpr int red_pitch() { return R == 1 ? 1 : R + 1; }
+
+// acc[r] += l * xq[r] for the R right-hand sides of one staged row; for
+// R >= 4 the row (16-byte aligned, pitch xs_pitch) is read 16 bytes at a
+// time.  Lanes beyond the caller's nrhs accumulate values that are never
+// written out.
+template <typename T, int R>
+__device__ __forceinline__ void axpy_row(T (&acc)[R], T l, const T* xq) {
+  if constexpr (R < 4) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = fma(l, xq[r], acc[r]);
+  } else if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int r = 0; r < R; r += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(xq + r);
+      acc[r] = fma(l, v.x, acc[r]);
+      acc[r + 1] = fma(l, v.y, acc[r + 1]);
+      acc[r + 2] = fma(l, v.z, acc[r + 2]);
+      acc[r + 3] = fma(l, v.w, acc[r + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(xq + r);
+      acc[r] = fma(l, v.x, acc[r]);
+      acc[r + 1] = fma(l, v.y, acc[r + 1]);
+    }
+  }
+}
+
 template <typename T, int R>
 constexpr size_t fw_level_smem() {
-  return ((size_t)6 * kNB * R + (size_t)kNB * (kNB + 1) + kNB) * sizeof(T);
+  return ((size_t)kNB * xs_pitch<R>() + (size_t)kNB * R + (size_t)4 * kNB * red_pitch<R>() +
+          (size_t)kNB * (kNB + 1) + kNB) * sizeof(T);
 }
 template <typename T, int R>
 constexpr size_t bw_level_smem() {
-  return ((size_t)5 * kNB * R + (size_t)kNB * (kNB + 1) + kNB) * sizeof(T);
+  return ((size_t)kNB * xs_pitch<R>() + (size_t)4 * kNB * red_pitch<R>() +
+          (size_t)kNB * (kNB + 1) + kNB) * sizeof(T);
 }
 
 // ---------------------------------------------------------------------------
@@ -137,10 +174,11 @@ template <typename T, int R>
 __global__ void __launch_bounds__(256, 2)
     k_fw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[q * R + r]
-  T* ws = xs + kNB * R;                    // ws[row * R + r]  gathered w
-  T* red = ws + kNB * R;                   // red[(g * kNB + row) * R + r]
-  T* D = red + 4 * kNB * R;                // D[c * (kNB + 1) + i] = L(r0 + i, r0 + c)
+  constexpr int RX = xs_pitch<R>(), RP = red_pitch<R>();
+  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[q * RX + r]
+  T* ws = xs + kNB * RX;                   // ws[row * R + r]  gathered w
+  T* red = ws + kNB * R;                   // red[(g * kNB + row) * RP + r]
+  T* D = red + 4 * kNB * RP;               // D[c * (kNB + 1) + i] = L(r0 + i, r0 + c)
   T* rinv = D + kNB * (kNB + 1);
   constexpr int ld = kNB + 1;
   __shared__ int s_item;
@@ -225,17 +263,13 @@ __global__ void __launch_bounds__(256, 2)
     const int bsa = min(kNB, k - a * kNB);
     for (int idx = tid; idx < bsa * nrhs; idx += blockDim.x) {
       const int r = idx / bsa, q = idx % bsa;
-      xs[q * R + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + a * kNB + q);
+      xs[q * RX + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + a * kNB + q);
     }
     __syncthreads();
 #pragma unroll
     for (int qq = 0; qq < 16; ++qq) {
       const int q = g * 16 + qq;
-      if (q < bsa) {
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (r < nrhs) acc[r] = fma(Lc[qq], xs[q * R + r], acc[r]);
-      }
+      if (q < bsa) axpy_row<T, R>(acc, Lc[qq], xs + q * RX);
     }
     __syncthreads();
 #pragma unroll
@@ -243,13 +277,13 @@ __global__ void __launch_bounds__(256, 2)
   }
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (r < nrhs) red[(g * kNB + row) * R + r] = acc[r];
+    if (r < nrhs) red[(g * kNB + row) * RP + r] = acc[r];
   __syncthreads();
   for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
     const int rw = idx / nrhs, r = idx % nrhs;
-    const T sum = red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
-                  red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
-    xs[rw * R + r] = ws[rw * R + r] - sum;
+    const T sum = red[(0 * kNB + rw) * RP + r] + red[(1 * kNB + rw) * RP + r] +
+                  red[(2 * kNB + rw) * RP + r] + red[(3 * kNB + rw) * RP + r];
+    xs[rw * RX + r] = ws[rw * R + r] - sum;
   }
   __syncthreads();
   if (islot >= 0) {
@@ -260,22 +294,17 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int qq = 0; qq < 16; ++qq) {
       const int c = g * 16 + qq;
-      if (c < rows) {
-        const T dv = D[c * ld + row];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (r < nrhs) a2[r] = fma(dv, xs[c * R + r], a2[r]);
-      }
+      if (c < rows) axpy_row<T, R>(a2, D[c * ld + row], xs + c * RX);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (r < nrhs) red[(g * kNB + row) * R + r] = a2[r];
+      if (r < nrhs) red[(g * kNB + row) * RP + r] = a2[r];
     __syncthreads();
     for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
       const int rw = idx / nrhs, r = idx % nrhs;
       d.Y[(int64_t)r * d.n + f.first + r0 + rw] =
-          red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
-          red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
+          red[(0 * kNB + rw) * RP + r] + red[(1 * kNB + rw) * RP + r] +
+          red[(2 * kNB + rw) * RP + r] + red[(3 * kNB + rw) * RP + r];
     }
     cta_publish(fl + r0 / kNB);
     return;
@@ -283,8 +312,8 @@ __global__ void __launch_bounds__(256, 2)
   // column-oriented substitution, one warp per right-hand side; lane owns
   // rows lane and lane + 32 of the block
   for (int r = warp; r < nrhs; r += 8) {
-    T v0 = lane < rows ? xs[lane * R + r] : T(0);
-    T v1 = lane + 32 < rows ? xs[(lane + 32) * R + r] : T(0);
+    T v0 = lane < rows ? xs[lane * RX + r] : T(0);
+    T v1 = lane + 32 < rows ? xs[(lane + 32) * RX + r] : T(0);
     for (int j = 0; j < rows; ++j) {
       const T xj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31) * rinv[j];
       if (j < 32) {
@@ -315,9 +344,10 @@ __global__ void __launch_bounds__(256, 2)
     k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ld = kNB + 1;
-  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[i * R + r]
-  T* red = xs + kNB * R;                   // red[(g * kNB + c) * R + r]
-  T* Dt = red + 4 * kNB * R;               // Dt[j * ld + c] = L(c0 + j, c0 + c)
+  constexpr int RX = xs_pitch<R>(), RP = red_pitch<R>();
+  T* xs = reinterpret_cast<T*>(smem_raw);  // xs[i * RX + r]
+  T* red = xs + kNB * RX;                  // red[(g * kNB + c) * RP + r]
+  T* Dt = red + 4 * kNB * RP;              // Dt[j * ld + c] = L(c0 + j, c0 + c)
   T* rinv = Dt + kNB * ld;
   __shared__ int s_item;
   if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -401,17 +431,13 @@ __global__ void __launch_bounds__(256, 2)
     cta_wait(fl + i0 / kNB, d.status);
     for (int idx = tid; idx < ti * nrhs; idx += blockDim.x) {
       const int i = idx % ti, r = idx / ti;
-      xs[i * R + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + i0 + i);
+      xs[i * RX + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + i0 + i);
     }
     __syncthreads();
 #pragma unroll
     for (int ii = 0; ii < 16; ++ii) {
       const int i = g * 16 + ii;
-      if (i < ti) {
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (r < nrhs) acc[r] = fma(Lc[ii], xs[i * R + r], acc[r]);
-      }
+      if (i < ti) axpy_row<T, R>(acc, Lc[ii], xs + i * RX);
     }
     __syncthreads();
 #pragma unroll
@@ -419,16 +445,16 @@ __global__ void __launch_bounds__(256, 2)
   }
 #pragma unroll
   for (int r = 0; r < R; ++r)
-    if (r < nrhs) red[(g * kNB + col) * R + r] = acc[r];
+    if (r < nrhs) red[(g * kNB + col) * RP + r] = acc[r];
   __syncthreads();
 #pragma unroll
   for (int u = 0; u < YP; ++u) {
     const int idx = tid + 256 * u;
     if (idx >= bs * nrhs) break;
     const int c = idx % bs, r = idx / bs;
-    const T sum = red[(0 * kNB + c) * R + r] + red[(1 * kNB + c) * R + r] +
-                  red[(2 * kNB + c) * R + r] + red[(3 * kNB + c) * R + r];
-    xs[c * R + r] = ypre[u] - sum;
+    const T sum = red[(0 * kNB + c) * RP + r] + red[(1 * kNB + c) * RP + r] +
+                  red[(2 * kNB + c) * RP + r] + red[(3 * kNB + c) * RP + r];
+    xs[c * RX + r] = ypre[u] - sum;
   }
   __syncthreads();
   if (islot >= 0) {
@@ -440,22 +466,17 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int qq = 0; qq < 16; ++qq) {
       const int j = g * 16 + qq;
-      if (j < bs) {
-        const T dv = Dt[j * ld + col];
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (r < nrhs) a2[r] = fma(dv, xs[j * R + r], a2[r]);
-      }
+      if (j < bs) axpy_row<T, R>(a2, Dt[j * ld + col], xs + j * RX);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (r < nrhs) red[(g * kNB + col) * R + r] = a2[r];
+      if (r < nrhs) red[(g * kNB + col) * RP + r] = a2[r];
     __syncthreads();
     for (int idx = tid; idx < bs * nrhs; idx += blockDim.x) {
       const int c = idx / nrhs, r = idx % nrhs;
       d.Y[(int64_t)r * d.n + f.first + c0 + c] =
-          red[(0 * kNB + c) * R + r] + red[(1 * kNB + c) * R + r] +
-          red[(2 * kNB + c) * R + r] + red[(3 * kNB + c) * R + r];
+          red[(0 * kNB + c) * RP + r] + red[(1 * kNB + c) * RP + r] +
+          red[(2 * kNB + c) * RP + r] + red[(3 * kNB + c) * RP + r];
     }
     cta_publish(fl + c0 / kNB);
     return;
@@ -463,8 +484,8 @@ __global__ void __launch_bounds__(256, 2)
   // right-looking substitution with L_cc^T, one warp per right-hand side;
   // lane owns columns lane and lane + 32 of the block
   for (int r = warp; r < nrhs; r += 8) {
-    T v0 = lane < bs ? xs[lane * R + r] : T(0);
-    T v1 = lane + 32 < bs ? xs[(lane + 32) * R + r] : T(0);
+    T v0 = lane < bs ? xs[lane * RX + r] : T(0);
+    T v1 = lane + 32 < bs ? xs[(lane + 32) * RX + r] : T(0);
     for (int j = bs - 1; j >= 0; --j) {
       const T xj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31) * rinv[j];
       if (j < 32) {
