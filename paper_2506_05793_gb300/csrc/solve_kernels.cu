@@ -711,11 +711,12 @@ __global__ void __launch_bounds__(256) k_bw_gemm(SD<T> d, int64_t item_off) {
 // ---------------------------------------------------------------------------
 // Fronts with k + m <= 64: one warp per front (8 per CTA), few registers so
 // that many fronts are in flight.  Lane l owns front rows l and l + 32.  The
-// work vector of front s lives in W[(woff_s + i) * nrhs + r].
+// work vector of front s lives in W[(woff_s + i) * nrhs + r].  Right-hand
+// sides go in blocks of RB, so every column of L loaded serves RB of them.
 // Forward: gather w, then for each pivot j: x_j = w_j / L_jj and
 // w_i -= L_ij x_j below it (the next column is loaded while this one is used).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int RB>
 __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int64_t count) {
   const int lane = threadIdx.x & 31;
   const int64_t w_id = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -726,19 +727,23 @@ __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int6
   const int i0 = lane, i1 = lane + 32;
   const T rd0 = i0 < k ? T(1) / Lp[(int64_t)i0 * nf + i0] : T(0);
   const T rd1 = i1 < k ? T(1) / Lp[(int64_t)i1 * nf + i1] : T(0);
-  for (int r = 0; r < nrhs; ++r) {
-    T w[2];
+  const int64_t g0 = f.woff + i0, g1 = f.woff + i1;
+  const int64_t e00 = i0 < nf ? d.ginv_ptr[g0] : 0, e01 = i0 < nf ? d.ginv_ptr[g0 + 1] : 0;
+  const int64_t e10 = i1 < nf ? d.ginv_ptr[g1] : 0, e11 = i1 < nf ? d.ginv_ptr[g1 + 1] : 0;
+  for (int rb = 0; rb < nrhs; rb += RB) {
+    T w0[RB], w1[RB];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = lane + 32 * h;
-      T v = T(0);
-      if (i < nf) {
-        v = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
-        const int64_t gi = f.woff + i;
-        for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e)
-          v += d.W[d.ginv_src[e] * nrhs + r];
+    for (int q = 0; q < RB; ++q) {
+      const int r = rb + q;
+      T v0 = T(0), v1 = T(0);
+      if (r < nrhs) {
+        if (i0 < k) v0 = d.Y[(int64_t)r * d.n + f.first + i0];
+        if (i1 < k) v1 = d.Y[(int64_t)r * d.n + f.first + i1];
+        for (int64_t e = e00; e < e01; ++e) v0 += d.W[d.ginv_src[e] * nrhs + r];
+        for (int64_t e = e10; e < e11; ++e) v1 += d.W[d.ginv_src[e] * nrhs + r];
       }
-      w[h] = v;
+      w0[q] = v0;
+      w1[q] = v1;
     }
     T c0 = i0 < nf ? Lp[i0] : T(0), c1 = i1 < nf ? Lp[i1] : T(0);
     for (int j = 0; j < k; ++j) {
@@ -749,19 +754,25 @@ __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int6
         n1 = i1 < nf ? nc[i1] : T(0);
       }
       const T rj = __shfl_sync(0xffffffffu, j < 32 ? rd0 : rd1, j & 31);
-      const T xj = __shfl_sync(0xffffffffu, j < 32 ? w[0] : w[1], j & 31) * rj;
-      if (i0 == j) w[0] = xj;
-      else if (i0 > j) w[0] = fma(-c0, xj, w[0]);
-      if (i1 == j) w[1] = xj;
-      else if (i1 > j) w[1] = fma(-c1, xj, w[1]);
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const T xj = __shfl_sync(0xffffffffu, j < 32 ? w0[q] : w1[q], j & 31) * rj;
+        if (i0 == j) w0[q] = xj;
+        else if (i0 > j) w0[q] = fma(-c0, xj, w0[q]);
+        if (i1 == j) w1[q] = xj;
+        else if (i1 > j) w1[q] = fma(-c1, xj, w1[q]);
+      }
       c0 = n0;
       c1 = n1;
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = lane + 32 * h;
-      if (i < k) d.Y[(int64_t)r * d.n + f.first + i] = w[h];
-      else if (i < nf) d.W[(f.woff + i) * nrhs + r] = w[h];
+    for (int q = 0; q < RB; ++q) {
+      const int r = rb + q;
+      if (r >= nrhs) break;
+      if (i0 < k) d.Y[(int64_t)r * d.n + f.first + i0] = w0[q];
+      else if (i0 < nf) d.W[(f.woff + i0) * nrhs + r] = w0[q];
+      if (i1 < k) d.Y[(int64_t)r * d.n + f.first + i1] = w1[q];
+      else if (i1 < nf) d.W[(f.woff + i1) * nrhs + r] = w1[q];
     }
   }
 }
@@ -769,8 +780,8 @@ __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int6
 // Backward, one warp per front with k + m <= 64: for j = k-1 .. 0,
 //   x_j = (y_j - sum_{i > j} L_ij x_i) / L_jj,
 // x_i being the ancestors' final values for the update rows and the values
-// just solved for the pivot rows; one warp reduction per column.
-template <typename T>
+// just solved for the pivot rows; one warp reduction per column and RHS.
+template <typename T, int RB>
 __global__ void __launch_bounds__(256) k_bw_tiny(SD<T> d, int64_t item_off, int64_t count) {
   const int lane = threadIdx.x & 31;
   const int64_t w_id = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -782,12 +793,20 @@ __global__ void __launch_bounds__(256) k_bw_tiny(SD<T> d, int64_t item_off, int6
   const int i0 = lane, i1 = lane + 32;
   const T rd0 = i0 < k ? T(1) / Lp[(int64_t)i0 * nf + i0] : T(0);
   const T rd1 = i1 < k ? T(1) / Lp[(int64_t)i1 * nf + i1] : T(0);
-  for (int r = 0; r < nrhs; ++r) {
-    const T* yr = d.Y + (int64_t)r * d.n;
-    T x0 = i0 < nf ? (i0 < k ? T(0) : yr[frow[i0]]) : T(0);
-    T x1 = i1 < nf ? (i1 < k ? T(0) : yr[frow[i1]]) : T(0);
-    const T y0 = i0 < k ? yr[f.first + i0] : T(0);
-    const T y1 = i1 < k ? yr[f.first + i1] : T(0);
+  const int32_t fr0 = (i0 >= k && i0 < nf) ? frow[i0] : 0;
+  const int32_t fr1 = (i1 >= k && i1 < nf) ? frow[i1] : 0;
+  for (int rb = 0; rb < nrhs; rb += RB) {
+    T x0[RB], x1[RB], y0[RB], y1[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int r = rb + q;
+      const T* yr = d.Y + (int64_t)(r < nrhs ? r : 0) * d.n;
+      const bool live = r < nrhs;
+      x0[q] = (live && i0 >= k && i0 < nf) ? yr[fr0] : T(0);
+      x1[q] = (live && i1 >= k && i1 < nf) ? yr[fr1] : T(0);
+      y0[q] = (live && i0 < k) ? yr[f.first + i0] : T(0);
+      y1[q] = (live && i1 < k) ? yr[f.first + i1] : T(0);
+    }
     T c0 = T(0), c1 = T(0);
     if (k > 0) {
       const T* col = Lp + (int64_t)(k - 1) * nf;
@@ -801,18 +820,26 @@ __global__ void __launch_bounds__(256) k_bw_tiny(SD<T> d, int64_t item_off, int6
         n0 = i0 < nf ? nc[i0] : T(0);
         n1 = i1 < nf ? nc[i1] : T(0);
       }
-      T p = (i0 > j ? c0 * x0 : T(0)) + (i1 > j ? c1 * x1 : T(0));
-      p = warp_sum(p);
-      const T yj = __shfl_sync(0xffffffffu, j < 32 ? y0 : y1, j & 31);
       const T rj = __shfl_sync(0xffffffffu, j < 32 ? rd0 : rd1, j & 31);
-      const T xj = (yj - p) * rj;
-      if (i0 == j) x0 = xj;
-      if (i1 == j) x1 = xj;
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        T p = (i0 > j ? c0 * x0[q] : T(0)) + (i1 > j ? c1 * x1[q] : T(0));
+        p = warp_sum(p);
+        const T yj = __shfl_sync(0xffffffffu, j < 32 ? y0[q] : y1[q], j & 31);
+        const T xj = (yj - p) * rj;
+        if (i0 == j) x0[q] = xj;
+        if (i1 == j) x1[q] = xj;
+      }
       c0 = n0;
       c1 = n1;
     }
-    if (i0 < k) d.Y[(int64_t)r * d.n + f.first + i0] = x0;
-    if (i1 < k) d.Y[(int64_t)r * d.n + f.first + i1] = x1;
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int r = rb + q;
+      if (r >= nrhs) break;
+      if (i0 < k) d.Y[(int64_t)r * d.n + f.first + i0] = x0[q];
+      if (i1 < k) d.Y[(int64_t)r * d.n + f.first + i1] = x1[q];
+    }
   }
 }
 
@@ -1140,8 +1167,13 @@ void launch_warp(bool fw, const Launch& L, const SolveArgs& a, cudaStream_t st) 
   const SD<T> d = make_sd<T>(a);
   const int blocks = (int)((L.count + 7) / 8);
   if constexpr (H == 2) {
-    if (fw) k_fw_tiny<T><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
-    else k_bw_tiny<T><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    if (a.nrhs >= 2) {
+      if (fw) k_fw_tiny<T, 8><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+      else k_bw_tiny<T, 8><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    } else {
+      if (fw) k_fw_tiny<T, 1><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+      else k_bw_tiny<T, 1><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    }
   } else {
     if (fw) k_fw_warp<T, H><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
     else k_bw_warp<T, H><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
