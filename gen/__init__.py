@@ -402,6 +402,26 @@ def random_perm(n, seed=0):
     return np.random.default_rng(seed).permutation(n).astype(np.int32)
 
 
+def random_nodes(n, max_size=4, seed=0, scatter=True):
+    """Group the n DoFs into nodes of U{1..max_size} DoFs.  Returns node_of
+    (node id per DoF, original numbering; with ``scatter`` a node's DoFs are
+    spread over the numbering) and a random ordering that keeps each node's
+    DoFs consecutive (nodes in random order, DoFs ascending inside)."""
+    rng = np.random.default_rng(seed)
+    sizes = []
+    while sum(sizes) < n:
+        sizes.append(int(rng.integers(1, max_size + 1)))
+    sizes[-1] -= sum(sizes) - n
+    lab = np.repeat(np.arange(len(sizes)), sizes)
+    dof = rng.permutation(n) if scatter else np.arange(n)
+    node_of = np.empty(n, dtype=np.int32)
+    node_of[dof] = lab
+    order = rng.permutation(len(sizes))
+    perm = np.concatenate([np.sort(np.nonzero(node_of == u)[0]) for u in order]) if n else \
+        np.zeros(0, dtype=np.int64)
+    return node_of, perm.astype(np.int32)
+
+
 def rhs(n, nrhs=1, seed=0):
     """Right-hand sides U[-1,1], shape (n,) or (n, nrhs), column-major usable."""
     rng = np.random.default_rng(seed)

@@ -134,6 +134,27 @@ int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr,
                         const int32_t* colind, const int32_t* perm,
                         mf_symbolic** s);
 
+/* Symbolic analysis on a condensed graph (paper Sec. 6, graph condensation:
+ * the DoFs of one mesh node are compressed into one vertex).  node_of[i]
+ * (n entries, original numbering, values in [0, n)) names the node of DoF i;
+ * with node_of NULL the nodes are fixed blocks of `block` consecutive DoFs
+ * (node_of[i] = i / block, block >= 1).  perm (as in mf_symbolic_analyze,
+ * NULL = identity) must place the DoFs of every node at consecutive
+ * positions.  Every node block of C that holds an entry, and every diagonal
+ * node block, is treated as dense: the result is the symbolic analysis of
+ * that block-expanded pattern, computed from the node graph (etree and
+ * DoF-weighted column counts on the nodes, expanded to DoFs).  The DoFs of a
+ * node therefore always share one supernode.  Entries of the expanded
+ * pattern that A lacks are explicit zeros of L.  When every node block of A
+ * that holds an entry is already full, the result equals
+ * mf_symbolic_analyze's.  Errors: as mf_symbolic_analyze, plus
+ * MF_ERR_INVALID for node_of out of range, block < 1 without node_of, or a
+ * node whose DoFs are not consecutive in the ordering. */
+int mf_symbolic_analyze_condensed(mf_handle* h, int64_t n, const int64_t* rowptr,
+                                  const int32_t* colind, const int32_t* perm,
+                                  const int32_t* node_of, int32_t block,
+                                  mf_symbolic** s);
+
 /* Block-diagonal union of `count` independent matrices (a batch of
  * subdomains, paper Sec. 5: many subdomain solves per GPU).  Matrix b
  * occupies rows/cols [off_b, off_b + n_b) of the union, off_b = sum of the

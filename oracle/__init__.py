@@ -16,6 +16,8 @@ the three phases of the paper's Ax=b statement in Sec. 2):
 * ``factor``     -- left-looking column Cholesky, FP64 (C); optionally only the
   columns of a descendant-closed set (exact for those columns).
 * ``solve``      -- ``x = P^T L^{-T} L^{-1} P b`` (C).
+* ``expand_node_blocks`` -- the block-expanded pattern a condensed-graph
+  analysis stands for (plain Python sets).
 * ``brute_symbolic`` -- dense boolean elimination on tiny inputs (pure Python),
   an independent pin for etree / counts / nnz(L).
 * ``berr``, ``rel_fro`` -- the error measures used by the parity tests.
@@ -311,6 +313,44 @@ def factor_sample(rowptr, colind, values, perm, seconds=15.0, sym=None):
         if dt >= seconds * 0.5 or J >= n:
             return F.flops, dt, J
         J = min(n, int(J * max(2.0, min(8.0, seconds / max(dt, 1e-3)))))
+
+
+# ---------------------------------------------------------------------------
+# Condensed graph (paper Sec. 6: the DoFs of one node compressed into one
+# vertex of the graph the symbolic analysis runs on)
+# ---------------------------------------------------------------------------
+def expand_node_blocks(rowptr, colind, values, node_of):
+    """The block-expanded matrix the condensed-graph analysis describes:
+    every node block (u, v) of A holding at least one entry, and every
+    diagonal block (u, u), becomes dense; the entries of A keep their values
+    (duplicates summed) and the added positions hold zeros.  Its symbolic
+    analysis and Cholesky factor are what the condensed analysis must
+    reproduce.  Returns (rowptr, colind, values) with columns sorted."""
+    n = len(rowptr) - 1
+    node_of = np.asarray(node_of, dtype=np.int64)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    cols = np.asarray(colind, dtype=np.int64)
+    nn = int(node_of.max()) + 1 if n else 0
+    pairs = set(zip(node_of[rows].tolist(), node_of[cols].tolist()))
+    pairs |= {(u, u) for u in set(node_of.tolist())}
+    dofs = [[] for _ in range(nn)]
+    for i in range(n):
+        dofs[node_of[i]].append(i)
+    entries = {}
+    for (u, v) in pairs:
+        for i in dofs[u]:
+            for j in dofs[v]:
+                entries[(i, j)] = 0.0
+    for r, c, x in zip(rows.tolist(), cols.tolist(), np.asarray(values, dtype=np.float64).tolist()):
+        entries[(r, c)] += x
+    keys = sorted(entries)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    for (r, _) in keys:
+        rp[r + 1] += 1
+    rp = np.cumsum(rp)
+    ci = np.array([c for (_, c) in keys], dtype=np.int32)
+    vx = np.array([entries[k] for k in keys], dtype=np.float64)
+    return rp, ci, vx
 
 
 # ---------------------------------------------------------------------------

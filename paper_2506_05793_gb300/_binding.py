@@ -66,6 +66,7 @@ _SIGS = {
     "mf_destroy": [_P],
     "mf_symbolic_analyze": [_P, _I64, _P, _P, _P, _P],
     "mf_symbolic_analyze_batch": [_P, _I32, _P, _P, _P, _P, _P],
+    "mf_symbolic_analyze_condensed": [_P, _I64, _P, _P, _P, _P, _I32, _P],
     "mf_symbolic_free": [_P],
     "mf_symbolic_get_info": [_P, _P],
     "mf_symbolic_etree": [_P, _P],
@@ -165,6 +166,20 @@ def mf_symbolic_analyze(h, rowptr, colind, perm=None):
     s = ctypes.c_void_p()
     _check(lib().mf_symbolic_analyze(h, len(rowptr) - 1, _ptr(rowptr), _ptr(colind), _ptr(perm),
                                      ctypes.byref(s)))
+    return s
+
+
+def mf_symbolic_analyze_condensed(h, rowptr, colind, perm=None, node_of=None, block=1):
+    """Symbolic analysis on the condensed (node) graph: node_of[i] is the node
+    of DoF i, else fixed blocks of `block` consecutive DoFs."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    perm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int32)
+    node_of = None if node_of is None else np.ascontiguousarray(node_of, dtype=np.int32)
+    s = ctypes.c_void_p()
+    _check(lib().mf_symbolic_analyze_condensed(h, len(rowptr) - 1, _ptr(rowptr), _ptr(colind),
+                                               _ptr(perm), _ptr(node_of), int(block),
+                                               ctypes.byref(s)))
     return s
 
 

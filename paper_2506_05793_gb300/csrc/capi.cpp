@@ -232,8 +232,9 @@ int64_t mf_last_error_column(void) { return g_errcol; }
 // ---------------------------------------------------------------------------
 // Symbolic
 // ---------------------------------------------------------------------------
-int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* colind,
-                        const int32_t* perm, mf_symbolic** s) {
+static int analyze_common(mf_handle* h, int64_t n, const int64_t* rowptr,
+                          const int32_t* colind, const int32_t* perm, const int32_t* node_of,
+                          mf_symbolic** s) {
   if (!h || !s) return set_error(MF_ERR_INVALID, "NULL handle or output");
   *s = nullptr;
   mf_symbolic* S = new (std::nothrow) mf_symbolic();
@@ -243,7 +244,7 @@ int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr, const in
   S->relax = h->opt.relax ? 1 : 0;
   S->keep_inv = h->opt.sptrsv == 2;
   try {
-    rc = mf::analyze(*S, n, rowptr, colind, perm, err);
+    rc = mf::analyze(*S, n, rowptr, colind, perm, node_of, err);
     if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max);
   } catch (const std::bad_alloc&) {
     rc = MF_ERR_OOM;
@@ -255,6 +256,29 @@ int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr, const in
   }
   *s = S;
   return MF_OK;
+}
+
+int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* colind,
+                        const int32_t* perm, mf_symbolic** s) {
+  return analyze_common(h, n, rowptr, colind, perm, nullptr, s);
+}
+
+int mf_symbolic_analyze_condensed(mf_handle* h, int64_t n, const int64_t* rowptr,
+                                  const int32_t* colind, const int32_t* perm,
+                                  const int32_t* node_of, int32_t block, mf_symbolic** s) {
+  if (!h || !s) return set_error(MF_ERR_INVALID, "NULL handle or output");
+  *s = nullptr;
+  if (node_of) return analyze_common(h, n, rowptr, colind, perm, node_of, s);
+  if (block < 1) return set_error(MF_ERR_INVALID, "block must be >= 1 without node_of");
+  if (n < 0 || n >= (int64_t)INT32_MAX) return set_error(MF_ERR_INVALID, "n out of range");
+  std::vector<int32_t> nodes;
+  try {
+    nodes.resize(n);
+  } catch (const std::bad_alloc&) {
+    return set_error(MF_ERR_OOM, "host allocation failed");
+  }
+  for (int64_t i = 0; i < n; ++i) nodes[i] = (int32_t)(i / block);
+  return analyze_common(h, n, rowptr, colind, perm, nodes.data(), s);
 }
 
 int mf_symbolic_analyze_batch(mf_handle* h, int32_t count, const int64_t* ns,

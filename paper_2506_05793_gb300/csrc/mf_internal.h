@@ -159,7 +159,7 @@ struct mf_handle {
 namespace mf {
 // symbolic.cpp
 int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
-            const int32_t* perm, std::string& err);
+            const int32_t* perm, const int32_t* node_of, std::string& err);
 void build_schedules(mf_symbolic& S, int small_max);
 void ensure_fundamental_rows(const mf_symbolic& S);
 // error reporting (capi.cpp)

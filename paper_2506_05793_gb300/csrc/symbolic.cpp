@@ -48,6 +48,191 @@ int invalid(std::string& err, const std::string& msg) {
   return MF_ERR_INVALID;
 }
 
+// Elimination tree and column counts of an n x n symmetric pattern given
+// by its strict lower triangle, by rows (rp/ri) and by columns (cp/cr).
+// Steps 3-4: Liu's etree with path compression, then the row-subtree
+// leaf/LCA counts of Gilbert, Ng and Peyton.  With weights w (one per
+// row/column), count[j] is the sum of w over the structure of column j of L
+// (the diagonal included); without, the plain count c_j.
+int etree_counts(int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ri,
+                 const std::vector<int64_t>& cp, const std::vector<int32_t>& cr,
+                 const int64_t* w, std::vector<int32_t>& parent, std::vector<int64_t>& delta,
+                 std::string& err) {
+  auto W = [w](int32_t j) -> int64_t { return w ? w[j] : 1; };
+  // ---- 3. elimination tree
+  parent.assign(n, -1);
+  {
+    std::vector<int32_t> anc(n, -1);
+    for (int32_t i = 0; i < n; ++i) {
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        int32_t r = ri[p];
+        while (r != -1 && r < i) {
+          const int32_t nx = anc[r];
+          anc[r] = i;
+          if (nx == -1) parent[r] = i;
+          r = nx;
+        }
+      }
+    }
+  }
+  // ---- 4. postorder + column counts (row-subtree leaves and LCAs)
+  std::vector<int32_t> post(n);
+  {
+    std::vector<int32_t> head(n, -1), next(n, -1), stack;
+    for (int32_t j = (int32_t)n - 1; j >= 0; --j) {
+      if (parent[j] != -1) {
+        next[j] = head[parent[j]];
+        head[parent[j]] = j;
+      }
+    }
+    int32_t k = 0;
+    stack.reserve(n);
+    for (int32_t r = 0; r < n; ++r) {
+      if (parent[r] != -1) continue;
+      stack.push_back(r);
+      while (!stack.empty()) {
+        const int32_t p = stack.back();
+        const int32_t c = head[p];
+        if (c == -1) {
+          stack.pop_back();
+          post[k++] = p;
+        } else {
+          head[p] = next[c];
+          stack.push_back(c);
+        }
+      }
+    }
+    if (k != n) {
+      err = "postorder incomplete";
+      return MF_ERR_INTERNAL;
+    }
+  }
+  delta.assign(n, 0);
+  {
+    std::vector<int32_t> first(n, -1), maxfirst(n, -1), prevleaf(n, -1), ancestor(n);
+    for (int32_t k = 0; k < n; ++k) {
+      int32_t j = post[k];
+      delta[j] = (first[j] == -1) ? W(j) : 0;  // etree leaf: row subtree {j}
+      for (; j != -1 && first[j] == -1; j = parent[j]) first[j] = k;
+    }
+    std::iota(ancestor.begin(), ancestor.end(), 0);
+    for (int32_t k = 0; k < n; ++k) {
+      const int32_t j = post[k];
+      if (parent[j] != -1) delta[parent[j]] -= W(j);  // row subtree j ends below parent(j)
+      for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
+        const int32_t i = cr[p];
+        if (first[j] <= maxfirst[i]) continue;  // j is not a leaf of row subtree i
+        maxfirst[i] = first[j];
+        const int32_t jprev = prevleaf[i];
+        prevleaf[i] = j;
+        delta[j] += W(i);
+        if (jprev != -1) {
+          int32_t q = jprev;
+          while (q != ancestor[q]) q = ancestor[q];
+          for (int32_t s = jprev; s != q;) {
+            const int32_t sp = ancestor[s];
+            ancestor[s] = q;
+            s = sp;
+          }
+          delta[q] -= W(i);  // lca of consecutive leaves counted twice
+        }
+      }
+      if (parent[j] != -1) ancestor[j] = parent[j];
+    }
+    for (int32_t k = 0; k < n; ++k) {
+      const int32_t j = post[k];
+      if (parent[j] != -1) delta[parent[j]] += delta[j];
+    }
+  }
+  return MF_OK;
+}
+
+// Condensed-graph analysis (paper Sec. 6, "condensed" graph option): the
+// degrees of freedom of one node (node_of[dof], original numbering) take
+// consecutive positions of the elimination order and are treated as one
+// dense block.  The elimination tree and column counts are computed on the
+// node graph (a node's weight is its DoF count) and expanded: within a node
+// the DoFs form a chain, the last DoF's parent is the first DoF of the
+// parent node, and DoF t of node q has count[q] - t entries.  cp/cr are
+// replaced by the block-expanded strict lower pattern, from which the front
+// rows follow; a node therefore never straddles two supernodes.
+int condensed_structure(int64_t n, const int32_t* node_of, const std::vector<int32_t>& perm,
+                        const std::vector<int64_t>& rp, const std::vector<int32_t>& ri,
+                        std::vector<int64_t>& cp, std::vector<int32_t>& cr,
+                        std::vector<int32_t>& parent, std::vector<int64_t>& delta,
+                        std::string& err) {
+  // nodes in elimination order; nq[i] = node of permuted DoF i
+  std::vector<int32_t> nq(n), seen(n, 0);
+  std::vector<int32_t> nstart;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t u = node_of[perm[i]];
+    if (u < 0 || u >= n) return invalid(err, "node_of out of range");
+    if (i == 0 || u != node_of[perm[i - 1]]) {
+      if (seen[u]) return invalid(err, "the DoFs of a node are not consecutive in the ordering");
+      seen[u] = 1;
+      nstart.push_back((int32_t)i);
+    }
+    nq[i] = (int32_t)nstart.size() - 1;
+  }
+  const int64_t nc = (int64_t)nstart.size();
+  nstart.push_back((int32_t)n);
+  std::vector<int64_t> size(nc);
+  for (int64_t q = 0; q < nc; ++q) size[q] = nstart[q + 1] - nstart[q];
+  // node graph: strict lower triangle by rows (deduplicated), then by columns
+  std::vector<int64_t> nrp(nc + 1, 0);
+  std::vector<int32_t> nri, mark(nc, -1);
+  for (int64_t u = 0; u < nc; ++u) {
+    for (int32_t i = nstart[u]; i < nstart[u + 1]; ++i)
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        const int32_t v = nq[ri[p]];
+        if (v < u && mark[v] != u) {
+          mark[v] = (int32_t)u;
+          nri.push_back(v);
+        }
+      }
+    nrp[u + 1] = (int64_t)nri.size();
+  }
+  std::vector<int64_t> ncp(nc + 1, 0);
+  for (int32_t v : nri) ncp[v + 1]++;
+  for (int64_t q = 0; q < nc; ++q) ncp[q + 1] += ncp[q];
+  std::vector<int32_t> ncr(nri.size());
+  {
+    std::vector<int64_t> fill(ncp.begin(), ncp.end() - 1);
+    for (int64_t u = 0; u < nc; ++u)
+      for (int64_t p = nrp[u]; p < nrp[u + 1]; ++p) ncr[fill[nri[p]]++] = (int32_t)u;
+  }
+  std::vector<int32_t> nparent;
+  std::vector<int64_t> ncount;
+  int rc = etree_counts(nc, nrp, nri, ncp, ncr, size.data(), nparent, ncount, err);
+  if (rc != MF_OK) return rc;
+  // expand to DoFs
+  parent.assign(n, -1);
+  delta.assign(n, 0);
+  for (int64_t q = 0; q < nc; ++q)
+    for (int32_t i = nstart[q]; i < nstart[q + 1]; ++i) {
+      parent[i] = i + 1 < nstart[q + 1] ? i + 1 : (nparent[q] < 0 ? -1 : nstart[nparent[q]]);
+      delta[i] = ncount[q] - (i - nstart[q]);
+    }
+  // block-expanded strict lower pattern by columns (rows sorted)
+  int64_t total = 0;
+  for (int64_t q = 0; q < nc; ++q) {
+    int64_t below = 0;
+    for (int64_t p = ncp[q]; p < ncp[q + 1]; ++p) below += size[ncr[p]];
+    total += size[q] * below + size[q] * (size[q] - 1) / 2;
+  }
+  cp.assign(n + 1, 0);
+  cr.clear();
+  cr.reserve(total);
+  for (int64_t q = 0; q < nc; ++q)
+    for (int32_t j = nstart[q]; j < nstart[q + 1]; ++j) {
+      for (int32_t i = j + 1; i < nstart[q + 1]; ++i) cr.push_back(i);
+      for (int64_t p = ncp[q]; p < ncp[q + 1]; ++p)
+        for (int32_t i = nstart[ncr[p]]; i < nstart[ncr[p] + 1]; ++i) cr.push_back(i);
+      cp[j + 1] = (int64_t)cr.size();
+    }
+  return MF_OK;
+}
+
 }  // namespace
 
 // Device memory of the update matrices.  U_s is written when front s is
@@ -135,7 +320,7 @@ int64_t plan_update_memory(mf_symbolic& S) {
 }
 
 int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
-            const int32_t* perm, std::string& err) {
+            const int32_t* perm, const int32_t* node_of, std::string& err) {
   if (n < 0 || n >= (int64_t)INT32_MAX) return invalid(err, "n out of range");
   if (!rowptr) return invalid(err, "rowptr is NULL");
   if (rowptr[0] != 0) return invalid(err, "rowptr[0] != 0");
@@ -193,93 +378,14 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
   }
 
   timer.mark("lower triangle");
-  // ---- 3. elimination tree
   std::vector<int32_t>& parent = S.parent;
-  parent.assign(n, -1);
-  {
-    std::vector<int32_t> anc(n, -1);
-    for (int32_t i = 0; i < n; ++i) {
-      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-        int32_t r = ri[p];
-        while (r != -1 && r < i) {
-          const int32_t nx = anc[r];
-          anc[r] = i;
-          if (nx == -1) parent[r] = i;
-          r = nx;
-        }
-      }
-    }
-  }
-
-  timer.mark("etree");
-  // ---- 4. postorder + column counts (row-subtree leaves and LCAs)
-  std::vector<int32_t> post(n);
-  {
-    std::vector<int32_t> head(n, -1), next(n, -1), stack;
-    for (int32_t j = (int32_t)n - 1; j >= 0; --j) {
-      if (parent[j] != -1) {
-        next[j] = head[parent[j]];
-        head[parent[j]] = j;
-      }
-    }
-    int32_t k = 0;
-    stack.reserve(n);
-    for (int32_t r = 0; r < n; ++r) {
-      if (parent[r] != -1) continue;
-      stack.push_back(r);
-      while (!stack.empty()) {
-        const int32_t p = stack.back();
-        const int32_t c = head[p];
-        if (c == -1) {
-          stack.pop_back();
-          post[k++] = p;
-        } else {
-          head[p] = next[c];
-          stack.push_back(c);
-        }
-      }
-    }
-    if (k != n) {
-      err = "postorder incomplete";
-      return MF_ERR_INTERNAL;
-    }
-  }
-  std::vector<int64_t> delta(n, 0);
-  {
-    std::vector<int32_t> first(n, -1), maxfirst(n, -1), prevleaf(n, -1), ancestor(n);
-    for (int32_t k = 0; k < n; ++k) {
-      int32_t j = post[k];
-      delta[j] = (first[j] == -1) ? 1 : 0;  // etree leaf: row subtree {j}
-      for (; j != -1 && first[j] == -1; j = parent[j]) first[j] = k;
-    }
-    std::iota(ancestor.begin(), ancestor.end(), 0);
-    for (int32_t k = 0; k < n; ++k) {
-      const int32_t j = post[k];
-      if (parent[j] != -1) delta[parent[j]]--;  // every row subtree ends below parent(root)
-      for (int64_t p = cp[j]; p < cp[j + 1]; ++p) {
-        const int32_t i = cr[p];
-        if (first[j] <= maxfirst[i]) continue;  // j is not a leaf of row subtree i
-        maxfirst[i] = first[j];
-        const int32_t jprev = prevleaf[i];
-        prevleaf[i] = j;
-        delta[j]++;
-        if (jprev != -1) {
-          int32_t q = jprev;
-          while (q != ancestor[q]) q = ancestor[q];
-          for (int32_t s = jprev; s != q;) {
-            const int32_t sp = ancestor[s];
-            ancestor[s] = q;
-            s = sp;
-          }
-          delta[q]--;  // lca of consecutive leaves counted twice
-        }
-      }
-      if (parent[j] != -1) ancestor[j] = parent[j];
-    }
-    for (int32_t k = 0; k < n; ++k) {
-      const int32_t j = post[k];
-      if (parent[j] != -1) delta[parent[j]] += delta[j];
-    }
+  std::vector<int64_t> delta;
+  if (!node_of) {
+    int rc = etree_counts(n, rp, ri, cp, cr, nullptr, parent, delta, err);
+    if (rc != MF_OK) return rc;
+  } else {
+    int rc = condensed_structure(n, node_of, S.perm, rp, ri, cp, cr, parent, delta, err);
+    if (rc != MF_OK) return rc;
   }
   timer.mark("column counts");
   S.colcount = delta;

@@ -261,3 +261,31 @@ def test_nd_perm_separates(shape, axes, dofs):
     left = (shape[ax] // 2) * (nn // shape[ax]) * dofs
     right_end = n - sep
     assert not C[:left, left:right_end].any()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_expand_node_blocks_definition(orc, seed):
+    """Block expansion against its dense definition: (i, j) is present iff
+    node(i) == node(j) or some entry of A joins node(i) to node(j); A's
+    values are kept and the added entries are zero; the expanded pattern
+    contains A's and nodes of one DoF change nothing."""
+    n = [6, 25, 60][seed % 3]
+    rp, ci, v = gen.random_spd(n, 0.15, seed + 40)
+    node_of, _ = gen.random_nodes(n, max_size=1 + seed % 3, seed=seed)
+    erp, eci, ev = orc.expand_node_blocks(rp, ci, v, node_of)
+    A = dense(rp, ci, v)
+    E = dense(erp, eci, ev)
+    want = np.zeros((n, n), dtype=bool)
+    for i in range(n):
+        for j in range(n):
+            same = node_of[i] == node_of[j]
+            link = any(A[a, b] != 0 for a in range(n) if node_of[a] == node_of[i]
+                       for b in range(n) if node_of[b] == node_of[j])
+            want[i, j] = same or link
+    got = np.zeros((n, n), dtype=bool)
+    got[np.repeat(np.arange(n), np.diff(erp)), eci] = True
+    assert np.array_equal(got, want)
+    assert np.array_equal(E, A)
+    if seed % 3 == 0:
+        one = orc.expand_node_blocks(rp, ci, v, np.arange(n))
+        assert np.array_equal(one[0], rp) and np.array_equal(one[1], ci)

@@ -145,3 +145,84 @@ def test_update_memory_plan_reuses_chains(mf, handle):
     all_u = float(np.sum(m.astype(np.float64) ** 2)) * 8
     assert info["factor_bytes_fp64"] < 0.5 * all_u
     mf.mf_symbolic_free(s)
+
+
+# ---- condensed graph (paper Sec. 6: DoFs of one node compressed) ----------
+def check_condensed(mf, handle, orc, rp, ci, perm, node_of=None, block=1):
+    """Condensed analysis = the plain analysis of the block-expanded pattern
+    (oracle), and no node is split between two supernodes."""
+    n = len(rp) - 1
+    nodes = node_of if node_of is not None else np.arange(n) // block
+    erp, eci, _ = orc.expand_node_blocks(rp, ci, np.ones(len(ci)), nodes)
+    s = mf.mf_symbolic_analyze_condensed(handle, rp, ci, perm, node_of=node_of, block=block)
+    try:
+        so = orc.symbolic(erp, eci, perm)
+        assert np.array_equal(mf.mf_symbolic_etree(s), so["parent"])
+        assert np.array_equal(mf.mf_symbolic_colcounts(s), so["colcount"])
+        assert np.array_equal(mf.mf_symbolic_supernodes(s), so["sup_ptr"])
+        info = mf.mf_symbolic_get_info(s)
+        assert info["nnz_L"] == so["nnzL"] and info["flops"] == so["flops"]
+        if n < 400:
+            F = orc.factor(erp, eci, np.ones(len(eci)), perm, sym=so)
+            Lp, Li = mf.mf_symbolic_pattern(s)
+            assert np.array_equal(Lp, F.Lp) and np.array_equal(Li, F.Li)
+        sup = mf.mf_symbolic_supernodes(s)
+        pm = np.arange(n) if perm is None else np.asarray(perm)
+        sn_of_col = np.repeat(np.arange(len(sup) - 1), np.diff(sup))
+        node_new = np.asarray(nodes)[pm]
+        for u in np.unique(node_new):
+            assert len(np.unique(sn_of_col[node_new == u])) == 1
+        return info
+    finally:
+        mf.mf_symbolic_free(s)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_condensed_random_nodes(mf, handle, orc, seed):
+    n = [7, 40, 150, 300][seed % 4]
+    rp, ci, _ = gen.random_spd(n, 0.2 if n < 50 else 0.03, seed + 100)
+    node_of, perm = gen.random_nodes(n, max_size=1 + seed % 4, seed=seed, scatter=seed % 2 == 0)
+    check_condensed(mf, handle, orc, rp, ci, perm, node_of=node_of)
+
+
+def test_condensed_fixed_blocks_and_identity(mf, handle, orc):
+    rp, ci, _ = gen.random_spd(90, 0.05, 7)
+    check_condensed(mf, handle, orc, rp, ci, None, block=3)
+    # block 1: the condensed graph is the graph itself
+    a = check_condensed(mf, handle, orc, rp, ci, None, block=1)
+    b = check_integers(mf, handle, orc, rp, ci, None)
+    assert a["nnz_L"] == b["nnz_L"]
+
+
+def test_condensed_q1_two_dofs_equals_plain(mf, handle, orc):
+    """The Q1 mesh couples both velocity DoFs of every node pair, so its node
+    blocks are full and condensing them changes nothing."""
+    rp, ci, v = gen.q1_extruded(12, 10, 3)
+    perm = gen.nd_perm((13, 11, 4), split_axes=(0, 1), dofs=2)
+    s0 = mf.mf_symbolic_analyze(handle, rp, ci, perm)
+    s1 = mf.mf_symbolic_analyze_condensed(handle, rp, ci, perm, block=2)
+    try:
+        for get in (mf.mf_symbolic_etree, mf.mf_symbolic_colcounts, mf.mf_symbolic_supernodes):
+            assert np.array_equal(get(s0), get(s1))
+        assert np.array_equal(mf.mf_symbolic_pattern(s0)[1], mf.mf_symbolic_pattern(s1)[1])
+    finally:
+        mf.mf_symbolic_free(s0)
+        mf.mf_symbolic_free(s1)
+    check_condensed(mf, handle, orc, rp, ci, perm, block=2)
+
+
+def test_condensed_invalid(mf, handle):
+    rp, ci, _ = gen.laplacian_2d(4)
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_symbolic_analyze_condensed(handle, rp, ci, None, block=0)
+    assert e.value.code == mf.MF_ERR_INVALID
+    # node {0, 1} split by the ordering
+    perm = np.array([0, 2, 1] + list(range(3, 16)), dtype=np.int32)
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_symbolic_analyze_condensed(handle, rp, ci, perm, block=2)
+    assert e.value.code == mf.MF_ERR_INVALID
+    bad = np.zeros(16, dtype=np.int32)
+    bad[3] = 16
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_symbolic_analyze_condensed(handle, rp, ci, None, node_of=bad)
+    assert e.value.code == mf.MF_ERR_INVALID
