@@ -37,6 +37,17 @@ sys.path.insert(0, ROOT)
 METRIC = "factor TFLOP/s (sum c_j^2 / step time; step = FP64 numeric factorization + 1-RHS solve)"
 
 
+def metric_for(args):
+    """The metric line names what one timed step does."""
+    if args.ir:
+        return ("factor TFLOP/s (sum c_j^2 / step time; step = FP32 tensor-core numeric "
+                "factorization + %d-RHS solve refined in FP64 to berr <= 1e-13)" % args.nrhs)
+    if args.prec == "fp32" or args.nrhs != 1:
+        return ("factor TFLOP/s (sum c_j^2 / step time; step = %s numeric factorization + "
+                "%d-RHS solve)" % (args.prec.upper(), args.nrhs))
+    return METRIC
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -61,8 +72,10 @@ def parse():
                    help="pick relaxation / small-front limit / tensor cores with mf_autotune first")
     p.add_argument("--count", type=int, default=512, help="batch: number of boxes")
     p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per solve")
-    p.add_argument("--sptrsv", type=int, default=2, choices=[1, 2],
-                   help="pivot-block solve: 1 substitution, 2 stored diagonal-block inverses")
+    p.add_argument("--sptrsv", type=int, default=2, choices=[1, 2, 3],
+                   help="pivot-block solve: 1 substitution, 2 stored diagonal-block inverses, "
+                        "3 partitioned inverse (one product per level; computed inside the "
+                        "timed factorization)")
     p.add_argument("--serve-rates", default="25,100,400",
                    help="serve: Poisson arrival rates (requests/s) to sweep")
     p.add_argument("--serve-requests", type=int, default=240, help="serve: requests per rate")
@@ -412,7 +425,7 @@ def main():
                         (anorm * np.max(np.abs(xx), axis=0) + np.max(np.abs(bb), axis=0))))
 
     out = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+        "metric": metric_for(args), "value": value, "unit": "TFLOP/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.prec == "fp32" else "f64",
@@ -440,8 +453,11 @@ def main():
                            "the step")
     out["factor_tflops_kernels"] = flops / (fac_ms / 1e3) / 1e12 if fac_ms > 0 else None
     out["kernels"] = prof
-    # dominant kernel roofline: FP64 FMA pipe (contraction) against the
-    # measured bf16 peak times the nominal FP64 / bf16 ratio (1.25 / 2250)
+    # dominant kernel roofline.  split-TF32 tensor cores: the measured bf16
+    # peak x nominal TF32/bf16 ratio, / 3 products per useful FMA.  FP64 and
+    # FP32 FMA work runs on the ALU pipes: peaks from unit counts and clock
+    # (152 SMs, 2.07 GHz; FP64: 2 FMA per clock per SM, the nominal
+    # 1.25 TFLOP/s; FP32: 128 FMA lanes per SM).
     dom = max(prof, key=lambda k: prof[k]["ms"])
     peaks = {}
     try:
@@ -451,16 +467,19 @@ def main():
     bf16 = peaks.get("bf16_tflops", 1900.0)
     ach = prof[dom]["flops"] / (prof[dom]["ms"] / 1e3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
     if dom == "syrk_tc":
-        # useful FP32 flops; split-TF32 issues three TF32 products per FMA
+        bound = "tensor"
         peak = bf16 * (1100.0 / 2250.0) / 3.0
         src = ("measured bf16 %.0f TFLOP/s x nominal TF32/bf16 1100/2250, / 3 for split-TF32 "
                "(useful FP32 flops)" % bf16)
     elif args.prec == "fp32":
-        peak = 73.8  # measured FFMA probe on this GB300 (FP32 FMA pipe)
-        src = "measured FP32 FMA 73.8 TFLOP/s (probe)"
+        bound = "alu"
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        src = "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
     else:
-        peak = bf16 * 1.25 / 2250.0
-        src = "measured bf16 %.0f TFLOP/s x nominal FP64/bf16 1.25/2250" % bf16
+        bound = "alu"
+        peak = 152 * 2 * 2 * 2.07e9 / 1e12
+        src = ("FP64 FMA (DFMA; FP64 tensor cores are no faster on GB300): 152 SMs x 2 FMA/clk "
+               "x 2 flops x 2.07 GHz = the nominal 1.25 TFLOP/s")
     traffic = None
     if (dom == "syrk" and args.prec == "fp64" and workload_name(args) == SYRK_TRAFFIC["workload"]
             and prof["syrk"]["launches"] == SYRK_TRAFFIC["launches"]
@@ -468,7 +487,7 @@ def main():
                                                 "factor_kernels.cu"), "k_syrk(FD<T> d")
             == SYRK_TRAFFIC["source_sha1"]):
         traffic = SYRK_TRAFFIC["bytes_per_launch"]
-    out["roofline"] = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak,
+    out["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak,
                        "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                        "peak_source": src}
     if rank == 0 and not args.no_extras:
@@ -507,7 +526,10 @@ def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm):
     t0 = time.perf_counter()
     for _ in range(K):
         mf.mf_factor_numeric(f, v)       # host values, sync + status read
-        mf.mf_solve(f, b, xh)            # host RHS and solution
+        if args.ir:                      # the same step as the timed one
+            mf.mf_solve_refined(f, b, xh, tol=1e-13, max_iter=30)
+        else:
+            mf.mf_solve(f, b, xh)        # host RHS and solution
     el = time.perf_counter() - t0
     out["e2e"] = {"value": info["flops"] * K / el / 1e12, "unit": "TFLOP/s",
                   "h2d_bytes_per_step": int(v.nbytes + b.nbytes),
@@ -524,8 +546,9 @@ def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm):
         _, rep = mf.mf_solve_refined(f32, bd, xr, tol=1e-13, max_iter=30, stream=st)
         z.record(st)
         torch.cuda.synchronize()
-        out["fp32_ir"] = {"ms_factor_plus_refined_solve": a.elapsed_time(z), "report": rep,
-                          "fp64_ms_per_step": out["ms_per_step"]}
+        out["fp32_ir"] = {"ms_factor_plus_refined_solve": a.elapsed_time(z), "report": rep}
+        if not args.ir:
+            out["fp32_ir"]["fp64_ms_per_step"] = out["ms_per_step"]
         mf.mf_factor_free(f32)
     except Exception as e:  # report, do not hide the main number
         out["fp32_ir"] = {"error": str(e)}

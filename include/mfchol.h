@@ -77,8 +77,15 @@ typedef struct mf_options {
                                64 x 64 diagonal blocks; 2 = product with their
                                inverses, kept from the factorization (default;
                                more memory: 64 x 64 values per 64 pivot columns
-                               of every large front, about 5% of the factor).
-                               Fixed at symbolic analysis. */
+                               of every large front, about 5% of the factor);
+                               3 = partitioned inverse: after the factorization
+                               every large front also stores
+                               [L11^{-1}; -L21 L11^{-1}] (the level's L_l^{-1},
+                               as much memory again as those fronts' L and
+                               about (k^3/3 + m k^2) more flops per front), and
+                               each level of the solve is one product with it
+                               instead of a chain of diagonal blocks.
+                               0 is taken as 1.  Fixed at symbolic analysis. */
 } mf_options;
 
 /* Summary of a symbolic analysis. */

@@ -100,11 +100,13 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
 size_t elem_size(int prec) { return prec == MF_FP32 ? sizeof(float) : sizeof(double); }
 
 // Device bytes of one factor: L, update matrices, diagonal-block inverses,
-// values in assembly order and the CSR values; FP32 adds the tensor-core
+// values in assembly order and the CSR values (plus the partitioned inverse,
+// the size of L, for SpTRSV variant 3); FP32 adds the tensor-core
 // staging rows (two panels of 64 hi + 64 lo floats per row).
 int64_t factor_bytes(const mf_symbolic* S, int prec) {
   const int64_t inv_slots = S->keep_inv ? S->ninv : S->max_large;
-  return (S->Lsize + S->Usize + inv_slots * mf::kNB * mf::kNB + S->nnz_lower) *
+  return (S->Lsize * (S->pinv ? 2 : 1) + S->Usize + inv_slots * mf::kNB * mf::kNB +
+          S->nnz_lower) *
              (int64_t)elem_size(prec) +
          S->nnzA * (int64_t)sizeof(double) +
          (prec == MF_FP32 ? (std::max<int64_t>(S->split_rows, 1) * 256 +
@@ -145,6 +147,7 @@ struct mf_factor {
   cudaStream_t crit = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_side = nullptr, ev_in = nullptr, ev_out = nullptr;
   void* dinv = nullptr;     // inverses of the current diagonal blocks (scratch)
+  void* P = nullptr;        // partitioned inverse (SpTRSV variant 3), layout of L
   void* av = nullptr;       // lower entries of C in assembly order (T)
   double* small = nullptr;  // per-RHS scalars for refinement
   // graph of the numeric factorization
@@ -183,6 +186,7 @@ struct mf_factor {
     if (side) cudaStreamDestroy(side);
     if (crit) cudaStreamDestroy(crit);
     cudaFree(dinv);
+    cudaFree(P);
     cudaFree(av);
     delete fb64;
   }
@@ -211,6 +215,11 @@ int mf_create(mf_handle** h, const mf_options* opt) {
   if (opt) H->opt = *opt; else mf_options_default(&H->opt);
   if (H->opt.small_front_max <= 0 || H->opt.small_front_max > mf::kSmallMax)
     H->opt.small_front_max = mf::kSmallMax;
+  if (H->opt.sptrsv == 0) H->opt.sptrsv = 1;  // zero-filled options: substitution
+  if (H->opt.sptrsv < 1 || H->opt.sptrsv > 3) {
+    delete H;
+    return set_error(MF_ERR_INVALID, "sptrsv must be 1, 2 or 3");
+  }
   // The symbolic phase is host-only, so a handle is usable without a GPU;
   // device calls report MF_ERR_CUDA later if no device is present.
   if (cudaGetDevice(&H->device) != cudaSuccess) {
@@ -242,7 +251,8 @@ static int analyze_common(mf_handle* h, int64_t n, const int64_t* rowptr,
   std::string err;
   int rc;
   S->relax = h->opt.relax ? 1 : 0;
-  S->keep_inv = h->opt.sptrsv == 2;
+  S->keep_inv = h->opt.sptrsv >= 2;
+  S->pinv = h->opt.sptrsv == 3;
   try {
     rc = mf::analyze(*S, n, rowptr, colind, perm, node_of, err);
     if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max);
@@ -430,6 +440,7 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   const int64_t inv_slots = s->keep_inv ? s->ninv : s->max_large;
   MF_CK(cudaMalloc(&F->dinv, std::max<int64_t>(inv_slots, 1) * mf::kNB * mf::kNB * es));
   MF_CK(cudaMalloc(&F->av, std::max<int64_t>(s->nnz_lower, 1) * es));
+  if (s->pinv) MF_CK(cudaMalloc(&F->P, std::max<int64_t>(s->Lsize, 1) * es));
   MF_CK(mf::factor_kernels_init(prec));
   MF_CK(mf::solve_kernels_init(prec));
   if (prec == MF_FP32 && h->opt.tc) {
@@ -466,6 +477,7 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
   a.split_map = F->tc ? F->split_map : nullptr;
   a.split_map_b = F->tc ? F->split_map_b : nullptr;
   a.dinv = F->dinv;
+  a.P = F->P;
   a.av = F->av;
   const std::vector<mf::Launch>& sched = F->tc ? S->fsched_tc : S->fsched;
   MF_CK(cudaMemsetAsync(F->status, 0xff, 2 * sizeof(unsigned long long), st));
@@ -573,6 +585,7 @@ int mf_factor_check(mf_factor* f, void* stream) {
         float ms = 0.f;
         MF_CK(cudaEventElapsedTime(&ms, f->ev[2 * i], f->ev[2 * i + 1]));
         const int k = sched[i].kind;
+        if (k >= mf::K_NKINDS_FACTOR) continue;  // partitioned-inverse pass
         f->prof_ms[k] += ms;
         f->prof_n[k] += 1;
         f->prof_fl[k] += sched[i].flops;
@@ -780,6 +793,7 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.nlevels = S->nlevels;
   a.nblk = S->blkoff.back();
   a.dinv = S->keep_inv ? f->dinv : nullptr;
+  a.P = f->P;
   for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, X, ldx, S->n, cn, scale, accumulate, st));

@@ -44,6 +44,8 @@ struct FD {
   float* split;    // staging area 0: rows of 256 floats (two panel slots)
   float* split_b;  // staging area 1: rows of 512 floats (four slots, lookahead levels)
   T* dinv;
+  const int64_t* ioff;  // per front: first kept diagonal-inverse slot (or -1)
+  T* P;                 // partitioned inverse (SpTRSV variant 3) or nullptr
 };
 
 template <typename T>
@@ -67,6 +69,8 @@ FD<T> make_fd(const FactorArgs& a) {
   d.split = a.split;
   d.split_b = a.split_b;
   d.dinv = static_cast<T*>(a.dinv);
+  d.ioff = a.sym.ioff;
+  d.P = static_cast<T*>(a.P);
   return d;
 }
 
@@ -560,6 +564,129 @@ __global__ void __launch_bounds__(256) k_syrk(FD<T> d, int64_t item_off) {
       if (p[i][j]) *p[i][j] = cur[i][j] - acc[i][j];
 }
 
+// ---------------------------------------------------------------------------
+// Partitioned inverse (SpTRSV variant 3, Sec. 5).  For a large front with
+// pivot columns [L11; L21], P = [L11^{-1}; -L21 L11^{-1}] in the layout of L:
+// the front's columns of the level's L_l^{-1}.  L11 X = I is solved by block
+// rows, right-looking, over all rows of the front at once (update rows start
+// at zero, so they end at -L21 X).  Init writes P = 0 and the kept inverses
+// L_jj^{-1} on the diagonal blocks; step t takes, for every tile (i, j) with
+// i > t >= j, P(i, j) -= L(i, t) P(t, j) and finalises block row t + 1 with
+// P(t+1, j) = L_{t+1,t+1}^{-1} P(t+1, j).
+// ---------------------------------------------------------------------------
+// Init, item (s, j): column block j of front s.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pinv_init(FD<T> d, int64_t item_off) {
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int nf = f.k + f.m, c0 = it.t * kNB, bj = min(kNB, f.k - c0);
+  const T* Dv = d.dinv + (d.ioff[it.s] + it.t) * (int64_t)(kNB * kNB);
+  T* Pc = d.P + f.Loff + (int64_t)c0 * nf;
+  for (int c = 0; c < bj; ++c)
+    for (int r = threadIdx.x; r < nf; r += blockDim.x) {
+      const int rr = r - c0;
+      Pc[(int64_t)c * nf + r] = (rr >= c && rr < bj) ? Dv[c * kNB + rr] : T(0);
+    }
+}
+
+template <typename T>
+constexpr size_t pinv_smem() {
+  return (size_t)2 * kNB * (kNB + 1) * sizeof(T);
+}
+
+// Step t, item (s, t, i, j): one 64 x 64 tile.  Thread (tx, ty) owns rows
+// tx + 16 a and columns ty + 16 b of the tile.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pinv_step(FD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T(*As)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // As[q][r]
+  T(*Bs)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(
+      smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));         // Bs[q][c]
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m, nb = (k + kNB - 1) / kNB;
+  const int t = it.t, i = it.a, j = it.b;
+  const int r0 = i < nb ? i * kNB : k + (i - nb) * kNB;
+  const int rows = min(kNB, (i < nb ? k : nf) - r0);
+  const int t0 = t * kNB, bt = min(kNB, k - t0);
+  const int c0 = j * kNB, bj = min(kNB, k - c0);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const T* Lp = d.L + f.Loff;
+  T* Pp = d.P + f.Loff;
+  // As[q][r] = L(r0 + r, t0 + q), Bs[q][c] = P(t0 + q, c0 + c) (final)
+  for (int idx = tid; idx < kNB * kNB; idx += 256) {
+    const int q = idx / kNB, r = idx % kNB;
+    As[q][r] = (q < bt && r < rows) ? Lp[(int64_t)(t0 + q) * nf + r0 + r] : T(0);
+  }
+  for (int idx = tid; idx < kNB * kNB; idx += 256) {
+    const int c = idx / kNB, q = idx % kNB;
+    Bs[q][c] = (q < bt && c < bj) ? Pp[(int64_t)(c0 + c) * nf + t0 + q] : T(0);
+  }
+  __syncthreads();
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int q = 0; q < bt; ++q) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = As[q][tx + 16 * a];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Bs[q][ty + 16 * b];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+  T cv[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = tx + 16 * a, c = ty + 16 * b;
+      cv[a][b] = (r < rows && c < bj) ? Pp[(int64_t)(c0 + c) * nf + r0 + r] - acc[a][b] : T(0);
+    }
+  if (i == t + 1 && i < nb) {
+    // block row i is complete: P(i, j) = L_ii^{-1} P(i, j) (lower triangular,
+    // so rows r < rows only need q <= r < rows)
+    const T* Dv = d.dinv + (d.ioff[it.s] + i) * (int64_t)(kNB * kNB);
+    __syncthreads();
+    for (int idx = tid; idx < kNB * kNB; idx += 256) As[idx / kNB][idx % kNB] = Dv[idx];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Bs[tx + 16 * a][ty + 16 * b] = cv[a][b];
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int q = 0; q < rows; ++q) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[q][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[q][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) cv[a][b] = acc[a][b];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = tx + 16 * a, c = ty + 16 * b;
+      if (r < rows && c < bj) Pp[(int64_t)(c0 + c) * nf + r0 + r] = cv[a][b];
+    }
+}
+
 // av[e] = T(sum of the CSR values of lower entry e): one pass per numeric
 // call, so the assembly kernels read values in their own order.
 template <typename T>
@@ -583,6 +710,9 @@ cudaError_t init_t() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)potrf_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pinv_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pinv_smem<T>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)syrk_smem<T>());
@@ -610,6 +740,12 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
       break;
     case K_SYRK_TC:
       return launch_syrk_tc(L, a, st);
+    case K_PINV_INIT:
+      k_pinv_init<T><<<grid, 256, 0, st>>>(d, L.item_off);
+      break;
+    case K_PINV:
+      k_pinv_step<T><<<grid, 256, pinv_smem<T>(), st>>>(d, L.item_off);
+      break;
     default:
       return cudaErrorInvalidValue;
   }

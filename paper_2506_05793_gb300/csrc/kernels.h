@@ -47,6 +47,8 @@ struct FactorArgs {
   // per large front of the level (slot in item field b): 64 x 64 inverse of
   // the current diagonal block of the factor, T
   void* dinv;
+  // partitioned inverse P (T[Lsize], layout of L) or nullptr
+  void* P = nullptr;
 };
 
 struct SolveArgs {
@@ -61,6 +63,8 @@ struct SolveArgs {
   // diagonal-block inverses of the large fronts (slots sym.ioff), or nullptr
   // to solve the pivot blocks by substitution
   const void* dinv = nullptr;
+  // partitioned inverse (SpTRSV variant 3), T[Lsize], or nullptr
+  const void* P = nullptr;
   int64_t n;
   int32_t nrhs;
   int32_t nlevels;

@@ -55,12 +55,18 @@ enum Kind : int32_t {
   K_SYRK = 4,      // trailing lower update
   K_SYRK_TC = 5,   // FP32 trailing update on tcgen05 tensor cores (128 x 128)
   K_NKINDS_FACTOR = 6,
+  K_PINV_INIT = 7,   // partitioned inverse: P = 0, diagonal blocks = their inverses
+  K_PINV = 8,        // partitioned inverse, step t: P(i, j) -= L(i, t) P(t, j), i > t >= j
   K_FW_LEVEL = 11,   // per 64-row block: gather, GEMV with solved blocks, diagonal solve
   K_BW_LEVEL = 12,   // per 64-column block: transposed GEMV, diagonal solve
   K_FW_WARP = 13,    // one warp per front with k + m <= kWarpSolve (forward)
   K_BW_WARP = 14,    // one warp per front with k + m <= kWarpSolve (backward)
   K_FW_GEMV = 15,    // per 64 update rows: w -= L21 x1 (after the level's pivots)
   K_BW_GEMV = 16,    // per 64 pivot columns: y -= L21^T x2 (before the chains)
+  K_FW_PGATHER = 17, // variant 3: gather the pivot rows' w into the front work vector
+  K_FW_PINV = 18,    // variant 3: rows of P times w (x for pivot rows, w update below)
+  K_BW_PCOPY = 19,   // variant 3: stage the forward result y of the pivot rows
+  K_BW_PINV = 20,    // variant 3: x(cols) = P^T [y; x of the update rows]
 };
 
 struct Launch {
@@ -138,6 +144,11 @@ struct mf_symbolic {
   bool keep_inv = false;
   std::vector<int64_t> ioff;
   int64_t ninv = 0;
+  // partitioned inverse (SpTRSV variant 3): per large front of the solve
+  // P = [L11^{-1}; -L21 L11^{-1}] in the layout of L, computed after the
+  // factorization (pinv_flops of extra work)
+  bool pinv = false;
+  double pinv_flops = 0.0;
   std::vector<mf::Item> arange;       // assembly: (child, lo, hi, 0) lists per chunk
   std::vector<mf::Launch> fwsched, bwsched;
   std::vector<int32_t> blkoff;     // per front: first 64-column block index

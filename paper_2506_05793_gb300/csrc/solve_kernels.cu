@@ -39,6 +39,7 @@ struct SD {
   const int64_t* ginv_src;
   const T* dinv;         // diagonal-block inverses (SpTRSV variant 2) or nullptr
   const int64_t* ioff;   // per front: first inverse slot, -1 if none
+  const T* P;            // partitioned inverse (SpTRSV variant 3) or nullptr
   unsigned long long* status;
   int64_t n;
   int nrhs;
@@ -60,6 +61,7 @@ SD<T> make_sd(const SolveArgs& a) {
   d.ginv_src = a.sym.ginv_src;
   d.dinv = static_cast<const T*>(a.dinv);
   d.ioff = a.sym.ioff;
+  d.P = static_cast<const T*>(a.P);
   d.status = a.status;
   d.n = a.n;
   d.nrhs = a.nrhs;
@@ -709,6 +711,237 @@ __global__ void __launch_bounds__(256) k_bw_gemm(SD<T> d, int64_t item_off) {
 }
 
 // ---------------------------------------------------------------------------
+// SpTRSV variant 3 (Sec. 5, partitioned inverse).  For a large front,
+// P = [L11^{-1}; -L21 L11^{-1}] (layout of L) turns the pivot solve and the
+// update-row product into one product whose row (column) blocks are
+// independent: no flags, no chains.  Forward: the pivot rows' gathered w is
+// staged in the front's work vector (rows woff .. woff + k of W); then
+// x = L11^{-1} w goes to Y and the update rows take w_u + (-L21 L11^{-1}) w.
+// Backward: the pivot rows' forward result y is staged in W; then
+// x_c = sum_i P(i, c) v_i with v = [y; x of the update rows].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_fw_pgather(SD<T> d, int64_t item_off) {
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int nrhs = d.nrhs;
+  for (int idx = threadIdx.x; idx < it.b * nrhs; idx += blockDim.x) {
+    const int rw = idx / nrhs, r = idx % nrhs;
+    const int i = it.a + rw;
+    const int64_t gi = f.woff + i;
+    T w = d.Y[(int64_t)r * d.n + f.first + i];
+    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e)
+      w += d.W[d.ginv_src[e] * nrhs + r];
+    d.W[gi * nrhs + r] = w;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bw_pcopy(SD<T> d, int64_t item_off) {
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int nrhs = d.nrhs;
+  for (int idx = threadIdx.x; idx < it.b * nrhs; idx += blockDim.x) {
+    const int rw = idx / nrhs, r = idx % nrhs;
+    const int i = it.a + rw;
+    d.W[(f.woff + i) * nrhs + r] = d.Y[(int64_t)r * d.n + f.first + i];
+  }
+}
+
+// Forward product, one right-hand side, four CTAs of 16 rows per 64-row item
+// (item field t: 0 pivot rows, 1 update rows); thread (row, g) sums the
+// columns j = g (mod 16), the 16 partial sums of a row in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fw_pinv1(SD<T> d, int64_t item_off) {
+  __shared__ T red[16][17];
+  const int sub = blockIdx.x & 3;
+  const Item it = d.items[item_off + (blockIdx.x >> 2)];
+  const int rows = min(16, it.b - 16 * sub);
+  if (rows <= 0) return;  // whole CTA
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m;
+  const int r0 = it.a + 16 * sub;
+  const bool piv = it.t == 0;
+  const int kend = piv ? r0 + rows : k;  // L11^{-1} is lower triangular
+  const int tid = threadIdx.x, row = tid & 15, g = tid >> 4;
+  const bool live = row < rows;
+  const T* Pr = d.P + f.Loff + r0 + (live ? row : 0);
+  const T* wv = d.W + f.woff;  // the pivot rows' gathered w
+  T a0 = T(0), a1 = T(0);
+  int j = g;
+  for (; j + 16 < kend; j += 32) {
+    a0 = fma(Pr[(int64_t)j * nf], wv[j], a0);
+    a1 = fma(Pr[(int64_t)(j + 16) * nf], wv[j + 16], a1);
+  }
+  if (j < kend) a0 = fma(Pr[(int64_t)j * nf], wv[j], a0);
+  red[g][row] = a0 + a1;
+  __syncthreads();
+  if (tid < rows) {
+    T sum = T(0);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) sum += red[q][tid];
+    const int i = r0 + tid;
+    if (piv) {
+      d.Y[f.first + i] = sum;
+    } else {
+      const int64_t gi = f.woff + i;
+      T w = T(0);
+      for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e) w += d.W[d.ginv_src[e]];
+      d.W[gi] = w + sum;
+    }
+  }
+}
+
+// Forward product, several right-hand sides: w staged in chunks of
+// kGemvStage / R columns, thread (row, g) takes columns g, g + 4, ...
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_fw_pinv(SD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sx = reinterpret_cast<T*>(smem_raw);  // sx[j * R + r]
+  T* red = sx + kGemvStage;                // red[(g * kNB + row) * R + r]
+  constexpr int CH = kGemvStage / R;
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
+  const int r0 = it.a, rows = it.b;
+  const bool piv = it.t == 0;
+  const int kend = piv ? r0 + rows : k;
+  const int tid = threadIdx.x, row = tid & 63, g = tid >> 6;
+  const bool live = row < rows;
+  const T* Pr = d.P + f.Loff + r0 + (live ? row : 0);
+  T acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = T(0);
+  for (int j0 = 0; j0 < kend; j0 += CH) {
+    const int cl = min(CH, kend - j0);
+    __syncthreads();
+    for (int idx = tid; idx < cl * nrhs; idx += blockDim.x) {
+      const int j = idx / nrhs, r = idx % nrhs;
+      sx[j * R + r] = d.W[(f.woff + j0 + j) * nrhs + r];
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int j = g; j < cl; j += 4) {
+      const T l = Pr[(int64_t)(j0 + j) * nf];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (r < nrhs) acc[r] = fma(l, sx[j * R + r], acc[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r < nrhs) red[(g * kNB + row) * R + r] = acc[r];
+  __syncthreads();
+  for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
+    const int rw = idx / nrhs, r = idx % nrhs;
+    const int i = r0 + rw;
+    const T sum = red[(0 * kNB + rw) * R + r] + red[(1 * kNB + rw) * R + r] +
+                  red[(2 * kNB + rw) * R + r] + red[(3 * kNB + rw) * R + r];
+    if (piv) {
+      d.Y[(int64_t)r * d.n + f.first + i] = sum;
+    } else {
+      const int64_t gi = f.woff + i;
+      T w = T(0);
+      for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e)
+        w += d.W[d.ginv_src[e] * nrhs + r];
+      d.W[gi * nrhs + r] = w + sum;
+    }
+  }
+}
+
+// Backward product, one right-hand side: CTA (item, sub) takes columns
+// c0 + 16 sub .. + 16; its warps split the rows i >= those columns
+// (coalesced), each lane keeps 16 column sums, warps added in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bw_pinv1(SD<T> d, int64_t item_off) {
+  __shared__ T red[8][16];
+  const int sub = blockIdx.x & 3;
+  const Item it = d.items[item_off + (blockIdx.x >> 2)];
+  const int nc = min(16, it.b - 16 * sub);
+  if (nc <= 0) return;  // whole CTA
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m;
+  const int cb = it.a + 16 * sub;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* Pb = d.P + f.Loff + (int64_t)cb * nf;
+  const int32_t* frow = d.rowidx + f.rows_off;
+  T acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = T(0);
+  for (int i = cb + warp * 32 + lane; i < nf; i += 256) {
+    const T vi = i < k ? d.W[f.woff + i] : d.Y[frow[i]];
+    T lv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) lv[q] = q < nc ? Pb[(int64_t)q * nf + i] : T(0);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = fma(lv[q], vi, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const T v = warp_sum(acc[q]);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (tid < nc) {
+    T sum = T(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += red[w][tid];
+    d.Y[f.first + cb + tid] = sum;
+  }
+}
+
+// Backward product, R >= 8 right-hand sides: chunks of kBwRows rows from the
+// block's first column down, staged transposed (P) and row-major (v).
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_bw_pinv(SD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int lds = kBwRows + 1;
+  constexpr int RG = R / 4;
+  T* Ls = reinterpret_cast<T*>(smem_raw);   // Ls[c * lds + i] = P(i0 + i, c0 + c)
+  T* xs = Ls + kNB * lds;                   // xs[i * R + r] = v(i0 + i, r)
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
+  const int c0 = it.a, bs = it.b;
+  const int tid = threadIdx.x, c = tid & (kNB - 1), g = tid >> 6;
+  const T* Pp = d.P + f.Loff;
+  const int32_t* frow = d.rowidx + f.rows_off;
+  T acc[RG];
+#pragma unroll
+  for (int q = 0; q < RG; ++q) acc[q] = T(0);
+  for (int i0 = c0; i0 < nf; i0 += kBwRows) {
+    const int ch = min(kBwRows, nf - i0);
+    __syncthreads();
+    for (int idx = tid; idx < kNB * kBwRows; idx += blockDim.x) {
+      const int cc = idx / kBwRows, i = idx % kBwRows;
+      Ls[cc * lds + i] = (cc < bs && i < ch) ? Pp[(int64_t)(c0 + cc) * nf + i0 + i] : T(0);
+    }
+    for (int idx = tid; idx < kBwRows * R; idx += blockDim.x) {
+      const int i = idx % kBwRows, r = idx / kBwRows;
+      const int gi = i0 + i;
+      T v = T(0);
+      if (i < ch && r < nrhs)
+        v = gi < k ? d.W[(f.woff + gi) * nrhs + r] : d.Y[(int64_t)r * d.n + frow[gi]];
+      xs[i * R + r] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < kBwRows; ++i) {
+      const T l = Ls[c * lds + i];
+#pragma unroll
+      for (int q = 0; q < RG; ++q) acc[q] = fma(l, xs[i * R + g + 4 * q], acc[q]);
+    }
+  }
+  if (c < bs) {
+#pragma unroll
+    for (int q = 0; q < RG; ++q) {
+      const int r = g + 4 * q;
+      if (r < nrhs) d.Y[(int64_t)r * d.n + f.first + c0 + c] = acc[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fronts with k + m <= 64: one warp per front (8 per CTA), few registers so
 // that many fronts are in flight.  Lane l owns front rows l and l + 32.  The
 // work vector of front s lives in W[(woff_s + i) * nrhs + r].  Right-hand
@@ -1127,9 +1360,15 @@ cudaError_t init_r() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fw_gemv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)gemv_smem<T, R>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fw_pinv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gemv_smem<T, R>());
   if constexpr (R >= 8) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_bw_gemm<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)bw_gemm_smem<T, R>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bw_pinv<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)bw_gemm_smem<T, R>());
   }
   return e;
@@ -1155,11 +1394,17 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   else if (L.kind == K_FW_GEMV) {
     if constexpr (R == 1) k_fw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
     else k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
-  }
-  else if constexpr (R >= 8)
+  } else if (L.kind == K_FW_PINV) {
+    if constexpr (R == 1) k_fw_pinv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
+    else k_fw_pinv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
+  } else if (L.kind == K_BW_PINV) {
+    if constexpr (R >= 8) k_bw_pinv<T, R><<<L.count, 256, bw_gemm_smem<T, R>(), st>>>(d, L.item_off);
+    else k_bw_pinv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
+  } else if constexpr (R >= 8) {
     k_bw_gemm<T, R><<<L.count, 256, bw_gemm_smem<T, R>(), st>>>(d, L.item_off);
-  else
+  } else {
     k_bw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
+  }
 }
 
 template <typename T, int H>
@@ -1193,7 +1438,14 @@ cudaError_t launch_t(const Launch& L, const SolveArgs& a, cudaStream_t st) {
     }
     return cudaGetLastError();
   }
-  if (L.kind != K_FW_LEVEL && L.kind != K_BW_LEVEL && L.kind != K_FW_GEMV && L.kind != K_BW_GEMV)
+  if (L.kind == K_FW_PGATHER || L.kind == K_BW_PCOPY) {
+    const SD<T> d = make_sd<T>(a);
+    if (L.kind == K_FW_PGATHER) k_fw_pgather<T><<<L.count, 256, 0, st>>>(d, L.item_off);
+    else k_bw_pcopy<T><<<L.count, 256, 0, st>>>(d, L.item_off);
+    return cudaGetLastError();
+  }
+  if (L.kind != K_FW_LEVEL && L.kind != K_BW_LEVEL && L.kind != K_FW_GEMV &&
+      L.kind != K_BW_GEMV && L.kind != K_FW_PINV && L.kind != K_BW_PINV)
     return cudaErrorInvalidValue;
   if (a.nrhs <= 1) launch_r<T, 1>(L, a, st);
   else if (a.nrhs <= 8) launch_r<T, 8>(L, a, st);

@@ -927,10 +927,36 @@ void build_schedules(mf_symbolic& S, int small_max) {
       v.clear();
     }
   };
-  std::vector<Item> wcls[4], upd;
-  std::vector<int32_t> big;
+  std::vector<Item> wcls[4], upd, pg, pv;
+  std::vector<int32_t> big, pfronts;
+  // SpTRSV variant 3: large fronts of the factor (those with kept diagonal
+  // inverses) that the solve takes as level-kernel fronts use the
+  // partitioned inverse instead of the flag-chained pivot blocks
+  auto take_pinv = [&](std::vector<int32_t>& B, std::vector<int32_t>& P) {
+    P.clear();
+    if (!S.pinv) return;
+    size_t w = 0;
+    for (int32_t s : B) {
+      if (S.ioff[s] >= 0) P.push_back(s);
+      else B[w++] = s;
+    }
+    B.resize(w);
+  };
+  std::vector<int32_t> all_pinv;
   for (int32_t lev = 0; lev < S.nlevels; ++lev) {
     split_level(bylev[lev], wcls, big);
+    take_pinv(big, pfronts);
+    all_pinv.insert(all_pinv.end(), pfronts.begin(), pfronts.end());
+    pg.clear();
+    pv.clear();
+    for (int32_t s : pfronts) {
+      const int k = S.sn[s].k, m = S.sn[s].m;
+      for (int r0 = 0; r0 < k; r0 += kNB) {
+        pg.push_back({s, 0, r0, std::min(kNB, k - r0)});
+        pv.push_back({s, 0, r0, std::min(kNB, k - r0)});
+      }
+      for (int r0 = 0; r0 < m; r0 += kNB) pv.push_back({s, 1, k + r0, std::min(kNB, m - r0)});
+    }
     upd.clear();
     for (int32_t s : big) {
       const int k = S.sn[s].k, m = S.sn[s].m;
@@ -946,9 +972,22 @@ void build_schedules(mf_symbolic& S, int small_max) {
     // of the level as a streaming product that never waits
     add(S.fwsched, K_FW_LEVEL, lev, 0, it, 0.0);
     add(S.fwsched, K_FW_GEMV, lev, 0, upd, 0.0);
+    // variant 3: gather the pivot rows' w, then one product per row block
+    add(S.fwsched, K_FW_PGATHER, lev, 0, pg, 0.0);
+    add(S.fwsched, K_FW_PINV, lev, 0, pv, 0.0);
   }
   for (int32_t lev = S.nlevels - 1; lev >= 0; --lev) {
     split_level(bylev[lev], wcls, big);
+    take_pinv(big, pfronts);
+    pg.clear();
+    pv.clear();
+    for (int32_t s : pfronts) {
+      const int k = S.sn[s].k;
+      for (int c0 = 0; c0 < k; c0 += kNB) {
+        pg.push_back({s, 0, c0, std::min(kNB, k - c0)});
+        pv.push_back({s, 0, c0, std::min(kNB, k - c0)});
+      }
+    }
     for (int32_t s : big) {
       const int k = S.sn[s].k;
       int dpt = 0;
@@ -966,6 +1005,51 @@ void build_schedules(mf_symbolic& S, int small_max) {
     // flag-chained triangles
     add(S.bwsched, K_BW_GEMV, lev, 0, upd, 0.0);
     add(S.bwsched, K_BW_LEVEL, lev, 1, it, 0.0);
+    // variant 3: stage the pivot rows' y, then one product per column block
+    add(S.bwsched, K_BW_PCOPY, lev, 0, pg, 0.0);
+    add(S.bwsched, K_BW_PINV, lev, 0, pv, 0.0);
+  }
+  // ---- partitioned inverse of the variant-3 fronts, after the whole
+  // factorization: P = [L11; L21] X with L11 X = I solved by block rows,
+  // right-looking.  Row blocks i of a front are its pivot blocks (i < nb)
+  // then its 64-row blocks of update rows.  Init: P = 0 with the kept
+  // diagonal inverses on the diagonal blocks.  Step t: every tile (i, j)
+  // with i > t >= j takes P(i, j) -= L(i, t) P(t, j); a pivot tile with
+  // i = t + 1 is then final after P(i, j) = L_ii^{-1} P(i, j).
+  S.pinv_flops = 0.0;
+  if (S.pinv && !all_pinv.empty()) {
+    std::vector<Item> init;
+    int32_t tmax = 0;
+    for (int32_t s : all_pinv) {
+      const int k = S.sn[s].k;
+      for (int j = 0; j * kNB < k; ++j) init.push_back({s, j, 0, 0});
+      tmax = std::max(tmax, (k + kNB - 1) / kNB);
+    }
+    const int32_t plev = S.nlevels;  // after every level of the factorization
+    add(S.fsched, K_PINV_INIT, plev, 0, init, 0.0);
+    add(S.fsched_tc, K_PINV_INIT, plev, 0, init, 0.0);
+    std::vector<Item> st;
+    for (int32_t t = 0; t < tmax; ++t) {
+      st.clear();
+      double fl = 0.0;
+      for (int32_t s : all_pinv) {
+        const int k = S.sn[s].k, m = S.sn[s].m;
+        const int nb = (k + kNB - 1) / kNB, mb = (m + kNB - 1) / kNB;
+        if (t >= nb) continue;
+        const double bt = std::min(kNB, k - t * kNB);
+        for (int i = t + 1; i < nb + mb; ++i) {
+          const double ri = i < nb ? std::min(kNB, k - i * kNB) : std::min(kNB, m - (i - nb) * kNB);
+          for (int j = 0; j <= t; ++j) {
+            const double bj = std::min(kNB, k - j * kNB);
+            st.push_back({s, t, i, j});
+            fl += 2.0 * ri * bt * bj + (i == t + 1 && i < nb ? 2.0 * ri * ri * bj : 0.0);
+          }
+        }
+      }
+      S.pinv_flops += fl;
+      add(S.fsched, K_PINV, plev, t, st, fl);
+      add(S.fsched_tc, K_PINV, plev, t, st, fl);
+    }
   }
 }
 

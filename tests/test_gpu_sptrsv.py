@@ -1,6 +1,8 @@
-"""SpTRSV variant 2 (Sec. 5): the solve of the large fronts' pivot blocks as a
-product with the inverses of the diagonal blocks, kept from the
-factorization, against the oracle and against the substitution variant."""
+"""SpTRSV variants (Sec. 5) against the oracle and against each other:
+variant 2 solves the large fronts' pivot blocks as a product with the kept
+inverses of their diagonal blocks; variant 3 (partitioned inverse) makes each
+level one product with [L11^{-1}; -L21 L11^{-1}], computed after the
+factorization."""
 import numpy as np
 import pytest
 
@@ -72,12 +74,55 @@ def test_inverse_variant_matches_oracle_and_substitution(mf, orc, case, nrhs):
     assert np.max(np.abs(X2 - X1)) <= 1e-9 * scale
 
 
-def test_inverse_variant_fp32_refinement(mf, orc):
+@pytest.mark.parametrize("case", ["dense_333", "dense_150", "lap3d_jump_20", "q1_14x12x4",
+                                  "lap2d_301x157"])
+@pytest.mark.parametrize("nrhs", [1, 5, 9])
+def test_partitioned_inverse_matches_oracle_and_substitution(mf, orc, case, nrhs):
+    rp, ci, v, perm = case_matrix(case)
+    n = len(rp) - 1
+    B = gen.rhs(n, nrhs, seed=21 + nrhs)
+    X3, info3 = solve_with(mf, 3, rp, ci, v, perm, B)
+    X1, info1 = solve_with(mf, 1, rp, ci, v, perm, B)
+    # the partitioned inverse takes memory: the variant really ran
+    assert info3["factor_bytes_fp64"] > info1["factor_bytes_fp64"]
+    assert orc.berr(rp, ci, v, X3, B) <= BERR
+    F = orc.factor(rp, ci, v, perm)
+    Xo = orc.solve(F, B, perm)
+    scale = np.max(np.abs(Xo))
+    assert np.max(np.abs(X3 - Xo)) <= 1e-9 * scale
+    assert np.max(np.abs(X3 - X1)) <= 1e-9 * scale
+
+
+def test_partitioned_inverse_repeated_factorizations(mf, orc):
+    """The inverse pass runs inside the factorization's CUDA graph: a second
+    numeric factorization with other values must refresh it."""
+    rp, ci, v, perm = case_matrix("lap3d_jump_20")
+    n = len(rp) - 1
+    B = gen.rhs(n, 2, seed=8)
+    opt = mf.mf_options_default()
+    opt.sptrsv = 3
+    h = mf.mf_create(opt)
+    s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+    f = mf.mf_factor_create(h, s, mf.MF_FP64)
+    try:
+        for scale in (1.0, 3.0):
+            v2 = v * scale
+            mf.mf_factor_numeric(f, v2)
+            X = mf.mf_solve(f, B)
+            assert orc.berr(rp, ci, v2, X, B) <= BERR
+    finally:
+        mf.mf_factor_free(f)
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+def test_inverse_variant_fp32_refinement(mf, orc, variant):
     rp, ci, v, perm = case_matrix("lap3d_jump_20")
     n = len(rp) - 1
     B = gen.rhs(n, 3, seed=5)
     opt = mf.mf_options_default()
-    opt.sptrsv = 2
+    opt.sptrsv = variant
     h = mf.mf_create(opt)
     s = mf.mf_symbolic_analyze(h, rp, ci, perm)
     f = mf.mf_factor_create(h, s, mf.MF_FP32)

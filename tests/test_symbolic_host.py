@@ -226,3 +226,24 @@ def test_condensed_invalid(mf, handle):
     with pytest.raises(mf.MFError) as e:
         mf.mf_symbolic_analyze_condensed(handle, rp, ci, None, node_of=bad)
     assert e.value.code == mf.MF_ERR_INVALID
+
+
+def test_sptrsv_option_values(mf, orc):
+    """Variants 1-3 are accepted (0 means 1); variant 3 adds the partitioned
+    inverse, the size of the large fronts' L, to the factor's memory."""
+    rp, ci, v, perm, _ = gen.config3(16)
+    sizes = {}
+    for variant in (0, 1, 2, 3):
+        opt = mf.mf_options_default()
+        opt.sptrsv = variant
+        h = mf.mf_create(opt)
+        s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+        sizes[variant] = mf.mf_symbolic_get_info(s)["factor_bytes_fp64"]
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
+    assert sizes[0] == sizes[1] < sizes[2] < sizes[3]
+    opt = mf.mf_options_default()
+    opt.sptrsv = 4
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_create(opt)
+    assert e.value.code == mf.MF_ERR_INVALID
