@@ -322,3 +322,70 @@ def test_fp32_tensor_core_update(mf, orc, case):
     assert r_fma <= 5e-4 and r_tc <= 5e-4
     # split-TF32 keeps FP32 accuracy: within a small factor of the FMA path
     assert r_tc <= 4.0 * r_fma + 1e-6
+
+
+def messy_csr(rp, ci, v, seed):
+    """The same matrix as a messier CSR: columns shuffled inside each row,
+    some entries split into two duplicates (summed back by the library), and
+    a few explicit zeros added symmetrically (structural entries)."""
+    rng = np.random.default_rng(seed)
+    n = len(rp) - 1
+    rows = [list(zip(ci[rp[i]:rp[i + 1]].tolist(), v[rp[i]:rp[i + 1]].tolist())) for i in range(n)]
+    for i in range(n):
+        out = []
+        for c, x in rows[i]:
+            if rng.random() < 0.2:
+                a = float(rng.uniform(-1.0, 1.0))
+                out += [(c, a), (c, x - a)]
+            else:
+                out.append((c, x))
+        rows[i] = out
+    for _ in range(n // 10):
+        i, j = (int(t) for t in rng.integers(0, n, 2))
+        if i != j:
+            rows[i].append((j, 0.0))
+            rows[j].append((i, 0.0))
+    for i in range(n):
+        rng.shuffle(rows[i])
+    nrp = np.zeros(n + 1, dtype=np.int64)
+    nrp[1:] = np.cumsum([len(r) for r in rows])
+    nci = np.array([c for r in rows for c, _ in r], dtype=np.int32)
+    nv = np.array([x for r in rows for _, x in r], dtype=np.float64)
+    return nrp, nci, nv
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_unsorted_duplicate_and_zero_entries(mf, handle, orc, prec):
+    rp, ci, v, perm, _ = gen.config3(12)
+    mrp, mci, mv = messy_csr(rp, ci, v, seed=3)
+    if prec == 0:
+        r = factor_and_compare(mf, handle, orc, mrp, mci, mv, perm, nrhs=2)
+        assert r["relF"] <= RELF64 and r["berr"] <= BERR
+        # the solution is that of the clean matrix
+        r0 = factor_and_compare(mf, handle, orc, rp, ci, v, perm, nrhs=2)
+        assert np.max(np.abs(r["X"] - r0["X"])) <= 1e-10 * np.max(np.abs(r0["X"]))
+    else:
+        s = mf.mf_symbolic_analyze(handle, mrp, mci, perm)
+        f = mf.mf_factor_create(handle, s, mf.MF_FP32)
+        try:
+            mf.mf_factor_numeric(f, mv)
+            B = gen.rhs(len(rp) - 1, 2, 4)
+            X, rep = mf.mf_solve_refined(f, B, tol=BERR, max_iter=30)
+            assert rep["fell_back"] == 0 and orc.berr(rp, ci, v, X, B) <= BERR
+        finally:
+            mf.mf_factor_free(f)
+            mf.mf_symbolic_free(s)
+
+
+def test_empty_matrix(mf, handle):
+    """n = 0: analysis, factorization and a solve of nothing succeed."""
+    rp = np.zeros(1, dtype=np.int64)
+    ci = np.zeros(0, dtype=np.int32)
+    s = mf.mf_symbolic_analyze(handle, rp, ci)
+    f = mf.mf_factor_create(handle, s, mf.MF_FP64)
+    try:
+        mf.mf_factor_numeric(f, np.zeros(0))
+        assert mf.mf_factor_export_L(f, 0).size == 0
+    finally:
+        mf.mf_factor_free(f)
+        mf.mf_symbolic_free(s)

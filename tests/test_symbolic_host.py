@@ -247,3 +247,29 @@ def test_sptrsv_option_values(mf, orc):
     with pytest.raises(mf.MFError) as e:
         mf.mf_create(opt)
     assert e.value.code == mf.MF_ERR_INVALID
+
+
+def test_messy_csr_same_integers(mf, handle, orc):
+    """Shuffled columns and duplicate entries leave every integer output
+    unchanged (explicit zeros are structural and are left out here)."""
+    rp, ci, v, perm, _ = gen.config3(10)
+    rng = np.random.default_rng(5)
+    n = len(rp) - 1
+    rows = []
+    for i in range(n):
+        r = ci[rp[i]:rp[i + 1]].tolist()
+        r += [c for c in r if rng.random() < 0.3]
+        rng.shuffle(r)
+        rows.append(r)
+    mrp = np.zeros(n + 1, dtype=np.int64)
+    mrp[1:] = np.cumsum([len(r) for r in rows])
+    mci = np.array([c for r in rows for c in r], dtype=np.int32)
+    a = mf.mf_symbolic_analyze(handle, rp, ci, perm)
+    b = mf.mf_symbolic_analyze(handle, mrp, mci, perm)
+    try:
+        for get in (mf.mf_symbolic_etree, mf.mf_symbolic_colcounts, mf.mf_symbolic_supernodes):
+            assert np.array_equal(get(a), get(b))
+        assert np.array_equal(mf.mf_symbolic_pattern(a)[1], mf.mf_symbolic_pattern(b)[1])
+    finally:
+        mf.mf_symbolic_free(a)
+        mf.mf_symbolic_free(b)
