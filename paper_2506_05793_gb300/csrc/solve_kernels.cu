@@ -547,12 +547,7 @@ __global__ void __launch_bounds__(256) k_fw_gemv(SD<T> d, int64_t item_off) {
     }
     __syncthreads();
 #pragma unroll 8
-    for (int j = g; j < cl; j += 4) {
-      const T l = Lr[(int64_t)(j0 + j) * nf];
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (r < nrhs) acc[r] = fma(l, sx[j * R + r], acc[r]);
-    }
+    for (int j = g; j < cl; j += 4) axpy_row<T, R>(acc, Lr[(int64_t)(j0 + j) * nf], sx + j * R);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r)
@@ -656,14 +651,38 @@ __global__ void __launch_bounds__(256) k_bw_gemv1(SD<T> d, int64_t item_off) {
 // [c0, c0 + bs) of a front takes Y(c0 + c, r) -= (L21^T X2)(c, r) as a small
 // GEMM over chunks of kBwRows update rows.  The chunk of L21 is staged
 // transposed in shared memory (coalesced loads, padded rows), the chunk of
-// X2 row-major; thread (c, g) accumulates column c for right-hand sides
-// g, g + 4, ... (the X2 reads are warp broadcasts).
+// X2 row-major; thread (c, g) accumulates column c for the R / 4 consecutive
+// right-hand sides of group g (16-byte shared reads, warp broadcasts).  The
+// next chunk's global loads are in registers while the current one is used.
 constexpr int kBwRows = 64;
 
 template <typename T, int R>
 constexpr size_t bw_gemm_smem() {
   return ((size_t)kNB * (kBwRows + 1) + (size_t)kBwRows * R) * sizeof(T);
 }
+
+// One chunk of rows [i0, i0 + kBwRows) of a column block, as registers: PL
+// values of the P / L block (transposed staging) and PX of the right-hand
+// side rows, then stored to shared memory after the previous chunk is done.
+template <typename T, int R>
+struct BwChunk {
+  static constexpr int PL = kNB * kBwRows / 256;
+  static constexpr int PX = kBwRows * R / 256;
+  T pl[PL], px[PX];
+  __device__ __forceinline__ void store(T* Ls, T* xs) const {
+    constexpr int lds = kBwRows + 1;
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      const int idx = threadIdx.x + u * 256;
+      Ls[(idx / kBwRows) * lds + idx % kBwRows] = pl[u];
+    }
+#pragma unroll
+    for (int u = 0; u < PX; ++u) {
+      const int idx = threadIdx.x + u * 256;
+      xs[(idx % kBwRows) * R + idx / kBwRows] = px[u];
+    }
+  }
+};
 
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_bw_gemm(SD<T> d, int64_t item_off) {
@@ -679,32 +698,36 @@ __global__ void __launch_bounds__(256) k_bw_gemm(SD<T> d, int64_t item_off) {
   const int tid = threadIdx.x, c = tid & (kNB - 1), g = tid >> 6;
   const T* Lp = d.L + f.Loff;
   const int32_t* frow = d.rowidx + f.rows_off + k;
+  BwChunk<T, R> nx;
+  auto fetch = [&](int i0) {
+    const int ch = min(kBwRows, m - i0);
+#pragma unroll
+    for (int u = 0; u < BwChunk<T, R>::PL; ++u) {
+      const int idx = tid + u * 256, cc = idx / kBwRows, i = idx % kBwRows;
+      nx.pl[u] = (cc < bs && i < ch) ? Lp[(int64_t)(c0 + cc) * nf + k + i0 + i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < BwChunk<T, R>::PX; ++u) {
+      const int idx = tid + u * 256, i = idx % kBwRows, r = idx / kBwRows;
+      nx.px[u] = (i < ch && r < nrhs) ? d.Y[(int64_t)r * d.n + frow[i0 + i]] : T(0);
+    }
+  };
   T acc[RG];
 #pragma unroll
   for (int q = 0; q < RG; ++q) acc[q] = T(0);
+  if (m > 0) fetch(0);
   for (int i0 = 0; i0 < m; i0 += kBwRows) {
-    const int ch = min(kBwRows, m - i0);
     __syncthreads();
-    for (int idx = tid; idx < kNB * kBwRows; idx += blockDim.x) {
-      const int cc = idx / kBwRows, i = idx % kBwRows;
-      Ls[cc * lds + i] = (cc < bs && i < ch) ? Lp[(int64_t)(c0 + cc) * nf + k + i0 + i] : T(0);
-    }
-    for (int idx = tid; idx < kBwRows * nrhs; idx += blockDim.x) {
-      const int i = idx % kBwRows, r = idx / kBwRows;
-      xs[i * R + r] = i < ch ? d.Y[(int64_t)r * d.n + frow[i0 + i]] : T(0);
-    }
+    nx.store(Ls, xs);
     __syncthreads();
+    if (i0 + kBwRows < m) fetch(i0 + kBwRows);
 #pragma unroll 4
-    for (int i = 0; i < kBwRows; ++i) {
-      const T l = Ls[c * lds + i];
-#pragma unroll
-      for (int q = 0; q < RG; ++q) acc[q] = fma(l, xs[i * R + g + 4 * q], acc[q]);
-    }
+    for (int i = 0; i < kBwRows; ++i) axpy_row<T, RG>(acc, Ls[c * lds + i], xs + i * R + g * RG);
   }
   if (c < bs) {
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
-      const int r = g + 4 * q;
+      const int r = g * RG + q;
       if (r < nrhs) d.Y[(int64_t)r * d.n + f.first + c0 + c] -= acc[q];
     }
   }
@@ -821,12 +844,7 @@ __global__ void __launch_bounds__(256) k_fw_pinv(SD<T> d, int64_t item_off) {
     }
     __syncthreads();
 #pragma unroll 8
-    for (int j = g; j < cl; j += 4) {
-      const T l = Pr[(int64_t)(j0 + j) * nf];
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (r < nrhs) acc[r] = fma(l, sx[j * R + r], acc[r]);
-    }
+    for (int j = g; j < cl; j += 4) axpy_row<T, R>(acc, Pr[(int64_t)(j0 + j) * nf], sx + j * R);
   }
 #pragma unroll
   for (int r = 0; r < R; ++r)
@@ -891,7 +909,8 @@ __global__ void __launch_bounds__(256) k_bw_pinv1(SD<T> d, int64_t item_off) {
 }
 
 // Backward product, R >= 8 right-hand sides: chunks of kBwRows rows from the
-// block's first column down, staged transposed (P) and row-major (v).
+// block's first column down, staged transposed (P) and row-major (v), the
+// next chunk prefetched into registers as in k_bw_gemm.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_bw_pinv(SD<T> d, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -906,36 +925,40 @@ __global__ void __launch_bounds__(256) k_bw_pinv(SD<T> d, int64_t item_off) {
   const int tid = threadIdx.x, c = tid & (kNB - 1), g = tid >> 6;
   const T* Pp = d.P + f.Loff;
   const int32_t* frow = d.rowidx + f.rows_off;
-  T acc[RG];
-#pragma unroll
-  for (int q = 0; q < RG; ++q) acc[q] = T(0);
-  for (int i0 = c0; i0 < nf; i0 += kBwRows) {
+  BwChunk<T, R> nx;
+  auto fetch = [&](int i0) {
     const int ch = min(kBwRows, nf - i0);
-    __syncthreads();
-    for (int idx = tid; idx < kNB * kBwRows; idx += blockDim.x) {
-      const int cc = idx / kBwRows, i = idx % kBwRows;
-      Ls[cc * lds + i] = (cc < bs && i < ch) ? Pp[(int64_t)(c0 + cc) * nf + i0 + i] : T(0);
+#pragma unroll
+    for (int u = 0; u < BwChunk<T, R>::PL; ++u) {
+      const int idx = tid + u * 256, cc = idx / kBwRows, i = idx % kBwRows;
+      nx.pl[u] = (cc < bs && i < ch) ? Pp[(int64_t)(c0 + cc) * nf + i0 + i] : T(0);
     }
-    for (int idx = tid; idx < kBwRows * R; idx += blockDim.x) {
-      const int i = idx % kBwRows, r = idx / kBwRows;
+#pragma unroll
+    for (int u = 0; u < BwChunk<T, R>::PX; ++u) {
+      const int idx = tid + u * 256, i = idx % kBwRows, r = idx / kBwRows;
       const int gi = i0 + i;
       T v = T(0);
       if (i < ch && r < nrhs)
         v = gi < k ? d.W[(f.woff + gi) * nrhs + r] : d.Y[(int64_t)r * d.n + frow[gi]];
-      xs[i * R + r] = v;
+      nx.px[u] = v;
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int i = 0; i < kBwRows; ++i) {
-      const T l = Ls[c * lds + i];
+  };
+  T acc[RG];
 #pragma unroll
-      for (int q = 0; q < RG; ++q) acc[q] = fma(l, xs[i * R + g + 4 * q], acc[q]);
-    }
+  for (int q = 0; q < RG; ++q) acc[q] = T(0);
+  fetch(c0);
+  for (int i0 = c0; i0 < nf; i0 += kBwRows) {
+    __syncthreads();
+    nx.store(Ls, xs);
+    __syncthreads();
+    if (i0 + kBwRows < nf) fetch(i0 + kBwRows);
+#pragma unroll 4
+    for (int i = 0; i < kBwRows; ++i) axpy_row<T, RG>(acc, Ls[c * lds + i], xs + i * R + g * RG);
   }
   if (c < bs) {
 #pragma unroll
     for (int q = 0; q < RG; ++q) {
-      const int r = g + 4 * q;
+      const int r = g * RG + q;
       if (r < nrhs) d.Y[(int64_t)r * d.n + f.first + c0 + c] = acc[q];
     }
   }
@@ -1078,24 +1101,26 @@ __global__ void __launch_bounds__(256) k_bw_tiny(SD<T> d, int64_t item_off, int6
 
 // ---------------------------------------------------------------------------
 // Fronts with 64 < k + m <= 32 H: one warp per front (8 per CTA), no flags;
-// the front's work vector is staged in shared memory.  Forward, per block of
-// 32 pivots [jb, jb + 32): the 32 x 32 triangle is solved in registers (lane
-// l owns row jb + l, one shuffle per pivot), then the rows below take
-// w_i -= sum_jj L(i, jb + jj) x_jj with all 32 loads of a row issued
-// together.  Rows of earlier blocks are not read again.
+// the front's work vectors for RB right-hand sides are staged in shared
+// memory (ws[i * RB + q]).  Forward, per block of 32 pivots [jb, jb + 32):
+// the 32 x 32 triangle is solved in registers (lane l owns row jb + l, one
+// shuffle per pivot and RHS, the RB solves interleaved), then the rows below
+// take w_i -= sum_jj L(i, jb + jj) x_jj with all loads of a row issued
+// together and each L value used for the RB right-hand sides.  Rows of
+// earlier blocks are not read again.
 // ---------------------------------------------------------------------------
-template <typename T, int H>
+template <typename T, int H, int RB>
 __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, int64_t count) {
   constexpr int LB = sizeof(T) == 8 ? 16 : 32;  // L loads issued together
-  __shared__ T ws_all[8 * 32 * H];
+  __shared__ __align__(16) T ws_all[8 * 32 * H * RB];
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
   const int64_t w_id = (int64_t)blockIdx.x * 8 + wq;
   if (w_id >= count) return;
-  T* ws = ws_all + wq * 32 * H;
+  T* ws = ws_all + wq * 32 * H * RB;
   const SnInfo f = d.sn[d.items[item_off + w_id].s];
   const int k = f.k, nf = k + f.m, nrhs = d.nrhs;
   const T* Lp = d.L + f.Loff;
-  for (int r = 0; r < nrhs; ++r) {
+  for (int rb = 0; rb < nrhs; rb += RB) {
     __syncwarp();
     {
       int64_t e0[H], e1[H];
@@ -1108,9 +1133,16 @@ __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, i
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int i = lane + 32 * h;
-        T v = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
-        for (int64_t e = e0[h]; e < e1[h]; ++e) v += d.W[d.ginv_src[e] * nrhs + r];
-        ws[i] = v;
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+          const int r = rb + q;
+          T v = T(0);
+          if (r < nrhs) {
+            if (i < k) v = d.Y[(int64_t)r * d.n + f.first + i];
+            for (int64_t e = e0[h]; e < e1[h]; ++e) v += d.W[d.ginv_src[e] * nrhs + r];
+          }
+          ws[i * RB + q] = v;
+        }
       }
     }
     __syncwarp();
@@ -1124,21 +1156,31 @@ __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, i
       for (int jj = 0; jj < 32; ++jj) dl[jj] = Lp[(int64_t)(jb + min(jj, bc - 1)) * nf + ir];
       const int id = jb + min(lane, bc - 1);
       const T rdb = lane < bc ? T(1) / Lp[(int64_t)id * nf + id] : T(0);
-      T v = ws[jb + lane];
+      T v[RB];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) v[q] = ws[(jb + lane) * RB + q];
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         if (jj < bc) {
-          const T xj = __shfl_sync(0xffffffffu, v * rdb, jj);
-          if (lane == jj) v = xj;
-          else if (lane > jj) v = fma(-dl[jj], xj, v);
+#pragma unroll
+          for (int q = 0; q < RB; ++q) {
+            const T xj = __shfl_sync(0xffffffffu, v[q] * rdb, jj);
+            if (lane == jj) v[q] = xj;
+            else if (lane > jj) v[q] = fma(-dl[jj], xj, v[q]);
+          }
         }
       }
-      if (jb + lane < nf) ws[jb + lane] = v;
+      if (jb + lane < nf) {
+#pragma unroll
+        for (int q = 0; q < RB; ++q) ws[(jb + lane) * RB + q] = v[q];
+      }
       __syncwarp();
       // later rows: w_i -= sum_jj L(i, jb + jj) x_jj (x_jj = ws[jb + jj])
       for (int i = jb + 32 + lane; i < nf + lane; i += 32) {
         const int ic = min(i, nf - 1);
-        T u = ws[ic];
+        T u[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) u[q] = ws[ic * RB + q];
 #pragma unroll
         for (int q0 = 0; q0 < 32; q0 += LB) {
           T lv[LB];
@@ -1146,17 +1188,25 @@ __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, i
           for (int q = 0; q < LB; ++q) lv[q] = Lp[(int64_t)(jb + min(q0 + q, bc - 1)) * nf + ic];
 #pragma unroll
           for (int q = 0; q < LB; ++q)
-            if (q0 + q < bc) u = fma(-lv[q], ws[jb + q0 + q], u);
+            if (q0 + q < bc) axpy_row<T, RB>(u, -lv[q], ws + (jb + q0 + q) * RB);
         }
-        if (i < nf) ws[i] = u;
+        if (i < nf) {
+#pragma unroll
+          for (int q = 0; q < RB; ++q) ws[i * RB + q] = u[q];
+        }
       }
       __syncwarp();
     }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       const int i = lane + 32 * h;
-      if (i < k) d.Y[(int64_t)r * d.n + f.first + i] = ws[i];
-      else if (i < nf) d.W[(f.woff + i) * nrhs + r] = ws[i];
+#pragma unroll
+      for (int q = 0; q < RB; ++q) {
+        const int r = rb + q;
+        if (r >= nrhs) break;
+        if (i < k) d.Y[(int64_t)r * d.n + f.first + i] = ws[i * RB + q];
+        else if (i < nf) d.W[(f.woff + i) * nrhs + r] = ws[i * RB + q];
+      }
     }
   }
 }
@@ -1420,8 +1470,18 @@ void launch_warp(bool fw, const Launch& L, const SolveArgs& a, cudaStream_t st) 
       else k_bw_tiny<T, 1><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
     }
   } else {
-    if (fw) k_fw_warp<T, H><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
-    else k_bw_warp<T, H><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    // right-hand sides per pass of the forward kernel: as many as its static
+    // shared memory (8 warps x 32 H rows x RB values) allows, up to 4
+    constexpr int rb_max = (48 * 1024) / (8 * 32 * H * (int)sizeof(T));
+    if (!fw) {
+      k_bw_warp<T, H><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    } else if (a.nrhs >= 4 && rb_max >= 4) {
+      if constexpr (rb_max >= 4) k_fw_warp<T, H, 4><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    } else if (a.nrhs >= 2 && rb_max >= 2) {
+      if constexpr (rb_max >= 2) k_fw_warp<T, H, 2><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    } else {
+      k_fw_warp<T, H, 1><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+    }
   }
 }
 
