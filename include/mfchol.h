@@ -173,6 +173,19 @@ int mf_symbolic_analyze_batch(mf_handle* h, int32_t count, const int64_t* ns,
                               const int32_t* const* colinds,
                               const int32_t* const* perms, mf_symbolic** s);
 
+/* Checkpoint / restart of the analysis (the paper has no counterpart; the
+ * analysis depends on the pattern only, so a restarted program can load it
+ * instead of repeating it).  mf_symbolic_save writes the complete analysis,
+ * schedules included, to the file at path; mf_symbolic_load reads it back
+ * into a new object owned by the caller (release with mf_symbolic_free).  The
+ * loaded analysis keeps the options it was made with (relaxation,
+ * small-front limit, SpTRSV variant), not h's.  The format is native-endian
+ * and tied to this library version: a file from another version or kind of
+ * machine, or a truncated or corrupt file, gives MF_ERR_INVALID, as does a
+ * path that cannot be opened.  Host only. */
+int mf_symbolic_save(const mf_symbolic* s, const char* path);
+int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s);
+
 int mf_symbolic_free(mf_symbolic* s);
 int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info);
 /* parent[j] of the column elimination tree (-1 for roots), n entries. */

@@ -67,6 +67,8 @@ _SIGS = {
     "mf_symbolic_analyze": [_P, _I64, _P, _P, _P, _P],
     "mf_symbolic_analyze_batch": [_P, _I32, _P, _P, _P, _P, _P],
     "mf_symbolic_analyze_condensed": [_P, _I64, _P, _P, _P, _P, _I32, _P],
+    "mf_symbolic_save": [_P, ctypes.c_char_p],
+    "mf_symbolic_load": [_P, ctypes.c_char_p, _P],
     "mf_symbolic_free": [_P],
     "mf_symbolic_get_info": [_P, _P],
     "mf_symbolic_etree": [_P, _P],
@@ -180,6 +182,16 @@ def mf_symbolic_analyze_condensed(h, rowptr, colind, perm=None, node_of=None, bl
     _check(lib().mf_symbolic_analyze_condensed(h, len(rowptr) - 1, _ptr(rowptr), _ptr(colind),
                                                _ptr(perm), _ptr(node_of), int(block),
                                                ctypes.byref(s)))
+    return s
+
+
+def mf_symbolic_save(s, path):
+    _check(lib().mf_symbolic_save(s, os.fsencode(path)))
+
+
+def mf_symbolic_load(h, path):
+    s = ctypes.c_void_p()
+    _check(lib().mf_symbolic_load(h, os.fsencode(path), ctypes.byref(s)))
     return s
 
 

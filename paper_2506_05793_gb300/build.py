@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libmfchol.so")
-SOURCES = ["symbolic.cpp", "capi.cpp", "factor_kernels.cu", "solve_kernels.cu", "noalloc.cu", "factor_tc.cu",
+SOURCES = ["symbolic.cpp", "symbolic_io.cpp", "capi.cpp", "factor_kernels.cu", "solve_kernels.cu", "noalloc.cu", "factor_tc.cu",
            "serve.cpp"]
 HEADERS = ["mf_internal.h", "kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 #include "mf_internal.h"
 
@@ -96,6 +98,16 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
   out = o;
   return MF_OK;
 }
+
+// NVTX range over one API phase (symbolic analysis, numeric factorization,
+// solve, refined solve), visible in timeline profilers; a no-op unless a
+// tool is attached.
+struct PhaseRange {
+  explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+  ~PhaseRange() { nvtxRangePop(); }
+  PhaseRange(const PhaseRange&) = delete;
+  PhaseRange& operator=(const PhaseRange&) = delete;
+};
 
 size_t elem_size(int prec) { return prec == MF_FP32 ? sizeof(float) : sizeof(double); }
 
@@ -244,6 +256,7 @@ int64_t mf_last_error_column(void) { return g_errcol; }
 static int analyze_common(mf_handle* h, int64_t n, const int64_t* rowptr,
                           const int32_t* colind, const int32_t* perm, const int32_t* node_of,
                           mf_symbolic** s) {
+  PhaseRange range_("mf_symbolic_analyze");
   if (!h || !s) return set_error(MF_ERR_INVALID, "NULL handle or output");
   *s = nullptr;
   mf_symbolic* S = new (std::nothrow) mf_symbolic();
@@ -533,6 +546,7 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
 
 int mf_factor_numeric(mf_factor* f, const double* values, int32_t values_on_device, void* stream,
                       int32_t async) {
+  PhaseRange range_("mf_factor_numeric");
   if (!f || (!values && f->S->nnzA)) return set_error(MF_ERR_INVALID, "NULL argument");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const mf_symbolic* S = f->S;
@@ -886,6 +900,7 @@ extern "C" {
 
 int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
              int32_t on_device, void* stream) {
+  PhaseRange range_("mf_solve");
   if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
   const int64_t n = f->S->n;
   if (nrhs < 0 || ldb < n || ldx < n || (nrhs > 0 && n > 0 && (!B || !X)))
@@ -913,6 +928,7 @@ int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X
 int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X,
                      int64_t ldx, int32_t on_device, double tol, int32_t max_iter,
                      int32_t allow_fallback, mf_ir_report* rep, void* stream) {
+  PhaseRange range_("mf_solve_refined");
   if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
   const mf_symbolic* S = f->S;
   const int64_t n = S->n;

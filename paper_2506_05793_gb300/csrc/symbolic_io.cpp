@@ -1,0 +1,232 @@
+// symbolic_io.cpp -- save and load a symbolic analysis (restart without
+// repeating the host analysis).  The paper has no counterpart; the analysis
+// depends on the pattern only (Sec. 2, phase 1), so a program that factors
+// the same pattern again after a restart can load it instead.
+//
+// Format: a fixed header (magic, version, byte-order mark, sizes of the
+// record types), then every member of mf_symbolic in declaration order:
+// scalars as raw bytes, vectors as a 64-bit count followed by the elements.
+// Native byte order: a file is read back on the same kind of machine.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "mf_internal.h"
+
+namespace {
+
+constexpr char kMagic[8] = {'M', 'F', 'S', 'Y', 'M', 'B', 'O', 'L'};
+constexpr uint32_t kVersion = 1;
+constexpr uint32_t kByteOrder = 0x01020304u;
+
+struct Header {
+  char magic[8];
+  uint32_t version;
+  uint32_t byte_order;
+  uint32_t size_sninfo, size_item, size_launch, size_pointer;
+};
+
+Header make_header() {
+  Header h;
+  std::memcpy(h.magic, kMagic, sizeof(kMagic));
+  h.version = kVersion;
+  h.byte_order = kByteOrder;
+  h.size_sninfo = sizeof(mf::SnInfo);
+  h.size_item = sizeof(mf::Item);
+  h.size_launch = sizeof(mf::Launch);
+  h.size_pointer = sizeof(void*);
+  return h;
+}
+
+struct Writer {
+  FILE* f;
+  bool ok = true;
+  void raw(const void* p, size_t n) {
+    if (ok && n && std::fwrite(p, 1, n, f) != n) ok = false;
+  }
+  template <typename T>
+  void operator()(const T& v) {
+    static_assert(std::is_trivially_copyable<T>::value, "raw scalar");
+    raw(&v, sizeof(T));
+  }
+  template <typename T>
+  void operator()(const std::vector<T>& v) {
+    static_assert(std::is_trivially_copyable<T>::value, "raw elements");
+    const uint64_t n = v.size();
+    raw(&n, sizeof(n));
+    raw(v.data(), n * sizeof(T));
+  }
+};
+
+struct Reader {
+  FILE* f;
+  uint64_t left;  // bytes not yet read
+  bool ok = true;
+  void raw(void* p, size_t n) {
+    if (!ok) return;
+    if (n > left || (n && std::fread(p, 1, n, f) != n)) {
+      ok = false;
+      return;
+    }
+    left -= n;
+  }
+  template <typename T>
+  void operator()(T& v) {
+    static_assert(std::is_trivially_copyable<T>::value, "raw scalar");
+    raw(&v, sizeof(T));
+  }
+  template <typename T>
+  void operator()(std::vector<T>& v) {
+    static_assert(std::is_trivially_copyable<T>::value, "raw elements");
+    uint64_t n = 0;
+    raw(&n, sizeof(n));
+    // a count the rest of the file cannot hold is corruption, not a reason
+    // to allocate
+    if (!ok || n > left / sizeof(T)) {
+      ok = false;
+      return;
+    }
+    v.resize(n);
+    raw(v.data(), n * sizeof(T));
+  }
+};
+
+// Every member of the analysis, in one place for both directions.
+template <class IO, class S>
+void members(IO& io, S& s) {
+  io(s.n);
+  io(s.nnzA);
+  io(s.rowptr);
+  io(s.colind);
+  io(s.perm);
+  io(s.iperm);
+  io(s.parent);
+  io(s.colcount);
+  io(s.sup_ptr);
+  io(s.col2sn);
+  io(s.fs_rowidx);
+  io(s.fs_rows_off);
+  io(s.low_cp);
+  io(s.low_cr);
+  io(s.fs_parent);
+  io(s.relax);
+  io(s.front_ptr);
+  io(s.col2front);
+  io(s.front_flops);
+  io(s.nsuper);
+  io(s.nnzL);
+  io(s.nnz_lower);
+  io(s.flops);
+  io(s.nlevels);
+  io(s.max_front);
+  io(s.max_k);
+  io(s.sn);
+  io(s.children);
+  io(s.rowidx);
+  io(s.relmap);
+  io(s.slevel);
+  io(s.acol_ptr);
+  io(s.arow);
+  io(s.asrc_ptr);
+  io(s.asrc);
+  io(s.Lsize);
+  io(s.Usize);
+  io(s.Wsize);
+  io(s.items);
+  io(s.fsched);
+  io(s.fsched_tc);
+  io(s.soff);
+  io(s.split_rows);
+  io(s.split_rows_b);
+  io(s.max_large);
+  io(s.keep_inv);
+  io(s.ioff);
+  io(s.ninv);
+  io(s.pinv);
+  io(s.pinv_flops);
+  io(s.arange);
+  io(s.fwsched);
+  io(s.bwsched);
+  io(s.blkoff);
+  io(s.ginv_ptr);
+  io(s.ginv_src);
+}
+
+// Sizes that the rest of the library relies on without checking again.
+bool consistent(const mf_symbolic& s) {
+  const size_t n = (size_t)s.n;
+  if (s.n < 0 || s.rowptr.size() != n + 1 || s.perm.size() != n || s.iperm.size() != n ||
+      s.parent.size() != n || s.colcount.size() != n || s.col2front.size() != n)
+    return false;
+  if ((int64_t)s.colind.size() != s.nnzA || (n && s.rowptr[n] != s.nnzA)) return false;
+  if (s.sup_ptr.size() != (size_t)(n ? s.nsuper + 1 : (s.sup_ptr.empty() ? 0 : 1))) return false;
+  const size_t nf = s.sn.size();
+  if (s.slevel.size() != nf || s.soff.size() != nf || s.ioff.size() != nf ||
+      s.blkoff.size() != nf + 1 || s.front_ptr.size() != nf + 1)
+    return false;
+  if (s.ginv_ptr.size() != (size_t)s.Wsize + 1) return false;
+  if (s.acol_ptr.size() != n + 1 || (int64_t)s.arow.size() != s.nnz_lower) return false;
+  for (const auto* sched : {&s.fsched, &s.fsched_tc, &s.fwsched, &s.bwsched})
+    for (const mf::Launch& L : *sched)
+      if (L.item_off < 0 || L.count < 0 || (size_t)(L.item_off + L.count) > s.items.size())
+        return false;
+  for (const mf::Item& it : s.items)
+    if (it.s < -1 || it.s >= (int64_t)nf) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mf_symbolic_save(const mf_symbolic* s, const char* path) {
+  if (!s || !path) return mf::set_error(MF_ERR_INVALID, "NULL argument");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return mf::set_error(MF_ERR_INVALID, std::string("cannot open for writing: ") + path);
+  Writer w{f};
+  const Header h = make_header();
+  w.raw(&h, sizeof(h));
+  members(w, *s);
+  const bool closed = std::fclose(f) == 0;
+  if (!w.ok || !closed) return mf::set_error(MF_ERR_INVALID, std::string("write failed: ") + path);
+  return MF_OK;
+}
+
+int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s) {
+  if (!h || !path || !s) return mf::set_error(MF_ERR_INVALID, "NULL argument");
+  *s = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return mf::set_error(MF_ERR_INVALID, std::string("cannot open: ") + path);
+  std::fseek(f, 0, SEEK_END);
+  const long size = std::ftell(f);
+  std::fseek(f, 0, SEEK_SET);
+  Reader r{f, size > 0 ? (uint64_t)size : 0};
+  Header hd;
+  r.raw(&hd, sizeof(hd));
+  const Header want = make_header();
+  if (!r.ok || std::memcmp(&hd, &want, sizeof(hd)) != 0) {
+    std::fclose(f);
+    return mf::set_error(MF_ERR_INVALID, "not a symbolic analysis of this library version/machine");
+  }
+  mf_symbolic* S = new (std::nothrow) mf_symbolic();
+  if (!S) {
+    std::fclose(f);
+    return mf::set_error(MF_ERR_OOM, "host allocation failed");
+  }
+  try {
+    members(r, *S);
+  } catch (const std::bad_alloc&) {
+    r.ok = false;
+  }
+  std::fclose(f);
+  if (!r.ok || r.left != 0 || !consistent(*S)) {
+    delete S;
+    return mf::set_error(MF_ERR_INVALID, std::string("truncated or corrupt file: ") + path);
+  }
+  *s = S;
+  return MF_OK;
+}
+
+}  // extern "C"

@@ -389,3 +389,33 @@ def test_empty_matrix(mf, handle):
     finally:
         mf.mf_factor_free(f)
         mf.mf_symbolic_free(s)
+
+
+def test_loaded_analysis_factors_identically(mf, orc, tmp_path):
+    """An analysis saved and loaded back drives the same kernels: the factor
+    and the solution are bit for bit those of the original analysis."""
+    rp, ci, v, perm, _ = gen.config3(16)
+    opt = mf.mf_options_default()
+    opt.sptrsv = 3
+    h = mf.mf_create(opt)
+    s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+    path = str(tmp_path / "a.sym")
+    mf.mf_symbolic_save(s, path)
+    t = mf.mf_symbolic_load(h, path)
+    out = []
+    try:
+        B = gen.rhs(len(rp) - 1, 3, 9)
+        for sym in (s, t):
+            f = mf.mf_factor_create(h, sym, mf.MF_FP64)
+            try:
+                mf.mf_factor_numeric(f, v)
+                Lx = mf.mf_factor_export_L(f, mf.mf_symbolic_get_info(sym)["nnz_L"])
+                out.append((Lx, mf.mf_solve(f, B)))
+            finally:
+                mf.mf_factor_free(f)
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+        assert orc.berr(rp, ci, v, out[1][1], B) <= BERR
+    finally:
+        mf.mf_symbolic_free(s)
+        mf.mf_symbolic_free(t)
+        mf.mf_destroy(h)

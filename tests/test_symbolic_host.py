@@ -273,3 +273,51 @@ def test_messy_csr_same_integers(mf, handle, orc):
     finally:
         mf.mf_symbolic_free(a)
         mf.mf_symbolic_free(b)
+
+
+def test_save_and_load_round_trip(mf, handle, orc, tmp_path):
+    """A saved analysis loads back identical: every integer output, the info
+    record, and a byte-identical second save."""
+    rp, ci, v, perm, _ = gen.config3(12)
+    opt = mf.mf_options_default()
+    opt.sptrsv = 3
+    h3 = mf.mf_create(opt)
+    s = mf.mf_symbolic_analyze(h3, rp, ci, perm)
+    mf.mf_symbolic_pattern(s)  # builds the lazily kept supernode rows first
+    p1, p2 = tmp_path / "a.sym", tmp_path / "b.sym"
+    mf.mf_symbolic_save(s, str(p1))
+    t = mf.mf_symbolic_load(handle, str(p1))
+    try:
+        for get in (mf.mf_symbolic_etree, mf.mf_symbolic_colcounts, mf.mf_symbolic_supernodes):
+            assert np.array_equal(get(s), get(t))
+        assert np.array_equal(mf.mf_symbolic_pattern(s)[1], mf.mf_symbolic_pattern(t)[1])
+        assert mf.mf_symbolic_get_info(s) == mf.mf_symbolic_get_info(t)
+        mf.mf_symbolic_save(t, str(p2))
+        assert p1.read_bytes() == p2.read_bytes()
+    finally:
+        mf.mf_symbolic_free(s)
+        mf.mf_symbolic_free(t)
+        mf.mf_destroy(h3)
+
+
+def test_load_rejects_bad_files(mf, handle, tmp_path):
+    rp, ci, _ = gen.laplacian_2d(9)
+    s = mf.mf_symbolic_analyze(handle, rp, ci)
+    good = tmp_path / "g.sym"
+    mf.mf_symbolic_save(s, str(good))
+    mf.mf_symbolic_free(s)
+    data = good.read_bytes()
+    cases = {"missing": None, "empty": b"", "truncated": data[:len(data) // 2],
+             "magic": b"X" + data[1:], "trailing": data + b"\\0" * 8}
+    # a vector count far beyond the file: the count of rowptr follows the
+    # header (32 bytes) and the two int64 scalars n, nnzA
+    bad = bytearray(data)
+    bad[48:56] = (1 << 60).to_bytes(8, "little")
+    cases["count"] = bytes(bad)
+    for name, content in cases.items():
+        p = tmp_path / (name + ".sym")
+        if content is not None:
+            p.write_bytes(content)
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_symbolic_load(handle, str(p))
+        assert e.value.code == mf.MF_ERR_INVALID, name
