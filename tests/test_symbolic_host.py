@@ -321,3 +321,20 @@ def test_load_rejects_bad_files(mf, handle, tmp_path):
         with pytest.raises(mf.MFError) as e:
             mf.mf_symbolic_load(handle, str(p))
         assert e.value.code == mf.MF_ERR_INVALID, name
+
+
+def test_factor_over_budget_is_oom(mf):
+    """A device budget smaller than the factor's bytes refuses the factor
+    before any device allocation (host-side check, no GPU needed)."""
+    opt = mf.mf_options_default()
+    opt.budget_bytes = 1024
+    h = mf.mf_create(opt)
+    rp, ci, _ = gen.laplacian_2d(20)
+    s = mf.mf_symbolic_analyze(h, rp, ci)
+    try:
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_factor_create(h, s, mf.MF_FP64)
+        assert e.value.code == mf.MF_ERR_OOM
+    finally:
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
