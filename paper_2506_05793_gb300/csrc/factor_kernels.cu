@@ -151,41 +151,53 @@ __global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) 
 }
 
 // ---------------------------------------------------------------------------
-// Large fronts, assembly of a chunk of front columns [a, b): zero, scatter
-// the entries of A, then pull every child's update matrix in order.
+// Large fronts, assembly of a chunk of front columns [a, b).  Warp w owns the
+// columns a + w, a + w + 8, ...: it zeroes each one, scatters the entries of
+// A into it, then adds every child's update column that lands on it,
+// children in their fixed order.  A parent column has a single owner, so the
+// CTA needs no barrier and the sums are deterministic.  The child columns
+// landing in [a, b) are the range [lo, hi) of the child's (increasing)
+// relative map; the one landing on column c is found by bisection.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_assemble(FD<T> d, int64_t item_off) {
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int k = f.k, nf = k + f.m, c0 = it.a, c1 = it.b;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = c0 + warp; c < c1; c += nw) {
-    T* col = front_col(d, f, c);
-    const int r0 = c < k ? 0 : c;
-    for (int r = r0 + lane; r < nf; r += 32) col[r] = T(0);
-  }
-  __syncthreads();
-  const int ce = c1 < k ? c1 : k;
-  for (int c = c0 + warp; c < ce; c += nw) {
-    T* col = front_col(d, f, c);
-    const int g = f.first + c;
-    for (int64_t e = d.acol_ptr[g] + lane; e < d.acol_ptr[g + 1]; e += 32)
-      col[d.arow[e]] = d.av[e];
-  }
-  __syncthreads();
-  for (const Item* rg = d.arange + it.t; rg->s >= 0; ++rg) {
-    const SnInfo ch = d.sn[rg->s];
-    const int mc = ch.m;
-    const int32_t* map = d.relmap + ch.map_off;
-    const int lo = rg->t, hi = rg->a;
-    const T* Uc = d.U + ch.Uoff;
-    for (int jc = lo + warp; jc < hi; jc += nw) {
-      T* col = front_col(d, f, map[jc]);
-      const T* u = Uc + (int64_t)jc * mc;
-      for (int ic = jc + lane; ic < mc; ic += 32) col[map[ic]] += u[ic];
+    T* __restrict__ col = front_col(d, f, c);
+    for (int r = (c < k ? 0 : c) + lane; r < nf; r += 32) col[r] = T(0);
+    __syncwarp();
+    if (c < k) {
+      const int g = f.first + c;
+      for (int64_t e = d.acol_ptr[g] + lane; e < d.acol_ptr[g + 1]; e += 32)
+        col[d.arow[e]] = d.av[e];
+      __syncwarp();
     }
-    __syncthreads();
+    for (const Item* rg = d.arange + it.t; rg->s >= 0; ++rg) {
+      const SnInfo ch = d.sn[rg->s];
+      const int32_t* __restrict__ map = d.relmap + ch.map_off;
+      int lo = rg->t, hi = rg->a;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (map[mid] < c) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= rg->a || map[lo] != c) continue;
+      const int jc = lo, mc = ch.m;
+      const T* __restrict__ u = d.U + ch.Uoff + (int64_t)jc * mc;
+      int ic = jc + lane;
+      for (; ic + 32 < mc; ic += 64) {
+        const int p0 = map[ic], p1 = map[ic + 32];
+        const T v0 = u[ic], v1 = u[ic + 32];
+        const T a0 = col[p0], a1 = col[p1];
+        col[p0] = a0 + v0;
+        col[p1] = a1 + v1;
+      }
+      if (ic < mc) col[map[ic]] += u[ic];
+      __syncwarp();
+    }
   }
 }
 
