@@ -8,7 +8,9 @@
  * pattern, repeated numerical factorizations as values change, many solves
  * per factorization).  The factorization is Tacho's multifrontal Cholesky of
  * an SPD matrix with level-set scheduling (paper Sec. 5); the solve is the
- * level-set supernodal SpTRSV ("variant 1", paper Sec. 5).
+ * level-set supernodal SpTRSV of paper Sec. 5, in its variants 1 (diagonal
+ * blocks by substitution), 2 (inverted diagonal blocks, the default) and 3
+ * (partitioned inverse), chosen by mf_options.sptrsv.
  *
  * Conventions
  *   - A is given as FULL symmetric CSR: rowptr (int64, n+1 entries, rowptr[0]
