@@ -27,6 +27,7 @@ import os
 import subprocess
 import sys
 import threading
+import tempfile
 import time
 
 import numpy as np
@@ -159,7 +160,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % index)
+        # raw samples go to BENCH_CLOCKS_DIR (default: the system temp dir);
+        # the JSON line carries their summary
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "clocks_bench_%d.csv" % index)
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
