@@ -52,22 +52,29 @@ def build(force=False):
     return _LIB
 
 
+def load_library(path):
+    """Open a compiled oracle.c with its argument types declared.  The tests
+    that plant a mistake in a copy of oracle.c load that copy with this and
+    put it in place of the real library while the pins run."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int64
+    lib.orc_etree.argtypes = [I, P, P, P, P]
+    lib.orc_counts.argtypes = [I, P, P, P, P, P, P, P]
+    lib.orc_pattern.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P]
+    lib.orc_factor.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P]
+    lib.orc_factor.restype = ctypes.c_int64
+    lib.orc_supernodes.argtypes = [I, P, P, P, P]
+    lib.orc_supernodes.restype = ctypes.c_int64
+    lib.orc_solve.argtypes = [I, P, P, P, P, I, I]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_LIB)
-        P = ctypes.c_void_p
-        I = ctypes.c_int64
-        lib.orc_etree.argtypes = [I, P, P, P, P]
-        lib.orc_counts.argtypes = [I, P, P, P, P, P, P, P]
-        lib.orc_pattern.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P]
-        lib.orc_factor.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P]
-        lib.orc_factor.restype = ctypes.c_int64
-        lib.orc_supernodes.argtypes = [I, P, P, P, P]
-        lib.orc_supernodes.restype = ctypes.c_int64
-        lib.orc_solve.argtypes = [I, P, P, P, P, I, I]
-        _lib = lib
+        _lib = load_library(_LIB)
     return _lib
 
 

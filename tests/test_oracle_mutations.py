@@ -1,0 +1,105 @@
+"""The oracle's pins must catch plausible mistakes.  Each case plants one
+mistake in a copy of oracle/oracle.c (a wrong sign, a dropped term, a
+transposed operand, a wrong index, a wrong operation), compiles it with gcc,
+runs the pins against it on the CPU and requires at least one to fail.  Only
+mistakes that keep every array size consistent are planted, so a mutated
+oracle computes wrong numbers but never writes outside its buffers."""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import gen
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                   "oracle.c")
+
+MUTATIONS = [
+    ("factor: update sign flipped", "x[Li[t]] -= Lx[t] * ljk;", "x[Li[t]] += Lx[t] * ljk;"),
+    ("factor: diagonal term of the update dropped",
+     "for (int64_t t = q; t < Lp[k + 1]; ++t) x[Li[t]]",
+     "for (int64_t t = q + 1; t < Lp[k + 1]; ++t) x[Li[t]]"),
+    ("factor: L_kk used for L_jk (transposed operand)", "double ljk = Lx[q];",
+     "double ljk = Lx[Lp[k]];"),
+    ("factor: square root dropped", "double ljj = sqrt(d);", "double ljj = d;"),
+    ("factor: column scaled by multiplying", "Lx[t] = x[i] / ljj;", "Lx[t] = x[i] * ljj;"),
+    ("etree: parent taken as the next column", "if (next == -1) parent[r] = (int32_t)i;",
+     "if (next == -1) parent[r] = (int32_t)(r + 1);"),
+    ("supernodes: count condition off by one", "colcnt[j] == colcnt[j + 1] + 1",
+     "colcnt[j] == colcnt[j + 1]"),
+    ("supernodes: only-child condition dropped", "&&\n                nchild[j + 1] == 1;", ";"),
+    ("solve: forward update sign flipped", "b[Li[t]] -= Lx[t] * zj;", "b[Li[t]] += Lx[t] * zj;"),
+    ("solve: backward uses L instead of L^T", "s -= Lx[t] * b[Li[t]];", "s -= Lx[t] * b[j];"),
+]
+
+
+def pins(orc):
+    """Pins of the oracle (independent of its C code: brute-force boolean
+    elimination, numpy dense Cholesky, the 1D closed form, the supernode
+    definition, manufactured solutions).  Returns the names of those that
+    fail."""
+    failed = set()
+
+    def check(name, fn):
+        try:
+            if not fn():
+                failed.add(name)
+        except Exception:
+            failed.add(name)
+
+    for seed in range(4):
+        n = [12, 30, 45, 60][seed]
+        rp, ci, v = gen.random_spd(n, 0.15, seed + 500)
+        perm = gen.random_perm(n, seed + 7)
+        so = orc.symbolic(rp, ci, perm)
+        bp, bc = orc.brute_symbolic(rp, ci, perm)
+        check("brute etree", lambda: np.array_equal(so["parent"], bp))
+        check("brute counts", lambda: np.array_equal(so["colcount"], bc))
+
+        def supernode_definition():
+            want = [0] + [j + 1 for j in range(n - 1)
+                          if not (bp[j] == j + 1 and bc[j] == bc[j + 1] + 1
+                                  and np.sum(bp == j + 1) == 1)] + [n]
+            return np.array_equal(so["sup_ptr"], want)
+        check("supernode definition", supernode_definition)
+
+        A = np.zeros((n, n))
+        A[np.repeat(np.arange(n), np.diff(rp)), ci] = v
+        C = A[np.ix_(perm, perm)]
+        F = orc.factor(rp, ci, v, perm)
+        check("numpy cholesky", lambda: F.bad_col == -1 and np.allclose(
+            F.dense(), np.linalg.cholesky(C), rtol=1e-12, atol=1e-12))
+        xs = np.random.default_rng(seed).uniform(-1, 1, n)
+        b = A @ xs
+        check("manufactured solve", lambda: np.allclose(orc.solve(F, b, perm), xs, rtol=1e-9,
+                                                       atol=1e-9))
+    n = 20
+    rp, ci, v = gen.laplacian_1d(n)
+    F = orc.factor(rp, ci, v, None)
+    k = np.arange(1, n + 1, dtype=np.float64)
+    check("1D closed form", lambda: F.bad_col == -1 and np.allclose(
+        F.Lx[F.Lp[:-1]], np.sqrt((k + 1) / k), rtol=1e-14))
+    return failed
+
+
+def test_pins_pass_on_the_oracle(orc):
+    assert pins(orc) == set()
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not unique: " + name
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib_path = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", str(lib_path), str(mutated),
+                           "-lm"])
+    saved = orc._load()
+    orc._lib = orc.load_library(str(lib_path))
+    try:
+        failed = pins(orc)
+    finally:
+        orc._lib = saved
+    assert failed, "no pin caught: " + name
