@@ -182,9 +182,10 @@ int mf_symbolic_analyze_batch(mf_handle* h, int32_t count, const int64_t* ns,
  * into a new object owned by the caller (release with mf_symbolic_free).  The
  * loaded analysis keeps the options it was made with (relaxation,
  * small-front limit, SpTRSV variant), not h's.  The format is native-endian
- * and tied to this library version: a file from another version or kind of
- * machine, or a truncated or corrupt file, gives MF_ERR_INVALID, as does a
- * path that cannot be opened.  Host only. */
+ * and tied to this library version, and carries a 64-bit hash of its
+ * contents: a file from another version or kind of machine, or a truncated
+ * or damaged file, gives MF_ERR_INVALID, as does a path that cannot be
+ * opened.  Host only. */
 int mf_symbolic_save(const mf_symbolic* s, const char* path);
 int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s);
 

@@ -5,8 +5,11 @@
 //
 // Format: a fixed header (magic, version, byte-order mark, sizes of the
 // record types), then every member of mf_symbolic in declaration order:
-// scalars as raw bytes, vectors as a 64-bit count followed by the elements.
-// Native byte order: a file is read back on the same kind of machine.
+// scalars as raw bytes, vectors as a 64-bit count followed by the elements,
+// then a 64-bit FNV-1a hash of those member bytes.  The hash rejects an
+// accidentally damaged file whose sizes still look consistent (its offsets
+// reach device code).  Native byte order: a file is read back on the same
+// kind of machine.
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -18,7 +21,16 @@
 namespace {
 
 constexpr char kMagic[8] = {'M', 'F', 'S', 'Y', 'M', 'B', 'O', 'L'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
+constexpr uint64_t kFnvOffset = 1469598103934665603ull;
+constexpr uint64_t kFnvPrime = 1099511628211ull;
+
+// FNV-1a, 64 bit, over a byte range, continuing from h.
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * kFnvPrime;
+  return h;
+}
 constexpr uint32_t kByteOrder = 0x01020304u;
 
 struct Header {
@@ -43,8 +55,10 @@ Header make_header() {
 struct Writer {
   FILE* f;
   bool ok = true;
+  uint64_t hash = kFnvOffset;  // of the member bytes
   void raw(const void* p, size_t n) {
     if (ok && n && std::fwrite(p, 1, n, f) != n) ok = false;
+    hash = fnv1a(hash, p, n);
   }
   template <typename T>
   void operator()(const T& v) {
@@ -64,6 +78,7 @@ struct Reader {
   FILE* f;
   uint64_t left;  // bytes not yet read
   bool ok = true;
+  uint64_t hash = kFnvOffset;  // of the member bytes
   void raw(void* p, size_t n) {
     if (!ok) return;
     if (n > left || (n && std::fread(p, 1, n, f) != n)) {
@@ -71,6 +86,7 @@ struct Reader {
       return;
     }
     left -= n;
+    hash = fnv1a(hash, p, n);
   }
   template <typename T>
   void operator()(T& v) {
@@ -185,10 +201,13 @@ int mf_symbolic_save(const mf_symbolic* s, const char* path) {
   if (!s || !path) return mf::set_error(MF_ERR_INVALID, "NULL argument");
   FILE* f = std::fopen(path, "wb");
   if (!f) return mf::set_error(MF_ERR_INVALID, std::string("cannot open for writing: ") + path);
-  Writer w{f};
   const Header h = make_header();
-  w.raw(&h, sizeof(h));
+  bool ok = std::fwrite(&h, 1, sizeof(h), f) == sizeof(h);
+  Writer w{f};
+  w.ok = ok;
   members(w, *s);
+  const uint64_t hash = w.hash;
+  w.raw(&hash, sizeof(hash));
   const bool closed = std::fclose(f) == 0;
   if (!w.ok || !closed) return mf::set_error(MF_ERR_INVALID, std::string("write failed: ") + path);
   return MF_OK;
@@ -202,11 +221,11 @@ int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s) {
   std::fseek(f, 0, SEEK_END);
   const long size = std::ftell(f);
   std::fseek(f, 0, SEEK_SET);
-  Reader r{f, size > 0 ? (uint64_t)size : 0};
   Header hd;
-  r.raw(&hd, sizeof(hd));
   const Header want = make_header();
-  if (!r.ok || std::memcmp(&hd, &want, sizeof(hd)) != 0) {
+  const bool head_ok = size >= (long)sizeof(hd) && std::fread(&hd, 1, sizeof(hd), f) == sizeof(hd);
+  Reader r{f, head_ok ? (uint64_t)size - sizeof(hd) : 0};
+  if (!head_ok || std::memcmp(&hd, &want, sizeof(hd)) != 0) {
     std::fclose(f);
     return mf::set_error(MF_ERR_INVALID, "not a symbolic analysis of this library version/machine");
   }
@@ -220,6 +239,10 @@ int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s) {
   } catch (const std::bad_alloc&) {
     r.ok = false;
   }
+  const uint64_t hash = r.hash;
+  uint64_t stored = 0;
+  r.raw(&stored, sizeof(stored));
+  if (stored != hash) r.ok = false;
   std::fclose(f);
   if (!r.ok || r.left != 0 || !consistent(*S)) {
     delete S;

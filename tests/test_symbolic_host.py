@@ -314,6 +314,10 @@ def test_load_rejects_bad_files(mf, handle, tmp_path):
     bad = bytearray(data)
     bad[48:56] = (1 << 60).to_bytes(8, "little")
     cases["count"] = bytes(bad)
+    # one flipped bit deep in the payload, sizes intact: the hash rejects it
+    flip = bytearray(data)
+    flip[len(data) // 2] ^= 0x10
+    cases["bitflip"] = bytes(flip)
     for name, content in cases.items():
         p = tmp_path / (name + ".sym")
         if content is not None:
