@@ -189,6 +189,15 @@ int mf_symbolic_analyze_batch(mf_handle* h, int32_t count, const int64_t* ns,
 int mf_symbolic_save(const mf_symbolic* s, const char* path);
 int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s);
 
+/* Host-side consistency check of the analysis's launch schedules: every
+ * front's work appears exactly once, in launches of its own level, in level
+ * order (assembly chunks, panels, TRSM rows, trailing tiles, the
+ * partitioned-inverse tiles, the solve blocks of both sweeps).  Returns MF_OK,
+ * or MF_ERR_INTERNAL with the first violation in mf_last_error_string.  For
+ * tests and diagnostics; the analysis calls do not run it.  The paper has no
+ * counterpart. */
+int mf_symbolic_check(const mf_symbolic* s);
+
 int mf_symbolic_free(mf_symbolic* s);
 int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info);
 /* parent[j] of the column elimination tree (-1 for roots), n entries. */

@@ -68,6 +68,7 @@ _SIGS = {
     "mf_symbolic_analyze_batch": [_P, _I32, _P, _P, _P, _P, _P],
     "mf_symbolic_analyze_condensed": [_P, _I64, _P, _P, _P, _P, _I32, _P],
     "mf_symbolic_save": [_P, ctypes.c_char_p],
+    "mf_symbolic_check": [_P],
     "mf_symbolic_load": [_P, ctypes.c_char_p, _P],
     "mf_symbolic_free": [_P],
     "mf_symbolic_get_info": [_P, _P],
@@ -183,6 +184,10 @@ def mf_symbolic_analyze_condensed(h, rowptr, colind, perm=None, node_of=None, bl
                                                _ptr(perm), _ptr(node_of), int(block),
                                                ctypes.byref(s)))
     return s
+
+
+def mf_symbolic_check(s):
+    _check(lib().mf_symbolic_check(s))
 
 
 def mf_symbolic_save(s, path):

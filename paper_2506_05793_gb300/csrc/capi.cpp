@@ -350,6 +350,13 @@ int mf_symbolic_analyze_batch(mf_handle* h, int32_t count, const int64_t* ns,
   return mf_symbolic_analyze(h, N, rp.data(), ci.data(), pm.data(), s);
 }
 
+int mf_symbolic_check(const mf_symbolic* s) {
+  if (!s) return set_error(MF_ERR_INVALID, "NULL argument");
+  std::string err;
+  const int rc = mf::check_schedules(*s, err);
+  return rc == MF_OK ? MF_OK : set_error(rc, err);
+}
+
 int mf_symbolic_free(mf_symbolic* s) {
   delete s;
   return MF_OK;

@@ -172,6 +172,7 @@ namespace mf {
 int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
             const int32_t* perm, const int32_t* node_of, std::string& err);
 void build_schedules(mf_symbolic& S, int small_max);
+int check_schedules(const mf_symbolic& S, std::string& err);
 void ensure_fundamental_rows(const mf_symbolic& S);
 // error reporting (capi.cpp)
 int set_error(int code, const std::string& msg);

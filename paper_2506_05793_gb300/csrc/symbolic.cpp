@@ -1053,6 +1053,238 @@ void build_schedules(mf_symbolic& S, int small_max) {
   }
 }
 
+// Consistency of the launch schedules, checked on the host: every front's
+// work appears exactly once, in launches of its own level, in level order.
+//   factor: a small front is one K_SMALL item; a large front has assembly
+//   chunks tiling [0, nf), one POTRF item per 64-column panel t, TRSM row
+//   blocks tiling [p0, nf) after it, and (FP64 schedule) the trailing tiles
+//   0 <= J <= I < nt of every panel exactly once; POTRF(t + 1) comes after
+//   TRSM(t) and the first tile column of SYRK(t);
+//   partitioned inverse: init column blocks tile [0, nb), and step t holds
+//   the tiles t < i < nb + mb, 0 <= j <= t exactly once, steps in order;
+//   solves: a front is one warp item (nf <= 32 H) or its pivot blocks tile
+//   [0, k) (and, forward, its update blocks tile [k, nf)).
+int check_schedules(const mf_symbolic& S, std::string& err) {
+  const int64_t ns = (int64_t)S.sn.size();
+  auto fail = [&](const std::string& m) {
+    err = m;
+    return MF_ERR_INTERNAL;
+  };
+  auto tiles = [&](const std::vector<std::pair<int, int>>& v, int lo, int hi, int step) {
+    // v: (start, length) segments; must tile [lo, hi) in blocks of `step`
+    std::vector<std::pair<int, int>> w(v);
+    std::sort(w.begin(), w.end());
+    int at = lo;
+    for (const auto& x : w) {
+      if (x.first != at || x.second <= 0 || x.second > step) return false;
+      at += x.second;
+    }
+    return at == hi;
+  };
+  for (const auto* schedp : {&S.fsched, &S.fsched_tc, &S.fwsched, &S.bwsched})
+    for (const Launch& L : *schedp) {
+      if (L.item_off < 0 || L.count < 0 || L.item_off + L.count > (int64_t)S.items.size())
+        return fail("launch items out of range");
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x)
+        if (S.items[x].s < 0 || S.items[x].s >= ns) return fail("item names no front");
+    }
+  auto nb_of = [&](int64_t s) { return (S.sn[s].k + kNB - 1) / kNB; };
+  // ---- factor schedules
+  for (int tc = 0; tc < 2; ++tc) {
+    const std::vector<Launch>& sched = tc ? S.fsched_tc : S.fsched;
+    std::vector<int> small(ns, 0);
+    std::vector<std::vector<std::pair<int, int>>> asmb(ns);
+    std::vector<std::vector<int>> potrf(ns);  // launch index per panel
+    std::vector<std::vector<int64_t>> syrk_tiles(ns);
+    std::vector<std::vector<std::vector<std::pair<int, int>>>> trsm(ns);
+    std::vector<std::vector<int>> trsm_at(ns), syrk0_at(ns);
+    int32_t last_level = -1;
+    for (size_t li = 0; li < sched.size(); ++li) {
+      const Launch& L = sched[li];
+      if (L.kind == K_PINV_INIT || L.kind == K_PINV) continue;
+      if (L.level < last_level) return fail("factor levels out of order");
+      last_level = L.level;
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const Item& it = S.items[x];
+        const SnInfo& f = S.sn[it.s];
+        const int nf = f.k + f.m, nb = (int)nb_of(it.s);
+        if (S.slevel[it.s] != L.level) return fail("factor item outside its front's level");
+        if (potrf[it.s].empty()) {
+          potrf[it.s].assign(nb, -1);
+          trsm[it.s].assign(nb, {});
+          trsm_at[it.s].assign(nb, -1);
+          syrk0_at[it.s].assign(nb, -1);
+        }
+        switch (L.kind) {
+          case K_SMALL:
+            if (nf > L.param) return fail("small front above its size class");
+            small[it.s]++;
+            break;
+          case K_ASSEMBLE:
+            asmb[it.s].push_back({it.a, it.b - it.a});
+            break;
+          case K_POTRF:
+            if (it.t != L.param || it.t < 0 || it.t >= nb || potrf[it.s][it.t] != -1)
+              return fail("POTRF panel repeated or out of range");
+            if (it.t > 0 && (trsm_at[it.s][it.t - 1] < 0 ||
+                             (nf > it.t * kNB && syrk0_at[it.s][it.t - 1] < 0 && !tc)))
+              return fail("POTRF before the previous panel's TRSM / first update column");
+            potrf[it.s][it.t] = (int)li;
+            break;
+          case K_TRSM:
+            if (it.t != L.param || it.t < 0 || it.t >= nb || potrf[it.s][it.t] < 0)
+              return fail("TRSM before its panel's POTRF");
+            trsm[it.s][it.t].push_back({it.a, std::min(kTrsmRows, nf - it.a)});
+            trsm_at[it.s][it.t] = (int)li;
+            break;
+          case K_SYRK: {
+            const int t = it.t;
+            const int p0 = t * kNB + std::min(kNB, f.k - t * kNB);
+            const int nt = (nf - p0 + kTile - 1) / kTile;
+            if (t != L.param || t < 0 || t >= nb || it.b < 0 || it.b > it.a || it.a >= nt)
+              return fail("SYRK tile out of range");
+            syrk_tiles[it.s].push_back(((int64_t)t << 40) | ((int64_t)it.a << 20) | it.b);
+            if (it.b == 0) syrk0_at[it.s][t] = (int)li;
+            break;
+          }
+          case K_SYRK_TC:
+            break;
+          default:
+            return fail("unknown factor kind");
+        }
+      }
+    }
+    for (int64_t s = 0; s < ns; ++s) {
+      const SnInfo& f = S.sn[s];
+      const int nf = f.k + f.m, nb = (int)nb_of(s);
+      if (small[s]) {
+        if (small[s] != 1 || !asmb[s].empty()) return fail("small front scheduled twice");
+        continue;
+      }
+      if (!tiles(asmb[s], 0, nf, kAsmCols)) return fail("assembly chunks do not tile the front");
+      if ((int)potrf[s].size() != nb) return fail("large front without panels");
+      int64_t want = 0;
+      for (int t = 0; t < nb; ++t) {
+        if (potrf[s][t] < 0) return fail("panel without POTRF");
+        const int p0 = t * kNB + std::min(kNB, f.k - t * kNB);
+        if (!tiles(trsm[s][t], p0, nf, kTrsmRows)) return fail("TRSM rows do not tile the panel");
+        const int64_t nt = (nf - p0 + kTile - 1) / kTile;
+        want += nt * (nt + 1) / 2;
+      }
+      if (!tc) {
+        std::vector<int64_t>& v = syrk_tiles[s];
+        std::sort(v.begin(), v.end());
+        if (std::adjacent_find(v.begin(), v.end()) != v.end() || (int64_t)v.size() != want)
+          return fail("trailing tiles missing or repeated");
+      }
+    }
+  }
+  // ---- solve schedules
+  std::vector<int> pinv_front(ns, 0);
+  for (int bw = 0; bw < 2; ++bw) {
+    const std::vector<Launch>& sched = bw ? S.bwsched : S.fwsched;
+    std::vector<int> warp(ns, 0);
+    std::vector<std::vector<std::pair<int, int>>> piv(ns), upd(ns), pv(ns), pg(ns), gemv(ns);
+    int32_t last_level = bw ? S.nlevels : -1;
+    for (const Launch& L : sched) {
+      if (bw ? L.level > last_level : L.level < last_level) return fail("solve levels out of order");
+      last_level = L.level;
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const Item& it = S.items[x];
+        const SnInfo& f = S.sn[it.s];
+        if (S.slevel[it.s] != L.level) return fail("solve item outside its front's level");
+        switch (L.kind) {
+          case K_FW_WARP:
+          case K_BW_WARP:
+            if (f.k + f.m > 32 * L.param) return fail("front too large for its warp class");
+            warp[it.s]++;
+            break;
+          case K_FW_LEVEL:
+          case K_BW_LEVEL:
+            piv[it.s].push_back({it.a, it.b});
+            break;
+          case K_FW_GEMV:
+            if (it.a < f.k) return fail("forward update block inside the pivots");
+            upd[it.s].push_back({it.a, it.b});
+            break;
+          case K_BW_GEMV:
+            gemv[it.s].push_back({it.a, it.b});
+            break;
+          case K_FW_PGATHER:
+          case K_BW_PCOPY:
+            pg[it.s].push_back({it.a, it.b});
+            break;
+          case K_FW_PINV:
+          case K_BW_PINV:
+            pinv_front[it.s] = 1;
+            if (it.t == 0) pv[it.s].push_back({it.a, it.b});
+            else upd[it.s].push_back({it.a, it.b});
+            break;
+          default:
+            return fail("unknown solve kind");
+        }
+      }
+    }
+    for (int64_t s = 0; s < ns; ++s) {
+      const SnInfo& f = S.sn[s];
+      const int nf = f.k + f.m;
+      const bool blocks = !piv[s].empty() || !pv[s].empty();
+      if (warp[s] + (blocks ? 1 : 0) != 1) return fail("front solved twice or never");
+      if (warp[s]) continue;
+      if (!pv[s].empty()) {  // partitioned inverse
+        if (S.ioff[s] < 0) return fail("partitioned-inverse front without kept inverses");
+        if (!tiles(pv[s], 0, f.k, kNB) || !tiles(pg[s], 0, f.k, kNB))
+          return fail("partitioned-inverse blocks do not tile the pivots");
+        if (!piv[s].empty() || !gemv[s].empty()) return fail("front in two solve variants");
+      } else {
+        if (!tiles(piv[s], 0, f.k, kNB)) return fail("pivot blocks do not tile the pivots");
+        if (bw && f.m > 0 && !tiles(gemv[s], 0, f.k, kNB))
+          return fail("backward update blocks do not tile the pivots");
+      }
+      if (!bw && !tiles(upd[s], f.k, nf, kNB)) return fail("update blocks do not tile the rows");
+    }
+  }
+  // ---- partitioned inverse pass (both factor schedules)
+  for (int tc = 0; tc < 2; ++tc) {
+    const std::vector<Launch>& sched = tc ? S.fsched_tc : S.fsched;
+    std::vector<std::vector<std::pair<int, int>>> init(ns);
+    std::vector<std::vector<int64_t>> steps(ns);
+    int32_t last_t = -1;
+    bool seen_init = false;
+    for (const Launch& L : sched) {
+      if (L.kind != K_PINV_INIT && L.kind != K_PINV) continue;
+      if (L.kind == K_PINV_INIT) seen_init = true;
+      else if (!seen_init || L.param <= last_t) return fail("inverse steps out of order");
+      if (L.kind == K_PINV) last_t = L.param;
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const Item& it = S.items[x];
+        if (!pinv_front[it.s]) return fail("inverse pass on a front the solve does not use it for");
+        const int nb = (int)nb_of(it.s), mb = (S.sn[it.s].m + kNB - 1) / kNB;
+        if (L.kind == K_PINV_INIT) {
+          init[it.s].push_back({it.t, 1});
+        } else {
+          if (it.t != L.param || it.t >= nb || it.a <= it.t || it.a >= nb + mb || it.b < 0 ||
+              it.b > it.t)
+            return fail("inverse tile out of range");
+          steps[it.s].push_back(((int64_t)it.t << 40) | ((int64_t)it.a << 20) | it.b);
+        }
+      }
+    }
+    for (int64_t s = 0; s < ns; ++s) {
+      if (!pinv_front[s]) continue;
+      const int64_t nb = nb_of(s), mb = (S.sn[s].m + kNB - 1) / kNB;
+      if (!tiles(init[s], 0, (int)nb, 1)) return fail("inverse init does not cover the columns");
+      int64_t want = 0;
+      for (int64_t t = 0; t < nb; ++t) want += (nb + mb - t - 1) * (t + 1);
+      std::vector<int64_t>& v = steps[s];
+      std::sort(v.begin(), v.end());
+      if (std::adjacent_find(v.begin(), v.end()) != v.end() || (int64_t)v.size() != want)
+        return fail("inverse tiles missing or repeated");
+    }
+  }
+  return MF_OK;
+}
+
 // Row lists of the fundamental supernodes (the exported pattern of L), built
 // on first request: column j's lower entries of C plus the children's update
 // rows, merged per supernode in increasing order.

@@ -342,3 +342,78 @@ def test_factor_over_budget_is_oom(mf):
     finally:
         mf.mf_symbolic_free(s)
         mf.mf_destroy(h)
+
+
+# ---- schedule consistency (host) ------------------------------------------
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("relax,small", [(0, 128), (1, 128), (1, 32)])
+def test_schedules_cover_every_front_once(mf, variant, relax, small):
+    opt = mf.mf_options_default()
+    opt.sptrsv, opt.relax, opt.small_front_max = variant, relax, small
+    h = mf.mf_create(opt)
+    try:
+        cases = [gen.config3(16)[:2] + (gen.config3(16)[3],)]
+        rp, ci, _ = gen.q1_extruded(12, 10, 3)
+        cases.append((rp, ci, gen.nd_perm((13, 11, 4), split_axes=(0, 1), dofs=2)))
+        rp, ci, _ = gen.random_spd(300, 0.04, 3)
+        cases.append((rp, ci, gen.random_perm(300, 4)))
+        import scipy.sparse as sp
+        M = np.random.default_rng(1).standard_normal((333, 333))
+        A = sp.csr_matrix(M @ M.T + 333 * np.eye(333))
+        cases.append((A.indptr.astype(np.int64), A.indices.astype(np.int32), None))
+        for rp, ci, perm in cases:
+            s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+            try:
+                mf.mf_symbolic_check(s)
+            finally:
+                mf.mf_symbolic_free(s)
+        mats, _ = gen.box_batch(12, 8, 20, seed=4)
+        s = mf.mf_symbolic_analyze_batch(h, [(a, b, p) for a, b, c, p in mats])
+        mf.mf_symbolic_check(s)
+        mf.mf_symbolic_free(s)
+    finally:
+        mf.mf_destroy(h)
+
+
+def _fnv1a(data):
+    h = 1469598103934665603
+    for byte in data:
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_schedule_check_catches_a_repeated_item(mf, handle, tmp_path):
+    """A saved analysis whose work list repeats one item (hash recomputed so
+    the loader accepts it) must fail the schedule check."""
+    rp, ci, v, perm, _ = gen.config3(8)
+    s = mf.mf_symbolic_analyze(handle, rp, ci, perm)
+    path = tmp_path / "a.sym"
+    mf.mf_symbolic_save(s, str(path))
+    mf.mf_symbolic_free(s)
+    data = bytearray(path.read_bytes())
+    # walk the members in file order to the work items
+    members = ["i8", "i8", ("v", 8), ("v", 4), ("v", 4), ("v", 4), ("v", 4), ("v", 8), ("v", 4),
+               ("v", 4), ("v", 4), ("v", 8), ("v", 8), ("v", 4), ("v", 4), "i4", ("v", 4),
+               ("v", 4), "i8", "i8", "i8", "i8", "i8", "i4", "i8", "i8", ("v", 64), ("v", 4),
+               ("v", 4), ("v", 4), ("v", 4), ("v", 8), ("v", 4), ("v", 8), ("v", 8), "i8", "i8",
+               "i8"]
+    pos = 32
+    for m in members:
+        if isinstance(m, tuple):
+            cnt = int.from_bytes(data[pos:pos + 8], "little")
+            pos += 8 + cnt * m[1]
+        else:
+            pos += int(m[1])
+    nitems = int.from_bytes(data[pos:pos + 8], "little")
+    assert nitems >= 2
+    first = pos + 8
+    data[first + 16:first + 32] = data[first:first + 16]  # item 1 := item 0
+    data[-8:] = _fnv1a(data[32:-8]).to_bytes(8, "little")
+    path.write_bytes(bytes(data))
+    t = mf.mf_symbolic_load(handle, str(path))
+    try:
+        with pytest.raises(mf.MFError) as e:
+            mf.mf_symbolic_check(t)
+        assert e.value.code == mf.MF_ERR_INTERNAL
+    finally:
+        mf.mf_symbolic_free(t)
