@@ -417,3 +417,20 @@ def test_schedule_check_catches_a_repeated_item(mf, handle, tmp_path):
         assert e.value.code == mf.MF_ERR_INTERNAL
     finally:
         mf.mf_symbolic_free(t)
+
+
+def test_condensed_edge_cases(mf, handle, orc):
+    """One node holding every DoF gives one dense supernode; node ids with
+    gaps and single-DoF nodes mixed with larger ones match the expanded
+    pattern; the empty matrix analyses."""
+    rp, ci, _ = gen.random_spd(40, 0.1, 11)
+    info = check_condensed(mf, handle, orc, rp, ci, None, node_of=np.zeros(40, dtype=np.int32))
+    assert info["nsuper"] == 1 and info["nnz_L"] == 40 * 41 // 2
+    node_of, perm = gen.random_nodes(60, max_size=3, seed=12)
+    gappy = (node_of.astype(np.int64) * 7 % 59).astype(np.int32)  # ids spread out, still < n
+    assert len(np.unique(gappy)) == len(np.unique(node_of))
+    check_condensed(mf, handle, orc, *gen.random_spd(60, 0.08, 13)[:2], perm, node_of=gappy)
+    s = mf.mf_symbolic_analyze_condensed(handle, np.zeros(1, dtype=np.int64),
+                                         np.zeros(0, dtype=np.int32), None, block=2)
+    assert mf.mf_symbolic_get_info(s)["n"] == 0
+    mf.mf_symbolic_free(s)
