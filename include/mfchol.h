@@ -1,7 +1,7 @@
 /*
  * mfchol.h -- C-ABI of the GB300 supernodal multifrontal sparse Cholesky.
  *
- * The calls follow the three phases of the paper's Ax=b statement (Sec. 2:
+ * The calls follow the three phases of the paper's Ax=b statement (Sec. 3:
  * symbolic analysis on the pattern only, numerical setup that copies the
  * values and factors P A P^T = L L^T, solve by forward and backward
  * substitution) and the reuse contract stated there (one analysis per
@@ -131,7 +131,7 @@ const char* mf_last_error_string(void);
 /* Permuted column of the last MF_ERR_NOT_SPD on this thread, else -1. */
 int64_t mf_last_error_column(void);
 
-/* ---- phase 1: symbolic analysis (host; paper Sec. 2 step 1) ------------- */
+/* ---- phase 1: symbolic analysis (host; paper Sec. 3 step 1) ------------- */
 
 /* Analyse the pattern of C = A(perm, perm): elimination tree (Liu),
  * column counts (Gilbert-Ng-Peyton row-subtree leaves), fundamental
@@ -143,7 +143,7 @@ int mf_symbolic_analyze(mf_handle* h, int64_t n, const int64_t* rowptr,
                         const int32_t* colind, const int32_t* perm,
                         mf_symbolic** s);
 
-/* Symbolic analysis on a condensed graph (paper Sec. 6, graph condensation:
+/* Symbolic analysis on a condensed graph (paper Sec. 5, graph condensation:
  * the DoFs of one mesh node are compressed into one vertex).  node_of[i]
  * (n entries, original numbering, values in [0, n)) names the node of DoF i;
  * with node_of NULL the nodes are fixed blocks of `block` consecutive DoFs
@@ -231,7 +231,7 @@ int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr,
                 const double* values, int32_t values_on_device, int32_t prec,
                 int32_t reps, mf_options* best, double* best_ms);
 
-/* ---- phase 2: numerical factorization (device; paper Sec. 2 step 2) ----- */
+/* ---- phase 2: numerical factorization (device; paper Sec. 3 step 2) ----- */
 
 /* Allocate device storage for the factor of s in the given precision
  * (MF_FP64 or MF_FP32): supernodal L panels, update matrices, the copy of
@@ -270,7 +270,7 @@ int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches,
 int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches,
                       double* flops);
 
-/* ---- phase 3: solve (device; paper Sec. 2 step 3, Sec. 5 SpTRSV) -------- */
+/* ---- phase 3: solve (device; paper Sec. 3 step 3, Sec. 5 SpTRSV) -------- */
 
 /* X = A^{-1} B for nrhs right-hand sides, column-major, FP64 at the
  * boundary (an FP32 factor solves in FP32).  B and X are both host or both

@@ -6,7 +6,7 @@ package imports nothing from the library.
 
 What it computes (paper Sec. 5, Tacho: symbolic analysis, numerical
 factorization ``P A P^T = L L^T`` of an SPD matrix, forward/backward solve;
-the three phases of the paper's Ax=b statement in Sec. 2):
+the three phases of the paper's Ax=b statement in Sec. 3):
 
 * ``lower_rows`` / ``lower_cols`` -- the lower triangle of ``C = A(perm, perm)``
   (``perm[new] = old``), duplicates summed.  Plain numpy.
@@ -323,7 +323,7 @@ def factor_sample(rowptr, colind, values, perm, seconds=15.0, sym=None):
 
 
 # ---------------------------------------------------------------------------
-# Condensed graph (paper Sec. 6: the DoFs of one node compressed into one
+# Condensed graph (paper Sec. 5: the DoFs of one node compressed into one
 # vertex of the graph the symbolic analysis runs on)
 # ---------------------------------------------------------------------------
 def expand_node_blocks(rowptr, colind, values, node_of):

@@ -1,7 +1,7 @@
 // capi.cpp -- the extern "C" boundary (include/mfchol.h): handles, symbolic
 // objects, device factors, solves and the mixed-precision refinement loop.
 //
-// Phases follow the paper's Ax=b statement (Sec. 2): symbolic analysis on
+// Phases follow the paper's Ax=b statement (Sec. 3): symbolic analysis on
 // the host, numerical setup (copy values, factor) and solve on the device.
 // Every step of the numeric path runs in this library's kernels; there is no
 // CPU fallback.

@@ -1,5 +1,5 @@
 // symbolic.cpp -- host symbolic analysis of the multifrontal Cholesky
-// (paper Sec. 2, phase 1: "symbolic analysis uses only the sparsity
+// (paper Sec. 3, phase 1: "symbolic analysis uses only the sparsity
 // structure"; run sequentially on one host core as the paper describes for
 // Tacho, its cost amortised over many numeric factorizations).
 //
@@ -147,7 +147,7 @@ int etree_counts(int64_t n, const std::vector<int64_t>& rp, const std::vector<in
   return MF_OK;
 }
 
-// Condensed-graph analysis (paper Sec. 6, "condensed" graph option): the
+// Condensed-graph analysis (paper Sec. 5, "condensed" graph option): the
 // degrees of freedom of one node (node_of[dof], original numbering) take
 // consecutive positions of the elimination order and are treated as one
 // dense block.  The elimination tree and column counts are computed on the

@@ -1,6 +1,6 @@
 // symbolic_io.cpp -- save and load a symbolic analysis (restart without
 // repeating the host analysis).  The paper has no counterpart; the analysis
-// depends on the pattern only (Sec. 2, phase 1), so a program that factors
+// depends on the pattern only (Sec. 3, phase 1), so a program that factors
 // the same pattern again after a restart can load it instead.
 //
 // Format: a fixed header (magic, version, byte-order mark, sizes of the

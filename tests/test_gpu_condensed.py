@@ -1,5 +1,5 @@
 """GPU parity of factorizations built on a condensed-graph symbolic analysis
-(paper Sec. 6): the factor is the Cholesky factor of the block-expanded
+(paper Sec. 5): the factor is the Cholesky factor of the block-expanded
 matrix (added positions are explicit zeros), compared element by element with
 the oracle's factor of that matrix; the solves are checked against A."""
 import numpy as np

@@ -147,7 +147,7 @@ def test_update_memory_plan_reuses_chains(mf, handle):
     mf.mf_symbolic_free(s)
 
 
-# ---- condensed graph (paper Sec. 6: DoFs of one node compressed) ----------
+# ---- condensed graph (paper Sec. 5: DoFs of one node compressed) ----------
 def check_condensed(mf, handle, orc, rp, ci, perm, node_of=None, block=1):
     """Condensed analysis = the plain analysis of the block-expanded pattern
     (oracle), and no node is split between two supernodes."""
