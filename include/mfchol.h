@@ -250,8 +250,26 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec,
 int mf_factor_numeric(mf_factor* f, const double* values,
                       int32_t values_on_device, void* stream, int32_t async);
 
-/* Wait for `stream` and return the status of the last numeric call. */
+/* Wait for `stream` and return the status of the last numeric call:
+ * MF_ERR_NOT_SPD (first failing column through mf_last_error_column) or
+ * MF_ERR_TIMEOUT if a bounded device wait of the factorization (the
+ * tensor-core trailing update's copy/MMA barriers) gave up.  Solve failures
+ * are reported by the solve calls and mf_solve_check, never here. */
 int mf_factor_check(mf_factor* f, void* stream);
+
+/* Bound of the solve kernels' flag waits on this factor, in polls of about
+ * 128 ns (0 restores the default, 2^22 polls, about half a second).  A wait
+ * that runs out records MF_ERR_TIMEOUT for the solve call in progress and
+ * lets its kernel finish (no hang); the values of that solve are then
+ * wrong, and the call (or mf_solve_check) reports it.  A very short bound
+ * makes the waits of a real solve run out, which tests that reporting.
+ * Errors: MF_ERR_INVALID for polls < 0. */
+int mf_factor_set_wait_limit(mf_factor* f, int32_t polls);
+
+/* Bytes of solve work memory (work vectors, right-hand-side staging, flags)
+ * that the factor currently holds on the device; 0 until a solve that
+ * allocates (mf_solve, mf_solve_refined) has run. */
+int mf_factor_solve_work_bytes(const mf_factor* f, int64_t* bytes);
 
 int mf_factor_free(mf_factor* f);
 
@@ -275,9 +293,19 @@ int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches,
 /* X = A^{-1} B for nrhs right-hand sides, column-major, FP64 at the
  * boundary (an FP32 factor solves in FP32).  B and X are both host or both
  * device pointers as on_device says; B may equal X.  Enqueued on stream;
- * synchronous for host pointers. */
+ * synchronous for host pointers.  Every solve call clears the factor's
+ * solve timeout record first; with host pointers the call returns
+ * MF_ERR_TIMEOUT if a bounded wait of its kernels gave up, with device
+ * pointers mf_solve_check reads the record. */
 int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
              double* X, int64_t ldx, int32_t on_device, void* stream);
+
+/* Wait for `stream` and return the status of the last solve call on f
+ * (mf_solve with device pointers, mf_solve_noalloc): MF_ERR_TIMEOUT if a
+ * bounded device wait of that solve gave up (its X is then wrong), else
+ * MF_OK.  Reads one word of device memory into pinned host memory that the
+ * factor already holds; allocates nothing. */
+int mf_solve_check(mf_factor* f, void* stream);
 
 /* Solve without allocating memory.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory on
@@ -297,15 +325,20 @@ int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
  * array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  Every call shares the
  * array, so calls whose work overlaps on the GPU (other streams, other
- * threads) race and corrupt each other's results; serialize them.
- * Enqueued on stream; returns without waiting. */
+ * threads) race and corrupt each other's results; serialize them.  The
+ * looked-up address is cached per device index for the life of the
+ * process: it does not survive cudaDeviceReset (or any other teardown of
+ * the device's primary context) -- do not call this entry point after one.
+ * Enqueued on stream; returns without waiting; mf_solve_check reports a
+ * solve whose bounded waits gave up. */
 int mf_solve_noalloc(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
                      double* X, int64_t ldx, void* stream);
 
 /* Diagnostic for the failure detection of the solve kernels (no paper
  * counterpart): runs the solve's bounded device wait, on one CTA, against a
  * flag that nothing sets, giving up after `polls` polls of about 128 ns each
- * (the solve itself uses 2^22).  The kernel records MF_ERR_TIMEOUT in a status
+ * (the solve itself uses 2^22 unless mf_factor_set_wait_limit says
+ * otherwise).  The kernel records MF_ERR_TIMEOUT in a status
  * word and returns; the device stays usable.  Allocates and frees 256 bytes
  * of device memory and synchronizes `stream`.  Returns MF_ERR_TIMEOUT (the
  * expected outcome), MF_ERR_INVALID for polls < 1, MF_ERR_CUDA on a CUDA
@@ -319,7 +352,9 @@ int mf_diag_wait_timeout(int32_t polls, void* stream);
  * residual scaled by 1/||r||_inf in FP32.  Stops when berr <= tol for every
  * RHS.  Stagnation (berr not halved over two steps, or max_iter reached)
  * triggers an FP64 factorization of the same values and an FP64 solve,
- * unless allow_fallback is 0 (then MF_ERR_STAGNATION).  rep may be NULL. */
+ * unless allow_fallback is 0 (then MF_ERR_STAGNATION).  rep may be NULL.
+ * Returns MF_ERR_TIMEOUT if a bounded wait of any of its solves gave up,
+ * even when the refinement then reached tol. */
 int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
                      double* X, int64_t ldx, int32_t on_device, double tol,
                      int32_t max_iter, int32_t allow_fallback,

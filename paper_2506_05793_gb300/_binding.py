@@ -97,6 +97,9 @@ _SIGS = {
     "mf_server_get_stats": [_P, _P],
     "mf_server_free": [_P],
     "mf_diag_wait_timeout": [_I32, _P],
+    "mf_solve_check": [_P, _P],
+    "mf_factor_set_wait_limit": [_P, _I32],
+    "mf_factor_solve_work_bytes": [_P, _P],
 }
 
 
@@ -308,6 +311,26 @@ def mf_factor_check(f, stream=None):
 
 def mf_factor_free(f):
     _check(lib().mf_factor_free(f))
+
+
+def mf_factor_set_wait_limit(f, polls):
+    """Bound of the solve's flag waits on f in polls (0: the default)."""
+    _check(lib().mf_factor_set_wait_limit(f, polls))
+
+
+def mf_factor_solve_work_bytes(f):
+    out = _I64(0)
+    _check(lib().mf_factor_solve_work_bytes(f, ctypes.byref(out)))
+    return int(out.value)
+
+
+def mf_solve_check(f, stream=None):
+    """Wait for ``stream`` and raise MFError(MF_ERR_TIMEOUT) if a bounded wait
+    of the last solve call on f gave up."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    _check(lib().mf_solve_check(f, _stream(stream)))
 
 
 def mf_factor_export_L(f, nnz_L):

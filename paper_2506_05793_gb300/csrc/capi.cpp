@@ -111,6 +111,9 @@ struct PhaseRange {
 
 size_t elem_size(int prec) { return prec == MF_FP32 ? sizeof(float) : sizeof(double); }
 
+constexpr int kStatusWords = 4;
+constexpr int kStatusSolve = 2;  // the solve's timeout record
+
 // Device bytes of one factor: L, update matrices, diagonal-block inverses,
 // values in assembly order and the CSR values (plus the partitioned inverse,
 // the size of L, for SpTRSV variant 3); FP32 adds the tensor-core
@@ -171,6 +174,7 @@ struct mf_factor {
   int64_t prof_n[mf::K_NKINDS_FACTOR] = {0};
   double prof_fl[mf::K_NKINDS_FACTOR] = {0};
   bool numeric_done = false;
+  int32_t wait_polls = 0;     // bound of the solve's flag waits (0: the default)
   mf_factor* fb64 = nullptr;  // FP64 fallback of the refinement loop
 
   ~mf_factor() {
@@ -452,9 +456,12 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   MF_CK(cudaMalloc(&F->L, std::max<int64_t>(s->Lsize, 1) * es));
   MF_CK(cudaMalloc(&F->U, std::max<int64_t>(s->Usize, 1) * es));
   MF_CK(cudaMalloc(&F->vals, std::max<int64_t>(s->nnzA, 1) * sizeof(double)));
-  MF_CK(cudaMalloc(&F->status, 2 * sizeof(unsigned long long)));
-  MF_CK(cudaMallocHost(&F->status_host, 2 * sizeof(unsigned long long)));
-  MF_CK(cudaMemset(F->status, 0xff, 2 * sizeof(unsigned long long)));
+  // status words (all-ones when clear): [0] first non-positive pivot column,
+  // [1] a bounded wait of the factorization gave up, [2] one of the solve
+  // gave up; [3] unused
+  MF_CK(cudaMalloc(&F->status, kStatusWords * sizeof(unsigned long long)));
+  MF_CK(cudaMallocHost(&F->status_host, kStatusWords * sizeof(unsigned long long)));
+  MF_CK(cudaMemset(F->status, 0xff, kStatusWords * sizeof(unsigned long long)));
   // diagonal-block inverses: one slot per large front of a level, or one per
   // 64 pivot columns of every large front when the solve uses them
   const int64_t inv_slots = s->keep_inv ? s->ninv : s->max_large;
@@ -615,7 +622,7 @@ int mf_factor_check(mf_factor* f, void* stream) {
   }
   const unsigned long long bad = f->status_host[0];
   if (f->status_host[1] != ~0ull)
-    return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
+    return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the factorization gave up");
   if (bad != ~0ull) {
     set_error(MF_ERR_NOT_SPD, "matrix is not positive definite");
     g_errcol = (int64_t)bad;
@@ -697,7 +704,7 @@ int mf_diag_wait_timeout(int32_t polls, void* stream) {
   void* buf = nullptr;
   MF_CK(cudaMalloc(&buf, 256));
   int rc = MF_OK;
-  unsigned long long host[2] = {0, 0};
+  unsigned long long host[1] = {0};
   int* flag = static_cast<int*>(buf);
   unsigned long long* status = reinterpret_cast<unsigned long long*>(static_cast<char*>(buf) + 128);
   cudaError_t e = cudaMemsetAsync(buf, 0, 256, st);
@@ -706,7 +713,7 @@ int mf_diag_wait_timeout(int32_t polls, void* stream) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(buf);
   if (e != cudaSuccess) return set_error(MF_ERR_CUDA, std::string("wait probe: ") + cudaGetErrorString(e));
-  if (host[1] == (unsigned long long)MF_ERR_TIMEOUT)
+  if (host[0] == (unsigned long long)MF_ERR_TIMEOUT)
     rc = set_error(MF_ERR_TIMEOUT, "device wait gave up after " + std::to_string(polls) + " polls");
   else
     rc = set_error(MF_ERR_INTERNAL, "wait probe returned without a timeout record");
@@ -808,7 +815,8 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.Y = Y;
   a.W = W;
   a.sync = sync;
-  a.status = f->status;
+  a.status = f->status + kStatusSolve;
+  a.wait_polls = f->wait_polls;
   a.n = S->n;
   a.nrhs = cn;
   a.nlevels = S->nlevels;
@@ -842,6 +850,24 @@ int ensure_io(mf_factor* f, int64_t doubles) {
   MF_CK(cudaMalloc(&f->Xd, doubles * sizeof(double)));
   MF_CK(cudaMalloc(&f->Rd, doubles * sizeof(double)));
   f->io_cap = doubles;
+  return MF_OK;
+}
+
+// Clear the solve's timeout record (stream-ordered).  Every public solve
+// call does this once before its first pass, so a record always belongs to
+// the last call.
+int reset_solve_status(mf_factor* f, cudaStream_t st) {
+  MF_CK(cudaMemsetAsync(f->status + kStatusSolve, 0xff, sizeof(unsigned long long), st));
+  return MF_OK;
+}
+
+// Read the solve's timeout record after synchronizing st.
+int read_solve_status(mf_factor* f, cudaStream_t st) {
+  MF_CK(cudaMemcpyAsync(f->status_host + kStatusSolve, f->status + kStatusSolve,
+                        sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  MF_CK(cudaStreamSynchronize(st));
+  if (f->status_host[kStatusSolve] != ~0ull)
+    return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
   return MF_OK;
 }
 
@@ -884,6 +910,8 @@ int solve_in_scratch(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
       (int32_t)std::min<size_t>(kSolveChunk, (scratch_bytes - slack - sync_bytes) / per_rhs);
   unsigned char* base = static_cast<unsigned char*>(scratch);
   int32_t* sync = reinterpret_cast<int32_t*>(base);
+  const int rs = reset_solve_status(f, st);
+  if (rs != MF_OK) return rs;
   for (int32_t c0 = 0; c0 < nrhs; c0 += chunk) {
     const int32_t cn = std::min<int32_t>(chunk, nrhs - c0);
     void* Y = base + sync_bytes;
@@ -915,8 +943,10 @@ int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X
   if (!f->numeric_done) return set_error(MF_ERR_INVALID, "factor has no numeric values");
   if (nrhs == 0 || n == 0) return MF_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = reset_solve_status(f, st);
+  if (rc != MF_OK) return rc;
   if (on_device) return solve_dev(f, nrhs, B, ldb, X, ldx, nullptr, nullptr, 0, st);
-  int rc = ensure_io(f, n * (int64_t)nrhs);
+  rc = ensure_io(f, n * (int64_t)nrhs);
   if (rc != MF_OK) return rc;
   MF_CK(cudaMemcpy2DAsync(f->Bd, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double),
                           nrhs, cudaMemcpyHostToDevice, st));
@@ -924,11 +954,31 @@ int mf_solve(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, double* X
   if (rc != MF_OK) return rc;
   MF_CK(cudaMemcpy2DAsync(X, ldx * sizeof(double), f->Xd, n * sizeof(double), n * sizeof(double),
                           nrhs, cudaMemcpyDeviceToHost, st));
-  MF_CK(cudaMemcpyAsync(f->status_host, f->status, 2 * sizeof(unsigned long long),
-                        cudaMemcpyDeviceToHost, st));
-  MF_CK(cudaStreamSynchronize(st));
-  if (f->status_host[1] != ~0ull)
-    return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the solve gave up");
+  return read_solve_status(f, st);
+}
+
+int mf_solve_check(mf_factor* f, void* stream) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  return read_solve_status(f, static_cast<cudaStream_t>(stream));
+}
+
+int mf_factor_set_wait_limit(mf_factor* f, int32_t polls) {
+  if (!f || polls < 0) return set_error(MF_ERR_INVALID, "invalid wait limit");
+  f->wait_polls = polls;
+  return MF_OK;
+}
+
+int mf_factor_solve_work_bytes(const mf_factor* f, int64_t* bytes) {
+  if (!f || !bytes) return set_error(MF_ERR_INVALID, "NULL argument");
+  const mf_symbolic* S = f->S;
+  const int64_t es = (int64_t)elem_size(f->prec);
+  int64_t b = 0;
+  if (f->Y) b += std::max<int64_t>(S->n * mf::kSolveChunk, 1) * es;
+  if (f->W) b += std::max<int64_t>(S->Wsize * mf::kSolveChunk, 1) * es;
+  if (f->small) b += 4096 * (int64_t)sizeof(double);
+  if (f->sync) b += sync_ints(S) * (int64_t)sizeof(int32_t);
+  b += 3 * f->io_cap * (int64_t)sizeof(double);
+  *bytes = b;
   return MF_OK;
 }
 
@@ -948,6 +998,8 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
   int rc = ensure_io(f, n * (int64_t)nrhs);
   if (rc != MF_OK) return rc;
   rc = ensure_solve_buffers(f);
+  if (rc != MF_OK) return rc;
+  rc = reset_solve_status(f, st);
   if (rc != MF_OK) return rc;
   // device B (ld n) and X (ld n)
   if (on_device)
@@ -1020,7 +1072,10 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
       rc = mf_factor_create(f->h, S, MF_FP64, &f->fb64);
       if (rc != MF_OK) return rc;
     }
+    f->fb64->wait_polls = f->wait_polls;
     rc = mf_factor_numeric(f->fb64, f->vals, 1, stream, 0);
+    if (rc != MF_OK) return rc;
+    rc = reset_solve_status(f->fb64, st);
     if (rc != MF_OK) return rc;
     rc = solve_dev(f->fb64, nrhs, f->Bd, n, f->Xd, n, nullptr, nullptr, 0, st);
     if (rc != MF_OK) return rc;
@@ -1048,7 +1103,11 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
     rep->fell_back = fell_back ? 1 : 0;
     rep->berr = berr;
   }
-  return MF_OK;
+  // a solve whose wait gave up has produced wrong values: report it even
+  // if the refinement recovered
+  rc = read_solve_status(f, st);
+  if (rc == MF_OK && fell_back) rc = read_solve_status(f->fb64, st);
+  return rc;
 }
 
 }  // extern "C"

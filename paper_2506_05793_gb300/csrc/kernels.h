@@ -37,7 +37,9 @@ struct FactorArgs {
   void* av;                    // T[nnz_lower]: lower entries of C in assembly order
   void* L;                     // T[Lsize]
   void* U;                     // T[Usize]
-  unsigned long long* status;  // [0] = first non-positive pivot column
+  // [0] = first non-positive pivot column, [1] = MF_ERR_TIMEOUT when a bounded
+  // wait of the factorization gave up (both all-ones when clear)
+  unsigned long long* status;
   // FP32 tensor-core path: per panel row 64 tf32 "hi" then 64 "lo" floats
   // (row soff[front] + front row); nullptr elsewhere
   float* split;
@@ -59,7 +61,7 @@ struct SolveArgs {
   // int32[2 * nlevels + 2 * nblk], zero before every solve: one ticket
   // counter per level and sweep, then forward and backward block flags
   int32_t* sync;
-  unsigned long long* status;  // status[1] receives MF_ERR_TIMEOUT
+  unsigned long long* status;  // the solve's timeout record: MF_ERR_TIMEOUT when a wait gives up
   // diagonal-block inverses of the large fronts (slots sym.ioff), or nullptr
   // to solve the pivot blocks by substitution
   const void* dinv = nullptr;
@@ -69,6 +71,7 @@ struct SolveArgs {
   int32_t nrhs;
   int32_t nlevels;
   int32_t nblk;
+  int32_t wait_polls = 0;  // polls before a flag wait gives up (0: the default bound)
 };
 
 // prec: MF_FP64 or MF_FP32.  All launchers return cudaGetLastError().

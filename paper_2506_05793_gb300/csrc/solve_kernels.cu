@@ -24,6 +24,9 @@
 namespace mf {
 namespace {
 
+// Default bound of a flag wait: about kSpinLimit x 128 ns (0.5 s).
+constexpr int kSpinLimit = 1 << 22;
+
 template <typename T>
 struct SD {
   const SnInfo* sn;
@@ -40,9 +43,10 @@ struct SD {
   const T* dinv;         // diagonal-block inverses (SpTRSV variant 2) or nullptr
   const int64_t* ioff;   // per front: first inverse slot, -1 if none
   const T* P;            // partitioned inverse (SpTRSV variant 3) or nullptr
-  unsigned long long* status;
+  unsigned long long* status;  // the solve's timeout record (one word)
   int64_t n;
   int nrhs;
+  int wait_polls;  // polls before a flag wait gives up
 };
 
 template <typename T>
@@ -65,6 +69,7 @@ SD<T> make_sd(const SolveArgs& a) {
   d.status = a.status;
   d.n = a.n;
   d.nrhs = a.nrhs;
+  d.wait_polls = a.wait_polls > 0 ? a.wait_polls : kSpinLimit;
   return d;
 }
 
@@ -75,9 +80,9 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Bounded spin: about kSpinLimit x 128 ns before a wait gives up, records
-// MF_ERR_TIMEOUT in status[1] and lets the block continue (no hang).
-constexpr int kSpinLimit = 1 << 22;
+// The whole CTA waits until *flag != 0 (thread 0 polls with acquire loads,
+// 128 ns apart); after `limit` polls it gives up, records MF_ERR_TIMEOUT in
+// *status and lets the block continue (no hang).
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -89,14 +94,12 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// The whole CTA waits until *flag != 0 (thread 0 polls with acquire loads).
-__device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* status,
-                                         int limit = kSpinLimit) {
+__device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* status, int limit) {
   if (threadIdx.x == 0) {
     int spins = 0;
     while (ld_acquire(flag) == 0) {
       if (++spins > limit) {
-        atomicExch(status + 1, (unsigned long long)MF_ERR_TIMEOUT);
+        atomicExch(status, (unsigned long long)MF_ERR_TIMEOUT);
         break;
       }
       __nanosleep(128);
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(256, 2)
       const int q = g * 16 + qq;
       Ln[qq] = (more && live && q < bsn) ? Lp[(int64_t)((a + 1) * kNB + q) * nf + r0 + row] : T(0);
     }
-    cta_wait(fl + a, d.status);
+    cta_wait(fl + a, d.status, d.wait_polls);
     const int bsa = min(kNB, k - a * kNB);
     for (int idx = tid; idx < bsa * nrhs; idx += blockDim.x) {
       const int r = idx / bsa, q = idx % bsa;
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(256, 2)
         Ln[ii] = (live && i < nt) ? Lcol[n0 + i] : T(0);
       }
     }
-    cta_wait(fl + i0 / kNB, d.status);
+    cta_wait(fl + i0 / kNB, d.status, d.wait_polls);
     for (int idx = tid; idx < ti * nrhs; idx += blockDim.x) {
       const int i = idx % ti, r = idx / ti;
       xs[i * RX + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + i0 + i);
@@ -1303,7 +1306,7 @@ __global__ void __launch_bounds__(256, 2) k_bw_warp(SD<T> d, int64_t item_off, i
 }
 
 // Diagnostic: the solve's bounded wait on a flag that nothing sets.  Gives
-// up after `limit` polls and records MF_ERR_TIMEOUT in status[1].
+// up after `limit` polls and records MF_ERR_TIMEOUT in *status.
 __global__ void k_wait_probe(const int* flag, unsigned long long* status, int limit) {
   cta_wait(flag, status, limit);
 }

@@ -10,6 +10,7 @@
 // accidentally damaged file whose sizes still look consistent (its offsets
 // reach device code).  Native byte order: a file is read back on the same
 // kind of machine.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -193,6 +194,134 @@ bool consistent(const mf_symbolic& s) {
   return true;
 }
 
+// Every index that a device kernel dereferences lies inside the array it
+// indexes.  The hash only catches accidental damage; this check keeps a
+// file made to carry a matching hash from reaching device code with an
+// out-of-range index.  Runs after consistent().
+bool indices_in_range(const mf_symbolic& s) {
+  const int64_t n = s.n, nfr = (int64_t)s.sn.size();
+  auto mono = [](const auto& v, int64_t first, int64_t last) {
+    if (v.empty() || (int64_t)v.front() != first || (int64_t)v.back() != last) return false;
+    for (size_t i = 1; i < v.size(); ++i)
+      if (v[i] < v[i - 1]) return false;
+    return true;
+  };
+  std::vector<char> seen(n, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t o = s.perm[i];
+    if (o < 0 || o >= n || seen[o] || s.iperm[o] != i) return false;
+    seen[o] = 1;
+  }
+  if (!mono(s.rowptr, 0, s.nnzA)) return false;
+  for (int32_t c : s.colind)
+    if (c < 0 || c >= n) return false;
+  if (!mono(s.front_ptr, 0, n)) return false;
+  for (int64_t j = 0; j < n; ++j) {
+    const int32_t F = s.col2front[j];
+    if (F < 0 || F >= nfr || j < s.front_ptr[F] || j >= s.front_ptr[F + 1]) return false;
+  }
+  for (int64_t F = 0; F < nfr; ++F) {
+    const mf::SnInfo& I = s.sn[F];
+    const int64_t nf = (int64_t)I.k + I.m;
+    if (I.first != s.front_ptr[F] || I.k != s.front_ptr[F + 1] - s.front_ptr[F] || I.k < 1 ||
+        I.m < 0 || I.first + (int64_t)I.k > n)
+      return false;
+    if (I.parent < -1 || I.parent >= nfr || (I.parent < 0 && I.m != 0)) return false;
+    if (I.Loff < 0 || I.Loff + nf * I.k > s.Lsize) return false;
+    if (I.m > 0 && (I.Uoff < 0 || I.Uoff + (int64_t)I.m * I.m > s.Usize)) return false;
+    if (I.rows_off < 0 || I.rows_off + nf > (int64_t)s.rowidx.size()) return false;
+    if (I.woff < 0 || I.woff + nf > s.Wsize) return false;
+    if (I.nchild < 0 || I.child_begin < 0 ||
+        (int64_t)I.child_begin + I.nchild > (int64_t)s.children.size())
+      return false;
+    for (int32_t c = 0; c < I.nchild; ++c) {
+      const int32_t ch = s.children[I.child_begin + c];
+      if (ch < 0 || ch >= nfr || s.sn[ch].parent != F) return false;
+    }
+    if (I.parent >= 0) {
+      const mf::SnInfo& P = s.sn[I.parent];
+      if (I.map_off < 0 || I.map_off + I.m > (int64_t)s.relmap.size()) return false;
+      for (int32_t i = 0; i < I.m; ++i) {
+        const int32_t r = s.relmap[I.map_off + i];
+        if (r < 0 || r >= P.k + P.m) return false;
+      }
+    }
+    const int64_t nb = (I.k + mf::kNB - 1) / mf::kNB;
+    if (s.ioff[F] != -1 && (s.ioff[F] < 0 || s.ioff[F] + nb > s.ninv)) return false;
+    if (s.soff[F] < 0 || (s.soff[F] >> mf::kSoffAreaShift) > 1) return false;
+  }
+  // panel items of the large fronts: panel index, rows, inverse slot, tile
+  // indices and the staging rows (soff) the panel kernels touch
+  const int64_t slots = s.keep_inv ? s.ninv : s.max_large;
+  for (const auto* sched : {&s.fsched, &s.fsched_tc})
+    for (const mf::Launch& L : *sched)
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const mf::Item& it = s.items[x];
+        const mf::SnInfo& I = s.sn[it.s];
+        const int64_t nf = (int64_t)I.k + I.m, nb = (I.k + mf::kNB - 1) / mf::kNB;
+        const int32_t tt = L.kind == mf::K_SYRK_TC ? (it.t & 0xffffff) : it.t;
+        switch (L.kind) {
+          case mf::K_POTRF:
+          case mf::K_TRSM:
+          case mf::K_SYRK_TC: {
+            if (tt < 0 || tt >= nb) return false;
+            if (L.kind != mf::K_SYRK_TC && (it.b < 0 || it.b >= slots)) return false;
+            if (L.kind == mf::K_TRSM && (it.a < 0 || it.a >= nf)) return false;
+            if (L.kind == mf::K_SYRK_TC && ((it.t >> 24) > 2 || it.a < 0 || it.b < 0 || it.b > it.a))
+              return false;
+            const int64_t so = s.soff[it.s];
+            const int64_t srow = so & (((int64_t)1 << mf::kSoffAreaShift) - 1);
+            if (srow + nf > ((so >> mf::kSoffAreaShift) ? s.split_rows_b : s.split_rows))
+              return false;
+            break;
+          }
+          case mf::K_PINV_INIT:
+          case mf::K_PINV:
+            if (it.t < 0 || it.t >= nb || it.a < 0 || it.b < 0 || it.b >= nb ||
+                it.a >= nb + (I.m + mf::kNB - 1) / mf::kNB || s.ioff[it.s] < 0)
+              return false;
+            break;
+          default:
+            break;
+        }
+      }
+  for (int32_t r : s.rowidx)
+    if (r < 0 || r >= n) return false;
+  if (!mono(s.blkoff, 0, s.blkoff.empty() ? 0 : (int64_t)s.blkoff.back())) return false;
+  if (!mono(s.acol_ptr, 0, s.nnz_lower)) return false;
+  for (int64_t j = 0; j < n; ++j) {
+    const mf::SnInfo& I = s.sn[s.col2front[j]];
+    for (int64_t e = s.acol_ptr[j]; e < s.acol_ptr[j + 1]; ++e)
+      if (s.arow[e] < 0 || s.arow[e] >= I.k + I.m) return false;
+  }
+  if (s.asrc_ptr.size() != (size_t)s.nnz_lower + 1 ||
+      !mono(s.asrc_ptr, 0, (int64_t)s.asrc.size()))
+    return false;
+  for (int64_t x : s.asrc)
+    if (x < 0 || x >= s.nnzA) return false;
+  if (!mono(s.ginv_ptr, 0, (int64_t)s.ginv_src.size())) return false;
+  for (int64_t x : s.ginv_src)
+    if (x < 0 || x >= s.Wsize) return false;
+  for (const mf::Item& r : s.arange) {
+    if (r.s < -1 || r.s >= nfr) return false;
+    if (r.s >= 0 && (r.t < 0 || r.t > r.a || r.a > s.sn[r.s].m)) return false;
+  }
+  for (const auto* sched : {&s.fsched, &s.fsched_tc})
+    for (const mf::Launch& L : *sched)
+      if (L.kind == mf::K_ASSEMBLE)
+        for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+          const mf::Item& it = s.items[x];
+          // the chunk's child ranges start at arange[t] and end at a sentinel
+          if (it.t < 0 || it.t >= (int64_t)s.arange.size()) return false;
+          int64_t q = it.t;
+          while (q < (int64_t)s.arange.size() && s.arange[q].s >= 0) ++q;
+          if (q == (int64_t)s.arange.size()) return false;
+          const mf::SnInfo& I = s.sn[it.s];
+          if (it.a < 0 || it.a > it.b || it.b > I.k + I.m) return false;
+        }
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -247,6 +376,20 @@ int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s) {
   if (!r.ok || r.left != 0 || !consistent(*S)) {
     delete S;
     return mf::set_error(MF_ERR_INVALID, std::string("truncated or corrupt file: ") + path);
+  }
+  std::string why;
+  bool ranged = false;
+  try {
+    ranged = indices_in_range(*S) && mf::check_schedules(*S, why) == MF_OK;
+  } catch (const std::bad_alloc&) {
+    delete S;
+    return mf::set_error(MF_ERR_OOM, "host allocation failed");
+  }
+  if (!ranged) {
+    delete S;
+    return mf::set_error(MF_ERR_INVALID,
+                         std::string("analysis with an index out of range or an invalid "
+                                     "schedule: ") + path + (why.empty() ? "" : " (" + why + ")"));
   }
   *s = S;
   return MF_OK;

@@ -289,3 +289,10 @@ def test_expand_node_blocks_definition(orc, seed):
     if seed % 3 == 0:
         one = orc.expand_node_blocks(rp, ci, v, np.arange(n))
         assert np.array_equal(one[0], rp) and np.array_equal(one[1], ci)
+
+
+def test_berr_hand_computed(orc):
+    """oracle.berr against the worked 3x3 example in tests/_berr_pins.py
+    (residuals, norms and the maximum over right-hand sides by hand)."""
+    import _berr_pins
+    assert _berr_pins.failures(orc.berr) == set()

@@ -3,7 +3,11 @@ mistake in a copy of oracle/oracle.c (a wrong sign, a dropped term, a
 transposed operand, a wrong index, a wrong operation), compiles it with gcc,
 runs the pins against it on the CPU and requires at least one to fail.  Only
 mistakes that keep every array size consistent are planted, so a mutated
-oracle computes wrong numbers but never writes outside its buffers."""
+oracle computes wrong numbers but never writes outside its buffers.  The
+backward error (plain numpy in oracle/__init__.py) gets the same treatment:
+a mistake planted in a copy of its source must fail the hand-computed pins
+of tests/_berr_pins.py."""
+import inspect
 import os
 import subprocess
 
@@ -103,3 +107,24 @@ def test_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
     finally:
         orc._lib = saved
     assert failed, "no pin caught: " + name
+
+
+BERR_MUTATIONS = [
+    ("berr: ||b|| term dropped", " + np.max(np.abs(Bm[:, r]))", ""),
+    ("berr: first right-hand side only", "for r in range(X.shape[1]):", "for r in range(1):"),
+    ("berr: ||A|| taken as the largest entry",
+     "np.max(np.bincount(rows, weights=np.abs(values), minlength=n))", "np.max(np.abs(values))"),
+    ("berr: residual sign flipped", "np.abs(Bm[:, r] - ax)", "np.abs(Bm[:, r] + ax)"),
+    ("berr: transposed operand in A x", "values * X[colind, r]", "values * X[rows, r]"),
+    ("berr: ||x|| as a 1-norm", "np.max(np.abs(X[:, r]))", "np.sum(np.abs(X[:, r]))"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", BERR_MUTATIONS, ids=[m[0] for m in BERR_MUTATIONS])
+def test_berr_pins_catch_planted_mistake(orc, name, old, new):
+    import _berr_pins
+    src = inspect.getsource(orc.berr)
+    assert src.count(old) == 1, "mutation site not unique: " + name
+    ns = {"np": np}
+    exec(src.replace(old, new), ns)
+    assert _berr_pins.failures(ns["berr"]), "no pin caught: " + name

@@ -382,41 +382,73 @@ def _fnv1a(data):
     return h
 
 
-def test_schedule_check_catches_a_repeated_item(mf, handle, tmp_path):
-    """A saved analysis whose work list repeats one item (hash recomputed so
-    the loader accepts it) must fail the schedule check."""
-    rp, ci, v, perm, _ = gen.config3(8)
-    s = mf.mf_symbolic_analyze(handle, rp, ci, perm)
-    path = tmp_path / "a.sym"
-    mf.mf_symbolic_save(s, str(path))
-    mf.mf_symbolic_free(s)
-    data = bytearray(path.read_bytes())
-    # walk the members in file order to the work items
-    members = ["i8", "i8", ("v", 8), ("v", 4), ("v", 4), ("v", 4), ("v", 4), ("v", 8), ("v", 4),
-               ("v", 4), ("v", 4), ("v", 8), ("v", 8), ("v", 4), ("v", 4), "i4", ("v", 4),
-               ("v", 4), "i8", "i8", "i8", "i8", "i8", "i4", "i8", "i8", ("v", 64), ("v", 4),
-               ("v", 4), ("v", 4), ("v", 4), ("v", 8), ("v", 4), ("v", 8), ("v", 8), "i8", "i8",
-               "i8"]
+# members of a saved analysis in file order, up to the work items
+_MEMBERS = ["i8", "i8", ("v", 8), ("v", 4), ("v", 4), ("v", 4), ("v", 4), ("v", 8), ("v", 4),
+            ("v", 4), ("v", 4), ("v", 8), ("v", 8), ("v", 4), ("v", 4), "i4", ("v", 4),
+            ("v", 4), "i8", "i8", "i8", "i8", "i8", "i4", "i8", "i8", ("v", 64), ("v", 4),
+            ("v", 4), ("v", 4), ("v", 4), ("v", 8), ("v", 4), ("v", 8), ("v", 8), "i8", "i8",
+            "i8"]
+_ROWIDX, _RELMAP, _ASRC, _ITEMS = 28, 29, 34, len(_MEMBERS)
+
+
+def _member_pos(data, index):
+    """Byte offset of member `index` (its element count for a vector)."""
     pos = 32
-    for m in members:
+    for m in _MEMBERS[:index]:
         if isinstance(m, tuple):
             cnt = int.from_bytes(data[pos:pos + 8], "little")
             pos += 8 + cnt * m[1]
         else:
             pos += int(m[1])
+    return pos
+
+
+def _saved(mf, handle, tmp_path):
+    rp, ci, v, perm, _ = gen.config3(8)
+    s = mf.mf_symbolic_analyze(handle, rp, ci, perm)
+    path = tmp_path / "a.sym"
+    mf.mf_symbolic_save(s, str(path))
+    mf.mf_symbolic_free(s)
+    return path, bytearray(path.read_bytes()), len(rp) - 1
+
+
+def _load_fails(mf, handle, path, data, what):
+    data[-8:] = _fnv1a(data[32:-8]).to_bytes(8, "little")  # a matching hash
+    path.write_bytes(bytes(data))
+    with pytest.raises(mf.MFError) as e:
+        mf.mf_symbolic_load(handle, str(path))
+    assert e.value.code == mf.MF_ERR_INVALID
+    assert what in str(e.value)
+
+
+def test_load_rejects_a_repeated_item(mf, handle, tmp_path):
+    """A saved analysis whose work list repeats one item, with its hash
+    recomputed, fails the schedule check that the loader runs."""
+    path, data, _ = _saved(mf, handle, tmp_path)
+    pos = _member_pos(data, _ITEMS)
     nitems = int.from_bytes(data[pos:pos + 8], "little")
     assert nitems >= 2
     first = pos + 8
     data[first + 16:first + 32] = data[first:first + 16]  # item 1 := item 0
-    data[-8:] = _fnv1a(data[32:-8]).to_bytes(8, "little")
-    path.write_bytes(bytes(data))
-    t = mf.mf_symbolic_load(handle, str(path))
-    try:
-        with pytest.raises(mf.MFError) as e:
-            mf.mf_symbolic_check(t)
-        assert e.value.code == mf.MF_ERR_INTERNAL
-    finally:
-        mf.mf_symbolic_free(t)
+    _load_fails(mf, handle, path, data, "invalid schedule")
+
+
+@pytest.mark.parametrize("member,width,value", [
+    ("rowidx", 4, "n"), ("relmap", 4, 1 << 20), ("asrc", 8, 1 << 40), ("rowidx", 4, -1)])
+def test_load_rejects_an_index_out_of_range(mf, handle, tmp_path, member, width, value):
+    """Indices that device kernels dereference (front rows, relative maps,
+    CSR source positions) are range-checked on load: a file planted with one
+    out-of-range entry and a matching hash is refused before any device code
+    could see it."""
+    path, data, n = _saved(mf, handle, tmp_path)
+    idx = {"rowidx": _ROWIDX, "relmap": _RELMAP, "asrc": _ASRC}[member]
+    pos = _member_pos(data, idx)
+    cnt = int.from_bytes(data[pos:pos + 8], "little")
+    assert cnt > 0
+    val = n if value == "n" else value
+    at = pos + 8 + (cnt // 2) * width
+    data[at:at + width] = int(val).to_bytes(width, "little", signed=True)
+    _load_fails(mf, handle, path, data, "index out of range")
 
 
 def test_condensed_edge_cases(mf, handle, orc):
