@@ -238,9 +238,54 @@ def kernel_source_sha1(path, signature):
     return None
 
 
+# Oracle sample: the etree subtree with the most flops that stays within
+# SAMPLE_FLOPS (sum c_j^2 over its columns).  Fixed flops, not a time budget,
+# so the CPU-baseline leg and the reference arm pick the same columns on any
+# host.  On the nested-dissection orders used here it holds a separator front
+# of several hundred to a few thousand columns and everything below it.
+SAMPLE_FLOPS = 2.5e10
+
+
+def oracle_sample(orc, rp, ci, perm, budget=SAMPLE_FLOPS):
+    """(sym, in_s mask, root, columns, flops) of the sample subtree."""
+    n = len(rp) - 1
+    so = orc.symbolic(rp, ci, perm)
+    parent, cc = so["parent"], so["colcount"].astype(np.float64)
+    sub = cc * cc
+    for j in range(n):  # parent(j) > j: children are complete before parents
+        p = parent[j]
+        if p >= 0:
+            sub[p] += sub[j]
+    ok = np.nonzero(sub <= budget)[0]
+    root = int(ok[np.argmax(sub[ok])])
+    in_s = orc.descendant_closed(parent, [root])
+    cols = np.nonzero(in_s)[0]
+    return {"rows": so["rows"], "parent": parent}, in_s, root, cols, float(sub[root])
+
+
+def host_info():
+    """Core counts of this host (the oracle's cores) and the CPU model."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        info["affinity"] = len(os.sched_getaffinity(0))
+    except AttributeError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                             text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Architecture", "CPU(s)", "Socket(s)",
+                             "Core(s) per socket", "Thread(s) per core"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
 def run_reference(args):
-    """The oracle on the host cores, each step a bounded sample (first J
-    columns of the elimination order) of the same matrix."""
+    """The oracle on all host cores, each step the fixed-flops etree subtree
+    sample of the same matrix that the CPU-baseline leg times."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -249,32 +294,27 @@ def run_reference(args):
     oracle.build()
     rp, ci, v, perm, b = load_workload(args)
     n = len(rp) - 1
-    rows = oracle.lower_rows(rp, ci, perm)
-    sym = {"rows": rows, "parent": oracle.etree(n, *rows)}
-    # calibrate J so that one step is ~ per_step seconds
-    per_step = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
-    flops, dt, J = oracle.factor_sample(rp, ci, v, perm, seconds=per_step, sym=sym)
-    in_s = np.zeros(n, dtype=np.uint8)
-    in_s[:J] = 1
+    sym, in_s, root, cols, sflops = oracle_sample(oracle, rp, ci, perm)
+    threads = oracle.threads_available()
     for _ in range(args.warmup):
-        oracle.factor(rp, ci, v, perm, in_s=in_s, sym=sym)
+        oracle.factor(rp, ci, v, perm, in_s=in_s, sym=sym, threads=threads)
     t0 = time.perf_counter()
     fl = 0.0
     for _ in range(args.steps):
-        F = oracle.factor(rp, ci, v, perm, in_s=in_s, sym=sym)
+        F = oracle.factor(rp, ci, v, perm, in_s=in_s, sym=sym, threads=threads)
         fl += F.flops
     el = time.perf_counter() - t0
     val = fl / el / 1e12
-    sample = "first %d of %d columns of the elimination order (descendant-closed), %.3g flops per step" % (
-        J, n, F.flops)
+    sample = ("etree subtree rooted at column %d: %d of %d columns, %.3g flops per step "
+              "(the same sample as the CPU-baseline leg)" % (root, len(cols), n, F.flops))
     out = {
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+        "impl": "reference", "metric": metric_for(args), "value": val, "unit": "TFLOP/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args), "n": n, "l2_flush": "inputs larger than L2"},
-        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": F.threads, "kind": "oracle",
+                         "sample": sample, "host": host_info()},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -401,6 +441,7 @@ def main():
         step()
     mf.mf_factor_check(f, stream=st)
     torch.cuda.synchronize()
+    fp64_peak = {"dfma": mf.mf_diag_fp64_peak(0, stream=st), "dmma": mf.mf_diag_fp64_peak(1, stream=st)}
     clk = ClockSampler(local)
     clk.start()
     barrier(ws)
@@ -420,13 +461,6 @@ def main():
     ms_max = max_over_ranks(ws, ms)
     flops = info["flops"]
     value = job_value(flops, args.steps, ws, ms_max) / 1e12
-    x = xd.cpu().numpy()
-    rows = np.repeat(np.arange(n), np.diff(rp))
-    anorm = np.max(np.bincount(rows, weights=np.abs(v), minlength=n))
-    res = (b - gen.csr_matvec(rp, ci, v, x)).reshape(n, -1)
-    xx, bb = x.reshape(n, -1), b.reshape(n, -1)
-    berr = float(np.max(np.max(np.abs(res), axis=0) /
-                        (anorm * np.max(np.abs(xx), axis=0) + np.max(np.abs(bb), axis=0))))
 
     out = {
         "metric": metric_for(args), "value": value, "unit": "TFLOP/s", "n_gpus": ws,
@@ -443,7 +477,6 @@ def main():
                    "l2_flush": "inputs larger than L2 (factor %.1f GB)" % (
                        info["factor_bytes_fp64"] / 1e9),
                    "symbolic_s": t_sym},
-        "berr": berr,
         "step": ("FP32 factor + FP64-refined solve to berr 1e-13" if args.ir else
                  "%s factor + %s solve" % (args.prec.upper(), args.prec.upper())),
         "autotune": tuned,
@@ -468,22 +501,28 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    bf16 = peaks.get("bf16_tflops", 1900.0)
+    bf16 = peaks.get("bf16_tflops")
+    bf16_src = "measured" if bf16 else "fallback"
+    bf16 = bf16 or 1900.0
     ach = prof[dom]["flops"] / (prof[dom]["ms"] / 1e3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
     if dom == "syrk_tc":
         bound = "tensor"
         peak = bf16 * (1100.0 / 2250.0) / 3.0
-        src = ("measured bf16 %.0f TFLOP/s x nominal TF32/bf16 1100/2250, / 3 for split-TF32 "
-               "(useful FP32 flops)" % bf16)
+        src = ("of %s: bf16 %.0f TFLOP/s x nominal TF32/bf16 1100/2250, / 3 for split-TF32 "
+               "(useful FP32 flops)" % (bf16_src, bf16))
     elif args.prec == "fp32":
         bound = "alu"
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        src = "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
+        src = "derived: FP32 FMA, 152 SMs x 128 lanes x 2 flops x 2.07 GHz"
     else:
+        # measured on this GPU by the two FP64 probes (register-resident
+        # DFMA and DMMA loops); the faster one is the FP64 pipe's peak
         bound = "alu"
-        peak = 152 * 2 * 2 * 2.07e9 / 1e12
-        src = ("FP64 FMA (DFMA; FP64 tensor cores are no faster on GB300): 152 SMs x 2 FMA/clk "
-               "x 2 flops x 2.07 GHz = the nominal 1.25 TFLOP/s")
+        out["fp64_peak_probe"] = fp64_peak
+        peak = max(fp64_peak.values())
+        src = ("of measured: best of the DFMA (%.3f) and DMMA (%.3f) TFLOP/s probes run by "
+               "mf_diag_fp64_peak on this GPU before the timed region"
+               % (fp64_peak["dfma"], fp64_peak["dmma"]))
     traffic = None
     if (dom == "syrk" and args.prec == "fp64" and workload_name(args) == SYRK_TRAFFIC["workload"]
             and prof["syrk"]["launches"] == SYRK_TRAFFIC["launches"]
@@ -495,7 +534,7 @@ def main():
                        "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                        "peak_source": src}
     if rank == 0 and not args.no_extras:
-        extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm)
+        extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, xd, st, dev, info, perm)
     if rank == 0:
         print(json.dumps(out))
     mf.mf_factor_free(f)
@@ -506,24 +545,39 @@ def main():
         dist.destroy_process_group()
 
 
-def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm):
+def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, xd, st, dev, info, perm):
     import torch
     n = len(rp) - 1
     # solve latency (nrhs right-hand sides), p50 / p99 over 200 solves
-    xd = torch.empty_like(bd)
+    xs = torch.empty_like(bd)
     for _ in range(3):
-        mf.mf_solve(f, bd, xd, stream=st)
-    lat = []
+        mf.mf_solve(f, bd, xs, stream=st)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(200)]
     for a, z in ev:
         a.record(st)
-        mf.mf_solve(f, bd, xd, stream=st)
+        mf.mf_solve(f, bd, xs, stream=st)
         z.record(st)
     torch.cuda.synchronize()
+    mf.mf_solve_check(f, stream=st)
     lat = np.array([a.elapsed_time(z) for a, z in ev])
-    out["solve_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))}
+    out["solve_ms"] = {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "samples": len(lat)}
     out["solves_per_s"] = float(1e3 / np.mean(lat))
     out["solve_nrhs"] = args.nrhs
+    # algorithmic bytes of one solve: L read once per sweep plus the
+    # right-hand side / solution vectors (4 passes of n x nrhs values)
+    es = 4 if args.prec == "fp32" else 8
+    sbytes = 2.0 * es * info["nnz_L"] + 4.0 * es * n * args.nrhs
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    gbs = sbytes / (out["solve_ms"]["p50"] / 1e3) / 1e9
+    out["solve_roofline"] = {"bound": "hbm", "bytes": sbytes, "achieved": gbs, "peak": hbm,
+                             "unit": "GB/s", "frac": gbs / hbm,
+                             "peak_source": "of measured" if peaks.get("hbm_gbs") else "of fallback"}
     # end to end through the C-ABI with host buffers (values H2D, B H2D, X D2H)
     K = 2
     xh = np.empty_like(b, order="F")
@@ -538,33 +592,107 @@ def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, st, dev, info, perm):
     out["e2e"] = {"value": info["flops"] * K / el / 1e12, "unit": "TFLOP/s",
                   "h2d_bytes_per_step": int(v.nbytes + b.nbytes),
                   "d2h_bytes_per_step": int(xh.nbytes + 16)}
-    # FP32 factorization + FP64 refinement to berr 1e-13 on the same matrix
+    # FP32 factorization + FP64 refinement to berr 1e-13 on the same matrix:
+    # 3 warm-up steps, then the median of 10; refined-solve p50 / p99 over
+    # 200 calls
+    f32 = None
+    x32 = None
     try:
         f32 = mf.mf_factor_create(h, s, mf.MF_FP32)
-        mf.mf_factor_numeric(f32, vd, stream=st)
         xr = torch.empty_like(bd)
+
+        def step32():
+            mf.mf_factor_numeric(f32, vd, stream=st, async_=True)
+            return mf.mf_solve_refined(f32, bd, xr, tol=1e-13, max_iter=30, stream=st)[1]
+
+        for _ in range(3):
+            step32()
         torch.cuda.synchronize()
-        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(st)
-        mf.mf_factor_numeric(f32, vd, stream=st, async_=True)
-        _, rep = mf.mf_solve_refined(f32, bd, xr, tol=1e-13, max_iter=30, stream=st)
-        z.record(st)
-        torch.cuda.synchronize()
-        out["fp32_ir"] = {"ms_factor_plus_refined_solve": a.elapsed_time(z), "report": rep}
+        ms32, reps = [], []
+        for _ in range(10):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            reps.append(step32())
+            z.record(st)
+            torch.cuda.synchronize()
+            ms32.append(a.elapsed_time(z))
+        mf.mf_factor_check(f32, stream=st)
+        lat32 = []
+        for _ in range(200):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            mf.mf_solve_refined(f32, bd, xr, tol=1e-13, max_iter=30, stream=st)
+            z.record(st)
+            torch.cuda.synchronize()
+            lat32.append(a.elapsed_time(z))
+        x32 = xr.cpu().numpy()
+        out["fp32_ir"] = {
+            "ms_factor_plus_refined_solve": {"median": float(np.median(ms32)),
+                                             "min": float(np.min(ms32)),
+                                             "max": float(np.max(ms32)), "steps": len(ms32),
+                                             "warmup": 3},
+            "tflops_median": info["flops"] / (np.median(ms32) / 1e3) / 1e12,
+            "refined_solve_ms": {"p50": float(np.percentile(lat32, 50)),
+                                 "p99": float(np.percentile(lat32, 99)), "samples": len(lat32)},
+            "report_last_step": reps[-1],
+            "iterations": sorted(set(int(r["iterations"]) for r in reps)),
+            "fell_back": any(r["fell_back"] for r in reps),
+        }
         if not args.ir:
             out["fp32_ir"]["fp64_ms_per_step"] = out["ms_per_step"]
-        mf.mf_factor_free(f32)
+            out["fp32_ir"]["speedup_vs_fp64_step"] = out["ms_per_step"] / float(np.median(ms32))
     except Exception as e:  # report, do not hide the main number
         out["fp32_ir"] = {"error": str(e)}
-    # the oracle on the host cores, bounded sample of the same workload
     if int(os.environ.get("WORLD_SIZE", "1")) == 1:
-        import oracle
-        oracle.build()
-        flops, dt, J = oracle.factor_sample(rp, ci, v, perm, seconds=args.cpu_seconds)
-        out["cpu_baseline"] = {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": 1,
-                               "kind": "oracle",
-                               "sample": "first %d of %d columns (descendant-closed), %.3g flops, %.1f s"
-                                         % (J, n, flops, dt)}
+        oracle_leg(args, out, mf, s, f, f32, rp, ci, v, b, xd, x32, perm)
+    if f32 is not None:
+        mf.mf_factor_free(f32)
+
+
+def oracle_leg(args, out, mf, s, f, f32, rp, ci, v, b, xd, x32, perm):
+    """The CPU-baseline leg (rank 0, one GPU): the oracle times a fixed-flops
+    etree subtree of the same matrix with one thread and with all host cores,
+    and that exact factor checks the GPU factors' columns entry by entry; the
+    backward errors of the timed step's solution and of the FP32 + refinement
+    solution are the oracle's measure."""
+    import oracle
+    oracle.build()
+    n = len(rp) - 1
+    sym, in_s, root, cols, sflops = oracle_sample(oracle, rp, ci, perm)
+    runs = {}
+    for threads in (1, oracle.threads_available()):
+        t0 = time.perf_counter()
+        F = oracle.factor(rp, ci, v, perm, in_s=in_s, sym=sym, threads=threads)
+        dt = time.perf_counter() - t0
+        runs[F.threads] = (F, dt)
+    F, dt = runs[max(runs)]
+    F1, dt1 = runs[min(runs)]
+    sample = ("etree subtree rooted at column %d: %d of %d columns, %.3g flops"
+              % (root, len(cols), n, F.flops))
+    out["cpu_baseline"] = {"value": F.flops / dt / 1e12, "unit": "TFLOP/s", "cores": F.threads,
+                           "kind": "oracle", "sample": sample, "seconds": dt,
+                           "one_thread": {"value": F1.flops / dt1 / 1e12, "cores": 1,
+                                          "seconds": dt1},
+                           "host": host_info()}
+    # element-wise parity of the GPU factors on the sample's columns
+    j0, j1 = int(cols[0]), int(cols[-1]) + 1
+    cc = mf.mf_symbolic_colcounts(s)[j0:j1]  # column counts of the global pattern
+    par = {"sample_columns": [j0, j1], "contiguous": bool(len(cols) == j1 - j0),
+           "sample_max_column_count": int(cc.max())}
+    ref = F.Lx[F.Lp[j0]:F.Lp[j1]]  # the oracle stores the sample's columns only
+    mask = np.repeat(in_s[j0:j1].astype(bool), cc)
+    for name, fac in (("fp64", f), ("fp32", f32)):
+        if fac is None:
+            continue
+        got = mf.mf_factor_export_columns(fac, j0, j1, int(cc.sum()))[mask]
+        assert len(got) == len(ref)
+        par["relF_sample_" + name] = oracle.rel_fro(got, ref)
+    x64 = xd.cpu().numpy()
+    par["berr_step_solution"] = oracle.berr(rp, ci, v, x64, b)
+    if x32 is not None:
+        par["berr_fp32_ir"] = oracle.berr(rp, ci, v, x32, b)
+        par["fwd_err_fp32_ir_vs_fp64"] = float(np.max(np.abs(x32 - x64)) / np.max(np.abs(x64)))
+    out["parity"] = par
 
 
 if __name__ == "__main__":

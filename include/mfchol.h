@@ -277,6 +277,15 @@ int mf_factor_free(mf_factor* f);
  * FP32 factors are widened).  Synchronous. */
 int mf_factor_export_L(const mf_factor* f, double* Lx);
 
+/* Copy the columns j0 .. j1-1 (permuted numbering) of L to the host: the
+ * sum of their column counts c_j doubles, column by column in the order of
+ * mf_symbolic_pattern (entries Lp[j0] .. Lp[j1] of mf_factor_export_L's
+ * output).  Copies only the fronts holding those columns, so a sample of a
+ * very large factor can be checked without moving all of L.  Synchronous.
+ * Errors: MF_ERR_INVALID for a range outside [0, n]. */
+int mf_factor_export_columns(const mf_factor* f, int64_t j0, int64_t j1,
+                             double* Lx);
+
 /* Kernel launches issued by one numeric factorization / one 1-RHS solve. */
 int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches,
                             int64_t* solve_launches);
@@ -344,6 +353,16 @@ int mf_solve_noalloc(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
  * expected outcome), MF_ERR_INVALID for polls < 1, MF_ERR_CUDA on a CUDA
  * error. */
 int mf_diag_wait_timeout(int32_t polls, void* stream);
+
+/* Diagnostic (no paper counterpart): the measured FP64 peak of the current
+ * GPU in TFLOP/s, the denominator of the FP64 front kernels' roofline.
+ * kind 0 times a register-resident DFMA loop (16 independent FMA chains per
+ * thread, one full wave of resident 256-thread blocks), kind 1 a DMMA loop (mma.sync m8n8k4 f64, 8
+ * independent accumulator tiles per warp); best of three launches of about
+ * 10^11 flops each, CUDA events on `stream` (synchronized).  Allocates and
+ * frees a small device buffer.  Errors: MF_ERR_INVALID for another kind or
+ * a NULL output, MF_ERR_CUDA. */
+int mf_diag_fp64_peak(int32_t kind, void* stream, double* tflops);
 
 /* Mixed-precision solve: f is an FP32 factor; the residual r = B - A X, the
  * update X += D and the backward error

@@ -42,12 +42,17 @@ _lib = None
 
 
 def build(force=False):
-    """Compile the C oracle with the host compiler (portable flags only)."""
+    """Compile the C oracle with the host compiler (portable flags only;
+    OpenMP for the multi-threaded factorization where the compiler has it)."""
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    try:
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC,
+                               "-lm"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -64,6 +69,11 @@ def load_library(path):
     lib.orc_pattern.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P]
     lib.orc_factor.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P]
     lib.orc_factor.restype = ctypes.c_int64
+    lib.orc_par_threads.argtypes = [ctypes.c_int]
+    lib.orc_par_threads.restype = ctypes.c_int
+    lib.orc_factor_par.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int, P, P, P,
+                                   P, P, P]
+    lib.orc_factor_par.restype = ctypes.c_int64
     lib.orc_supernodes.argtypes = [I, P, P, P, P]
     lib.orc_supernodes.restype = ctypes.c_int64
     lib.orc_solve.argtypes = [I, P, P, P, P, I, I]
@@ -106,12 +116,14 @@ def lower_rows(rowptr, colind, perm):
     """Strict lower triangle of C by rows: (rp int64[n+1], ci int32), sorted, unique."""
     n, i, j, _ = _lower_coo(rowptr, colind, None, perm)
     strict = i > j
-    key = np.unique(i[strict] * n + j[strict])
+    key = np.sort(i[strict] * n + j[strict])
+    if len(key):
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     r = key // n
     c = (key % n).astype(np.int32)
     rp = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(rp, r + 1, 1)
-    return np.cumsum(rp), c
+    rp[1:] = np.cumsum(np.bincount(r, minlength=n))
+    return rp, c
 
 
 def lower_cols(rowptr, colind, values, perm):
@@ -127,8 +139,8 @@ def lower_cols(rowptr, colind, values, perm):
     c = uniq // n
     r = (uniq % n).astype(np.int32)
     cp = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(cp, c + 1, 1)
-    return np.cumsum(cp), r, cx
+    cp[1:] = np.cumsum(np.bincount(c, minlength=n))
+    return cp, r, cx
 
 
 # ---------------------------------------------------------------------------
@@ -232,8 +244,23 @@ class Factor:
         return 2.0 * float(np.sum(np.log(self.Lx[self.Lp[:-1]])))
 
 
-def factor(rowptr, colind, values, perm, in_s=None, sym=None):
-    """Left-looking FP64 Cholesky of C = A(perm, perm); columns in S only."""
+def threads_available():
+    """Host threads the multi-threaded oracle uses by default (the CPUs this
+    process may run on); 1 if the library was built without OpenMP."""
+    lib = _load()
+    try:
+        cpus = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cpus = os.cpu_count() or 1
+    return min(cpus, lib.orc_par_threads(cpus))
+
+
+def factor(rowptr, colind, values, perm, in_s=None, sym=None, threads=1):
+    """Left-looking FP64 Cholesky of C = A(perm, perm); columns in S only.
+
+    threads > 1 computes the columns of equal etree height in parallel
+    (columns read only their own etree subtree), bitwise identical to the
+    one-thread result; threads = 0 takes ``threads_available()``."""
     lib = _load()
     n = len(rowptr) - 1
     if sym is None:
@@ -259,11 +286,27 @@ def factor(rowptr, colind, values, perm, in_s=None, sym=None):
                     _p(Rk), _p(Rq), _p(mark), _p(fill))
     Cp, Cr, Cx = lower_cols(rowptr, colind, values, perm)
     Lx = np.zeros(int(Lp[-1]), dtype=np.float64)
-    x = np.zeros(n, dtype=np.float64)
     fl = ctypes.c_double(0.0)
-    bad = lib.orc_factor(n, _p(Cp), _p(Cr), _p(Cx), _p(in_s), _p(Lp), _p(Li), _p(Lx),
-                         _p(Rp), _p(Rk), _p(Rq), _p(x), ctypes.byref(fl))
-    return Factor(n, Lp, Li, Lx, int(bad), fl.value)
+    if threads == 0:
+        threads = threads_available()
+    nt = lib.orc_par_threads(int(threads)) if threads > 1 else 1
+    if nt > 1:
+        xs = np.zeros(nt * n, dtype=np.float64)
+        height = np.empty(n, dtype=np.int32)
+        order = np.empty(n, dtype=np.int32)
+        hptr = np.empty(n + 2, dtype=np.int64)
+        badm = np.empty(n, dtype=np.uint8)
+        parent = np.ascontiguousarray(parent, dtype=np.int32)
+        bad = lib.orc_factor_par(n, _p(Cp), _p(Cr), _p(Cx), _p(in_s), _p(Lp), _p(Li), _p(Lx),
+                                 _p(Rp), _p(Rk), _p(Rq), _p(parent), nt, _p(xs), _p(height),
+                                 _p(order), _p(hptr), _p(badm), ctypes.byref(fl))
+    else:
+        x = np.zeros(n, dtype=np.float64)
+        bad = lib.orc_factor(n, _p(Cp), _p(Cr), _p(Cx), _p(in_s), _p(Lp), _p(Li), _p(Lx),
+                             _p(Rp), _p(Rk), _p(Rq), _p(x), ctypes.byref(fl))
+    F = Factor(n, Lp, Li, Lx, int(bad), fl.value)
+    F.threads = nt
+    return F
 
 
 def solve(F, b, perm):

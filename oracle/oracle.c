@@ -31,6 +31,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* Elimination tree by Liu's algorithm with path compression over the rows of
  * the strict lower triangle.  anc: workspace of n ints. */
@@ -107,6 +110,39 @@ void orc_pattern(int64_t n, const int64_t* rp, const int32_t* ci,
   }
 }
 
+/* Column j of the left-looking factorization: x = C[j:, j] minus the
+ * contributions L[j:, k] L_jk of every column k < j with L_jk != 0 (in the
+ * order of j's row list), then L_jj = sqrt(x_j) and L[j+1:, j] = x / L_jj.
+ * x: dense workspace of n doubles, zero on entry and exit.  Reads only
+ * columns of j's etree subtree.  Returns 0, or 1 if the pivot is not
+ * positive (column j is then left unwritten). */
+static int factor_column(int64_t j, const int64_t* Cp, const int32_t* Cr,
+                         const double* Cx, const int64_t* Lp, const int32_t* Li,
+                         double* Lx, const int64_t* Rp, const int32_t* Rk,
+                         const int64_t* Rq, double* x) {
+  for (int64_t p = Cp[j]; p < Cp[j + 1]; ++p) x[Cr[p]] += Cx[p];
+  for (int64_t r = Rp[j]; r < Rp[j + 1]; ++r) {
+    int32_t k = Rk[r];
+    int64_t q = Rq[r]; /* position of L_jk in column k */
+    double ljk = Lx[q];
+    for (int64_t t = q; t < Lp[k + 1]; ++t) x[Li[t]] -= Lx[t] * ljk;
+  }
+  double d = x[j];
+  if (!(d > 0.0)) {
+    for (int64_t t = Lp[j]; t < Lp[j + 1]; ++t) x[Li[t]] = 0.0;
+    return 1;
+  }
+  double ljj = sqrt(d);
+  Lx[Lp[j]] = ljj;
+  x[j] = 0.0;
+  for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) {
+    int32_t i = Li[t];
+    Lx[t] = x[i] / ljj;
+    x[i] = 0.0;
+  }
+  return 0;
+}
+
 /* Left-looking numeric factorization of the columns in S, in increasing
  * order.  Cp/Cr/Cx: lower triangle of C by columns.  x: dense workspace of n
  * doubles, zero on entry and exit.  Returns -1 on success or the first column
@@ -120,32 +156,89 @@ int64_t orc_factor(int64_t n, const int64_t* Cp, const int32_t* Cr,
   double fl = 0.0;
   for (int64_t j = 0; j < n; ++j) {
     if (!in_s[j]) continue;
-    for (int64_t p = Cp[j]; p < Cp[j + 1]; ++p) x[Cr[p]] += Cx[p];
-    for (int64_t r = Rp[j]; r < Rp[j + 1]; ++r) {
-      int32_t k = Rk[r];
-      int64_t q = Rq[r]; /* position of L_jk in column k */
-      double ljk = Lx[q];
-      for (int64_t t = q; t < Lp[k + 1]; ++t) x[Li[t]] -= Lx[t] * ljk;
-    }
-    double d = x[j];
-    if (!(d > 0.0)) {
-      for (int64_t t = Lp[j]; t < Lp[j + 1]; ++t) x[Li[t]] = 0.0;
+    if (factor_column(j, Cp, Cr, Cx, Lp, Li, Lx, Rp, Rk, Rq, x)) {
       *flops_done = fl;
       return j;
-    }
-    double ljj = sqrt(d);
-    Lx[Lp[j]] = ljj;
-    x[j] = 0.0;
-    for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) {
-      int32_t i = Li[t];
-      Lx[t] = x[i] / ljj;
-      x[i] = 0.0;
     }
     double c = (double)(Lp[j + 1] - Lp[j]);
     fl += c * c;
   }
   *flops_done = fl;
   return -1;
+}
+
+/* The same factorization on several host threads (OpenMP), exact and
+ * deterministic: column j reads only columns of its own etree subtree, so
+ * columns of equal height in the etree (height = 1 + the largest height of a
+ * child, leaves 0) never read one another and are computed in parallel, one
+ * height after the other.  Each column is computed by factor_column exactly
+ * as in orc_factor, so L is bitwise the same.  A column whose subtree holds a
+ * failed pivot is skipped; the smallest failing column is returned, which is
+ * the column orc_factor reports.  parent: the etree; threads <= 0 means the
+ * OpenMP default; xs: threads * n doubles of zeroed workspace (threads as
+ * orc_par_threads returns); height, order: n ints of workspace; hptr: n + 2
+ * int64 of workspace.  flops_done: sum c_j^2 over the completed columns. */
+int orc_par_threads(int threads) {
+#ifdef _OPENMP
+  return threads > 0 ? threads : omp_get_max_threads();
+#else
+  (void)threads;
+  return 1;
+#endif
+}
+
+int64_t orc_factor_par(int64_t n, const int64_t* Cp, const int32_t* Cr,
+                       const double* Cx, const uint8_t* in_s, const int64_t* Lp,
+                       const int32_t* Li, double* Lx, const int64_t* Rp,
+                       const int32_t* Rk, const int64_t* Rq, const int32_t* parent,
+                       int threads, double* xs, int32_t* height, int32_t* order,
+                       int64_t* hptr, uint8_t* bad, double* flops_done) {
+  int nt = orc_par_threads(threads);
+  int32_t hmax = 0;
+  for (int64_t j = 0; j < n; ++j) height[j] = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    bad[j] = 0;
+    if (height[j] > hmax) hmax = height[j];
+    if (parent[j] >= 0 && height[parent[j]] < height[j] + 1) height[parent[j]] = height[j] + 1;
+  }
+  for (int64_t h = 0; h <= (int64_t)hmax + 1; ++h) hptr[h] = 0;
+  for (int64_t j = 0; j < n; ++j) hptr[height[j] + 1] += 1;
+  for (int64_t h = 0; h <= hmax; ++h) hptr[h + 1] += hptr[h];
+  for (int64_t j = 0; j < n; ++j) order[hptr[height[j]]++] = (int32_t)j;
+  for (int64_t h = hmax; h > 0; --h) hptr[h] = hptr[h - 1];
+  hptr[0] = 0;
+  double fl = 0.0;
+  int64_t first_bad = -1;
+  for (int64_t h = 0; h <= hmax; ++h) {
+    const int64_t lo = hptr[h], hi = hptr[h + 1];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt) reduction(+ : fl)
+#endif
+    for (int64_t q = lo; q < hi; ++q) {
+      const int64_t j = order[q];
+      if (!in_s[j]) continue;
+      int tid = 0;
+#ifdef _OPENMP
+      tid = omp_get_thread_num();
+#endif
+      if (bad[j]) continue; /* a descendant failed */
+      if (factor_column(j, Cp, Cr, Cx, Lp, Li, Lx, Rp, Rk, Rq, xs + (int64_t)tid * n)) {
+        bad[j] = 2;
+      } else {
+        double c = (double)(Lp[j + 1] - Lp[j]);
+        fl += c * c;
+      }
+    }
+    /* serial: propagate failures to the parents (next heights) */
+    for (int64_t q = lo; q < hi; ++q) {
+      const int64_t j = order[q];
+      if (bad[j] == 2 && (first_bad < 0 || j < first_bad)) first_bad = j;
+      if (bad[j] && parent[j] >= 0) bad[parent[j]] = bad[parent[j]] ? bad[parent[j]] : 1;
+    }
+  }
+  (void)nt;
+  *flops_done = fl;
+  return first_bad;
 }
 
 /* Fundamental supernodes.  sup_ptr receives the first column of every

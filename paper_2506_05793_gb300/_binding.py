@@ -98,6 +98,8 @@ _SIGS = {
     "mf_server_free": [_P],
     "mf_diag_wait_timeout": [_I32, _P],
     "mf_solve_check": [_P, _P],
+    "mf_factor_export_columns": [_P, _I64, _I64, _P],
+    "mf_diag_fp64_peak": [_I32, _P, _P],
     "mf_factor_set_wait_limit": [_P, _I32],
     "mf_factor_solve_work_bytes": [_P, _P],
 }
@@ -339,6 +341,13 @@ def mf_factor_export_L(f, nnz_L):
     return out
 
 
+def mf_factor_export_columns(f, j0, j1, count):
+    """Values of columns j0..j1-1 of L (``count`` = sum of their column counts)."""
+    out = np.empty(count, dtype=np.float64)
+    _check(lib().mf_factor_export_columns(f, j0, j1, _ptr(out)))
+    return out
+
+
 def mf_factor_launch_counts(f):
     a, b = _I64(), _I64()
     _check(lib().mf_factor_launch_counts(f, ctypes.byref(a), ctypes.byref(b)))
@@ -358,6 +367,13 @@ def mf_diag_wait_timeout(polls=1 << 14, stream=None):
     """Run the solve's bounded device wait on a flag nothing sets; returns the
     status code (MF_ERR_TIMEOUT expected) instead of raising."""
     return int(lib().mf_diag_wait_timeout(polls, _stream(stream)))
+
+
+def mf_diag_fp64_peak(kind, stream=None):
+    """Measured FP64 peak in TFLOP/s: kind 0 DFMA loop, 1 DMMA loop."""
+    out = _D(0.0)
+    _check(lib().mf_diag_fp64_peak(kind, _stream(stream), ctypes.byref(out)))
+    return float(out.value)
 
 
 def _rhs_layout(B):

@@ -678,6 +678,53 @@ int mf_factor_export_L(const mf_factor* f, double* Lx) {
   return MF_OK;
 }
 
+int mf_factor_export_columns(const mf_factor* f, int64_t j0, int64_t j1, double* Lx) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  const mf_symbolic* S = f->S;
+  if (j0 < 0 || j1 < j0 || j1 > S->n || (!Lx && j1 > j0))
+    return set_error(MF_ERR_INVALID, "invalid column range");
+  if (j1 == j0) return MF_OK;
+  const size_t es = elem_size(f->prec);
+  std::vector<unsigned char> buf;
+  std::vector<int32_t> pos;
+  try {
+    mf::ensure_fundamental_rows(*S);
+    pos.assign(S->n, -1);
+  } catch (const std::bad_alloc&) {
+    return set_error(MF_ERR_OOM, "host allocation failed");
+  }
+  MF_CK(cudaDeviceSynchronize());
+  int64_t out = 0;
+  for (int32_t F = S->col2front[j0]; F <= S->col2front[j1 - 1]; ++F) {
+    const mf::SnInfo& I = S->sn[F];
+    const int64_t nf = I.k + I.m;
+    try {
+      buf.resize((size_t)(nf * I.k) * es);
+    } catch (const std::bad_alloc&) {
+      return set_error(MF_ERR_OOM, "host allocation failed");
+    }
+    MF_CK(cudaMemcpy(buf.data(), static_cast<const unsigned char*>(f->L) + I.Loff * es,
+                     buf.size(), cudaMemcpyDeviceToHost));
+    const float* b32 = reinterpret_cast<const float*>(buf.data());
+    const double* b64 = reinterpret_cast<const double*>(buf.data());
+    const int32_t* frows = S->rowidx.data() + I.rows_off;
+    for (int64_t r = 0; r < nf; ++r) pos[frows[r]] = (int32_t)r;
+    const int64_t c0 = std::max<int64_t>(I.first, j0), c1 = std::min<int64_t>(I.first + I.k, j1);
+    for (int64_t j = c0; j < c1; ++j) {
+      const int32_t sn = S->col2sn[j];
+      const int32_t t = (int32_t)(j - S->sup_ptr[sn]);
+      const int32_t* rows = S->fs_rowidx.data() + S->fs_rows_off[sn];
+      const int64_t nr = S->fs_rows_off[sn + 1] - S->fs_rows_off[sn];
+      const int64_t col = (j - I.first) * nf;
+      for (int64_t r = t; r < nr; ++r) {
+        const int64_t idx = col + pos[rows[r]];
+        Lx[out++] = f->prec == MF_FP32 ? (double)b32[idx] : b64[idx];
+      }
+    }
+  }
+  return MF_OK;
+}
+
 int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches, int64_t* solve_launches) {
   if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
   // + 1: the gather of the values into assembly order
@@ -718,6 +765,39 @@ int mf_diag_wait_timeout(int32_t polls, void* stream) {
   else
     rc = set_error(MF_ERR_INTERNAL, "wait probe returned without a timeout record");
   return rc;
+}
+
+int mf_diag_fp64_peak(int32_t kind, void* stream, double* tflops) {
+  if ((kind != 0 && kind != 1) || !tflops) return set_error(MF_ERR_INVALID, "invalid peak probe");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  MF_CK(cudaGetDevice(&dev));
+  MF_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * mf::peak_fp64_blocks_per_sm(kind);  // one full wave
+  const int64_t iters = kind == 0 ? 20000 : 6000;
+  double* out = nullptr;
+  MF_CK(cudaMalloc(&out, (size_t)blocks * 256 * sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.f;
+  // one short warm-up launch, then the best of three timed launches
+  if (e == cudaSuccess) e = mf::launch_peak_fp64(kind, out, blocks, iters / 16, st);
+  for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+    e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = mf::launch_peak_fp64(kind, out, blocks, iters, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (best == 0.f || ms < best)) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess) return set_error(MF_ERR_CUDA, std::string("peak probe: ") + cudaGetErrorString(e));
+  *tflops = best > 0.f ? mf::peak_fp64_flops(kind, blocks, iters) / (best * 1e-3) / 1e12 : 0.0;
+  return MF_OK;
 }
 
 }  // extern "C"

@@ -89,6 +89,11 @@ cudaError_t solve_kernels_init(int prec);
 cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStream_t st);
 cudaError_t launch_wait_probe(const int* flag, unsigned long long* status, int limit,
                               cudaStream_t st);
+// FP64 peak probes (diag.cu): kind 0 DFMA, 1 DMMA; out holds blocks x 256
+// doubles; peak_fp64_flops gives the flops of one launch
+cudaError_t launch_peak_fp64(int kind, double* out, int blocks, int64_t iters, cudaStream_t st);
+double peak_fp64_flops(int kind, int blocks, int64_t iters);
+int peak_fp64_blocks_per_sm(int kind);  // resident 256-thread blocks per SM
 
 // Y[i, r] = T(scale_r * B[perm[i], r]) with scale_r = inv_scale ? inv_scale[r] : 1.
 cudaError_t launch_perm_in(int prec, const double* B, int64_t ldb, const int32_t* perm,
