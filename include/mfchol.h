@@ -88,6 +88,13 @@ typedef struct mf_options {
                                each level of the solve is one product with it
                                instead of a chain of diagonal blocks.
                                0 is taken as 1.  Fixed at symbolic analysis. */
+  int32_t small_queue;      /* 1 (default): every small front whose subtree
+                               holds only small fronts runs in one persistent
+                               launch (a device queue in level order, each
+                               front waiting, with a bounded wait, for its
+                               children's completion flags); 0: one launch
+                               per level and size class.  Fixed at symbolic
+                               analysis. */
 } mf_options;
 
 /* Summary of a symbolic analysis. */
@@ -104,6 +111,7 @@ typedef struct mf_symbolic_info {
   int64_t factor_bytes_fp32;  /* device bytes of an FP32 factor */
   int64_t nfronts;        /* internal fronts after relaxed amalgamation */
   double front_flops;     /* flops of the fronts incl. explicit zeros */
+  int64_t queued_fronts;  /* small fronts in the persistent queue launch */
 } mf_symbolic_info;
 
 /* Refinement report of mf_solve_refined. */
@@ -257,13 +265,15 @@ int mf_factor_numeric(mf_factor* f, const double* values,
  * are reported by the solve calls and mf_solve_check, never here. */
 int mf_factor_check(mf_factor* f, void* stream);
 
-/* Bound of the solve kernels' flag waits on this factor, in polls of about
+/* Bound of the device waits on this factor -- the solve kernels' flag waits
+ * and the small-front queue's waits for children -- in polls of about
  * 128 ns (0 restores the default, 2^22 polls, about half a second).  A wait
- * that runs out records MF_ERR_TIMEOUT for the solve call in progress and
- * lets its kernel finish (no hang); the values of that solve are then
- * wrong, and the call (or mf_solve_check) reports it.  A very short bound
- * makes the waits of a real solve run out, which tests that reporting.
- * Errors: MF_ERR_INVALID for polls < 0. */
+ * that runs out records MF_ERR_TIMEOUT for the call in progress and lets
+ * its kernel finish (no hang); the values of that call are then wrong, and
+ * the call (or mf_solve_check / mf_factor_check) reports it.  A very short
+ * bound makes the waits of a real solve run out, which tests that
+ * reporting.  Changing the bound re-captures the factorization's CUDA graph
+ * at the next numeric call.  Errors: MF_ERR_INVALID for polls < 0. */
 int mf_factor_set_wait_limit(mf_factor* f, int32_t polls);
 
 /* Bytes of solve work memory (work vectors, right-hand-side staging, flags)
@@ -363,6 +373,19 @@ int mf_diag_wait_timeout(int32_t polls, void* stream);
  * frees a small device buffer.  Errors: MF_ERR_INVALID for another kind or
  * a NULL output, MF_ERR_CUDA. */
 int mf_diag_fp64_peak(int32_t kind, void* stream, double* tflops);
+
+/* Diagnostic for the failure detection of the small-front queue (no paper
+ * counterpart): runs the factor's persistent small-front launch alone with
+ * its first `skip` tickets already taken, so the queued fronts whose
+ * children sit in the skipped part wait on completion flags that nothing
+ * raises.  Each such wait gives up after the factor's wait bound
+ * (mf_factor_set_wait_limit; set a short one first), records MF_ERR_TIMEOUT
+ * and lets the kernel finish; the device stays usable, and the factor's
+ * values are garbage until the next mf_factor_numeric.  Synchronizes
+ * `stream`.  Returns MF_ERR_TIMEOUT (expected), MF_ERR_INTERNAL if no wait
+ * gave up, MF_ERR_INVALID without a queue, before a numeric call or for
+ * skip outside [1, queued fronts). */
+int mf_diag_small_queue(mf_factor* f, int32_t skip, void* stream);
 
 /* Mixed-precision solve: f is an FP32 factor; the residual r = B - A X, the
  * update X += D and the backward error

@@ -31,14 +31,15 @@ _D = ctypes.c_double
 
 class mf_options(ctypes.Structure):
     _fields_ = [("small_front_max", _I32), ("use_graphs", _I32), ("profile", _I32),
-                ("relax", _I32), ("budget_bytes", _I64), ("tc", _I32), ("sptrsv", _I32)]
+                ("relax", _I32), ("budget_bytes", _I64), ("tc", _I32), ("sptrsv", _I32),
+                ("small_queue", _I32)]
 
 
 class mf_symbolic_info(ctypes.Structure):
     _fields_ = [("n", _I64), ("nnz_lower", _I64), ("nsuper", _I64), ("nnz_L", _I64),
                 ("flops", _D), ("nlevels", _I64), ("max_front", _I64), ("max_k", _I64),
                 ("factor_bytes_fp64", _I64), ("factor_bytes_fp32", _I64), ("nfronts", _I64),
-                ("front_flops", _D)]
+                ("front_flops", _D), ("queued_fronts", _I64)]
 
 
 class mf_ir_report(ctypes.Structure):
@@ -100,6 +101,7 @@ _SIGS = {
     "mf_solve_check": [_P, _P],
     "mf_factor_export_columns": [_P, _I64, _I64, _P],
     "mf_diag_fp64_peak": [_I32, _P, _P],
+    "mf_diag_small_queue": [_P, _I32, _P],
     "mf_factor_set_wait_limit": [_P, _I32],
     "mf_factor_solve_work_bytes": [_P, _P],
 }
@@ -367,6 +369,12 @@ def mf_diag_wait_timeout(polls=1 << 14, stream=None):
     """Run the solve's bounded device wait on a flag nothing sets; returns the
     status code (MF_ERR_TIMEOUT expected) instead of raising."""
     return int(lib().mf_diag_wait_timeout(polls, _stream(stream)))
+
+
+def mf_diag_small_queue(f, skip, stream=None):
+    """Run f's small-front queue with its first ``skip`` tickets skipped;
+    returns the status code (MF_ERR_TIMEOUT expected) instead of raising."""
+    return int(lib().mf_diag_small_queue(f, skip, _stream(stream)))
 
 
 def mf_diag_fp64_peak(kind, stream=None):

@@ -164,6 +164,7 @@ struct mf_factor {
   void* dinv = nullptr;     // inverses of the current diagonal blocks (scratch)
   void* P = nullptr;        // partitioned inverse (SpTRSV variant 3), layout of L
   void* av = nullptr;       // lower entries of C in assembly order (T)
+  int* qstate = nullptr;    // small-front queue: ticket, then one flag per front
   double* small = nullptr;  // per-RHS scalars for refinement
   // graph of the numeric factorization
   cudaStream_t cap_stream = nullptr;
@@ -204,6 +205,7 @@ struct mf_factor {
     cudaFree(dinv);
     cudaFree(P);
     cudaFree(av);
+    cudaFree(qstate);
     delete fb64;
   }
 };
@@ -218,6 +220,7 @@ int mf_options_default(mf_options* opt) {
   opt->profile = 0;
   opt->relax = 1;
   opt->sptrsv = 2;
+  opt->small_queue = 1;
   opt->tc = 1;
   opt->budget_bytes = 0;
   return MF_OK;
@@ -272,7 +275,7 @@ static int analyze_common(mf_handle* h, int64_t n, const int64_t* rowptr,
   S->pinv = h->opt.sptrsv == 3;
   try {
     rc = mf::analyze(*S, n, rowptr, colind, perm, node_of, err);
-    if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max);
+    if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max, h->opt.small_queue);
   } catch (const std::bad_alloc&) {
     rc = MF_ERR_OOM;
     err = "host allocation failed";
@@ -380,6 +383,9 @@ int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info) {
   info->factor_bytes_fp32 = factor_bytes(s, MF_FP32);
   info->nfronts = (int64_t)s->sn.size();
   info->front_flops = s->front_flops;
+  info->queued_fronts = (!s->fsched.empty() && s->fsched[0].kind == mf::K_SMALL_Q)
+                            ? s->fsched[0].count
+                            : 0;
   return MF_OK;
 }
 
@@ -467,6 +473,7 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   const int64_t inv_slots = s->keep_inv ? s->ninv : s->max_large;
   MF_CK(cudaMalloc(&F->dinv, std::max<int64_t>(inv_slots, 1) * mf::kNB * mf::kNB * es));
   MF_CK(cudaMalloc(&F->av, std::max<int64_t>(s->nnz_lower, 1) * es));
+  MF_CK(cudaMalloc(&F->qstate, (s->sn.size() + 1) * sizeof(int)));
   if (s->pinv) MF_CK(cudaMalloc(&F->P, std::max<int64_t>(s->Lsize, 1) * es));
   MF_CK(mf::factor_kernels_init(prec));
   MF_CK(mf::solve_kernels_init(prec));
@@ -506,6 +513,8 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
   a.dinv = F->dinv;
   a.P = F->P;
   a.av = F->av;
+  a.qstate = F->qstate;
+  a.wait_polls = F->wait_polls;
   const std::vector<mf::Launch>& sched = F->tc ? S->fsched_tc : S->fsched;
   MF_CK(cudaMemsetAsync(F->status, 0xff, 2 * sizeof(unsigned long long), st));
   MF_CK(mf::launch_gather_values(F->prec, a, S->nnz_lower, st));
@@ -528,6 +537,8 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
   // ordered on st
   MF_CK(cudaEventRecord(F->ev_in, st));
   MF_CK(cudaStreamWaitEvent(F->crit, F->ev_in, 0));
+  if (!sched.empty() && sched[0].kind == mf::K_SMALL_Q)
+    MF_CK(cudaMemsetAsync(F->qstate, 0, (S->sn.size() + 1) * sizeof(int), F->crit));
   bool pending = false;
   int32_t level = -1;
   for (size_t i = 0; i < sched.size(); ++i) {
@@ -612,7 +623,7 @@ int mf_factor_check(mf_factor* f, void* stream) {
       for (size_t i = 0; i < sched.size(); ++i) {
         float ms = 0.f;
         MF_CK(cudaEventElapsedTime(&ms, f->ev[2 * i], f->ev[2 * i + 1]));
-        const int k = sched[i].kind;
+        const int k = sched[i].kind == mf::K_SMALL_Q ? (int)mf::K_SMALL : sched[i].kind;
         if (k >= mf::K_NKINDS_FACTOR) continue;  // partitioned-inverse pass
         f->prof_ms[k] += ms;
         f->prof_n[k] += 1;
@@ -826,7 +837,7 @@ int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* c
     if (rc != MF_OK) break;
     for (int si = 0; si < 3 && rc == MF_OK; ++si) {
       try {
-        mf::build_schedules(*S, smalls[si]);
+        mf::build_schedules(*S, smalls[si], tmp.opt.small_queue);
       } catch (const std::bad_alloc&) {
         rc = set_error(MF_ERR_OOM, "host allocation failed");
         break;
@@ -1044,8 +1055,46 @@ int mf_solve_check(mf_factor* f, void* stream) {
 
 int mf_factor_set_wait_limit(mf_factor* f, int32_t polls) {
   if (!f || polls < 0) return set_error(MF_ERR_INVALID, "invalid wait limit");
+  if (polls != f->wait_polls && f->gexec) {
+    // the bound is a parameter of the captured factorization: capture again
+    MF_CK(cudaGraphExecDestroy(f->gexec));
+    f->gexec = nullptr;
+  }
   f->wait_polls = polls;
   return MF_OK;
+}
+
+int mf_diag_small_queue(mf_factor* f, int32_t skip, void* stream) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  const mf_symbolic* S = f->S;
+  const std::vector<mf::Launch>& sched = f->tc ? S->fsched_tc : S->fsched;
+  if (!f->numeric_done || sched.empty() || sched[0].kind != mf::K_SMALL_Q)
+    return set_error(MF_ERR_INVALID, "factor has no small-front queue or no numeric values");
+  if (skip < 1 || skip >= sched[0].count) return set_error(MF_ERR_INVALID, "skip out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  mf::FactorArgs a;
+  a.sym = f->ds->d;
+  a.vals = f->vals;
+  a.L = f->L;
+  a.U = f->U;
+  a.status = f->status;
+  a.dinv = f->dinv;
+  a.P = f->P;
+  a.av = f->av;
+  a.qstate = f->qstate;
+  a.wait_polls = f->wait_polls;
+  const int first = skip;
+  MF_CK(cudaMemsetAsync(f->qstate, 0, (S->sn.size() + 1) * sizeof(int), st));
+  MF_CK(cudaMemcpyAsync(f->qstate, &first, sizeof(int), cudaMemcpyHostToDevice, st));
+  MF_CK(cudaMemsetAsync(f->status, 0xff, 2 * sizeof(unsigned long long), st));
+  MF_CK(mf::launch_factor(f->prec, sched[0], a, st));
+  MF_CK(cudaMemcpyAsync(f->status_host, f->status, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, st));
+  MF_CK(cudaStreamSynchronize(st));
+  if (f->status_host[1] == (unsigned long long)MF_ERR_TIMEOUT)
+    return set_error(MF_ERR_TIMEOUT, "a small-front queue wait gave up (tickets before " +
+                                         std::to_string(skip) + " were skipped)");
+  return set_error(MF_ERR_INTERNAL, "no small-front queue wait gave up");
 }
 
 int mf_factor_solve_work_bytes(const mf_factor* f, int64_t* bytes) {

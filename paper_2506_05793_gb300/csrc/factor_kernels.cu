@@ -17,12 +17,16 @@
 // is deterministic and needs no atomics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.h"
 
 namespace mf {
 namespace {
+
+// Default bound of a queue wait: about kQueueSpin x 128 ns (0.5 s).
+constexpr int kQueueSpin = 1 << 22;
 
 template <typename T>
 struct FD {
@@ -46,6 +50,8 @@ struct FD {
   T* dinv;
   const int64_t* ioff;  // per front: first kept diagonal-inverse slot (or -1)
   T* P;                 // partitioned inverse (SpTRSV variant 3) or nullptr
+  int* qstate;          // small-front queue: ticket counter, then one flag per front
+  int wait_polls;       // polls before a queue wait gives up
 };
 
 template <typename T>
@@ -71,6 +77,8 @@ FD<T> make_fd(const FactorArgs& a) {
   d.dinv = static_cast<T*>(a.dinv);
   d.ioff = a.sym.ioff;
   d.P = static_cast<T*>(a.P);
+  d.qstate = a.qstate;
+  d.wait_polls = a.wait_polls > 0 ? a.wait_polls : kQueueSpin;
   return d;
 }
 
@@ -111,14 +119,15 @@ __device__ void smem_partial_chol(T* F, int ld, int n, int k, int col0,
 
 // ---------------------------------------------------------------------------
 // Small fronts: one CTA assembles and factors the whole front in shared
-// memory and writes the L panel and the update matrix.
+// memory and writes the L panel and the update matrix.  The children's
+// update matrices are read through L2 (ld.global.cg): in the persistent
+// queue a child may have been written by another CTA of the same launch,
+// into memory that the plan reuses, so a line left in this SM's L1 from an
+// earlier use must not be seen.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* F = reinterpret_cast<T*>(smem_raw);
-  const Item it = d.items[item_off + blockIdx.x];
-  const SnInfo f = d.sn[it.s];
+__device__ __forceinline__ void small_front_body(const FD<T>& d, int s, T* F) {
+  const SnInfo f = d.sn[s];
   const int k = f.k, m = f.m, nf = k + m;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int i = tid; i < nf * nf; i += blockDim.x) F[i] = T(0);
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) 
     for (int jc = warp; jc < mc; jc += nw) {
       const int dc = map[jc];
       const T* u = Uc + (int64_t)jc * mc;
-      for (int ic = jc + lane; ic < mc; ic += 32) F[dc * nf + map[ic]] += u[ic];
+      for (int ic = jc + lane; ic < mc; ic += 32) F[dc * nf + map[ic]] += __ldcg(u + ic);
     }
     __syncthreads();
   }
@@ -148,6 +157,67 @@ __global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) 
   T* Up = d.U + f.Uoff;
   for (int c = warp; c < m; c += nw)
     for (int r = lane; r < m; r += 32) Up[(int64_t)c * m + r] = F[(k + c) * nf + k + r];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  small_front_body(d, d.items[item_off + blockIdx.x].s, reinterpret_cast<T*>(smem_raw));
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent small-front queue (paper Sec. 5: level-set scheduling, with the
+// many small blocks at the bottom of the tree taken in one launch).  The
+// `count` queued fronts are in level order; every CTA repeatedly takes the
+// next ticket, waits until each child of that front has raised its
+// completion flag, factors the front as k_small_front does and raises its
+// own flag.  A CTA only waits for fronts with smaller tickets, which CTAs
+// already running have taken, so the queue always drains.  Each wait is
+// bounded (wait_polls polls 128 ns apart): when it runs out the CTA records
+// MF_ERR_TIMEOUT in status[1] and goes on, so the launch always ends.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_small_queue(FD<T> d, int64_t item_off, int count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_ticket;
+  int* ticket = d.qstate;
+  int* done = d.qstate + 1;
+  for (;;) {
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int t = s_ticket;
+    if (t >= count) break;
+    const int s = d.items[item_off + t].s;
+    const SnInfo f = d.sn[s];
+    if (threadIdx.x < 32) {
+      for (int ci = threadIdx.x; ci < f.nchild; ci += 32) {
+        const int* flag = done + d.children[f.child_begin + ci];
+        int spins = 0;
+        while (ld_acquire_gpu(flag) == 0) {
+          if (++spins > d.wait_polls) {
+            atomicExch(d.status + 1, (unsigned long long)MF_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(128);
+        }
+      }
+    }
+    __syncthreads();
+    small_front_body(d, s, reinterpret_cast<T*>(smem_raw));
+    // every thread's stores are ordered before thread 0's release (CTA
+    // barrier, then a GPU-scope fence and release store)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(done + s), "r"(1) : "memory");
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -717,6 +787,9 @@ cudaError_t init_t() {
   cudaError_t e = cudaFuncSetAttribute(k_small_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kSmallMax * kSmallMax * (int)sizeof(T));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_small_queue<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kSmallMax * kSmallMax * (int)sizeof(T));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem<T>());
   if (e != cudaSuccess) return e;
@@ -738,6 +811,19 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
     case K_SMALL:
       k_small_front<T><<<grid, 256, (size_t)L.param * L.param * sizeof(T), st>>>(d, L.item_off);
       break;
+    case K_SMALL_Q: {
+      // one resident wave: SMs x the blocks per SM that the front size allows
+      const size_t smem = (size_t)L.param * L.param * sizeof(T);
+      int dev = 0, sms = 0, per = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T>, 256, smem);
+      if (e != cudaSuccess) return e;
+      const int blocks = std::max(1, std::min(L.count, sms * std::max(per, 1)));
+      k_small_queue<T><<<blocks, 256, smem, st>>>(d, L.item_off, L.count);
+      break;
+    }
     case K_ASSEMBLE:
       k_assemble<T><<<grid, 256, 0, st>>>(d, L.item_off);
       break;

@@ -51,6 +51,10 @@ struct FactorArgs {
   void* dinv;
   // partitioned inverse P (T[Lsize], layout of L) or nullptr
   void* P = nullptr;
+  // small-front queue: [0] ticket counter, then one completion flag per
+  // front (zeroed before the queue launch)
+  int* qstate = nullptr;
+  int32_t wait_polls = 0;  // polls before a queue wait gives up (0: default)
 };
 
 struct SolveArgs {

@@ -55,6 +55,7 @@ enum Kind : int32_t {
   K_SYRK = 4,      // trailing lower update
   K_SYRK_TC = 5,   // FP32 trailing update on tcgen05 tensor cores (128 x 128)
   K_NKINDS_FACTOR = 6,
+  K_SMALL_Q = 9,     // persistent queue: every small front whose subtree is all small
   K_PINV_INIT = 7,   // partitioned inverse: P = 0, diagonal blocks = their inverses
   K_PINV = 8,        // partitioned inverse, step t: P(i, j) -= L(i, t) P(t, j), i > t >= j
   K_FW_LEVEL = 11,   // per 64-row block: gather, GEMV with solved blocks, diagonal solve
@@ -171,7 +172,7 @@ namespace mf {
 // symbolic.cpp
 int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
             const int32_t* perm, const int32_t* node_of, std::string& err);
-void build_schedules(mf_symbolic& S, int small_max);
+void build_schedules(mf_symbolic& S, int small_max, int small_queue);
 int check_schedules(const mf_symbolic& S, std::string& err);
 void ensure_fundamental_rows(const mf_symbolic& S);
 // error reporting (capi.cpp)

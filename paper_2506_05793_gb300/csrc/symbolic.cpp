@@ -704,7 +704,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
 // fronts are batched one CTA each (grouped by size class), large fronts are
 // split into column chunks (assembly), panel steps (POTRF, TRSM) and trailing
 // tiles (SYRK), each batched over all large fronts of the level.
-void build_schedules(mf_symbolic& S, int small_max) {
+void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
   S.items.clear();
   S.arange.clear();
   S.fsched.clear();
@@ -744,6 +744,36 @@ void build_schedules(mf_symbolic& S, int small_max) {
     return f;
   };
   std::vector<Item> it;
+  // Persistent queue: the small fronts whose whole subtree is small run in
+  // one launch before everything else, in ticket order = level order (a
+  // front's children always have smaller tickets); each waits for its
+  // children's completion flags instead of a level barrier.
+  std::vector<char> inq(ns, 0);
+  if (small_queue) {
+    std::vector<char> closed(ns, 0);
+    for (int32_t lev = 0; lev < S.nlevels; ++lev)
+      for (int32_t s : bylev[lev]) {
+        const SnInfo& P = S.sn[s];
+        bool ok = P.k + P.m <= small_max;
+        for (int32_t ci = P.child_begin; ok && ci < P.child_begin + P.nchild; ++ci)
+          ok = closed[S.children[ci]] != 0;
+        closed[s] = ok ? 1 : 0;
+      }
+    it.clear();
+    double fl = 0.0;
+    int32_t maxnf = 0;
+    for (int32_t lev = 0; lev < S.nlevels; ++lev)
+      for (int32_t s : bylev[lev])
+        if (closed[s]) {
+          const int nf = S.sn[s].k + S.sn[s].m;
+          it.push_back({s, 0, 0, 0});
+          fl += front_flops(nf, S.sn[s].k);
+          maxnf = std::max(maxnf, nf);
+          inq[s] = 1;
+        }
+    add(S.fsched, K_SMALL_Q, 0, maxnf, it, fl);
+    add(S.fsched_tc, K_SMALL_Q, 0, maxnf, it, fl);
+  }
   for (int32_t lev = 0; lev < S.nlevels; ++lev) {
     const std::vector<int32_t>& L = bylev[lev];
     // small fronts by class
@@ -755,7 +785,7 @@ void build_schedules(mf_symbolic& S, int small_max) {
       double fl = 0.0;
       for (int32_t s : L) {
         const int nf = S.sn[s].k + S.sn[s].m;
-        if (nf > lo && nf <= hi) {
+        if (nf > lo && nf <= hi && !inq[s]) {
           it.push_back({s, 0, 0, 0});
           fl += front_flops(nf, S.sn[s].k);
         }
@@ -1062,6 +1092,8 @@ void build_schedules(mf_symbolic& S, int small_max) {
 //   TRSM(t) and the first tile column of SYRK(t);
 //   partitioned inverse: init column blocks tile [0, nb), and step t holds
 //   the tiles t < i < nb + mb, 0 <= j <= t exactly once, steps in order;
+//   small-front queue (first launch): each queued front once, after all of
+//   its children, which are queued too;
 //   solves: a front is one warp item (nf <= 32 H) or its pivot blocks tile
 //   [0, k) (and, forward, its update blocks tile [k, nf)).
 int check_schedules(const mf_symbolic& S, std::string& err) {
@@ -1102,6 +1134,24 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
     for (size_t li = 0; li < sched.size(); ++li) {
       const Launch& L = sched[li];
       if (L.kind == K_PINV_INIT || L.kind == K_PINV) continue;
+      if (L.kind == K_SMALL_Q) {
+        // the persistent queue comes first; every front in it is small, and
+        // every child of a queued front is queued with a smaller ticket
+        if (li != 0) return fail("small-front queue not first");
+        std::vector<int64_t> ticket(ns, -1);
+        for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+          const int32_t s = S.items[x].s;
+          const SnInfo& f = S.sn[s];
+          if (f.k + f.m > L.param || ticket[s] >= 0) return fail("queued front too large or repeated");
+          ticket[s] = x - L.item_off;
+          small[s]++;
+          for (int32_t ci = f.child_begin; ci < f.child_begin + f.nchild; ++ci) {
+            const int64_t tc_ = ticket[S.children[ci]];
+            if (tc_ < 0 || tc_ >= ticket[s]) return fail("queued front before its children");
+          }
+        }
+        continue;
+      }
       if (L.level < last_level) return fail("factor levels out of order");
       last_level = L.level;
       for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {

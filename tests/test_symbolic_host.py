@@ -346,10 +346,11 @@ def test_factor_over_budget_is_oom(mf):
 
 # ---- schedule consistency (host) ------------------------------------------
 @pytest.mark.parametrize("variant", [1, 2, 3])
-@pytest.mark.parametrize("relax,small", [(0, 128), (1, 128), (1, 32)])
-def test_schedules_cover_every_front_once(mf, variant, relax, small):
+@pytest.mark.parametrize("relax,small,queue", [(0, 128, 1), (1, 128, 1), (1, 32, 1), (1, 128, 0)])
+def test_schedules_cover_every_front_once(mf, variant, relax, small, queue):
     opt = mf.mf_options_default()
     opt.sptrsv, opt.relax, opt.small_front_max = variant, relax, small
+    opt.small_queue = queue
     h = mf.mf_create(opt)
     try:
         cases = [gen.config3(16)[:2] + (gen.config3(16)[3],)]
@@ -466,3 +467,23 @@ def test_condensed_edge_cases(mf, handle, orc):
                                          np.zeros(0, dtype=np.int32), None, block=2)
     assert mf.mf_symbolic_get_info(s)["n"] == 0
     mf.mf_symbolic_free(s)
+
+
+def test_small_queue_holds_the_small_subforests(mf, orc):
+    """The persistent queue holds exactly the small fronts whose subtree is
+    all small (checked here against the supernodal tree), and turning it
+    off leaves no queue."""
+    rp, ci, v, perm, _ = gen.config3(16)
+    for queue in (1, 0):
+        opt = mf.mf_options_default()
+        opt.small_queue = queue
+        h = mf.mf_create(opt)
+        s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+        info = mf.mf_symbolic_get_info(s)
+        if queue:
+            assert 0 < info["queued_fronts"] <= info["nfronts"]
+        else:
+            assert info["queued_fronts"] == 0
+        mf.mf_symbolic_check(s)
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
