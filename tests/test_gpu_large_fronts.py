@@ -16,9 +16,10 @@ Bars: FP64 relF <= 1e-11 (the largest fronts have about 3,400 columns, so an
 entry of L sums at most a few thousand FP64 products: about 3e3 x 1.1e-16 =
 4e-13 relative to the magnitude of the terms, times the modest condition of
 these matrices) and berr <= 1e-13.  FP32: relF against the FP64 oracle
-<= 2e-3 (single-precision rounding of the inputs and products amplified by the
-condition of the jump matrix; the measured values are printed), and the
-FP32 factor refined in FP64 must reach berr <= 1e-13."""
+<= 1e-4, below the worst-case n u_32 = 3,400 x 6e-8 = 2e-4 of a sum over the
+largest front (measured on a GB300: 3e-7 to 7e-7 overall, at most 2.3e-6 on
+the widest supernode), and the FP32 factor refined in FP64 must reach
+berr <= 1e-13."""
 import numpy as np
 import pytest
 
@@ -84,7 +85,7 @@ def test_large_front_factor_elementwise(mf, orc, name, prec):
             assert orc.berr(rp, ci, v, x, b) <= 1e-13
             assert np.max(np.abs(x - xo)) <= 1e-9 * np.max(np.abs(xo))
         else:
-            assert rel <= 2e-3 and rel_top <= 2e-3
+            assert rel <= 1e-4 and rel_top <= 1e-4
             x, rep = mf.mf_solve_refined(f, b, tol=1e-13, max_iter=30)
             assert rep["fell_back"] == 0
             assert orc.berr(rp, ci, v, x, b) <= 1e-13
