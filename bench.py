@@ -73,10 +73,11 @@ def parse():
                    help="pick relaxation / small-front limit / tensor cores with mf_autotune first")
     p.add_argument("--count", type=int, default=512, help="batch: number of boxes")
     p.add_argument("--nrhs", type=int, default=1, help="right-hand sides per solve")
-    p.add_argument("--sptrsv", type=int, default=2, choices=[1, 2, 3],
+    p.add_argument("--sptrsv", type=int, default=2, choices=[1, 2, 3, 4],
                    help="pivot-block solve: 1 substitution, 2 stored diagonal-block inverses, "
                         "3 partitioned inverse (one product per level; computed inside the "
-                        "timed factorization)")
+                        "timed factorization), 4 partitioned inverse of every front as one "
+                        "sparse product per level and sweep")
     p.add_argument("--serve-rates", default="25,100,400",
                    help="serve: Poisson arrival rates (requests/s) to sweep")
     p.add_argument("--serve-requests", type=int, default=240, help="serve: requests per rate")

@@ -86,8 +86,15 @@ typedef struct mf_options {
                                as much memory again as those fronts' L and
                                about (k^3/3 + m k^2) more flops per front), and
                                each level of the solve is one product with it
-                               instead of a chain of diagonal blocks.
-                               0 is taken as 1.  Fixed at symbolic analysis. */
+                               instead of a chain of diagonal blocks;
+                               4 = the level's partitioned inverse as one
+                               sparse matrix per level and sweep: every front
+                               (small ones too) stores P and its transpose
+                               (about twice the memory of L), and the solve is
+                               one product per level and sweep on the global
+                               vector, with no front work vectors and no
+                               waits.  0 is taken as 1.  Fixed at symbolic
+                               analysis. */
   int32_t small_queue;      /* 1 (default): every small front whose subtree
                                holds only small fronts runs in one persistent
                                launch (a device queue in level order, each

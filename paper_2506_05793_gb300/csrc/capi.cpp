@@ -93,6 +93,7 @@ int get_devsym(const mf_symbolic* S, std::shared_ptr<DevSymOwner>& out) {
   MF_CK(o->up(&o->d.perm, S->perm));
   MF_CK(o->up(&o->d.rowptr, S->rowptr));
   MF_CK(o->up(&o->d.colind, S->colind));
+  MF_CK(o->up(&o->d.v4grp, S->v4_grp));
   S->dev = o;
   S->dev_device = dev;
   out = o;
@@ -120,7 +121,7 @@ constexpr int kStatusSolve = 2;  // the solve's timeout record
 // staging rows (two panels of 64 hi + 64 lo floats per row).
 int64_t factor_bytes(const mf_symbolic* S, int prec) {
   const int64_t inv_slots = S->keep_inv ? S->ninv : S->max_large;
-  return (S->Lsize * (S->pinv ? 2 : 1) + S->Usize + inv_slots * mf::kNB * mf::kNB +
+  return (S->Lsize * (S->v4 ? 3 : S->pinv ? 2 : 1) + S->Usize + inv_slots * mf::kNB * mf::kNB +
           S->nnz_lower) *
              (int64_t)elem_size(prec) +
          S->nnzA * (int64_t)sizeof(double) +
@@ -162,7 +163,8 @@ struct mf_factor {
   cudaStream_t crit = nullptr, side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_side = nullptr, ev_in = nullptr, ev_out = nullptr;
   void* dinv = nullptr;     // inverses of the current diagonal blocks (scratch)
-  void* P = nullptr;        // partitioned inverse (SpTRSV variant 3), layout of L
+  void* P = nullptr;        // partitioned inverse (SpTRSV variants 3, 4), layout of L
+  void* PT = nullptr;       // variant 4: P transposed front by front
   void* av = nullptr;       // lower entries of C in assembly order (T)
   int* qstate = nullptr;    // small-front queue: ticket, then one flag per front
   double* small = nullptr;  // per-RHS scalars for refinement
@@ -204,6 +206,7 @@ struct mf_factor {
     if (crit) cudaStreamDestroy(crit);
     cudaFree(dinv);
     cudaFree(P);
+    cudaFree(PT);
     cudaFree(av);
     cudaFree(qstate);
     delete fb64;
@@ -235,9 +238,9 @@ int mf_create(mf_handle** h, const mf_options* opt) {
   if (H->opt.small_front_max <= 0 || H->opt.small_front_max > mf::kSmallMax)
     H->opt.small_front_max = mf::kSmallMax;
   if (H->opt.sptrsv == 0) H->opt.sptrsv = 1;  // zero-filled options: substitution
-  if (H->opt.sptrsv < 1 || H->opt.sptrsv > 3) {
+  if (H->opt.sptrsv < 1 || H->opt.sptrsv > 4) {
     delete H;
-    return set_error(MF_ERR_INVALID, "sptrsv must be 1, 2 or 3");
+    return set_error(MF_ERR_INVALID, "sptrsv must be 1, 2, 3 or 4");
   }
   // The symbolic phase is host-only, so a handle is usable without a GPU;
   // device calls report MF_ERR_CUDA later if no device is present.
@@ -272,7 +275,8 @@ static int analyze_common(mf_handle* h, int64_t n, const int64_t* rowptr,
   int rc;
   S->relax = h->opt.relax ? 1 : 0;
   S->keep_inv = h->opt.sptrsv >= 2;
-  S->pinv = h->opt.sptrsv == 3;
+  S->pinv = h->opt.sptrsv >= 3;
+  S->v4 = h->opt.sptrsv == 4;
   try {
     rc = mf::analyze(*S, n, rowptr, colind, perm, node_of, err);
     if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max, h->opt.small_queue);
@@ -475,6 +479,7 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   MF_CK(cudaMalloc(&F->av, std::max<int64_t>(s->nnz_lower, 1) * es));
   MF_CK(cudaMalloc(&F->qstate, (s->sn.size() + 1) * sizeof(int)));
   if (s->pinv) MF_CK(cudaMalloc(&F->P, std::max<int64_t>(s->Lsize, 1) * es));
+  if (s->v4) MF_CK(cudaMalloc(&F->PT, std::max<int64_t>(s->Lsize, 1) * es));
   MF_CK(mf::factor_kernels_init(prec));
   MF_CK(mf::solve_kernels_init(prec));
   if (prec == MF_FP32 && h->opt.tc) {
@@ -512,6 +517,7 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
   a.split_map_b = F->tc ? F->split_map_b : nullptr;
   a.dinv = F->dinv;
   a.P = F->P;
+  a.PT = F->PT;
   a.av = F->av;
   a.qstate = F->qstate;
   a.wait_polls = F->wait_polls;
@@ -914,6 +920,7 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.nblk = S->blkoff.back();
   a.dinv = S->keep_inv ? f->dinv : nullptr;
   a.P = f->P;
+  a.PT = f->PT;
   for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, X, ldx, S->n, cn, scale, accumulate, st));

@@ -49,7 +49,8 @@ struct FD {
   float* split_b;  // staging area 1: rows of 512 floats (four slots, lookahead levels)
   T* dinv;
   const int64_t* ioff;  // per front: first kept diagonal-inverse slot (or -1)
-  T* P;                 // partitioned inverse (SpTRSV variant 3) or nullptr
+  T* P;                 // partitioned inverse (SpTRSV variants 3, 4) or nullptr
+  T* PT;                // variant 4: P transposed per front (k x nf, ld k) or nullptr
   int* qstate;          // small-front queue: ticket counter, then one flag per front
   int wait_polls;       // polls before a queue wait gives up
 };
@@ -77,6 +78,7 @@ FD<T> make_fd(const FactorArgs& a) {
   d.dinv = static_cast<T*>(a.dinv);
   d.ioff = a.sym.ioff;
   d.P = static_cast<T*>(a.P);
+  d.PT = static_cast<T*>(a.PT);
   d.qstate = a.qstate;
   d.wait_polls = a.wait_polls > 0 ? a.wait_polls : kQueueSpin;
   return d;
@@ -769,6 +771,77 @@ __global__ void __launch_bounds__(256) k_pinv_step(FD<T> d, int64_t item_off) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// SpTRSV variant 4 (Sec. 5): the partitioned inverse of every front, then
+// its transpose.  k_pinv_small takes a front without kept diagonal-block
+// inverses (k + m <= 128) in one CTA: with L11 and L21 in shared memory
+// (L11 and Z packed by rows), thread c solves L11 z = e_c by substitution
+// into column c of Z = L11^{-1}, then P = [Z; -L21 Z] is written in the
+// layout of L (zero above the diagonal of Z).
+// ---------------------------------------------------------------------------
+template <typename T>
+constexpr size_t pinv_small_smem() {
+  return (size_t)kSmallMax * (kSmallMax + 1) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pinv_small(FD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SnInfo f = d.sn[d.items[item_off + blockIdx.x].s];
+  const int k = f.k, m = f.m, nf = k + m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int np = k * (k + 1) / 2;
+  T* Ls = reinterpret_cast<T*>(smem_raw);  // L11 packed by rows: (i, c) at i(i+1)/2 + c
+  T* Zs = Ls + np;                         // Z packed the same way
+  T* Ws = Zs + np;                         // L21: (r, p) at p m + r
+  const T* Lp = d.L + f.Loff;
+  T* Pp = d.P + f.Loff;
+  for (int c = warp; c < k; c += nw) {
+    for (int i = c + lane; i < k; i += 32) Ls[i * (i + 1) / 2 + c] = Lp[(int64_t)c * nf + i];
+    for (int r = lane; r < m; r += 32) Ws[c * m + r] = Lp[(int64_t)c * nf + k + r];
+  }
+  __syncthreads();
+  for (int c = tid; c < k; c += blockDim.x)
+    for (int i = c; i < k; ++i) {
+      const T* li = Ls + i * (i + 1) / 2;
+      T acc = i == c ? T(1) : T(0);
+      for (int q = c; q < i; ++q) acc -= li[q] * Zs[q * (q + 1) / 2 + c];
+      Zs[i * (i + 1) / 2 + c] = acc / li[i];
+    }
+  __syncthreads();
+  for (int c = warp; c < k; c += nw) {
+    T* pc = Pp + (int64_t)c * nf;
+    for (int i = lane; i < k; i += 32) pc[i] = i >= c ? Zs[i * (i + 1) / 2 + c] : T(0);
+    for (int r = lane; r < m; r += 32) {
+      T acc = T(0);
+      for (int q = c; q < k; ++q) acc += Ws[q * m + r] * Zs[q * (q + 1) / 2 + c];
+      pc[k + r] = -acc;
+    }
+  }
+}
+
+// PT = P^T front by front (64 x 64 tiles through shared memory): row i of
+// P_s becomes the k contiguous values PT[Loff + i k ...], so the forward
+// products read each row of P with unit stride.  Item (s, 0, i0, j0).
+template <typename T>
+__global__ void __launch_bounds__(256) k_pt(FD<T> d, int64_t item_off) {
+  __shared__ T tile[kNB][kNB + 1];
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m, i0 = it.a, j0 = it.b;
+  const T* Pp = d.P + f.Loff;
+  T* Q = d.PT + f.Loff;
+  for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, r = idx % kNB;
+    if (i0 + r < nf && j0 + c < k) tile[c][r] = Pp[(int64_t)(j0 + c) * nf + i0 + r];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+    const int r = idx / kNB, c = idx % kNB;
+    if (i0 + r < nf && j0 + c < k) Q[(int64_t)(i0 + r) * k + j0 + c] = tile[c][r];
+  }
+}
+
 // av[e] = T(sum of the CSR values of lower entry e): one pass per numeric
 // call, so the assembly kernels read values in their own order.
 template <typename T>
@@ -798,6 +871,9 @@ cudaError_t init_t() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_pinv_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)pinv_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pinv_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)pinv_small_smem<T>());
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)syrk_smem<T>());
@@ -843,6 +919,12 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
       break;
     case K_PINV:
       k_pinv_step<T><<<grid, 256, pinv_smem<T>(), st>>>(d, L.item_off);
+      break;
+    case K_PINV_SMALL:
+      k_pinv_small<T><<<grid, 256, pinv_small_smem<T>(), st>>>(d, L.item_off);
+      break;
+    case K_PT:
+      k_pt<T><<<grid, 256, 0, st>>>(d, L.item_off);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -29,6 +29,7 @@ struct DevSym {
   int32_t* perm = nullptr;     // perm[new] = old
   int64_t* rowptr = nullptr;   // A (original order) for the FP64 residual
   int32_t* colind = nullptr;
+  Item* v4grp = nullptr;       // variant 4: forward row groups (front, front row)
 };
 
 struct FactorArgs {
@@ -51,6 +52,7 @@ struct FactorArgs {
   void* dinv;
   // partitioned inverse P (T[Lsize], layout of L) or nullptr
   void* P = nullptr;
+  void* PT = nullptr;  // variant 4: P transposed per front (k x nf, ld k) or nullptr
   // small-front queue: [0] ticket counter, then one completion flag per
   // front (zeroed before the queue launch)
   int* qstate = nullptr;
@@ -69,8 +71,9 @@ struct SolveArgs {
   // diagonal-block inverses of the large fronts (slots sym.ioff), or nullptr
   // to solve the pivot blocks by substitution
   const void* dinv = nullptr;
-  // partitioned inverse (SpTRSV variant 3), T[Lsize], or nullptr
+  // partitioned inverse (SpTRSV variants 3, 4), T[Lsize], or nullptr
   const void* P = nullptr;
+  const void* PT = nullptr;  // variant 4: P transposed per front
   int64_t n;
   int32_t nrhs;
   int32_t nlevels;

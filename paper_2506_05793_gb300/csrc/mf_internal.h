@@ -68,6 +68,10 @@ enum Kind : int32_t {
   K_FW_PINV = 18,    // variant 3: rows of P times w (x for pivot rows, w update below)
   K_BW_PCOPY = 19,   // variant 3: stage the forward result y of the pivot rows
   K_BW_PINV = 20,    // variant 3: x(cols) = P^T [y; x of the update rows]
+  K_PINV_SMALL = 21, // variant 4: partitioned inverse of a front without kept inverses (one CTA)
+  K_PT = 22,         // variant 4: PT = P^T per front (64 x 64 tiles)
+  K_V4_FW = 23,      // variant 4, forward: one warp per row of the level's matrix
+  K_V4_BW = 24,      // variant 4, backward: one warp per pivot column
 };
 
 struct Launch {
@@ -150,6 +154,10 @@ struct mf_symbolic {
   // factorization (pinv_flops of extra work)
   bool pinv = false;
   double pinv_flops = 0.0;
+  // SpTRSV variant 4: per-level sparse products (groups (front, front row)
+  // of the forward rows, in the order of the forward items)
+  bool v4 = false;
+  std::vector<mf::Item> v4_grp;
   std::vector<mf::Item> arange;       // assembly: (child, lo, hi, 0) lists per chunk
   std::vector<mf::Launch> fwsched, bwsched;
   std::vector<int32_t> blkoff;     // per front: first 64-column block index

@@ -42,7 +42,9 @@ struct SD {
   const int64_t* ginv_src;
   const T* dinv;         // diagonal-block inverses (SpTRSV variant 2) or nullptr
   const int64_t* ioff;   // per front: first inverse slot, -1 if none
-  const T* P;            // partitioned inverse (SpTRSV variant 3) or nullptr
+  const T* P;            // partitioned inverse (SpTRSV variants 3, 4) or nullptr
+  const T* PT;           // variant 4: P transposed per front or nullptr
+  const Item* v4grp;     // variant 4: forward row groups (front, front row)
   unsigned long long* status;  // the solve's timeout record (one word)
   int64_t n;
   int nrhs;
@@ -66,6 +68,8 @@ SD<T> make_sd(const SolveArgs& a) {
   d.dinv = static_cast<const T*>(a.dinv);
   d.ioff = a.sym.ioff;
   d.P = static_cast<const T*>(a.P);
+  d.PT = static_cast<const T*>(a.PT);
+  d.v4grp = a.sym.v4grp;
   d.status = a.status;
   d.n = a.n;
   d.nrhs = a.nrhs;
@@ -1305,6 +1309,95 @@ __global__ void __launch_bounds__(256, 2) k_bw_warp(SD<T> d, int64_t item_off, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// SpTRSV variant 4 (Sec. 5): one sparse product per level and sweep with the
+// level's partitioned inverse, on the permuted global vectors: Y holds the
+// right-hand side and receives the forward additions, then the solution;
+// F (the first n x nrhs values of W) the forward results of the pivot rows.
+// Nothing waits: a level reads only rows that earlier levels finished.
+// Forward, one warp per row of the level's matrix (item: row, first group,
+// end group, pivot?): sum over its groups (front s, front row i) of row i of
+// P_s (contiguous in PT) times y at the front's pivot columns; a pivot row
+// stores the sum in F, an update row adds it to Y.
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+__device__ __forceinline__ void warp_reduce_r(T (&acc)[R]) {
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) acc[rr] = warp_sum(acc[rr]);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_v4_fw(SD<T> d, int64_t item_off, int count) {
+  const int w = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= count) return;
+  const Item it = d.items[item_off + w];
+  const int nr = d.nrhs;
+  T acc[R];
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
+  for (int g = it.t; g < it.a; ++g) {
+    const Item gr = d.v4grp[g];
+    const SnInfo f = d.sn[gr.s];
+    const int len = gr.t < f.k ? gr.t + 1 : f.k;
+    const T* pv = d.PT + f.Loff + (int64_t)gr.t * f.k;
+    const T* y = d.Y + f.first;
+    for (int c = lane; c < len; c += 32) {
+      const T v = pv[c];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr)
+        if (rr < nr) acc[rr] = fma(v, y[c + (int64_t)rr * d.n], acc[rr]);
+    }
+  }
+  warp_reduce_r<T, R>(acc);
+  if (lane == 0) {
+    const int64_t r = it.s;
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (rr < nr) {
+        if (it.b) d.W[r + rr * d.n] = acc[rr];
+        else d.Y[r + rr * d.n] += acc[rr];
+      }
+  }
+}
+
+// Backward, one warp per pivot column c of a front s of the level (item:
+// s, c): x(first_s + c) = sum over the front rows i >= c of P_s(i, c) times
+// F (pivot rows) or the final x (update rows, finished by earlier levels).
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_v4_bw(SD<T> d, int64_t item_off, int count) {
+  const int w = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= count) return;
+  const Item it = d.items[item_off + w];
+  const SnInfo f = d.sn[it.s];
+  const int c = it.t, k = f.k, nf = k + f.m, nr = d.nrhs;
+  const T* pc = d.P + f.Loff + (int64_t)c * nf;
+  const int32_t* rows = d.rowidx + f.rows_off;
+  T acc[R];
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
+  for (int i = c + lane; i < nf; i += 32) {
+    const T v = pc[i];
+    const T* src = i < k ? d.W + f.first + i : d.Y + rows[i];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (rr < nr) acc[rr] = fma(v, src[(int64_t)rr * d.n], acc[rr]);
+  }
+  warp_reduce_r<T, R>(acc);
+  if (lane == 0) {
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr)
+      if (rr < nr) d.Y[f.first + c + (int64_t)rr * d.n] = acc[rr];
+  }
+}
+
+template <typename T, int R>
+void launch_v4(const Launch& L, const SolveArgs& a, cudaStream_t st) {
+  const SD<T> d = make_sd<T>(a);
+  const int blocks = (int)((L.count + 7) / 8);
+  if (L.kind == K_V4_FW) k_v4_fw<T, R><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+  else k_v4_bw<T, R><<<blocks, 256, 0, st>>>(d, L.item_off, L.count);
+}
+
 // Diagnostic: the solve's bounded wait on a flag that nothing sets.  Gives
 // up after `limit` polls and records MF_ERR_TIMEOUT in *status.
 __global__ void k_wait_probe(const int* flag, unsigned long long* status, int limit) {
@@ -1499,6 +1592,13 @@ cudaError_t launch_t(const Launch& L, const SolveArgs& a, cudaStream_t st) {
       case 16: launch_warp<T, 16>(fw, L, a, st); break;
       default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+  }
+  if (L.kind == K_V4_FW || L.kind == K_V4_BW) {
+    if (a.nrhs <= 1) launch_v4<T, 1>(L, a, st);
+    else if (a.nrhs <= 4) launch_v4<T, 4>(L, a, st);
+    else if (a.nrhs <= 8) launch_v4<T, 8>(L, a, st);
+    else launch_v4<T, kSolveChunk>(L, a, st);
     return cudaGetLastError();
   }
   if (L.kind == K_FW_PGATHER || L.kind == K_BW_PCOPY) {

@@ -236,13 +236,26 @@ int condensed_structure(int64_t n, const int32_t* node_of, const std::vector<int
 }  // namespace
 
 // Device memory of the update matrices.  U_s is written when front s is
-// factored (level(s)) and read when its parent is assembled
-// (level(parent(s))); after that level it is dead.  Blocks are placed best fit
-// in a simulated heap, level by level (free blocks indexed by offset for
-// coalescing and by size for the fit), so chains of thin fronts reuse the same
-// memory instead of holding every update matrix at once.  Returns the peak
-// size (elements) and sets Uoff for every front.
-int64_t plan_update_memory(mf_symbolic& S) {
+// factored and read when its parent is assembled; after that it is dead.
+//
+// Fronts in the persistent small-front queue (inq) run first, in any order
+// that respects the tree, several at once: a block may only be reused by a
+// front that is certain to start after the block's reader finished, i.e. by
+// the reader itself or one of its ancestors.  So the queued part is planned
+// subtree by subtree: every queued front inherits, as its pool, the free
+// ranges of its children's pools plus the children's update matrices (which
+// it reads before it writes its own), takes its own block from the pool
+// (best fit) or from new memory at the top, and passes the rest on.  After
+// the queue, the pools of its top fronts are free.
+//
+// The other fronts run level by level (every launch of a level completes
+// before the next level starts): blocks are placed best fit in a simulated
+// heap, level by level (free blocks indexed by offset for coalescing and by
+// size for the fit), and a block read at level l is free from level l + 1.
+// Chains of thin fronts reuse the same memory instead of holding every
+// update matrix at once.  Returns the peak size (elements) and sets Uoff for
+// every front.
+int64_t plan_update_memory(mf_symbolic& S, const std::vector<char>& inq) {
   const int64_t ns = (int64_t)S.sn.size();
   std::vector<std::vector<int32_t>> bylev(S.nlevels);
   for (int64_t s = 0; s < ns; ++s) bylev[S.slevel[s]].push_back((int32_t)s);
@@ -250,41 +263,98 @@ int64_t plan_update_memory(mf_symbolic& S) {
   std::set<std::pair<int64_t, int64_t>> by_size;   // (size, offset)
   auto erase_size = [&](int64_t size, int64_t off) { by_size.erase({size, off}); };
   std::vector<std::vector<std::pair<int64_t, int64_t>>> release(S.nlevels + 1);
+  // 32-element alignment keeps every update matrix 128/256-byte aligned
+  auto usize = [&](int64_t s) -> int64_t {
+    const SnInfo& I = S.sn[s];
+    return I.parent < 0 ? 0 : (((int64_t)I.m * I.m) + 31) / 32 * 32;
+  };
+  auto free_block = [&](int64_t off, int64_t size) {
+    auto nx = by_off.lower_bound(off);
+    if (nx != by_off.end() && off + size == nx->first) {
+      size += nx->second;
+      erase_size(nx->second, nx->first);
+      nx = by_off.erase(nx);
+    }
+    if (nx != by_off.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        off = pv->first;
+        size += pv->second;
+        erase_size(pv->second, pv->first);
+        by_off.erase(pv);
+      }
+    }
+    by_off.emplace(off, size);
+    by_size.insert({size, off});
+  };
   int64_t top = 0;
+  // ---- queued fronts: pools passed up the tree (children have smaller
+  // indices than their parents)
+  {
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> pool(ns);
+    for (int64_t s = 0; s < ns; ++s) {
+      if (!inq[s]) continue;
+      SnInfo& I = S.sn[s];
+      std::vector<std::pair<int64_t, int64_t>>& P = pool[s];
+      for (int32_t ci = I.child_begin; ci < I.child_begin + I.nchild; ++ci) {
+        const int32_t c = S.children[ci];
+        std::vector<std::pair<int64_t, int64_t>>& Q = pool[c];
+        P.insert(P.end(), Q.begin(), Q.end());
+        std::vector<std::pair<int64_t, int64_t>>().swap(Q);
+        const int64_t cs = usize(c);
+        if (cs > 0) P.push_back({S.sn[c].Uoff, cs});
+      }
+      std::sort(P.begin(), P.end());
+      size_t w = 0;
+      for (size_t q = 0; q < P.size(); ++q) {
+        if (w > 0 && P[w - 1].first + P[w - 1].second == P[q].first) P[w - 1].second += P[q].second;
+        else P[w++] = P[q];
+      }
+      P.resize(w);
+      const int64_t sz = usize(s);
+      I.Uoff = 0;
+      if (sz == 0) continue;
+      size_t best = P.size();
+      for (size_t q = 0; q < P.size(); ++q)
+        if (P[q].second >= sz && (best == P.size() || P[q].second < P[best].second)) best = q;
+      if (best < P.size()) {
+        I.Uoff = P[best].first;
+        P[best].first += sz;
+        P[best].second -= sz;
+        if (P[best].second == 0) P.erase(P.begin() + best);
+      } else {
+        I.Uoff = top;
+        top += sz;
+      }
+    }
+    // after the queue: the pools of its top fronts are free; the update
+    // matrices of those tops stay live until their (level-scheduled) parent
+    for (int64_t s = 0; s < ns; ++s) {
+      if (!inq[s]) continue;
+      const int32_t p = S.sn[s].parent;
+      if (p >= 0 && inq[p]) continue;
+      for (const auto& r : pool[s]) free_block(r.first, r.second);
+      const int64_t sz = usize(s);
+      if (sz > 0) release[S.slevel[p]].push_back({S.sn[s].Uoff, sz});
+    }
+  }
+  // ---- the other fronts, level by level
   for (int32_t lev = 0; lev < S.nlevels; ++lev) {
     // blocks read at level lev-1 are dead now
     if (lev >= 1) {
-      for (const auto& blk : release[lev - 1]) {
-        int64_t off = blk.first, size = blk.second;
-        auto nx = by_off.lower_bound(off);
-        if (nx != by_off.end() && off + size == nx->first) {
-          size += nx->second;
-          erase_size(nx->second, nx->first);
-          nx = by_off.erase(nx);
-        }
-        if (nx != by_off.begin()) {
-          auto pv = std::prev(nx);
-          if (pv->first + pv->second == off) {
-            off = pv->first;
-            size += pv->second;
-            erase_size(pv->second, pv->first);
-            by_off.erase(pv);
-          }
-        }
-        by_off.emplace(off, size);
-        by_size.insert({size, off});
-      }
+      for (const auto& blk : release[lev - 1]) free_block(blk.first, blk.second);
       release[lev - 1].clear();
     }
-    std::vector<int32_t> L = bylev[lev];
+    std::vector<int32_t> L;
+    for (int32_t s : bylev[lev])
+      if (!inq[s]) L.push_back(s);
     std::sort(L.begin(), L.end(), [&](int32_t a, int32_t b) {
       return (int64_t)S.sn[a].m * S.sn[a].m > (int64_t)S.sn[b].m * S.sn[b].m;
     });
     for (int32_t s : L) {
       SnInfo& I = S.sn[s];
-      // 32-element alignment keeps every update matrix 128/256-byte aligned
-      const int64_t sz = (((int64_t)I.m * I.m) + 31) / 32 * 32;
-      if (sz == 0 || I.parent < 0) {
+      const int64_t sz = usize(s);
+      if (sz == 0) {
         I.Uoff = 0;
         continue;
       }
@@ -601,7 +671,7 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
   timer.mark("front rows + maps");
   S.Lsize = Loff;
   S.Wsize = woff;
-  S.Usize = plan_update_memory(S);
+  S.Usize = plan_update_memory(S, std::vector<char>(S.sn.size(), 0));
   S.low_cp = std::move(cp);
   S.low_cr = std::move(cr);
   timer.mark("update-memory plan");
@@ -699,6 +769,65 @@ int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* col
   return MF_OK;
 }
 
+// SpTRSV variant 4 (Sec. 5): the level's partitioned inverse L_l^{-1} as one
+// sparse product per level and sweep, on the permuted global vector (no
+// front work vectors, no flags).  Forward, level l: for every front s of the
+// level, P_s = [L11^{-1}; -L21 L11^{-1}] maps the front's pivot values y(s)
+// to its pivot results (replace: F(r) = row of P11 times y(s)) and to
+// additions into its update rows (y(r) += row of P21 times y(s)); an update
+// row shared by several fronts of the level is one row of the level's
+// matrix whose entries are those fronts' rows of P, in front order.  Items:
+// one per row of the level's matrix, (global row, first group, end group,
+// pivot?), with groups (front, front row) in S.v4_grp.  Backward, level l:
+// x(first_s + c) = column c of P_s (rows c .. nf-1) times [F of the pivot
+// rows; x of the update rows]; items (front, column).  Every large front
+// (with kept diagonal inverses) takes the blocked partitioned inverse;
+// the others are returned in `pinv` as empty and get the one-CTA kernel.
+template <class Add>
+static void build_v4_solves(mf_symbolic& S, const std::vector<std::vector<int32_t>>& bylev,
+                            Add& add, std::vector<int32_t>& pinv) {
+  const int64_t n = S.n;
+  std::vector<int32_t> stamp(n, -1), slot(n, -1);
+  std::vector<std::vector<Item>> groups;  // per level row: its groups
+  std::vector<Item> it;
+  for (int32_t lev = 0; lev < S.nlevels; ++lev) {
+    const std::vector<int32_t>& L = bylev[lev];
+    std::vector<int32_t> rows;
+    std::vector<char> pivot;
+    groups.clear();
+    for (int32_t s : L) {
+      const SnInfo& f = S.sn[s];
+      if (S.ioff[s] >= 0) pinv.push_back(s);
+      const int nf = f.k + f.m;
+      const int32_t* rw = S.rowidx.data() + f.rows_off;
+      for (int i = 0; i < nf; ++i) {
+        const int32_t r = rw[i];
+        if (stamp[r] != lev) {
+          stamp[r] = lev;
+          slot[r] = (int32_t)rows.size();
+          rows.push_back(r);
+          pivot.push_back(i < f.k ? 1 : 0);
+          groups.emplace_back();
+        }
+        groups[slot[r]].push_back({s, i, 0, 0});
+      }
+    }
+    it.clear();
+    for (size_t q = 0; q < rows.size(); ++q) {
+      const int32_t g0 = (int32_t)S.v4_grp.size();
+      S.v4_grp.insert(S.v4_grp.end(), groups[q].begin(), groups[q].end());
+      it.push_back({rows[q], g0, (int32_t)S.v4_grp.size(), pivot[q]});
+    }
+    add(S.fwsched, K_V4_FW, lev, 0, it, 0.0);
+  }
+  for (int32_t lev = S.nlevels - 1; lev >= 0; --lev) {
+    it.clear();
+    for (int32_t s : bylev[lev])
+      for (int c = 0; c < S.sn[s].k; ++c) it.push_back({s, c, 0, 0});
+    add(S.bwsched, K_V4_BW, lev, 0, it, 0.0);
+  }
+}
+
 // Launch schedules of the numeric factorization and of the solves.  Fronts
 // of one level are independent (paper Sec. 5: level-set scheduling); small
 // fronts are batched one CTA each (grouped by size class), large fronts are
@@ -750,7 +879,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
   // children's completion flags instead of a level barrier.
   std::vector<char> inq(ns, 0);
   if (small_queue) {
-    std::vector<char> closed(ns, 0);
+    std::vector<char>& closed = inq;
     for (int32_t lev = 0; lev < S.nlevels; ++lev)
       for (int32_t s : bylev[lev]) {
         const SnInfo& P = S.sn[s];
@@ -759,17 +888,20 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
           ok = closed[S.children[ci]] != 0;
         closed[s] = ok ? 1 : 0;
       }
+  }
+  // the update-matrix plan follows the execution order of the schedule
+  S.Usize = plan_update_memory(S, inq);
+  if (small_queue) {
     it.clear();
     double fl = 0.0;
     int32_t maxnf = 0;
     for (int32_t lev = 0; lev < S.nlevels; ++lev)
       for (int32_t s : bylev[lev])
-        if (closed[s]) {
+        if (inq[s]) {
           const int nf = S.sn[s].k + S.sn[s].m;
           it.push_back({s, 0, 0, 0});
           fl += front_flops(nf, S.sn[s].k);
           maxnf = std::max(maxnf, nf);
-          inq[s] = 1;
         }
     add(S.fsched, K_SMALL_Q, 0, maxnf, it, fl);
     add(S.fsched_tc, K_SMALL_Q, 0, maxnf, it, fl);
@@ -949,6 +1081,11 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
       }
     }
   };
+  std::vector<int32_t> all_pinv;
+  S.v4_grp.clear();
+  if (S.v4) {
+    build_v4_solves(S, bylev, add, all_pinv);
+  } else {
   std::vector<std::vector<Item>> bydepth;
   auto flatten = [&](std::vector<Item>& out) {
     out.clear();
@@ -972,7 +1109,6 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
     }
     B.resize(w);
   };
-  std::vector<int32_t> all_pinv;
   for (int32_t lev = 0; lev < S.nlevels; ++lev) {
     split_level(bylev[lev], wcls, big);
     take_pinv(big, pfronts);
@@ -1039,6 +1175,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
     add(S.bwsched, K_BW_PCOPY, lev, 0, pg, 0.0);
     add(S.bwsched, K_BW_PINV, lev, 0, pv, 0.0);
   }
+  }  // variants 1-3
   // ---- partitioned inverse of the variant-3 fronts, after the whole
   // factorization: P = [L11; L21] X with L11 X = I solved by block rows,
   // right-looking.  Row blocks i of a front are its pivot blocks (i < nb)
@@ -1081,6 +1218,31 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
       add(S.fsched_tc, K_PINV, plev, t, st, fl);
     }
   }
+  // ---- variant 4: the partitioned inverse of every other front (one CTA
+  // each), then P transposed front by front (PT, rows of P contiguous) for
+  // the forward products
+  if (S.v4) {
+    const int32_t plev = S.nlevels;
+    std::vector<Item> sm, tr;
+    double fl = 0.0;
+    for (int64_t s = 0; s < ns; ++s) {
+      const SnInfo& P = S.sn[s];
+      if (S.ioff[s] < 0) {
+        sm.push_back({(int32_t)s, 0, 0, 0});
+        fl += (double)P.k * P.k * P.k / 3.0 + (double)P.m * P.k * P.k;
+      }
+      const int nf = P.k + P.m;
+      for (int i = 0; i < nf; i += kNB)
+        for (int j = 0; j < P.k; j += kNB) tr.push_back({(int32_t)s, 0, i, j});
+    }
+    S.pinv_flops += fl;
+    int32_t maxnf = 0;
+    for (const Item& x : sm) maxnf = std::max(maxnf, S.sn[x.s].k + S.sn[x.s].m);
+    add(S.fsched, K_PINV_SMALL, plev, maxnf, sm, fl);
+    add(S.fsched_tc, K_PINV_SMALL, plev, maxnf, sm, fl);
+    add(S.fsched, K_PT, plev, 0, tr, 0.0);
+    add(S.fsched_tc, K_PT, plev, 0, tr, 0.0);
+  }
 }
 
 // Consistency of the launch schedules, checked on the host: every front's
@@ -1118,7 +1280,8 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
       if (L.item_off < 0 || L.count < 0 || L.item_off + L.count > (int64_t)S.items.size())
         return fail("launch items out of range");
       for (int64_t x = L.item_off; x < L.item_off + L.count; ++x)
-        if (S.items[x].s < 0 || S.items[x].s >= ns) return fail("item names no front");
+        if (S.items[x].s < 0 || S.items[x].s >= (L.kind == K_V4_FW ? S.n : ns))
+          return fail(L.kind == K_V4_FW ? "row item out of range" : "item names no front");
     }
   auto nb_of = [&](int64_t s) { return (S.sn[s].k + kNB - 1) / kNB; };
   // ---- factor schedules
@@ -1133,7 +1296,8 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
     int32_t last_level = -1;
     for (size_t li = 0; li < sched.size(); ++li) {
       const Launch& L = sched[li];
-      if (L.kind == K_PINV_INIT || L.kind == K_PINV) continue;
+      if (L.kind == K_PINV_INIT || L.kind == K_PINV || L.kind == K_PINV_SMALL || L.kind == K_PT)
+        continue;
       if (L.kind == K_SMALL_Q) {
         // the persistent queue comes first; every front in it is small, and
         // every child of a queued front is queued with a smaller ticket
@@ -1231,7 +1395,70 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
   }
   // ---- solve schedules
   std::vector<int> pinv_front(ns, 0);
-  for (int bw = 0; bw < 2; ++bw) {
+  if (S.v4) {
+    // forward: every front row once, in a row item of its front's level
+    // (pivot rows alone, update rows merged by global row); backward: every
+    // pivot column once
+    std::vector<int64_t> rowoff(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) rowoff[s + 1] = rowoff[s] + S.sn[s].k + S.sn[s].m;
+    std::vector<char> seen(rowoff[ns], 0);
+    int32_t last = -1;
+    for (const Launch& L : S.fwsched) {
+      if (L.kind != K_V4_FW || L.level < last) return fail("variant-4 forward schedule");
+      last = L.level;
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const Item& it = S.items[x];
+        if (it.t < 0 || it.t >= it.a || it.a > (int64_t)S.v4_grp.size())
+          return fail("variant-4 row without groups");
+        if (it.b && it.a - it.t != 1) return fail("variant-4 pivot row with several groups");
+        for (int32_t g = it.t; g < it.a; ++g) {
+          const Item& gr = S.v4_grp[g];
+          const SnInfo& f = S.sn[gr.s];
+          if (S.slevel[gr.s] != L.level || gr.t < 0 || gr.t >= f.k + f.m)
+            return fail("variant-4 group outside its level or front");
+          if ((gr.t < f.k) != (it.b != 0) || S.rowidx[f.rows_off + gr.t] != it.s)
+            return fail("variant-4 group on the wrong row");
+          if (seen[rowoff[gr.s] + gr.t]++) return fail("variant-4 front row repeated");
+        }
+      }
+    }
+    for (char c : seen)
+      if (c != 1) return fail("variant-4 front row missing");
+    std::vector<int64_t> cols(ns, 0);
+    last = S.nlevels;
+    for (const Launch& L : S.bwsched) {
+      if (L.kind != K_V4_BW || L.level > last) return fail("variant-4 backward schedule");
+      last = L.level;
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const Item& it = S.items[x];
+        if (S.slevel[it.s] != L.level || it.t != cols[it.s]) return fail("variant-4 column order");
+        cols[it.s]++;
+      }
+    }
+    for (int64_t s = 0; s < ns; ++s) {
+      if (cols[s] != S.sn[s].k) return fail("variant-4 pivot column missing");
+      pinv_front[s] = S.ioff[s] >= 0;  // the blocked inverse, checked below
+    }
+    // the partitioned inverse of every front: blocked (kept inverses) or
+    // one CTA, then its transpose tile by tile
+    for (int tc = 0; tc < 2; ++tc) {
+      std::vector<int> once(ns, 0);
+      std::vector<int64_t> tiles_(ns, 0);
+      for (const Launch& L : tc ? S.fsched_tc : S.fsched)
+        for (int64_t x = L.item_off; L.kind >= K_PINV_INIT && x < L.item_off + L.count; ++x) {
+          const Item& it = S.items[x];
+          if (L.kind == K_PINV_SMALL || (L.kind == K_PINV_INIT && it.t == 0)) once[it.s]++;
+          if (L.kind == K_PT) tiles_[it.s]++;
+        }
+      for (int64_t s = 0; s < ns; ++s) {
+        const int64_t nf = S.sn[s].k + S.sn[s].m;
+        if (once[s] != 1) return fail("variant-4 front without a partitioned inverse");
+        if (tiles_[s] != ((nf + kNB - 1) / kNB) * ((S.sn[s].k + kNB - 1) / kNB))
+          return fail("variant-4 transpose tiles");
+      }
+    }
+  }
+  for (int bw = 0; bw < 2 && !S.v4; ++bw) {
     const std::vector<Launch>& sched = bw ? S.bwsched : S.fwsched;
     std::vector<int> warp(ns, 0);
     std::vector<std::vector<std::pair<int, int>>> piv(ns), upd(ns), pv(ns), pg(ns), gemv(ns);

@@ -22,7 +22,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'M', 'F', 'S', 'Y', 'M', 'B', 'O', 'L'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 constexpr uint64_t kFnvOffset = 1469598103934665603ull;
 constexpr uint64_t kFnvPrime = 1099511628211ull;
 
@@ -169,6 +169,8 @@ void members(IO& io, S& s) {
   io(s.blkoff);
   io(s.ginv_ptr);
   io(s.ginv_src);
+  io(s.v4);
+  io(s.v4_grp);
 }
 
 // Sizes that the rest of the library relies on without checking again.
@@ -275,6 +277,12 @@ bool indices_in_range(const mf_symbolic& s) {
               return false;
             break;
           }
+          case mf::K_PINV_SMALL:
+            if (nf > mf::kSmallMax || s.ioff[it.s] >= 0) return false;
+            break;
+          case mf::K_PT:
+            if (it.a < 0 || it.a >= nf || it.b < 0 || it.b >= I.k) return false;
+            break;
           case mf::K_PINV_INIT:
           case mf::K_PINV:
             if (it.t < 0 || it.t >= nb || it.a < 0 || it.b < 0 || it.b >= nb ||
@@ -306,6 +314,23 @@ bool indices_in_range(const mf_symbolic& s) {
     if (r.s < -1 || r.s >= nfr) return false;
     if (r.s >= 0 && (r.t < 0 || r.t > r.a || r.a > s.sn[r.s].m)) return false;
   }
+  // variant 4: forward groups name a front row; forward items a global row
+  // and a range of groups; backward items a pivot column
+  for (const mf::Item& g : s.v4_grp)
+    if (g.s < 0 || g.s >= nfr || g.t < 0 || g.t >= s.sn[g.s].k + s.sn[g.s].m) return false;
+  for (const mf::Launch& L : s.fwsched)
+    if (L.kind == mf::K_V4_FW)
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const mf::Item& it = s.items[x];
+        if (it.s < 0 || it.s >= n || it.t < 0 || it.t > it.a || it.a > (int64_t)s.v4_grp.size())
+          return false;
+      }
+  for (const mf::Launch& L : s.bwsched)
+    if (L.kind == mf::K_V4_BW)
+      for (int64_t x = L.item_off; x < L.item_off + L.count; ++x) {
+        const mf::Item& it = s.items[x];
+        if (it.t < 0 || it.t >= s.sn[it.s].k) return false;
+      }
   for (const auto* sched : {&s.fsched, &s.fsched_tc})
     for (const mf::Launch& L : *sched)
       if (L.kind == mf::K_ASSEMBLE)

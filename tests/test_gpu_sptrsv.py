@@ -2,7 +2,9 @@
 variant 2 solves the large fronts' pivot blocks as a product with the kept
 inverses of their diagonal blocks; variant 3 (partitioned inverse) makes each
 level one product with [L11^{-1}; -L21 L11^{-1}], computed after the
-factorization."""
+factorization; variant 4 stores that inverse for every front as one sparse
+matrix per level and sweep and solves on the global vector (one launch per
+level and sweep, no front work vectors, no waits)."""
 import numpy as np
 import pytest
 
@@ -116,7 +118,58 @@ def test_partitioned_inverse_repeated_factorizations(mf, orc):
         mf.mf_destroy(h)
 
 
-@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("case", ["dense_333", "dense_150", "lap3d_jump_20", "q1_14x12x4",
+                                  "lap2d_301x157"])
+@pytest.mark.parametrize("nrhs", [1, 3, 9, 33])
+def test_level_matrix_variant_matches_oracle_and_substitution(mf, orc, case, nrhs):
+    rp, ci, v, perm = case_matrix(case)
+    n = len(rp) - 1
+    B = gen.rhs(n, nrhs, seed=31 + nrhs)
+    X4, info4 = solve_with(mf, 4, rp, ci, v, perm, B)
+    X1, info1 = solve_with(mf, 1, rp, ci, v, perm, B)
+    X3, info3 = solve_with(mf, 3, rp, ci, v, perm, B)
+    # P and its transpose for every front: more memory than variant 3
+    assert info4["factor_bytes_fp64"] > info3["factor_bytes_fp64"]
+    assert orc.berr(rp, ci, v, X4, B) <= BERR
+    F = orc.factor(rp, ci, v, perm)
+    Xo = orc.solve(F, B, perm)
+    scale = np.max(np.abs(Xo))
+    assert np.max(np.abs(X4 - Xo)) <= 1e-9 * scale
+    assert np.max(np.abs(X4 - X1)) <= 1e-9 * scale
+
+
+def test_level_matrix_variant_refactor_and_noalloc(mf, orc):
+    """The inverses and their transposes are part of the factorization's
+    graph: a second numeric factorization with other values refreshes them;
+    the no-allocation entry point runs the same per-level products."""
+    import torch
+    rp, ci, v, perm = case_matrix("q1_14x12x4")
+    n = len(rp) - 1
+    B = gen.rhs(n, 2, seed=8)
+    opt = mf.mf_options_default()
+    opt.sptrsv = 4
+    h = mf.mf_create(opt)
+    s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+    mf.mf_symbolic_check(s)
+    f = mf.mf_factor_create(h, s, mf.MF_FP64)
+    try:
+        for scale in (1.0, 3.0):
+            v2 = v * scale
+            mf.mf_factor_numeric(f, v2)
+            X = mf.mf_solve(f, B)
+            assert orc.berr(rp, ci, v2, X, B) <= BERR
+            Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+            Xd = torch.from_numpy(np.zeros((2, n))).cuda().t()
+            mf.mf_solve_noalloc(f, Bd, Xd)
+            mf.mf_solve_check(f)
+            assert np.array_equal(Xd.cpu().numpy(), X)
+    finally:
+        mf.mf_factor_free(f)
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4])
 def test_inverse_variant_fp32_refinement(mf, orc, variant):
     rp, ci, v, perm = case_matrix("lap3d_jump_20")
     n = len(rp) - 1

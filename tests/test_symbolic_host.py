@@ -229,11 +229,12 @@ def test_condensed_invalid(mf, handle):
 
 
 def test_sptrsv_option_values(mf, orc):
-    """Variants 1-3 are accepted (0 means 1); variant 3 adds the partitioned
-    inverse, the size of the large fronts' L, to the factor's memory."""
+    """Variants 1-4 are accepted (0 means 1); variant 3 adds the partitioned
+    inverse, the size of the large fronts' L, to the factor's memory, and
+    variant 4 its transpose as well; 5 is refused."""
     rp, ci, v, perm, _ = gen.config3(16)
     sizes = {}
-    for variant in (0, 1, 2, 3):
+    for variant in (0, 1, 2, 3, 4):
         opt = mf.mf_options_default()
         opt.sptrsv = variant
         h = mf.mf_create(opt)
@@ -241,9 +242,9 @@ def test_sptrsv_option_values(mf, orc):
         sizes[variant] = mf.mf_symbolic_get_info(s)["factor_bytes_fp64"]
         mf.mf_symbolic_free(s)
         mf.mf_destroy(h)
-    assert sizes[0] == sizes[1] < sizes[2] < sizes[3]
+    assert sizes[0] == sizes[1] < sizes[2] < sizes[3] < sizes[4]
     opt = mf.mf_options_default()
-    opt.sptrsv = 4
+    opt.sptrsv = 5
     with pytest.raises(mf.MFError) as e:
         mf.mf_create(opt)
     assert e.value.code == mf.MF_ERR_INVALID
@@ -345,7 +346,7 @@ def test_factor_over_budget_is_oom(mf):
 
 
 # ---- schedule consistency (host) ------------------------------------------
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("relax,small,queue", [(0, 128, 1), (1, 128, 1), (1, 32, 1), (1, 128, 0)])
 def test_schedules_cover_every_front_once(mf, variant, relax, small, queue):
     opt = mf.mf_options_default()
