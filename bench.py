@@ -78,6 +78,9 @@ def parse():
                         "3 partitioned inverse (one product per level; computed inside the "
                         "timed factorization), 4 partitioned inverse of every front as one "
                         "sparse product per level and sweep")
+    p.add_argument("--small-queue", type=int, default=1,
+                   help="small fronts in one persistent launch: 0 off, 1 fronts of k+m <= 64 "
+                        "(default), q >= 2 fronts of k+m <= q")
     p.add_argument("--serve-rates", default="25,100,400",
                    help="serve: Poisson arrival rates (requests/s) to sweep")
     p.add_argument("--serve-requests", type=int, default=240, help="serve: requests per rate")
@@ -419,6 +422,8 @@ def main():
                  "ms": tuned_ms}
     opt.profile = 1  # per-launch CUDA events: per-kernel-kind device time
     opt.sptrsv = args.sptrsv
+    if not args.autotune:
+        opt.small_queue = args.small_queue
     h = mf.mf_create(opt)
     t0 = time.perf_counter()
     s = mf.mf_symbolic_analyze(h, rp, ci, perm)

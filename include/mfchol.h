@@ -95,13 +95,14 @@ typedef struct mf_options {
                                vector, with no front work vectors and no
                                waits.  0 is taken as 1.  Fixed at symbolic
                                analysis. */
-  int32_t small_queue;      /* 1 (default): every small front whose subtree
-                               holds only small fronts runs in one persistent
-                               launch (a device queue in level order, each
-                               front waiting, with a bounded wait, for its
-                               children's completion flags); 0: one launch
-                               per level and size class.  Fixed at symbolic
-                               analysis. */
+  int32_t small_queue;      /* 1 (default): every front of k+m <= 64 whose
+                               subtree holds only such fronts runs in one
+                               persistent launch (a device queue in level
+                               order, each front waiting, with a bounded
+                               wait, for its children's completion flags);
+                               a value q >= 2 takes fronts of k+m <= q (at
+                               most small_front_max); 0: one launch per level
+                               and size class.  Fixed at symbolic analysis. */
 } mf_options;
 
 /* Summary of a symbolic analysis. */

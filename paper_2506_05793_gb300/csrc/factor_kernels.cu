@@ -27,6 +27,9 @@ namespace {
 
 // Default bound of a queue wait: about kQueueSpin x 128 ns (0.5 s).
 constexpr int kQueueSpin = 1 << 22;
+// threads of a queue CTA: queued fronts are small (k + m <= 64 by default),
+// so more, smaller CTAs per SM overlap the latency of the per-column steps
+constexpr int kQueueThreads = 128;
 
 template <typename T>
 struct FD {
@@ -894,10 +897,10 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
       cudaError_t e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T>, 256, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T>, kQueueThreads, smem);
       if (e != cudaSuccess) return e;
       const int blocks = std::max(1, std::min(L.count, sms * std::max(per, 1)));
-      k_small_queue<T><<<blocks, 256, smem, st>>>(d, L.item_off, L.count);
+      k_small_queue<T><<<blocks, kQueueThreads, smem, st>>>(d, L.item_off, L.count);
       break;
     }
     case K_ASSEMBLE:

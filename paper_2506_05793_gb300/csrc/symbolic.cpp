@@ -878,12 +878,15 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
   // front's children always have smaller tickets); each waits for its
   // children's completion flags instead of a level barrier.
   std::vector<char> inq(ns, 0);
+  // fronts up to qmax rows join the queue (option 1: the default of 64, which
+  // keeps the queue's shared memory small enough for many CTAs per SM)
+  const int qmax = std::min(small_max, small_queue == 1 ? 64 : small_queue);
   if (small_queue) {
     std::vector<char>& closed = inq;
     for (int32_t lev = 0; lev < S.nlevels; ++lev)
       for (int32_t s : bylev[lev]) {
         const SnInfo& P = S.sn[s];
-        bool ok = P.k + P.m <= small_max;
+        bool ok = P.k + P.m <= qmax;
         for (int32_t ci = P.child_begin; ok && ci < P.child_begin + P.nchild; ++ci)
           ok = closed[S.children[ci]] != 0;
         closed[s] = ok ? 1 : 0;
