@@ -45,13 +45,13 @@ def _coo_to_csr(n, rows, cols, vals):
     order = np.argsort(key, kind="stable")
     key = key[order]
     vals = vals[order]
-    uniq, start = np.unique(key, return_index=True)
+    start = np.nonzero(np.concatenate(([True], key[1:] != key[:-1])))[0] if len(key) else key
+    uniq = key[start]
     summed = np.add.reduceat(vals, start) if len(vals) else vals
     r = uniq // n
     c = (uniq % n).astype(np.int32)
     rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(rowptr, r + 1, 1)
-    rowptr = np.cumsum(rowptr)
+    rowptr[1:] = np.cumsum(np.bincount(r, minlength=n))
     return rowptr, c, summed.astype(np.float64)
 
 
@@ -305,6 +305,67 @@ def q1_extruded(ex, ey, ez, hx=1.0, hy=1.0, hz=0.01, beta=1.0, seed=1):
         colind[dst] = cflat.astype(np.int32)
         values[dst] = vflat
     return rowptr, colind, values
+
+
+def _q1_elasticity_element(h, E, nu):
+    """24 x 24 stiffness of a cube Q1 element of side h for isotropic linear
+    elasticity (Lame lambda, mu from E, nu), 2 x 2 x 2 Gauss points; local
+    node (a, b, c) in {0,1}^3, x fastest, dof = 3 node + component."""
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(6), np.arange(6)] += np.array([2 * mu, 2 * mu, 2 * mu, mu, mu, mu])
+    local = [(a, b, c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+    g = [-1 / np.sqrt(3), 1 / np.sqrt(3)]
+    K = np.zeros((24, 24))
+    for xi in g:
+        for eta in g:
+            for ze in g:
+                B = np.zeros((6, 24))
+                for p, (a, b, c) in enumerate(local):
+                    sa, sb, sc = 2 * a - 1, 2 * b - 1, 2 * c - 1
+                    # derivatives of (1 + s xi)(1 + s eta)(1 + s ze) / 8, times 2 / h
+                    dx = sa * (1 + sb * eta) * (1 + sc * ze) / 8 * 2 / h
+                    dy = sb * (1 + sa * xi) * (1 + sc * ze) / 8 * 2 / h
+                    dz = sc * (1 + sa * xi) * (1 + sb * eta) / 8 * 2 / h
+                    B[0, 3 * p] = dx
+                    B[1, 3 * p + 1] = dy
+                    B[2, 3 * p + 2] = dz
+                    B[3, 3 * p], B[3, 3 * p + 1] = dy, dx
+                    B[4, 3 * p + 1], B[4, 3 * p + 2] = dz, dy
+                    B[5, 3 * p], B[5, 3 * p + 2] = dz, dx
+                K += B.T @ D @ B * (h / 2) ** 3
+    return K
+
+
+def elasticity_3d(N, E=1.0, nu=0.3):
+    """3D linear elasticity on N^3 nodes of a unit cube of Q1 hexahedra, 3
+    dofs per node (interleaved; node index x fastest): the 27-point stencil
+    of the paper's FastILU experiments (n = 3 N^3).  The nodes of the face
+    x = 0 are clamped: their rows and columns become those of the identity,
+    which keeps the matrix SPD."""
+    h = 1.0 / (N - 1)
+    Ke = _q1_elasticity_element(h, E, nu)
+    e = np.arange(N - 1)
+    ez, ey, ex = np.meshgrid(e, e, e, indexing="ij")
+    base = (ex + N * (ey + N * ez)).reshape(-1)
+    local = np.array([a + N * (b + N * c) for c in (0, 1) for b in (0, 1) for a in (0, 1)])
+    nodes = base[:, None] + local[None, :]                        # (elements, 8)
+    dofs = (3 * nodes[:, :, None] + np.arange(3)[None, None, :]).reshape(len(base), 24)
+    rows = np.repeat(dofs, 24, axis=1).reshape(-1)
+    cols = np.tile(dofs, (1, 24)).reshape(-1)
+    vals = np.tile(Ke.reshape(-1), len(base))
+    n = 3 * N ** 3
+    node_of = np.arange(n) // 3
+    fixed = (node_of % N) == 0
+    keep = ~(fixed[rows] | fixed[cols])
+    rows, cols, vals = rows[keep], cols[keep], vals[keep]
+    fd = np.nonzero(fixed)[0]
+    rows = np.concatenate([rows, fd])
+    cols = np.concatenate([cols, fd])
+    vals = np.concatenate([vals, np.ones(len(fd))])
+    return _coo_to_csr(n, rows, cols, vals)
 
 
 # --------------------------------------------------------------------------

@@ -21,6 +21,10 @@ the three phases of the paper's Ax=b statement in Sec. 3):
 * ``brute_symbolic`` -- dense boolean elimination on tiny inputs (pure Python),
   an independent pin for etree / counts / nnz(L).
 * ``berr``, ``rel_fro`` -- the error measures used by the parity tests.
+* ``iluk_pattern``, ``ilu_exact``, ``fastilu``, ``fast_trsv`` -- FastILU and
+  FastSpTRSV (paper Sec. 6): the ILU(k) pattern by levels of fill, the
+  incomplete LU on it (the sweeps' fixed point), the sweeps of the factor
+  (out of place) and of the triangular solves (C).
 
 Pins (tests/test_oracle.py): dense numpy Cholesky, the closed-form 1D
 Laplacian factor, the Dirichlet-Laplacian log-determinant, brute-force symbolic
@@ -77,6 +81,13 @@ def load_library(path):
     lib.orc_supernodes.argtypes = [I, P, P, P, P]
     lib.orc_supernodes.restype = ctypes.c_int64
     lib.orc_solve.argtypes = [I, P, P, P, P, I, I]
+    lib.orc_iluk_pattern.argtypes = [I, P, P, ctypes.c_int32, I, P, P, P, P, P, P]
+    lib.orc_iluk_pattern.restype = ctypes.c_int64
+    lib.orc_ilu_exact.argtypes = [I, P, P, P, ctypes.c_int32, P, P, P]
+    lib.orc_fastilu_sweep.argtypes = [I, P, P, P, ctypes.c_int32, P, P, P, P, P, P, P,
+                                      ctypes.c_double, P, P]
+    lib.orc_fast_trsv_sweep.argtypes = [I, P, P, P, ctypes.c_int32, P, P, ctypes.c_int, P, P, P,
+                                        ctypes.c_double]
     return lib
 
 
@@ -426,3 +437,121 @@ def rel_fro(Lx_test, Lx_ref):
     """||L - L_ref||_F / ||L_ref||_F over a common pattern."""
     d = np.asarray(Lx_test, dtype=np.float64) - np.asarray(Lx_ref, dtype=np.float64)
     return float(np.linalg.norm(d) / np.linalg.norm(Lx_ref))
+
+
+# ---------------------------------------------------------------------------
+# FastILU / FastSpTRSV (paper Sec. 6; the algorithms of Chow and Patel)
+# ---------------------------------------------------------------------------
+class IluPattern:
+    """ILU(k) pattern S with the level of fill of every entry; the CSC of S
+    (cp, cr, cq) and the diagonal positions, for the sweeps."""
+
+    def __init__(self, n, Sp, Sj, Slev, K):
+        self.n, self.Sp, self.Sj, self.Slev, self.K = n, Sp, Sj, Slev, K
+        rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(Sp))
+        self.diag = np.empty(n, dtype=np.int64)
+        on = np.nonzero(rows == Sj)[0]
+        self.diag[rows[on]] = on
+        order = np.lexsort((rows, Sj))  # by column, then row
+        self.cr = rows[order].astype(np.int32)
+        self.cq = order.astype(np.int64)
+        self.cp = np.zeros(n + 1, dtype=np.int64)
+        self.cp[1:] = np.cumsum(np.bincount(Sj, minlength=n))
+        self.rows = rows
+
+    def values_of(self, rowptr, colind, values, shift=0.0):
+        """A on S (zeros at the fill; the diagonal times 1 + shift)."""
+        n = self.n
+        a = np.zeros(len(self.Sj))
+        key = self.rows * n + self.Sj
+        rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+        k2 = rows * n + np.asarray(colind, dtype=np.int64)
+        at = np.searchsorted(key, k2)
+        np.add.at(a, at, np.asarray(values, dtype=np.float64))
+        a[self.diag] *= 1.0 + shift
+        return a
+
+
+def iluk_pattern(rowptr, colind, K):
+    """ILU(K) pattern by levels of fill (C), with its levels."""
+    lib = _load()
+    n = len(rowptr) - 1
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    cap = max(16, 4 * len(ci) + n)
+    work = [np.empty(max(n, 1), dtype=np.int32) for _ in range(3)]
+    while True:
+        Sp = np.empty(n + 1, dtype=np.int64)
+        Sj = np.empty(cap, dtype=np.int32)
+        Sl = np.empty(cap, dtype=np.int32)
+        nnz = lib.orc_iluk_pattern(n, _p(rp), _p(ci), int(K), cap, _p(Sp), _p(Sj), _p(Sl),
+                                   *[_p(w) for w in work])
+        if nnz >= 0:
+            return IluPattern(n, Sp, Sj[:nnz].copy(), Sl[:nnz].copy(), int(K))
+        cap *= 2
+
+
+def ilu_exact(pat, a, K=None):
+    """Incomplete LU on the entries of level <= K (default: the pattern's)."""
+    lib = _load()
+    vals = np.array(a, dtype=np.float64)
+    pos = np.empty(pat.n, dtype=np.int64)
+    lib.orc_ilu_exact(pat.n, _p(pat.Sp), _p(pat.Sj), _p(pat.Slev),
+                      pat.K if K is None else int(K), _p(pat.diag), _p(vals), _p(pos))
+    return vals
+
+
+def fastilu_initial(pat, a, K=None):
+    """Initial guess of the sweeps: l_ij = a_ij / a_jj, u_ij = a_ij (zero at
+    the fill)."""
+    v = np.array(a, dtype=np.float64)
+    low = pat.rows > pat.Sj
+    v[low] = v[low] / a[pat.diag[pat.Sj[low]]]
+    return v
+
+
+def fastilu(pat, a, sweeps, omega=1.0, warmup=False, start=None, K=None):
+    """FastILU(K) on the pattern (K defaults to the pattern's level):
+    `sweeps` out-of-place sweeps from the initial guess (or `start`); with
+    warmup, FastILU(K-1) first (recursively, same sweeps) gives the initial
+    values of the entries of level < K, those of level K starting at zero.
+    Returns the factors on S (entries of level > K hold the initial guess
+    and are not part of the result)."""
+    lib = _load()
+    K = pat.K if K is None else int(K)
+    if start is None:
+        if warmup and K > 0:
+            prev = fastilu(pat, a, sweeps, omega, warmup=True, K=K - 1)
+            start = np.where(pat.Slev < K, prev, 0.0)
+        else:
+            start = fastilu_initial(pat, a)
+    return _sweeps(lib, pat, a, start, sweeps, omega, K)
+
+
+def _sweeps(lib, pat, a, start, sweeps, omega, K):
+    cur = np.array(start, dtype=np.float64)
+    nxt = np.empty_like(cur)
+    w = np.zeros(pat.n)
+    mark = np.zeros(pat.n, dtype=np.int8)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    for _ in range(sweeps):
+        lib.orc_fastilu_sweep(pat.n, _p(pat.Sp), _p(pat.Sj), _p(pat.Slev), int(K), _p(pat.diag),
+                              _p(pat.cp), _p(pat.cr), _p(pat.cq), _p(a), _p(cur), _p(nxt),
+                              float(omega), _p(w), _p(mark))
+        cur, nxt = nxt, cur
+    return cur
+
+
+def fast_trsv(pat, lu, b, upper, sweeps, omega=1.0, K=None):
+    """FastSpTRSV: `sweeps` Jacobi sweeps on L (unit diagonal) or U from x = 0."""
+    lib = _load()
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    lu = np.ascontiguousarray(lu, dtype=np.float64)
+    x = np.zeros(pat.n)
+    y = np.empty(pat.n)
+    for _ in range(sweeps):
+        lib.orc_fast_trsv_sweep(pat.n, _p(pat.Sp), _p(pat.Sj), _p(pat.Slev),
+                                pat.K if K is None else int(K), _p(pat.diag), _p(lu),
+                                1 if upper else 0, _p(b), _p(x), _p(y), float(omega))
+        x, y = y, x
+    return x

@@ -282,3 +282,186 @@ void orc_solve(int64_t n, const int64_t* Lp, const int32_t* Li,
     }
   }
 }
+
+/* ------------------------------------------------------------------------
+ * FastILU and FastSpTRSV (paper Sec. 6, the algorithms of Chow and Patel).
+ *
+ * Pattern S of ILU(k) by levels of fill: entries of A (and the diagonal) have
+ * level 0; eliminating with row k gives entry (i, j) the level
+ * lev(i, k) + lev(k, j) + 1, the smallest over all k < min(i, j); S keeps the
+ * entries of level <= K.  The rows are built in order, row i from the finished
+ * upper parts of the rows k < i it meets, taking those k in increasing order
+ * (a min-heap of column indices).  Output: Sp (n + 1), Sj (columns sorted),
+ * Slev (levels).  Returns nnz(S), or -1 if cap entries are not enough.
+ * Work: lev, heap, list (n ints each).
+ * ------------------------------------------------------------------------ */
+static void heap_push(int32_t* h, int64_t* hn, int32_t v) {
+  int64_t c = (*hn)++;
+  h[c] = v;
+  while (c > 0) {
+    int64_t p = (c - 1) / 2;
+    if (h[p] <= h[c]) break;
+    int32_t t = h[p];
+    h[p] = h[c];
+    h[c] = t;
+    c = p;
+  }
+}
+
+static int32_t heap_pop(int32_t* h, int64_t* hn) {
+  int32_t top = h[0];
+  h[0] = h[--(*hn)];
+  int64_t c = 0;
+  for (;;) {
+    int64_t l = 2 * c + 1, r = l + 1, m = c;
+    if (l < *hn && h[l] < h[m]) m = l;
+    if (r < *hn && h[r] < h[m]) m = r;
+    if (m == c) break;
+    int32_t t = h[m];
+    h[m] = h[c];
+    h[c] = t;
+    c = m;
+  }
+  return top;
+}
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+int64_t orc_iluk_pattern(int64_t n, const int64_t* rp, const int32_t* ci, int32_t K,
+                         int64_t cap, int64_t* Sp, int32_t* Sj, int32_t* Slev,
+                         int32_t* lev, int32_t* heap, int32_t* list) {
+  const int32_t INF = 0x7fffffff;
+  for (int64_t i = 0; i < n; ++i) lev[i] = INF;
+  int64_t nnz = 0;
+  Sp[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t cnt = 0, hn = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      int32_t c = ci[p];
+      if (lev[c] == INF) {
+        lev[c] = 0;
+        list[cnt++] = c;
+        if (c < i) heap_push(heap, &hn, c);
+      }
+    }
+    if (lev[i] == INF) {
+      lev[i] = 0;
+      list[cnt++] = (int32_t)i;
+    }
+    while (hn > 0) {
+      int32_t k = heap_pop(heap, &hn);
+      int32_t lk = lev[k];
+      for (int64_t q = Sp[k]; q < Sp[k + 1]; ++q) {
+        int32_t j = Sj[q];
+        if (j <= k) continue;
+        int32_t nl = lk + Slev[q] + 1;
+        if (nl > K) continue;
+        if (lev[j] == INF) {
+          lev[j] = nl;
+          list[cnt++] = j;
+          if (j < i) heap_push(heap, &hn, j);
+        } else if (nl < lev[j]) {
+          lev[j] = nl;
+        }
+      }
+    }
+    qsort(list, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    if (nnz + cnt > cap) return -1;
+    for (int64_t q = 0; q < cnt; ++q) {
+      Sj[nnz + q] = list[q];
+      Slev[nnz + q] = lev[list[q]];
+      lev[list[q]] = INF;
+    }
+    nnz += cnt;
+    Sp[i + 1] = nnz;
+  }
+  return nnz;
+}
+
+/* Incomplete LU on the entries of S with level <= K (the fixed point that the
+ * FastILU sweeps approach): row by row, for each k < i of row i in increasing
+ * order, l_ik = a_ik / u_kk and a_ij -= l_ik u_kj for the entries (i, j) of
+ * S.  vals: A on S (zeros at fill) in, L (strictly lower, unit diagonal
+ * implied) and U (upper with the diagonal) on S out.  diag: position of
+ * (i, i) in row i.  pos: n int64 of work. */
+void orc_ilu_exact(int64_t n, const int64_t* Sp, const int32_t* Sj, const int32_t* Slev,
+                   int32_t K, const int64_t* diag, double* vals, int64_t* pos) {
+  for (int64_t i = 0; i < n; ++i) pos[i] = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t q = Sp[i]; q < Sp[i + 1]; ++q)
+      if (Slev[q] <= K) pos[Sj[q]] = q;
+    for (int64_t q = Sp[i]; q < diag[i]; ++q) {
+      if (Slev[q] > K) continue;
+      int32_t k = Sj[q];
+      double lik = vals[q] / vals[diag[k]];
+      vals[q] = lik;
+      for (int64_t r = diag[k] + 1; r < Sp[k + 1]; ++r) {
+        if (Slev[r] > K) continue;
+        int64_t at = pos[Sj[r]];
+        if (at >= 0) vals[at] -= lik * vals[r];
+      }
+    }
+    for (int64_t q = Sp[i]; q < Sp[i + 1]; ++q) pos[Sj[q]] = -1;
+  }
+}
+
+/* One FastILU sweep, out of place (every entry from the previous sweep's
+ * factors, so the result does not depend on the order of the updates): for
+ * each (i, j) in S of level <= K,
+ *   s = a_ij - sum_{k < min(i, j)} l_ik u_kj,
+ *   l_ij = (1 - omega) l_ij + omega s / u_jj   (i > j),
+ *   u_ij = (1 - omega) u_ij + omega s          (i <= j),
+ * with l and u read from `old`.  The sum runs over k in increasing order,
+ * through row i of L (scattered into w) and column j of S (cp, cr, cq: the
+ * CSC of S, rows increasing, cq the CSR position).  w: n doubles, zero on
+ * entry and exit; mark: n chars, zero on entry and exit. */
+void orc_fastilu_sweep(int64_t n, const int64_t* Sp, const int32_t* Sj, const int32_t* Slev,
+                       int32_t K, const int64_t* diag, const int64_t* cp, const int32_t* cr,
+                       const int64_t* cq, const double* a, const double* old, double* out,
+                       double omega, double* w, char* mark) {
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t q = Sp[i]; q < diag[i]; ++q)
+      if (Slev[q] <= K) {
+        w[Sj[q]] = old[q];
+        mark[Sj[q]] = 1;
+      }
+    for (int64_t q = Sp[i]; q < Sp[i + 1]; ++q) {
+      if (Slev[q] > K) {
+        out[q] = old[q];
+        continue;
+      }
+      int32_t j = Sj[q];
+      int64_t m = i < j ? i : j;
+      double s = a[q];
+      for (int64_t t = cp[j]; t < cp[j + 1] && cr[t] < m; ++t)
+        if (Slev[cq[t]] <= K && mark[cr[t]]) s -= w[cr[t]] * old[cq[t]];
+      if (i > j) out[q] = (1.0 - omega) * old[q] + omega * s / old[diag[j]];
+      else out[q] = (1.0 - omega) * old[q] + omega * s;
+    }
+    for (int64_t q = Sp[i]; q < diag[i]; ++q) {
+      w[Sj[q]] = 0.0;
+      mark[Sj[q]] = 0;
+    }
+  }
+}
+
+/* One FastSpTRSV sweep (Jacobi, out of place) with the factors on S of level
+ * <= K: lower (unit diagonal) x_i = (1 - omega) x_i + omega (b_i -
+ * sum_{j < i} l_ij x_j), or upper x_i = (1 - omega) x_i + omega (b_i -
+ * sum_{j > i} u_ij x_j) / u_ii, every x_j from the previous sweep (xo). */
+void orc_fast_trsv_sweep(int64_t n, const int64_t* Sp, const int32_t* Sj, const int32_t* Slev,
+                         int32_t K, const int64_t* diag, const double* lu, int upper,
+                         const double* b, const double* xo, double* x, double omega) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = b[i];
+    int64_t q0 = upper ? diag[i] + 1 : Sp[i];
+    int64_t q1 = upper ? Sp[i + 1] : diag[i];
+    for (int64_t q = q0; q < q1; ++q)
+      if (Slev[q] <= K) s -= lu[q] * xo[Sj[q]];
+    if (upper) s /= lu[diag[i]];
+    x[i] = (1.0 - omega) * xo[i] + omega * s;
+  }
+}

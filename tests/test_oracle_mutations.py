@@ -128,3 +128,46 @@ def test_berr_pins_catch_planted_mistake(orc, name, old, new):
     ns = {"np": np}
     exec(src.replace(old, new), ns)
     assert _berr_pins.failures(ns["berr"]), "no pin caught: " + name
+
+
+ILU_MUTATIONS = [
+    ("iluk: level rule without the + 1", "int32_t nl = lk + Slev[q] + 1;", "int32_t nl = lk + Slev[q];"),
+    ("ilu: multiplier not divided by the pivot", "double lik = vals[q] / vals[diag[k]];",
+     "double lik = vals[q];"),
+    ("fastilu: sum includes k = min(i, j)",
+     "t < cp[j + 1] && cr[t] < m;", "t < cp[j + 1] && cr[t] <= m;"),
+    ("fastilu: divided by u_ij instead of u_jj",
+     "omega * s / old[diag[j]];", "omega * s / old[q];"),
+    ("fastilu: damping applied to the wrong term",
+     "out[q] = (1.0 - omega) * old[q] + omega * s;", "out[q] = omega * old[q] + (1.0 - omega) * s;"),
+    ("fast_trsv: upper diagonal not divided", "if (upper) s /= lu[diag[i]];", ""),
+]
+
+
+def ilu_pins(orc):
+    """The hand-worked first sweeps, the fixed point, the complete-fill LU,
+    brute-force levels and exact triangular solves; names of the failures."""
+    import _ilu_pin_cases as c
+    return c.failures(orc)
+
+
+@pytest.mark.parametrize("name,old,new", ILU_MUTATIONS, ids=[m[0] for m in ILU_MUTATIONS])
+def test_ilu_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not unique: " + name
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib_path = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", str(lib_path), str(mutated),
+                           "-lm"])
+    saved = orc._load()
+    orc._lib = orc.load_library(str(lib_path))
+    try:
+        failed = ilu_pins(orc)
+    finally:
+        orc._lib = saved
+    assert failed, "no pin caught: " + name
+
+
+def test_ilu_pins_pass_on_the_oracle(orc):
+    assert ilu_pins(orc) == set()
