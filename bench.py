@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="q1", choices=["q1", "lap3d", "jump3d", "batch", "serve"],
+    p.add_argument("--workload", default="q1",
+                   choices=["q1", "lap3d", "jump3d", "batch", "serve", "fastilu"],
                    help="q1: extruded Q1 ice-sheet mesh (default); lap3d: 7-point Laplacian size^3 "
                         "(small cases for profiling); jump3d: 7-point Laplacian size^3 with "
                         "coefficients 1 / 1e3 on 8^3 blocks (seed 2); batch: 512 7-point Laplacian "
@@ -324,6 +325,66 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_fastilu(args):
+    """FastILU(k) and FastSpTRSV (paper Sec. 6) on the 3D Q1 elasticity
+    matrix (27-point stencil, 3 dofs per node) of N^3 nodes, N = --size
+    (default 32: n = 98,304): per level k = 0..3, the numeric phase (2
+    out-of-place sweeps, no warm-up, as the paper's tables) and one
+    preconditioner application (5 Jacobi sweeps per triangle), CUDA events,
+    median of 10 after 3 warm-ups.  Bytes per triangular sweep: one read of
+    the triangle's values, columns and levels (16 bytes per entry) plus the
+    gathered x (8 per entry) and b, x (16 per row)."""
+    import torch
+    import paper_2506_05793_gb300 as mf
+    import gen
+    mf.build()
+    N = args.size or 32
+    rp, ci, v = gen.elasticity_3d(N)
+    n = len(rp) - 1
+    vd = torch.from_numpy(v).cuda()
+    b = torch.from_numpy(gen.rhs(n, 1, seed=3)).cuda()
+    x = torch.empty_like(b)
+    st = torch.cuda.current_stream()
+    h = mf.mf_create()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs") or 6800.0
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ms = []
+        for _ in range(reps):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fn()
+            z.record(st)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(z))
+        return float(np.median(ms))
+
+    rows = []
+    for K in range(4):
+        ilu = mf.mf_ilu_symbolic(h, rp, ci, K)
+        _, nnz = mf.mf_ilu_info(ilu)
+        t_num = timed(lambda: mf.mf_ilu_numeric(ilu, vd, sweeps=2, stream=st))
+        t_app = timed(lambda: mf.mf_ilu_apply(ilu, b, 5, x=x, stream=st))
+        sweep_bytes = 24.0 * nnz / 2 + 16.0 * n  # one triangle
+        gbs = 10 * sweep_bytes / (t_app / 1e3) / 1e9
+        rows.append({"level": K, "nnz_per_row": nnz / n, "numeric_ms_2_sweeps": t_num,
+                     "apply_ms_5_sweeps_per_triangle": t_app, "apply_GBs": gbs,
+                     "apply_frac_of_hbm": gbs / hbm})
+        mf.mf_ilu_free(ilu)
+    mf.mf_destroy(h)
+    print(json.dumps({"metric": "FastILU(k) numeric ms (2 sweeps) and FastSpTRSV apply ms",
+                      "workload": "elasticity_q1_%d^3_nodes_3dof" % N, "n": n, "levels": rows,
+                      "unit": "ms", "data": "synthetic",
+                      "peak_source": "of measured" if peaks.get("hbm_gbs") else "of fallback"}))
+
+
 def run_serve(args):
     """Serving stream: Poisson arrivals of factor+solve requests (90% boxes
     with sides U{8..48}, 10% 64^3 Laplacians) and solve-only requests with
@@ -394,6 +455,9 @@ def main():
     args = parse()
     if args.workload == "serve":
         run_serve(args)
+        return
+    if args.workload == "fastilu":
+        run_fastilu(args)
         return
     if args.size is None:
         args.size = {"lap3d": 48, "jump3d": 96}.get(args.workload, 256)

@@ -410,6 +410,61 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
                      int32_t max_iter, int32_t allow_fallback,
                      mf_ir_report* rep, void* stream);
 
+/* ---- FastILU / FastSpTRSV (paper Sec. 6, after Chow and Patel) -----------
+ * An incomplete LU factorization A ~ L U (L unit lower, U upper) on the
+ * ILU(k) pattern S, computed by sweeps in which every entry of S is updated
+ * independently, and triangular solves by Jacobi sweeps in which every
+ * entry of the solution is updated independently.  FP64, one GPU. */
+
+typedef struct mf_ilu mf_ilu;
+
+/* Pattern S of ILU(level) by levels of fill (host): entries of A and the
+ * diagonal have level 0; eliminating row k gives (i, j) the level
+ * lev(i, k) + lev(k, j) + 1; S keeps the entries of level <= `level`.  A is
+ * CSR (rowptr n + 1 int64, colind int32, any order, duplicates allowed);
+ * the caller keeps ownership.  Host only: the first mf_ilu_numeric call
+ * uploads S and allocates the device work of the sweeps.  Errors:
+ * MF_ERR_INVALID for a bad CSR or level < 0, MF_ERR_OOM. */
+int mf_ilu_symbolic(mf_handle* h, int64_t n, const int64_t* rowptr,
+                    const int32_t* colind, int32_t level, mf_ilu** out);
+/* n and |S|. */
+int mf_ilu_info(const mf_ilu* ilu, int64_t* n, int64_t* nnz);
+/* S as CSR (Sp n + 1, Sj |S| columns increasing per row) and the level of
+ * every entry (Slev |S|); Sj and Slev may be NULL. */
+int mf_ilu_pattern(const mf_ilu* ilu, int64_t* Sp, int32_t* Sj, int32_t* Slev);
+/* FastILU: values (CSR order of the analysed pattern, host or device) with
+ * the diagonal scaled by 1 + shift (the Manteuffel shift); initial guess
+ * l_ij = a_ij / a_jj, u_ij = a_ij (zero at fill entries); then `sweeps`
+ * sweeps over S, each entry (i, j):
+ *   s = a_ij - sum_{k < min(i, j)} l_ik u_kj,
+ *   l_ij = (1 - omega) l_ij + omega s / u_jj  (i > j),
+ *   u_ij = (1 - omega) u_ij + omega s         (i <= j),
+ * out of place (in_place = 0: every entry from the previous sweep; the
+ * result does not depend on the order of the updates) or in place
+ * (in_place = 1: entries read what other threads have already written, the
+ * asynchronous sweep of the paper; results vary from run to run).  With
+ * warmup, FastILU(level - 1) runs first, recursively, and initializes the
+ * entries of lower level (those of level `level` start at zero).  0 < omega
+ * <= 1.  Enqueued on stream. */
+int mf_ilu_numeric(mf_ilu* ilu, const double* values, int32_t values_on_device,
+                   int32_t sweeps, double omega, double shift, int32_t warmup,
+                   int32_t in_place, void* stream);
+/* The factors on S in the order of mf_ilu_pattern: l_ij for i > j, u_ij for
+ * i <= j (|S| doubles, host).  Synchronous. */
+int mf_ilu_export(const mf_ilu* ilu, double* LU);
+/* FastSpTRSV: `sweeps` Jacobi sweeps from x = 0 with L (upper = 0, unit
+ * diagonal) or U (upper = 1):
+ *   x_i = (1 - omega) x_i + omega (b_i - sum_{j != i} t_ij x_j) / t_ii,
+ * every x_j from the previous sweep.  b and x (n doubles) are both host or
+ * both device pointers as on_device says; synchronous for host pointers. */
+int mf_ilu_trsv(mf_ilu* ilu, int32_t upper, int32_t sweeps, double omega,
+                const double* b, double* x, int32_t on_device, void* stream);
+/* Preconditioner application x = U^-1 L^-1 b with FastSpTRSV (`sweeps`
+ * each), as mf_ilu_trsv. */
+int mf_ilu_apply(mf_ilu* ilu, int32_t sweeps, double omega, const double* b,
+                 double* x, int32_t on_device, void* stream);
+int mf_ilu_free(mf_ilu* ilu);
+
 /* ---- serving loop (no paper counterpart beyond Sec. 5's many subdomain
  * solves per GPU; continuous batching of factor and solve requests) ----- */
 

@@ -102,6 +102,14 @@ _SIGS = {
     "mf_factor_export_columns": [_P, _I64, _I64, _P],
     "mf_diag_fp64_peak": [_I32, _P, _P],
     "mf_diag_small_queue": [_P, _I32, _P],
+    "mf_ilu_symbolic": [_P, _I64, _P, _P, _I32, _P],
+    "mf_ilu_info": [_P, _P, _P],
+    "mf_ilu_pattern": [_P, _P, _P, _P],
+    "mf_ilu_numeric": [_P, _P, _I32, _I32, _D, _D, _I32, _I32, _P],
+    "mf_ilu_export": [_P, _P],
+    "mf_ilu_trsv": [_P, _I32, _I32, _D, _P, _P, _I32, _P],
+    "mf_ilu_apply": [_P, _I32, _D, _P, _P, _I32, _P],
+    "mf_ilu_free": [_P],
     "mf_factor_set_wait_limit": [_P, _I32],
     "mf_factor_solve_work_bytes": [_P, _P],
 }
@@ -521,3 +529,70 @@ def mf_server_free(sv):
 def exported_symbols():
     """Names of the C entry points this binding wraps plus the error helpers."""
     return sorted(list(_SIGS) + ["mf_last_error_string", "mf_last_error_column"])
+
+
+# ---------------------------------------------------------------------------
+# FastILU / FastSpTRSV
+def mf_ilu_symbolic(h, rowptr, colind, level):
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().mf_ilu_symbolic(h, len(rp) - 1, _ptr(rp), _ptr(ci), level, ctypes.byref(out)))
+    return out
+
+
+def mf_ilu_info(ilu):
+    n, nnz = _I64(0), _I64(0)
+    _check(lib().mf_ilu_info(ilu, ctypes.byref(n), ctypes.byref(nnz)))
+    return int(n.value), int(nnz.value)
+
+
+def mf_ilu_pattern(ilu):
+    n, nnz = mf_ilu_info(ilu)
+    Sp = np.empty(n + 1, dtype=np.int64)
+    Sj = np.empty(nnz, dtype=np.int32)
+    Sl = np.empty(nnz, dtype=np.int32)
+    _check(lib().mf_ilu_pattern(ilu, _ptr(Sp), _ptr(Sj), _ptr(Sl)))
+    return Sp, Sj, Sl
+
+
+def mf_ilu_numeric(ilu, values, sweeps=2, omega=1.0, shift=0.0, warmup=False, in_place=False,
+                   stream=None):
+    dev = 1 if _is_device(values) else 0
+    v = values if dev else np.ascontiguousarray(values, dtype=np.float64)
+    if dev and stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    _check(lib().mf_ilu_numeric(ilu, _ptr(v), dev, sweeps, omega, shift, 1 if warmup else 0,
+                                1 if in_place else 0, _stream(stream)))
+
+
+def mf_ilu_export(ilu):
+    _, nnz = mf_ilu_info(ilu)
+    out = np.empty(nnz, dtype=np.float64)
+    _check(lib().mf_ilu_export(ilu, _ptr(out)))
+    return out
+
+
+def _ilu_vec(ilu, fn, b, x, stream, *args):
+    dev = 1 if _is_device(b) else 0
+    if x is None:
+        x = _alloc_like(b, dev) if dev else np.empty(len(b))
+    bb = b if dev else np.ascontiguousarray(b, dtype=np.float64)
+    if dev and stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    _check(fn(ilu, *args, _ptr(bb), _ptr(x), dev, _stream(stream)))
+    return x
+
+
+def mf_ilu_trsv(ilu, b, upper, sweeps, omega=1.0, x=None, stream=None):
+    return _ilu_vec(ilu, lib().mf_ilu_trsv, b, x, stream, 1 if upper else 0, sweeps, omega)
+
+
+def mf_ilu_apply(ilu, b, sweeps, omega=1.0, x=None, stream=None):
+    return _ilu_vec(ilu, lib().mf_ilu_apply, b, x, stream, sweeps, omega)
+
+
+def mf_ilu_free(ilu):
+    _check(lib().mf_ilu_free(ilu))

@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libmfchol.so")
 SOURCES = ["symbolic.cpp", "symbolic_io.cpp", "capi.cpp", "factor_kernels.cu", "solve_kernels.cu", "noalloc.cu", "factor_tc.cu",
-           "serve.cpp", "diag.cu"]
-HEADERS = ["mf_internal.h", "kernels.h"]
+           "serve.cpp", "diag.cu", "ilu.cpp", "ilu_kernels.cu"]
+HEADERS = ["mf_internal.h", "kernels.h", "ilu.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr"]
