@@ -103,6 +103,14 @@ typedef struct mf_options {
                                a value q >= 2 takes fronts of k+m <= q (at
                                most small_front_max); 0: one launch per level
                                and size class.  Fixed at symbolic analysis. */
+  int32_t update_tile[4];   /* trailing update of the large fronts per front
+                               size bucket (k+m <= 512, <= 2048, <= 8192,
+                               larger): 0 default (FP32 with tc: tcgen05
+                               128 x 128 tiles; otherwise FMA 64 x 64), 1 FMA
+                               64 x 64, 2 FMA 128 x 128, 3 tcgen05 128 x 128
+                               (FP32 with tc; FMA 64 x 64 otherwise), 4 FMA
+                               32 x 32.  mf_autotune picks them.  Fixed at
+                               symbolic analysis. */
 } mf_options;
 
 /* Summary of a symbolic analysis. */
@@ -214,6 +222,10 @@ int mf_symbolic_load(mf_handle* h, const char* path, mf_symbolic** s);
  * counterpart. */
 int mf_symbolic_check(const mf_symbolic* s);
 
+/* The options the analysis was made with (from mf_create, or the tuned ones
+ * mf_autotune returned); kept by mf_symbolic_save / mf_symbolic_load. */
+int mf_symbolic_options(const mf_symbolic* s, mf_options* opt);
+
 int mf_symbolic_free(mf_symbolic* s);
 int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info);
 /* parent[j] of the column elimination tree (-1 for roots), n entries. */
@@ -234,13 +246,22 @@ int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent,
                                int32_t* level);
 
 /* Autotuner (no paper counterpart; the paper tunes by hand).  Times the
- * numeric factorization of the given matrix and values in precision prec
- * for every combination of: relaxed amalgamation on/off, small-front limit
- * 32/64/128 (which fronts go to the one-CTA kernel vs the tiled kernels)
- * and, for MF_FP32, tensor-core or FMA trailing updates.  Each candidate is
- * factored once to warm up, then `reps` times (CUDA events, the factor's
- * own graph).  *best receives h's options with the fastest combination and
- * *best_ms its mean time.  Values: host or device pointer as
+ * numeric factorization of the given matrix and values in precision prec,
+ * each candidate factored once to warm up, then `reps` times (CUDA events,
+ * the factor's own graph):
+ *   1. relaxed amalgamation on/off x small-front limit 32/64/128 x the
+ *      small-front queue on/off, with the default trailing updates;
+ *   2. then, for each front-size bucket that holds large fronts (largest
+ *      bucket first, the others fixed), the trailing-update tile
+ *      (update_tile: FMA 64 / 32 / 128 for FP64 and FP32 without tensor
+ *      cores; tcgen05 128 / FMA 64 / FMA 128 for FP32 with them).
+ * *best receives h's options with the fastest choices and *best_ms its mean
+ * time.  Results are cached for the life of the process under a hash of
+ * the pattern, the ordering, prec, reps, h's solve variant / tensor-core /
+ * graph options and the device: a second call on the same pattern returns
+ * the cached choice without factoring.  An analysis made with the returned
+ * options records them, and mf_symbolic_save / _load keep them
+ * (mf_symbolic_options).  Values: host or device pointer as
  * values_on_device says.  Errors as mf_symbolic_analyze / mf_factor_*. */
 int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr,
                 const int32_t* colind, const int32_t* perm,

@@ -32,7 +32,7 @@ _D = ctypes.c_double
 class mf_options(ctypes.Structure):
     _fields_ = [("small_front_max", _I32), ("use_graphs", _I32), ("profile", _I32),
                 ("relax", _I32), ("budget_bytes", _I64), ("tc", _I32), ("sptrsv", _I32),
-                ("small_queue", _I32)]
+                ("small_queue", _I32), ("update_tile", _I32 * 4)]
 
 
 class mf_symbolic_info(ctypes.Structure):
@@ -102,6 +102,7 @@ _SIGS = {
     "mf_factor_export_columns": [_P, _I64, _I64, _P],
     "mf_diag_fp64_peak": [_I32, _P, _P],
     "mf_diag_small_queue": [_P, _I32, _P],
+    "mf_symbolic_options": [_P, _P],
     "mf_ilu_symbolic": [_P, _I64, _P, _P, _I32, _P],
     "mf_ilu_info": [_P, _P, _P],
     "mf_ilu_pattern": [_P, _P, _P, _P],
@@ -596,3 +597,10 @@ def mf_ilu_apply(ilu, b, sweeps, omega=1.0, x=None, stream=None):
 
 def mf_ilu_free(ilu):
     _check(lib().mf_ilu_free(ilu))
+
+
+def mf_symbolic_options(s):
+    """The options the analysis was made with (mf_options)."""
+    o = mf_options()
+    _check(lib().mf_symbolic_options(s, ctypes.byref(o)))
+    return o

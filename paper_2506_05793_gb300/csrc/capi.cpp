@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <memory>
 #include <new>
 #include <string>
@@ -274,12 +275,14 @@ static int analyze_common(mf_handle* h, int64_t n, const int64_t* rowptr,
   std::string err;
   int rc;
   S->relax = h->opt.relax ? 1 : 0;
+  S->opt_used = h->opt;
   S->keep_inv = h->opt.sptrsv >= 2;
   S->pinv = h->opt.sptrsv >= 3;
   S->v4 = h->opt.sptrsv == 4;
   try {
     rc = mf::analyze(*S, n, rowptr, colind, perm, node_of, err);
-    if (rc == MF_OK) mf::build_schedules(*S, h->opt.small_front_max, h->opt.small_queue);
+    if (rc == MF_OK)
+      mf::build_schedules(*S, h->opt.small_front_max, h->opt.small_queue, h->opt.update_tile);
   } catch (const std::bad_alloc&) {
     rc = MF_ERR_OOM;
     err = "host allocation failed";
@@ -819,75 +822,173 @@ int mf_diag_fp64_peak(int32_t kind, void* stream, double* tflops) {
 
 }  // extern "C"
 
+namespace {
+
+// Results of mf_autotune, keyed by a 64-bit FNV-1a hash of the pattern, the
+// ordering, the precision, the repetitions, the options that shape the
+// search and the device (SM count and compute capability), for the life of
+// the process.  A repeated call on the same pattern returns at once.
+struct TuneResult {
+  mf_options opt;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<uint64_t, TuneResult> g_tune_cache;
+
+uint64_t fnv(uint64_t h, const void* p, size_t bytes) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
 int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* colind,
                 const int32_t* perm, const double* values, int32_t values_on_device, int32_t prec,
                 int32_t reps, mf_options* best, double* best_ms) {
-  if (!h || !best || !best_ms || reps < 1) return set_error(MF_ERR_INVALID, "invalid autotune arguments");
+  if (!h || !best || !best_ms || reps < 1 || !rowptr || n < 0)
+    return set_error(MF_ERR_INVALID, "invalid autotune arguments");
   if (prec != MF_FP64 && prec != MF_FP32) return set_error(MF_ERR_INVALID, "bad precision");
   *best = h->opt;
   *best_ms = -1.0;
+  int dev = 0, sms = 0, ccmaj = 0, ccmin = 0;
+  MF_CK(cudaGetDevice(&dev));
+  MF_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  MF_CK(cudaDeviceGetAttribute(&ccmaj, cudaDevAttrComputeCapabilityMajor, dev));
+  MF_CK(cudaDeviceGetAttribute(&ccmin, cudaDevAttrComputeCapabilityMinor, dev));
+  uint64_t key = 1469598103934665603ull;
+  key = fnv(key, &n, sizeof(n));
+  key = fnv(key, rowptr, (n + 1) * sizeof(int64_t));
+  if (rowptr[n] > 0) key = fnv(key, colind, rowptr[n] * sizeof(int32_t));
+  if (perm) key = fnv(key, perm, n * sizeof(int32_t));
+  const int32_t shape[8] = {prec, reps, h->opt.sptrsv, h->opt.tc, h->opt.use_graphs, sms, ccmaj, ccmin};
+  key = fnv(key, shape, sizeof(shape));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto hit = g_tune_cache.find(key);
+    if (hit != g_tune_cache.end()) {
+      *best = hit->second.opt;
+      best->budget_bytes = h->opt.budget_bytes;
+      best->profile = h->opt.profile;
+      *best_ms = hit->second.ms;
+      return MF_OK;
+    }
+  }
   cudaStream_t st = nullptr;
   MF_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   MF_CK(cudaEventCreate(&e0));
   MF_CK(cudaEventCreate(&e1));
   int rc = MF_OK;
-  const int smalls[3] = {mf::kSmallMax, 64, 32};
-  for (int relax = 1; relax >= 0 && rc == MF_OK; --relax) {
+  const bool tc_on = prec == MF_FP32 && h->opt.tc;
+  // one candidate: analysis with its options (reused while relax is the
+  // same), then a warm-up factorization and `reps` timed ones
+  mf_symbolic* S = nullptr;
+  int S_relax = -1;
+  auto measure = [&](const mf_options& o, double* ms) -> int {
     mf_handle tmp = *h;
-    tmp.opt.relax = relax;
+    tmp.opt = o;
     tmp.opt.profile = 0;
     tmp.opt.use_graphs = 1;
-    mf_symbolic* S = nullptr;
-    rc = mf_symbolic_analyze(&tmp, n, rowptr, colind, perm, &S);
-    if (rc != MF_OK) break;
-    for (int si = 0; si < 3 && rc == MF_OK; ++si) {
+    if (!S || S_relax != o.relax) {
+      if (S) mf_symbolic_free(S);
+      S = nullptr;
+      int r = mf_symbolic_analyze(&tmp, n, rowptr, colind, perm, &S);
+      if (r != MF_OK) return r;
+      S_relax = o.relax;
+    } else {
       try {
-        mf::build_schedules(*S, smalls[si], tmp.opt.small_queue);
+        mf::build_schedules(*S, o.small_front_max, o.small_queue, o.update_tile);
       } catch (const std::bad_alloc&) {
-        rc = set_error(MF_ERR_OOM, "host allocation failed");
-        break;
+        return set_error(MF_ERR_OOM, "host allocation failed");
       }
-      {
-        std::lock_guard<std::mutex> lk(S->dev_mu);  // schedules changed: new device copy
-        S->dev.reset();
-        S->dev_device = -1;
-      }
-      const int ntc = prec == MF_FP32 ? 2 : 1;
-      for (int tci = 0; tci < ntc && rc == MF_OK; ++tci) {
-        tmp.opt.small_front_max = smalls[si];
-        tmp.opt.tc = prec == MF_FP32 ? 1 - tci : h->opt.tc;
-        mf_factor* f = nullptr;
-        rc = mf_factor_create(&tmp, S, prec, &f);
-        if (rc != MF_OK) break;
-        rc = mf_factor_numeric(f, values, values_on_device, st, 0);
-        float ms = 0.f;
-        if (rc == MF_OK) {
-          cudaEventRecord(e0, st);
-          for (int r = 0; r < reps && rc == MF_OK; ++r) rc = mf_factor_numeric(f, values, values_on_device, st, 1);
-          cudaEventRecord(e1, st);
-          if (rc == MF_OK) rc = mf_factor_check(f, st);
-          if (rc == MF_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-            rc = set_error(MF_ERR_CUDA, "cudaEventElapsedTime failed");
-        }
-        mf_factor_free(f);
-        if (rc != MF_OK) break;
-        const double mean = (double)ms / reps;
-        if (*best_ms < 0 || mean < *best_ms) {
-          *best_ms = mean;
-          *best = h->opt;
-          best->relax = relax;
-          best->small_front_max = smalls[si];
-          best->tc = tmp.opt.tc;
-        }
-      }
+      S->opt_used = tmp.opt;
+      std::lock_guard<std::mutex> lk(S->dev_mu);  // schedules changed: new device copy
+      S->dev.reset();
+      S->dev_device = -1;
     }
-    mf_symbolic_free(S);
+    mf_factor* f = nullptr;
+    int r = mf_factor_create(&tmp, S, prec, &f);
+    if (r != MF_OK) return r;
+    r = mf_factor_numeric(f, values, values_on_device, st, 0);
+    float t = 0.f;
+    if (r == MF_OK) {
+      cudaEventRecord(e0, st);
+      for (int i = 0; i < reps && r == MF_OK; ++i) r = mf_factor_numeric(f, values, values_on_device, st, 1);
+      cudaEventRecord(e1, st);
+      if (r == MF_OK) r = mf_factor_check(f, st);
+      if (r == MF_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+        r = set_error(MF_ERR_CUDA, "cudaEventElapsedTime failed");
+    }
+    mf_factor_free(f);
+    *ms = (double)t / reps;
+    return r;
+  };
+  mf_options cur = h->opt;
+  for (int b = 0; b < 4; ++b) cur.update_tile[b] = 0;
+  double cur_ms = -1.0;
+  auto consider = [&](const mf_options& o) {
+    double ms = 0.0;
+    const int r = measure(o, &ms);
+    if (r == MF_OK && (cur_ms < 0 || ms < cur_ms)) {
+      cur = o;
+      cur_ms = ms;
+    }
+    return r;
+  };
+  // 1) relaxation x small-front limit x queue, default tiles
+  const int smalls[3] = {mf::kSmallMax, 64, 32};
+  for (int relax = 1; relax >= 0 && rc == MF_OK; --relax)
+    for (int si = 0; si < 3 && rc == MF_OK; ++si)
+      for (int q = 1; q >= 0 && rc == MF_OK; --q) {
+        mf_options o = cur;
+        o.relax = relax;
+        o.small_front_max = smalls[si];
+        o.small_queue = q;
+        rc = consider(o);
+      }
+  // 2) per front-size bucket, largest first: the trailing-update tile of
+  // the buckets that hold large fronts (coordinate descent)
+  if (rc == MF_OK) {
+    mf_options o = cur;
+    double ms = 0.0;
+    rc = measure(o, &ms);  // the winner's analysis, for its buckets
+    bool present[4] = {false, false, false, false};
+    if (rc == MF_OK)
+      for (const mf::SnInfo& f : S->sn)
+        if (f.k + f.m > cur.small_front_max) present[mf::tile_bucket(f.k + f.m)] = true;
+    const int cand_tc[3] = {3, 1, 2}, cand_fma[3] = {1, 4, 2};
+    const int* cand = tc_on ? cand_tc : cand_fma;
+    for (int b = 3; b >= 0 && rc == MF_OK; --b) {
+      if (!present[b]) continue;
+      for (int c = 0; c < 3 && rc == MF_OK; ++c) {
+        mf_options t = cur;
+        t.update_tile[b] = cand[c];
+        if (cand[c] == (cur.update_tile[b] ? cur.update_tile[b] : cand[0])) continue;
+        rc = consider(t);
+      }
+      if (rc == MF_OK && cur.update_tile[b] == 0) cur.update_tile[b] = cand[0];
+    }
   }
+  if (S) mf_symbolic_free(S);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamDestroy(st);
-  return rc;
+  if (rc != MF_OK) return rc;
+  *best = cur;
+  *best_ms = cur_ms;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {cur, cur_ms};
+  return MF_OK;
+}
+
+int mf_symbolic_options(const mf_symbolic* s, mf_options* opt) {
+  if (!s || !opt) return set_error(MF_ERR_INVALID, "NULL argument");
+  *opt = s->opt_used;
+  return MF_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -581,74 +581,84 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
 }
 
 // ---------------------------------------------------------------------------
-// Large fronts, panel step t: trailing lower update of the kTile x kTile
-// tile (I, J), I >= J:  C -= P_I P_J^T with P the b panel columns.
+// Large fronts, panel step t: trailing lower update of the TILE x TILE tile
+// (I, J), I >= J:  C -= P_I P_J^T with P the b panel columns.  256 threads,
+// thread (tr, tc) of a 16 x 16 grid holds the (TILE/16)^2 entries
+// (tr + 16 i, tc + 16 j); the tile is a per-front-size choice of the
+// schedule (32, 64 or 128).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int TILE>
 constexpr size_t syrk_smem() {
-  return (size_t)2 * kNB * kTile * sizeof(T);
+  return (size_t)2 * kNB * TILE * sizeof(T);
 }
 
-template <typename T>
+template <typename T, int TILE>
 __global__ void __launch_bounds__(256) k_syrk(FD<T> d, int64_t item_off) {
+  constexpr int R = TILE / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*As)[kTile] = reinterpret_cast<T(*)[kTile]>(smem_raw);
-  T(*Bs)[kTile] = reinterpret_cast<T(*)[kTile]>(smem_raw + (size_t)kNB * kTile * sizeof(T));
+  T(*As)[TILE] = reinterpret_cast<T(*)[TILE]>(smem_raw);
+  T(*Bs)[TILE] = reinterpret_cast<T(*)[TILE]>(smem_raw + (size_t)kNB * TILE * sizeof(T));
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int nf = f.k + f.m;
   const int c0 = it.t * kNB;
   const int b = min(kNB, f.k - c0);
   const int p0 = c0 + b;
-  const int rI = p0 + it.a * kTile, rJ = p0 + it.b * kTile;
+  const int rI = p0 + it.a * TILE, rJ = p0 + it.b * TILE;
   const int tid = threadIdx.x;
   const T* P = d.L + f.Loff + (int64_t)c0 * nf;
-  for (int idx = tid; idx < b * kTile; idx += blockDim.x) {
-    const int q = idx / kTile, r = idx % kTile;
+  for (int idx = tid; idx < b * TILE; idx += blockDim.x) {
+    const int q = idx / TILE, r = idx % TILE;
     const T* col = P + (int64_t)q * nf;
     As[q][r] = (rI + r < nf) ? col[rI + r] : T(0);
     Bs[q][r] = (rJ + r < nf) ? col[rJ + r] : T(0);
   }
   __syncthreads();
   const int tr = tid & 15, tc = tid >> 4;
-  T acc[4][4];
+  T acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < R; ++j) acc[i][j] = T(0);
   for (int q = 0; q < b; ++q) {
-    T a[4], bb[4];
+    T a[R], bb[R];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = As[q][tr + 16 * i];
+    for (int i = 0; i < R; ++i) a[i] = As[q][tr + 16 * i];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bb[j] = Bs[q][tc + 16 * j];
+    for (int j = 0; j < R; ++j) bb[j] = Bs[q][tc + 16 * j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < R; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+      for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
   }
-  // two-phase read-modify-write: all 16 loads in flight before any store
-  T* p[4][4];
-  T cur[4][4];
+  // two-phase read-modify-write: for tiles up to 64 all R^2 loads of the
+  // thread are in flight before any store; for 128 (64 values per thread)
+  // one column's R loads at a time, to stay within registers
+  constexpr int G = R <= 4 ? R : 1;  // columns per load/store group
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int c = rJ + tc + 16 * j;
-    T* col = c < nf ? front_col(d, f, c) : nullptr;
+  for (int j0 = 0; j0 < R; j0 += G) {
+    T* p[R][G];
+    T cur[R][G];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = rI + tr + 16 * i;
-      p[i][j] = (col && r < nf && r >= c) ? col + r : nullptr;
+    for (int jj = 0; jj < G; ++jj) {
+      const int c = rJ + tc + 16 * (j0 + jj);
+      T* col = c < nf ? front_col(d, f, c) : nullptr;
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const int r = rI + tr + 16 * i;
+        p[i][jj] = (col && r < nf && r >= c) ? col + r : nullptr;
+      }
     }
+#pragma unroll
+    for (int jj = 0; jj < G; ++jj)
+#pragma unroll
+      for (int i = 0; i < R; ++i) cur[i][jj] = p[i][jj] ? *p[i][jj] : T(0);
+#pragma unroll
+    for (int jj = 0; jj < G; ++jj)
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+        if (p[i][jj]) *p[i][jj] = cur[i][jj] - acc[i][j0 + jj];
   }
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) cur[i][j] = p[i][j] ? *p[i][j] : T(0);
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (p[i][j]) *p[i][j] = cur[i][j] - acc[i][j];
 }
 
 // ---------------------------------------------------------------------------
@@ -878,8 +888,14 @@ cudaError_t init_t() {
   e = cudaFuncSetAttribute(k_pinv_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)pinv_small_smem<T>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_syrk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)syrk_smem<T>());
+  e = cudaFuncSetAttribute(k_syrk<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)syrk_smem<T, 32>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_syrk<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)syrk_smem<T, 128>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_syrk<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)syrk_smem<T, 64>());
 }
 
 template <typename T>
@@ -913,7 +929,9 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
       k_trsm<T><<<grid, 256, trsm_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_SYRK:
-      k_syrk<T><<<grid, 256, syrk_smem<T>(), st>>>(d, L.item_off);
+      if (L.tile == 32) k_syrk<T, 32><<<grid, 256, syrk_smem<T, 32>(), st>>>(d, L.item_off);
+      else if (L.tile == 128) k_syrk<T, 128><<<grid, 256, syrk_smem<T, 128>(), st>>>(d, L.item_off);
+      else k_syrk<T, 64><<<grid, 256, syrk_smem<T, 64>(), st>>>(d, L.item_off);
       break;
     case K_SYRK_TC:
       return launch_syrk_tc(L, a, st);

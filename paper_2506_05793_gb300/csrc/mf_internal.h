@@ -88,6 +88,8 @@ struct Launch {
   int8_t side = 0;
   int8_t join = 0;
   int8_t area = 0;
+  // K_SYRK: square tile of the FMA trailing update (32, 64 or 128; 0 = 64)
+  uint8_t tile = 0;
 };
 
 // levels with at most this many large fronts factor with lookahead
@@ -116,6 +118,7 @@ struct mf_symbolic {
   // fronts: contiguous column ranges after relaxed amalgamation; every
   // numeric structure below (sn, rowidx, relmap, schedules) is per front
   int32_t relax = 1;
+  mf_options opt_used{};           // the options the analysis was made with
   std::vector<int32_t> front_ptr;  // nfronts + 1
   std::vector<int32_t> col2front;
   double front_flops = 0.0;        // sum over front columns of (rows)^2
@@ -180,7 +183,10 @@ namespace mf {
 // symbolic.cpp
 int analyze(mf_symbolic& S, int64_t n, const int64_t* rowptr, const int32_t* colind,
             const int32_t* perm, const int32_t* node_of, std::string& err);
-void build_schedules(mf_symbolic& S, int small_max, int small_queue);
+// update_tile: the per-front-size-bucket trailing-update choice (4 codes,
+// mf_options.update_tile) or nullptr for the defaults
+void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32_t* update_tile);
+int tile_bucket(int nf);
 int check_schedules(const mf_symbolic& S, std::string& err);
 void ensure_fundamental_rows(const mf_symbolic& S);
 // error reporting (capi.cpp)

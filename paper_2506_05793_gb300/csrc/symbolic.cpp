@@ -833,7 +833,11 @@ static void build_v4_solves(mf_symbolic& S, const std::vector<std::vector<int32_
 // fronts are batched one CTA each (grouped by size class), large fronts are
 // split into column chunks (assembly), panel steps (POTRF, TRSM) and trailing
 // tiles (SYRK), each batched over all large fronts of the level.
-void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
+// Front-size buckets of the per-bucket trailing-update choice (k + m of a
+// large front): <= 512, <= 2048, <= 8192, larger.
+int tile_bucket(int nf) { return nf <= 512 ? 0 : nf <= 2048 ? 1 : nf <= 8192 ? 2 : 3; }
+
+void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32_t* update_tile) {
   S.items.clear();
   S.arange.clear();
   S.fsched.clear();
@@ -852,9 +856,10 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
   const int classes[3] = {32, 64, 128};
   auto add = [&](std::vector<Launch>& sched, int32_t kind, int32_t lev, int32_t param,
                  const std::vector<Item>& it, double flops, int side = 0, int join = 0,
-                 int area = 0) {
+                 int area = 0, int tile = 0) {
     if (it.empty()) return;
     Launch L;
+    L.tile = (uint8_t)tile;
     L.kind = kind;
     L.level = lev;
     L.count = (int32_t)it.size();
@@ -975,9 +980,24 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
         S.ninv += (S.sn[s].k + kNB - 1) / kNB;
       }
     std::unordered_map<int32_t, double> fpair;  // panel t's deferred flops
+    // per front: the FMA tile of the FP64 / FP32-FMA schedule and, in the
+    // tensor-core schedule, tensor cores or that FMA tile (update_tile code
+    // of the front's size bucket: 0 default, 1 FMA 64, 2 FMA 128, 3 tensor
+    // cores (FMA 64 where there are none), 4 FMA 32)
+    auto code_of = [&](int32_t s) {
+      const int c = update_tile ? update_tile[tile_bucket(S.sn[s].k + S.sn[s].m)] : 0;
+      return c < 0 || c > 4 ? 0 : c;
+    };
+    auto fma_tile = [&](int32_t s) {
+      const int c = code_of(s);
+      return c == 2 ? 128 : c == 4 ? 32 : 64;
+    };
+    auto uses_tc = [&](int32_t s) { return code_of(s) == 0 || code_of(s) == 3; };
     for (int32_t t = 0; t < T; ++t) {
-      std::vector<Item> ip, it3, is, itc;
-      double fp = 0, ft = 0, fs = 0, fstc = 0;
+      std::vector<Item> ip, it3, itc;
+      std::vector<Item> is[3], isf[3];  // FMA tiles 32 / 64 / 128: FP64 and FP32-TC schedules
+      double fp = 0, ft = 0, fs[3] = {0, 0, 0}, fsf[3] = {0, 0, 0}, fstc = 0;
+      auto tix = [](int T) { return T == 32 ? 0 : T == 64 ? 1 : 2; };
       bool normal_tc = false;  // a tensor-core front takes a plain update this step
       for (size_t gi = 0; gi < G.size(); ++gi) {
         const int32_t s = G[gi];
@@ -991,16 +1011,23 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
         fp += (double)b * b * b / 3.0;
         for (int r0 = p0; r0 < nf; r0 += kTrsmRows) it3.push_back({s, t, r0, lpos});
         ft += (double)(nf - p0) * b * b;
-        const int nt = (nf - p0 + kTile - 1) / kTile;
+        const int Tf = fma_tile(s), x = tix(Tf);
+        const int nt = (nf - p0 + Tf - 1) / Tf;
         for (int I = 0; I < nt; ++I)
-          for (int J = 0; J <= I; ++J) is.push_back({s, t, I, J});
+          for (int J = 0; J <= I; ++J) is[x].push_back({s, t, I, J});
+        const double full = (double)(nf - p0) * (double)(nf - p0 + 1) * b;
+        fs[x] += full;
+        if (!uses_tc(s)) {  // the tensor-core schedule takes the FMA tile too
+          isf[x].insert(isf[x].end(), is[x].end() - (int64_t)nt * (nt + 1) / 2, is[x].end());
+          fsf[x] += full;
+          continue;
+        }
         // tensor-core path: panels are paired.  Even step t with a next
         // panel: update only the next panel's 64 columns (strip, mode 1);
         // odd step t: update everything beyond panel t with both panels at
         // once (K = 128, mode 2, item carries the first panel t - 1).  An
         // even last step updates its trailing matrix alone (mode 0).
         const int nt2 = (nf - p0 + kTcTile - 1) / kTcTile;
-        const double full = (double)(nf - p0) * (double)(nf - p0 + 1) * b;
         if ((t & 1) == 0 && (t + 1) * kNB < k) {
           const int b1 = std::min(kNB, k - (t + 1) * kNB);
           for (int I = 0; I < nt2; ++I) itc.push_back({s, t | (1 << 24), I, 0});
@@ -1016,14 +1043,17 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
             for (int J = 0; J <= I; ++J) itc.push_back({s, (t - 1) | (2 << 24), I, J});
           fstc += full + fpair[s];
         }
-        fs += full;
       }
+      static const int kTiles[3] = {32, 64, 128};
       add(S.fsched, K_POTRF, lev, t, ip, fp);
       add(S.fsched, K_TRSM, lev, t, it3, ft);
       add(S.fsched_tc, K_POTRF, lev, t, ip, fp, 0, 0, la);
       add(S.fsched_tc, K_TRSM, lev, t, it3, ft, 0, 0, la);
       if (!la) {
-        add(S.fsched, K_SYRK, lev, t, is, fs);
+        for (int x = 0; x < 3; ++x) {
+          add(S.fsched, K_SYRK, lev, t, is[x], fs[x], 0, 0, 0, kTiles[x]);
+          add(S.fsched_tc, K_SYRK, lev, t, isf[x], fsf[x], 0, 0, 0, kTiles[x]);
+        }
         add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fstc);
         continue;
       }
@@ -1034,12 +1064,18 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue) {
       auto split_j0 = [](const std::vector<Item>& v, std::vector<Item>& a, std::vector<Item>& b) {
         for (const Item& x : v) (x.b == 0 ? a : b).push_back(x);
       };
-      {
+      // FMA tiles: the tile columns covering the next panel (J T < 64) on the
+      // critical stream, the rest on the side stream
+      auto fma_split = [&](std::vector<Launch>& sched, const std::vector<Item>& v, double fl, int T) {
         std::vector<Item> a, b;
-        split_j0(is, a, b);
-        const double fa = is.empty() ? 0.0 : fs * (double)a.size() / (double)is.size();
-        add(S.fsched, K_SYRK, lev, t, a, fa, 0, 1);
-        add(S.fsched, K_SYRK, lev, t, b, fs - fa, 1, 0);
+        for (const Item& x : v) (x.b * T < kNB ? a : b).push_back(x);
+        const double fa = v.empty() ? 0.0 : fl * (double)a.size() / (double)v.size();
+        add(sched, K_SYRK, lev, t, a, fa, 0, 1, 0, T);
+        add(sched, K_SYRK, lev, t, b, fl - fa, 1, 0, 0, T);
+      };
+      for (int x = 0; x < 3; ++x) {
+        fma_split(S.fsched, is[x], fs[x], kTiles[x]);
+        fma_split(S.fsched_tc, isf[x], fsf[x], kTiles[x]);
       }
       if ((t & 1) == 1) {  // pair step
         std::vector<Item> a, b;
@@ -1296,6 +1332,7 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
     std::vector<std::vector<int64_t>> syrk_tiles(ns);
     std::vector<std::vector<std::vector<std::pair<int, int>>>> trsm(ns);
     std::vector<std::vector<int>> trsm_at(ns), syrk0_at(ns);
+    std::vector<int> syrk_tile(ns, 0);  // FMA tile of a front (0: none seen)
     int32_t last_level = -1;
     for (size_t li = 0; li < sched.size(); ++li) {
       const Launch& L = sched[li];
@@ -1356,12 +1393,17 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
             break;
           case K_SYRK: {
             const int t = it.t;
+            const int Tl = L.tile ? L.tile : kTile;
+            if (Tl != 32 && Tl != 64 && Tl != 128) return fail("SYRK tile size");
+            if (syrk_tile[it.s] == 0) syrk_tile[it.s] = Tl;
+            if (syrk_tile[it.s] != Tl) return fail("front with two SYRK tile sizes");
             const int p0 = t * kNB + std::min(kNB, f.k - t * kNB);
-            const int nt = (nf - p0 + kTile - 1) / kTile;
+            const int nt = (nf - p0 + Tl - 1) / Tl;
             if (t != L.param || t < 0 || t >= nb || it.b < 0 || it.b > it.a || it.a >= nt)
               return fail("SYRK tile out of range");
             syrk_tiles[it.s].push_back(((int64_t)t << 40) | ((int64_t)it.a << 20) | it.b);
-            if (it.b == 0) syrk0_at[it.s][t] = (int)li;
+            // the tile columns covering the next panel
+            if (it.b * Tl < kNB) syrk0_at[it.s][t] = (int)li;
             break;
           }
           case K_SYRK_TC:
@@ -1385,10 +1427,13 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
         if (potrf[s][t] < 0) return fail("panel without POTRF");
         const int p0 = t * kNB + std::min(kNB, f.k - t * kNB);
         if (!tiles(trsm[s][t], p0, nf, kTrsmRows)) return fail("TRSM rows do not tile the panel");
-        const int64_t nt = (nf - p0 + kTile - 1) / kTile;
+        const int Tl = syrk_tile[s] ? syrk_tile[s] : kTile;
+        const int64_t nt = (nf - p0 + Tl - 1) / Tl;
         want += nt * (nt + 1) / 2;
       }
-      if (!tc) {
+      // every front of the FMA schedule, and the FMA fronts of the
+      // tensor-core schedule, take each trailing tile exactly once
+      if (!tc || syrk_tile[s]) {
         std::vector<int64_t>& v = syrk_tiles[s];
         std::sort(v.begin(), v.end());
         if (std::adjacent_find(v.begin(), v.end()) != v.end() || (int64_t)v.size() != want)

@@ -22,7 +22,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'M', 'F', 'S', 'Y', 'M', 'B', 'O', 'L'};
-constexpr uint32_t kVersion = 3;
+constexpr uint32_t kVersion = 4;
 constexpr uint64_t kFnvOffset = 1469598103934665603ull;
 constexpr uint64_t kFnvPrime = 1099511628211ull;
 
@@ -171,6 +171,15 @@ void members(IO& io, S& s) {
   io(s.ginv_src);
   io(s.v4);
   io(s.v4_grp);
+  io(s.opt_used.small_front_max);
+  io(s.opt_used.use_graphs);
+  io(s.opt_used.profile);
+  io(s.opt_used.relax);
+  io(s.opt_used.budget_bytes);
+  io(s.opt_used.tc);
+  io(s.opt_used.sptrsv);
+  io(s.opt_used.small_queue);
+  for (int b = 0; b < 4; ++b) io(s.opt_used.update_tile[b]);
 }
 
 // Sizes that the rest of the library relies on without checking again.

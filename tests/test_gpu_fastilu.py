@@ -65,7 +65,7 @@ def test_sweeps_match_oracle(mf, orc, N, K, sweeps, omega, shift, warmup):
 @pytest.mark.parametrize("K", [0, 2])
 def test_in_place_sweeps_reach_the_incomplete_factors(mf, orc, K):
     rp, ci, v = gen.elasticity_3d(8)
-    h, ilu, lu = run(mf, rp, ci, v, K, sweeps=40, in_place=True)
+    h, ilu, lu = run(mf, rp, ci, v, K, sweeps=100, in_place=True)
     try:
         pat = orc.iluk_pattern(rp, ci, K)
         ex = orc.ilu_exact(pat, pat.values_of(rp, ci, v))

@@ -488,3 +488,50 @@ def test_small_queue_holds_the_small_subforests(mf, orc):
         mf.mf_symbolic_check(s)
         mf.mf_symbolic_free(s)
         mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("tiles", [(0, 0, 0, 0), (4, 1, 2, 2), (2, 2, 2, 2), (1, 3, 4, 3),
+                                   (4, 4, 4, 4)])
+@pytest.mark.parametrize("variant", [2, 4])
+def test_schedules_with_update_tiles(mf, tiles, variant):
+    """Every per-bucket trailing-update choice gives schedules that cover
+    each front's tiles exactly once (FMA 32 / 64 / 128 and tensor cores,
+    mixed within a level), with and without the lookahead levels."""
+    opt = mf.mf_options_default()
+    opt.sptrsv = variant
+    for b in range(4):
+        opt.update_tile[b] = tiles[b]
+    h = mf.mf_create(opt)
+    try:
+        rp, ci, v, perm, _ = gen.config3(24)
+        s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+        mf.mf_symbolic_check(s)
+        assert list(mf.mf_symbolic_options(s).update_tile) == list(tiles)
+        mf.mf_symbolic_free(s)
+        mats, _ = gen.box_batch(16, 8, 30, seed=4)
+        s = mf.mf_symbolic_analyze_batch(h, [(a, b, p) for a, b, c, p in mats])
+        mf.mf_symbolic_check(s)
+        mf.mf_symbolic_free(s)
+    finally:
+        mf.mf_destroy(h)
+
+
+def test_saved_analysis_keeps_its_options(mf, tmp_path):
+    opt = mf.mf_options_default()
+    opt.update_tile[2] = 2
+    opt.small_queue = 32
+    opt.relax = 0
+    h = mf.mf_create(opt)
+    rp, ci, v, perm, _ = gen.config3(10)
+    s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+    path = str(tmp_path / "o.sym")
+    mf.mf_symbolic_save(s, path)
+    t = mf.mf_symbolic_load(h, path)
+    a, b = mf.mf_symbolic_options(s), mf.mf_symbolic_options(t)
+    for name, _ in mf.mf_options._fields_:
+        assert list(getattr(a, name)) == list(getattr(b, name)) if name == "update_tile" \
+            else getattr(a, name) == getattr(b, name)
+    assert b.update_tile[2] == 2 and b.small_queue == 32 and b.relax == 0
+    mf.mf_symbolic_free(s)
+    mf.mf_symbolic_free(t)
+    mf.mf_destroy(h)
