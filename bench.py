@@ -79,6 +79,9 @@ def parse():
                         "3 partitioned inverse (one product per level; computed inside the "
                         "timed factorization), 4 partitioned inverse of every front as one "
                         "sparse product per level and sweep")
+    p.add_argument("--tile", type=int, default=0,
+                   help="trailing-update tile of every front-size bucket (mf_options.update_tile "
+                        "code: 0 default, 1 FMA 64, 2 FMA 128, 3 tcgen05 128, 4 FMA 32)")
     p.add_argument("--small-queue", type=int, default=1,
                    help="small fronts in one persistent launch: 0 off, 1 fronts of k+m <= 64 "
                         "(default), q >= 2 fronts of k+m <= q")
@@ -483,11 +486,14 @@ def main():
         opt, tuned_ms = mf.mf_autotune(h0, rp, ci, perm, v, prec=prec, reps=2)
         mf.mf_destroy(h0)
         tuned = {"relax": opt.relax, "small_front_max": opt.small_front_max, "tc": opt.tc,
+                 "small_queue": opt.small_queue, "update_tile": list(opt.update_tile),
                  "ms": tuned_ms}
     opt.profile = 1  # per-launch CUDA events: per-kernel-kind device time
     opt.sptrsv = args.sptrsv
     if not args.autotune:
         opt.small_queue = args.small_queue
+        for bk in range(4):
+            opt.update_tile[bk] = args.tile
     h = mf.mf_create(opt)
     t0 = time.perf_counter()
     s = mf.mf_symbolic_analyze(h, rp, ci, perm)

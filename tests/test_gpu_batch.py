@@ -68,23 +68,66 @@ def test_batch_factor_equals_individual(mf, orc, prec):
     mf.mf_destroy(h)
 
 
-def test_autotune_returns_working_options(mf, orc):
-    rp, ci, v, perm, _ = gen.config3(16)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotune_returns_working_options_and_caches(mf, orc, prec):
+    """The tuned options (relaxation, small-front limit, queue and the
+    per-bucket trailing-update tiles) factor the matrix within the parity
+    bars; a second call on the same pattern is served from the cache (no
+    factorization: far faster); the analysis records the tuned tiles."""
+    import time
+    rp, ci, v, perm, _ = gen.config3(24)
     h = mf.mf_create()
-    best, ms = mf.mf_autotune(h, rp, ci, perm, v, prec=1, reps=1)
-    assert ms > 0
-    assert best.small_front_max in (32, 64, 128) and best.relax in (0, 1) and best.tc in (0, 1)
+    t0 = time.perf_counter()
+    best, ms = mf.mf_autotune(h, rp, ci, perm, v, prec=prec, reps=1)
+    t1 = time.perf_counter()
+    best2, ms2 = mf.mf_autotune(h, rp, ci, perm, v, prec=prec, reps=1)
+    t2 = time.perf_counter()
+    assert ms > 0 and ms2 == ms and list(best2.update_tile) == list(best.update_tile)
+    assert (t2 - t1) < 0.2 * (t1 - t0)
+    assert best.small_front_max in (32, 64, 128) and best.relax in (0, 1)
+    assert all(c in (0, 1, 2, 3, 4) for c in best.update_tile)
+    assert any(c != 0 for c in best.update_tile)  # buckets with large fronts were tuned
     h2 = mf.mf_create(best)
     s = mf.mf_symbolic_analyze(h2, rp, ci, perm)
-    f = mf.mf_factor_create(h2, s, 1)
+    assert list(mf.mf_symbolic_options(s).update_tile) == list(best.update_tile)
+    f = mf.mf_factor_create(h2, s, prec)
     mf.mf_factor_numeric(f, v)
     B = gen.rhs(len(rp) - 1, 1, seed=2)
-    X, rep = mf.mf_solve_refined(f, B, tol=1e-13)
+    if prec == 1:
+        X, rep = mf.mf_solve_refined(f, B, tol=1e-13)
+    else:
+        X = mf.mf_solve(f, B)
     assert orc.berr(rp, ci, v, X, B) <= 1e-13
     mf.mf_factor_free(f)
     mf.mf_symbolic_free(s)
     mf.mf_destroy(h2)
     mf.mf_destroy(h)
+
+
+@pytest.mark.parametrize("tiles", [(4, 4, 4, 4), (2, 2, 2, 2), (1, 1, 1, 1), (4, 2, 3, 1)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_update_tile_matches_oracle(mf, orc, tiles, prec):
+    """FMA 32 / 64 / 128 and tensor-core trailing updates, alone and mixed
+    per front-size bucket, against the oracle's factor."""
+    # fronts of up to about 600 rows: buckets 0 and 1
+    rp, ci, v = gen.q1_extruded(60, 40, 4, seed=2)
+    perm = gen.nd_perm((61, 41, 5), split_axes=(0, 1), dofs=2)
+    opt = mf.mf_options_default()
+    for b in range(4):
+        opt.update_tile[b] = tiles[b]
+    h = mf.mf_create(opt)
+    s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+    info = mf.mf_symbolic_get_info(s)
+    f = mf.mf_factor_create(h, s, prec)
+    try:
+        mf.mf_factor_numeric(f, v)
+        L = mf.mf_factor_export_L(f, info["nnz_L"])
+        F = orc.factor(rp, ci, v, perm)
+        assert orc.rel_fro(L, F.Lx) <= (1e-11 if prec == 0 else 5e-4)
+    finally:
+        mf.mf_factor_free(f)
+        mf.mf_symbolic_free(s)
+        mf.mf_destroy(h)
 
 
 @pytest.mark.parametrize("small_max", [32, 64])
