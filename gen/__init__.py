@@ -368,6 +368,31 @@ def elasticity_3d(N, E=1.0, nu=0.3):
     return _coo_to_csr(n, rows, cols, vals)
 
 
+def kkt_3d(nx, ny=None, nz=None, delta=1e-2, seed=0):
+    """Symmetric quasi-definite saddle-point matrix on an nx x ny x nz grid,
+    2 unknowns per node interleaved (dof 2 i: u_i, 2 i + 1: p_i):
+        [ K    B^T     ]
+        [ B   -delta I ],
+    K the 7-point Dirichlet Laplacian on u, B a node-local coupling of p_i
+    to u_i (weight U[1, 2]) and to the grid neighbours of node i (weights
+    -U[0.1, 0.3]), seeded.  Indefinite (n/2 negative eigenvalues) but
+    quasi-definite, so every symmetric permutation of it has an LDL^T
+    factorization with D diagonal."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    kp, kc, kv = laplacian_3d(nx, ny, nz)
+    nn = len(kp) - 1
+    krow = np.repeat(np.arange(nn, dtype=np.int64), np.diff(kp))
+    kcol = kc.astype(np.int64)
+    # B has the pattern of K: the diagonal and the neighbours
+    bval = np.where(krow == kcol, rng.uniform(1.0, 2.0, len(kv)), -rng.uniform(0.1, 0.3, len(kv)))
+    rows = np.concatenate([2 * krow, 2 * krow + 1, 2 * kcol, 2 * np.arange(nn) + 1])
+    cols = np.concatenate([2 * kcol, 2 * kcol, 2 * krow + 1, 2 * np.arange(nn) + 1])
+    vals = np.concatenate([kv, bval, bval, -delta * np.ones(nn)])
+    return _coo_to_csr(2 * nn, rows, cols, vals)
+
+
 # --------------------------------------------------------------------------
 # Geometric nested dissection
 # --------------------------------------------------------------------------

@@ -16,6 +16,8 @@ the three phases of the paper's Ax=b statement in Sec. 3):
 * ``factor``     -- left-looking column Cholesky, FP64 (C); optionally only the
   columns of a descendant-closed set (exact for those columns).
 * ``solve``      -- ``x = P^T L^{-T} L^{-1} P b`` (C).
+* ``factor_ldlt`` / ``solve_ldlt`` -- LDL^T without pivoting of a symmetric
+  (possibly indefinite) C, and its solve (C).
 * ``expand_node_blocks`` -- the block-expanded pattern a condensed-graph
   analysis stands for (plain Python sets).
 * ``brute_symbolic`` -- dense boolean elimination on tiny inputs (pure Python),
@@ -81,6 +83,9 @@ def load_library(path):
     lib.orc_supernodes.argtypes = [I, P, P, P, P]
     lib.orc_supernodes.restype = ctypes.c_int64
     lib.orc_solve.argtypes = [I, P, P, P, P, I, I]
+    lib.orc_factor_ldlt.argtypes = [I, P, P, P, P, P, P, P, P, P, P, P, P]
+    lib.orc_factor_ldlt.restype = ctypes.c_int64
+    lib.orc_solve_ldlt.argtypes = [I, P, P, P, P, P, I, I]
     lib.orc_iluk_pattern.argtypes = [I, P, P, ctypes.c_int32, I, P, P, P, P, P, P]
     lib.orc_iluk_pattern.restype = ctypes.c_int64
     lib.orc_ilu_exact.argtypes = [I, P, P, P, ctypes.c_int32, P, P, P]
@@ -318,6 +323,60 @@ def factor(rowptr, colind, values, perm, in_s=None, sym=None, threads=1):
     F = Factor(n, Lp, Li, Lx, int(bad), fl.value)
     F.threads = nt
     return F
+
+
+def factor_ldlt(rowptr, colind, values, perm, in_s=None, sym=None):
+    """Left-looking FP64 LDL^T (no pivoting) of C = A(perm, perm); columns in
+    S only.  Returns a Factor with L (unit diagonal stored) and F.D."""
+    lib = _load()
+    n = len(rowptr) - 1
+    if sym is None:
+        rp, ci = lower_rows(rowptr, colind, perm)
+        parent = etree(n, rp, ci)
+    else:
+        rp, ci = sym["rows"]
+        parent = sym["parent"]
+    if in_s is None:
+        in_s = np.ones(n, dtype=np.uint8)
+    in_s = np.ascontiguousarray(in_s, dtype=np.uint8)
+    colcnt, rowcnt = counts(n, rp, ci, parent, in_s)
+    Lp = np.zeros(n + 1, dtype=np.int64)
+    Lp[1:] = np.cumsum(colcnt)
+    Rp = np.zeros(n + 1, dtype=np.int64)
+    Rp[1:] = np.cumsum(rowcnt)
+    Li = np.empty(int(Lp[-1]), dtype=np.int32)
+    Rk = np.empty(int(Rp[-1]), dtype=np.int32)
+    Rq = np.empty(int(Rp[-1]), dtype=np.int64)
+    mark = np.empty(n, dtype=np.int32)
+    fill = np.empty(n, dtype=np.int64)
+    lib.orc_pattern(n, _p(rp), _p(ci), _p(parent), _p(in_s), _p(Lp), _p(Li), _p(Rp),
+                    _p(Rk), _p(Rq), _p(mark), _p(fill))
+    Cp, Cr, Cx = lower_cols(rowptr, colind, values, perm)
+    Lx = np.zeros(int(Lp[-1]), dtype=np.float64)
+    D = np.zeros(n, dtype=np.float64)
+    x = np.zeros(n, dtype=np.float64)
+    bad = lib.orc_factor_ldlt(n, _p(Cp), _p(Cr), _p(Cx), _p(in_s), _p(Lp), _p(Li), _p(Lx),
+                              _p(D), _p(Rp), _p(Rk), _p(Rq), _p(x))
+    F = Factor(n, Lp, Li, Lx, int(bad), float(np.sum(colcnt.astype(np.float64) ** 2)))
+    F.D = D
+    return F
+
+
+def solve_ldlt(F, b, perm):
+    """x = P^T L^{-T} D^{-1} L^{-1} P b."""
+    lib = _load()
+    n = F.n
+    b = np.asarray(b, dtype=np.float64)
+    one = b.ndim == 1
+    B = b.reshape(n, -1)
+    y = np.asfortranarray(B[perm] if perm is not None else B.copy())
+    lib.orc_solve_ldlt(n, _p(F.Lp), _p(F.Li), _p(F.Lx), _p(F.D), _p(y), y.shape[1], n)
+    x = np.empty_like(y)
+    if perm is not None:
+        x[perm] = y
+    else:
+        x[:] = y
+    return x[:, 0] if one else x
 
 
 def solve(F, b, perm):

@@ -465,3 +465,60 @@ void orc_fast_trsv_sweep(int64_t n, const int64_t* Sp, const int32_t* Sj, const 
     x[i] = (1.0 - omega) * xo[i] + omega * s;
   }
 }
+
+/* ------------------------------------------------------------------------
+ * LDL^T of a symmetric (possibly indefinite) C = P A P^T without pivoting
+ * (paper Sec. 5: the symmetric factorizations Tacho offers besides
+ * Cholesky): C = L D L^T, L unit lower triangular, D diagonal.  It exists
+ * when every leading principal minor is nonzero, e.g. for any symmetric
+ * permutation of a quasi-definite matrix.  Left-looking, column j:
+ *   x = C[j:, j] - sum_{k < j, L_jk != 0} L[j:, k] d_k L_jk,
+ *   d_j = x_j,  L[j+1:, j] = x[j+1:] / d_j,  L_jj = 1.
+ * Same pattern and row lists as orc_factor (struct(L) does not depend on
+ * the values).  Lx receives L (diagonal entries 1), D the pivots.  Returns
+ * -1, or the first column whose pivot is zero. */
+int64_t orc_factor_ldlt(int64_t n, const int64_t* Cp, const int32_t* Cr, const double* Cx,
+                        const uint8_t* in_s, const int64_t* Lp, const int32_t* Li, double* Lx,
+                        double* D, const int64_t* Rp, const int32_t* Rk, const int64_t* Rq,
+                        double* x) {
+  for (int64_t j = 0; j < n; ++j) {
+    if (!in_s[j]) continue;
+    for (int64_t p = Cp[j]; p < Cp[j + 1]; ++p) x[Cr[p]] += Cx[p];
+    for (int64_t r = Rp[j]; r < Rp[j + 1]; ++r) {
+      int32_t k = Rk[r];
+      int64_t q = Rq[r]; /* position of L_jk in column k */
+      double w = Lx[q] * D[k];
+      for (int64_t t = q; t < Lp[k + 1]; ++t) x[Li[t]] -= Lx[t] * w;
+    }
+    double d = x[j];
+    if (d == 0.0) {
+      for (int64_t t = Lp[j]; t < Lp[j + 1]; ++t) x[Li[t]] = 0.0;
+      return j;
+    }
+    D[j] = d;
+    Lx[Lp[j]] = 1.0;
+    x[j] = 0.0;
+    for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) {
+      int32_t i = Li[t];
+      Lx[t] = x[i] / d;
+      x[i] = 0.0;
+    }
+  }
+  return -1;
+}
+
+/* Solve L D L^T w = y in place (nrhs columns, leading dimension ld). */
+void orc_solve_ldlt(int64_t n, const int64_t* Lp, const int32_t* Li, const double* Lx,
+                    const double* D, double* y, int64_t nrhs, int64_t ld) {
+  for (int64_t r = 0; r < nrhs; ++r) {
+    double* b = y + r * ld;
+    for (int64_t j = 0; j < n; ++j) /* forward: L z = b (unit diagonal) */
+      for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) b[Li[t]] -= Lx[t] * b[j];
+    for (int64_t j = 0; j < n; ++j) b[j] /= D[j];
+    for (int64_t j = n - 1; j >= 0; --j) { /* backward: L^T w = z */
+      double s = b[j];
+      for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) s -= Lx[t] * b[Li[t]];
+      b[j] = s;
+    }
+  }
+}

@@ -171,3 +171,51 @@ def test_ilu_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
 
 def test_ilu_pins_pass_on_the_oracle(orc):
     assert ilu_pins(orc) == set()
+
+
+LDLT_MUTATIONS = [
+    ("ldlt: pivot weight d_k dropped from the update", "double w = Lx[q] * D[k];",
+     "double w = Lx[q];"),
+    ("ldlt: diagonal of L set to the pivot", "Lx[Lp[j]] = 1.0;", "Lx[Lp[j]] = d;"),
+    ("ldlt: column not divided by the pivot", "Lx[t] = x[i] / d;", "Lx[t] = x[i];"),
+    ("ldlt solve: D^{-1} step dropped", "for (int64_t j = 0; j < n; ++j) b[j] /= D[j];", ""),
+    ("ldlt solve: backward uses L instead of L^T",
+     "for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) s -= Lx[t] * b[Li[t]];\n      b[j] = s;",
+     "for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) s -= Lx[t] * b[j];\n      b[j] = s;"),
+]
+
+
+def ldlt_pins(orc):
+    import test_oracle_ldlt as t
+    bad = set()
+    for name, fn in [("cholesky", lambda: t.test_spd_relates_to_cholesky(orc, 1)),
+                     ("minors", lambda: t.test_indefinite_pivots_are_minor_ratios(orc, (3, 3, 2), 0)),
+                     ("1d", lambda: t.test_1d_closed_form(orc)),
+                     ("manufactured", lambda: t.test_indefinite_manufactured_solution(orc))]:
+        try:
+            fn()
+        except Exception:
+            bad.add(name)
+    return bad
+
+
+@pytest.mark.parametrize("name,old,new", LDLT_MUTATIONS, ids=[m[0] for m in LDLT_MUTATIONS])
+def test_ldlt_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not unique: " + name
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib_path = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", str(lib_path), str(mutated),
+                           "-lm"])
+    saved = orc._load()
+    orc._lib = orc.load_library(str(lib_path))
+    try:
+        failed = ldlt_pins(orc)
+    finally:
+        orc._lib = saved
+    assert failed, "no pin caught: " + name
+
+
+def test_ldlt_pins_pass_on_the_oracle(orc):
+    assert ldlt_pins(orc) == set()
