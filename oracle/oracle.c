@@ -488,7 +488,7 @@ int64_t orc_factor_ldlt(int64_t n, const int64_t* Cp, const int32_t* Cr, const d
       int32_t k = Rk[r];
       int64_t q = Rq[r]; /* position of L_jk in column k */
       double w = Lx[q] * D[k];
-      for (int64_t t = q; t < Lp[k + 1]; ++t) x[Li[t]] -= Lx[t] * w;
+      for (int64_t u = q; u < Lp[k + 1]; ++u) x[Li[u]] -= Lx[u] * w;
     }
     double d = x[j];
     if (d == 0.0) {
