@@ -516,9 +516,9 @@ void orc_solve_ldlt(int64_t n, const int64_t* Lp, const int32_t* Li, const doubl
       for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) b[Li[t]] -= Lx[t] * b[j];
     for (int64_t j = 0; j < n; ++j) b[j] /= D[j];
     for (int64_t j = n - 1; j >= 0; --j) { /* backward: L^T w = z */
-      double s = b[j];
-      for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) s -= Lx[t] * b[Li[t]];
-      b[j] = s;
+      double acc = b[j];
+      for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) acc -= Lx[t] * b[Li[t]];
+      b[j] = acc;
     }
   }
 }

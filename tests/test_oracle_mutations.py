@@ -179,9 +179,8 @@ LDLT_MUTATIONS = [
     ("ldlt: diagonal of L set to the pivot", "Lx[Lp[j]] = 1.0;", "Lx[Lp[j]] = d;"),
     ("ldlt: column not divided by the pivot", "Lx[t] = x[i] / d;", "Lx[t] = x[i];"),
     ("ldlt solve: D^{-1} step dropped", "for (int64_t j = 0; j < n; ++j) b[j] /= D[j];", ""),
-    ("ldlt solve: backward uses L instead of L^T",
-     "for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) s -= Lx[t] * b[Li[t]];\n      b[j] = s;",
-     "for (int64_t t = Lp[j] + 1; t < Lp[j + 1]; ++t) s -= Lx[t] * b[j];\n      b[j] = s;"),
+    ("ldlt solve: backward uses L instead of L^T", "acc -= Lx[t] * b[Li[t]];",
+     "acc -= Lx[t] * b[j];"),
 ]
 
 
