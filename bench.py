@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="q1",
-                   choices=["q1", "lap3d", "jump3d", "batch", "serve", "fastilu"],
+                   choices=["q1", "lap3d", "jump3d", "batch", "serve", "fastilu", "dense"],
                    help="q1: extruded Q1 ice-sheet mesh (default); lap3d: 7-point Laplacian size^3 "
                         "(small cases for profiling); jump3d: 7-point Laplacian size^3 with "
                         "coefficients 1 / 1e3 on 8^3 blocks (seed 2); batch: 512 7-point Laplacian "
@@ -102,6 +102,9 @@ def load_workload(args):
     elif args.workload == "jump3d":
         rp, ci, v = gen.laplacian_3d(args.size, jump_block=8, jump_value=1e3, seed=2)
         perm = gen.nd_perm((args.size,) * 3)
+    elif args.workload == "dense":
+        rp, ci, v = gen.dense_spd(args.size, seed=0)
+        perm = None
     elif args.workload == "batch":
         mats, _ = gen.box_batch(args.count, 8, 48, seed=4)
         rp, ci, v = gen.block_diag_csr([(a, b, c) for a, b, c, _ in mats])
@@ -123,6 +126,8 @@ def workload_name(args):
         return "laplacian7_%d^3_jump1e3_8^3blocks_nd" % args.size
     if args.workload == "batch":
         return "batch_%d_laplacian7_boxes_8-48_seed4" % args.count
+    if args.workload == "dense":
+        return "dense_spd_%d" % args.size
     return "q1_extruded_%dx%dx%d_2dof_hnd" % (args.size, args.size, args.layers)
 
 
@@ -463,7 +468,7 @@ def main():
         run_fastilu(args)
         return
     if args.size is None:
-        args.size = {"lap3d": 48, "jump3d": 96}.get(args.workload, 256)
+        args.size = {"lap3d": 48, "jump3d": 96, "dense": 8192}.get(args.workload, 256)
     if args.impl == "reference":
         run_reference(args)
         return

@@ -368,6 +368,21 @@ def elasticity_3d(N, E=1.0, nu=0.3):
     return _coo_to_csr(n, rows, cols, vals)
 
 
+def dense_spd(n, seed=0):
+    """Dense SPD matrix as CSR: a_ij = u_ij / (1 + |i - j|) with u_ij =
+    u_ji ~ U[0.5, 1] (seeded), a_ii = n (diagonally dominant).  One front of
+    n pivot columns: every trailing update is one large dense matrix."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(0.5, 1.0, size=(n, n))
+    u = np.triu(u) + np.triu(u, 1).T
+    i = np.arange(n)
+    A = u / (1.0 + np.abs(i[:, None] - i[None, :]))
+    A[i, i] = float(n)
+    rowptr = np.arange(0, n * n + 1, n, dtype=np.int64)
+    colind = np.tile(np.arange(n, dtype=np.int32), n)
+    return rowptr, colind, A.reshape(-1)
+
+
 def kkt_3d(nx, ny=None, nz=None, delta=1e-2, seed=0):
     """Symmetric quasi-definite saddle-point matrix on an nx x ny x nz grid,
     2 unknowns per node interleaved (dof 2 i: u_i, 2 i + 1: p_i):

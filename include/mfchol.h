@@ -106,9 +106,9 @@ typedef struct mf_options {
   int32_t update_tile[4];   /* trailing update of the large fronts per front
                                size bucket (k+m <= 512, <= 2048, <= 8192,
                                larger): 0 default (FP32 with tc: tcgen05
-                               128 x 128 tiles; otherwise FMA 64 x 64), 1 FMA
+                               128 x 128 tiles; otherwise FMA 32 x 32), 1 FMA
                                64 x 64, 2 FMA 128 x 128, 3 tcgen05 128 x 128
-                               (FP32 with tc; FMA 64 x 64 otherwise), 4 FMA
+                               (FP32 with tc; FMA 32 x 32 otherwise), 4 FMA
                                32 x 32.  mf_autotune picks them.  Fixed at
                                symbolic analysis. */
 } mf_options;
@@ -253,8 +253,8 @@ int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent,
  *      small-front queue on/off, with the default trailing updates;
  *   2. then, for each front-size bucket that holds large fronts (largest
  *      bucket first, the others fixed), the trailing-update tile
- *      (update_tile: FMA 64 / 32 / 128 for FP64 and FP32 without tensor
- *      cores; tcgen05 128 / FMA 64 / FMA 128 for FP32 with them).
+ *      (update_tile: FMA 32 / 64 / 128 for FP64 and FP32 without tensor
+ *      cores; tcgen05 128 / FMA 32 / FMA 64 for FP32 with them).
  * *best receives h's options with the fastest choices and *best_ms its mean
  * time.  Results are cached for the life of the process under a hash of
  * the pattern, the ordering, prec, reps, h's solve variant / tensor-core /
@@ -276,6 +276,27 @@ int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr,
  * fails or exceeds the handle's budget. */
 int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec,
                      mf_factor** f);
+
+/* As mf_factor_create, for the LDL^T factorization P A P^T = L D L^T of a
+ * symmetric, possibly indefinite matrix (paper Sec. 5: besides Cholesky,
+ * Tacho factors symmetric indefinite matrices as LDL^T): L unit lower
+ * triangular (its unit diagonal is stored, so mf_factor_export_L returns
+ * it), D diagonal with 1 x 1 pivots taken in the analysed order, without
+ * pivoting.  It exists when every leading principal minor of P A P^T is
+ * nonzero, for instance for every ordering of a symmetric quasi-definite
+ * matrix ([K B^T; B -C] with K and C positive definite).  mf_factor_numeric
+ * then returns MF_ERR_NOT_SPD for the first zero pivot (its column through
+ * mf_last_error_column).  The same analysis, kernels and solves serve
+ * (every SpTRSV variant; the solve applies D^{-1} between the sweeps);
+ * FP32 factors use the FMA trailing update (no tensor cores) and refine in
+ * FP64 as with Cholesky, their fallback being an FP64 LDL^T. */
+int mf_factor_create_ldlt(mf_handle* h, const mf_symbolic* s, int32_t prec,
+                          mf_factor** f);
+
+/* LDL^T factor: the pivots D (n doubles, permuted order: D[j] belongs to
+ * column j of P A P^T).  Synchronous.  MF_ERR_INVALID for a Cholesky
+ * factor. */
+int mf_factor_export_D(const mf_factor* f, double* D);
 
 /* Numerical factorization P A P^T = L L^T with the given values (CSR order
  * of the analysed pattern; nnz = rowptr[n] entries; host or device pointer
@@ -335,6 +356,11 @@ int mf_factor_launch_counts(const mf_factor* f, int64_t* factor_launches,
  * (algorithmic) for 6 kinds. */
 int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches,
                       double* flops);
+
+/* Work items (CTAs) and launches per kernel kind (the 6 kinds of
+ * mf_factor_profile) of one numeric factorization, from its schedule; for
+ * the trailing-update kinds an item is one tile.  launches may be NULL. */
+int mf_factor_kind_items(const mf_factor* f, int64_t* items, int64_t* launches);
 
 /* ---- phase 3: solve (device; paper Sec. 3 step 3, Sec. 5 SpTRSV) -------- */
 

@@ -103,6 +103,9 @@ _SIGS = {
     "mf_diag_fp64_peak": [_I32, _P, _P],
     "mf_diag_small_queue": [_P, _I32, _P],
     "mf_symbolic_options": [_P, _P],
+    "mf_factor_create_ldlt": [_P, _P, _I32, _P],
+    "mf_factor_export_D": [_P, _P],
+    "mf_factor_kind_items": [_P, _P, _P],
     "mf_ilu_symbolic": [_P, _I64, _P, _P, _I32, _P],
     "mf_ilu_info": [_P, _P, _P],
     "mf_ilu_pattern": [_P, _P, _P, _P],
@@ -604,3 +607,24 @@ def mf_symbolic_options(s):
     o = mf_options()
     _check(lib().mf_symbolic_options(s, ctypes.byref(o)))
     return o
+
+
+def mf_factor_create_ldlt(h, s, prec=MF_FP64):
+    """LDL^T factor object (see the C header)."""
+    f = ctypes.c_void_p()
+    _check(lib().mf_factor_create_ldlt(h, s, prec, ctypes.byref(f)))
+    return f
+
+
+def mf_factor_export_D(f, n):
+    out = np.empty(n, dtype=np.float64)
+    _check(lib().mf_factor_export_D(f, _ptr(out)))
+    return out
+
+
+def mf_factor_kind_items(f):
+    """{kind: (items, launches)} of one numeric factorization."""
+    items = np.zeros(6, dtype=np.int64)
+    launches = np.zeros(6, dtype=np.int64)
+    _check(lib().mf_factor_kind_items(f, _ptr(items), _ptr(launches)))
+    return {k: (int(items[i]), int(launches[i])) for i, k in enumerate(FACTOR_KINDS)}

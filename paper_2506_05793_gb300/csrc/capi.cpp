@@ -168,6 +168,8 @@ struct mf_factor {
   void* PT = nullptr;       // variant 4: P transposed front by front
   void* av = nullptr;       // lower entries of C in assembly order (T)
   int* qstate = nullptr;    // small-front queue: ticket, then one flag per front
+  bool ldlt = false;        // LDL^T (unit L, pivots in D) instead of Cholesky
+  void* Dp = nullptr;       // LDL^T pivots by permuted column (T[n])
   double* small = nullptr;  // per-RHS scalars for refinement
   // graph of the numeric factorization
   cudaStream_t cap_stream = nullptr;
@@ -210,6 +212,7 @@ struct mf_factor {
     cudaFree(PT);
     cudaFree(av);
     cudaFree(qstate);
+    cudaFree(Dp);
     delete fb64;
   }
 };
@@ -451,7 +454,19 @@ int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent, int32_t* 
 // ---------------------------------------------------------------------------
 // Factor
 // ---------------------------------------------------------------------------
+static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt,
+                         mf_factor** f);
+
 int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
+  return factor_create(h, s, prec, false, f);
+}
+
+int mf_factor_create_ldlt(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
+  return factor_create(h, s, prec, true, f);
+}
+
+static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt,
+                         mf_factor** f) {
   if (!h || !s || !f) return set_error(MF_ERR_INVALID, "NULL argument");
   if (prec != MF_FP64 && prec != MF_FP32) return set_error(MF_ERR_INVALID, "bad precision");
   *f = nullptr;
@@ -485,7 +500,11 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor
   if (s->v4) MF_CK(cudaMalloc(&F->PT, std::max<int64_t>(s->Lsize, 1) * es));
   MF_CK(mf::factor_kernels_init(prec));
   MF_CK(mf::solve_kernels_init(prec));
-  if (prec == MF_FP32 && h->opt.tc) {
+  F->ldlt = ldlt;
+  if (ldlt) MF_CK(cudaMalloc(&F->Dp, std::max<int64_t>(s->n, 1) * es));
+  // LDL^T: the pivots enter the trailing update as a scaling of one operand,
+  // which the FMA tiles do; the tensor-core path stays with Cholesky
+  if (prec == MF_FP32 && h->opt.tc && !ldlt) {
     F->tc = true;
     MF_CK(mf::factor_tc_init());
     const int64_t srows = std::max<int64_t>(s->split_rows, 1);
@@ -524,6 +543,7 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
   a.av = F->av;
   a.qstate = F->qstate;
   a.wait_polls = F->wait_polls;
+  a.D = F->Dp;
   const std::vector<mf::Launch>& sched = F->tc ? S->fsched_tc : S->fsched;
   MF_CK(cudaMemsetAsync(F->status, 0xff, 2 * sizeof(unsigned long long), st));
   MF_CK(mf::launch_gather_values(F->prec, a, S->nnz_lower, st));
@@ -644,7 +664,8 @@ int mf_factor_check(mf_factor* f, void* stream) {
   if (f->status_host[1] != ~0ull)
     return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the factorization gave up");
   if (bad != ~0ull) {
-    set_error(MF_ERR_NOT_SPD, "matrix is not positive definite");
+    set_error(MF_ERR_NOT_SPD, f->ldlt ? "zero pivot in the LDL^T factorization"
+                                      : "matrix is not positive definite");
     g_errcol = (int64_t)bad;
     return MF_ERR_NOT_SPD;
   }
@@ -694,6 +715,21 @@ int mf_factor_export_L(const mf_factor* f, double* Lx) {
         Lx[out++] = f->prec == MF_FP32 ? (double)b32[idx] : b64[idx];
       }
     }
+  }
+  return MF_OK;
+}
+
+int mf_factor_export_D(const mf_factor* f, double* D) {
+  if (!f || (!D && f->S->n)) return set_error(MF_ERR_INVALID, "NULL argument");
+  if (!f->ldlt) return set_error(MF_ERR_INVALID, "not an LDL^T factor");
+  const int64_t n = f->S->n;
+  MF_CK(cudaDeviceSynchronize());
+  if (f->prec == MF_FP32) {
+    std::vector<float> t(n);
+    if (n) MF_CK(cudaMemcpy(t.data(), f->Dp, n * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < n; ++i) D[i] = t[i];
+  } else if (n) {
+    MF_CK(cudaMemcpy(D, f->Dp, n * sizeof(double), cudaMemcpyDeviceToHost));
   }
   return MF_OK;
 }
@@ -761,6 +797,21 @@ int mf_factor_profile(const mf_factor* f, double* ms, int64_t* launches, double*
     if (ms) ms[k] = f->prof_ms[k];
     if (launches) launches[k] = f->prof_n[k];
     if (flops) flops[k] = f->prof_fl[k];
+  }
+  return MF_OK;
+}
+
+int mf_factor_kind_items(const mf_factor* f, int64_t* items, int64_t* launches) {
+  if (!f || !items) return set_error(MF_ERR_INVALID, "NULL argument");
+  for (int k = 0; k < mf::K_NKINDS_FACTOR; ++k) {
+    items[k] = 0;
+    if (launches) launches[k] = 0;
+  }
+  for (const mf::Launch& L : f->tc ? f->S->fsched_tc : f->S->fsched) {
+    const int k = L.kind == mf::K_SMALL_Q ? (int)mf::K_SMALL : L.kind;
+    if (k >= mf::K_NKINDS_FACTOR) continue;
+    items[k] += L.count;
+    if (launches) launches[k] += 1;
   }
   return MF_OK;
 }
@@ -960,7 +1011,7 @@ int mf_autotune(mf_handle* h, int64_t n, const int64_t* rowptr, const int32_t* c
     if (rc == MF_OK)
       for (const mf::SnInfo& f : S->sn)
         if (f.k + f.m > cur.small_front_max) present[mf::tile_bucket(f.k + f.m)] = true;
-    const int cand_tc[3] = {3, 1, 2}, cand_fma[3] = {1, 4, 2};
+    const int cand_tc[3] = {3, 4, 1}, cand_fma[3] = {4, 1, 2};  // the default first
     const int* cand = tc_on ? cand_tc : cand_fma;
     for (int b = 3; b >= 0 && rc == MF_OK; --b) {
       if (!present[b]) continue;
@@ -1023,6 +1074,9 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.P = f->P;
   a.PT = f->PT;
   for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
+  // LDL^T: z = D^{-1} z between the sweeps (the forward results sit in Y,
+  // or for SpTRSV variant 4 in the first n x nrhs values of W)
+  if (f->ldlt) MF_CK(mf::launch_dscale(f->prec, S->v4 ? W : Y, f->Dp, S->n, cn, st));
   for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, X, ldx, S->n, cn, scale, accumulate, st));
   return MF_OK;
@@ -1306,7 +1360,7 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
       return set_error(MF_ERR_STAGNATION, "iterative refinement stagnated");
     }
     if (!f->fb64) {
-      rc = mf_factor_create(f->h, S, MF_FP64, &f->fb64);
+      rc = factor_create(f->h, S, MF_FP64, f->ldlt, &f->fb64);
       if (rc != MF_OK) return rc;
     }
     f->fb64->wait_polls = f->wait_polls;

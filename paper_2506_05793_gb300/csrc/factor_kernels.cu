@@ -56,6 +56,7 @@ struct FD {
   T* PT;                // variant 4: P transposed per front (k x nf, ld k) or nullptr
   int* qstate;          // small-front queue: ticket counter, then one flag per front
   int wait_polls;       // polls before a queue wait gives up
+  T* D;                 // LDL^T: the pivots by permuted column; nullptr for Cholesky
 };
 
 template <typename T>
@@ -84,6 +85,7 @@ FD<T> make_fd(const FactorArgs& a) {
   d.PT = static_cast<T*>(a.PT);
   d.qstate = a.qstate;
   d.wait_polls = a.wait_polls > 0 ? a.wait_polls : kQueueSpin;
+  d.D = static_cast<T*>(a.D);
   return d;
 }
 
@@ -100,22 +102,37 @@ __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 
 // Unblocked right-looking partial Cholesky of the first `k` columns of an
 // n x n lower-triangular block held column-major in shared memory (ld).
-// Records the first non-positive pivot (global column col0 + j).
+// Records the first non-positive pivot (global column col0 + j).  With D
+// (LDL^T, paper Sec. 5) the partial factorization is F = L D L^T instead:
+// d_j = F_jj (recorded in D[col0 + j]; a zero pivot is the failure),
+// L(:, j) = F(:, j) / d_j with L_jj = 1, and the trailing update subtracts
+// L(i, j) d_j L(c, j).
 template <typename T>
 __device__ void smem_partial_chol(T* F, int ld, int n, int k, int col0,
-                                  unsigned long long* status) {
+                                  unsigned long long* status, T* D) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < k; ++j) {
     const T dj = F[j * ld + j];
-    if (tid == 0 && !(dj > T(0))) atomicMin(status, (unsigned long long)(col0 + j));
-    const T ljj = dsqrt(dj);
-    const T rinv = T(1) / ljj;
+    T ljj, rinv;
+    if (D) {
+      if (tid == 0 && !(dj != T(0))) atomicMin(status, (unsigned long long)(col0 + j));
+      ljj = T(1);
+      rinv = T(1) / dj;
+    } else {
+      if (tid == 0 && !(dj > T(0))) atomicMin(status, (unsigned long long)(col0 + j));
+      ljj = dsqrt(dj);
+      rinv = T(1) / ljj;
+    }
     __syncthreads();
     for (int i = j + 1 + tid; i < n; i += blockDim.x) F[j * ld + i] *= rinv;
-    if (tid == 0) F[j * ld + j] = ljj;
+    if (tid == 0) {
+      F[j * ld + j] = ljj;
+      if (D) D[col0 + j] = dj;
+    }
     __syncthreads();
+    const T w = D ? dj : T(1);  // L(c, j) w is the multiplier of column c
     for (int c = j + 1 + warp; c < n; c += nw) {
-      const T lc = F[j * ld + c];
+      const T lc = F[j * ld + c] * w;
       for (int i = c + lane; i < n; i += 32) F[c * ld + i] -= F[j * ld + i] * lc;
     }
     __syncthreads();
@@ -155,7 +172,7 @@ __device__ __forceinline__ void small_front_body(const FD<T>& d, int s, T* F) {
     }
     __syncthreads();
   }
-  smem_partial_chol(F, nf, nf, k, f.first, d.status);
+  smem_partial_chol(F, nf, nf, k, f.first, d.status, d.D);
   T* Lp = d.L + f.Loff;
   for (int c = warp; c < k; c += nw)
     for (int r = lane; r < nf; r += 32) Lp[(int64_t)c * nf + r] = F[c * nf + r];
@@ -330,6 +347,10 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
   T* D = reinterpret_cast<T*>(smem_raw);  // D[c * ld + r] = A(r, c), then L(r, c)
   T* Y = D + kNB * ld;                    // Y[c * ld + r] = L^{-1}(r, c)
   T* Tm = Y + kNB * ld;                   // Tm[(m * kPB + c) * tld + r]: block products
+  // LDL^T (d.D set): the block's pivots; L_BB has a unit diagonal, so its
+  // inverse is computed the same way
+  __shared__ T piv_of[kNB];
+  const bool ldlt = d.D != nullptr;
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int c0 = it.t * kNB;
@@ -352,17 +373,22 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
       for (int t = 0; t < kPB; ++t) {
         T* col = D + (j0 + t) * ld + j0;
         const T piv = col[t];
-        if (r == 0 && j0 + t < b && !(piv > T(0)))
+        if (r == 0 && j0 + t < b && !(ldlt ? piv != T(0) : piv > T(0)))
           atomicMin(d.status, (unsigned long long)(f.first + c0 + j0 + t));
-        const T ljj = dsqrt(piv);
-        const T rinv = T(1) / ljj;
+        const T ljj = ldlt ? T(1) : dsqrt(piv);
+        const T rinv = T(1) / (ldlt ? piv : ljj);
         __syncwarp();  // the pivot has been read
-        if (r == t) col[t] = ljj;
-        else if (r > t && r < kPB) col[r] *= rinv;  // each lane scales its own entry
+        if (r == t) {
+          col[t] = ljj;
+          piv_of[j0 + t] = piv;
+        } else if (r > t && r < kPB) {
+          col[r] *= rinv;  // each lane scales its own entry
+        }
         __syncwarp();
         if (r > t && r < kPB) {
-          // all loads first (fixed trip count, so they issue together)
-          const T lr = col[r];
+          // all loads first (fixed trip count, so they issue together);
+          // LDL^T: A_rc -= L_rt d_t L_ct
+          const T lr = ldlt ? col[r] * piv : col[r];
           T lc[kPB], dv[kPB];
 #pragma unroll
           for (int c = 0; c < kPB; ++c) {
@@ -414,7 +440,7 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
           T s = T(0);
 #pragma unroll
           for (int k = 0; k < kPB; ++k) s = fma(av[k], yv[k], s);
-          v[q] = s;
+          v[q] = ldlt ? s / piv_of[j0 + t] : s;  // LDL^T: L_iB = A_iB L_BB^-T D_B^-1
         }
       }
       __syncthreads();
@@ -436,6 +462,7 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
       for (int t = 0; t < kPB; ++t) {
         li[t] = D[(j0 + t) * ld + base + i];
         lc[t] = D[(j0 + t) * ld + base + c];
+        if (ldlt) lc[t] *= piv_of[j0 + t];  // A_ic -= L_iB D_B L_cB^T
       }
       T s = D[(base + c) * ld + base + i];
 #pragma unroll
@@ -483,6 +510,8 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
     const int cc = idx / b, rr = idx % b;
     if (rr >= cc) front_col(d, f, c0 + cc)[c0 + rr] = D[cc * ld + rr];
   }
+  if (ldlt)
+    for (int i = tid; i < b; i += blockDim.x) d.D[f.first + c0 + i] = piv_of[i];
   T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
   for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
     const int cc = idx / kNB, rr = idx % kNB;
@@ -546,6 +575,13 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
     const T* lrow = &Li[c][16 * g];
 #pragma unroll
     for (int q = 0; q < 16; ++q) x[q] = fma(a, lrow[q], x[q]);
+  }
+  if (d.D) {  // LDL^T: L21 = A L_tt^{-T} D_t^{-1}
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = 16 * g + q;
+      if (j < b) x[q] /= d.D[f.first + c0 + j];
+    }
   }
   if (r < rows) {
 #pragma unroll
@@ -611,7 +647,9 @@ __global__ void __launch_bounds__(256) k_syrk(FD<T> d, int64_t item_off) {
     const int q = idx / TILE, r = idx % TILE;
     const T* col = P + (int64_t)q * nf;
     As[q][r] = (rI + r < nf) ? col[rI + r] : T(0);
-    Bs[q][r] = (rJ + r < nf) ? col[rJ + r] : T(0);
+    // LDL^T: C -= P_I D P_J^T, the pivots folded into the B operand
+    const T w = d.D ? d.D[f.first + c0 + q] : T(1);
+    Bs[q][r] = (rJ + r < nf) ? col[rJ + r] * w : T(0);
   }
   __syncthreads();
   const int tr = tid & 15, tc = tid >> 4;

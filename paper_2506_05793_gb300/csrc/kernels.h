@@ -57,6 +57,7 @@ struct FactorArgs {
   // front (zeroed before the queue launch)
   int* qstate = nullptr;
   int32_t wait_polls = 0;  // polls before a queue wait gives up (0: default)
+  void* D = nullptr;       // LDL^T: T[n] pivots by permuted column; nullptr for Cholesky
 };
 
 struct SolveArgs {
@@ -93,6 +94,9 @@ cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st
 // `rows` rows of `width` floats (256 or 512)
 cudaError_t make_split_map(float* split, int64_t rows, int width, void* map_out);
 cudaError_t solve_kernels_init(int prec);
+// LDL^T solve: Y[i + r n] /= D[i] for the n x nrhs values (between sweeps)
+cudaError_t launch_dscale(int prec, void* Y, const void* D, int64_t n, int32_t nrhs,
+                          cudaStream_t st);
 cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStream_t st);
 cudaError_t launch_wait_probe(const int* flag, unsigned long long* status, int limit,
                               cudaStream_t st);

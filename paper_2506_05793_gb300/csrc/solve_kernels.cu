@@ -1639,6 +1639,28 @@ cudaError_t launch_solve(int prec, const Launch& L, const SolveArgs& a, cudaStre
   return prec == MF_FP32 ? launch_t<float>(L, a, st) : launch_t<double>(L, a, st);
 }
 
+namespace {
+template <typename T>
+__global__ void k_dscale(T* Y, const T* D, int64_t n, int32_t nrhs) {
+  const int64_t total = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    Y[e] /= D[e % n];
+}
+}  // namespace
+
+cudaError_t launch_dscale(int prec, void* Y, const void* D, int64_t n, int32_t nrhs,
+                          cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  const int g = grid_for(n * nrhs);
+  if (prec == MF_FP32)
+    k_dscale<float><<<g, 256, 0, st>>>(static_cast<float*>(Y), static_cast<const float*>(D), n, nrhs);
+  else
+    k_dscale<double><<<g, 256, 0, st>>>(static_cast<double*>(Y), static_cast<const double*>(D), n,
+                                        nrhs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_perm_in(int prec, const double* B, int64_t ldb, const int32_t* perm, void* Y,
                            int64_t n, int32_t nrhs, const double* inv_scale, cudaStream_t st) {
   const int g = grid_for(n * nrhs);

@@ -983,14 +983,16 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     // per front: the FMA tile of the FP64 / FP32-FMA schedule and, in the
     // tensor-core schedule, tensor cores or that FMA tile (update_tile code
     // of the front's size bucket: 0 default, 1 FMA 64, 2 FMA 128, 3 tensor
-    // cores (FMA 64 where there are none), 4 FMA 32)
+    // cores, 4 FMA 32; the FMA schedule takes 32 for 0 and 3, the tile that
+    // measured fastest for FP64 on GB300: most CTAs per SM for the
+    // read-modify-write of the trailing tiles)
     auto code_of = [&](int32_t s) {
       const int c = update_tile ? update_tile[tile_bucket(S.sn[s].k + S.sn[s].m)] : 0;
       return c < 0 || c > 4 ? 0 : c;
     };
     auto fma_tile = [&](int32_t s) {
       const int c = code_of(s);
-      return c == 2 ? 128 : c == 4 ? 32 : 64;
+      return c == 1 ? 64 : c == 2 ? 128 : 32;
     };
     auto uses_tc = [&](int32_t s) { return code_of(s) == 0 || code_of(s) == 3; };
     for (int32_t t = 0; t < T; ++t) {
