@@ -90,6 +90,8 @@ def parse():
     p.add_argument("--serve-requests", type=int, default=240, help="serve: requests per rate")
     p.add_argument("--serve-workers", type=int, default=8)
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--solve-only-extras", action="store_true",
+                   help="after the timed steps measure only the solve latency (p50/p99 over 200)")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     return p.parse_args()
 
@@ -614,7 +616,9 @@ def main():
     out["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak,
                        "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                        "peak_source": src}
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and args.solve_only_extras:
+        solve_latency(args, out, mf, f, bd, st, info, len(rp) - 1)
+    elif rank == 0 and not args.no_extras:
         extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, xd, st, dev, info, perm)
     if rank == 0:
         print(json.dumps(out))
@@ -626,10 +630,11 @@ def main():
         dist.destroy_process_group()
 
 
-def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, xd, st, dev, info, perm):
+def solve_latency(args, out, mf, f, bd, st, info, n):
+    """Solve latency (nrhs right-hand sides), p50 / p99 over 200 solves, and
+    the solve's roofline: L read once per sweep plus the right-hand side /
+    solution vectors (4 passes of n x nrhs values)."""
     import torch
-    n = len(rp) - 1
-    # solve latency (nrhs right-hand sides), p50 / p99 over 200 solves
     xs = torch.empty_like(bd)
     for _ in range(3):
         mf.mf_solve(f, bd, xs, stream=st)
@@ -659,6 +664,12 @@ def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, xd, st, dev, info, perm
     out["solve_roofline"] = {"bound": "hbm", "bytes": sbytes, "achieved": gbs, "peak": hbm,
                              "unit": "GB/s", "frac": gbs / hbm,
                              "peak_source": "of measured" if peaks.get("hbm_gbs") else "of fallback"}
+
+
+def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, xd, st, dev, info, perm):
+    import torch
+    n = len(rp) - 1
+    solve_latency(args, out, mf, f, bd, st, info, n)
     # end to end through the C-ABI with host buffers (values H2D, B H2D, X D2H)
     K = 2
     xh = np.empty_like(b, order="F")
