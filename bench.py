@@ -222,15 +222,18 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-# DRAM traffic of the dominant FP64 kernel, from one ncu pass
-# (dram__bytes_read.sum + dram__bytes_write.sum) over all 717 k_syrk launches
-# of one FP64 factorization of the default Q1 workload: 234.5 GB read +
-# 195.6 GB written.  Reported per launch, like `achieved`; valid only while
-# the kernel's source text is the one measured (SHA-1 below) and the
-# factorization issues the same number of launches.
-SYRK_TRAFFIC = {"workload": "q1_extruded_256x256x10_2dof_hnd", "prec": "fp64",
-                "launches": 717, "bytes_per_launch": (234.48e9 + 195.60e9) / 717,
-                "source_sha1": "59cc60931be4e84f3320740ff8aa588657291de9"}
+# DRAM traffic of the dominant FP64 kernel (k_syrk, 32 x 32 tiles): one ncu
+# capture of the bulk trailing update of panel step 0 of a dense 8,192-column
+# front (trailing matrix 264 MB, larger than L2 like the top fronts of the
+# benchmark's meshes): 467.2 MB for 31,878 tiles, 14.66 KB per tile -- one
+# read and one write of the 16 KB FP64 tile, the panel slices from L2.  A
+# launch's traffic is that per-tile figure times the launch's tiles (the
+# schedule's count); valid while the kernel's source text is the measured
+# one (SHA-1 below) and the tile is 32.  Fronts whose trailing matrices fit
+# in L2 move less, so on a whole factorization this is an upper estimate.
+SYRK_TRAFFIC = {"kernel": "k_syrk<double, 32>", "workload": "dense_spd_8192",
+                "bytes_per_tile": 467.206e6 / 31878,
+                "source_sha1": "a937128192250b3e1851a88491328e14370b9c96"}
 
 
 def kernel_source_sha1(path, signature):
@@ -607,15 +610,22 @@ def main():
                "mf_diag_fp64_peak on this GPU before the timed region"
                % (fp64_peak["dfma"], fp64_peak["dmma"]))
     traffic = None
-    if (dom == "syrk" and args.prec == "fp64" and workload_name(args) == SYRK_TRAFFIC["workload"]
-            and prof["syrk"]["launches"] == SYRK_TRAFFIC["launches"]
+    items = mf.mf_factor_kind_items(f)
+    if (dom == "syrk" and args.prec == "fp64" and args.tile in (0, 3, 4)
             and kernel_source_sha1(os.path.join(ROOT, "paper_2506_05793_gb300", "csrc",
                                                 "factor_kernels.cu"), "k_syrk(FD<T> d")
             == SYRK_TRAFFIC["source_sha1"]):
-        traffic = SYRK_TRAFFIC["bytes_per_launch"]
+        tiles, launches = items["syrk"]
+        traffic = SYRK_TRAFFIC["bytes_per_tile"] * tiles / max(launches, 1)
     out["roofline"] = {"kernel": dom, "bound": bound, "achieved": ach, "peak": peak,
                        "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
                        "peak_source": src}
+    if traffic is not None:
+        out["roofline"]["traffic_source"] = (
+            "bytes per launch = %.0f bytes per 32 x 32 tile (ncu dram__bytes_read.sum + "
+            "dram__bytes_write.sum, bulk launch on a dense 8192-column front) x %.0f tiles per "
+            "launch of this schedule; an upper estimate where trailing matrices fit in L2"
+            % (SYRK_TRAFFIC["bytes_per_tile"], items["syrk"][0] / max(items["syrk"][1], 1)))
     if rank == 0 and args.solve_only_extras:
         solve_latency(args, out, mf, f, bd, st, info, len(rp) - 1)
     elif rank == 0 and not args.no_extras:
@@ -739,6 +749,32 @@ def extras(args, out, mf, h, s, f, rp, ci, v, b, vd, bd, xd, st, dev, info, perm
         oracle_leg(args, out, mf, s, f, f32, rp, ci, v, b, xd, x32, perm)
     if f32 is not None:
         mf.mf_factor_free(f32)
+    # the same solve with SpTRSV variant 4 (every front's partitioned
+    # inverse as one sparse product per level and sweep): its own analysis
+    # and factor; setup = the extra factorization time
+    if args.sptrsv != 4:
+        try:
+            o4 = mf.mf_options_default()
+            o4.sptrsv = 4
+            h4 = mf.mf_create(o4)
+            s4 = mf.mf_symbolic_analyze(h4, rp, ci, perm)
+            f4 = mf.mf_factor_create(h4, s4, mf.MF_FP64 if args.prec == "fp64" else mf.MF_FP32)
+            mf.mf_factor_numeric(f4, vd, stream=st)
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            mf.mf_factor_numeric(f4, vd, stream=st, async_=True)
+            z.record(st)
+            mf.mf_factor_check(f4, stream=st)
+            sub = {}
+            solve_latency(args, sub, mf, f4, bd, st, info, n)
+            out["solve_variant4"] = {"solve_ms": sub["solve_ms"], "solves_per_s": sub["solves_per_s"],
+                                     "solve_roofline": sub["solve_roofline"],
+                                     "factor_ms_with_setup": a.elapsed_time(z)}
+            mf.mf_factor_free(f4)
+            mf.mf_symbolic_free(s4)
+            mf.mf_destroy(h4)
+        except Exception as e:
+            out["solve_variant4"] = {"error": str(e)}
 
 
 def oracle_leg(args, out, mf, s, f, f32, rp, ci, v, b, xd, x32, perm):

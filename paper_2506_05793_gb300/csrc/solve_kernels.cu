@@ -1341,7 +1341,22 @@ __global__ void __launch_bounds__(256) k_v4_fw(SD<T> d, int64_t item_off, int co
     const int len = gr.t < f.k ? gr.t + 1 : f.k;
     const T* pv = d.PT + f.Loff + (int64_t)gr.t * f.k;
     const T* y = d.Y + f.first;
-    for (int c = lane; c < len; c += 32) {
+    // four independent loads per lane in flight (rows of the top fronts
+    // hold thousands of values)
+    int c = lane;
+    for (; c + 96 < len; c += 128) {
+      const T v0 = pv[c], v1 = pv[c + 32], v2 = pv[c + 64], v3 = pv[c + 96];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr)
+        if (rr < nr) {
+          const T* yr = y + (int64_t)rr * d.n;
+          acc[rr] = fma(v0, yr[c], acc[rr]);
+          acc[rr] = fma(v1, yr[c + 32], acc[rr]);
+          acc[rr] = fma(v2, yr[c + 64], acc[rr]);
+          acc[rr] = fma(v3, yr[c + 96], acc[rr]);
+        }
+    }
+    for (; c < len; c += 32) {
       const T v = pv[c];
 #pragma unroll
       for (int rr = 0; rr < R; ++rr)
@@ -1375,7 +1390,23 @@ __global__ void __launch_bounds__(256) k_v4_bw(SD<T> d, int64_t item_off, int co
   T acc[R];
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) acc[rr] = T(0);
-  for (int i = c + lane; i < nf; i += 32) {
+  int i = c + lane;
+  for (; i + 96 < nf; i += 128) {  // four independent loads per lane in flight
+    T v[4];
+    const T* src[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = i + 32 * u;
+      v[u] = pc[q];
+      src[u] = q < k ? d.W + f.first + q : d.Y + rows[q];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr)
+        if (rr < nr) acc[rr] = fma(v[u], src[u][(int64_t)rr * d.n], acc[rr]);
+  }
+  for (; i < nf; i += 32) {
     const T v = pc[i];
     const T* src = i < k ? d.W + f.first + i : d.Y + rows[i];
 #pragma unroll
