@@ -126,8 +126,8 @@ int64_t factor_bytes(const mf_symbolic* S, int prec) {
           S->nnz_lower) *
              (int64_t)elem_size(prec) +
          S->nnzA * (int64_t)sizeof(double) +
-         (prec == MF_FP32 ? (std::max<int64_t>(S->split_rows, 1) * 256 +
-                             std::max<int64_t>(S->split_rows_b, 1) * 512) *
+         (prec == MF_FP32 ? (std::max<int64_t>(S->split_rows, 1) * 512 +
+                             std::max<int64_t>(S->split_rows_b, 1) * 1024) *
                                 (int64_t)sizeof(float)
                           : 0);
 }
@@ -509,14 +509,14 @@ static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool 
     MF_CK(mf::factor_tc_init());
     const int64_t srows = std::max<int64_t>(s->split_rows, 1);
     const int64_t srows_b = std::max<int64_t>(s->split_rows_b, 1);
-    MF_CK(cudaMalloc(&F->split, srows * 256 * sizeof(float)));
-    MF_CK(cudaMalloc(&F->split_b, srows_b * 512 * sizeof(float)));
+    MF_CK(cudaMalloc(&F->split, srows * 512 * sizeof(float)));
+    MF_CK(cudaMalloc(&F->split_b, srows_b * 1024 * sizeof(float)));
     // rows past a front are read (and discarded) by the tile kernel: keep
     // them finite
-    MF_CK(cudaMemset(F->split, 0, srows * 256 * sizeof(float)));
-    MF_CK(cudaMemset(F->split_b, 0, srows_b * 512 * sizeof(float)));
-    MF_CK(mf::make_split_map(F->split, srows, 256, F->split_map));
-    MF_CK(mf::make_split_map(F->split_b, srows_b, 512, F->split_map_b));
+    MF_CK(cudaMemset(F->split, 0, srows * 512 * sizeof(float)));
+    MF_CK(cudaMemset(F->split_b, 0, srows_b * 1024 * sizeof(float)));
+    MF_CK(mf::make_split_map(F->split, srows, 512, F->split_map));
+    MF_CK(mf::make_split_map(F->split_b, srows_b, 1024, F->split_map_b));
   }
   *f = F.release();
   return MF_OK;

@@ -592,8 +592,8 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
   }
   if (d.split != nullptr) {
     // FP32 tensor-core path: tf32 hi / lo split of the solved rows, row-major
-    // staging rows holding two panel slots (area 0, slot = step parity) or
-    // four (area 1, lookahead levels, slot = step mod 4), each slot 64 hi
+    // staging rows holding four panel slots (area 0, slot = step mod 4) or
+    // eight (area 1, lookahead levels, slot = step mod 8), each slot 64 hi
     // then 64 lo floats; zero beyond the panel width b
     __syncthreads();
 #pragma unroll
@@ -602,8 +602,8 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
     const int64_t so = d.soff[it.s];
     const bool area1 = (so >> kSoffAreaShift) != 0;
     const int64_t srow = so & (((int64_t)1 << kSoffAreaShift) - 1);
-    const int sw = area1 ? 512 : 256;
-    float* out = (area1 ? d.split_b : d.split) + (srow + r0) * sw + (it.t & (area1 ? 3 : 1)) * 128;
+    const int sw = area1 ? 1024 : 512;
+    float* out = (area1 ? d.split_b : d.split) + (srow + r0) * sw + (it.t & (area1 ? 7 : 3)) * 128;
     for (int idx = tid; idx < rows * kNB; idx += blockDim.x) {
       const int rw = idx / kNB, c = idx % kNB;
       const float xv = (float)As[c][rw];

@@ -7,17 +7,20 @@
 // tensor cores each panel value is split, p = hi + lo with hi = tf32(p) and
 // lo = p - hi, and C -= hi hi^T + hi lo^T + lo hi^T (the lo lo^T term is
 // below FP32 rounding).  The TRSM kernel writes hi and lo of every panel row
-// into a row-major staging buffer (256 floats per row: two panel slots of
-// 64 hi then 64 lo, the slot being the panel step's parity).
+// into a row-major staging buffer (512 floats per row: four panel slots of
+// 64 hi then 64 lo, slot = panel mod 4; 1024 floats and eight slots on the
+// lookahead levels, where a group's bulk pass runs beside the next group's
+// panels).
 //
-// Panels are paired to halve the traffic of the trailing matrix: after an
-// even panel t only the next panel's 64 columns are updated (mode 1), and
-// after panel t + 1 both panels update the rest in one pass with K = 128
-// (mode 2); a front ending on an even panel updates normally (mode 0).
+// Panels are grouped by four to quarter the traffic of the trailing matrix:
+// inside a group g0 .. gl the next panel's 64 columns are updated
+// left-looking after each panel t < gl (a strip with panels g0 .. t), and
+// after gl one pass with K up to 256 updates everything beyond it.
 //
 // One CTA (128 threads) computes one 128 x 128 tile (I, J), I >= J:
-//   - the 64-wide K range is staged in two halves of 32 through one 64 KB
-//     shared-memory buffer (so three CTAs fit on an SM and overlap); one thread
+//   - the K range (64 per panel, up to 256) is staged in quarters of 32
+//     through one 64 KB shared-memory buffer (so three CTAs fit on an SM
+//     and overlap); one thread
 //     copies each half with TMA (a tensor map over the staging buffer, boxes
 //     of 128 rows x 32 floats with 128-byte swizzle), which writes the
 //     canonical K-major layout the MMA descriptors expect (8-row atoms of
@@ -43,7 +46,8 @@ constexpr int kTcM = 128;
 constexpr int kTcN = 128;
 constexpr uint32_t kTmemCols = 128;
 constexpr int kOpBytes = 128 * 128;  // one 128-row x 32-float swizzled K-chunk
-constexpr size_t kTcSmem = 4 * (size_t)kOpBytes + 1024 + 128;
+constexpr int kMaxQuarters = 8;  // K = 256: four panels of two 32-wide quarters
+constexpr size_t kTcSmem = 4 * (size_t)kOpBytes + 1024 + 256;
 constexpr long long kMbarSpin = 1ll << 22;  // try_wait polls before giving up
 
 // instruction descriptor: D = F32, A = B = TF32, both K-major, M = N = 128
@@ -126,30 +130,30 @@ __global__ void __launch_bounds__(128, 3)
   const uint32_t a_hi = sbase, a_lo = sbase + kOpBytes;
   const uint32_t b_hi = sbase + 2 * kOpBytes, b_lo = sbase + 3 * kOpBytes;
   // one single-use barrier per event (MMAs of quarter q at + 8 q, TMA of
-  // quarter q at + 32 + 8 q), each waited once on phase 0: a thread that
-  // reaches its wait late can never mistake a later phase for its own
+  // quarter q at + 64 + 8 q, q < 8), each waited once on phase 0: a thread
+  // that reaches its wait late can never mistake a later phase for its own
   uint64_t* mbar = reinterpret_cast<uint64_t*>(gbase + 4 * kOpBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + 4 * kOpBytes + 64);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + 4 * kOpBytes + 16 * 8);
 
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int nf = f.k + f.m;
-  // mode 0: panel tt on the trailing matrix; 1: panel tt on the next panel's
-  // columns only (strip); 2: panels tt and tt + 1 together (K = 128) on the
-  // trailing matrix beyond panel tt + 1
-  const int tt = it.t & 0xffffff, mode = it.t >> 24;
-  const int tl = mode == 2 ? tt + 1 : tt;  // last panel applied
+  // panels tt .. tt + nK - 1 (one group) applied to the columns beyond the
+  // last of them: all of them (a group pass) or, for a strip, only the next
+  // panel's 64 columns
+  const int tt = it.t & 0xffff, nK = (it.t >> 16) & 0xff, strip = it.t >> 24;
+  const int tl = tt + nK - 1;  // last panel applied
   const int c0 = tl * kNB;
   const int b = min(kNB, f.k - c0);
   const int p0 = c0 + b;
   const int rI = p0 + it.a * kTcM, rJ = p0 + it.b * kTcN;
-  const int cmax = mode == 1 ? min(f.k, p0 + kNB) : nf;  // columns updated: [p0, cmax)
-  const int nq = mode == 2 ? 4 : 2;                      // K quarters of 32
+  const int cmax = strip ? min(f.k, p0 + kNB) : nf;  // columns updated: [p0, cmax)
+  const int nq = min(2 * nK, kMaxQuarters);          // K quarters of 32
   const bool diag = it.a == it.b;
-  // staging rows: area 0 holds two panel slots per row, area 1 four
+  // staging rows: area 0 holds four panel slots per row, area 1 eight
   const int64_t R0 = d.soff[it.s] & (((int64_t)1 << kSoffAreaShift) - 1);
   const CUtensorMap* smap = area ? &smap1 : &smap0;
-  const int smask = area ? 3 : 1;
+  const int smask = area ? 7 : 3;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mb0 = smem_u32(mbar);
 
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(128, 3)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < 2 * kMaxQuarters; ++q)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb0 + 8 * q) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -226,9 +230,9 @@ __global__ void __launch_bounds__(128, 3)
   const uint32_t bh = diag ? a_hi : b_hi, bl = diag ? a_lo : b_lo;
   bool ok = true;
   for (int q = 0; q < nq; ++q) {
-    const uint32_t mb = mb0 + 8 * q, mbt = mb0 + 32 + 8 * q;
+    const uint32_t mb = mb0 + 8 * q, mbt = mb0 + 8 * kMaxQuarters + 8 * q;
     const int h = q & 1;                                           // half of a panel
-    const int slot = (mode == 2 ? tt + (q >> 1) : tt) & smask;    // staging slot of the panel
+    const int slot = (tt + (q >> 1)) & smask;                     // staging slot of the panel
     const int x0 = slot * 128 + h * 32;
     // rows of the staging buffer beyond the front belong to other fronts (or
     // are zero); they only reach accumulator rows / columns that the

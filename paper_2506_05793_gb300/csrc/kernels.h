@@ -41,10 +41,10 @@ struct FactorArgs {
   // [0] = first non-positive pivot column, [1] = MF_ERR_TIMEOUT when a bounded
   // wait of the factorization gave up (both all-ones when clear)
   unsigned long long* status;
-  // FP32 tensor-core path: per panel row 64 tf32 "hi" then 64 "lo" floats
+  // FP32 tensor-core path: four panel slots per row, each 64 tf32 "hi" then 64 "lo" floats
   // (row soff[front] + front row); nullptr elsewhere
   float* split;
-  float* split_b;           // four-slot staging rows of lookahead levels
+  float* split_b;           // eight-slot staging rows of lookahead levels
   const void* split_map;    // host copy of the TMA tensor map over split (128 bytes)
   const void* split_map_b;  // same over split_b
   // per large front of the level (slot in item field b): 64 x 64 inverse of
@@ -91,7 +91,7 @@ cudaError_t launch_gather_values(int prec, const FactorArgs& a, int64_t nnz_lowe
 cudaError_t factor_tc_init();
 cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st);
 // tensor map (128 bytes, written to map_out) over a staging buffer of
-// `rows` rows of `width` floats (256 or 512)
+// `rows` rows of `width` floats (512 or 1024)
 cudaError_t make_split_map(float* split, int64_t rows, int width, void* map_out);
 cudaError_t solve_kernels_init(int prec);
 // LDL^T solve: Y[i + r n] /= D[i] for the n x nrhs values (between sweeps)

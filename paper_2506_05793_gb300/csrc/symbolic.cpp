@@ -964,7 +964,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     add(S.fsched, K_ASSEMBLE, lev, 0, it, 0.0);
     add(S.fsched_tc, K_ASSEMBLE, lev, 0, it, 0.0);
     // rows of the split buffer: the level's large fronts side by side, in
-    // the four-slot area on lookahead levels
+    // the eight-slot area on lookahead levels (four slots elsewhere)
     const bool la = (int)G.size() <= kLookaheadFronts;
     int64_t srow = 0;
     for (int32_t s : G) {
@@ -979,7 +979,6 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
         S.ioff[s] = S.ninv;
         S.ninv += (S.sn[s].k + kNB - 1) / kNB;
       }
-    std::unordered_map<int32_t, double> fpair;  // panel t's deferred flops
     // per front: the FMA tile of the FP64 / FP32-FMA schedule and, in the
     // tensor-core schedule, tensor cores or that FMA tile (update_tile code
     // of the front's size bucket: 0 default, 1 FMA 64, 2 FMA 128, 3 tensor
@@ -1000,7 +999,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
       std::vector<Item> is[3], isf[3];  // FMA tiles 32 / 64 / 128: FP64 and FP32-TC schedules
       double fp = 0, ft = 0, fs[3] = {0, 0, 0}, fsf[3] = {0, 0, 0}, fstc = 0;
       auto tix = [](int T) { return T == 32 ? 0 : T == 64 ? 1 : 2; };
-      bool normal_tc = false;  // a tensor-core front takes a plain update this step
+      bool group_end = false;  // a tensor-core front ends its group of panels this step
       for (size_t gi = 0; gi < G.size(); ++gi) {
         const int32_t s = G[gi];
         // slot of the diagonal-block inverse: per level, or kept per block
@@ -1024,26 +1023,29 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
           fsf[x] += full;
           continue;
         }
-        // tensor-core path: panels are paired.  Even step t with a next
-        // panel: update only the next panel's 64 columns (strip, mode 1);
-        // odd step t: update everything beyond panel t with both panels at
-        // once (K = 128, mode 2, item carries the first panel t - 1).  An
-        // even last step updates its trailing matrix alone (mode 0).
+        // tensor-core path: panels in groups of four (g0 .. gl), the
+        // trailing matrix read and written once per group (K up to 256).
+        // Inside a group the next panel's columns are brought up to date
+        // left-looking: after panel t < gl a strip updates the 64 columns of
+        // panel t + 1 with panels g0 .. t; after gl one pass updates
+        // everything beyond gl with the whole group.  Item field t packs the
+        // group's first panel, the number of panels applied and the strip
+        // flag.
         const int nt2 = (nf - p0 + kTcTile - 1) / kTcTile;
-        if ((t & 1) == 0 && (t + 1) * kNB < k) {
+        const int g0 = t & ~3;
+        const int gl = std::min(g0 + 3, (k - 1) / kNB);
+        if (t < gl) {
+          const int nK = t - g0 + 1;
           const int b1 = std::min(kNB, k - (t + 1) * kNB);
-          for (int I = 0; I < nt2; ++I) itc.push_back({s, t | (1 << 24), I, 0});
-          fstc += 2.0 * ((double)b1 * (nf - p0) - (double)b1 * (b1 - 1) / 2.0) * b;
-          fpair[s] = full - 2.0 * ((double)b1 * (nf - p0) - (double)b1 * (b1 - 1) / 2.0) * b;
-        } else if ((t & 1) == 0) {
-          for (int I = 0; I < nt2; ++I)
-            for (int J = 0; J <= I; ++J) itc.push_back({s, t, I, J});
-          fstc += full;
-          normal_tc = true;
+          for (int I = 0; I < nt2; ++I) itc.push_back({s, g0 | (nK << 16) | (1 << 24), I, 0});
+          fstc += 2.0 * (double)kNB * nK * ((double)b1 * (nf - p0) - (double)b1 * (b1 - 1) / 2.0);
         } else {
+          const int nK = gl - g0 + 1;
           for (int I = 0; I < nt2; ++I)
-            for (int J = 0; J <= I; ++J) itc.push_back({s, (t - 1) | (2 << 24), I, J});
-          fstc += full + fpair[s];
+            for (int J = 0; J <= I; ++J) itc.push_back({s, g0 | (nK << 16), I, J});
+          const double Kw = (double)kNB * (nK - 1) + b;
+          fstc += Kw * (double)(nf - p0) * (double)(nf - p0 + 1);
+          group_end = true;
         }
       }
       static const int kTiles[3] = {32, 64, 128};
@@ -1079,14 +1081,19 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
         fma_split(S.fsched, is[x], fs[x], kTiles[x]);
         fma_split(S.fsched_tc, isf[x], fsf[x], kTiles[x]);
       }
-      if ((t & 1) == 1) {  // pair step
+      // tensor cores: the strips (next panel only) and the first two tile
+      // columns of a group pass (the next group's four panels) on the
+      // critical stream, after the previous group's bulk (join); the rest
+      // of the pass on the side stream.  A group's bulk on the side stream
+      // runs while the next group's panels are factored: their staging slots
+      // differ (eight per row on lookahead levels), and their strips touch
+      // only columns inside those two tile columns.
+      {
         std::vector<Item> a, b;
-        split_j0(itc, a, b);
+        for (const Item& x : itc) ((x.t >> 24) != 0 || x.b * kTcTile < 4 * kNB ? a : b).push_back(x);
         const double fa = itc.empty() ? 0.0 : fstc * (double)a.size() / (double)itc.size();
-        add(S.fsched_tc, K_SYRK_TC, lev, t, a, fa, 0, 1, 1);
+        add(S.fsched_tc, K_SYRK_TC, lev, t, a, fa, 0, group_end ? 1 : 0, 1);
         add(S.fsched_tc, K_SYRK_TC, lev, t, b, fstc - fa, 1, 0, 1);
-      } else {  // strips touch only the next panel; a plain update waits
-        add(S.fsched_tc, K_SYRK_TC, lev, t, itc, fstc, 0, normal_tc ? 1 : 0, 1);
       }
     }
   }
@@ -1335,6 +1342,7 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
     std::vector<std::vector<std::vector<std::pair<int, int>>>> trsm(ns);
     std::vector<std::vector<int>> trsm_at(ns), syrk0_at(ns);
     std::vector<int> syrk_tile(ns, 0);  // FMA tile of a front (0: none seen)
+    std::vector<std::vector<int64_t>> tc_tiles(ns);
     int32_t last_level = -1;
     for (size_t li = 0; li < sched.size(); ++li) {
       const Launch& L = sched[li];
@@ -1409,6 +1417,10 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
             break;
           }
           case K_SYRK_TC:
+            // (group first panel, panels, strip, I, J) in 8/4/1/24/24 bits
+            tc_tiles[it.s].push_back(((int64_t)(it.t & 0xffff) << 40) |
+                                     ((int64_t)((it.t >> 16) & 0xff) << 36) |
+                                     ((int64_t)(it.t >> 24) << 35) | ((int64_t)it.a << 17) | it.b);
             break;
           default:
             return fail("unknown factor kind");
@@ -1432,6 +1444,32 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
         const int Tl = syrk_tile[s] ? syrk_tile[s] : kTile;
         const int64_t nt = (nf - p0 + Tl - 1) / Tl;
         want += nt * (nt + 1) / 2;
+      }
+      // tensor-core fronts: per group of four panels g0 .. gl, the strips
+      // after each t < gl (panels g0 .. t, the 128-row tiles of the next
+      // panel's columns) and the pass after gl (panels g0 .. gl, the lower
+      // tiles beyond it), each tile exactly once
+      if (tc && !tc_tiles[s].empty()) {
+        if (syrk_tile[s]) return fail("front on both trailing-update paths");
+        std::vector<int64_t> want_tc;
+        for (int g0 = 0; g0 < nb; g0 += 4) {
+          const int gl = std::min(g0 + 3, nb - 1);
+          for (int t = g0; t <= gl; ++t) {
+            const int p0 = t * kNB + std::min(kNB, f.k - t * kNB);
+            const int nt2 = (nf - p0 + kTcTile - 1) / kTcTile;
+            const int64_t head = ((int64_t)g0 << 40) | ((int64_t)(t - g0 + 1) << 36);
+            if (t < gl) {
+              for (int I = 0; I < nt2; ++I) want_tc.push_back(head | (1ll << 35) | ((int64_t)I << 17));
+            } else {
+              for (int I = 0; I < nt2; ++I)
+                for (int J = 0; J <= I; ++J) want_tc.push_back(head | ((int64_t)I << 17) | J);
+            }
+          }
+        }
+        std::vector<int64_t>& v = tc_tiles[s];
+        std::sort(v.begin(), v.end());
+        std::sort(want_tc.begin(), want_tc.end());
+        if (v != want_tc) return fail("tensor-core strips or group passes missing or repeated");
       }
       // every front of the FMA schedule, and the FMA fronts of the
       // tensor-core schedule, take each trailing tile exactly once

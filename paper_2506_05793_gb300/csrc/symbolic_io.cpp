@@ -270,15 +270,17 @@ bool indices_in_range(const mf_symbolic& s) {
         const mf::Item& it = s.items[x];
         const mf::SnInfo& I = s.sn[it.s];
         const int64_t nf = (int64_t)I.k + I.m, nb = (I.k + mf::kNB - 1) / mf::kNB;
-        const int32_t tt = L.kind == mf::K_SYRK_TC ? (it.t & 0xffffff) : it.t;
+        // tensor-core items pack (first panel, panels, strip) into t
+        const int32_t tt = L.kind == mf::K_SYRK_TC ? (it.t & 0xffff) : it.t;
+        const int32_t nK = L.kind == mf::K_SYRK_TC ? ((it.t >> 16) & 0xff) : 1;
         switch (L.kind) {
           case mf::K_POTRF:
           case mf::K_TRSM:
           case mf::K_SYRK_TC: {
-            if (tt < 0 || tt >= nb) return false;
+            if (tt < 0 || tt >= nb || nK < 1 || nK > 4 || tt + nK > nb) return false;
             if (L.kind != mf::K_SYRK_TC && (it.b < 0 || it.b >= slots)) return false;
             if (L.kind == mf::K_TRSM && (it.a < 0 || it.a >= nf)) return false;
-            if (L.kind == mf::K_SYRK_TC && ((it.t >> 24) > 2 || it.a < 0 || it.b < 0 || it.b > it.a))
+            if (L.kind == mf::K_SYRK_TC && ((it.t >> 24) > 1 || it.a < 0 || it.b < 0 || it.b > it.a))
               return false;
             const int64_t so = s.soff[it.s];
             const int64_t srow = so & (((int64_t)1 << mf::kSoffAreaShift) - 1);
