@@ -592,14 +592,19 @@ __global__ void __launch_bounds__(256) k_fw_gemv1(SD<T> d, int64_t item_off) {
   const bool live = row < rows;
   const T* Lr = d.L + f.Loff + r0 + (live ? row : 0);
   const T* yx = d.Y + f.first;  // the front's solved pivots
-  T a0 = T(0), a1 = T(0);
+  // four independent loads of L per thread in flight
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
   int j = g;
-  for (; j + 16 < k; j += 32) {
-    a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
-    a1 = fma(Lr[(int64_t)(j + 16) * nf], yx[j + 16], a1);
+  for (; j + 48 < k; j += 64) {
+    const T l0 = Lr[(int64_t)j * nf], l1 = Lr[(int64_t)(j + 16) * nf];
+    const T l2 = Lr[(int64_t)(j + 32) * nf], l3 = Lr[(int64_t)(j + 48) * nf];
+    a0 = fma(l0, yx[j], a0);
+    a1 = fma(l1, yx[j + 16], a1);
+    a2 = fma(l2, yx[j + 32], a2);
+    a3 = fma(l3, yx[j + 48], a3);
   }
-  if (j < k) a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
-  red[g][row] = a0 + a1;
+  for (; j < k; j += 16) a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
+  red[g][row] = (a0 + a1) + (a2 + a3);
   __syncthreads();
   if (tid < rows) {
     T sum = T(0);

@@ -1100,7 +1100,8 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
   // ---- solves.  Per level and sweep, fronts with k + m <= kWarpSolve go to
   // the one-warp kernels (no flags, one launch per row class, 32 H rows with
   // H = 2, 4, 8, 16) unless the class is too sparse to fill the GPU and the
-  // front has a long pivot chain (k > 64); all other fronts are split into
+  // front has a long pivot chain (k > 64) or more than 128 rows (one warp
+  // would stream all its update rows alone); all other fronts are split into
   // 64-row blocks for the sync-free level kernel.  Level-kernel items are
   // taken in ticket order, so a block only waits on blocks with earlier
   // tickets; they are ordered by depth in their front's chain (every
@@ -1124,7 +1125,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
       wcls[c].clear();
       const bool sparse = cls[c].size() < kWarpMinFronts;
       for (int32_t s : cls[c]) {
-        if (sparse && S.sn[s].k > 2 * 32) big.push_back(s);
+        if (sparse && (S.sn[s].k > 2 * 32 || c >= 2)) big.push_back(s);
         else wcls[c].push_back({s, 0, 0, 0});
       }
     }
