@@ -232,13 +232,11 @@ __global__ void __launch_bounds__(256) k_small_queue(FD<T> d, int64_t item_off, 
     }
     __syncthreads();
     small_front_body(d, s, reinterpret_cast<T*>(smem_raw));
-    // every thread's stores are ordered before thread 0's release (CTA
-    // barrier, then a GPU-scope fence and release store)
+    // every thread's stores are ordered before thread 0's release by the
+    // CTA barrier; the GPU-scope release store is cumulative
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
+    if (threadIdx.x == 0)
       asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(done + s), "r"(1) : "memory");
-    }
   }
 }
 

@@ -106,20 +106,21 @@ __device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* st
         atomicExch(status, (unsigned long long)MF_ERR_TIMEOUT);
         break;
       }
-      __nanosleep(128);
+      // the first polls back to back (a chain's next block usually arrives
+      // within a few microseconds), then 128 ns apart
+      if (spins > 64) __nanosleep(128);
     }
   }
   __syncthreads();
 }
 
 // The CTA barrier orders every thread's writes before thread 0, whose
-// fence and release store publish them at GPU scope (release is cumulative).
+// release store publishes them at GPU scope: release is cumulative, so the
+// writes ordered before it by the barrier are visible to a thread that
+// acquires the flag (no separate fence needed).
 __device__ __forceinline__ void cta_publish(int* flag) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    st_release(flag, 1);
-  }
+  if (threadIdx.x == 0) st_release(flag, 1);
 }
 
 // Row pitches of the per-RHS shared arrays: padded so that lanes stepping
