@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "laplacian_1d", "laplacian_2d", "laplacian_3d", "q1_extruded", "nd_perm",
-    "random_spd", "rhs", "box_batch", "block_diag_csr", "csr_matvec",
+    "random_spd", "random_nonsym", "nonsym_3d", "pivot_nodes_3d", "rhs", "box_batch", "block_diag_csr", "csr_matvec",
     "config1", "config2", "config3", "config5",
 ]
 
@@ -497,6 +497,95 @@ def random_spd(n, density=0.1, seed=0, dense_rows=0):
     cols = np.concatenate([cols, np.arange(n)])
     vals = np.concatenate([vals, d])
     return _coo_to_csr(n, rows, cols, vals)
+
+
+def random_nonsym(n, density=0.1, seed=0, dominance=2.0):
+    """Random sparse nonsymmetric matrix with a symmetric pattern: entries
+    (i, j) and (j, i) drawn independently from U[-1, 1].  With dominance > 0
+    the diagonal is dominance x (the column's off-diagonal |sum|) + U[0.5, 1],
+    so C is strictly column diagonally dominant (LU without pivoting exists
+    for every symmetric ordering, and partial pivoting swaps nothing); with
+    dominance = 0 the diagonal is U[-1, 1] too."""
+    rng = np.random.default_rng(seed)
+    m = np.triu(rng.random((n, n)) < density, 1)
+    iu, ju = np.nonzero(m)
+    rows = np.concatenate([iu, ju])
+    cols = np.concatenate([ju, iu])
+    vals = rng.uniform(-1.0, 1.0, size=len(rows))
+    if dominance > 0:
+        colsum = np.bincount(cols, weights=np.abs(vals), minlength=n)
+        d = dominance * colsum + rng.uniform(0.5, 1.0, size=n)
+    else:
+        d = rng.uniform(-1.0, 1.0, size=n)
+    rows = np.concatenate([rows, np.arange(n)])
+    cols = np.concatenate([cols, np.arange(n)])
+    vals = np.concatenate([vals, d])
+    return _coo_to_csr(n, rows, cols, vals)
+
+
+def nonsym_3d(nx, ny=None, nz=None, wind=2.0, small_diag=0.0, seed=0):
+    """7-point convection-diffusion operator -Laplace(u) + w . grad(u) on an
+    nx x ny x nz grid (Dirichlet, central differences, unit spacing): entry
+    (i, i +- e_a) = -1 +- w_a / 2 with a seeded wind w_a in U[-wind, wind]
+    per node and axis, diagonal 6.  The pattern is symmetric, the values are
+    not; for |w_a| > 2 the matrix is no longer diagonally dominant.  A
+    fraction ``small_diag`` of the diagonal entries (seeded) is replaced by
+    U[-0.5, 0.5], so that partial pivoting really swaps rows."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    kp, kc, kv = laplacian_3d(nx, ny, nz)
+    n = len(kp) - 1
+    row = np.repeat(np.arange(n, dtype=np.int64), np.diff(kp))
+    col = kc.astype(np.int64)
+    w = rng.uniform(-wind, wind, size=(n, 3))
+    off = row != col
+    d = col - row
+    axis = np.where(np.abs(d) == 1, 0, np.where(np.abs(d) == nx, 1, 2))
+    vals = np.where(off, -1.0 + np.sign(d) * w[row, axis] / 2.0, 6.0)
+    if small_diag > 0:
+        pick = rng.random(n) < small_diag
+        dv = np.where(pick, rng.uniform(-0.5, 0.5, size=n), 6.0)
+        vals = np.where(off, vals, dv[row])
+    return _coo_to_csr(n, row, col, vals)
+
+
+def pivot_nodes_3d(nx, ny=None, nz=None, dofs=2, seed=0):
+    """Node-block matrix that needs pivoting, with a unique pivot sequence:
+    A = Pi_0 B on an nx x ny x nz grid with `dofs` unknowns per node
+    (dof d i + t), dense dofs x dofs blocks between a node and itself and
+    its 7-point neighbours (so every row of a node has the same pattern).
+    B is strictly column diagonally dominant (diagonal 4 x the column's
+    off-diagonal |sum| + 1, off-diagonal U[-1, 1] x 0.2); Pi_0 reverses the
+    dof order inside every node, and the entries of B that Pi_0 puts on
+    the diagonal of dof 0 of each node are exactly zero.  So LU without
+    pivoting stops at the first column with a zero pivot, while partial
+    pivoting within any diagonal block that holds a whole node picks the
+    dominant row of B each time: it finds Pi_0 and factors B."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    kp, kc, _ = laplacian_3d(nx, ny, nz)
+    nn = len(kp) - 1
+    a = np.repeat(np.arange(nn, dtype=np.int64), np.diff(kp))
+    b = kc.astype(np.int64)
+    t = np.arange(dofs)
+    ti, tj = np.meshgrid(t, t, indexing="ij")
+    rows = (dofs * a[:, None, None] + ti[None]).ravel()
+    cols = (dofs * b[:, None, None] + tj[None]).ravel()
+    vals = rng.uniform(-1.0, 1.0, size=rows.shape) * 0.2
+    n = dofs * nn
+    # the entry of B that lands on the diagonal of (node, dof 0): row
+    # (node, dofs - 1), column (node, dof 0)
+    same = (rows // dofs == cols // dofs)
+    vals[same & (rows % dofs == dofs - 1) & (cols % dofs == 0) & (dofs > 1)] = 0.0
+    diag = rows == cols
+    vals[diag] = 0.0
+    colsum = np.bincount(cols, weights=np.abs(vals), minlength=n)
+    vals[diag] = 4.0 * colsum[cols[diag]] + 1.0
+    node = rows // dofs
+    prow = dofs * node + (dofs - 1 - rows % dofs)  # Pi_0: reverse inside the node
+    return _coo_to_csr(n, prow, cols, vals)
 
 
 def random_perm(n, seed=0):

@@ -18,6 +18,9 @@ the three phases of the paper's Ax=b statement in Sec. 3):
 * ``solve``      -- ``x = P^T L^{-T} L^{-1} P b`` (C).
 * ``factor_ldlt`` / ``solve_ldlt`` -- LDL^T without pivoting of a symmetric
   (possibly indefinite) C, and its solve (C).
+* ``lu_dense`` / ``solve_lu`` / ``pivot_windows`` -- LU of a general matrix
+  with a symmetric pattern (Crout: L lower, U unit upper), pivots looked for
+  only within diagonal blocks, and its solve (dense, C).
 * ``expand_node_blocks`` -- the block-expanded pattern a condensed-graph
   analysis stands for (plain Python sets).
 * ``brute_symbolic`` -- dense boolean elimination on tiny inputs (pure Python),
@@ -28,7 +31,8 @@ the three phases of the paper's Ax=b statement in Sec. 3):
   incomplete LU on it (the sweeps' fixed point), the sweeps of the factor
   (out of place) and of the triangular solves (C).
 
-Pins (tests/test_oracle.py): dense numpy Cholesky, the closed-form 1D
+Pins (tests/test_oracle.py; LU: tests/test_oracle_lu.py, scipy's partially
+pivoted LU, the Thomas recurrence, the Cholesky relation): dense numpy Cholesky, the closed-form 1D
 Laplacian factor, the Dirichlet-Laplacian log-determinant, brute-force symbolic
 elimination and the etree/count invariants.
 """
@@ -93,6 +97,8 @@ def load_library(path):
                                       ctypes.c_double, P, P]
     lib.orc_fast_trsv_sweep.argtypes = [I, P, P, P, ctypes.c_int32, P, P, ctypes.c_int, P, P, P,
                                         ctypes.c_double]
+    lib.orc_lu_dense.argtypes = [I, P, P, P, P, P]
+    lib.orc_lu_dense.restype = ctypes.c_int64
     return lib
 
 
@@ -471,6 +477,70 @@ def expand_node_blocks(rowptr, colind, values, node_of):
     ci = np.array([c for (_, c) in keys], dtype=np.int32)
     vx = np.array([entries[k] for k in keys], dtype=np.float64)
     return rp, ci, vx
+
+
+# ---------------------------------------------------------------------------
+# LU with a symmetric pattern, pivoting within diagonal blocks (Sec. 5)
+# ---------------------------------------------------------------------------
+class LU:
+    """Pi C = L U of C = A(perm, perm): ``L`` dense lower triangular, ``U``
+    dense unit upper triangular, ``rho[i]`` the row of C in position i,
+    ``bad_col`` -1 or the first zero pivot."""
+
+    def __init__(self, L, U, rho, bad_col):
+        self.L, self.U, self.rho, self.bad_col = L, U, rho, bad_col
+        self.n = len(rho)
+
+
+def pivot_windows(starts, n, nb=64):
+    """wend[j] for pivot windows cut out of a partition of 0..n-1: the blocks
+    start at ``starts`` (ascending, starts[0] = 0), each block is cut into
+    pieces of nb columns from its first one, and column j may take its pivot
+    from the rows j .. wend[j]-1 of its piece."""
+    bounds = list(np.asarray(starts, dtype=np.int64)) + [n]
+    wend = np.empty(n, dtype=np.int64)
+    for b0, b1 in zip(bounds[:-1], bounds[1:]):
+        for c0 in range(int(b0), int(b1), nb):
+            wend[c0:min(c0 + nb, b1)] = min(c0 + nb, b1)
+    return wend
+
+
+def lu_dense(rowptr, colind, values, perm, wend=None):
+    """Dense right-looking Crout LU of C = A(perm, perm) (n up to a few
+    thousand), pivots only from rows j .. wend[j]-1 (default: no pivoting)."""
+    lib = _load()
+    n = len(rowptr) - 1
+    A = np.zeros((n, n))
+    np.add.at(A, (np.repeat(np.arange(n), np.diff(rowptr)), colind), values)
+    C = A if perm is None else A[np.ix_(perm, perm)]
+    M = np.asfortranarray(C)
+    if wend is None:
+        wend = np.arange(1, n + 1, dtype=np.int64)
+    wend = np.ascontiguousarray(wend, dtype=np.int64)
+    rho = np.empty(n, dtype=np.int64)
+    nzr = np.empty(n, dtype=np.int64)
+    nzc = np.empty(n, dtype=np.int64)
+    bad = lib.orc_lu_dense(n, _p(M), _p(wend), _p(rho), _p(nzr), _p(nzc))
+    L = np.tril(M)
+    U = np.triu(M, 1) + np.eye(n)
+    return LU(L, U, rho, int(bad))
+
+
+def solve_lu(F, b, perm):
+    """x = P^T U^{-1} L^{-1} Pi P b (triangular solves by scipy)."""
+    from scipy.linalg import solve_triangular
+    b = np.asarray(b, dtype=np.float64)
+    one = b.ndim == 1
+    B = b.reshape(F.n, -1)
+    y = B[perm] if perm is not None else B.copy()
+    z = solve_triangular(F.L, y[F.rho], lower=True)
+    w = solve_triangular(F.U, z, lower=False, unit_diagonal=True)
+    x = np.empty_like(w)
+    if perm is not None:
+        x[perm] = w
+    else:
+        x[:] = w
+    return x[:, 0] if one else x
 
 
 # ---------------------------------------------------------------------------

@@ -522,3 +522,64 @@ void orc_solve_ldlt(int64_t n, const int64_t* Lp, const int32_t* Li, const doubl
     }
   }
 }
+
+/*
+ * LU of a general matrix with a symmetric sparsity pattern (paper Sec. 5:
+ * besides Cholesky and LDL^T, Tacho factors general matrices whose
+ * structure is symmetric), pivots looked for only within diagonal blocks
+ * (paper Sec. 5, the comparison with SuperLU: Tacho searches each diagonal
+ * block for its pivots instead of pivoting across whole columns).
+ *
+ * Dense right-looking Gaussian elimination in Crout form on the n x n
+ * column-major M = C = P A P^T:  Pi C = L U, L lower triangular, U unit
+ * upper triangular, Pi a row permutation.  Column j takes its pivot from
+ * the rows j .. wend[j]-1 of its diagonal block (wend[j] = j + 1: no
+ * pivoting): the row of largest magnitude, ties going to the row that
+ * started in the smallest position of C.  That row is swapped with row j
+ * across all n columns; then U(j, c) = M(j, c) / M(j, j) for c > j and
+ * M(i, c) -= M(i, j) U(j, c) for i, c > j.  On return M holds L on and
+ * below the diagonal and U above it, and rho[i] is the row of C now in
+ * position i.  Returns -1, or the first column whose pivot is zero.  Zero
+ * entries of column j and of row j are skipped in the update (the result is
+ * the same; sparse C just goes faster).  nzr, nzc: workspace of n each.
+ */
+int64_t orc_lu_dense(int64_t n, double* M, const int64_t* wend, int64_t* rho, int64_t* nzr,
+                     int64_t* nzc) {
+  for (int64_t i = 0; i < n; ++i) rho[i] = i;
+  for (int64_t j = 0; j < n; ++j) {
+    double* colj = M + j * n;
+    int64_t p = j;
+    for (int64_t i = j + 1; i < wend[j]; ++i) {
+      double a = fabs(colj[i]), b = fabs(colj[p]);
+      if (a > b || (a == b && rho[i] < rho[p])) p = i;
+    }
+    if (p != j) {
+      for (int64_t c = 0; c < n; ++c) {
+        double tmp = M[c * n + j];
+        M[c * n + j] = M[c * n + p];
+        M[c * n + p] = tmp;
+      }
+      int64_t tr = rho[j];
+      rho[j] = rho[p];
+      rho[p] = tr;
+    }
+    double piv = colj[j];
+    if (piv == 0.0) return j;
+    int64_t nr = 0, nc = 0;
+    for (int64_t i = j + 1; i < n; ++i)
+      if (colj[i] != 0.0) nzr[nr++] = i;
+    for (int64_t c = j + 1; c < n; ++c) {
+      double* ujc = M + c * n + j;
+      if (*ujc != 0.0) {
+        *ujc /= piv;
+        nzc[nc++] = c;
+      }
+    }
+    for (int64_t t = 0; t < nc; ++t) {
+      double* colc = M + nzc[t] * n;
+      double u = colc[j];
+      for (int64_t q = 0; q < nr; ++q) colc[nzr[q]] -= colj[nzr[q]] * u;
+    }
+  }
+  return -1;
+}

@@ -218,3 +218,61 @@ def test_ldlt_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
 
 def test_ldlt_pins_pass_on_the_oracle(orc):
     assert ldlt_pins(orc) == set()
+
+
+LU_MUTATIONS = [
+    ("lu: pivot of smallest magnitude", "if (a > b || (a == b && rho[i] < rho[p])) p = i;",
+     "if (a < b || (a == b && rho[i] < rho[p])) p = i;"),
+    ("lu: ties to the largest original row", "if (a > b || (a == b && rho[i] < rho[p])) p = i;",
+     "if (a > b || (a == b && rho[i] > rho[p])) p = i;"),
+    ("lu: window ignored", "for (int64_t i = j + 1; i < wend[j]; ++i) {",
+     "for (int64_t i = j + 1; i < n; ++i) {"),
+    ("lu: factored columns not swapped", "for (int64_t c = 0; c < n; ++c) {\n        double tmp",
+     "for (int64_t c = j; c < n; ++c) {\n        double tmp"),
+    ("lu: row order not recorded", "rho[p] = tr;", "rho[p] = rho[j];"),
+    ("lu: U row multiplied by the pivot", "*ujc /= piv;", "*ujc *= piv;"),
+    ("lu: update sign flipped", "colc[nzr[q]] -= colj[nzr[q]] * u;",
+     "colc[nzr[q]] += colj[nzr[q]] * u;"),
+    ("lu: L_cj used for U_jc (transposed operand)", "double u = colc[j];",
+     "double u = colj[nzc[t]];"),
+]
+
+
+def lu_pins(orc):
+    import test_oracle_lu as t
+    bad = set()
+    for name, fn in [("dominant", lambda: t.test_no_pivoting_matches_scipy_on_column_dominant(orc, 1)),
+                     ("one window", lambda: t.test_one_window_is_partial_pivoting(orc, 0)),
+                     ("blocks", lambda: t.test_block_diagonal_windows_are_per_block_partial_pivoting(orc)),
+                     ("invariants", lambda: t.test_windowed_pivoting_invariants(orc, 4, 1)),
+                     ("cholesky", lambda: t.test_spd_without_pivoting_relates_to_cholesky(orc, 0)),
+                     ("tridiagonal", lambda: t.test_tridiagonal_closed_form(orc)),
+                     ("zero diagonal", lambda: t.test_zero_diagonal_needs_pivoting(orc)),
+                     ("ties", lambda: t.test_ties_go_to_the_smallest_original_row(orc))]:
+        try:
+            fn()
+        except Exception:
+            bad.add(name)
+    return bad
+
+
+@pytest.mark.parametrize("name,old,new", LU_MUTATIONS, ids=[m[0] for m in LU_MUTATIONS])
+def test_lu_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not unique: " + name
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib_path = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", str(lib_path), str(mutated),
+                           "-lm"])
+    saved = orc._load()
+    orc._lib = orc.load_library(str(lib_path))
+    try:
+        failed = lu_pins(orc)
+    finally:
+        orc._lib = saved
+    assert failed, "no pin caught: " + name
+
+
+def test_lu_pins_pass_on_the_oracle(orc):
+    assert lu_pins(orc) == set()
