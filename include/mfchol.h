@@ -244,6 +244,10 @@ int mf_symbolic_pattern(const mf_symbolic* s, int64_t* Lp, int32_t* Li);
  * exported etree, supernodes, counts and pattern never change with it. */
 int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent,
                                int32_t* level);
+/* First column of each internal front followed by n: nfronts + 1 entries
+ * (mf_symbolic_info.nfronts).  With relax = 0 the fronts are the
+ * fundamental supernodes. */
+int mf_symbolic_fronts(const mf_symbolic* s, int32_t* front_ptr);
 
 /* Autotuner (no paper counterpart; the paper tunes by hand).  Times the
  * numeric factorization of the given matrix and values in precision prec,
@@ -297,6 +301,52 @@ int mf_factor_create_ldlt(mf_handle* h, const mf_symbolic* s, int32_t prec,
  * column j of P A P^T).  Synchronous.  MF_ERR_INVALID for a Cholesky
  * factor. */
 int mf_factor_export_D(const mf_factor* f, double* D);
+
+/* As mf_factor_create, for the LU factorization of a general matrix with a
+ * structurally symmetric pattern (paper Sec. 5: besides Cholesky and
+ * LDL^T, Tacho factors general matrices whose sparsity structure is
+ * symmetric): Pi P A P^T = L U, L lower triangular, U unit upper triangular
+ * (Crout form), on the same analysis; the analysed pattern must be
+ * structurally symmetric, the values need not be symmetric.
+ *   pivot = 0: no pivoting (Pi = I); the factorization exists when every
+ *     leading principal minor of P A P^T is nonzero (for instance for
+ *     column diagonally dominant matrices).
+ *   pivot = 1: pivots looked for only within diagonal blocks (paper Sec. 5,
+ *     the comparison with SuperLU: Tacho searches each diagonal block for
+ *     its pivots instead of whole columns).  The diagonal blocks are the
+ *     64-column pieces into which each internal front's pivot columns are
+ *     cut from its first column (mf_symbolic_fronts).  Column j takes the
+ *     row of largest magnitude among the rows of its block not yet chosen,
+ *     ties going to the row that started first, so Pi only reorders rows
+ *     inside those blocks and L and U keep the analysed sparsity.
+ * Values are given to mf_factor_numeric as for Cholesky (all entries of the
+ * CSR pattern, both triangles); it returns MF_ERR_NOT_SPD for the first
+ * zero pivot (its column through mf_last_error_column).  Solves, refinement
+ * and serving take LU factors like Cholesky ones (SpTRSV variants 1 and 2;
+ * an analysis made for variant 3 or 4 is refused); FP32 factors use the FMA
+ * trailing update and refine in FP64 with an FP64 LU of the same kind as
+ * fallback.  Device memory: about twice that of a Cholesky factor.
+ * Errors: MF_ERR_INVALID for pivot not in {0, 1}, for an analysis of
+ * SpTRSV variant 3 or 4, or when an upper entry of A falls outside the
+ * analysed structure (pattern not structurally symmetric). */
+int mf_factor_create_lu(mf_handle* h, const mf_symbolic* s, int32_t prec, int32_t pivot,
+                        mf_factor** f);
+
+/* LU factor: U transposed in the layout of mf_factor_export_L (entry (i, j)
+ * of the pattern, i >= j, receives U(j, i); the diagonal is 1).
+ * Synchronous.  MF_ERR_INVALID for a factor that is not LU. */
+int mf_factor_export_U(const mf_factor* f, double* Ux);
+
+/* LU factor: rho[i] = the row of P A P^T (permuted numbering) that ended in
+ * pivot position i; the identity without pivoting.  Synchronous.  With
+ * pivoting, the rows of L are labelled as follows by mf_factor_export_L and
+ * mf_factor_export_columns: in a column j of internal front F, a pattern row
+ * i that is a pivot column of F holds L(i, j) (pivot order), and a row i of
+ * a later front keeps the label it had before that front pivoted, so it
+ * holds L(rho^{-1}(i), j).  U is not affected (its rows are pivot
+ * positions, its columns are never permuted).  MF_ERR_INVALID for a factor
+ * that is not LU. */
+int mf_factor_export_pivots(const mf_factor* f, int32_t* rho);
 
 /* Numerical factorization P A P^T = L L^T with the given values (CSR order
  * of the analysed pattern; nnz = rowptr[n] entries; host or device pointer

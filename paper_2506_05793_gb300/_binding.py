@@ -105,6 +105,10 @@ _SIGS = {
     "mf_symbolic_options": [_P, _P],
     "mf_factor_create_ldlt": [_P, _P, _I32, _P],
     "mf_factor_export_D": [_P, _P],
+    "mf_factor_create_lu": [_P, _P, _I32, _I32, _P],
+    "mf_factor_export_U": [_P, _P],
+    "mf_factor_export_pivots": [_P, _P],
+    "mf_symbolic_fronts": [_P, _P],
     "mf_factor_kind_items": [_P, _P, _P],
     "mf_ilu_symbolic": [_P, _I64, _P, _P, _I32, _P],
     "mf_ilu_info": [_P, _P, _P],
@@ -614,6 +618,32 @@ def mf_factor_create_ldlt(h, s, prec=MF_FP64):
     f = ctypes.c_void_p()
     _check(lib().mf_factor_create_ldlt(h, s, prec, ctypes.byref(f)))
     return f
+
+
+def mf_factor_create_lu(h, s, prec=MF_FP64, pivot=0):
+    """LU factor object, pivot 0 (none) or 1 (within diagonal blocks); see the C header."""
+    f = ctypes.c_void_p()
+    _check(lib().mf_factor_create_lu(h, s, prec, pivot, ctypes.byref(f)))
+    return f
+
+
+def mf_factor_export_U(f, nnz_L):
+    out = np.empty(nnz_L, dtype=np.float64)
+    _check(lib().mf_factor_export_U(f, _ptr(out)))
+    return out
+
+
+def mf_factor_export_pivots(f, n):
+    out = np.empty(n, dtype=np.int32)
+    _check(lib().mf_factor_export_pivots(f, _ptr(out)))
+    return out
+
+
+def mf_symbolic_fronts(s):
+    nf = mf_symbolic_get_info(s)["nfronts"]
+    out = np.empty(nf + 1, dtype=np.int32)
+    _check(lib().mf_symbolic_fronts(s, _ptr(out)))
+    return out
 
 
 def mf_factor_export_D(f, n):

@@ -170,6 +170,20 @@ struct mf_factor {
   int* qstate = nullptr;    // small-front queue: ticket, then one flag per front
   bool ldlt = false;        // LDL^T (unit L, pivots in D) instead of Cholesky
   void* Dp = nullptr;       // LDL^T pivots by permuted column (T[n])
+  // LU with a symmetric pattern: 1 without pivoting, 2 with pivots looked
+  // for within the diagonal blocks
+  int lu = 0;
+  void* Lu = nullptr;         // U^T in the layout of L (T[Lsize])
+  void* dinvu = nullptr;      // inverses of the U^T diagonal blocks (slots of dinv)
+  void* avu = nullptr;        // strictly upper entries of C in assembly order (T)
+  int64_t* uacol_ptr = nullptr;  // their assembly lists (n + 1 / entries / entries + 1 / sources)
+  int32_t* uarow = nullptr;
+  int64_t* uasrc_ptr = nullptr;
+  int64_t* uasrc = nullptr;
+  int64_t nnz_upper = 0;
+  uint8_t* piv = nullptr;     // pivoting: row taken by each pivot position of its 64-row block
+  mf::Item* lu_swap = nullptr;  // pivoting: (front, step) of the later pivot blocks of large fronts
+  int32_t lu_swap_count = 0;
   double* small = nullptr;  // per-RHS scalars for refinement
   // graph of the numeric factorization
   cudaStream_t cap_stream = nullptr;
@@ -213,6 +227,15 @@ struct mf_factor {
     cudaFree(av);
     cudaFree(qstate);
     cudaFree(Dp);
+    cudaFree(Lu);
+    cudaFree(dinvu);
+    cudaFree(avu);
+    cudaFree(uacol_ptr);
+    cudaFree(uarow);
+    cudaFree(uasrc_ptr);
+    cudaFree(uasrc);
+    cudaFree(piv);
+    cudaFree(lu_swap);
     delete fb64;
   }
 };
@@ -399,6 +422,13 @@ int mf_symbolic_get_info(const mf_symbolic* s, mf_symbolic_info* info) {
   return MF_OK;
 }
 
+int mf_symbolic_fronts(const mf_symbolic* s, int32_t* front_ptr) {
+  if (!s || !front_ptr) return set_error(MF_ERR_INVALID, "NULL argument");
+  for (size_t F = 0; F < s->sn.size(); ++F) front_ptr[F] = s->sn[F].first;
+  front_ptr[s->sn.size()] = (int32_t)s->n;
+  return MF_OK;
+}
+
 int mf_symbolic_etree(const mf_symbolic* s, int32_t* parent) {
   if (!s || (!parent && s->n)) return set_error(MF_ERR_INVALID, "NULL argument");
   std::copy(s->parent.begin(), s->parent.end(), parent);
@@ -454,23 +484,78 @@ int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent, int32_t* 
 // ---------------------------------------------------------------------------
 // Factor
 // ---------------------------------------------------------------------------
-static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt,
+static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt, int lu,
                          mf_factor** f);
 
 int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
-  return factor_create(h, s, prec, false, f);
+  return factor_create(h, s, prec, false, 0, f);
 }
 
 int mf_factor_create_ldlt(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
-  return factor_create(h, s, prec, true, f);
+  return factor_create(h, s, prec, true, 0, f);
 }
 
-static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt,
+int mf_factor_create_lu(mf_handle* h, const mf_symbolic* s, int32_t prec, int32_t pivot,
+                        mf_factor** f) {
+  if (pivot != 0 && pivot != 1) return set_error(MF_ERR_INVALID, "pivot must be 0 or 1");
+  return factor_create(h, s, prec, false, pivot ? 2 : 1, f);
+}
+
+// Device copies of the LU extras: U^T half, second update pool (in U),
+// inverses of the U^T blocks, upper assembly lists and values, pivots and
+// the reordering items of the later pivot blocks.
+static int lu_extras(mf_factor* F) {
+  const mf_symbolic* s = F->S;
+  const size_t es = elem_size(F->prec);
+  mf::UpperAssembly ua;
+  std::string err;
+  try {
+    const int rc = mf::build_upper_assembly(*s, ua, err);
+    if (rc != MF_OK) return set_error(rc, err);
+  } catch (const std::bad_alloc&) {
+    return set_error(MF_ERR_OOM, "host allocation failed");
+  }
+  F->nnz_upper = (int64_t)ua.row.size();
+  const int64_t inv_slots = s->keep_inv ? s->ninv : s->max_large;
+  MF_CK(cudaMalloc(&F->Lu, std::max<int64_t>(s->Lsize, 1) * es));
+  MF_CK(cudaMalloc(&F->dinvu, std::max<int64_t>(inv_slots, 1) * mf::kNB * mf::kNB * es));
+  MF_CK(cudaMalloc(&F->avu, std::max<int64_t>(F->nnz_upper, 1) * es));
+  auto up = [](void** d, const void* h, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(d, std::max<size_t>(bytes, 8));
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice);
+    return e;
+  };
+  MF_CK(up((void**)&F->uacol_ptr, ua.col_ptr.data(), ua.col_ptr.size() * sizeof(int64_t)));
+  MF_CK(up((void**)&F->uarow, ua.row.data(), ua.row.size() * sizeof(int32_t)));
+  MF_CK(up((void**)&F->uasrc_ptr, ua.src_ptr.data(), ua.src_ptr.size() * sizeof(int64_t)));
+  MF_CK(up((void**)&F->uasrc, ua.src.data(), ua.src.size() * sizeof(int64_t)));
+  if (F->lu == 2) {
+    MF_CK(cudaMalloc(&F->piv, std::max<int64_t>(s->n, 1)));
+    // pivot positions not factored by a pivoting kernel keep their own row
+    MF_CK(cudaMemset(F->piv, 0, std::max<int64_t>(s->n, 1)));
+    std::vector<mf::Item> sw;
+    for (const mf::Launch& L : s->fsched)
+      if (L.kind == mf::K_POTRF)
+        for (int32_t i = 0; i < L.count; ++i) {
+          const mf::Item& it = s->items[L.item_off + i];
+          if (it.t >= 1) sw.push_back({it.s, it.t, 0, 0});
+        }
+    F->lu_swap_count = (int32_t)sw.size();
+    MF_CK(up((void**)&F->lu_swap, sw.data(), sw.size() * sizeof(mf::Item)));
+  }
+  return MF_OK;
+}
+
+static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt, int lu,
                          mf_factor** f) {
   if (!h || !s || !f) return set_error(MF_ERR_INVALID, "NULL argument");
   if (prec != MF_FP64 && prec != MF_FP32) return set_error(MF_ERR_INVALID, "bad precision");
   *f = nullptr;
-  const int64_t need = factor_bytes(s, prec);
+  if (lu && (s->pinv || s->v4))
+    return set_error(MF_ERR_INVALID, "LU factors solve with SpTRSV variants 1 and 2 only");
+  // LU keeps a second half of the same size as L and the update matrices
+  const int64_t need = factor_bytes(s, prec) +
+                       (lu ? (s->Lsize + s->Usize + s->nnz_lower) * (int64_t)elem_size(prec) : 0);
   if (h->opt.budget_bytes > 0 && need > h->opt.budget_bytes)
     return set_error(MF_ERR_OOM, "factor exceeds the device budget");
   std::unique_ptr<mf_factor> F(new (std::nothrow) mf_factor());
@@ -482,7 +567,8 @@ static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool 
   if (rc != MF_OK) return rc;
   const size_t es = elem_size(prec);
   MF_CK(cudaMalloc(&F->L, std::max<int64_t>(s->Lsize, 1) * es));
-  MF_CK(cudaMalloc(&F->U, std::max<int64_t>(s->Usize, 1) * es));
+  // LU: the transposed upper update matrices follow the lower ones
+  MF_CK(cudaMalloc(&F->U, std::max<int64_t>(s->Usize, 1) * es * (lu ? 2 : 1)));
   MF_CK(cudaMalloc(&F->vals, std::max<int64_t>(s->nnzA, 1) * sizeof(double)));
   // status words (all-ones when clear): [0] first non-positive pivot column,
   // [1] a bounded wait of the factorization gave up, [2] one of the solve
@@ -502,9 +588,15 @@ static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool 
   MF_CK(mf::solve_kernels_init(prec));
   F->ldlt = ldlt;
   if (ldlt) MF_CK(cudaMalloc(&F->Dp, std::max<int64_t>(s->n, 1) * es));
+  F->lu = lu;
+  if (lu) {
+    const int rc = lu_extras(F.get());
+    if (rc != MF_OK) return rc;
+  }
   // LDL^T: the pivots enter the trailing update as a scaling of one operand,
-  // which the FMA tiles do; the tensor-core path stays with Cholesky
-  if (prec == MF_FP32 && h->opt.tc && !ldlt) {
+  // and LU updates with two different operands, which the FMA tiles do; the
+  // tensor-core path stays with Cholesky
+  if (prec == MF_FP32 && h->opt.tc && !ldlt && !lu) {
     F->tc = true;
     MF_CK(mf::factor_tc_init());
     const int64_t srows = std::max<int64_t>(s->split_rows, 1);
@@ -525,8 +617,7 @@ static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool 
 // Enqueue the numeric factorization on st.  With `capturing` the calls are
 // being recorded into a CUDA graph: profile events then become event-record
 // nodes of the graph, so per-launch timing also works for graph replays.
-static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capturing) {
-  const mf_symbolic* S = F->S;
+static mf::FactorArgs factor_args(const mf_factor* F) {
   mf::FactorArgs a;
   a.sym = F->ds->d;
   a.vals = F->vals;
@@ -544,9 +635,30 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
   a.qstate = F->qstate;
   a.wait_polls = F->wait_polls;
   a.D = F->Dp;
+  if (F->lu) {
+    a.lu = F->lu;
+    a.Lu = F->Lu;
+    a.Uu = static_cast<unsigned char*>(F->U) + F->S->Usize * elem_size(F->prec);
+    a.dinvu = F->dinvu;
+    a.uacol_ptr = F->uacol_ptr;
+    a.uarow = F->uarow;
+    a.avu = F->avu;
+    a.piv = F->piv;
+    a.lu_swap = F->lu_swap;
+    a.lu_swap_count = F->lu_swap_count;
+  }
+  return a;
+}
+
+static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capturing) {
+  const mf_symbolic* S = F->S;
+  const mf::FactorArgs a = factor_args(F);
   const std::vector<mf::Launch>& sched = F->tc ? S->fsched_tc : S->fsched;
   MF_CK(cudaMemsetAsync(F->status, 0xff, 2 * sizeof(unsigned long long), st));
   MF_CK(mf::launch_gather_values(F->prec, a, S->nnz_lower, st));
+  if (F->lu)
+    MF_CK(mf::launch_gather_upper(F->prec, F->uasrc_ptr, F->uasrc, F->vals, F->avu, F->nnz_upper,
+                                  st));
   if (profile && F->ev.size() < 2 * sched.size()) {
     const size_t old = F->ev.size();
     F->ev.resize(2 * sched.size());
@@ -593,6 +705,7 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
     }
   }
   if (pending) MF_CK(cudaStreamWaitEvent(F->crit, F->ev_side, 0));
+  if (F->lu == 2) MF_CK(mf::launch_lu_swap(F->prec, a, F->crit));
   MF_CK(cudaEventRecord(F->ev_out, F->crit));
   MF_CK(cudaStreamWaitEvent(st, F->ev_out, 0));
   return MF_OK;
@@ -665,6 +778,7 @@ int mf_factor_check(mf_factor* f, void* stream) {
     return set_error(MF_ERR_TIMEOUT, "a bounded device wait in the factorization gave up");
   if (bad != ~0ull) {
     set_error(MF_ERR_NOT_SPD, f->ldlt ? "zero pivot in the LDL^T factorization"
+                              : f->lu ? "zero pivot in the LU factorization"
                                       : "matrix is not positive definite");
     g_errcol = (int64_t)bad;
     return MF_ERR_NOT_SPD;
@@ -734,8 +848,35 @@ int mf_factor_export_D(const mf_factor* f, double* D) {
   return MF_OK;
 }
 
+static int export_columns(const mf_factor* f, const void* base, int64_t j0, int64_t j1,
+                          double* Lx);
+
 int mf_factor_export_columns(const mf_factor* f, int64_t j0, int64_t j1, double* Lx) {
   if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  return export_columns(f, f->L, j0, j1, Lx);
+}
+
+int mf_factor_export_U(const mf_factor* f, double* Ux) {
+  if (!f) return set_error(MF_ERR_INVALID, "NULL factor");
+  if (!f->lu) return set_error(MF_ERR_INVALID, "not an LU factor");
+  return export_columns(f, f->Lu, 0, f->S->n, Ux);
+}
+
+int mf_factor_export_pivots(const mf_factor* f, int32_t* rho) {
+  if (!f || (!rho && f->S->n)) return set_error(MF_ERR_INVALID, "NULL argument");
+  if (!f->lu) return set_error(MF_ERR_INVALID, "not an LU factor");
+  const int64_t n = f->S->n;
+  std::vector<uint8_t> p(f->piv ? n : 0);
+  MF_CK(cudaDeviceSynchronize());
+  if (f->piv && n) MF_CK(cudaMemcpy(p.data(), f->piv, n, cudaMemcpyDeviceToHost));
+  for (const mf::SnInfo& I : f->S->sn)
+    for (int32_t c = 0; c < I.k; ++c)
+      rho[I.first + c] = f->piv ? I.first + (c & ~(mf::kNB - 1)) + p[I.first + c] : I.first + c;
+  return MF_OK;
+}
+
+static int export_columns(const mf_factor* f, const void* base, int64_t j0, int64_t j1,
+                          double* Lx) {
   const mf_symbolic* S = f->S;
   if (j0 < 0 || j1 < j0 || j1 > S->n || (!Lx && j1 > j0))
     return set_error(MF_ERR_INVALID, "invalid column range");
@@ -759,7 +900,7 @@ int mf_factor_export_columns(const mf_factor* f, int64_t j0, int64_t j1, double*
     } catch (const std::bad_alloc&) {
       return set_error(MF_ERR_OOM, "host allocation failed");
     }
-    MF_CK(cudaMemcpy(buf.data(), static_cast<const unsigned char*>(f->L) + I.Loff * es,
+    MF_CK(cudaMemcpy(buf.data(), static_cast<const unsigned char*>(base) + I.Loff * es,
                      buf.size(), cudaMemcpyDeviceToHost));
     const float* b32 = reinterpret_cast<const float*>(buf.data());
     const double* b64 = reinterpret_cast<const double*>(buf.data());
@@ -1073,10 +1214,17 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.dinv = S->keep_inv ? f->dinv : nullptr;
   a.P = f->P;
   a.PT = f->PT;
+  a.piv = f->piv;
   for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   // LDL^T: z = D^{-1} z between the sweeps (the forward results sit in Y,
   // or for SpTRSV variant 4 in the first n x nrhs values of W)
   if (f->ldlt) MF_CK(mf::launch_dscale(f->prec, S->v4 ? W : Y, f->Dp, S->n, cn, st));
+  // LU: the backward sweep solves U x = y with U^T, stored like L
+  if (f->lu) {
+    a.L = f->Lu;
+    a.dinv = S->keep_inv ? f->dinvu : nullptr;
+    a.piv = nullptr;
+  }
   for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, X, ldx, S->n, cn, scale, accumulate, st));
   return MF_OK;
@@ -1234,17 +1382,7 @@ int mf_diag_small_queue(mf_factor* f, int32_t skip, void* stream) {
     return set_error(MF_ERR_INVALID, "factor has no small-front queue or no numeric values");
   if (skip < 1 || skip >= sched[0].count) return set_error(MF_ERR_INVALID, "skip out of range");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  mf::FactorArgs a;
-  a.sym = f->ds->d;
-  a.vals = f->vals;
-  a.L = f->L;
-  a.U = f->U;
-  a.status = f->status;
-  a.dinv = f->dinv;
-  a.P = f->P;
-  a.av = f->av;
-  a.qstate = f->qstate;
-  a.wait_polls = f->wait_polls;
+  const mf::FactorArgs a = factor_args(f);
   const int first = skip;
   MF_CK(cudaMemsetAsync(f->qstate, 0, (S->sn.size() + 1) * sizeof(int), st));
   MF_CK(cudaMemcpyAsync(f->qstate, &first, sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1360,7 +1498,7 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
       return set_error(MF_ERR_STAGNATION, "iterative refinement stagnated");
     }
     if (!f->fb64) {
-      rc = factor_create(f->h, S, MF_FP64, f->ldlt, &f->fb64);
+      rc = factor_create(f->h, S, MF_FP64, f->ldlt, f->lu, &f->fb64);
       if (rc != MF_OK) return rc;
     }
     f->fb64->wait_polls = f->wait_polls;

@@ -57,6 +57,19 @@ struct FD {
   int* qstate;          // small-front queue: ticket counter, then one flag per front
   int wait_polls;       // polls before a queue wait gives up
   T* D;                 // LDL^T: the pivots by permuted column; nullptr for Cholesky
+  // LU (lu != 0): Lu holds U^T in the layout of L and Uu the transposed
+  // update matrices; Lb is the trailing update's second operand and dinv_t
+  // the inverse the panel solve multiplies by (Cholesky: L and dinv)
+  const T* Lb;
+  const T* dinv_t;
+  int lu;
+  T* Lu;
+  T* Uu;
+  T* dinvu;
+  const int64_t* uacol_ptr;
+  const int32_t* uarow;
+  const T* avu;
+  uint8_t* piv;  // pivoting: row taken by each pivot position of a 64-row block
 };
 
 template <typename T>
@@ -86,7 +99,47 @@ FD<T> make_fd(const FactorArgs& a) {
   d.qstate = a.qstate;
   d.wait_polls = a.wait_polls > 0 ? a.wait_polls : kQueueSpin;
   d.D = static_cast<T*>(a.D);
+  d.lu = a.lu;
+  d.Lu = static_cast<T*>(a.Lu);
+  d.Uu = static_cast<T*>(a.Uu);
+  d.dinvu = static_cast<T*>(a.dinvu);
+  d.uacol_ptr = a.uacol_ptr;
+  d.uarow = a.uarow;
+  d.avu = static_cast<const T*>(a.avu);
+  d.piv = a.piv;
+  // LU, lower half: L21 = F21 U11^{-1} (the inverse of the U^T block), the
+  // update's second operand is U^T
+  d.Lb = a.lu ? d.Lu : d.L;
+  d.dinv_t = a.lu ? d.dinvu : d.dinv;
   return d;
+}
+
+// LU with a symmetric pattern (paper Sec. 5): the upper half of a front is
+// kept transposed, U^T in the layout of L, so the same assembly, panel solve
+// and trailing-update kernels serve it with the two halves exchanged:
+// U12^T = (Pi F12)^T L11^{-T} and (F22 - L21 U12)^T = F22^T - U12^T L21^T.
+// These kernels run twice as many CTAs for an LU factor; the second half
+// takes the upper view.
+template <typename T>
+__device__ __forceinline__ FD<T> upper_view(const FD<T>& d) {
+  FD<T> e = d;
+  e.L = d.Lu;
+  e.Lb = d.L;
+  e.U = d.Uu;
+  e.acol_ptr = d.uacol_ptr;
+  e.arow = d.uarow;
+  e.av = d.avu;
+  e.dinv_t = d.dinv;
+  return e;
+}
+
+// Block index within the launch's items, and whether this CTA works on the
+// upper half of an LU factor.
+template <typename T>
+__device__ __forceinline__ int lu_block(const FD<T>& d, bool& upper) {
+  const int half = (int)(gridDim.x >> 1);
+  upper = d.lu != 0 && (int)blockIdx.x >= half;
+  return upper ? (int)blockIdx.x - half : (int)blockIdx.x;
 }
 
 // Column c of front f: element (r, c) is col[r] (r >= k when c >= k).
@@ -181,10 +234,155 @@ __device__ __forceinline__ void small_front_body(const FD<T>& d, int s, T* F) {
     for (int r = lane; r < m; r += 32) Up[(int64_t)c * m + r] = F[(k + c) * nf + k + r];
 }
 
+// Pivot search of LU with pivoting within diagonal blocks (paper Sec. 5:
+// Tacho looks for pivots only inside each diagonal block): warp 0 returns
+// the row of largest |col[i]| over i in [j, we), ties going to the row
+// that started in the smallest position (orig[i]).
 template <typename T>
+__device__ __forceinline__ int block_pivot(const T* col, const int* orig, int j, int we) {
+  const int lane = threadIdx.x & 31;
+  T bv = T(-1);
+  int bo = 1 << 30, bi = j;
+  for (int i = j + lane; i < we; i += 32) {
+    const T a = fabs(col[i]);
+    const int o = orig[i];
+    if (a > bv || (a == bv && o < bo)) {
+      bv = a;
+      bo = o;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const T ov = __shfl_down_sync(0xffffffffu, bv, off);
+    const int oo = __shfl_down_sync(0xffffffffu, bo, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ov > bv || (ov == bv && oo < bo)) {
+      bv = ov;
+      bo = oo;
+      bi = oi;
+    }
+  }
+  return __shfl_sync(0xffffffffu, bi, 0);
+}
+
+// Unblocked right-looking LU in Crout form (L lower, U unit upper) of the
+// first k columns of an n x n block held column-major in shared memory
+// (ld): for j < k, U(j, c) = F(j, c) / F(j, j) for c > j, then
+// F(i, c) -= F(i, j) U(j, c) for i, c > j.  With `orig` (pivoting) column
+// j first takes the largest-magnitude row among the rows j .. end of its
+// 64-row block (rows < k only) and swaps it with row j across all n
+// columns; orig tracks where each row started.  Records the first zero
+// pivot (global column col0 + j).
+template <typename T>
+__device__ __forceinline__ void smem_partial_lu(T* F, int ld, int n, int k, int col0,
+                                unsigned long long* status, int* orig) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ int s_p;
+  for (int j = 0; j < k; ++j) {
+    if (orig) {
+      if (warp == 0) {
+        const int p = block_pivot(F + j * ld, orig, j, min(k, (j & ~(kNB - 1)) + kNB));
+        if (lane == 0) s_p = p;
+      }
+      __syncthreads();
+      const int p = s_p;
+      if (p != j) {
+        for (int c = tid; c < n; c += blockDim.x) {
+          const T t = F[c * ld + j];
+          F[c * ld + j] = F[c * ld + p];
+          F[c * ld + p] = t;
+        }
+        if (tid == 0) {
+          const int t = orig[j];
+          orig[j] = orig[p];
+          orig[p] = t;
+        }
+      }
+      __syncthreads();
+    }
+    const T piv = F[j * ld + j];
+    if (tid == 0 && !(piv != T(0))) atomicMin(status, (unsigned long long)(col0 + j));
+    const T rinv = T(1) / piv;
+    for (int c = j + 1 + tid; c < n; c += blockDim.x) F[c * ld + j] *= rinv;
+    __syncthreads();
+    for (int c = j + 1 + warp; c < n; c += nw) {
+      const T u = F[c * ld + j];
+      for (int i = j + 1 + lane; i < n; i += 32) F[c * ld + i] -= F[j * ld + i] * u;
+    }
+    __syncthreads();
+  }
+}
+
+// Small front of an LU factor: the whole front F (lower entries of C into
+// their columns, upper entries into their rows, the children's lower and
+// transposed-upper update matrices) in shared memory with leading dimension
+// nf + 1, partial LU, then L, U^T (unit diagonal) and the two halves of the
+// update matrix written out.
+template <typename T>
+__device__ __forceinline__ void small_front_lu(const FD<T>& d, int s, T* F) {
+  __shared__ int orig[kSmallMax];
+  const SnInfo f = d.sn[s];
+  const int k = f.k, m = f.m, nf = k + m, ld = nf + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < nf * ld; i += blockDim.x) F[i] = T(0);
+  for (int i = tid; i < k; i += blockDim.x) orig[i] = i;
+  __syncthreads();
+  for (int c = warp; c < k; c += nw) {
+    const int g = f.first + c;
+    for (int64_t e = d.acol_ptr[g] + lane; e < d.acol_ptr[g + 1]; e += 32)
+      F[c * ld + d.arow[e]] = d.av[e];
+    for (int64_t e = d.uacol_ptr[g] + lane; e < d.uacol_ptr[g + 1]; e += 32)
+      F[d.uarow[e] * ld + c] = d.avu[e];
+  }
+  __syncthreads();
+  for (int ci = 0; ci < f.nchild; ++ci) {
+    const SnInfo ch = d.sn[d.children[f.child_begin + ci]];
+    const int mc = ch.m;
+    const int32_t* map = d.relmap + ch.map_off;
+    const T* Ul = d.U + ch.Uoff;
+    const T* Uh = d.Uu + ch.Uoff;
+    for (int jc = warp; jc < mc; jc += nw) {
+      const int dc = map[jc];
+      const T* ul = Ul + (int64_t)jc * mc;
+      const T* uh = Uh + (int64_t)jc * mc;
+      for (int ic = jc + lane; ic < mc; ic += 32) {
+        const int di = map[ic];
+        F[dc * ld + di] += __ldcg(ul + ic);
+        if (ic > jc) F[di * ld + dc] += __ldcg(uh + ic);
+      }
+    }
+    __syncthreads();
+  }
+  smem_partial_lu(F, ld, nf, k, f.first, d.status, d.piv ? orig : nullptr);
+  T* Lp = d.L + f.Loff;
+  T* Up = d.Lu + f.Loff;
+  for (int c = warp; c < k; c += nw)
+    for (int r = lane; r < nf; r += 32) {
+      Lp[(int64_t)c * nf + r] = r >= c ? F[c * ld + r] : T(0);
+      Up[(int64_t)c * nf + r] = r > c ? F[r * ld + c] : (r == c ? T(1) : T(0));
+    }
+  if (d.piv)
+    for (int i = tid; i < k; i += blockDim.x) d.piv[f.first + i] = (uint8_t)(orig[i] - (i & ~(kNB - 1)));
+  T* Ul = d.U + f.Uoff;
+  T* Uh = d.Uu + f.Uoff;
+  for (int c = warp; c < m; c += nw)
+    for (int r = lane; r < m; r += 32) {
+      Ul[(int64_t)c * m + r] = F[(k + c) * ld + k + r];
+      Uh[(int64_t)c * m + r] = F[(k + r) * ld + k + c];
+    }
+}
+
+template <typename T, bool LU>
+__device__ __forceinline__ void small_front(const FD<T>& d, int s, T* F) {
+  if (LU) small_front_lu(d, s, F);
+  else small_front_body(d, s, F);
+}
+
+template <typename T, bool LU>
 __global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  small_front_body(d, d.items[item_off + blockIdx.x].s, reinterpret_cast<T*>(smem_raw));
+  small_front<T, LU>(d, d.items[item_off + blockIdx.x].s, reinterpret_cast<T*>(smem_raw));
 }
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
@@ -204,8 +402,8 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
 // bounded (wait_polls polls 128 ns apart): when it runs out the CTA records
 // MF_ERR_TIMEOUT in status[1] and goes on, so the launch always ends.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_small_queue(FD<T> d, int64_t item_off, int count) {
+template <typename T, bool LU>
+__global__ void __launch_bounds__(kQueueThreads) k_small_queue(FD<T> d, int64_t item_off, int count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ticket;
   int* ticket = d.qstate;
@@ -231,7 +429,7 @@ __global__ void __launch_bounds__(256) k_small_queue(FD<T> d, int64_t item_off, 
       }
     }
     __syncthreads();
-    small_front_body(d, s, reinterpret_cast<T*>(smem_raw));
+    small_front<T, LU>(d, s, reinterpret_cast<T*>(smem_raw));
     // every thread's stores are ordered before thread 0's release by the
     // CTA barrier; the GPU-scope release store is cumulative
     __syncthreads();
@@ -250,8 +448,11 @@ __global__ void __launch_bounds__(256) k_small_queue(FD<T> d, int64_t item_off, 
 // relative map; the one landing on column c is found by bisection.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_assemble(FD<T> d, int64_t item_off) {
-  const Item it = d.items[item_off + blockIdx.x];
+__global__ void __launch_bounds__(256) k_assemble(FD<T> d0, int64_t item_off) {
+  bool upper;
+  const int bid = lu_block(d0, upper);
+  const FD<T> d = upper ? upper_view(d0) : d0;
+  const Item it = d.items[item_off + bid];
   const SnInfo f = d.sn[it.s];
   const int k = f.k, nf = k + f.m, c0 = it.a, c1 = it.b;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -518,6 +719,145 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
 }
 
 // ---------------------------------------------------------------------------
+// LU (paper Sec. 5), large fronts, panel step t: the b x b diagonal block
+// F = [lower part from L, upper part from U^T] (padded with the identity to
+// 64 x 64), one CTA per front: Crout LU Pi F = L U (U unit upper), with
+// pivoting Pi chosen within the block (largest magnitude in the column among
+// the block's remaining rows); L and U^T go back to the two halves of the
+// front, their inverses to the slots of dinv and dinvu, and Pi to piv.
+// Nothing outside the block moves here: the upper half's panel solve reads
+// F12 in pivot order, and the rows' earlier columns of the front are
+// reordered once the factorization is done (k_lu_swap).
+// ---------------------------------------------------------------------------
+template <typename T>
+constexpr size_t getrf_smem() {
+  return (size_t)3 * kNB * (kNB + 1) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_getrf(FD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ld = kNB + 1;
+  T* A = reinterpret_cast<T*>(smem_raw);  // A[c * ld + r] = F(r, c), then L / U
+  T* Yl = A + kNB * ld;                   // L^{-1}, column-major
+  T* Yu = Yl + kNB * ld;                  // (U^T)^{-1}; first the U^T block as loaded
+  __shared__ int orig[kNB];
+  __shared__ int s_p;
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int64_t nf = (int64_t)f.k + f.m;
+  const int c0 = it.t * kNB;
+  const int b = min(kNB, f.k - c0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* FL = d.L + f.Loff + (int64_t)c0 * nf + c0;  // element (r, c) at [c * nf + r]
+  T* FU = d.Lu + f.Loff + (int64_t)c0 * nf + c0;
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, r = idx % kNB;
+    const bool in = r < b && c < b;
+    A[c * ld + r] = in ? (r >= c ? FL[(int64_t)c * nf + r] : T(0)) : (r == c ? T(1) : T(0));
+    Yu[c * ld + r] = (in && r > c) ? FU[(int64_t)c * nf + r] : T(0);
+  }
+  if (tid < kNB) orig[tid] = tid;
+  __syncthreads();
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, r = idx % kNB;
+    if (r < c) A[c * ld + r] = Yu[r * ld + c];  // F(r, c) = U^T(c, r)
+  }
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (d.piv) {
+      if (warp == 0) {
+        const int p = block_pivot(A + j * ld, orig, j, b);
+        if (lane == 0) s_p = p;
+      }
+      __syncthreads();
+      const int p = s_p;
+      if (p != j) {
+        if (tid < kNB) {
+          const T t = A[tid * ld + j];
+          A[tid * ld + j] = A[tid * ld + p];
+          A[tid * ld + p] = t;
+        }
+        if (tid == 0) {
+          const int t = orig[j];
+          orig[j] = orig[p];
+          orig[p] = t;
+        }
+      }
+      __syncthreads();
+    }
+    const T piv = A[j * ld + j];
+    if (tid == 0 && !(piv != T(0))) atomicMin(d.status, (unsigned long long)(f.first + c0 + j));
+    const T rinv = T(1) / piv;
+    if (tid > j && tid < b) A[tid * ld + j] *= rinv;  // U(j, c), c = tid
+    __syncthreads();
+    const int nt = b - j - 1;
+    for (int e = tid; e < nt * nt; e += blockDim.x) {
+      const int c = j + 1 + e / nt, r = j + 1 + e % nt;
+      A[c * ld + r] -= A[j * ld + r] * A[c * ld + j];
+    }
+    __syncthreads();
+  }
+  // inverses by column substitution: thread c < 64 solves L y = e_c,
+  // thread 64 + c solves U^T y = e_c (unit diagonal, U^T(i, q) = A(q, i))
+  if (tid < 2 * kNB) {
+    const int c = tid & (kNB - 1);
+    const bool up = tid >= kNB;
+    T* Y = up ? Yu : Yl;
+    for (int i = 0; i < kNB; ++i) {
+      T y = T(0);
+      if (i >= c) {
+        T acc = i == c ? T(1) : T(0);
+        for (int q = c; q < i; ++q) acc -= (up ? A[i * ld + q] : A[q * ld + i]) * Y[c * ld + q];
+        y = up ? acc : acc / A[i * ld + i];
+      }
+      Y[c * ld + i] = y;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < b * b; idx += blockDim.x) {
+    const int cc = idx / b, rr = idx % b;
+    if (rr >= cc) FL[(int64_t)cc * nf + rr] = A[cc * ld + rr];
+    if (rr >= cc) FU[(int64_t)cc * nf + rr] = rr == cc ? T(1) : A[rr * ld + cc];
+  }
+  if (d.piv && tid < b) d.piv[f.first + c0 + tid] = (uint8_t)orig[tid];
+  T* Dl = d.dinv + (int64_t)it.b * kNB * kNB;
+  T* Du = d.dinvu + (int64_t)it.b * kNB * kNB;
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int cc = idx / kNB, rr = idx % kNB;
+    Dl[idx] = Yl[cc * ld + rr];
+    Du[idx] = Yu[cc * ld + rr];
+  }
+}
+
+// LU with pivoting, after the factorization: in a large front, the rows of
+// each later 64-row pivot block t take the order of their pivots in the
+// front's earlier columns too (k_getrf reordered them only from the block
+// on), so that every pivot row of a front is stored in pivot order.  One
+// CTA per (front, t >= 1); warp w moves columns w, w + 8, ...; lanes hold
+// rows lane and lane + 32 and take their new values by shuffles.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lu_swap(FD<T> d, const Item* items) {
+  const Item it = items[blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int64_t nf = (int64_t)f.k + f.m;
+  const int c0 = it.t * kNB, b = min(kNB, f.k - c0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint8_t* pv = d.piv + f.first + c0;
+  const int s0 = lane < b ? (int)pv[lane] : lane;
+  const int s1 = lane + 32 < b ? (int)pv[lane + 32] : lane + 32;
+  for (int c = warp; c < c0; c += 8) {
+    T* col = d.L + f.Loff + (int64_t)c * nf + c0;
+    const T v0 = lane < b ? col[lane] : T(0);
+    const T v1 = lane + 32 < b ? col[lane + 32] : T(0);
+    const T a0 = __shfl_sync(0xffffffffu, v0, s0 & 31), a1 = __shfl_sync(0xffffffffu, v1, s0 & 31);
+    const T b0 = __shfl_sync(0xffffffffu, v0, s1 & 31), b1 = __shfl_sync(0xffffffffu, v1, s1 & 31);
+    if (lane < b) col[lane] = s0 < 32 ? a0 : a1;
+    if (lane + 32 < b) col[lane + 32] = s1 < 32 ? b0 : b1;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Large fronts, panel step t: rows [r0, r0 + kTrsmRows) of the panel below
 // the diagonal block, X = A L_tt^{-T} as a product with the inverse from
 // k_potrf.  Thread (r, g) computes X(r, j) for j = 16 g .. 16 g + 15.
@@ -528,12 +868,15 @@ constexpr size_t trsm_smem() {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
+__global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  bool upper;
+  const int bid = lu_block(d0, upper);
+  const FD<T> d = upper ? upper_view(d0) : d0;
   T(*As)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // As[c][r] = A(r0 + r, c0 + c)
   T(*Li)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(
       smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));          // Li[c][j] = Linv(j, c)
-  const Item it = d.items[item_off + blockIdx.x];
+  const Item it = d.items[item_off + bid];
   const SnInfo f = d.sn[it.s];
   const int nf = f.k + f.m;
   const int c0 = it.t * kNB;
@@ -541,7 +884,10 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
   const int r0 = it.a;
   const int rows = min(kTrsmRows, nf - r0);
   const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
-  const T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
+  const T* Dv = d.dinv_t + (int64_t)it.b * kNB * kNB;
+  // LU with pivoting, upper half: the columns of F12^T come in the pivot
+  // order of the diagonal block (Pi F12), the rows' own permutation
+  const uint8_t* pv = (upper && d.piv) ? d.piv + f.first + c0 : nullptr;
   {
     // all global loads of this thread in flight before the first shared store
     constexpr int PER = kNB * kNB / 256;
@@ -550,7 +896,8 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d, int64_t item_off) {
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int idx = tid + u * 256, c = idx / kNB, rr = idx % kNB;
-      va[u] = (c < b && rr < rows) ? P[(int64_t)c * nf + rr] : T(0);
+      const int cs = (pv && c < b) ? (int)pv[c] : c;
+      va[u] = (c < b && rr < rows) ? P[(int64_t)cs * nf + rr] : T(0);
       vl[u] = Dv[idx];
     }
 #pragma unroll
@@ -627,12 +974,15 @@ constexpr size_t syrk_smem() {
 }
 
 template <typename T, int TILE>
-__global__ void __launch_bounds__(256) k_syrk(FD<T> d, int64_t item_off) {
+__global__ void __launch_bounds__(256) k_syrk(FD<T> d0, int64_t item_off) {
   constexpr int R = TILE / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T(*As)[TILE] = reinterpret_cast<T(*)[TILE]>(smem_raw);
   T(*Bs)[TILE] = reinterpret_cast<T(*)[TILE]>(smem_raw + (size_t)kNB * TILE * sizeof(T));
-  const Item it = d.items[item_off + blockIdx.x];
+  bool upper;
+  const int bid = lu_block(d0, upper);
+  const FD<T> d = upper ? upper_view(d0) : d0;
+  const Item it = d.items[item_off + bid];
   const SnInfo f = d.sn[it.s];
   const int nf = f.k + f.m;
   const int c0 = it.t * kNB;
@@ -641,13 +991,15 @@ __global__ void __launch_bounds__(256) k_syrk(FD<T> d, int64_t item_off) {
   const int rI = p0 + it.a * TILE, rJ = p0 + it.b * TILE;
   const int tid = threadIdx.x;
   const T* P = d.L + f.Loff + (int64_t)c0 * nf;
+  const T* Pb = d.Lb + f.Loff + (int64_t)c0 * nf;  // LU: the other half
   for (int idx = tid; idx < b * TILE; idx += blockDim.x) {
     const int q = idx / TILE, r = idx % TILE;
     const T* col = P + (int64_t)q * nf;
+    const T* colb = Pb + (int64_t)q * nf;
     As[q][r] = (rI + r < nf) ? col[rI + r] : T(0);
     // LDL^T: C -= P_I D P_J^T, the pivots folded into the B operand
     const T w = d.D ? d.D[f.first + c0 + q] : T(1);
-    Bs[q][r] = (rJ + r < nf) ? col[rJ + r] * w : T(0);
+    Bs[q][r] = (rJ + r < nf) ? colb[rJ + r] * w : T(0);
   }
   __syncthreads();
   const int tr = tid & 15, tc = tid >> 4;
@@ -904,13 +1256,31 @@ __global__ void k_gather_values(const int64_t* asrc_ptr, const int64_t* asrc, co
   }
 }
 
+// Shared memory of a small front of size class `param` (LU pads the leading
+// dimension by one).
+template <typename T>
+size_t small_smem(int param, bool lu) {
+  return (size_t)param * (param + (lu ? 1 : 0)) * sizeof(T);
+}
+
 template <typename T>
 cudaError_t init_t() {
-  cudaError_t e = cudaFuncSetAttribute(k_small_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kSmallMax * kSmallMax * (int)sizeof(T));
+  const int small_max = (int)small_smem<T>(kSmallMax, false);
+  const int small_max_lu = (int)small_smem<T>(kSmallMax, true);
+  cudaError_t e = cudaFuncSetAttribute(k_small_front<T, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, small_max);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_small_queue<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kSmallMax * kSmallMax * (int)sizeof(T));
+  e = cudaFuncSetAttribute(k_small_front<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           small_max_lu);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_small_queue<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           small_max);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_small_queue<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           small_max_lu);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_getrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)getrf_smem<T>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem<T>());
@@ -938,36 +1308,44 @@ template <typename T>
 cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
   const FD<T> d = make_fd<T>(a);
   const dim3 grid(L.count);
+  // LU: assembly, panel solve and trailing update run both halves
+  const dim3 grid2(a.lu ? 2 * L.count : L.count);
   switch (L.kind) {
     case K_SMALL:
-      k_small_front<T><<<grid, 256, (size_t)L.param * L.param * sizeof(T), st>>>(d, L.item_off);
+      if (a.lu) k_small_front<T, true><<<grid, 256, small_smem<T>(L.param, true), st>>>(d, L.item_off);
+      else k_small_front<T, false><<<grid, 256, small_smem<T>(L.param, false), st>>>(d, L.item_off);
       break;
     case K_SMALL_Q: {
       // one resident wave: SMs x the blocks per SM that the front size allows
-      const size_t smem = (size_t)L.param * L.param * sizeof(T);
+      const size_t smem = small_smem<T>(L.param, a.lu != 0);
       int dev = 0, sms = 0, per = 0;
       cudaError_t e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T>, kQueueThreads, smem);
+        e = a.lu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T, true>,
+                                                                 kQueueThreads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T, false>,
+                                                                 kQueueThreads, smem);
       if (e != cudaSuccess) return e;
       const int blocks = std::max(1, std::min(L.count, sms * std::max(per, 1)));
-      k_small_queue<T><<<blocks, kQueueThreads, smem, st>>>(d, L.item_off, L.count);
+      if (a.lu) k_small_queue<T, true><<<blocks, kQueueThreads, smem, st>>>(d, L.item_off, L.count);
+      else k_small_queue<T, false><<<blocks, kQueueThreads, smem, st>>>(d, L.item_off, L.count);
       break;
     }
     case K_ASSEMBLE:
-      k_assemble<T><<<grid, 256, 0, st>>>(d, L.item_off);
+      k_assemble<T><<<grid2, 256, 0, st>>>(d, L.item_off);
       break;
     case K_POTRF:
-      k_potrf<T><<<grid, 256, potrf_smem<T>(), st>>>(d, L.item_off);
+      if (a.lu) k_getrf<T><<<grid, 256, getrf_smem<T>(), st>>>(d, L.item_off);
+      else k_potrf<T><<<grid, 256, potrf_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_TRSM:
-      k_trsm<T><<<grid, 256, trsm_smem<T>(), st>>>(d, L.item_off);
+      k_trsm<T><<<grid2, 256, trsm_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_SYRK:
-      if (L.tile == 32) k_syrk<T, 32><<<grid, 256, syrk_smem<T, 32>(), st>>>(d, L.item_off);
-      else if (L.tile == 128) k_syrk<T, 128><<<grid, 256, syrk_smem<T, 128>(), st>>>(d, L.item_off);
-      else k_syrk<T, 64><<<grid, 256, syrk_smem<T, 64>(), st>>>(d, L.item_off);
+      if (L.tile == 32) k_syrk<T, 32><<<grid2, 256, syrk_smem<T, 32>(), st>>>(d, L.item_off);
+      else if (L.tile == 128) k_syrk<T, 128><<<grid2, 256, syrk_smem<T, 128>(), st>>>(d, L.item_off);
+      else k_syrk<T, 64><<<grid2, 256, syrk_smem<T, 64>(), st>>>(d, L.item_off);
       break;
     case K_SYRK_TC:
       return launch_syrk_tc(L, a, st);
@@ -1005,6 +1383,27 @@ cudaError_t launch_gather_values(int prec, const FactorArgs& a, int64_t n, cudaS
   else
     k_gather_values<double><<<(int)g, 256, 0, st>>>(a.sym.asrc_ptr, a.sym.asrc, a.vals,
                                                     static_cast<double*>(a.av), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_upper(int prec, const int64_t* src_ptr, const int64_t* src,
+                                const double* vals, void* avu, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  if (prec == MF_FP32)
+    k_gather_values<float><<<(int)g, 256, 0, st>>>(src_ptr, src, vals, static_cast<float*>(avu), n);
+  else
+    k_gather_values<double><<<(int)g, 256, 0, st>>>(src_ptr, src, vals, static_cast<double*>(avu), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_swap(int prec, const FactorArgs& a, cudaStream_t st) {
+  if (a.lu_swap_count <= 0 || a.piv == nullptr) return cudaSuccess;
+  if (prec == MF_FP32)
+    k_lu_swap<float><<<a.lu_swap_count, 256, 0, st>>>(make_fd<float>(a), a.lu_swap);
+  else
+    k_lu_swap<double><<<a.lu_swap_count, 256, 0, st>>>(make_fd<double>(a), a.lu_swap);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,24 @@ struct FactorArgs {
   int* qstate = nullptr;
   int32_t wait_polls = 0;  // polls before a queue wait gives up (0: default)
   void* D = nullptr;       // LDL^T: T[n] pivots by permuted column; nullptr for Cholesky
+  // LU with a symmetric pattern (lu != 0): U^T in the layout of L (Lu), the
+  // transposed update matrices (Uu), the inverses of the U^T diagonal blocks
+  // (dinvu, slots as dinv), the upper entries of C in their own assembly
+  // lists (uacol_ptr / uarow, values avu), and with pivoting (lu == 2) the
+  // row chosen for each pivot position inside its 64-row block (piv[n])
+  int32_t lu = 0;
+  void* Lu = nullptr;
+  void* Uu = nullptr;
+  void* dinvu = nullptr;
+  const int64_t* uacol_ptr = nullptr;
+  const int32_t* uarow = nullptr;
+  void* avu = nullptr;
+  uint8_t* piv = nullptr;
+  // pivoting: the rows of each later 64-row block of a large front are
+  // reordered in the front's earlier columns once the factorization is done
+  // (items (front, step), count lu_swap_count)
+  const Item* lu_swap = nullptr;
+  int32_t lu_swap_count = 0;
 };
 
 struct SolveArgs {
@@ -80,13 +98,22 @@ struct SolveArgs {
   int32_t nlevels;
   int32_t nblk;
   int32_t wait_polls = 0;  // polls before a flag wait gives up (0: the default bound)
+  // LU with pivoting, forward sweep: pivot position i of a 64-row block
+  // takes row (i & ~63) + piv[i] of that block; nullptr elsewhere
+  const uint8_t* piv = nullptr;
 };
 
 // prec: MF_FP64 or MF_FP32.  All launchers return cudaGetLastError().
 cudaError_t factor_kernels_init(int prec);
 cudaError_t launch_factor(int prec, const Launch& L, const FactorArgs& a, cudaStream_t st);
-// av[e] = sum of the CSR values of lower entry e (duplicates summed), cast to T
+// av[e] = sum of the CSR values of lower entry e (duplicates summed), cast to
+// T; for LU also avu from the upper entries' lists (src_ptr / src, nnz_upper)
 cudaError_t launch_gather_values(int prec, const FactorArgs& a, int64_t nnz_lower, cudaStream_t st);
+cudaError_t launch_gather_upper(int prec, const int64_t* src_ptr, const int64_t* src,
+                                const double* vals, void* avu, int64_t nnz_upper, cudaStream_t st);
+// LU with pivoting: reorder the later pivot blocks' rows in their fronts'
+// earlier columns (after the factorization; no-op without pivoting)
+cudaError_t launch_lu_swap(int prec, const FactorArgs& a, cudaStream_t st);
 // tcgen05 FP32 trailing update (factor_tc.cu)
 cudaError_t factor_tc_init();
 cudaError_t launch_syrk_tc(const Launch& L, const FactorArgs& a, cudaStream_t st);

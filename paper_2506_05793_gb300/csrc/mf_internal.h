@@ -189,6 +189,18 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
 int tile_bucket(int nf);
 int check_schedules(const mf_symbolic& S, std::string& err);
 void ensure_fundamental_rows(const mf_symbolic& S);
+// LU with a symmetric pattern: assembly lists of the strictly upper entries
+// of C = P A P^T (entry C(j, i), i > j, goes to row i of column j of the
+// front's U^T half), in the format of acol_ptr / arow / asrc_ptr / asrc.
+// MF_ERR_INVALID when an upper entry falls outside its front (the pattern
+// is not structurally symmetric).
+struct UpperAssembly {
+  std::vector<int64_t> col_ptr;  // n + 1
+  std::vector<int32_t> row;      // front-relative rows
+  std::vector<int64_t> src_ptr;  // entries + 1
+  std::vector<int64_t> src;      // CSR positions (duplicates summed)
+};
+int build_upper_assembly(const mf_symbolic& S, UpperAssembly& out, std::string& err);
 // error reporting (capi.cpp)
 int set_error(int code, const std::string& msg);
 // solve with caller-provided work memory (capi.cpp)

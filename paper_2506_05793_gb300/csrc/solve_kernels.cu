@@ -46,6 +46,9 @@ struct SD {
   const T* PT;           // variant 4: P transposed per front or nullptr
   const Item* v4grp;     // variant 4: forward row groups (front, front row)
   unsigned long long* status;  // the solve's timeout record (one word)
+  // LU with pivoting (forward sweep): pivot position i of a front takes the
+  // values of row (i & ~63) + piv[first + i]; nullptr elsewhere
+  const uint8_t* piv;
   int64_t n;
   int nrhs;
   int wait_polls;  // polls before a flag wait gives up
@@ -71,6 +74,7 @@ SD<T> make_sd(const SolveArgs& a) {
   d.PT = static_cast<const T*>(a.PT);
   d.v4grp = a.sym.v4grp;
   d.status = a.status;
+  d.piv = a.piv;
   d.n = a.n;
   d.nrhs = a.nrhs;
   d.wait_polls = a.wait_polls > 0 ? a.wait_polls : kSpinLimit;
@@ -250,7 +254,8 @@ __global__ void __launch_bounds__(256, 2)
   // gather w for the rows of this block
   for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
     const int rw = idx / nrhs, r = idx % nrhs;
-    const int i = r0 + rw;
+    const int i0 = r0 + rw;
+    const int i = (d.piv && i0 < k) ? r0 + (int)d.piv[f.first + i0] : i0;
     T w = i < k ? d.Y[(int64_t)r * d.n + f.first + i] : T(0);
     const int64_t gi = f.woff + i;
     for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e)
@@ -996,7 +1001,11 @@ __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int6
   const int i0 = lane, i1 = lane + 32;
   const T rd0 = i0 < k ? T(1) / Lp[(int64_t)i0 * nf + i0] : T(0);
   const T rd1 = i1 < k ? T(1) / Lp[(int64_t)i1 * nf + i1] : T(0);
-  const int64_t g0 = f.woff + i0, g1 = f.woff + i1;
+  // LU with pivoting: pivot position i takes the values of row piv (one
+  // 64-row block here)
+  const int s0 = (d.piv && i0 < k) ? (int)d.piv[f.first + i0] : i0;
+  const int s1 = (d.piv && i1 < k) ? (int)d.piv[f.first + i1] : i1;
+  const int64_t g0 = f.woff + s0, g1 = f.woff + s1;
   const int64_t e00 = i0 < nf ? d.ginv_ptr[g0] : 0, e01 = i0 < nf ? d.ginv_ptr[g0 + 1] : 0;
   const int64_t e10 = i1 < nf ? d.ginv_ptr[g1] : 0, e11 = i1 < nf ? d.ginv_ptr[g1 + 1] : 0;
   for (int rb = 0; rb < nrhs; rb += RB) {
@@ -1006,8 +1015,8 @@ __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int6
       const int r = rb + q;
       T v0 = T(0), v1 = T(0);
       if (r < nrhs) {
-        if (i0 < k) v0 = d.Y[(int64_t)r * d.n + f.first + i0];
-        if (i1 < k) v1 = d.Y[(int64_t)r * d.n + f.first + i1];
+        if (i0 < k) v0 = d.Y[(int64_t)r * d.n + f.first + s0];
+        if (i1 < k) v1 = d.Y[(int64_t)r * d.n + f.first + s1];
         for (int64_t e = e00; e < e01; ++e) v0 += d.W[d.ginv_src[e] * nrhs + r];
         for (int64_t e = e10; e < e11; ++e) v1 += d.W[d.ginv_src[e] * nrhs + r];
       }
@@ -1137,11 +1146,13 @@ __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, i
     __syncwarp();
     {
       int64_t e0[H], e1[H];
+      int si[H];  // LU with pivoting: the row whose values pivot position i takes
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int i = lane + 32 * h;
-        e0[h] = i < nf ? d.ginv_ptr[f.woff + i] : 0;
-        e1[h] = i < nf ? d.ginv_ptr[f.woff + i + 1] : 0;
+        si[h] = (d.piv && i < k) ? (i & ~(kNB - 1)) + (int)d.piv[f.first + i] : i;
+        e0[h] = i < nf ? d.ginv_ptr[f.woff + si[h]] : 0;
+        e1[h] = i < nf ? d.ginv_ptr[f.woff + si[h] + 1] : 0;
       }
 #pragma unroll
       for (int h = 0; h < H; ++h) {
@@ -1151,7 +1162,7 @@ __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, i
           const int r = rb + q;
           T v = T(0);
           if (r < nrhs) {
-            if (i < k) v = d.Y[(int64_t)r * d.n + f.first + i];
+            if (i < k) v = d.Y[(int64_t)r * d.n + f.first + si[h]];
             for (int64_t e = e0[h]; e < e1[h]; ++e) v += d.W[d.ginv_src[e] * nrhs + r];
           }
           ws[i * RB + q] = v;

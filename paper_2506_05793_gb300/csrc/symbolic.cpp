@@ -23,6 +23,7 @@
 #include <set>
 #include <numeric>
 #include <unordered_map>
+#include <utility>
 
 #include "mf_internal.h"
 
@@ -1654,6 +1655,45 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
 // Row lists of the fundamental supernodes (the exported pattern of L), built
 // on first request: column j's lower entries of C plus the children's update
 // rows, merged per supernode in increasing order.
+int build_upper_assembly(const mf_symbolic& S, UpperAssembly& out, std::string& err) {
+  const int64_t n = S.n;
+  out.col_ptr.assign(n + 1, 0);
+  out.row.clear();
+  out.src_ptr.assign(1, 0);
+  out.src.clear();
+  std::vector<int32_t> posn(n, -1);
+  std::vector<std::pair<int32_t, int64_t>> ent;  // (front row, CSR position)
+  for (const SnInfo& I : S.sn) {
+    const int32_t* frows = S.rowidx.data() + I.rows_off;
+    for (int32_t r = 0; r < I.k + I.m; ++r) posn[frows[r]] = r;
+    for (int32_t j = I.first; j < I.first + I.k; ++j) {
+      ent.clear();
+      const int32_t ro = S.perm[j];
+      for (int64_t p = S.rowptr[ro]; p < S.rowptr[ro + 1]; ++p) {
+        const int32_t i = S.iperm[S.colind[p]];
+        if (i <= j) continue;
+        const int32_t r = posn[i];
+        if (r < 0 || frows[r] != i) {
+          err = "an upper entry of A falls outside its front: the pattern is not structurally symmetric";
+          return MF_ERR_INVALID;
+        }
+        ent.emplace_back(r, p);
+      }
+      std::sort(ent.begin(), ent.end());
+      for (size_t e = 0; e < ent.size(); ++e) {
+        if (e == 0 || ent[e].first != ent[e - 1].first) {
+          out.row.push_back(ent[e].first);
+          out.src_ptr.push_back(out.src_ptr.back());
+        }
+        out.src.push_back(ent[e].second);
+        out.src_ptr.back()++;
+      }
+      out.col_ptr[j + 1] = (int64_t)out.row.size();
+    }
+  }
+  return MF_OK;
+}
+
 void ensure_fundamental_rows(const mf_symbolic& Sc) {
   std::lock_guard<std::mutex> lk(Sc.dev_mu);
   if (!Sc.fs_rows_off.empty() || Sc.nsuper == 0) return;
