@@ -447,11 +447,11 @@ __global__ void __launch_bounds__(kQueueThreads) k_small_queue(FD<T> d, int64_t 
 // landing in [a, b) are the range [lo, hi) of the child's (increasing)
 // relative map; the one landing on column c is found by bisection.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool LU>
 __global__ void __launch_bounds__(256) k_assemble(FD<T> d0, int64_t item_off) {
-  bool upper;
-  const int bid = lu_block(d0, upper);
-  const FD<T> d = upper ? upper_view(d0) : d0;
+  bool upper = false;
+  const int bid = LU ? lu_block(d0, upper) : (int)blockIdx.x;
+  const FD<T> d = (LU && upper) ? upper_view(d0) : d0;
   const Item it = d.items[item_off + bid];
   const SnInfo f = d.sn[it.s];
   const int k = f.k, nf = k + f.m, c0 = it.a, c1 = it.b;
@@ -867,12 +867,12 @@ constexpr size_t trsm_smem() {
   return (size_t)2 * kNB * (kNB + 1) * sizeof(T);
 }
 
-template <typename T>
+template <typename T, bool LU>
 __global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  bool upper;
-  const int bid = lu_block(d0, upper);
-  const FD<T> d = upper ? upper_view(d0) : d0;
+  bool upper = false;
+  const int bid = LU ? lu_block(d0, upper) : (int)blockIdx.x;
+  const FD<T> d = (LU && upper) ? upper_view(d0) : d0;
   T(*As)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // As[c][r] = A(r0 + r, c0 + c)
   T(*Li)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(
       smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));          // Li[c][j] = Linv(j, c)
@@ -884,10 +884,10 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
   const int r0 = it.a;
   const int rows = min(kTrsmRows, nf - r0);
   const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
-  const T* Dv = d.dinv_t + (int64_t)it.b * kNB * kNB;
+  const T* Dv = (LU ? d.dinv_t : d.dinv) + (int64_t)it.b * kNB * kNB;
   // LU with pivoting, upper half: the columns of F12^T come in the pivot
   // order of the diagonal block (Pi F12), the rows' own permutation
-  const uint8_t* pv = (upper && d.piv) ? d.piv + f.first + c0 : nullptr;
+  const uint8_t* pv = (LU && upper && d.piv) ? d.piv + f.first + c0 : nullptr;
   {
     // all global loads of this thread in flight before the first shared store
     constexpr int PER = kNB * kNB / 256;
@@ -896,7 +896,7 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int idx = tid + u * 256, c = idx / kNB, rr = idx % kNB;
-      const int cs = (pv && c < b) ? (int)pv[c] : c;
+      const int cs = (LU && pv && c < b) ? (int)pv[c] : c;
       va[u] = (c < b && rr < rows) ? P[(int64_t)cs * nf + rr] : T(0);
       vl[u] = Dv[idx];
     }
@@ -973,15 +973,12 @@ constexpr size_t syrk_smem() {
   return (size_t)2 * kNB * TILE * sizeof(T);
 }
 
-template <typename T, int TILE>
-__global__ void __launch_bounds__(256) k_syrk(FD<T> d0, int64_t item_off) {
+template <typename T, int TILE, bool LU>
+__device__ __forceinline__ void syrk_tile(const FD<T>& d, int bid, int64_t item_off) {
   constexpr int R = TILE / 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T(*As)[TILE] = reinterpret_cast<T(*)[TILE]>(smem_raw);
   T(*Bs)[TILE] = reinterpret_cast<T(*)[TILE]>(smem_raw + (size_t)kNB * TILE * sizeof(T));
-  bool upper;
-  const int bid = lu_block(d0, upper);
-  const FD<T> d = upper ? upper_view(d0) : d0;
   const Item it = d.items[item_off + bid];
   const SnInfo f = d.sn[it.s];
   const int nf = f.k + f.m;
@@ -991,11 +988,11 @@ __global__ void __launch_bounds__(256) k_syrk(FD<T> d0, int64_t item_off) {
   const int rI = p0 + it.a * TILE, rJ = p0 + it.b * TILE;
   const int tid = threadIdx.x;
   const T* P = d.L + f.Loff + (int64_t)c0 * nf;
-  const T* Pb = d.Lb + f.Loff + (int64_t)c0 * nf;  // LU: the other half
+  const T* Pb = LU ? d.Lb + f.Loff + (int64_t)c0 * nf : P;  // LU: the other half
   for (int idx = tid; idx < b * TILE; idx += blockDim.x) {
     const int q = idx / TILE, r = idx % TILE;
     const T* col = P + (int64_t)q * nf;
-    const T* colb = Pb + (int64_t)q * nf;
+    const T* colb = LU ? Pb + (int64_t)q * nf : col;
     As[q][r] = (rI + r < nf) ? col[rI + r] : T(0);
     // LDL^T: C -= P_I D P_J^T, the pivots folded into the B operand
     const T w = d.D ? d.D[f.first + c0 + q] : T(1);
@@ -1046,6 +1043,18 @@ __global__ void __launch_bounds__(256) k_syrk(FD<T> d0, int64_t item_off) {
 #pragma unroll
       for (int i = 0; i < R; ++i)
         if (p[i][jj]) *p[i][jj] = cur[i][jj] - acc[i][j0 + jj];
+  }
+}
+
+template <typename T, int TILE, bool LU>
+__global__ void __launch_bounds__(256) k_syrk(FD<T> d, int64_t item_off) {
+  if (LU) {
+    bool upper = false;
+    const int bid = lu_block(d, upper);
+    if (upper) syrk_tile<T, TILE, LU>(upper_view(d), bid, item_off);
+    else syrk_tile<T, TILE, LU>(d, bid, item_off);
+  } else {
+    syrk_tile<T, TILE, LU>(d, (int)blockIdx.x, item_off);
   }
 }
 
@@ -1263,6 +1272,27 @@ size_t small_smem(int param, bool lu) {
   return (size_t)param * (param + (lu ? 1 : 0)) * sizeof(T);
 }
 
+template <typename T, bool LU>
+cudaError_t syrk_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_syrk<T, 32, LU>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)syrk_smem<T, 32>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_syrk<T, 128, LU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)syrk_smem<T, 128>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_syrk<T, 64, LU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)syrk_smem<T, 64>());
+}
+
+// Trailing-update launch with the schedule's tile; LU runs both halves.
+template <typename T, bool LU>
+void launch_syrk(const Launch& L, const FD<T>& d, dim3 grid, cudaStream_t st) {
+  if (L.tile == 32) k_syrk<T, 32, LU><<<grid, 256, syrk_smem<T, 32>(), st>>>(d, L.item_off);
+  else if (L.tile == 128) k_syrk<T, 128, LU><<<grid, 256, syrk_smem<T, 128>(), st>>>(d, L.item_off);
+  else k_syrk<T, 64, LU><<<grid, 256, syrk_smem<T, 64>(), st>>>(d, L.item_off);
+}
+
 template <typename T>
 cudaError_t init_t() {
   const int small_max = (int)small_smem<T>(kSmallMax, false);
@@ -1282,7 +1312,10 @@ cudaError_t init_t() {
   e = cudaFuncSetAttribute(k_getrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)getrf_smem<T>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_trsm<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)trsm_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_trsm<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem<T>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_potrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1294,14 +1327,9 @@ cudaError_t init_t() {
   e = cudaFuncSetAttribute(k_pinv_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)pinv_small_smem<T>());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_syrk<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)syrk_smem<T, 32>());
+  e = syrk_attributes<T, false>();
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_syrk<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)syrk_smem<T, 128>());
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_syrk<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)syrk_smem<T, 64>());
+  return syrk_attributes<T, true>();
 }
 
 template <typename T>
@@ -1333,19 +1361,20 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
       break;
     }
     case K_ASSEMBLE:
-      k_assemble<T><<<grid2, 256, 0, st>>>(d, L.item_off);
+      if (a.lu) k_assemble<T, true><<<grid2, 256, 0, st>>>(d, L.item_off);
+      else k_assemble<T, false><<<grid, 256, 0, st>>>(d, L.item_off);
       break;
     case K_POTRF:
       if (a.lu) k_getrf<T><<<grid, 256, getrf_smem<T>(), st>>>(d, L.item_off);
       else k_potrf<T><<<grid, 256, potrf_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_TRSM:
-      k_trsm<T><<<grid2, 256, trsm_smem<T>(), st>>>(d, L.item_off);
+      if (a.lu) k_trsm<T, true><<<grid2, 256, trsm_smem<T>(), st>>>(d, L.item_off);
+      else k_trsm<T, false><<<grid, 256, trsm_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_SYRK:
-      if (L.tile == 32) k_syrk<T, 32><<<grid2, 256, syrk_smem<T, 32>(), st>>>(d, L.item_off);
-      else if (L.tile == 128) k_syrk<T, 128><<<grid2, 256, syrk_smem<T, 128>(), st>>>(d, L.item_off);
-      else k_syrk<T, 64><<<grid2, 256, syrk_smem<T, 64>(), st>>>(d, L.item_off);
+      if (a.lu) launch_syrk<T, true>(L, d, grid2, st);
+      else launch_syrk<T, false>(L, d, grid, st);
       break;
     case K_SYRK_TC:
       return launch_syrk_tc(L, a, st);
