@@ -21,6 +21,8 @@ the three phases of the paper's Ax=b statement in Sec. 3):
 * ``lu_dense`` / ``solve_lu`` / ``pivot_windows`` -- LU of a general matrix
   with a symmetric pattern (Crout: L lower, U unit upper), pivots looked for
   only within diagonal blocks, and its solve (dense, C).
+* ``ldlt_dense`` / ``solve_ldlt_piv`` -- LDL^T with symmetric (1x1) pivoting
+  within diagonal blocks and its solve (dense, C).
 * ``expand_node_blocks`` -- the block-expanded pattern a condensed-graph
   analysis stands for (plain Python sets).
 * ``brute_symbolic`` -- dense boolean elimination on tiny inputs (pure Python),
@@ -99,6 +101,8 @@ def load_library(path):
                                         ctypes.c_double]
     lib.orc_lu_dense.argtypes = [I, P, P, P, P, P]
     lib.orc_lu_dense.restype = ctypes.c_int64
+    lib.orc_ldlt_dense.argtypes = [I, P, P, P, P, P]
+    lib.orc_ldlt_dense.restype = ctypes.c_int64
     return lib
 
 
@@ -540,6 +544,58 @@ def solve_lu(F, b, perm):
         x[perm] = w
     else:
         x[:] = w
+    return x[:, 0] if one else x
+
+
+class LDLT:
+    """Pi C Pi^T = L D L^T of C = A(perm, perm): ``L`` dense unit lower
+    triangular, ``D`` the pivots, ``rho[i]`` the row (and column) of C in
+    position i, ``bad_col`` -1 or the first zero pivot."""
+
+    def __init__(self, L, D, rho, bad_col):
+        self.L, self.D, self.rho, self.bad_col = L, D, rho, bad_col
+        self.n = len(rho)
+
+
+def ldlt_dense(rowptr, colind, values, perm, wend=None):
+    """Dense LDL^T of the symmetric C = A(perm, perm) with symmetric
+    pivoting: column j takes the largest-magnitude diagonal entry among
+    positions j .. wend[j]-1 of the current Schur complement (default: no
+    pivoting)."""
+    lib = _load()
+    n = len(rowptr) - 1
+    A = np.zeros((n, n))
+    np.add.at(A, (np.repeat(np.arange(n), np.diff(rowptr)), colind), values)
+    C = A if perm is None else A[np.ix_(perm, perm)]
+    M = np.asfortranarray(C)
+    if wend is None:
+        wend = np.arange(1, n + 1, dtype=np.int64)
+    wend = np.ascontiguousarray(wend, dtype=np.int64)
+    rho = np.empty(n, dtype=np.int64)
+    D = np.zeros(n)
+    nzr = np.empty(n, dtype=np.int64)
+    bad = lib.orc_ldlt_dense(n, _p(M), _p(wend), _p(rho), _p(D), _p(nzr))
+    L = np.tril(M, -1) + np.eye(n)
+    return LDLT(L, D, rho, int(bad))
+
+
+def solve_ldlt_piv(F, b, perm):
+    """x = P^T Pi^T L^{-T} D^{-1} L^{-1} Pi P b (triangular solves by scipy)."""
+    from scipy.linalg import solve_triangular
+    b = np.asarray(b, dtype=np.float64)
+    one = b.ndim == 1
+    B = b.reshape(F.n, -1)
+    y = B[perm] if perm is not None else B.copy()
+    z = solve_triangular(F.L, y[F.rho], lower=True, unit_diagonal=True)
+    z = z / F.D[:, None]
+    w = solve_triangular(F.L.T, z, lower=False, unit_diagonal=True)
+    u = np.empty_like(w)
+    u[F.rho] = w
+    x = np.empty_like(u)
+    if perm is not None:
+        x[perm] = u
+    else:
+        x[:] = u
     return x[:, 0] if one else x
 
 

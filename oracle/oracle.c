@@ -583,3 +583,59 @@ int64_t orc_lu_dense(int64_t n, double* M, const int64_t* wend, int64_t* rho, in
   }
   return -1;
 }
+
+/*
+ * LDL^T of a symmetric C = P A P^T with symmetric pivoting within diagonal
+ * blocks (paper Sec. 5: Tacho's LDL^T of symmetric indefinite matrices,
+ * with pivots looked for only inside each diagonal block): Pi C Pi^T =
+ * L D L^T, L unit lower triangular, D diagonal (1x1 pivots).  Dense, on the
+ * full symmetric n x n column-major M = C.  Column j takes as pivot the
+ * diagonal entry of largest magnitude among positions j .. wend[j]-1 of the
+ * current Schur complement (wend[j] = j + 1: no pivoting), ties going to the
+ * row that started in the smallest position; rows j and p and columns j and
+ * p are swapped; then d_j = M(j, j) and, for i, c > j,
+ * M(i, c) -= M(i, j) M(c, j) / d_j, which keeps M symmetric; finally
+ * L(i, j) = M(i, j) / d_j.  On return the strict lower part of M holds L,
+ * D the pivots and rho[i] the row of C now in position i.  Returns -1, or
+ * the first column whose pivot is zero.  nzr: workspace of n.
+ */
+int64_t orc_ldlt_dense(int64_t n, double* M, const int64_t* wend, int64_t* rho, double* D,
+                       int64_t* nzr) {
+  for (int64_t i = 0; i < n; ++i) rho[i] = i;
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = j;
+    for (int64_t i = j + 1; i < wend[j]; ++i) {
+      double a = fabs(M[i * n + i]), b = fabs(M[p * n + p]);
+      if (a > b || (a == b && rho[i] < rho[p])) p = i;
+    }
+    if (p != j) {
+      for (int64_t c = 0; c < n; ++c) { /* rows j and p */
+        double tmp = M[c * n + j];
+        M[c * n + j] = M[c * n + p];
+        M[c * n + p] = tmp;
+      }
+      for (int64_t r = 0; r < n; ++r) { /* columns j and p */
+        double tmp = M[j * n + r];
+        M[j * n + r] = M[p * n + r];
+        M[p * n + r] = tmp;
+      }
+      int64_t tr = rho[j];
+      rho[j] = rho[p];
+      rho[p] = tr;
+    }
+    double* colj = M + j * n;
+    double dj = colj[j];
+    if (dj == 0.0) return j;
+    D[j] = dj;
+    int64_t nr = 0;
+    for (int64_t i = j + 1; i < n; ++i)
+      if (colj[i] != 0.0) nzr[nr++] = i;
+    for (int64_t t = 0; t < nr; ++t) {
+      double* colc = M + nzr[t] * n;
+      double w = colj[nzr[t]] / dj;
+      for (int64_t q = 0; q < nr; ++q) colc[nzr[q]] -= colj[nzr[q]] * w;
+    }
+    for (int64_t q = 0; q < nr; ++q) colj[nzr[q]] /= dj;
+  }
+  return -1;
+}

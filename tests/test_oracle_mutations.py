@@ -221,15 +221,19 @@ def test_ldlt_pins_pass_on_the_oracle(orc):
 
 
 LU_MUTATIONS = [
-    ("lu: pivot of smallest magnitude", "if (a > b || (a == b && rho[i] < rho[p])) p = i;",
-     "if (a < b || (a == b && rho[i] < rho[p])) p = i;"),
-    ("lu: ties to the largest original row", "if (a > b || (a == b && rho[i] < rho[p])) p = i;",
-     "if (a > b || (a == b && rho[i] > rho[p])) p = i;"),
-    ("lu: window ignored", "for (int64_t i = j + 1; i < wend[j]; ++i) {",
-     "for (int64_t i = j + 1; i < n; ++i) {"),
+    ("lu: pivot of smallest magnitude",
+     "fabs(colj[i]), b = fabs(colj[p]);\n      if (a > b || (a == b && rho[i] < rho[p])) p = i;",
+     "fabs(colj[i]), b = fabs(colj[p]);\n      if (a < b || (a == b && rho[i] < rho[p])) p = i;"),
+    ("lu: ties to the largest original row",
+     "fabs(colj[i]), b = fabs(colj[p]);\n      if (a > b || (a == b && rho[i] < rho[p])) p = i;",
+     "fabs(colj[i]), b = fabs(colj[p]);\n      if (a > b || (a == b && rho[i] > rho[p])) p = i;"),
+    ("lu: window ignored",
+     "for (int64_t i = j + 1; i < wend[j]; ++i) {\n      double a = fabs(colj[i])",
+     "for (int64_t i = j + 1; i < n; ++i) {\n      double a = fabs(colj[i])"),
     ("lu: factored columns not swapped", "for (int64_t c = 0; c < n; ++c) {\n        double tmp",
      "for (int64_t c = j; c < n; ++c) {\n        double tmp"),
-    ("lu: row order not recorded", "rho[p] = tr;", "rho[p] = rho[j];"),
+    ("lu: row order not recorded", "rho[p] = tr;\n    }\n    double piv = colj[j];",
+     "rho[p] = rho[j];\n    }\n    double piv = colj[j];"),
     ("lu: U row multiplied by the pivot", "*ujc /= piv;", "*ujc *= piv;"),
     ("lu: update sign flipped", "colc[nzr[q]] -= colj[nzr[q]] * u;",
      "colc[nzr[q]] += colj[nzr[q]] * u;"),
@@ -276,3 +280,62 @@ def test_lu_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
 
 def test_lu_pins_pass_on_the_oracle(orc):
     assert lu_pins(orc) == set()
+
+
+LDLT_PIV_MUTATIONS = [
+    ("ldlt piv: smallest diagonal as pivot",
+     "double a = fabs(M[i * n + i]), b = fabs(M[p * n + p]);\n      if (a > b ||",
+     "double a = fabs(M[i * n + i]), b = fabs(M[p * n + p]);\n      if (a < b ||"),
+    ("ldlt piv: window ignored",
+     "for (int64_t i = j + 1; i < wend[j]; ++i) {\n      double a = fabs(M[i * n + i])",
+     "for (int64_t i = j + 1; i < n; ++i) {\n      double a = fabs(M[i * n + i])"),
+    ("ldlt piv: columns not swapped", "for (int64_t r = 0; r < n; ++r) { /* columns j and p */",
+     "for (int64_t r = 0; r < 0; ++r) { /* columns j and p */"),
+    ("ldlt piv: rows not swapped", "for (int64_t c = 0; c < n; ++c) { /* rows j and p */",
+     "for (int64_t c = 0; c < 0; ++c) { /* rows j and p */"),
+    ("ldlt piv: row order not recorded", "rho[p] = tr;\n    }\n    double* colj",
+     "rho[p] = rho[j];\n    }\n    double* colj"),
+    ("ldlt piv: update sign flipped", "colc[nzr[q]] -= colj[nzr[q]] * w;",
+     "colc[nzr[q]] += colj[nzr[q]] * w;"),
+    ("ldlt piv: column not divided by the pivot", "for (int64_t q = 0; q < nr; ++q) colj[nzr[q]] /= dj;",
+     "for (int64_t q = 0; q < nr; ++q) colj[nzr[q]] *= 1.0;"),
+    ("ldlt piv: update without the pivot", "double w = colj[nzr[t]] / dj;",
+     "double w = colj[nzr[t]];"),
+]
+
+
+def ldlt_piv_pins(orc):
+    import test_oracle_ldlt_piv as t
+    bad = set()
+    for name, fn in [("no pivoting", lambda: t.test_no_pivoting_equals_left_looking_ldlt(orc, (3, 3, 2), 0)),
+                     ("pstrf", lambda: t.test_one_window_spd_is_pivoted_cholesky(orc, 1)),
+                     ("invariants", lambda: t.test_windowed_symmetric_pivoting_invariants(orc, 2, 1)),
+                     ("zero block", lambda: t.test_zero_block_needs_pivoting(orc)),
+                     ("hand", lambda: t.test_hand_worked_with_tie(orc))]:
+        try:
+            fn()
+        except Exception:
+            bad.add(name)
+    return bad
+
+
+@pytest.mark.parametrize("name,old,new", LDLT_PIV_MUTATIONS, ids=[m[0] for m in LDLT_PIV_MUTATIONS])
+def test_ldlt_piv_pins_catch_planted_mistake(orc, tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not unique: " + name
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib_path = tmp_path / "liboracle_mut.so"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", str(lib_path), str(mutated),
+                           "-lm"])
+    saved = orc._load()
+    orc._lib = orc.load_library(str(lib_path))
+    try:
+        failed = ldlt_piv_pins(orc)
+    finally:
+        orc._lib = saved
+    assert failed, "no pin caught: " + name
+
+
+def test_ldlt_piv_pins_pass_on_the_oracle(orc):
+    assert ldlt_piv_pins(orc) == set()
