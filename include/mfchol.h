@@ -297,9 +297,27 @@ int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec,
 int mf_factor_create_ldlt(mf_handle* h, const mf_symbolic* s, int32_t prec,
                           mf_factor** f);
 
+/* As mf_factor_create_ldlt, with symmetric pivoting within the diagonal
+ * blocks (paper Sec. 5: Tacho's LDL^T of symmetric indefinite matrices
+ * looks for pivots only inside each diagonal block): Pi P A P^T Pi^T =
+ * L D L^T with 1x1 pivots.  The diagonal blocks are those of
+ * mf_factor_create_lu (64-column pieces of each internal front's pivot
+ * columns); column j takes the diagonal entry of largest magnitude among the
+ * block's remaining positions of the current Schur complement, ties going
+ * to the row that started first.  Pi only reorders rows and columns inside
+ * those blocks.  A block whose remaining diagonal is all zero (for instance
+ * [[0, 1], [1, 0]]) is reported as a zero pivot (MF_ERR_NOT_SPD): 2x2
+ * pivots are not used.  D is in pivot order (mf_factor_export_D), the row
+ * order comes from mf_factor_export_pivots, and the rows of L are labelled
+ * as for a pivoted LU.  Solves, refinement and fallback as for LDL^T, with
+ * SpTRSV variants 1 and 2 only (an analysis for variant 3 or 4 is refused
+ * with MF_ERR_INVALID). */
+int mf_factor_create_ldlt_piv(mf_handle* h, const mf_symbolic* s, int32_t prec,
+                              mf_factor** f);
+
 /* LDL^T factor: the pivots D (n doubles, permuted order: D[j] belongs to
- * column j of P A P^T).  Synchronous.  MF_ERR_INVALID for a Cholesky
- * factor. */
+ * column j of P A P^T, or pivot position j with symmetric pivoting).
+ * Synchronous.  MF_ERR_INVALID for a Cholesky factor. */
 int mf_factor_export_D(const mf_factor* f, double* D);
 
 /* As mf_factor_create, for the LU factorization of a general matrix with a
@@ -337,15 +355,16 @@ int mf_factor_create_lu(mf_handle* h, const mf_symbolic* s, int32_t prec, int32_
  * Synchronous.  MF_ERR_INVALID for a factor that is not LU. */
 int mf_factor_export_U(const mf_factor* f, double* Ux);
 
-/* LU factor: rho[i] = the row of P A P^T (permuted numbering) that ended in
- * pivot position i; the identity without pivoting.  Synchronous.  With
+/* LU or pivoted LDL^T factor: rho[i] = the row (LDL^T: row and column) of
+ * P A P^T (permuted numbering) that ended in pivot position i; the
+ * identity without pivoting.  Synchronous.  With
  * pivoting, the rows of L are labelled as follows by mf_factor_export_L and
  * mf_factor_export_columns: in a column j of internal front F, a pattern row
  * i that is a pivot column of F holds L(i, j) (pivot order), and a row i of
  * a later front keeps the label it had before that front pivoted, so it
  * holds L(rho^{-1}(i), j).  U is not affected (its rows are pivot
  * positions, its columns are never permuted).  MF_ERR_INVALID for a factor
- * that is not LU. */
+ * that is neither. */
 int mf_factor_export_pivots(const mf_factor* f, int32_t* rho);
 
 /* Numerical factorization P A P^T = L L^T with the given values (CSR order

@@ -106,6 +106,7 @@ _SIGS = {
     "mf_factor_create_ldlt": [_P, _P, _I32, _P],
     "mf_factor_export_D": [_P, _P],
     "mf_factor_create_lu": [_P, _P, _I32, _I32, _P],
+    "mf_factor_create_ldlt_piv": [_P, _P, _I32, _P],
     "mf_factor_export_U": [_P, _P],
     "mf_factor_export_pivots": [_P, _P],
     "mf_symbolic_fronts": [_P, _P],
@@ -624,6 +625,13 @@ def mf_factor_create_lu(h, s, prec=MF_FP64, pivot=0):
     """LU factor object, pivot 0 (none) or 1 (within diagonal blocks); see the C header."""
     f = ctypes.c_void_p()
     _check(lib().mf_factor_create_lu(h, s, prec, pivot, ctypes.byref(f)))
+    return f
+
+
+def mf_factor_create_ldlt_piv(h, s, prec=MF_FP64):
+    """LDL^T factor with symmetric pivoting within the diagonal blocks (see the C header)."""
+    f = ctypes.c_void_p()
+    _check(lib().mf_factor_create_ldlt_piv(h, s, prec, ctypes.byref(f)))
     return f
 
 

@@ -184,6 +184,8 @@ struct mf_factor {
   uint8_t* piv = nullptr;     // pivoting: row taken by each pivot position of its 64-row block
   mf::Item* lu_swap = nullptr;  // pivoting: (front, step) of the later pivot blocks of large fronts
   int32_t lu_swap_count = 0;
+  bool sympiv = false;        // LDL^T with symmetric pivoting within the diagonal blocks
+  int32_t* ipos = nullptr;    // symmetric pivoting: position each row of P A P^T ended in
   double* small = nullptr;  // per-RHS scalars for refinement
   // graph of the numeric factorization
   cudaStream_t cap_stream = nullptr;
@@ -236,6 +238,7 @@ struct mf_factor {
     cudaFree(uasrc);
     cudaFree(piv);
     cudaFree(lu_swap);
+    cudaFree(ipos);
     delete fb64;
   }
 };
@@ -485,20 +488,46 @@ int mf_symbolic_supernode_tree(const mf_symbolic* s, int32_t* sparent, int32_t* 
 // Factor
 // ---------------------------------------------------------------------------
 static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt, int lu,
-                         mf_factor** f);
+                         bool sympiv, mf_factor** f);
 
 int mf_factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
-  return factor_create(h, s, prec, false, 0, f);
+  return factor_create(h, s, prec, false, 0, false, f);
 }
 
 int mf_factor_create_ldlt(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
-  return factor_create(h, s, prec, true, 0, f);
+  return factor_create(h, s, prec, true, 0, false, f);
+}
+
+int mf_factor_create_ldlt_piv(mf_handle* h, const mf_symbolic* s, int32_t prec, mf_factor** f) {
+  return factor_create(h, s, prec, true, 0, true, f);
 }
 
 int mf_factor_create_lu(mf_handle* h, const mf_symbolic* s, int32_t prec, int32_t pivot,
                         mf_factor** f) {
   if (pivot != 0 && pivot != 1) return set_error(MF_ERR_INVALID, "pivot must be 0 or 1");
-  return factor_create(h, s, prec, false, pivot ? 2 : 1, f);
+  return factor_create(h, s, prec, false, pivot ? 2 : 1, false, f);
+}
+
+// Pivoting within the diagonal blocks (LU rows, LDL^T rows and columns): the
+// per-column pivot bytes, the reordering items of the later pivot blocks of
+// large fronts and, for symmetric pivoting, each row's final position.
+static int pivot_extras(mf_factor* F) {
+  const mf_symbolic* s = F->S;
+  MF_CK(cudaMalloc(&F->piv, std::max<int64_t>(s->n, 1)));
+  MF_CK(cudaMemset(F->piv, 0, std::max<int64_t>(s->n, 1)));
+  if (F->sympiv) MF_CK(cudaMalloc(&F->ipos, std::max<int64_t>(s->n, 1) * sizeof(int32_t)));
+  std::vector<mf::Item> sw;
+  for (const mf::Launch& L : s->fsched)
+    if (L.kind == mf::K_POTRF)
+      for (int32_t i = 0; i < L.count; ++i) {
+        const mf::Item& it = s->items[L.item_off + i];
+        if (it.t >= 1) sw.push_back({it.s, it.t, 0, 0});
+      }
+  F->lu_swap_count = (int32_t)sw.size();
+  MF_CK(cudaMalloc(&F->lu_swap, std::max<size_t>(sw.size() * sizeof(mf::Item), 8)));
+  if (!sw.empty())
+    MF_CK(cudaMemcpy(F->lu_swap, sw.data(), sw.size() * sizeof(mf::Item), cudaMemcpyHostToDevice));
+  return MF_OK;
 }
 
 // Device copies of the LU extras: U^T half, second update pool (in U),
@@ -529,30 +558,17 @@ static int lu_extras(mf_factor* F) {
   MF_CK(up((void**)&F->uarow, ua.row.data(), ua.row.size() * sizeof(int32_t)));
   MF_CK(up((void**)&F->uasrc_ptr, ua.src_ptr.data(), ua.src_ptr.size() * sizeof(int64_t)));
   MF_CK(up((void**)&F->uasrc, ua.src.data(), ua.src.size() * sizeof(int64_t)));
-  if (F->lu == 2) {
-    MF_CK(cudaMalloc(&F->piv, std::max<int64_t>(s->n, 1)));
-    // pivot positions not factored by a pivoting kernel keep their own row
-    MF_CK(cudaMemset(F->piv, 0, std::max<int64_t>(s->n, 1)));
-    std::vector<mf::Item> sw;
-    for (const mf::Launch& L : s->fsched)
-      if (L.kind == mf::K_POTRF)
-        for (int32_t i = 0; i < L.count; ++i) {
-          const mf::Item& it = s->items[L.item_off + i];
-          if (it.t >= 1) sw.push_back({it.s, it.t, 0, 0});
-        }
-    F->lu_swap_count = (int32_t)sw.size();
-    MF_CK(up((void**)&F->lu_swap, sw.data(), sw.size() * sizeof(mf::Item)));
-  }
   return MF_OK;
 }
 
 static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool ldlt, int lu,
-                         mf_factor** f) {
+                         bool sympiv, mf_factor** f) {
   if (!h || !s || !f) return set_error(MF_ERR_INVALID, "NULL argument");
   if (prec != MF_FP64 && prec != MF_FP32) return set_error(MF_ERR_INVALID, "bad precision");
   *f = nullptr;
-  if (lu && (s->pinv || s->v4))
-    return set_error(MF_ERR_INVALID, "LU factors solve with SpTRSV variants 1 and 2 only");
+  if ((lu || sympiv) && (s->pinv || s->v4))
+    return set_error(MF_ERR_INVALID,
+                     "LU and pivoted LDL^T factors solve with SpTRSV variants 1 and 2 only");
   // LU keeps a second half of the same size as L and the update matrices
   const int64_t need = factor_bytes(s, prec) +
                        (lu ? (s->Lsize + s->Usize + s->nnz_lower) * (int64_t)elem_size(prec) : 0);
@@ -589,14 +605,19 @@ static int factor_create(mf_handle* h, const mf_symbolic* s, int32_t prec, bool 
   F->ldlt = ldlt;
   if (ldlt) MF_CK(cudaMalloc(&F->Dp, std::max<int64_t>(s->n, 1) * es));
   F->lu = lu;
+  F->sympiv = sympiv;
   if (lu) {
     const int rc = lu_extras(F.get());
+    if (rc != MF_OK) return rc;
+  }
+  if (lu == 2 || sympiv) {
+    const int rc = pivot_extras(F.get());
     if (rc != MF_OK) return rc;
   }
   // LDL^T: the pivots enter the trailing update as a scaling of one operand,
   // and LU updates with two different operands, which the FMA tiles do; the
   // tensor-core path stays with Cholesky
-  if (prec == MF_FP32 && h->opt.tc && !ldlt && !lu) {
+  if (prec == MF_FP32 && h->opt.tc && !ldlt && !lu && !sympiv) {
     F->tc = true;
     MF_CK(mf::factor_tc_init());
     const int64_t srows = std::max<int64_t>(s->split_rows, 1);
@@ -643,10 +664,11 @@ static mf::FactorArgs factor_args(const mf_factor* F) {
     a.uacol_ptr = F->uacol_ptr;
     a.uarow = F->uarow;
     a.avu = F->avu;
-    a.piv = F->piv;
-    a.lu_swap = F->lu_swap;
-    a.lu_swap_count = F->lu_swap_count;
   }
+  a.piv = F->piv;
+  a.lu_swap = F->lu_swap;
+  a.lu_swap_count = F->lu_swap_count;
+  a.ipos = F->ipos;
   return a;
 }
 
@@ -705,7 +727,7 @@ static int enqueue_factor(mf_factor* F, cudaStream_t st, bool profile, bool capt
     }
   }
   if (pending) MF_CK(cudaStreamWaitEvent(F->crit, F->ev_side, 0));
-  if (F->lu == 2) MF_CK(mf::launch_lu_swap(F->prec, a, F->crit));
+  if (F->piv) MF_CK(mf::launch_lu_swap(F->prec, a, F->crit));
   MF_CK(cudaEventRecord(F->ev_out, F->crit));
   MF_CK(cudaStreamWaitEvent(st, F->ev_out, 0));
   return MF_OK;
@@ -864,7 +886,7 @@ int mf_factor_export_U(const mf_factor* f, double* Ux) {
 
 int mf_factor_export_pivots(const mf_factor* f, int32_t* rho) {
   if (!f || (!rho && f->S->n)) return set_error(MF_ERR_INVALID, "NULL argument");
-  if (!f->lu) return set_error(MF_ERR_INVALID, "not an LU factor");
+  if (!f->lu && !f->sympiv) return set_error(MF_ERR_INVALID, "not an LU or pivoted LDL^T factor");
   const int64_t n = f->S->n;
   std::vector<uint8_t> p(f->piv ? n : 0);
   MF_CK(cudaDeviceSynchronize());
@@ -1215,6 +1237,7 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.P = f->P;
   a.PT = f->PT;
   a.piv = f->piv;
+  a.ipos = f->ipos;
   for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   // LDL^T: z = D^{-1} z between the sweeps (the forward results sit in Y,
   // or for SpTRSV variant 4 in the first n x nrhs values of W)
@@ -1226,7 +1249,8 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
     a.piv = nullptr;
   }
   for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
-  MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, X, ldx, S->n, cn, scale, accumulate, st));
+  MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, f->ipos, X, ldx, S->n, cn, scale,
+                            accumulate, st));
   return MF_OK;
 }
 
@@ -1498,7 +1522,7 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
       return set_error(MF_ERR_STAGNATION, "iterative refinement stagnated");
     }
     if (!f->fb64) {
-      rc = factor_create(f->h, S, MF_FP64, f->ldlt, f->lu, &f->fb64);
+      rc = factor_create(f->h, S, MF_FP64, f->ldlt, f->lu, f->sympiv, &f->fb64);
       if (rc != MF_OK) return rc;
     }
     f->fb64->wait_polls = f->wait_polls;

@@ -70,6 +70,7 @@ struct FD {
   const int32_t* uarow;
   const T* avu;
   uint8_t* piv;  // pivoting: row taken by each pivot position of a 64-row block
+  int32_t* ipos;  // LDL^T with symmetric pivoting: position each row ended in
 };
 
 template <typename T>
@@ -107,6 +108,7 @@ FD<T> make_fd(const FactorArgs& a) {
   d.uarow = a.uarow;
   d.avu = static_cast<const T*>(a.avu);
   d.piv = a.piv;
+  d.ipos = a.ipos;
   // LU, lower half: L21 = F21 U11^{-1} (the inverse of the U^T block), the
   // update's second operand is U^T
   d.Lb = a.lu ? d.Lu : d.L;
@@ -266,6 +268,93 @@ __device__ __forceinline__ int block_pivot(const T* col, const int* orig, int j,
   return __shfl_sync(0xffffffffu, bi, 0);
 }
 
+// The same search over the diagonal entries F(i, i) of a column-major block
+// (leading dimension ld): symmetric pivoting of LDL^T.
+template <typename T>
+__device__ __forceinline__ int block_pivot_diag(const T* F, int ld, const int* orig, int j, int we) {
+  const int lane = threadIdx.x & 31;
+  T bv = T(-1);
+  int bo = 1 << 30, bi = j;
+  for (int i = j + lane; i < we; i += 32) {
+    const T a = fabs(F[i * ld + i]);
+    const int o = orig[i];
+    if (a > bv || (a == bv && o < bo)) {
+      bv = a;
+      bo = o;
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const T ov = __shfl_down_sync(0xffffffffu, bv, off);
+    const int oo = __shfl_down_sync(0xffffffffu, bo, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ov > bv || (ov == bv && oo < bo)) {
+      bv = ov;
+      bo = oo;
+      bi = oi;
+    }
+  }
+  return __shfl_sync(0xffffffffu, bi, 0);
+}
+
+// Unblocked right-looking LDL^T with symmetric pivoting (paper Sec. 5: LDL^T
+// of symmetric indefinite matrices, pivots looked for only inside each
+// diagonal block) of the first k columns of an n x n symmetric block held in
+// full, column-major, in shared memory (ld): column j takes the diagonal
+// entry of largest magnitude among positions j .. end of its 64-row block
+// (ties to the row that started first, orig), swaps rows and columns j and p,
+// then F(i, c) -= F(i, j) F(c, j) / d_j for i, c > j (both triangles, so F
+// stays symmetric) and L(i, j) = F(i, j) / d_j, L_jj = 1.  Records the
+// pivots in D[col0 + j] and the first zero pivot.
+template <typename T>
+__device__ __forceinline__ void smem_ldlt_piv(T* F, int ld, int n, int k, int col0,
+                                              unsigned long long* status, T* D, int* orig) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ int s_p;
+  for (int j = 0; j < k; ++j) {
+    if (warp == 0) {
+      const int p = block_pivot_diag(F, ld, orig, j, min(k, (j & ~(kNB - 1)) + kNB));
+      if (lane == 0) s_p = p;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j) {
+      for (int c = tid; c < n; c += blockDim.x) {  // rows j and p
+        const T t = F[c * ld + j];
+        F[c * ld + j] = F[c * ld + p];
+        F[c * ld + p] = t;
+      }
+      __syncthreads();
+      for (int r = tid; r < n; r += blockDim.x) {  // columns j and p
+        const T t = F[j * ld + r];
+        F[j * ld + r] = F[p * ld + r];
+        F[p * ld + r] = t;
+      }
+      if (tid == 0) {
+        const int t = orig[j];
+        orig[j] = orig[p];
+        orig[p] = t;
+      }
+    }
+    __syncthreads();
+    const T dj = F[j * ld + j];
+    if (tid == 0 && !(dj != T(0))) atomicMin(status, (unsigned long long)(col0 + j));
+    const T rinv = T(1) / dj;
+    for (int c = j + 1 + warp; c < n; c += nw) {
+      const T w = F[j * ld + c] * rinv;
+      for (int i = j + 1 + lane; i < n; i += 32) F[c * ld + i] -= F[j * ld + i] * w;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) F[j * ld + i] *= rinv;
+    if (tid == 0) {
+      F[j * ld + j] = T(1);
+      D[col0 + j] = dj;
+    }
+    __syncthreads();
+  }
+}
+
 // Unblocked right-looking LU in Crout form (L lower, U unit upper) of the
 // first k columns of an n x n block held column-major in shared memory
 // (ld): for j < k, U(j, c) = F(j, c) / F(j, j) for c > j, then
@@ -373,16 +462,69 @@ __device__ __forceinline__ void small_front_lu(const FD<T>& d, int s, T* F) {
     }
 }
 
-template <typename T, bool LU>
+// Small front of an LDL^T factor with symmetric pivoting: the front as for
+// Cholesky (lower entries, children's update matrices), mirrored into the
+// upper triangle, leading dimension nf + 1; then the pivoted partial LDL^T,
+// L, the pivots and the update matrix written out, and each row's final
+// position recorded.
+template <typename T>
+__device__ __forceinline__ void small_front_ldlt_piv(const FD<T>& d, int s, T* F) {
+  __shared__ int orig[kSmallMax];
+  const SnInfo f = d.sn[s];
+  const int k = f.k, m = f.m, nf = k + m, ld = nf + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < nf * ld; i += blockDim.x) F[i] = T(0);
+  for (int i = tid; i < k; i += blockDim.x) orig[i] = i;
+  __syncthreads();
+  for (int c = warp; c < k; c += nw) {
+    const int g = f.first + c;
+    for (int64_t e = d.acol_ptr[g] + lane; e < d.acol_ptr[g + 1]; e += 32)
+      F[c * ld + d.arow[e]] = d.av[e];
+  }
+  __syncthreads();
+  for (int ci = 0; ci < f.nchild; ++ci) {
+    const SnInfo ch = d.sn[d.children[f.child_begin + ci]];
+    const int mc = ch.m;
+    const int32_t* map = d.relmap + ch.map_off;
+    const T* Uc = d.U + ch.Uoff;
+    for (int jc = warp; jc < mc; jc += nw) {
+      const int dc = map[jc];
+      const T* u = Uc + (int64_t)jc * mc;
+      for (int ic = jc + lane; ic < mc; ic += 32) F[dc * ld + map[ic]] += __ldcg(u + ic);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nf * nf; idx += blockDim.x) {
+    const int c = idx / nf, r = idx % nf;
+    if (r < c) F[c * ld + r] = F[r * ld + c];
+  }
+  __syncthreads();
+  smem_ldlt_piv(F, ld, nf, k, f.first, d.status, d.D, orig);
+  T* Lp = d.L + f.Loff;
+  for (int c = warp; c < k; c += nw)
+    for (int r = lane; r < nf; r += 32) Lp[(int64_t)c * nf + r] = r >= c ? F[c * ld + r] : T(0);
+  for (int i = tid; i < k; i += blockDim.x) {
+    d.piv[f.first + i] = (uint8_t)(orig[i] - (i & ~(kNB - 1)));
+    d.ipos[f.first + orig[i]] = f.first + i;
+  }
+  T* Up = d.U + f.Uoff;
+  for (int c = warp; c < m; c += nw)
+    for (int r = lane; r < m; r += 32) Up[(int64_t)c * m + r] = F[(k + c) * ld + k + r];
+}
+
+// Small-front kinds: 0 Cholesky / LDL^T without pivoting, 1 LU, 2 LDL^T
+// with symmetric pivoting (1 and 2 pad the shared leading dimension).
+template <typename T, int MODE>
 __device__ __forceinline__ void small_front(const FD<T>& d, int s, T* F) {
-  if (LU) small_front_lu(d, s, F);
+  if (MODE == 1) small_front_lu(d, s, F);
+  else if (MODE == 2) small_front_ldlt_piv(d, s, F);
   else small_front_body(d, s, F);
 }
 
-template <typename T, bool LU>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_small_front(FD<T> d, int64_t item_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  small_front<T, LU>(d, d.items[item_off + blockIdx.x].s, reinterpret_cast<T*>(smem_raw));
+  small_front<T, MODE>(d, d.items[item_off + blockIdx.x].s, reinterpret_cast<T*>(smem_raw));
 }
 
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
@@ -402,7 +544,7 @@ __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
 // bounded (wait_polls polls 128 ns apart): when it runs out the CTA records
 // MF_ERR_TIMEOUT in status[1] and goes on, so the launch always ends.
 // ---------------------------------------------------------------------------
-template <typename T, bool LU>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kQueueThreads) k_small_queue(FD<T> d, int64_t item_off, int count) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_ticket;
@@ -429,7 +571,7 @@ __global__ void __launch_bounds__(kQueueThreads) k_small_queue(FD<T> d, int64_t 
       }
     }
     __syncthreads();
-    small_front<T, LU>(d, s, reinterpret_cast<T*>(smem_raw));
+    small_front<T, MODE>(d, s, reinterpret_cast<T*>(smem_raw));
     // every thread's stores are ordered before thread 0's release by the
     // CTA barrier; the GPU-scope release store is cumulative
     __syncthreads();
@@ -830,6 +972,121 @@ __global__ void __launch_bounds__(256) k_getrf(FD<T> d, int64_t item_off) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// LDL^T with symmetric pivoting (paper Sec. 5), large fronts, panel step t:
+// the b x b diagonal block (lower part of L's half, mirrored, padded with
+// the identity), one CTA per front: Pi F Pi^T = L D L^T with the pivots
+// chosen inside the block (largest remaining diagonal, ties to the row that
+// started first); L (unit diagonal), D, the inverse of L (dinv slot), the
+// block's permutation (piv) and each row's final position (ipos) are
+// written.  The panel solve reads F21 in the block's pivot order, and the
+// rows' earlier columns are reordered after the factorization (k_lu_swap).
+// ---------------------------------------------------------------------------
+template <typename T>
+constexpr size_t sytrf_smem() {
+  return (size_t)2 * kNB * (kNB + 1) * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sytrf(FD<T> d, int64_t item_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ld = kNB + 1;
+  T* A = reinterpret_cast<T*>(smem_raw);  // A[c * ld + r] = F(r, c), both triangles
+  T* Y = A + kNB * ld;                    // L^{-1}, column-major
+  __shared__ int orig[kNB];
+  __shared__ T piv_of[kNB];
+  __shared__ int s_p;
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int64_t nf = (int64_t)f.k + f.m;
+  const int c0 = it.t * kNB;
+  const int b = min(kNB, f.k - c0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* FL = d.L + f.Loff + (int64_t)c0 * nf + c0;
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int c = idx / kNB, r = idx % kNB;
+    A[c * ld + r] = (r < b && c < b) ? (r >= c ? FL[(int64_t)c * nf + r] : T(0))
+                                     : (r == c ? T(1) : T(0));
+  }
+  if (tid < kNB) orig[tid] = tid;
+  __syncthreads();
+  for (int idx = tid; idx < b * b; idx += blockDim.x) {
+    const int c = idx / b, r = idx % b;
+    if (r < c) A[c * ld + r] = A[r * ld + c];
+  }
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (warp == 0) {
+      const int p = block_pivot_diag(A, ld, orig, j, b);
+      if (lane == 0) s_p = p;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j) {
+      if (tid < kNB) {  // rows j and p
+        const T t = A[tid * ld + j];
+        A[tid * ld + j] = A[tid * ld + p];
+        A[tid * ld + p] = t;
+      }
+      __syncthreads();
+      if (tid < kNB) {  // columns j and p
+        const T t = A[j * ld + tid];
+        A[j * ld + tid] = A[p * ld + tid];
+        A[p * ld + tid] = t;
+      }
+      if (tid == 0) {
+        const int t = orig[j];
+        orig[j] = orig[p];
+        orig[p] = t;
+      }
+      __syncthreads();
+    }
+    const T dj = A[j * ld + j];
+    if (tid == 0 && !(dj != T(0))) atomicMin(d.status, (unsigned long long)(f.first + c0 + j));
+    const T rinv = T(1) / dj;
+    const int nt = b - j - 1;
+    for (int e = tid; e < nt * nt; e += blockDim.x) {
+      const int c = j + 1 + e / nt, r = j + 1 + e % nt;
+      A[c * ld + r] -= A[j * ld + r] * (A[j * ld + c] * rinv);
+    }
+    __syncthreads();
+    if (tid > j && tid < b) A[j * ld + tid] *= rinv;
+    if (tid == 0) {
+      piv_of[j] = dj;
+      A[j * ld + j] = T(1);
+    }
+    __syncthreads();
+  }
+  // inverse of the unit lower L: thread c < 64 solves L y = e_c
+  if (tid < kNB) {
+    const int c = tid;
+    for (int i = 0; i < kNB; ++i) {
+      T y = T(0);
+      if (i >= c) {
+        T acc = i == c ? T(1) : T(0);
+        for (int q = c; q < i; ++q) acc -= A[q * ld + i] * Y[c * ld + q];
+        y = acc;
+      }
+      Y[c * ld + i] = y;
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < b * b; idx += blockDim.x) {
+    const int cc = idx / b, rr = idx % b;
+    if (rr >= cc) FL[(int64_t)cc * nf + rr] = A[cc * ld + rr];
+  }
+  if (tid < b) {
+    d.D[f.first + c0 + tid] = piv_of[tid];
+    d.piv[f.first + c0 + tid] = (uint8_t)orig[tid];
+    d.ipos[f.first + c0 + orig[tid]] = f.first + c0 + tid;
+  }
+  T* Dv = d.dinv + (int64_t)it.b * kNB * kNB;
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    const int cc = idx / kNB, rr = idx % kNB;
+    Dv[idx] = Y[cc * ld + rr];
+  }
+}
+
 // LU with pivoting, after the factorization: in a large front, the rows of
 // each later 64-row pivot block t take the order of their pivots in the
 // front's earlier columns too (k_getrf reordered them only from the block
@@ -887,7 +1144,8 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
   const T* Dv = (LU ? d.dinv_t : d.dinv) + (int64_t)it.b * kNB * kNB;
   // LU with pivoting, upper half: the columns of F12^T come in the pivot
   // order of the diagonal block (Pi F12), the rows' own permutation
-  const uint8_t* pv = (LU && upper && d.piv) ? d.piv + f.first + c0 : nullptr;
+  // (LDL^T with symmetric pivoting: F21's columns, likewise)
+  const uint8_t* pv = (LU ? (upper && d.piv) : (d.D && d.piv)) ? d.piv + f.first + c0 : nullptr;
   {
     // all global loads of this thread in flight before the first shared store
     constexpr int PER = kNB * kNB / 256;
@@ -896,7 +1154,7 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int idx = tid + u * 256, c = idx / kNB, rr = idx % kNB;
-      const int cs = (LU && pv && c < b) ? (int)pv[c] : c;
+      const int cs = (pv && c < b) ? (int)pv[c] : c;
       va[u] = (c < b && rr < rows) ? P[(int64_t)cs * nf + rr] : T(0);
       vl[u] = Dv[idx];
     }
@@ -1272,6 +1530,36 @@ size_t small_smem(int param, bool lu) {
   return (size_t)param * (param + (lu ? 1 : 0)) * sizeof(T);
 }
 
+template <typename T, int MODE>
+cudaError_t small_attributes(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_small_front<T, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_small_queue<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              bytes);
+}
+
+// Small-front launches of one kind (one CTA per front, or the queue).
+template <typename T, int MODE>
+cudaError_t launch_small(const Launch& L, const FD<T>& d, cudaStream_t st) {
+  const size_t smem = small_smem<T>(L.param, MODE != 0);
+  if (L.kind == K_SMALL) {
+    k_small_front<T, MODE><<<L.count, 256, smem, st>>>(d, L.item_off);
+    return cudaGetLastError();
+  }
+  // the queue: one resident wave, SMs x the blocks per SM the front size allows
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T, MODE>, kQueueThreads,
+                                                      smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = std::max(1, std::min(L.count, sms * std::max(per, 1)));
+  k_small_queue<T, MODE><<<blocks, kQueueThreads, smem, st>>>(d, L.item_off, L.count);
+  return cudaGetLastError();
+}
+
 template <typename T, bool LU>
 cudaError_t syrk_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_syrk<T, 32, LU>,
@@ -1296,21 +1584,18 @@ void launch_syrk(const Launch& L, const FD<T>& d, dim3 grid, cudaStream_t st) {
 template <typename T>
 cudaError_t init_t() {
   const int small_max = (int)small_smem<T>(kSmallMax, false);
-  const int small_max_lu = (int)small_smem<T>(kSmallMax, true);
-  cudaError_t e = cudaFuncSetAttribute(k_small_front<T, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, small_max);
+  const int small_max_pad = (int)small_smem<T>(kSmallMax, true);
+  cudaError_t e = small_attributes<T, 0>(small_max);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_small_front<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           small_max_lu);
+  e = small_attributes<T, 1>(small_max_pad);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_small_queue<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           small_max);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_small_queue<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           small_max_lu);
+  e = small_attributes<T, 2>(small_max_pad);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_getrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)getrf_smem<T>());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sytrf<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sytrf_smem<T>());
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_trsm<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)trsm_smem<T>());
@@ -1340,32 +1625,17 @@ cudaError_t launch_t(const Launch& L, const FactorArgs& a, cudaStream_t st) {
   const dim3 grid2(a.lu ? 2 * L.count : L.count);
   switch (L.kind) {
     case K_SMALL:
-      if (a.lu) k_small_front<T, true><<<grid, 256, small_smem<T>(L.param, true), st>>>(d, L.item_off);
-      else k_small_front<T, false><<<grid, 256, small_smem<T>(L.param, false), st>>>(d, L.item_off);
-      break;
-    case K_SMALL_Q: {
-      // one resident wave: SMs x the blocks per SM that the front size allows
-      const size_t smem = small_smem<T>(L.param, a.lu != 0);
-      int dev = 0, sms = 0, per = 0;
-      cudaError_t e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess)
-        e = a.lu ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T, true>,
-                                                                 kQueueThreads, smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_small_queue<T, false>,
-                                                                 kQueueThreads, smem);
-      if (e != cudaSuccess) return e;
-      const int blocks = std::max(1, std::min(L.count, sms * std::max(per, 1)));
-      if (a.lu) k_small_queue<T, true><<<blocks, kQueueThreads, smem, st>>>(d, L.item_off, L.count);
-      else k_small_queue<T, false><<<blocks, kQueueThreads, smem, st>>>(d, L.item_off, L.count);
-      break;
-    }
+    case K_SMALL_Q:
+      if (a.lu) return launch_small<T, 1>(L, d, st);
+      if (a.D && a.piv) return launch_small<T, 2>(L, d, st);
+      return launch_small<T, 0>(L, d, st);
     case K_ASSEMBLE:
       if (a.lu) k_assemble<T, true><<<grid2, 256, 0, st>>>(d, L.item_off);
       else k_assemble<T, false><<<grid, 256, 0, st>>>(d, L.item_off);
       break;
     case K_POTRF:
       if (a.lu) k_getrf<T><<<grid, 256, getrf_smem<T>(), st>>>(d, L.item_off);
+      else if (a.D && a.piv) k_sytrf<T><<<grid, 256, sytrf_smem<T>(), st>>>(d, L.item_off);
       else k_potrf<T><<<grid, 256, potrf_smem<T>(), st>>>(d, L.item_off);
       break;
     case K_TRSM:

@@ -76,6 +76,9 @@ struct FactorArgs {
   // (items (front, step), count lu_swap_count)
   const Item* lu_swap = nullptr;
   int32_t lu_swap_count = 0;
+  // LDL^T with symmetric pivoting (D and piv set, lu == 0): ipos[r] = the
+  // pivot position that row r of P A P^T ended in (int32[n])
+  int32_t* ipos = nullptr;
 };
 
 struct SolveArgs {
@@ -101,6 +104,9 @@ struct SolveArgs {
   // LU with pivoting, forward sweep: pivot position i of a 64-row block
   // takes row (i & ~63) + piv[i] of that block; nullptr elsewhere
   const uint8_t* piv = nullptr;
+  // LDL^T with symmetric pivoting (backward sweep and output): the solution
+  // of row r of P A P^T sits at position ipos[r]; nullptr elsewhere
+  const int32_t* ipos = nullptr;
 };
 
 // prec: MF_FP64 or MF_FP32.  All launchers return cudaGetLastError().
@@ -138,8 +144,9 @@ cudaError_t launch_perm_in(int prec, const double* B, int64_t ldb, const int32_t
                            void* Y, int64_t n, int32_t nrhs, const double* inv_scale,
                            cudaStream_t st);
 // X[perm[i], r] (=|+=) scale_r * Y[i, r]; accumulate != 0 adds.
-cudaError_t launch_perm_out(int prec, const void* Y, const int32_t* perm, double* X,
-                            int64_t ldx, int64_t n, int32_t nrhs, const double* scale,
+// X(perm[i], r) = Y(i, r) (ipos: Y(ipos[i], r), LDL^T with symmetric pivoting)
+cudaError_t launch_perm_out(int prec, const void* Y, const int32_t* perm, const int32_t* ipos,
+                            double* X, int64_t ldx, int64_t n, int32_t nrhs, const double* scale,
                             int32_t accumulate, cudaStream_t st);
 
 // FP64 residual R = B - A X (A in original order), with per-RHS maxima of

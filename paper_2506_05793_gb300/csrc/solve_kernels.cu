@@ -49,6 +49,10 @@ struct SD {
   // LU with pivoting (forward sweep): pivot position i of a front takes the
   // values of row (i & ~63) + piv[first + i]; nullptr elsewhere
   const uint8_t* piv;
+  // LDL^T with symmetric pivoting, backward sweep: the solution of row r
+  // sits at position ipos[r] (update rows are read through it); nullptr
+  // elsewhere
+  const int32_t* ipos;
   int64_t n;
   int nrhs;
   int wait_polls;  // polls before a flag wait gives up
@@ -75,6 +79,7 @@ SD<T> make_sd(const SolveArgs& a) {
   d.v4grp = a.sym.v4grp;
   d.status = a.status;
   d.piv = a.piv;
+  d.ipos = a.ipos;
   d.n = a.n;
   d.nrhs = a.nrhs;
   d.wait_polls = a.wait_polls > 0 ? a.wait_polls : kSpinLimit;
@@ -644,7 +649,7 @@ __global__ void __launch_bounds__(256) k_bw_gemv1(SD<T> d, int64_t item_off) {
 #pragma unroll
   for (int q = 0; q < 16; ++q) acc[q] = T(0);
   for (int i = warp * 32 + lane; i < m; i += 256) {
-    const T xi = d.Y[frow[i]];
+    const T xi = d.Y[d.ipos ? d.ipos[frow[i]] : frow[i]];
     T lv[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) lv[q] = q < nc ? Lb[(int64_t)q * nf + i] : T(0);
@@ -727,7 +732,9 @@ __global__ void __launch_bounds__(256) k_bw_gemm(SD<T> d, int64_t item_off) {
 #pragma unroll
     for (int u = 0; u < BwChunk<T, R>::PX; ++u) {
       const int idx = tid + u * 256, i = idx % kBwRows, r = idx / kBwRows;
-      nx.px[u] = (i < ch && r < nrhs) ? d.Y[(int64_t)r * d.n + frow[i0 + i]] : T(0);
+      nx.px[u] = (i < ch && r < nrhs)
+                     ? d.Y[(int64_t)r * d.n + (d.ipos ? d.ipos[frow[i0 + i]] : frow[i0 + i])]
+                     : T(0);
     }
   };
   T acc[RG];
@@ -1071,8 +1078,12 @@ __global__ void __launch_bounds__(256) k_bw_tiny(SD<T> d, int64_t item_off, int6
   const int i0 = lane, i1 = lane + 32;
   const T rd0 = i0 < k ? T(1) / Lp[(int64_t)i0 * nf + i0] : T(0);
   const T rd1 = i1 < k ? T(1) / Lp[(int64_t)i1 * nf + i1] : T(0);
-  const int32_t fr0 = (i0 >= k && i0 < nf) ? frow[i0] : 0;
-  const int32_t fr1 = (i1 >= k && i1 < nf) ? frow[i1] : 0;
+  int32_t fr0 = (i0 >= k && i0 < nf) ? frow[i0] : 0;
+  int32_t fr1 = (i1 >= k && i1 < nf) ? frow[i1] : 0;
+  if (d.ipos) {  // LDL^T with symmetric pivoting: where those rows' solution sits
+    fr0 = (i0 >= k && i0 < nf) ? d.ipos[fr0] : 0;
+    fr1 = (i1 >= k && i1 < nf) ? d.ipos[fr1] : 0;
+  }
   for (int rb = 0; rb < nrhs; rb += RB) {
     T x0[RB], x1[RB], y0[RB], y1[RB];
 #pragma unroll
@@ -1278,7 +1289,7 @@ __global__ void __launch_bounds__(256, 2) k_bw_warp(SD<T> d, int64_t item_off, i
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       const int i = lane + 32 * h;
-      if (i >= k && i < nf) xs[i] = yr[frow[i]];
+      if (i >= k && i < nf) xs[i] = yr[d.ipos ? d.ipos[frow[i]] : frow[i]];
     }
     __syncwarp();
     for (int b = (k - 1) >> 5; b >= 0; --b) {
@@ -1469,14 +1480,15 @@ __global__ void k_perm_in(const double* B, int64_t ldb, const int32_t* perm, T* 
 }
 
 template <typename T>
-__global__ void k_perm_out(const T* Y, const int32_t* perm, double* X, int64_t ldx, int64_t n,
-                           int nrhs, const double* scale, int accumulate) {
+__global__ void k_perm_out(const T* Y, const int32_t* perm, const int32_t* ipos, double* X,
+                           int64_t ldx, int64_t n, int nrhs, const double* scale, int accumulate) {
   const int64_t total = n * nrhs;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(idx / n);
     const int64_t i = idx % n;
-    const double v = (double)Y[idx] * (scale ? scale[r] : 1.0);
+    const int64_t src = ipos ? (int64_t)r * n + ipos[i] : idx;
+    const double v = (double)Y[src] * (scale ? scale[r] : 1.0);
     double* dst = X + r * ldx + perm[i];
     if (accumulate) *dst += v; else *dst = v;
   }
@@ -1719,16 +1731,16 @@ cudaError_t launch_perm_in(int prec, const double* B, int64_t ldb, const int32_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_perm_out(int prec, const void* Y, const int32_t* perm, double* X, int64_t ldx,
-                            int64_t n, int32_t nrhs, const double* scale, int32_t accumulate,
-                            cudaStream_t st) {
+cudaError_t launch_perm_out(int prec, const void* Y, const int32_t* perm, const int32_t* ipos,
+                            double* X, int64_t ldx, int64_t n, int32_t nrhs, const double* scale,
+                            int32_t accumulate, cudaStream_t st) {
   const int g = grid_for(n * nrhs);
   if (prec == MF_FP32)
-    k_perm_out<float><<<g, 256, 0, st>>>(static_cast<const float*>(Y), perm, X, ldx, n, nrhs, scale,
-                                         accumulate);
+    k_perm_out<float><<<g, 256, 0, st>>>(static_cast<const float*>(Y), perm, ipos, X, ldx, n, nrhs,
+                                         scale, accumulate);
   else
-    k_perm_out<double><<<g, 256, 0, st>>>(static_cast<const double*>(Y), perm, X, ldx, n, nrhs,
-                                          scale, accumulate);
+    k_perm_out<double><<<g, 256, 0, st>>>(static_cast<const double*>(Y), perm, ipos, X, ldx, n,
+                                          nrhs, scale, accumulate);
   return cudaGetLastError();
 }
 
