@@ -464,6 +464,44 @@ def run_serve(args):
     mf.mf_destroy(h)
 
 
+def ldlt_piv_case(mf, gen, torch, st, timed, N):
+    """Pivoted LDL^T (symmetric pivoting within the diagonal blocks) of the
+    saddle point [K B^T; B 0] on N^3 nodes, multiplier first in each node
+    (the unpivoted LDL^T stops at column 0), condensed analysis with 2 dofs
+    per node: factorization ms (median of 5), the 1-RHS solve, berr."""
+    import oracle
+    rp, ci, v = gen.kkt_3d(N, N, N, delta=0.0, seed=12)
+    perm = gen.nd_perm((N, N, N), dofs=2)
+    perm = np.ascontiguousarray(perm.reshape(-1, 2)[:, ::-1].ravel()).astype(np.int32)
+    n = len(rp) - 1
+    h = mf.mf_create(mf.mf_options_default())
+    s = mf.mf_symbolic_analyze_condensed(h, rp, ci, perm, block=2)
+    info = mf.mf_symbolic_get_info(s)
+    vd = torch.from_numpy(v).cuda()
+    b = torch.from_numpy(gen.rhs(n, 1, seed=3)).cuda()
+    out = {"workload": "saddle_kkt_%d^3_nodes_zero_block_multiplier_first" % N, "n": n,
+           "flops": info["flops"]}
+    f = mf.mf_factor_create_ldlt(h, s, mf.MF_FP64)
+    try:
+        mf.mf_factor_numeric(f, vd, stream=st)
+        out["unpivoted"] = "factored"
+    except mf.MFError as e:
+        out["unpivoted"] = "zero pivot at column %d" % e.column
+    mf.mf_factor_free(f)
+    f = mf.mf_factor_create_ldlt_piv(h, s, mf.MF_FP64)
+    out["ms"] = timed(lambda: mf.mf_factor_numeric(f, vd, stream=st, async_=1))
+    out["tflops"] = info["flops"] / (out["ms"] / 1e3) / 1e12
+    mf.mf_factor_numeric(f, vd, stream=st)
+    x = mf.mf_solve(f, b, stream=st)
+    out["solve_ms"] = timed(lambda: mf.mf_solve(f, b, stream=st), reps=20)
+    torch.cuda.synchronize()
+    out["berr"] = oracle.berr(rp, ci, v, x.cpu().numpy(), b.cpu().numpy())
+    mf.mf_factor_free(f)
+    mf.mf_symbolic_free(s)
+    mf.mf_destroy(h)
+    return out
+
+
 def run_lu(args):
     """LU with a symmetric pattern (paper Sec. 5) on the 7-point
     convection-diffusion operator of N^3 nodes (N = --size, default 64),
@@ -552,6 +590,7 @@ def run_lu(args):
            "lu_pivot_fp64_profiled": case(rp, ci, v, perm, "lu", pivot=1, profile=True)}
     lp, lc, lv = gen.laplacian_3d(N)
     res["cholesky_fp64_same_pattern"] = case(lp, lc, lv, perm, "chol")
+    res["ldlt_piv_saddle_fp64"] = ldlt_piv_case(mf, gen, torch, st, timed, max(8, (N * 3) // 4))
     # parity of the run at a size the dense oracle factors in seconds
     import oracle as orc
     shape = (15, 14, 16)
