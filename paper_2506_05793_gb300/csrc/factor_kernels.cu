@@ -676,6 +676,10 @@ __device__ __forceinline__ void load_diag_block(const FD<T>& d, const SnInfo& f,
 // ---------------------------------------------------------------------------
 constexpr int kPB = 16;  // block size inside the diagonal-block kernel
 
+// IEEE round-to-nearest reciprocal (the CUDA intrinsics)
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+
 template <typename T>
 constexpr size_t potrf_smem() {
   return ((size_t)2 * kNB * (kNB + 1) + (size_t)3 * kPB * (kPB + 1)) * sizeof(T);
@@ -708,40 +712,45 @@ __global__ void __launch_bounds__(256) k_potrf(FD<T> d, int64_t item_off) {
   }
   __syncthreads();
   for (int j0 = 0; j0 < bend; j0 += kPB) {
-    // (a) diagonal block: lane r < 16 owns row j0 + r
+    // (a) diagonal block: lane r < 16 owns row j0 + r (lanes 16..31 repeat
+    // rows 0..15 and write nothing).  The rows stay in registers and the
+    // elimination takes no square root: A(r, c) -= A(r, t) A(c, t) / d_t,
+    // one reciprocal per step, the values of column t by shuffles, so a
+    // step's dependent chain is shuffle -> reciprocal -> FMA; the scaling
+    // to L (by 1 / sqrt(d_t), or 1 / d_t for LDL^T) comes after all 16 steps.
     if (warp == 0) {
-      const int r = lane;
+      const int r = lane & (kPB - 1);
+      T a[kPB];
+#pragma unroll
+      for (int c = 0; c < kPB; ++c) a[c] = c <= r ? D[(j0 + c) * ld + j0 + r] : T(0);
+      T myd = T(1);  // this lane's pivot d_r
+#pragma unroll
       for (int t = 0; t < kPB; ++t) {
-        T* col = D + (j0 + t) * ld + j0;
-        const T piv = col[t];
-        if (r == 0 && j0 + t < b && !(ldlt ? piv != T(0) : piv > T(0)))
-          atomicMin(d.status, (unsigned long long)(f.first + c0 + j0 + t));
-        const T ljj = ldlt ? T(1) : dsqrt(piv);
-        const T rinv = T(1) / (ldlt ? piv : ljj);
-        __syncwarp();  // the pivot has been read
-        if (r == t) {
-          col[t] = ljj;
-          piv_of[j0 + t] = piv;
-        } else if (r > t && r < kPB) {
-          col[r] *= rinv;  // each lane scales its own entry
-        }
-        __syncwarp();
-        if (r > t && r < kPB) {
-          // all loads first (fixed trip count, so they issue together);
-          // LDL^T: A_rc -= L_rt d_t L_ct
-          const T lr = ldlt ? col[r] * piv : col[r];
-          T lc[kPB], dv[kPB];
+        const T dt = __shfl_sync(0xffffffffu, a[t], t);
+        if (t == r) myd = dt;
+        const T art = a[t] * recip_rn(dt);
+        // (fixed trip count: the loop unrolls and a[] stays in registers)
 #pragma unroll
-          for (int c = 0; c < kPB; ++c) {
-            lc[c] = col[c];
-            dv[c] = D[(j0 + c) * ld + j0 + r];
+        for (int c = 0; c < kPB; ++c) {
+          if (c > t) {
+            const T act = __shfl_sync(0xffffffffu, a[t], c);
+            if (c <= r && r > t) a[c] = fma(-art, act, a[c]);
           }
-#pragma unroll
-          for (int c = 0; c < kPB; ++c)
-            if (c > t && c <= r) D[(j0 + c) * ld + j0 + r] = fma(-lr, lc[c], dv[c]);
         }
-        __syncwarp();
       }
+      if (lane < kPB && j0 + r < b && !(ldlt ? myd != T(0) : myd > T(0)))
+        atomicMin(d.status, (unsigned long long)(f.first + c0 + j0 + r));
+      const T mys = ldlt ? recip_rn(myd) : recip_rn(dsqrt(myd));
+      if (lane < kPB) {
+#pragma unroll
+        for (int c = 0; c < kPB; ++c) {
+          const T sc = __shfl_sync(0x0000ffffu, mys, c);
+          if (c < r) D[(j0 + c) * ld + j0 + r] = a[c] * sc;
+        }
+        D[(j0 + r) * ld + j0 + r] = ldlt ? T(1) : myd * mys;
+        piv_of[j0 + r] = myd;
+      }
+      __syncwarp();
       // inverse of L_BB: lane c < 16 solves L_BB y = e_c, right-looking with
       // y in registers; the reciprocals of the diagonal are computed once
       const T rdl = T(1) / D[(j0 + (lane & (kPB - 1))) * ld + j0 + (lane & (kPB - 1))];
