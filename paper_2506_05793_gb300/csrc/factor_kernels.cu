@@ -1129,8 +1129,13 @@ __global__ void __launch_bounds__(256) k_lu_swap(FD<T> d, const Item* items) {
 // k_potrf.  Thread (r, g) computes X(r, j) for j = 16 g .. 16 g + 15.
 // ---------------------------------------------------------------------------
 template <typename T>
+__host__ __device__ constexpr int trsm_li_pitch() {
+  return kNB + 16 / (int)sizeof(T);  // rows of Li 16-byte aligned
+}
+
+template <typename T>
 constexpr size_t trsm_smem() {
-  return (size_t)2 * kNB * (kNB + 1) * sizeof(T);
+  return (size_t)kNB * (kNB + 1) * sizeof(T) + (size_t)kNB * trsm_li_pitch<T>() * sizeof(T);
 }
 
 template <typename T, bool LU>
@@ -1140,7 +1145,8 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
   const int bid = LU ? lu_block(d0, upper) : (int)blockIdx.x;
   const FD<T> d = (LU && upper) ? upper_view(d0) : d0;
   T(*As)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);  // As[c][r] = A(r0 + r, c0 + c)
-  T(*Li)[kNB + 1] = reinterpret_cast<T(*)[kNB + 1]>(
+  constexpr int LP = trsm_li_pitch<T>();
+  T(*Li)[LP] = reinterpret_cast<T(*)[LP]>(
       smem_raw + (size_t)kNB * (kNB + 1) * sizeof(T));          // Li[c][j] = Linv(j, c)
   const Item it = d.items[item_off + bid];
   const SnInfo f = d.sn[it.s];
@@ -1184,9 +1190,14 @@ __global__ void __launch_bounds__(256) k_trsm(FD<T> d0, int64_t item_off) {
   const int cend = 16 * g < b ? min(16 * g + 15, b - 1) : -1;
   for (int c = 0; c <= cend; ++c) {
     const T a = As[c][r];
-    const T* lrow = &Li[c][16 * g];
+    // the 16 inverse values as four (FP64: eight) 16-byte shared loads
+    T lv[16];
+    const uint4* lrow = reinterpret_cast<const uint4*>(&Li[c][16 * g]);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) x[q] = fma(a, lrow[q], x[q]);
+    for (int v = 0; v < 16 * (int)sizeof(T) / 16; ++v)
+      reinterpret_cast<uint4*>(lv)[v] = lrow[v];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) x[q] = fma(a, lv[q], x[q]);
   }
   if (d.D) {  // LDL^T: L21 = A L_tt^{-T} D_t^{-1}
 #pragma unroll
