@@ -611,14 +611,12 @@ __global__ void __launch_bounds__(256) k_assemble(FD<T> d0, int64_t item_off) {
     for (const Item* rg = d.arange + it.t; rg->s >= 0; ++rg) {
       const SnInfo ch = d.sn[rg->s];
       const int32_t* __restrict__ map = d.relmap + ch.map_off;
-      int lo = rg->t, hi = rg->a;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (map[mid] < c) lo = mid + 1;
-        else hi = mid;
-      }
-      if (lo >= rg->a || map[lo] != c) continue;
-      const int jc = lo, mc = ch.m;
+      // at most kAsmCols child columns land in the chunk: one lane each
+      // reads its map entry and a ballot finds the one landing on c
+      const int lo = rg->t, hi = rg->a;
+      const unsigned hit = __ballot_sync(0xffffffffu, lo + lane < hi && map[lo + lane] == c);
+      if (!hit) continue;
+      const int jc = lo + __ffs(hit) - 1, mc = ch.m;
       const T* __restrict__ u = d.U + ch.Uoff + (int64_t)jc * mc;
       int ic = jc + lane;
       for (; ic + 32 < mc; ic += 64) {

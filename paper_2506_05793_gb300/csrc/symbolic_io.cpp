@@ -324,6 +324,9 @@ bool indices_in_range(const mf_symbolic& s) {
   for (const mf::Item& r : s.arange) {
     if (r.s < -1 || r.s >= nfr) return false;
     if (r.s >= 0 && (r.t < 0 || r.t > r.a || r.a > s.sn[r.s].m)) return false;
+    // a chunk of kAsmCols parent columns receives at most that many columns
+    // of a child (the assembly kernel reads one per lane)
+    if (r.s >= 0 && r.a - r.t > mf::kAsmCols) return false;
   }
   // variant 4: forward groups name a front row; forward items a global row
   // and a range of groups; backward items a pivot column
@@ -353,7 +356,7 @@ bool indices_in_range(const mf_symbolic& s) {
           while (q < (int64_t)s.arange.size() && s.arange[q].s >= 0) ++q;
           if (q == (int64_t)s.arange.size()) return false;
           const mf::SnInfo& I = s.sn[it.s];
-          if (it.a < 0 || it.a > it.b || it.b > I.k + I.m) return false;
+          if (it.a < 0 || it.a > it.b || it.b > I.k + I.m || it.b - it.a > mf::kAsmCols) return false;
         }
   return true;
 }
