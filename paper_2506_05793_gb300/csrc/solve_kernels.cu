@@ -1516,11 +1516,21 @@ __global__ void k_residual(const int64_t* rowptr, const int32_t* colind, const d
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = wid; row < n; row += nwarps) {
+    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
     for (int r = 0; r < nrhs; ++r) {
       const double* x = X + r * ldx;
-      double s = 0.0;
-      for (int64_t p = rowptr[row] + lane; p < rowptr[row + 1]; p += 32) s = fma(vals[p], x[colind[p]], s);
-      s = warp_sum(s);
+      double s = 0.0, s2 = 0.0;
+      // two entries per lane and step, all their loads issued together
+      // (a step covers 64 entries: most rows in one)
+      for (int64_t p = p0 + lane; p < p1; p += 64) {
+        const bool two = p + 32 < p1;
+        const double v0 = vals[p], v1 = two ? vals[p + 32] : 0.0;
+        const int32_t j0 = colind[p], j1 = two ? colind[p + 32] : 0;
+        const double x0 = x[j0], x1 = two ? x[j1] : 0.0;
+        s = fma(v0, x0, s);
+        s2 = fma(v1, x1, s2);
+      }
+      s = warp_sum(s + s2);
       if (lane == 0) {
         const double res = B[r * ldb + row] - s;
         R[r * n + row] = res;
