@@ -589,6 +589,40 @@ __global__ void __launch_bounds__(256) k_fw_gemv(SD<T> d, int64_t item_off) {
 // r0 + 16 sub .. + 16 of the item's 64 update rows, thread (row, g) sums the
 // columns j = g (mod 16); the 16 partial sums of a row are added in a fixed
 // order.
+// The same product for fronts with few pivot columns (at most 128): one CTA
+// per 64 update rows, thread (row, g) summing the columns j = g mod 4 of its
+// row (coalesced over the rows of a column), one barrier to add the four
+// partial sums.  Four times fewer CTAs than k_fw_gemv1 on the lower levels,
+// where the per-CTA overhead dominated.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fw_gemv1r(SD<T> d, int64_t item_off) {
+  __shared__ T red[4][kNB];
+  const Item it = d.items[item_off + blockIdx.x];
+  const SnInfo f = d.sn[it.s];
+  const int k = f.k, nf = k + f.m;
+  const int tid = threadIdx.x, row = tid & (kNB - 1), g = tid >> 6;
+  const int rows = it.b, r0 = it.a;
+  const T* Lr = d.L + f.Loff + r0 + (row < rows ? row : 0);
+  const T* yx = d.Y + f.first;  // the front's solved pivots
+  T a0 = T(0), a1 = T(0);
+  int j = g;
+  for (; j + 4 < k; j += 8) {
+    const T l0 = Lr[(int64_t)j * nf], l1 = Lr[(int64_t)(j + 4) * nf];
+    a0 = fma(l0, yx[j], a0);
+    a1 = fma(l1, yx[j + 4], a1);
+  }
+  if (j < k) a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
+  red[g][row] = a0 + a1;
+  __syncthreads();
+  if (tid < rows) {
+    const T sum = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+    const int64_t gi = f.woff + r0 + tid;
+    T w = T(0);
+    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e) w += d.W[d.ginv_src[e]];
+    d.W[gi] = w - sum;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fw_gemv1(SD<T> d, int64_t item_off) {
   __shared__ T red[16][17];
@@ -1608,7 +1642,10 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
     k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(
         d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
   else if (L.kind == K_FW_GEMV) {
-    if constexpr (R == 1) k_fw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
+    if constexpr (R == 1) {
+      if (L.tile == 1) k_fw_gemv1r<T><<<L.count, 256, 0, st>>>(d, L.item_off);
+      else k_fw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
+    }
     else k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
   } else if (L.kind == K_FW_PINV) {
     if constexpr (R == 1) k_fw_pinv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);

@@ -1187,7 +1187,11 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     // pivot blocks (flag chains within a front), then the update-row blocks
     // of the level as a streaming product that never waits
     add(S.fwsched, K_FW_LEVEL, lev, 0, it, 0.0);
-    add(S.fwsched, K_FW_GEMV, lev, 0, upd, 0.0);
+    // fronts of at most 128 pivot columns: one CTA per 64 update rows
+    // (tile 1), else four
+    int maxk = 0;
+    for (const Item& x : upd) maxk = std::max(maxk, S.sn[x.s].k);
+    add(S.fwsched, K_FW_GEMV, lev, 0, upd, 0.0, 0, 0, 0, maxk <= 2 * kNB ? 1 : 0);
     // variant 3: gather the pivot rows' w, then one product per row block
     add(S.fwsched, K_FW_PGATHER, lev, 0, pg, 0.0);
     add(S.fwsched, K_FW_PINV, lev, 0, pv, 0.0);
