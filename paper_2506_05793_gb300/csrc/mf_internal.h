@@ -90,7 +90,8 @@ struct Launch {
   int8_t area = 0;
   // K_SYRK: square tile of the FMA trailing update (32, 64 or 128; 0 = 64);
   // K_FW_GEMV: 1 when every front of the launch has at most 128 pivot
-  // columns (one CTA per 64 update rows), else 0
+  // columns (one CTA per 64 update rows), else 0; K_BW_GEMV: CTAs per item
+  // (1 to 4, 16 columns each; 0 = 4)
   uint8_t tile = 0;
 };
 

@@ -667,10 +667,10 @@ __global__ void __launch_bounds__(256) k_fw_gemv1(SD<T> d, int64_t item_off) {
 // rows (lane-consecutive rows, coalesced), each lane keeps 16 column sums,
 // and the warps' sums are added in a fixed order.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bw_gemv1(SD<T> d, int64_t item_off) {
+__global__ void __launch_bounds__(256) k_bw_gemv1(SD<T> d, int64_t item_off, int per) {
   __shared__ T red[8][16];
-  const int sub = blockIdx.x & 3;
-  const Item it = d.items[item_off + (blockIdx.x >> 2)];
+  const int sub = blockIdx.x % per;
+  const Item it = d.items[item_off + blockIdx.x / per];
   const int nc = min(16, it.b - 16 * sub);
   if (nc <= 0) return;  // whole CTA
   const SnInfo f = d.sn[it.s];
@@ -1656,7 +1656,10 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   } else if constexpr (R >= 8) {
     k_bw_gemm<T, R><<<L.count, 256, bw_gemm_smem<T, R>(), st>>>(d, L.item_off);
   } else {
-    k_bw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
+    // CTAs per item: the schedule's count (the widest item's 16-column
+    // pieces), 4 for analyses that do not record it
+    const int per = (L.tile >= 1 && L.tile <= 4) ? (int)L.tile : 4;
+    k_bw_gemv1<T><<<per * L.count, 256, 0, st>>>(d, L.item_off, per);
   }
 }
 

@@ -1223,7 +1223,10 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     for (int c = 0; c < 4; ++c) add(S.bwsched, K_BW_WARP, lev, 2 << c, wcls[c], 0.0);
     // update-row products of every column block first (no waiting), then the
     // flag-chained triangles
-    add(S.bwsched, K_BW_GEMV, lev, 0, upd, 0.0);
+    // CTAs per 64-column item (16 columns each): as many as the widest item needs
+    int maxb = 0;
+    for (const Item& x : upd) maxb = std::max(maxb, x.b);
+    add(S.bwsched, K_BW_GEMV, lev, 0, upd, 0.0, 0, 0, 0, (maxb + 15) / 16);
     add(S.bwsched, K_BW_LEVEL, lev, 1, it, 0.0);
     // variant 3: stage the pivot rows' y, then one product per column block
     add(S.bwsched, K_BW_PCOPY, lev, 0, pg, 0.0);
