@@ -155,43 +155,45 @@ __device__ __forceinline__ T* front_col(const FD<T>& d, const SnInfo& f, int c) 
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 
+// IEEE round-to-nearest reciprocal (the CUDA intrinsics)
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+
 // Unblocked right-looking partial Cholesky of the first `k` columns of an
 // n x n lower-triangular block held column-major in shared memory (ld).
 // Records the first non-positive pivot (global column col0 + j).  With D
 // (LDL^T, paper Sec. 5) the partial factorization is F = L D L^T instead:
 // d_j = F_jj (recorded in D[col0 + j]; a zero pivot is the failure),
-// L(:, j) = F(:, j) / d_j with L_jj = 1, and the trailing update subtracts
-// L(i, j) d_j L(c, j).
+// L(:, j) = F(:, j) / d_j with L_jj = 1.  Both take one barrier per column:
+// the columns stay unscaled during the elimination, F(i, c) -= F(i, j)
+// F(c, j) / d_j (one reciprocal per step, no square root), which leaves the
+// Schur complement in the trailing part, and column j is scaled afterwards
+// by 1 / sqrt(d_j) (L_jj = sqrt(d_j)) or 1 / d_j (L_jj = 1).
 template <typename T>
 __device__ void smem_partial_chol(T* F, int ld, int n, int k, int col0,
                                   unsigned long long* status, T* D) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < k; ++j) {
     const T dj = F[j * ld + j];
-    T ljj, rinv;
-    if (D) {
-      if (tid == 0 && !(dj != T(0))) atomicMin(status, (unsigned long long)(col0 + j));
-      ljj = T(1);
-      rinv = T(1) / dj;
-    } else {
-      if (tid == 0 && !(dj > T(0))) atomicMin(status, (unsigned long long)(col0 + j));
-      ljj = dsqrt(dj);
-      rinv = T(1) / ljj;
-    }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < n; i += blockDim.x) F[j * ld + i] *= rinv;
-    if (tid == 0) {
-      F[j * ld + j] = ljj;
-      if (D) D[col0 + j] = dj;
-    }
-    __syncthreads();
-    const T w = D ? dj : T(1);  // L(c, j) w is the multiplier of column c
+    if (tid == 0 && !(D ? dj != T(0) : dj > T(0)))
+      atomicMin(status, (unsigned long long)(col0 + j));
+    const T rd = recip_rn(dj);
     for (int c = j + 1 + warp; c < n; c += nw) {
-      const T lc = F[j * ld + c] * w;
-      for (int i = c + lane; i < n; i += 32) F[c * ld + i] -= F[j * ld + i] * lc;
+      const T fc = F[j * ld + c] * rd;
+      for (int i = c + lane; i < n; i += 32) F[c * ld + i] -= F[j * ld + i] * fc;
     }
     __syncthreads();
   }
+  for (int j = warp; j < k; j += nw) {
+    const T dj = F[j * ld + j];
+    const T sj = D ? recip_rn(dj) : recip_rn(dsqrt(dj));
+    for (int i = j + 1 + lane; i < n; i += 32) F[j * ld + i] *= sj;
+    if (lane == 0) {
+      F[j * ld + j] = D ? T(1) : dj * sj;
+      if (D) D[col0 + j] = dj;
+    }
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -674,9 +676,6 @@ __device__ __forceinline__ void load_diag_block(const FD<T>& d, const SnInfo& f,
 // ---------------------------------------------------------------------------
 constexpr int kPB = 16;  // block size inside the diagonal-block kernel
 
-// IEEE round-to-nearest reciprocal (the CUDA intrinsics)
-__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
-__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
 
 template <typename T>
 constexpr size_t potrf_smem() {
