@@ -1484,7 +1484,7 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
   bool converged = false;
   for (;; ++it) {
     MF_CK(cudaMemsetAsync(d_rn, 0, 2 * nrhs * sizeof(double), st));
-    MF_CK(mf::launch_residual(f->ds->d.rowptr, f->ds->d.colind, f->vals, n, f->Bd, n, f->Xd, n,
+    MF_CK(mf::launch_residual(f->ds->d.rowptr, f->ds->d.colind, f->vals, n, S->nnzA, f->Bd, n, f->Xd, n,
                               f->Rd, nrhs, d_rn, d_xn, st));
     MF_CK(cudaMemcpyAsync(hn.data() + 1, d_rn, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     MF_CK(cudaStreamSynchronize(st));
@@ -1533,7 +1533,7 @@ int mf_solve_refined(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb, d
     rc = solve_dev(f->fb64, nrhs, f->Bd, n, f->Xd, n, nullptr, nullptr, 0, st);
     if (rc != MF_OK) return rc;
     MF_CK(cudaMemsetAsync(d_rn, 0, 2 * nrhs * sizeof(double), st));
-    MF_CK(mf::launch_residual(f->ds->d.rowptr, f->ds->d.colind, f->vals, n, f->Bd, n, f->Xd, n,
+    MF_CK(mf::launch_residual(f->ds->d.rowptr, f->ds->d.colind, f->vals, n, S->nnzA, f->Bd, n, f->Xd, n,
                               f->Rd, nrhs, d_rn, d_xn, st));
     MF_CK(cudaMemcpyAsync(hn.data() + 1, d_rn, 2 * nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
     MF_CK(cudaStreamSynchronize(st));

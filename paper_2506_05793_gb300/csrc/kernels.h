@@ -151,9 +151,10 @@ cudaError_t launch_perm_out(int prec, const void* Y, const int32_t* perm, const 
 
 // FP64 residual R = B - A X (A in original order), with per-RHS maxima of
 // |R|, |X| accumulated into rnorm[r], xnorm[r] (must be zeroed before).
+// nnz_hint: entries of A (the lanes per row follow the mean row length)
 cudaError_t launch_residual(const int64_t* rowptr, const int32_t* colind, const double* vals,
-                            int64_t n, const double* B, int64_t ldb, const double* X,
-                            int64_t ldx, double* R, int32_t nrhs, double* rnorm,
+                            int64_t n, int64_t nnz_hint, const double* B, int64_t ldb,
+                            const double* X, int64_t ldx, double* R, int32_t nrhs, double* rnorm,
                             double* xnorm, cudaStream_t st);
 // out[0] = max_i sum_j |A_ij|; out[1 + r] = max_i |B_ir|  (out zeroed before)
 cudaError_t launch_norms(const int64_t* rowptr, const double* vals, int64_t n,

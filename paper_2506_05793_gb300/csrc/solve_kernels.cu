@@ -1538,39 +1538,58 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 // global atomic per block and value: a global atomic per row would serialize
 // millions of updates on the same address.
 
-// one warp per row: r = b - A x, plus max |r| and max |x| per RHS
-// (dynamic shared memory: 2 nrhs doubles)
+// r = b - A x, plus max |r| and max |x| per RHS.  G lanes per row (G = 4 to
+// 32 by the mean row length, so short rows do not leave most of a warp
+// idle); a group's lanes take the row's entries G apart and add their sums
+// by shuffles.  The rows of a warp advance together, so the shuffles see
+// every lane; the max-norms are kept per thread and reduced once per warp.
+template <int G>
 __global__ void k_residual(const int64_t* rowptr, const int32_t* colind, const double* vals,
                            int64_t n, const double* B, int64_t ldb, const double* X, int64_t ldx,
                            double* R, int nrhs, double* rnorm, double* xnorm) {
   extern __shared__ double smax[];  // [0, nrhs): |r|, [nrhs, 2 nrhs): |x|
   for (int i = threadIdx.x; i < 2 * nrhs; i += blockDim.x) smax[i] = 0.0;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  constexpr int RPW = 32 / G;  // rows per warp and step
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = wid; row < n; row += nwarps) {
-    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    for (int r = 0; r < nrhs; ++r) {
-      const double* x = X + r * ldx;
-      double s = 0.0, s2 = 0.0;
-      // two entries per lane and step, all their loads issued together
-      // (a step covers 64 entries: most rows in one)
-      for (int64_t p = p0 + lane; p < p1; p += 64) {
-        const bool two = p + 32 < p1;
-        const double v0 = vals[p], v1 = two ? vals[p + 32] : 0.0;
-        const int32_t j0 = colind[p], j1 = two ? colind[p + 32] : 0;
-        const double x0 = x[j0], x1 = two ? x[j1] : 0.0;
-        s = fma(v0, x0, s);
-        s2 = fma(v1, x1, s2);
+  for (int r = 0; r < nrhs; ++r) {
+    const double* x = X + r * ldx;
+    double rmax = 0.0, xmax = 0.0;
+    for (int64_t base = gwarp * RPW; base < n; base += nwarps * RPW) {
+      const int64_t row = base + lane / G;
+      double s = 0.0;
+      if (row < n) {
+        const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+        double s2 = 0.0;
+        int64_t p = p0 + sub;
+        for (; p + G < p1; p += 2 * G) {
+          const double v0 = vals[p], v1 = vals[p + G];
+          const int32_t j0 = colind[p], j1 = colind[p + G];
+          s = fma(v0, x[j0], s);
+          s2 = fma(v1, x[j1], s2);
+        }
+        if (p < p1) s = fma(vals[p], x[colind[p]], s);
+        s += s2;
       }
-      s = warp_sum(s + s2);
-      if (lane == 0) {
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (sub == 0 && row < n) {
         const double res = B[r * ldb + row] - s;
         R[r * n + row] = res;
-        atomic_max_nonneg(&smax[r], fabs(res));
-        atomic_max_nonneg(&smax[nrhs + r], fabs(x[row]));
+        rmax = fmax(rmax, fabs(res));
+        xmax = fmax(xmax, fabs(x[row]));
       }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if (lane == 0) {
+      atomic_max_nonneg(&smax[r], rmax);
+      atomic_max_nonneg(&smax[nrhs + r], xmax);
     }
   }
   __syncthreads();
@@ -1795,14 +1814,26 @@ cudaError_t launch_perm_out(int prec, const void* Y, const int32_t* perm, const 
 }
 
 cudaError_t launch_residual(const int64_t* rowptr, const int32_t* colind, const double* vals,
-                            int64_t n, const double* B, int64_t ldb, const double* X, int64_t ldx,
-                            double* R, int32_t nrhs, double* rnorm, double* xnorm,
-                            cudaStream_t st) {
-  int64_t g = (n * 32 + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
+                            int64_t n, int64_t nnz_hint, const double* B, int64_t ldb,
+                            const double* X, int64_t ldx, double* R, int32_t nrhs, double* rnorm,
+                            double* xnorm, cudaStream_t st) {
+  // lanes per row by the mean row length (the CSR's last row pointer is on
+  // the device, so the length comes from the caller: nnz / n)
+  const int64_t nnz = nnz_hint;
+  const double mean = n > 0 ? (double)nnz / (double)n : 0.0;
+  const int G = mean <= 8 ? 4 : mean <= 16 ? 8 : mean <= 32 ? 16 : 32;
+  int64_t g = (n * G + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
   if (g < 1) g = 1;
-  k_residual<<<(int)g, 256, 2 * (size_t)nrhs * sizeof(double), st>>>(rowptr, colind, vals, n, B, ldb,
-                                                                      X, ldx, R, nrhs, rnorm, xnorm);
+  const size_t sm = 2 * (size_t)nrhs * sizeof(double);
+  if (G == 4)
+    k_residual<4><<<(int)g, 256, sm, st>>>(rowptr, colind, vals, n, B, ldb, X, ldx, R, nrhs, rnorm, xnorm);
+  else if (G == 8)
+    k_residual<8><<<(int)g, 256, sm, st>>>(rowptr, colind, vals, n, B, ldb, X, ldx, R, nrhs, rnorm, xnorm);
+  else if (G == 16)
+    k_residual<16><<<(int)g, 256, sm, st>>>(rowptr, colind, vals, n, B, ldb, X, ldx, R, nrhs, rnorm, xnorm);
+  else
+    k_residual<32><<<(int)g, 256, sm, st>>>(rowptr, colind, vals, n, B, ldb, X, ldx, R, nrhs, rnorm, xnorm);
   return cudaGetLastError();
 }
 
