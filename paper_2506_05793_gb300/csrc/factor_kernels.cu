@@ -159,16 +159,19 @@ __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
 
-// Unblocked right-looking partial Cholesky of the first `k` columns of an
-// n x n lower-triangular block held column-major in shared memory (ld).
-// Records the first non-positive pivot (global column col0 + j).  With D
-// (LDL^T, paper Sec. 5) the partial factorization is F = L D L^T instead:
-// d_j = F_jj (recorded in D[col0 + j]; a zero pivot is the failure),
-// L(:, j) = F(:, j) / d_j with L_jj = 1.  Both take one barrier per column:
-// the columns stay unscaled during the elimination, F(i, c) -= F(i, j)
-// F(c, j) / d_j (one reciprocal per step, no square root), which leaves the
-// Schur complement in the trailing part, and column j is scaled afterwards
-// by 1 / sqrt(d_j) (L_jj = sqrt(d_j)) or 1 / d_j (L_jj = 1).
+// Partial Cholesky of the first `k` columns of an n x n lower-triangular
+// block held column-major in shared memory (ld), n <= kSmallMax.  Records
+// the first non-positive pivot (global column col0 + j).  With D (LDL^T,
+// paper Sec. 5) the partial factorization is F = L D L^T instead: d_j =
+// F_jj (recorded in D[col0 + j]; a zero pivot is the failure), L(:, j) =
+// F(:, j) / d_j with L_jj = 1.
+//   1. the k pivot columns, right-looking inside them, one barrier per
+//      column: F(i, c) -= F(i, j) F(c, j) / d_j for j < c < k, i >= c, the
+//      columns left unscaled (one reciprocal per step, no square root);
+//   2. column j scaled by 1 / sqrt(d_j) (L_jj = sqrt(d_j)) or 1 / d_j;
+//   3. the trailing m x m block (m = n - k) in one pass, F22 -= L21 L21^T
+//      (LDL^T: L21 D L21^T), each thread accumulating 4 x 4 tiles over the k
+//      columns in registers (about half a shared load per FMA).
 template <typename T>
 __device__ void smem_partial_chol(T* F, int ld, int n, int k, int col0,
                                   unsigned long long* status, T* D) {
@@ -178,7 +181,7 @@ __device__ void smem_partial_chol(T* F, int ld, int n, int k, int col0,
     if (tid == 0 && !(D ? dj != T(0) : dj > T(0)))
       atomicMin(status, (unsigned long long)(col0 + j));
     const T rd = recip_rn(dj);
-    for (int c = j + 1 + warp; c < n; c += nw) {
+    for (int c = j + 1 + warp; c < k; c += nw) {
       const T fc = F[j * ld + c] * rd;
       for (int i = c + lane; i < n; i += 32) F[c * ld + i] -= F[j * ld + i] * fc;
     }
@@ -191,6 +194,43 @@ __device__ void smem_partial_chol(T* F, int ld, int n, int k, int col0,
     if (lane == 0) {
       F[j * ld + j] = D ? T(1) : dj * sj;
       if (D) D[col0 + j] = dj;
+    }
+  }
+  __syncthreads();
+  const int m = n - k;
+  if (m <= 0 || k == 0) return;
+  const int nt = (m + 3) >> 2;
+  for (int e = tid; e < nt * nt; e += blockDim.x) {
+    const int I = e / nt, J = e - I * nt;
+    if (I < J) continue;
+    const int r0 = k + 4 * I, q0 = k + 4 * J;
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    for (int j = 0; j < k; ++j) {
+      const T* colj = F + j * ld;
+      const T w = D ? D[col0 + j] : T(1);
+      T a[4], bq[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = r0 + u < n ? colj[r0 + u] : T(0);
+        bq[u] = q0 + u < n ? colj[q0 + u] * w : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], bq[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = q0 + v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + u;
+        if (r < n && c < n && r >= c) F[c * ld + r] -= acc[u][v];
+      }
     }
   }
   __syncthreads();
@@ -222,10 +262,22 @@ __device__ __forceinline__ void small_front_body(const FD<T>& d, int s, T* F) {
     const int mc = ch.m;
     const int32_t* map = d.relmap + ch.map_off;
     const T* Uc = d.U + ch.Uoff;
+    // a child of a small front has mc < kSmallMax rows: its column in at
+    // most four lanes' steps, loads issued together
     for (int jc = warp; jc < mc; jc += nw) {
       const int dc = map[jc];
       const T* u = Uc + (int64_t)jc * mc;
-      for (int ic = jc + lane; ic < mc; ic += 32) F[dc * nf + map[ic]] += __ldcg(u + ic);
+      int pi[kSmallMax / 32];
+      T uv[kSmallMax / 32];
+#pragma unroll
+      for (int q = 0; q < kSmallMax / 32; ++q) {
+        const int ic = jc + lane + 32 * q;
+        pi[q] = ic < mc ? map[ic] : 0;
+        uv[q] = ic < mc ? __ldcg(u + ic) : T(0);
+      }
+#pragma unroll
+      for (int q = 0; q < kSmallMax / 32; ++q)
+        if (jc + lane + 32 * q < mc) F[dc * nf + pi[q]] += uv[q];
     }
     __syncthreads();
   }
