@@ -189,3 +189,20 @@ def test_pivoted_ldlt_on_spd_and_variant_3_refused(mf, orc):
     finally:
         mf.mf_symbolic_free(s)
         mf.mf_destroy(h)
+
+
+def test_pivoted_ldlt_refinement_falls_back(mf, orc):
+    """max_iter = 0: the FP64 pivoted LDL^T fallback delivers the FP64
+    backward error."""
+    rp, ci, v, perm, node_of = saddle((10, 9, 8), seed=3)
+    n = len(rp) - 1
+    h, s = analyse(mf, rp, ci, perm, node_of, relax=1)
+    f = mf.mf_factor_create_ldlt_piv(h, s, 1)
+    try:
+        mf.mf_factor_numeric(f, v)
+        B = gen.rhs(n, 1, seed=7)
+        X, rep = mf.mf_solve_refined(f, B, tol=1e-15, max_iter=0)
+        assert rep["fell_back"] == 1
+        assert orc.berr(rp, ci, v, X, B) <= BERR
+    finally:
+        free(mf, h, s, f)

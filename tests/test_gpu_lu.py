@@ -278,3 +278,66 @@ def test_lu_refuses_variant_3_and_unsymmetric_patterns(mf):
     finally:
         mf.mf_symbolic_free(s)
         mf.mf_destroy(h)
+
+
+def test_lu_many_rhs_and_device_values(mf, orc):
+    """40 right-hand sides (two solve chunks), values and right-hand sides
+    given on the device."""
+    import torch
+    rp, ci, v = gen.nonsym_3d(12, 11, 10, wind=3.0, small_diag=0.2, seed=11)
+    perm = gen.nd_perm((12, 11, 10))
+    n = len(rp) - 1
+    h, s, f = lu_factor(mf, rp, ci, v, perm, pivot=1)
+    try:
+        mf.mf_factor_numeric(f, torch.from_numpy(v).cuda())
+        B = gen.rhs(n, 40, seed=12)
+        X = mf.mf_solve(f, B)
+        assert orc.berr(rp, ci, v, X, B) <= BERR
+        Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+        Xd = mf.mf_solve(f, Bd)
+        torch.cuda.synchronize()
+        assert np.array_equal(Xd.cpu().numpy(), X)
+    finally:
+        free(mf, h, s, f)
+
+
+def test_lu_refinement_falls_back_to_fp64_lu(mf, orc):
+    """max_iter = 0 forces the stagnation branch: the FP64 LU of the same
+    kind (pivoting within the diagonal blocks) must deliver the FP64
+    backward error."""
+    rp, ci, v = gen.nonsym_3d(12, 11, 10, wind=3.0, small_diag=0.2, seed=13)
+    perm = gen.nd_perm((12, 11, 10))
+    n = len(rp) - 1
+    h, s, f = lu_factor(mf, rp, ci, v, perm, prec=1, pivot=1)
+    try:
+        mf.mf_factor_numeric(f, v)
+        B = gen.rhs(n, 1, seed=14)
+        X, rep = mf.mf_solve_refined(f, B, tol=1e-15, max_iter=0)
+        assert rep["fell_back"] == 1
+        assert orc.berr(rp, ci, v, X, B) <= BERR
+    finally:
+        free(mf, h, s, f)
+
+
+def test_lu_on_a_loaded_analysis(mf, orc, tmp_path):
+    """An analysis saved and loaded again factors bit-identically."""
+    rp, ci, v = gen.nonsym_3d(10, 9, 8, wind=3.0, small_diag=0.2, seed=15)
+    perm = gen.nd_perm((10, 9, 8))
+    h, s, f = lu_factor(mf, rp, ci, v, perm, pivot=1)
+    path = str(tmp_path / "lu.mfs")
+    try:
+        mf.mf_factor_numeric(f, v)
+        info = mf.mf_symbolic_get_info(s)
+        a = mf.mf_factor_export_L(f, info["nnz_L"]), mf.mf_factor_export_U(f, info["nnz_L"])
+        mf.mf_symbolic_save(s, path)
+        t = mf.mf_symbolic_load(h, path)
+        g = mf.mf_factor_create_lu(h, t, 0, 1)
+        try:
+            mf.mf_factor_numeric(g, v)
+            b = mf.mf_factor_export_L(g, info["nnz_L"]), mf.mf_factor_export_U(g, info["nnz_L"])
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        finally:
+            mf.mf_factor_free(g)
+            mf.mf_symbolic_free(t)
+    finally:
+        free(mf, h, s, f)
