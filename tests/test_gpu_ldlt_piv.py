@@ -206,3 +206,41 @@ def test_pivoted_ldlt_refinement_falls_back(mf, orc):
         assert orc.berr(rp, ci, v, X, B) <= BERR
     finally:
         free(mf, h, s, f)
+
+
+@pytest.mark.parametrize("case", ["diagonal", "dense"])
+def test_pivoted_ldlt_degenerate_shapes(mf, orc, case):
+    """A diagonal matrix with negative entries (one-column fronts) and a dense
+    symmetric indefinite 150 x 150 block (one front, three pivot blocks with a
+    ragged last one) against the oracle."""
+    rng = np.random.default_rng(18)
+    if case == "diagonal":
+        A = np.diag(np.where(rng.random(40) < 0.5, -1.0, 1.0) * rng.uniform(1, 3, 40))
+    else:
+        M = rng.uniform(-1, 1, (150, 150))
+        A = M + M.T
+    n = len(A)
+    rows, cols = np.nonzero(np.ones_like(A) if case == "dense" else A)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    ci = cols.astype(np.int32)
+    v = A[rows, cols]
+    h = mf.mf_create(mf.mf_options_default())
+    s = mf.mf_symbolic_analyze(h, rp, ci, None)
+    f = mf.mf_factor_create_ldlt_piv(h, s, 0)
+    try:
+        mf.mf_factor_numeric(f, v)
+        B = gen.rhs(n, 2, seed=19)
+        X = mf.mf_solve(f, B)
+        assert orc.berr(rp, ci, v, X, B) <= BERR
+        so = orc.symbolic(rp, ci, None)
+        assert np.array_equal(mf.mf_symbolic_fronts(s), so["sup_ptr"])
+        F = orc.ldlt_dense(rp, ci, v, None, wend=orc.pivot_windows(so["sup_ptr"][:-1], n))
+        L, rho = dense_L(mf, s, f, n)
+        assert np.array_equal(rho, F.rho)
+        g = np.linalg.norm(np.abs(F.L) @ np.diag(np.abs(F.D)) @ np.abs(F.L).T) / np.linalg.norm(A)
+        tol = max(1e-11, 1e-12 * g)
+        assert rel(L, F.L) <= tol
+        assert rel(mf.mf_factor_export_D(f, n), F.D) <= tol
+    finally:
+        free(mf, h, s, f)

@@ -341,3 +341,39 @@ def test_lu_on_a_loaded_analysis(mf, orc, tmp_path):
             mf.mf_symbolic_free(t)
     finally:
         free(mf, h, s, f)
+
+
+@pytest.mark.parametrize("case", ["one", "diagonal", "dense"])
+def test_lu_degenerate_shapes(mf, orc, case):
+    """A 1 x 1 matrix, a diagonal matrix (fronts of one column, no update
+    rows) and a dense nonsymmetric 150 x 150 block (one front, three 64-row
+    pivot blocks with a ragged last one), with pivoting."""
+    rng = np.random.default_rng(16)
+    if case == "one":
+        A = np.array([[-3.0]])
+    elif case == "diagonal":
+        A = np.diag(rng.uniform(-2, 2, 50) + np.where(rng.random(50) < 0.5, 3.0, -3.0))
+    else:
+        A = rng.uniform(-1, 1, (150, 150))
+    n = len(A)
+    rows, cols = np.nonzero(np.ones_like(A) if case == "dense" else A)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    rp[1:] = np.cumsum(np.bincount(rows, minlength=n))
+    ci = cols.astype(np.int32)
+    v = A[rows, cols]
+    h, s, f = lu_factor(mf, rp, ci, v, None, pivot=1)
+    try:
+        mf.mf_factor_numeric(f, v)
+        B = gen.rhs(n, 2, seed=17)
+        X = mf.mf_solve(f, B)
+        assert orc.berr(rp, ci, v, X, B) <= BERR
+        if case == "dense":
+            so = orc.symbolic(rp, ci, None)  # one supernode: windows of 64 columns
+            assert np.array_equal(mf.mf_symbolic_fronts(s), so["sup_ptr"])
+            F = orc.lu_dense(rp, ci, v, None, wend=orc.pivot_windows(so["sup_ptr"][:-1], n))
+            L, U, rho = dense_factors(mf, s, f, n)
+            assert np.array_equal(rho, F.rho)
+            tol = factor_tol(F, rp, ci, v, np.arange(n))
+            assert rel(L, F.L) <= tol and rel(U, F.U) <= tol
+    finally:
+        free(mf, h, s, f)
