@@ -89,11 +89,23 @@ struct Launch {
   int8_t join = 0;
   int8_t area = 0;
   // K_SYRK: square tile of the FMA trailing update (32, 64 or 128; 0 = 64);
-  // K_FW_GEMV: 1 when every front of the launch has at most 128 pivot
-  // columns (one CTA per 64 update rows), else 0; K_BW_GEMV: CTAs per item
-  // (1 to 4, 16 columns each; 0 = 4)
+  // K_FW_GEMV: 2 when every front of the launch has at most 128 pivot
+  // columns, 1 when at most kFwNarrowK (one CTA per 64 update rows), else 0
+  // (four); K_BW_GEMV: CTAs per item (1, 2, 4 or 8: bw_gemv_split of the
+  // launch's largest number of update rows)
   uint8_t tile = 0;
 };
+
+// Forward update-row product of one right-hand side: launches whose fronts
+// have at most this many pivot columns take one CTA per 64 update rows,
+// wider ones four
+constexpr int kFwNarrowK = 512;
+inline int fw_gemv_tile(int maxk) { return maxk <= 2 * kNB ? 2 : maxk <= kFwNarrowK ? 1 : 0; }
+
+// Backward update-row product of one right-hand side: CTAs per 64-column
+// item for a launch whose fronts have at most m update rows, so that a warp
+// reads at most about 512 rows (1, 2, 4 or 8)
+inline int bw_gemv_split(int m) { return m <= 512 ? 1 : m <= 1024 ? 2 : m <= 2048 ? 4 : 8; }
 
 // levels with at most this many large fronts factor with lookahead
 constexpr int kLookaheadFronts = 64;

@@ -584,41 +584,55 @@ __global__ void __launch_bounds__(256) k_fw_gemv(SD<T> d, int64_t item_off) {
   }
 }
 
-// One right-hand side, four CTAs per item (more CTAs for the few, tall
-// fronts of the upper levels).  Forward: CTA (item, sub) takes rows
-// r0 + 16 sub .. + 16 of the item's 64 update rows, thread (row, g) sums the
-// columns j = g (mod 16); the 16 partial sums of a row are added in a fixed
-// order.
-// The same product for fronts with few pivot columns (at most 128): one CTA
-// per 64 update rows, thread (row, g) summing the columns j = g mod 4 of its
-// row (coalesced over the rows of a column), one barrier to add the four
-// partial sums.  Four times fewer CTAs than k_fw_gemv1 on the lower levels,
-// where the per-CTA overhead dominated.
-template <typename T>
-__global__ void __launch_bounds__(256) k_fw_gemv1r(SD<T> d, int64_t item_off) {
+// One right-hand side.  Launches whose fronts have at most kFwNarrowK pivot
+// columns: one CTA per 64 update rows, thread (row, g) summing the columns
+// j = g mod 4 of its row (a warp reads 32 consecutive rows of one column),
+// U loads of L per thread in flight, one barrier to add the four partial
+// sums; U = 2 (32 registers, eight CTAs per SM) when every front of the
+// launch has at most 128 pivot columns, else 8.  Wider launches: four CTAs
+// per item, CTA (item, sub) taking rows r0 + 16 sub .. + 16 and thread
+// (row, g) the columns j = g mod 16, the 16 partial sums of a row added in
+// a fixed order.  The threads that finish a row load its children's entry
+// range before the product, so one round trip of the gather is off the
+// critical path.
+template <typename T, int U>
+__global__ void __launch_bounds__(256, U == 2 ? 8 : 5) k_fw_gemv1r(SD<T> d, int64_t item_off) {
   __shared__ T red[4][kNB];
   const Item it = d.items[item_off + blockIdx.x];
   const SnInfo f = d.sn[it.s];
   const int k = f.k, nf = k + f.m;
   const int tid = threadIdx.x, row = tid & (kNB - 1), g = tid >> 6;
   const int rows = it.b, r0 = it.a;
+  const int64_t gi = f.woff + r0 + tid;
+  int64_t e0 = 0, e1 = 0;
+  if (tid < rows) {
+    e0 = d.ginv_ptr[gi];
+    e1 = d.ginv_ptr[gi + 1];
+  }
   const T* Lr = d.L + f.Loff + r0 + (row < rows ? row : 0);
   const T* yx = d.Y + f.first;  // the front's solved pivots
-  T a0 = T(0), a1 = T(0);
+  T a[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) a[u] = T(0);
   int j = g;
-  for (; j + 4 < k; j += 8) {
-    const T l0 = Lr[(int64_t)j * nf], l1 = Lr[(int64_t)(j + 4) * nf];
-    a0 = fma(l0, yx[j], a0);
-    a1 = fma(l1, yx[j + 4], a1);
+  for (; j + 4 * (U - 1) < k; j += 4 * U) {
+    T l[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) l[u] = Lr[(int64_t)(j + 4 * u) * nf];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = fma(l[u], yx[j + 4 * u], a[u]);
   }
-  if (j < k) a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
-  red[g][row] = a0 + a1;
+  for (; j < k; j += 4) a[0] = fma(Lr[(int64_t)j * nf], yx[j], a[0]);
+#pragma unroll
+  for (int w = 1; w < U; w *= 2)
+#pragma unroll
+    for (int u = 0; u < U; u += 2 * w) a[u] += a[u + w];
+  red[g][row] = a[0];
   __syncthreads();
   if (tid < rows) {
     const T sum = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
-    const int64_t gi = f.woff + r0 + tid;
     T w = T(0);
-    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e) w += d.W[d.ginv_src[e]];
+    for (int64_t e = e0; e < e1; ++e) w += d.W[d.ginv_src[e]];
     d.W[gi] = w - sum;
   }
 }
@@ -634,73 +648,110 @@ __global__ void __launch_bounds__(256) k_fw_gemv1(SD<T> d, int64_t item_off) {
   const int k = f.k, nf = k + f.m;
   const int r0 = it.a + 16 * sub;
   const int tid = threadIdx.x, row = tid & 15, g = tid >> 4;
+  const int64_t gi = f.woff + r0 + tid;
+  int64_t e0 = 0, e1 = 0;
+  if (tid < rows) {
+    e0 = d.ginv_ptr[gi];
+    e1 = d.ginv_ptr[gi + 1];
+  }
   const bool live = row < rows;
   const T* Lr = d.L + f.Loff + r0 + (live ? row : 0);
   const T* yx = d.Y + f.first;  // the front's solved pivots
-  // four independent loads of L per thread in flight
-  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  // eight independent loads of L per thread in flight
+  T a[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) a[u] = T(0);
   int j = g;
-  for (; j + 48 < k; j += 64) {
-    const T l0 = Lr[(int64_t)j * nf], l1 = Lr[(int64_t)(j + 16) * nf];
-    const T l2 = Lr[(int64_t)(j + 32) * nf], l3 = Lr[(int64_t)(j + 48) * nf];
-    a0 = fma(l0, yx[j], a0);
-    a1 = fma(l1, yx[j + 16], a1);
-    a2 = fma(l2, yx[j + 32], a2);
-    a3 = fma(l3, yx[j + 48], a3);
+  for (; j + 112 < k; j += 128) {
+    T l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) l[u] = Lr[(int64_t)(j + 16 * u) * nf];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] = fma(l[u], yx[j + 16 * u], a[u]);
   }
-  for (; j < k; j += 16) a0 = fma(Lr[(int64_t)j * nf], yx[j], a0);
-  red[g][row] = (a0 + a1) + (a2 + a3);
+  for (; j < k; j += 16) a[0] = fma(Lr[(int64_t)j * nf], yx[j], a[0]);
+  red[g][row] = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   __syncthreads();
   if (tid < rows) {
     T sum = T(0);
 #pragma unroll
     for (int q = 0; q < 16; ++q) sum += red[q][tid];
-    const int64_t gi = f.woff + r0 + tid;
     T w = T(0);
-    for (int64_t e = d.ginv_ptr[gi]; e < d.ginv_ptr[gi + 1]; ++e) w += d.W[d.ginv_src[e]];
+    for (int64_t e = e0; e < e1; ++e) w += d.W[d.ginv_src[e]];
     d.W[gi] = w - sum;
   }
 }
 
-// Backward, one right-hand side: CTA (item, sub) takes columns
-// c0 + 16 sub .. + 16 of the item's 64; its eight warps split the update
-// rows (lane-consecutive rows, coalesced), each lane keeps 16 column sums,
-// and the warps' sums are added in a fixed order.
+// Backward, one right-hand side: the P CTAs of a 64-column item (P = 1, 2,
+// 4 or 8, chosen per launch by the largest number of update rows of its
+// fronts, so that one warp reads at most about 512 of them) take 64 / P
+// columns each.  Warp w of a
+// CTA takes 8 of those columns (column group w mod (8 / P)) and one of P row
+// groups (w div (8 / P)); a lane reads NR = 16 bytes / sizeof(T) rows per
+// step (rows t + 32 u, u < NR, coalesced per column), so every thread has
+// 128 bytes of L in flight (16 FP64 or 32 FP32 loads) without spills: FP64
+// 80 registers (three CTAs per SM), FP32 64 (four).  Each lane keeps 8
+// column sums; the warps' sums of a column are added over the row groups in
+// a fixed order.  Levels whose fronts have few update rows thus run one CTA
+// per item and many rows per CTA, which amortises the CTA's start-up and
+// gather latency; levels with many update rows split the rows for
+// parallelism.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bw_gemv1(SD<T> d, int64_t item_off, int per) {
-  __shared__ T red[8][16];
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4)
+    k_bw_gemv1(SD<T> d, int64_t item_off, int per) {
+  constexpr int NC = 8;                    // columns per warp
+  constexpr int NR = 16 / (int)sizeof(T);  // rows per lane and step
+  __shared__ T red[8][NC];
   const int sub = blockIdx.x % per;
   const Item it = d.items[item_off + blockIdx.x / per];
-  const int nc = min(16, it.b - 16 * sub);
-  if (nc <= 0) return;  // whole CTA
+  const int ncta = kNB / per;  // columns of this CTA: 64, 32, 16 or 8
+  if (ncta * sub >= it.b) return;  // whole CTA
   const SnInfo f = d.sn[it.s];
-  const int k = f.k, m = f.m, nf = k + m;
-  const int c0 = it.a + 16 * sub;
+  const int k = f.k, m = f.m, nf = k + f.m;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ngrp = ncta / NC;  // column groups of the CTA: 8 / P
+  const int cg = warp % ngrp, rg = warp / ngrp;
+  const int cb = it.a + ncta * sub;  // first column of the CTA
+  const int c0 = cb + NC * cg;       // first column of the warp
+  const int nc = min(NC, it.a + it.b - c0);
   const T* Lb = d.L + f.Loff + (int64_t)c0 * nf + k;
   const int32_t* frow = d.rowidx + f.rows_off + k;
-  T acc[16];
+  T acc[NC];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) acc[q] = T(0);
-  for (int i = warp * 32 + lane; i < m; i += 256) {
-    const T xi = d.Y[d.ipos ? d.ipos[frow[i]] : frow[i]];
-    T lv[16];
+  for (int q = 0; q < NC; ++q) acc[q] = T(0);
+  if (nc > 0) {
+#pragma unroll 1
+    for (int t = rg * 32 * NR + lane; t < m; t += per * 32 * NR) {
+      T xv[NR];
+      T lv[NR][NC];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) lv[q] = q < nc ? Lb[(int64_t)q * nf + i] : T(0);
+      for (int u = 0; u < NR; ++u) {
+        const int i = t + 32 * u;
+        const bool ok = i < m;
+        const int ir = ok ? i : 0;
+        const T* p = Lb + ir;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = fma(lv[q], xi, acc[q]);
+        for (int q = 0; q < NC; ++q, p += nf) lv[u][q] = (ok && q < nc) ? *p : T(0);
+        const int32_t g = frow[ir];
+        xv[u] = ok ? d.Y[d.ipos ? d.ipos[g] : g] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < NR; ++u)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) acc[q] = fma(lv[u][q], xv[u], acc[q]);
+    }
   }
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
+  for (int q = 0; q < NC; ++q) {
     const T v = warp_sum(acc[q]);
     if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
-  if (tid < nc) {
+  if (tid < ncta && cb + tid < it.a + it.b) {
+    const int g = tid / NC, q = tid % NC;
     T sum = T(0);
-#pragma unroll
-    for (int w = 0; w < 8; ++w) sum += red[w][tid];
-    d.Y[f.first + c0 + tid] -= sum;
+    for (int r = 0; r < per; ++r) sum += red[r * ngrp + g][q];
+    d.Y[f.first + cb + tid] -= sum;
   }
 }
 
@@ -1049,6 +1100,9 @@ __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int6
   const int64_t g0 = f.woff + s0, g1 = f.woff + s1;
   const int64_t e00 = i0 < nf ? d.ginv_ptr[g0] : 0, e01 = i0 < nf ? d.ginv_ptr[g0 + 1] : 0;
   const int64_t e10 = i1 < nf ? d.ginv_ptr[g1] : 0, e11 = i1 < nf ? d.ginv_ptr[g1 + 1] : 0;
+  // the first child's entry of both rows loads together; rows with more
+  // children add the rest afterwards, in the same order
+  const int64_t src0 = e00 < e01 ? d.ginv_src[e00] : -1, src1 = e10 < e11 ? d.ginv_src[e10] : -1;
   for (int rb = 0; rb < nrhs; rb += RB) {
     T w0[RB], w1[RB];
 #pragma unroll
@@ -1058,8 +1112,10 @@ __global__ void __launch_bounds__(256) k_fw_tiny(SD<T> d, int64_t item_off, int6
       if (r < nrhs) {
         if (i0 < k) v0 = d.Y[(int64_t)r * d.n + f.first + s0];
         if (i1 < k) v1 = d.Y[(int64_t)r * d.n + f.first + s1];
-        for (int64_t e = e00; e < e01; ++e) v0 += d.W[d.ginv_src[e] * nrhs + r];
-        for (int64_t e = e10; e < e11; ++e) v1 += d.W[d.ginv_src[e] * nrhs + r];
+        if (src0 >= 0) v0 += d.W[src0 * nrhs + r];
+        if (src1 >= 0) v1 += d.W[src1 * nrhs + r];
+        for (int64_t e = e00 + 1; e < e01; ++e) v0 += d.W[d.ginv_src[e] * nrhs + r];
+        for (int64_t e = e10 + 1; e < e11; ++e) v1 += d.W[d.ginv_src[e] * nrhs + r];
       }
       w0[q] = v0;
       w1[q] = v1;
@@ -1178,6 +1234,7 @@ __global__ void __launch_bounds__(256) k_bw_tiny(SD<T> d, int64_t item_off, int6
 // ---------------------------------------------------------------------------
 template <typename T, int H, int RB>
 __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, int64_t count) {
+  static_assert(H % 4 == 0, "rows per lane are gathered four at a time");
   constexpr int LB = sizeof(T) == 8 ? 16 : 32;  // L loads issued together
   __shared__ __align__(16) T ws_all[8 * 32 * H * RB];
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
@@ -1189,28 +1246,40 @@ __global__ void __launch_bounds__(256, 2) k_fw_warp(SD<T> d, int64_t item_off, i
   const T* Lp = d.L + f.Loff;
   for (int rb = 0; rb < nrhs; rb += RB) {
     __syncwarp();
-    {
-      int64_t e0[H], e1[H];
-      int si[H];  // LU with pivoting: the row whose values pivot position i takes
+    // four rows per lane at a time: their entry ranges, then their first
+    // children's entries, then those values load together (rows with more
+    // children add the rest afterwards, in the same order)
+#pragma unroll 1
+    for (int h0 = 0; h0 < H; h0 += 4) {
+      int64_t e0[4], e1[4], src[4];
+      int si[4];  // LU with pivoting: the row whose values pivot position i takes
 #pragma unroll
-      for (int h = 0; h < H; ++h) {
-        const int i = lane + 32 * h;
-        si[h] = (d.piv && i < k) ? (i & ~(kNB - 1)) + (int)d.piv[f.first + i] : i;
-        e0[h] = i < nf ? d.ginv_ptr[f.woff + si[h]] : 0;
-        e1[h] = i < nf ? d.ginv_ptr[f.woff + si[h] + 1] : 0;
+      for (int hh = 0; hh < 4; ++hh) {
+        const int i = lane + 32 * (h0 + hh);
+        si[hh] = (d.piv && i < k) ? (i & ~(kNB - 1)) + (int)d.piv[f.first + i] : i;
+        e0[hh] = i < nf ? d.ginv_ptr[f.woff + si[hh]] : 0;
+        e1[hh] = i < nf ? d.ginv_ptr[f.woff + si[hh] + 1] : 0;
       }
 #pragma unroll
-      for (int h = 0; h < H; ++h) {
-        const int i = lane + 32 * h;
+      for (int hh = 0; hh < 4; ++hh) src[hh] = e0[hh] < e1[hh] ? d.ginv_src[e0[hh]] : -1;
 #pragma unroll
-        for (int q = 0; q < RB; ++q) {
-          const int r = rb + q;
-          T v = T(0);
-          if (r < nrhs) {
-            if (i < k) v = d.Y[(int64_t)r * d.n + f.first + si[h]];
-            for (int64_t e = e0[h]; e < e1[h]; ++e) v += d.W[d.ginv_src[e] * nrhs + r];
-          }
-          ws[i * RB + q] = v;
+      for (int q = 0; q < RB; ++q) {
+        const int r = rb + q;
+        T v[4];
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh) {
+          const int i = lane + 32 * (h0 + hh);
+          v[hh] = (r < nrhs && i < k) ? d.Y[(int64_t)r * d.n + f.first + si[hh]] : T(0);
+        }
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh)
+          if (r < nrhs && src[hh] >= 0) v[hh] += d.W[src[hh] * nrhs + r];
+#pragma unroll
+        for (int hh = 0; hh < 4; ++hh) {
+          const int i = lane + 32 * (h0 + hh);
+          if (r < nrhs)
+            for (int64_t e = e0[hh] + 1; e < e1[hh]; ++e) v[hh] += d.W[d.ginv_src[e] * nrhs + r];
+          ws[i * RB + q] = v[hh];
         }
       }
     }
@@ -1305,8 +1374,10 @@ __device__ __forceinline__ T transpose_sum32(T (&p)[32], int lane) {
 // hands column j0 + l's sum to lane l, and the triangle of the diagonal
 // block is solved with lane l owning column j0 + l (one shuffle per pivot).
 // ---------------------------------------------------------------------------
+// FP32 fits three CTAs per SM without spills.
 template <typename T, int H>
-__global__ void __launch_bounds__(256, 2) k_bw_warp(SD<T> d, int64_t item_off, int64_t count) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    k_bw_warp(SD<T> d, int64_t item_off, int64_t count) {
   constexpr int LB = sizeof(T) == 8 ? 16 : 32;
   __shared__ T xs_all[8 * 32 * H];
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
@@ -1662,7 +1733,8 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
         d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
   else if (L.kind == K_FW_GEMV) {
     if constexpr (R == 1) {
-      if (L.tile == 1) k_fw_gemv1r<T><<<L.count, 256, 0, st>>>(d, L.item_off);
+      if (L.tile == 2) k_fw_gemv1r<T, 2><<<L.count, 256, 0, st>>>(d, L.item_off);
+      else if (L.tile == 1) k_fw_gemv1r<T, 8><<<L.count, 256, 0, st>>>(d, L.item_off);
       else k_fw_gemv1<T><<<4 * L.count, 256, 0, st>>>(d, L.item_off);
     }
     else k_fw_gemv<T, R><<<L.count, 256, gemv_smem<T, R>(), st>>>(d, L.item_off);
@@ -1675,9 +1747,9 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   } else if constexpr (R >= 8) {
     k_bw_gemm<T, R><<<L.count, 256, bw_gemm_smem<T, R>(), st>>>(d, L.item_off);
   } else {
-    // CTAs per item: the schedule's count (the widest item's 16-column
-    // pieces), 4 for analyses that do not record it
-    const int per = (L.tile >= 1 && L.tile <= 4) ? (int)L.tile : 4;
+    // CTAs per item: the launch's row split P (1, 2, 4 or 8)
+    const int per = (int)L.tile;
+    if (per != 1 && per != 2 && per != 4 && per != 8) return;  // rejected on load
     k_bw_gemv1<T><<<per * L.count, 256, 0, st>>>(d, L.item_off, per);
   }
 }

@@ -1187,11 +1187,13 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     // pivot blocks (flag chains within a front), then the update-row blocks
     // of the level as a streaming product that never waits
     add(S.fwsched, K_FW_LEVEL, lev, 0, it, 0.0);
-    // fronts of at most 128 pivot columns: one CTA per 64 update rows
-    // (tile 1), else four
-    int maxk = 0;
-    for (const Item& x : upd) maxk = std::max(maxk, S.sn[x.s].k);
-    add(S.fwsched, K_FW_GEMV, lev, 0, upd, 0.0, 0, 0, 0, maxk <= 2 * kNB ? 1 : 0);
+    // one CTA per 64 update rows when every front has at most kFwNarrowK
+    // pivot columns (tile 2 up to 128 of them, 1 beyond), else four (tile 0)
+    {
+      int maxk = 0;
+      for (const Item& x : upd) maxk = std::max(maxk, S.sn[x.s].k);
+      add(S.fwsched, K_FW_GEMV, lev, 0, upd, 0.0, 0, 0, 0, fw_gemv_tile(maxk));
+    }
     // variant 3: gather the pivot rows' w, then one product per row block
     add(S.fwsched, K_FW_PGATHER, lev, 0, pg, 0.0);
     add(S.fwsched, K_FW_PINV, lev, 0, pv, 0.0);
@@ -1223,10 +1225,12 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     for (int c = 0; c < 4; ++c) add(S.bwsched, K_BW_WARP, lev, 2 << c, wcls[c], 0.0);
     // update-row products of every column block first (no waiting), then the
     // flag-chained triangles
-    // CTAs per 64-column item (16 columns each): as many as the widest item needs
-    int maxb = 0;
-    for (const Item& x : upd) maxb = std::max(maxb, x.b);
-    add(S.bwsched, K_BW_GEMV, lev, 0, upd, 0.0, 0, 0, 0, (maxb + 15) / 16);
+    // CTAs per 64-column item: the row split of the launch's tallest front
+    {
+      int maxm = 0;
+      for (const Item& x : upd) maxm = std::max(maxm, S.sn[x.s].m);
+      add(S.bwsched, K_BW_GEMV, lev, 0, upd, 0.0, 0, 0, 0, bw_gemv_split(maxm));
+    }
     add(S.bwsched, K_BW_LEVEL, lev, 1, it, 0.0);
     // variant 3: stage the pivot rows' y, then one product per column block
     add(S.bwsched, K_BW_PCOPY, lev, 0, pg, 0.0);
@@ -1579,9 +1583,11 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
             break;
           case K_FW_GEMV:
             if (it.a < f.k) return fail("forward update block inside the pivots");
+            if (L.tile > fw_gemv_tile(f.k)) return fail("forward update product too narrow for its front");
             upd[it.s].push_back({it.a, it.b});
             break;
           case K_BW_GEMV:
+            if (L.tile < bw_gemv_split(f.m)) return fail("backward update split below its front's");
             gemv[it.s].push_back({it.a, it.b});
             break;
           case K_FW_PGATHER:

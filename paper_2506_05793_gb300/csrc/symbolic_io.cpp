@@ -22,7 +22,7 @@
 namespace {
 
 constexpr char kMagic[8] = {'M', 'F', 'S', 'Y', 'M', 'B', 'O', 'L'};
-constexpr uint32_t kVersion = 4;
+constexpr uint32_t kVersion = 5;
 constexpr uint64_t kFnvOffset = 1469598103934665603ull;
 constexpr uint64_t kFnvPrime = 1099511628211ull;
 
@@ -200,6 +200,10 @@ bool consistent(const mf_symbolic& s) {
     for (const mf::Launch& L : *sched)
       if (L.item_off < 0 || L.count < 0 || (size_t)(L.item_off + L.count) > s.items.size())
         return false;
+  // the backward update-row product launches P = tile CTAs per item
+  for (const mf::Launch& L : s.bwsched)
+    if (L.kind == mf::K_BW_GEMV && L.tile != 1 && L.tile != 2 && L.tile != 4 && L.tile != 8)
+      return false;
   for (const mf::Item& it : s.items)
     if (it.s < -1 || it.s >= (int64_t)nf) return false;
   return true;
