@@ -685,12 +685,14 @@ __global__ void __launch_bounds__(256) k_fw_gemv1(SD<T> d, int64_t item_off) {
 // Backward, one right-hand side: the P CTAs of a 64-column item (P = 1, 2,
 // 4 or 8, chosen per launch by the largest number of update rows of its
 // fronts, so that one warp reads at most about 512 of them) take 64 / P
-// columns each.  Warp w of a
-// CTA takes 8 of those columns (column group w mod (8 / P)) and one of P row
-// groups (w div (8 / P)); a lane reads NR = 16 bytes / sizeof(T) rows per
-// step (rows t + 32 u, u < NR, coalesced per column), so every thread has
-// 128 bytes of L in flight (16 FP64 or 32 FP32 loads) without spills: FP64
-// 80 registers (three CTAs per SM), FP32 64 (four).  Each lane keeps 8
+// columns each.  Warp w of a CTA takes 8 of those columns (column group
+// w mod G) and one of 8 / G row groups (w div G), G the number of 8-column
+// groups the CTA's columns fill (a power of two up to 8 / P, so all eight
+// warps of an item of two columns read its rows); a lane reads NR =
+// 16 bytes / sizeof(T) rows per step (rows t + 32 u, u < NR, coalesced per
+// column), so every thread has 128 bytes of L in flight (16 FP64 or 32 FP32
+// loads) without spills: FP64 80 registers (three CTAs per SM), FP32 64
+// (four).  Each lane keeps 8
 // column sums; the warps' sums of a column are added over the row groups in
 // a fixed order.  Levels whose fronts have few update rows thus run one CTA
 // per item and many rows per CTA, which amortises the CTA's start-up and
@@ -709,7 +711,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4)
   const SnInfo f = d.sn[it.s];
   const int k = f.k, m = f.m, nf = k + f.m;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ngrp = ncta / NC;  // column groups of the CTA: 8 / P
+  // column groups: as many 8-column groups as the CTA's columns need (a
+  // power of two up to 8 / P), the other warps split the rows further
+  const int wc = min(ncta, it.b - ncta * sub);
+  int ngrp = 1;
+  while (ngrp * NC < wc) ngrp *= 2;
+  const int nrg = 8 / ngrp;  // row groups
   const int cg = warp % ngrp, rg = warp / ngrp;
   const int cb = it.a + ncta * sub;  // first column of the CTA
   const int c0 = cb + NC * cg;       // first column of the warp
@@ -721,7 +728,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4)
   for (int q = 0; q < NC; ++q) acc[q] = T(0);
   if (nc > 0) {
 #pragma unroll 1
-    for (int t = rg * 32 * NR + lane; t < m; t += per * 32 * NR) {
+    for (int t = rg * 32 * NR + lane; t < m; t += nrg * 32 * NR) {
       T xv[NR];
       T lv[NR][NC];
 #pragma unroll
@@ -747,10 +754,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4)
     if (lane == 0) red[warp][q] = v;
   }
   __syncthreads();
-  if (tid < ncta && cb + tid < it.a + it.b) {
+  if (tid < wc) {
     const int g = tid / NC, q = tid % NC;
     T sum = T(0);
-    for (int r = 0; r < per; ++r) sum += red[r * ngrp + g][q];
+    for (int r = 0; r < nrg; ++r) sum += red[r * ngrp + g][q];
     d.Y[f.first + cb + tid] -= sum;
   }
 }
