@@ -1210,9 +1210,7 @@ int mf_symbolic_options(const mf_symbolic* s, mf_options* opt) {
 // ---------------------------------------------------------------------------
 namespace {
 
-int64_t sync_ints(const mf_symbolic* S) {
-  return 2 * (int64_t)S->nlevels + 2 * (int64_t)S->blkoff.back() + 1;
-}
+int64_t sync_ints(const mf_symbolic* S) { return 2 * (int64_t)S->nlevels + 1; }
 
 // Enqueue one solve pass (nrhs <= kSolveChunk) on Y/W/sync work memory.
 int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X, int64_t ldx,
@@ -1232,12 +1230,16 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
   a.n = S->n;
   a.nrhs = cn;
   a.nlevels = S->nlevels;
-  a.nblk = S->blkoff.back();
   a.dinv = S->keep_inv ? f->dinv : nullptr;
   a.P = f->P;
   a.PT = f->PT;
   a.piv = f->piv;
   a.ipos = f->ipos;
+  // the flag-chained pivot blocks hand their values over through slots of W
+  // that must start as the all-ones pattern in each sweep (variant 4 keeps
+  // its forward results in W and has no chains)
+  const size_t wbytes = (size_t)S->Wsize * cn * elem_size(f->prec);
+  if (!S->v4) MF_CK(cudaMemsetAsync(W, 0xff, wbytes, st));
   for (const mf::Launch& L : S->fwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   // LDL^T: z = D^{-1} z between the sweeps (the forward results sit in Y,
   // or for SpTRSV variant 4 in the first n x nrhs values of W)
@@ -1248,6 +1250,7 @@ int solve_pass(mf_factor* f, int32_t cn, const double* B, int64_t ldb, double* X
     a.dinv = S->keep_inv ? f->dinvu : nullptr;
     a.piv = nullptr;
   }
+  if (!S->v4) MF_CK(cudaMemsetAsync(W, 0xff, wbytes, st));
   for (const mf::Launch& L : S->bwsched) MF_CK(mf::launch_solve(f->prec, L, a, st));
   MF_CK(mf::launch_perm_out(f->prec, Y, f->ds->d.perm, f->ipos, X, ldx, S->n, cn, scale,
                             accumulate, st));

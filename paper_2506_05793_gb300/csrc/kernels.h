@@ -85,9 +85,11 @@ struct SolveArgs {
   DevSym sym;
   const void* L;  // T
   void* Y;        // T[n * nrhs]  permuted RHS / solution
-  void* W;        // T[Wsize * nrhs] front work vectors
-  // int32[2 * nlevels + 2 * nblk], zero before every solve: one ticket
-  // counter per level and sweep, then forward and backward block flags
+  // T[Wsize * nrhs] front work vectors; the pivot rows' slots of the
+  // flag-chained fronts carry their solved values, all ones before a sweep
+  void* W;
+  // int32[2 * nlevels + 1], zero before every solve: one ticket counter per
+  // level and sweep
   int32_t* sync;
   unsigned long long* status;  // the solve's timeout record: MF_ERR_TIMEOUT when a wait gives up
   // diagonal-block inverses of the large fronts (slots sym.ioff), or nullptr
@@ -99,8 +101,7 @@ struct SolveArgs {
   int64_t n;
   int32_t nrhs;
   int32_t nlevels;
-  int32_t nblk;
-  int32_t wait_polls = 0;  // polls before a flag wait gives up (0: the default bound)
+  int32_t wait_polls = 0;  // polls before a wait gives up (0: the default bound)
   // LU with pivoting, forward sweep: pivot position i of a 64-row block
   // takes row (i & ~63) + piv[i] of that block; nullptr elsewhere
   const uint8_t* piv = nullptr;

@@ -95,16 +95,13 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // The whole CTA waits until *flag != 0 (thread 0 polls with acquire loads,
 // 128 ns apart); after `limit` polls it gives up, records MF_ERR_TIMEOUT in
-// *status and lets the block continue (no hang).
+// *status and lets the block continue (no hang).  Used by the wait probe of
+// the diagnostics; the solve's chains poll value slots instead.
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* status, int limit) {
@@ -123,13 +120,47 @@ __device__ __forceinline__ void cta_wait(const int* flag, unsigned long long* st
   __syncthreads();
 }
 
-// The CTA barrier orders every thread's writes before thread 0, whose
-// release store publishes them at GPU scope: release is cumulative, so the
-// writes ordered before it by the barrier are visible to a thread that
-// acquires the flag (no separate fence needed).
-__device__ __forceinline__ void cta_publish(int* flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) st_release(flag, 1);
+// Solved values of a pivot block reach the later blocks of the same front
+// through the pivot rows' slots of the front work vector W (unused
+// otherwise by the chained fronts), which the host fills with the
+// all-ones bit pattern before each sweep: a NaN that IEEE arithmetic never
+// returns (its NaNs are canonical).  The producer stores each value with a
+// relaxed GPU-scope store; a consumer thread polls its slot with relaxed
+// loads until the pattern is gone, so a hand-off costs the store's trip to
+// L2 and one poll, not a release, an acquire and a reload of the values.
+// A poll gives up after `limit` tries, records MF_ERR_TIMEOUT in *status
+// and returns the pattern (the CTA goes on; no hang).
+__device__ __forceinline__ void st_slot(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(__double_as_longlong(v))
+               : "memory");
+}
+__device__ __forceinline__ void st_slot(float* p, float v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(__float_as_uint(v)) : "memory");
+}
+__device__ __forceinline__ bool ld_slot(const double* p, double* v) {
+  long long b;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p) : "memory");
+  *v = __longlong_as_double(b);
+  return b != -1ll;
+}
+__device__ __forceinline__ bool ld_slot(const float* p, float* v) {
+  unsigned b;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(b) : "l"(p) : "memory");
+  *v = __uint_as_float(b);
+  return b != 0xffffffffu;
+}
+template <typename T>
+__device__ __forceinline__ T poll_slot(const T* p, unsigned long long* status, int limit) {
+  T v;
+  int spins = 0;
+  while (!ld_slot(p, &v)) {
+    if (++spins > limit) {
+      atomicExch(status, (unsigned long long)MF_ERR_TIMEOUT);
+      break;
+    }
+    if (spins > 64) __nanosleep(128);
+  }
+  return v;
 }
 
 // Row pitches of the per-RHS shared arrays: padded so that lanes stepping
@@ -184,14 +215,14 @@ constexpr size_t bw_level_smem() {
 // front work vector, w = b(first..) + the children's update entries (inverse
 // relative maps, children in fixed order), then
 //   x_p = L_pp^{-1} (w_p - sum_{a<p} L_pa x_a),
-// written to Y and published through flag p; earlier blocks are awaited
-// through their flags.  Thread (row, g): row of the block, g = quarter of the
+// written to Y and to block p's slots; the values of earlier blocks are
+// polled from their slots (st_slot / poll_slot).  Thread (row, g): row of the block, g = quarter of the
 // 64 columns of L_pa.  The L values of block a+1 are loaded into registers
 // while the block waits for x_a, so the DRAM latency is off the critical path.
 // ---------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(256, 2)
-    k_fw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
+    k_fw_level(SD<T> d, int64_t item_off, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RX = xs_pitch<R>(), RP = red_pitch<R>();
   T* xs = reinterpret_cast<T*>(smem_raw);  // xs[q * RX + r]
@@ -209,7 +240,6 @@ __global__ void __launch_bounds__(256, 2)
   const int k = f.k, nf = k + f.m;
   const int r0 = it.a, rows = it.b;
   const int tid = threadIdx.x, row = tid & 63, g = tid >> 6, lane = tid & 31, warp = tid >> 5;
-  int* fl = flags + d.blkoff[it.s];
   const T* Lp = d.L + f.Loff;
   const int nblk = r0 / kNB;  // earlier pivot blocks of the front
   // L values of block 0 (thread: column 16 g + qq of the block, its row)
@@ -279,11 +309,11 @@ __global__ void __launch_bounds__(256, 2)
       const int q = g * 16 + qq;
       Ln[qq] = (more && live && q < bsn) ? Lp[(int64_t)((a + 1) * kNB + q) * nf + r0 + row] : T(0);
     }
-    cta_wait(fl + a, d.status, d.wait_polls);
     const int bsa = min(kNB, k - a * kNB);
+    const T* sl = d.W + (f.woff + (int64_t)a * kNB) * nrhs;  // block a's slots
     for (int idx = tid; idx < bsa * nrhs; idx += blockDim.x) {
       const int r = idx / bsa, q = idx % bsa;
-      xs[q * RX + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + a * kNB + q);
+      xs[q * RX + r] = poll_slot(sl + (int64_t)q * nrhs + r, d.status, d.wait_polls);
     }
     __syncthreads();
 #pragma unroll
@@ -322,11 +352,11 @@ __global__ void __launch_bounds__(256, 2)
     __syncthreads();
     for (int idx = tid; idx < rows * nrhs; idx += blockDim.x) {
       const int rw = idx / nrhs, r = idx % nrhs;
-      d.Y[(int64_t)r * d.n + f.first + r0 + rw] =
-          red[(0 * kNB + rw) * RP + r] + red[(1 * kNB + rw) * RP + r] +
-          red[(2 * kNB + rw) * RP + r] + red[(3 * kNB + rw) * RP + r];
+      const T x = red[(0 * kNB + rw) * RP + r] + red[(1 * kNB + rw) * RP + r] +
+                  red[(2 * kNB + rw) * RP + r] + red[(3 * kNB + rw) * RP + r];
+      d.Y[(int64_t)r * d.n + f.first + r0 + rw] = x;
+      st_slot(d.W + (f.woff + r0 + rw) * nrhs + r, x);
     }
-    cta_publish(fl + r0 / kNB);
     return;
   }
   // column-oriented substitution, one warp per right-hand side; lane owns
@@ -345,23 +375,28 @@ __global__ void __launch_bounds__(256, 2)
         else if (lane + 32 > j && lane + 32 < rows) v1 = fma(-D[j * ld + lane + 32], xj, v1);
       }
     }
-    if (lane < rows) d.Y[(int64_t)r * d.n + f.first + r0 + lane] = v0;
-    if (lane + 32 < rows) d.Y[(int64_t)r * d.n + f.first + r0 + lane + 32] = v1;
+    if (lane < rows) {
+      d.Y[(int64_t)r * d.n + f.first + r0 + lane] = v0;
+      st_slot(d.W + (f.woff + r0 + lane) * nrhs + r, v0);
+    }
+    if (lane + 32 < rows) {
+      d.Y[(int64_t)r * d.n + f.first + r0 + lane + 32] = v1;
+      st_slot(d.W + (f.woff + r0 + lane + 32) * nrhs + r, v1);
+    }
   }
-  cta_publish(fl + r0 / kNB);
 }
 
 // ---------------------------------------------------------------------------
 // Backward, one 64-column pivot block c of a large front:
 //   x_c = L_cc^{-T} (y'_c - sum_{a>c} L_ac^T x_a),
 // y' = y - L21[:, c]^T x(update rows), already formed by k_bw_gemv1 /
-// k_bw_gemm; later blocks are awaited through their flags.  Thread (col, g)
+// k_bw_gemm; the values of later blocks are polled from their slots.  Thread (col, g)
 // holds rows 16 g .. 16 g + 15 of its column of the current 64-row tile in
 // registers; the next tile is loaded while the block waits.
 // ---------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(256, 2)
-    k_bw_level(SD<T> d, int64_t item_off, int* counter, int* flags) {
+    k_bw_level(SD<T> d, int64_t item_off, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ld = kNB + 1;
   constexpr int RX = xs_pitch<R>(), RP = red_pitch<R>();
@@ -378,7 +413,6 @@ __global__ void __launch_bounds__(256, 2)
   const int k = f.k, nf = k + f.m;
   const int c0 = it.a, bs = it.b;
   const int tid = threadIdx.x, col = tid & 63, g = tid >> 6, lane = tid & 31, warp = tid >> 5;
-  int* fl = flags + d.blkoff[it.s];
   const T* Lp = d.L + f.Loff;
   const bool live = col < bs;
   const T* Lcol = Lp + (int64_t)(c0 + (live ? col : 0)) * nf;
@@ -448,10 +482,10 @@ __global__ void __launch_bounds__(256, 2)
         Ln[ii] = (live && i < nt) ? Lcol[n0 + i] : T(0);
       }
     }
-    cta_wait(fl + i0 / kNB, d.status, d.wait_polls);
+    const T* sl = d.W + (f.woff + i0) * nrhs;  // the later block's slots
     for (int idx = tid; idx < ti * nrhs; idx += blockDim.x) {
       const int i = idx % ti, r = idx / ti;
-      xs[i * RX + r] = __ldcg(d.Y + (int64_t)r * d.n + f.first + i0 + i);
+      xs[i * RX + r] = poll_slot(sl + (int64_t)i * nrhs + r, d.status, d.wait_polls);
     }
     __syncthreads();
 #pragma unroll
@@ -494,11 +528,11 @@ __global__ void __launch_bounds__(256, 2)
     __syncthreads();
     for (int idx = tid; idx < bs * nrhs; idx += blockDim.x) {
       const int c = idx / nrhs, r = idx % nrhs;
-      d.Y[(int64_t)r * d.n + f.first + c0 + c] =
-          red[(0 * kNB + c) * RP + r] + red[(1 * kNB + c) * RP + r] +
-          red[(2 * kNB + c) * RP + r] + red[(3 * kNB + c) * RP + r];
+      const T x = red[(0 * kNB + c) * RP + r] + red[(1 * kNB + c) * RP + r] +
+                  red[(2 * kNB + c) * RP + r] + red[(3 * kNB + c) * RP + r];
+      d.Y[(int64_t)r * d.n + f.first + c0 + c] = x;
+      st_slot(d.W + (f.woff + c0 + c) * nrhs + r, x);
     }
-    cta_publish(fl + c0 / kNB);
     return;
   }
   // right-looking substitution with L_cc^T, one warp per right-hand side;
@@ -517,10 +551,15 @@ __global__ void __launch_bounds__(256, 2)
         v0 = fma(-Dt[j * ld + lane], xj, v0);
       }
     }
-    if (lane < bs) d.Y[(int64_t)r * d.n + f.first + c0 + lane] = v0;
-    if (lane + 32 < bs) d.Y[(int64_t)r * d.n + f.first + c0 + lane + 32] = v1;
+    if (lane < bs) {
+      d.Y[(int64_t)r * d.n + f.first + c0 + lane] = v0;
+      st_slot(d.W + (f.woff + c0 + lane) * nrhs + r, v0);
+    }
+    if (lane + 32 < bs) {
+      d.Y[(int64_t)r * d.n + f.first + c0 + lane + 32] = v1;
+      st_slot(d.W + (f.woff + c0 + lane + 32) * nrhs + r, v1);
+    }
   }
-  cta_publish(fl + c0 / kNB);
 }
 
 // ---------------------------------------------------------------------------
@@ -1733,11 +1772,11 @@ template <typename T, int R>
 void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   const SD<T> d = make_sd<T>(a);
   if (L.kind == K_FW_LEVEL)
-    k_fw_level<T, R><<<L.count, 256, fw_level_smem<T, R>(), st>>>(
-        d, L.item_off, a.sync + 2 * L.level, a.sync + 2 * a.nlevels);
+    k_fw_level<T, R><<<L.count, 256, fw_level_smem<T, R>(), st>>>(d, L.item_off,
+                                                                   a.sync + 2 * L.level);
   else if (L.kind == K_BW_LEVEL)
-    k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(
-        d, L.item_off, a.sync + 2 * L.level + 1, a.sync + 2 * a.nlevels + a.nblk);
+    k_bw_level<T, R><<<L.count, 256, bw_level_smem<T, R>(), st>>>(d, L.item_off,
+                                                                   a.sync + 2 * L.level + 1);
   else if (L.kind == K_FW_GEMV) {
     if constexpr (R == 1) {
       if (L.tile == 2) k_fw_gemv1r<T, 2><<<L.count, 256, 0, st>>>(d, L.item_off);
