@@ -730,16 +730,14 @@ __global__ void __launch_bounds__(256) k_fw_gemv1(SD<T> d, int64_t item_off) {
 // warps of an item of two columns read its rows); a lane reads NR =
 // 16 bytes / sizeof(T) rows per step (rows t + 32 u, u < NR, coalesced per
 // column), so every thread has 128 bytes of L in flight (16 FP64 or 32 FP32
-// loads) without spills: FP64 80 registers (three CTAs per SM), FP32 64
-// (four).  Each lane keeps 8
-// column sums; the warps' sums of a column are added over the row groups in
-// a fixed order.  Levels whose fronts have few update rows thus run one CTA
+// loads) without spills at 80 registers (three CTAs per SM).  Each lane
+// keeps 8 column sums; the warps' sums of a column are added over the row
+// groups in a fixed order.  Levels whose fronts have few update rows thus run one CTA
 // per item and many rows per CTA, which amortises the CTA's start-up and
 // gather latency; levels with many update rows split the rows for
 // parallelism.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4)
-    k_bw_gemv1(SD<T> d, int64_t item_off, int per) {
+__global__ void __launch_bounds__(256, 3) k_bw_gemv1(SD<T> d, int64_t item_off, int per) {
   constexpr int NC = 8;                    // columns per warp
   constexpr int NR = 16 / (int)sizeof(T);  // rows per lane and step
   __shared__ T red[8][NC];
@@ -766,20 +764,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 4)
 #pragma unroll
   for (int q = 0; q < NC; ++q) acc[q] = T(0);
   if (nc > 0) {
+    // the rows' global indices are loaded one step ahead, so a step waits
+    // for one round trip (L and the gathered x together), not two
+    const int step = nrg * 32 * NR;
+    int32_t gn[NR];
+#pragma unroll
+    for (int u = 0; u < NR; ++u) {
+      const int i = rg * 32 * NR + lane + 32 * u;
+      gn[u] = frow[i < m ? i : 0];
+    }
 #pragma unroll 1
-    for (int t = rg * 32 * NR + lane; t < m; t += nrg * 32 * NR) {
+    for (int t = rg * 32 * NR + lane; t < m; t += step) {
       T xv[NR];
       T lv[NR][NC];
+      int32_t gc[NR];
+#pragma unroll
+      for (int u = 0; u < NR; ++u) {
+        gc[u] = gn[u];
+        const int i = t + step + 32 * u;
+        gn[u] = frow[i < m ? i : 0];
+      }
 #pragma unroll
       for (int u = 0; u < NR; ++u) {
         const int i = t + 32 * u;
         const bool ok = i < m;
-        const int ir = ok ? i : 0;
-        const T* p = Lb + ir;
+        const T* p = Lb + (ok ? i : 0);
 #pragma unroll
         for (int q = 0; q < NC; ++q, p += nf) lv[u][q] = (ok && q < nc) ? *p : T(0);
-        const int32_t g = frow[ir];
-        xv[u] = ok ? d.Y[d.ipos ? d.ipos[g] : g] : T(0);
+        xv[u] = ok ? d.Y[d.ipos ? d.ipos[gc[u]] : gc[u]] : T(0);
       }
 #pragma unroll
       for (int u = 0; u < NR; ++u)
