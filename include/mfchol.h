@@ -384,8 +384,9 @@ int mf_factor_numeric(mf_factor* f, const double* values,
  * are reported by the solve calls and mf_solve_check, never here. */
 int mf_factor_check(mf_factor* f, void* stream);
 
-/* Bound of the device waits on this factor -- the solve kernels' flag waits
- * and the small-front queue's waits for children -- in polls of about
+/* Bound of the device waits on this factor -- the solve kernels' waits for
+ * the values of earlier pivot blocks and the small-front queue's waits for
+ * children -- in polls of about
  * 128 ns (0 restores the default, 2^22 polls, about half a second).  A wait
  * that runs out records MF_ERR_TIMEOUT for the call in progress and lets
  * its kernel finish (no hang); the values of that call are then wrong, and
@@ -395,7 +396,8 @@ int mf_factor_check(mf_factor* f, void* stream);
  * at the next numeric call.  Errors: MF_ERR_INVALID for polls < 0. */
 int mf_factor_set_wait_limit(mf_factor* f, int32_t polls);
 
-/* Bytes of solve work memory (work vectors, right-hand-side staging, flags)
+/* Bytes of solve work memory (work vectors, right-hand-side staging, ticket
+ * counters)
  * that the factor currently holds on the device; 0 until a solve that
  * allocates (mf_solve, mf_solve_refined) has run. */
 int mf_factor_solve_work_bytes(const mf_factor* f, int64_t* bytes);
