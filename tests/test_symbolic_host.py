@@ -377,6 +377,31 @@ def test_schedules_cover_every_front_once(mf, variant, relax, small, queue):
         mf.mf_destroy(h)
 
 
+def test_schedules_of_tall_and_wide_fronts(mf):
+    """Fronts with more than 512 pivot columns and more than 2,048 update
+    rows: the one-right-hand-side update-row products then take every width
+    of the forward product (tile 2: at most 128 pivot columns, 1: at most
+    512, 0: wider) and every row split of the backward one (1, 2, 4 and 8
+    CTAs per 64-column block).  The host check verifies for every launch
+    that its width and split are ones its fronts allow, besides the
+    coverage of every front."""
+    h = mf.mf_create()
+    try:
+        cases = [(gen.laplacian_3d(48)[:2], gen.nd_perm((48, 48, 48)))]
+        rp, ci, _ = gen.q1_extruded(96, 48, 10, seed=1)
+        cases.append(((rp, ci), gen.nd_perm((97, 49, 11), split_axes=(0, 1), dofs=2)))
+        for (rp, ci), perm in cases:
+            s = mf.mf_symbolic_analyze(h, rp, ci, perm)
+            try:
+                info = mf.mf_symbolic_get_info(s)
+                assert info["max_k"] > 512 and info["max_front"] > 2048
+                mf.mf_symbolic_check(s)
+            finally:
+                mf.mf_symbolic_free(s)
+    finally:
+        mf.mf_destroy(h)
+
+
 def _fnv1a(data):
     h = 1469598103934665603
     for byte in data:
