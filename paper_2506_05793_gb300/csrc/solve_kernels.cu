@@ -1424,6 +1424,26 @@ __device__ __forceinline__ T transpose_sum32(T (&p)[32], int lane) {
   return p[0];
 }
 
+// Sum over the warp of 32 per-lane vectors of 16 values: lane l returns
+// sum_lanes p[l mod 16].  One exchange across the half-warps, then four
+// halving steps within each half (31 shuffles).
+template <typename T>
+__device__ __forceinline__ T transpose_sum16(T (&p)[16], int lane) {
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) p[jj] += __shfl_xor_sync(0xffffffffu, p[jj], 16);
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int jj = 0; jj < o; ++jj) {
+      const T send = hi ? p[jj] : p[jj + o];
+      const T keep = hi ? p[jj + o] : p[jj];
+      p[jj] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return p[0];
+}
+
 // Backward, one warp per front, pivot columns in blocks of 32 from the last:
 //   x_j = (y_j - sum_{i > j} L_ij x_i) / L_jj.
 // x of the update rows (ancestors' final values) and of solved pivot rows
@@ -1432,10 +1452,9 @@ __device__ __forceinline__ T transpose_sum32(T (&p)[32], int lane) {
 // hands column j0 + l's sum to lane l, and the triangle of the diagonal
 // block is solved with lane l owning column j0 + l (one shuffle per pivot).
 // ---------------------------------------------------------------------------
-// FP32 fits three CTAs per SM without spills.
+// Three CTAs per SM without spills.
 template <typename T, int H>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
-    k_bw_warp(SD<T> d, int64_t item_off, int64_t count) {
+__global__ void __launch_bounds__(256, 3) k_bw_warp(SD<T> d, int64_t item_off, int64_t count) {
   constexpr int LB = sizeof(T) == 8 ? 16 : 32;
   __shared__ T xs_all[8 * 32 * H];
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
@@ -1457,38 +1476,71 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     __syncwarp();
     for (int b = (k - 1) >> 5; b >= 0; --b) {
       const int j0 = 32 * b, bc = min(32, k - j0);
-      T p[32];
+      T acc;
+      if constexpr (sizeof(T) == 8) {
+        // FP64: two passes of 16 columns (16 sums and 16 loads per lane at
+        // a time), so the kernel fits three CTAs per SM; the loads and round
+        // trips per front are those of one pass over 32 columns
+        T part[2];
 #pragma unroll
-      for (int jj = 0; jj < 32; ++jj) p[jj] = T(0);
-      for (int i = j0 + bc + lane; i < nf; i += 32) {
-        const T xi = xs[i];
+        for (int hf = 0; hf < 2; ++hf) {
+          T p[16];
 #pragma unroll
-        for (int q0 = 0; q0 < 32; q0 += LB) {
-          T lv[LB];
+          for (int jj = 0; jj < 16; ++jj) p[jj] = T(0);
+          if (16 * hf < bc) {  // the same for the whole warp
+            for (int i = j0 + bc + lane; i < nf; i += 32) {
+              const T xi = xs[i];
+              T lv[16];
 #pragma unroll
-          for (int q = 0; q < LB; ++q) lv[q] = Lp[(int64_t)(j0 + min(q0 + q, bc - 1)) * nf + i];
+              for (int q = 0; q < 16; ++q)
+                lv[q] = Lp[(int64_t)(j0 + min(16 * hf + q, bc - 1)) * nf + i];
 #pragma unroll
-          for (int q = 0; q < LB; ++q) p[q0 + q] = fma(lv[q], xi, p[q0 + q]);
+              for (int q = 0; q < 16; ++q) p[q] = fma(lv[q], xi, p[q]);
+            }
+          }
+          part[hf] = transpose_sum16(p, lane);
         }
+        acc = lane < 16 ? part[0] : part[1];
+      } else {
+        T p[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) p[jj] = T(0);
+        for (int i = j0 + bc + lane; i < nf; i += 32) {
+          const T xi = xs[i];
+#pragma unroll
+          for (int q0 = 0; q0 < 32; q0 += LB) {
+            T lv[LB];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) lv[q] = Lp[(int64_t)(j0 + min(q0 + q, bc - 1)) * nf + i];
+#pragma unroll
+            for (int q = 0; q < LB; ++q) p[q0 + q] = fma(lv[q], xi, p[q0 + q]);
+          }
+        }
+        acc = transpose_sum32(p, lane);
       }
-      T acc = transpose_sum32(p, lane);
       const bool own = lane < bc;
       const int j = j0 + min(lane, bc - 1);
-      T lc[32];
-#pragma unroll
-      for (int ii = 0; ii < 32; ++ii) lc[ii] = Lp[(int64_t)j * nf + j0 + min(ii, bc - 1)];
-#pragma unroll
-      for (int ii = 0; ii < 32; ++ii)
-        if (!(own && ii > lane && ii < bc)) lc[ii] = T(0);
       const T yv = own ? yr[f.first + j] : T(0);
       const T rinv = own ? T(1) / Lp[(int64_t)j * nf + j] : T(0);
       T xj = T(0);
+      // the triangle of the diagonal block, rows from the last, in halves of
+      // 16 (lane: its column j, rows j0 + ii with ii > lane)
 #pragma unroll
-      for (int ii = 31; ii >= 0; --ii) {
-        if (ii < bc) {
-          const T xi = __shfl_sync(0xffffffffu, (yv - acc) * rinv, ii);
-          if (lane == ii) xj = xi;
-          acc = fma(lc[ii], xi, acc);
+      for (int h0 = 16; h0 >= 0; h0 -= 16) {
+        T lc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) lc[q] = Lp[(int64_t)j * nf + j0 + min(h0 + q, bc - 1)];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (!(own && h0 + q > lane && h0 + q < bc)) lc[q] = T(0);
+#pragma unroll
+        for (int q = 15; q >= 0; --q) {
+          const int ii = h0 + q;
+          if (ii < bc) {
+            const T xi = __shfl_sync(0xffffffffu, (yv - acc) * rinv, ii);
+            if (lane == ii) xj = xi;
+            acc = fma(lc[q], xi, acc);
+          }
         }
       }
       if (own) {
