@@ -1833,7 +1833,7 @@ cudaError_t init_t() {
 }
 
 template <typename T, int R>
-void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
+cudaError_t launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   const SD<T> d = make_sd<T>(a);
   if (L.kind == K_FW_LEVEL)
     k_fw_level<T, R><<<L.count, 256, fw_level_smem<T, R>(), st>>>(d, L.item_off,
@@ -1859,9 +1859,11 @@ void launch_r(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   } else {
     // CTAs per item: the launch's row split P (1, 2, 4 or 8)
     const int per = (int)L.tile;
-    if (per != 1 && per != 2 && per != 4 && per != 8) return;  // rejected on load
+    // the builder writes 1, 2, 4 or 8 and a loaded analysis is checked for it
+    if (per != 1 && per != 2 && per != 4 && per != 8) return cudaErrorInvalidValue;
     k_bw_gemv1<T><<<per * L.count, 256, 0, st>>>(d, L.item_off, per);
   }
+  return cudaSuccess;
 }
 
 template <typename T, int H>
@@ -1921,9 +1923,11 @@ cudaError_t launch_t(const Launch& L, const SolveArgs& a, cudaStream_t st) {
   if (L.kind != K_FW_LEVEL && L.kind != K_BW_LEVEL && L.kind != K_FW_GEMV &&
       L.kind != K_BW_GEMV && L.kind != K_FW_PINV && L.kind != K_BW_PINV)
     return cudaErrorInvalidValue;
-  if (a.nrhs <= 1) launch_r<T, 1>(L, a, st);
-  else if (a.nrhs <= 8) launch_r<T, 8>(L, a, st);
-  else launch_r<T, kSolveChunk>(L, a, st);
+  cudaError_t e;
+  if (a.nrhs <= 1) e = launch_r<T, 1>(L, a, st);
+  else if (a.nrhs <= 8) e = launch_r<T, 8>(L, a, st);
+  else e = launch_r<T, kSolveChunk>(L, a, st);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
