@@ -480,10 +480,10 @@ int mf_solve_noalloc(mf_factor* f, int32_t nrhs, const double* B, int64_t ldb,
                      double* X, int64_t ldx, void* stream);
 
 /* Diagnostic for the failure detection of the solve kernels (no paper
- * counterpart): runs the solve's bounded device wait, on one CTA, against a
- * flag that nothing sets, giving up after `polls` polls of about 128 ns each
- * (the solve itself uses 2^22 unless mf_factor_set_wait_limit says
- * otherwise).  The kernel records MF_ERR_TIMEOUT in a status
+ * counterpart): runs a bounded device wait of the kind the solve's chains
+ * use, on one CTA, against a flag that nothing sets, giving up after
+ * `polls` polls of about 128 ns each (the solve itself uses 2^22 unless
+ * mf_factor_set_wait_limit says otherwise).  The kernel records MF_ERR_TIMEOUT in a status
  * word and returns; the device stays usable.  Allocates and frees 256 bytes
  * of device memory and synchronizes `stream`.  Returns MF_ERR_TIMEOUT (the
  * expected outcome), MF_ERR_INVALID for polls < 1, MF_ERR_CUDA on a CUDA

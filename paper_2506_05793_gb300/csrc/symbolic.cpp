@@ -1099,7 +1099,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     }
   }
   // ---- solves.  Per level and sweep, fronts with k + m <= kWarpSolve go to
-  // the one-warp kernels (no flags, one launch per row class, 32 H rows with
+  // the one-warp kernels (no waits, one launch per row class, 32 H rows with
   // H = 2, 4, 8, 16) unless the class is too sparse to fill the GPU and the
   // front has a long pivot chain (k > 64) or more than 128 rows (one warp
   // would stream all its update rows alone); all other fronts are split into
@@ -1148,7 +1148,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
   std::vector<int32_t> big, pfronts;
   // SpTRSV variant 3: large fronts of the factor (those with kept diagonal
   // inverses) that the solve takes as level-kernel fronts use the
-  // partitioned inverse instead of the flag-chained pivot blocks
+  // partitioned inverse instead of the chained pivot blocks
   auto take_pinv = [&](std::vector<int32_t>& B, std::vector<int32_t>& P) {
     P.clear();
     if (!S.pinv) return;
@@ -1184,7 +1184,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
     }
     flatten(it);
     for (int c = 0; c < 4; ++c) add(S.fwsched, K_FW_WARP, lev, 2 << c, wcls[c], 0.0);
-    // pivot blocks (flag chains within a front), then the update-row blocks
+    // pivot blocks (chains within a front), then the update-row blocks
     // of the level as a streaming product that never waits
     add(S.fwsched, K_FW_LEVEL, lev, 0, it, 0.0);
     // one CTA per 64 update rows when every front has at most kFwNarrowK
@@ -1224,7 +1224,7 @@ void build_schedules(mf_symbolic& S, int small_max, int small_queue, const int32
       if (S.sn[x.s].m > 0) upd.push_back(x);
     for (int c = 0; c < 4; ++c) add(S.bwsched, K_BW_WARP, lev, 2 << c, wcls[c], 0.0);
     // update-row products of every column block first (no waiting), then the
-    // flag-chained triangles
+    // chained triangles
     // CTAs per 64-column item: the row split of the launch's tallest front
     {
       int maxm = 0;
