@@ -1336,6 +1336,23 @@ int check_schedules(const mf_symbolic& S, std::string& err) {
     }
     return at == hi;
   };
+  // the forward gather reads only update rows of the children's work
+  // vectors, so the pivot rows of every front's work vector are free: the
+  // chained pivot blocks pass their solved values through them
+  if (!S.v4 && S.Wsize > 0) {
+    std::vector<int32_t> owner(S.Wsize, -1);
+    for (int64_t s = 0; s < ns; ++s)
+      for (int64_t i = 0; i < (int64_t)S.sn[s].k + S.sn[s].m; ++i) {
+        const int64_t g = S.sn[s].woff + i;
+        if (g < 0 || g >= S.Wsize || owner[g] >= 0) return fail("work vectors overlap");
+        owner[g] = (int32_t)s;
+      }
+    for (int64_t g : S.ginv_src) {
+      if (g < 0 || g >= S.Wsize || owner[g] < 0) return fail("gather source outside a work vector");
+      const SnInfo& c = S.sn[owner[g]];
+      if (g - c.woff < c.k) return fail("gather source on a pivot row (a value slot)");
+    }
+  }
   for (const auto* schedp : {&S.fsched, &S.fsched_tc, &S.fwsched, &S.bwsched})
     for (const Launch& L : *schedp) {
       if (L.item_off < 0 || L.count < 0 || L.item_off + L.count > (int64_t)S.items.size())
