@@ -418,10 +418,10 @@ _MEMBERS = ["i8", "i8", ("v", 8), ("v", 4), ("v", 4), ("v", 4), ("v", 4), ("v", 
 _ROWIDX, _RELMAP, _ASRC, _ITEMS = 28, 29, 34, len(_MEMBERS)
 
 
-def _member_pos(data, index):
+def _member_pos(data, index, members=None):
     """Byte offset of member `index` (its element count for a vector)."""
     pos = 32
-    for m in _MEMBERS[:index]:
+    for m in (members or _MEMBERS)[:index]:
         if isinstance(m, tuple):
             cnt = int.from_bytes(data[pos:pos + 8], "little")
             pos += 8 + cnt * m[1]
@@ -476,6 +476,32 @@ def test_load_rejects_an_index_out_of_range(mf, handle, tmp_path, member, width,
     at = pos + 8 + (cnt // 2) * width
     data[at:at + width] = int(val).to_bytes(width, "little", signed=True)
     _load_fails(mf, handle, path, data, "index out of range")
+
+
+# the serialized members after Wsize, up to the forward gather sources:
+# items, fsched, fsched_tc, soff, split_rows, split_rows_b, max_large,
+# keep_inv, ioff, ninv, pinv, pinv_flops, arange, fwsched, bwsched, blkoff,
+# ginv_ptr, ginv_src (Launch records are 40 bytes, Item records 16)
+_TAIL = [("v", 16), ("v", 40), ("v", 40), ("v", 8), "i8", "i8", "i8", "i1", ("v", 8), "i8",
+         "i1", "i8", ("v", 16), ("v", 40), ("v", 40), ("v", 4), ("v", 8), ("v", 8)]
+_GINV_SRC = len(_MEMBERS) + len(_TAIL) - 1
+
+
+def test_load_rejects_a_gather_source_on_a_pivot_row(mf, handle, tmp_path):
+    """The chained pivot blocks of the solve pass their values through the
+    pivot rows of their fronts' work vectors, which the forward gather must
+    never read.  A saved analysis with one gather source moved onto a pivot
+    row (row 0 of the first front's work vector; still inside the vector,
+    so the range check passes) and a matching hash is refused by the
+    schedule check."""
+    path, data, _ = _saved(mf, handle, tmp_path)
+    pos = _member_pos(data, _GINV_SRC, _MEMBERS + _TAIL)
+    cnt = int.from_bytes(data[pos:pos + 8], "little")
+    assert cnt > 0
+    at = pos + 8 + (cnt // 2) * 8
+    assert int.from_bytes(data[at:at + 8], "little", signed=True) > 0
+    data[at:at + 8] = (0).to_bytes(8, "little", signed=True)
+    _load_fails(mf, handle, path, data, "value slot")
 
 
 def test_condensed_edge_cases(mf, handle, orc):
